@@ -1,0 +1,472 @@
+"""Pins of the FP64 oracle against facts outside the oracle itself.
+
+Each pin compares the oracle with something it does not share code with:
+exact values of the paper's Table 1 (tests/golden/wendland_table1.txt), the
+algebraically expanded polynomial of Eq. 2, library routines (numpy / scipy
+Cholesky, dense solve, eigenvalues, distance matrices), and invariants the
+equations imply (exact interpolation at the controls, telescoping over levels,
+zero displacement where psi = 0, the dense RBF solve of Eq. 9 / Eq. 10 as the
+limit of the greedy).
+
+The same pin functions run against deliberately broken builds of the oracle
+source at the end of this file, to show that each plausible mistake (a
+dropped term, a wrong sign, a transposed index, a skipped blend) fails at
+least one of them.
+"""
+import os
+import shutil
+from fractions import Fraction
+
+import numpy as np
+import pytest
+from scipy.spatial.distance import cdist
+
+import oracle
+from paper_2107_13887_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "wendland_table1.txt")
+
+# (1 - e)^4 (4 e + 1) multiplied out: 1 - 10 e^2 + 20 e^3 - 15 e^4 + 4 e^5
+C2_EXPANDED = [4.0, -15.0, 20.0, -10.0, 0.0, 1.0]
+
+
+def phi_expanded(eta):
+    eta = np.asarray(eta, dtype=np.float64)
+    return np.where(eta < 1.0, np.polyval(C2_EXPANDED, np.minimum(eta, 1.0)), 0.0)
+
+
+def psi_ref(xi):
+    xi = np.maximum(np.asarray(xi, dtype=np.float64), 0.0)
+    return np.where(xi < 1.0, 1.0 - xi, 0.0)
+
+
+def tiny_airfoil(n=48, displacement="bump", seed=0, R=(0.5,), eps=1e-6, layers=6):
+    return synth.airfoil_case(n, layers, displacement=displacement, seed=seed, R=R, eps=eps, D=2.0, k=0.0)
+
+
+def tiny_airfoil_k5():
+    c = tiny_airfoil(n=60, displacement="horns", R=(1.0, 0.2), eps=1e-6, layers=8)
+    c.k = 5.0
+    return c
+
+
+def tiny_wing(seed=0, R=(1.5, 0.4), eps=1e-4):
+    return synth.wing_case(16, 6, 3, displacement="ridge", seed=seed, R=R, eps=eps, D=1.0, k=4.0)
+
+
+# ------------------------------------------------------------------ pins
+# Each returns a list of failure strings (empty = pinned).
+
+
+def pin_table1(o):
+    bad = []
+    for line in open(GOLDEN):
+        if line.startswith("#"):
+            continue
+        name, e, v, _ = line.split()
+        eta = float(Fraction(e))
+        want = float(Fraction(v))
+        got = float(o.phi([eta], basis=name)[0])
+        if abs(got - want) > 4e-16:
+            bad.append(f"Table 1 {name} at eta={e}: {got!r} != {want!r}")
+    return bad
+
+
+def pin_phi_expanded(o):
+    eta = np.linspace(0.0, 1.3, 1001)
+    got = o.phi(eta)
+    err = np.abs(got - phi_expanded(eta)).max()
+    return [] if err < 1e-14 else [f"C2 differs from its expanded polynomial by {err:g}"]
+
+
+def pin_phi_smoothness(o):
+    # C2 (Eq. 2) is twice continuously differentiable with phi(0) = 1, phi'(0) = 0
+    # and phi, phi', phi'' vanishing at eta = 1
+    h = 1e-4
+    f = lambda e: float(o.phi([e])[0])
+    bad = []
+    if abs(f(0.0) - 1.0) > 0:
+        bad.append("phi(0) != 1")
+    if abs((f(h) - f(0.0)) / h) > 1e-3:
+        bad.append("phi'(0) != 0")
+    d1 = (f(1.0) - f(1.0 - h)) / h
+    d2 = (f(1.0) - 2 * f(1.0 - h) + f(1.0 - 2 * h)) / h**2
+    if abs(d1) > 1e-6 or abs(d2) > 1e-3:
+        bad.append(f"phi not C2 at eta=1 (d1={d1:g}, d2={d2:g})")
+    return bad
+
+
+def pin_psi(o):
+    xi = np.array([-0.5, 0.0, 0.25, 0.5, 0.999, 1.0, 1.5, 7.0])
+    err = np.abs(o.psi(xi) - psi_ref(xi)).max()
+    return [] if err == 0 else [f"psi differs from Section 4 by {err:g}"]
+
+
+def pin_cholesky(o):
+    rng = np.random.default_rng(1)
+    M = rng.standard_normal((12, 12))
+    A = M @ M.T + 12 * np.eye(12)
+    L = o.cholesky(A)
+    bad = []
+    if L is None:
+        return ["SPD matrix reported not positive definite"]
+    if np.abs(L - np.linalg.cholesky(A)).max() > 1e-12:
+        bad.append("Cholesky factor differs from numpy.linalg.cholesky")
+    B = rng.standard_normal((12, 3))
+    X = o.chol_solve(L, B)
+    if np.abs(X - np.linalg.solve(A, B)).max() > 1e-12:
+        bad.append("Cholesky solve differs from numpy.linalg.solve")
+    Aneg = A.copy()
+    Aneg[5, 5] = -1.0
+    if o.cholesky(Aneg) is not None:
+        bad.append("indefinite matrix accepted")
+    return bad
+
+
+def pin_eval_dense(o):
+    rng = np.random.default_rng(2)
+    bad = []
+    for dim in (2, 3):
+        xc = rng.uniform(-1, 1, (40, dim))
+        al = rng.standard_normal((40, dim))
+        xp = rng.uniform(-1, 1, (70, dim))
+        R = 0.9
+        want = phi_expanded(cdist(xp, xc) / R) @ al
+        got = o.evaluate(xc, al, xp, R)
+        if np.abs(got - want).max() > 1e-12:
+            bad.append(f"evaluation ({dim}D) differs from the dense product")
+    return bad
+
+
+def pin_spd(o):
+    # Wendland's theorem: C2 (and C4, C6) are positive definite in up to 3 dimensions
+    rng = np.random.default_rng(3)
+    bad = []
+    for dim in (2, 3):
+        x = rng.uniform(0, 1, (30, dim))
+        A = phi_expanded(cdist(x, x) / 0.8)
+        lam = np.linalg.eigvalsh(A)
+        if lam.min() <= 0:
+            bad.append(f"{dim}D Phi_cc not SPD (lambda_min={lam.min():g})")
+        if o.cholesky(A) is None:
+            bad.append(f"{dim}D Phi_cc rejected by the oracle Cholesky")
+    return bad
+
+
+U = 2.0**-53  # unit roundoff of IEEE double
+
+
+def _level_targets(case, res):
+    """dS_l for every level, recomputed from the oracle's (C, alpha) by dense
+    products, with an absolute bound on how far two summation orders of those
+    products can drift apart (8 n u max_i sum_j |alpha_j| phi_ij, summed over
+    the levels so far)."""
+    cur = case.dS.copy()
+    out, bounds = [], []
+    acc = 0.0
+    for l, R in enumerate(case.R):
+        out.append(cur.copy())
+        bounds.append(acc)
+        C = res.idx[l]
+        P = phi_expanded(cdist(case.xyz_s, case.xyz_s[C]) / R)
+        cur = cur - P @ res.alpha[l]
+        acc += 8 * max(len(C), 1) * U * ((P @ np.abs(res.alpha[l])).max() + np.abs(out[-1]).max())
+    return out, cur, bounds, acc
+
+
+def pin_greedy(o, case, first_rule=0):
+    """alpha solves Eq. 9 on the controls, each added control is the brute-force
+    argmax of Eq. 12, every level meets its tolerance, E is exact at the controls,
+    and the levels telescope to dS - E_final."""
+    res = o.greedy(case.xyz_s, case.dS, case.R, case.eps, first_rule=first_rule)
+    bad = []
+    S0 = float(np.sqrt((case.dS**2).sum(1)).max())
+    if abs(res.S0 - S0) > 0:
+        bad.append("S0 mismatch")
+    targets, final, bounds, final_bound = _level_targets(case, res)
+    L = len(case.R)
+    for l, R in enumerate(case.R):
+        C = list(res.idx[l])
+        tgt = targets[l]
+        if first_rule == 0 and C[0] != 0:
+            bad.append(f"level {l}: first control {C[0]} != 0")
+        if abs(res.smax[l] - np.sqrt((tgt**2).sum(1)).max()) > 1e-14 * S0 + 2 * bounds[l]:
+            bad.append(f"level {l}: smax mismatch")
+        # alpha against a library solve of Phi_cc alpha = dS_l(C)
+        A = phi_expanded(cdist(case.xyz_s[C], case.xyz_s[C]) / R)
+        a_ref = np.linalg.solve(A, tgt[C])
+        scale = np.abs(a_ref).max() + S0
+        if np.abs(res.alpha[l] - a_ref).max() > 1e-7 * scale:
+            bad.append(f"level {l}: alpha differs from numpy.linalg.solve")
+        # brute-force argmax at every step
+        for k in range(1, len(C)):
+            Ck = C[:k]
+            Ak = phi_expanded(cdist(case.xyz_s[Ck], case.xyz_s[Ck]) / R)
+            ak = np.linalg.solve(Ak, tgt[Ck])
+            E = tgt - phi_expanded(cdist(case.xyz_s, case.xyz_s[Ck]) / R) @ ak
+            key = (E**2).sum(1)
+            key[Ck] = -1.0
+            best = int(np.argmax(key))
+            if best != C[k]:
+                tie = abs(key[best] - key[C[k]]) <= 1e-9 * key[best]
+                if not tie:
+                    bad.append(f"level {l} step {k}: picked {C[k]}, brute-force argmax is {best}")
+                    break
+        # the level's final error is below its tolerance and ~0 at the controls
+        P = phi_expanded(cdist(case.xyz_s, case.xyz_s[C]) / R)
+        E = tgt - P @ res.alpha[l]
+        tau = case.eps ** ((l + 1) / L)
+        emax = np.sqrt((E**2).sum(1)).max() / S0
+        if len(C) < case.n_s and not emax < tau:
+            bad.append(f"level {l}: error {emax:g} not below tau {tau:g}")
+        # two summation orders of Eq. 12 differ by at most ~ n u sum_j |alpha_j| phi_ij
+        round_tol = (8 * len(C) * U * (P @ np.abs(res.alpha[l])).max() + 2 * bounds[l]) / S0
+        if abs(emax - res.emax[l]) > 1e-9 * emax + round_tol:
+            bad.append(f"level {l}: reported emax {res.emax[l]:g} != {emax:g}")
+        if np.abs(E[C]).max() > 1e-10 * S0:
+            bad.append(f"level {l}: not interpolating at the controls ({np.abs(E[C]).max():g})")
+    # telescoping: dS = sum_l Phi_sc^(l) alpha^(l) + E_final
+    if np.abs(final - res.E).max() > 1e-14 * S0 + final_bound:
+        bad.append("levels do not telescope to dS - E_final")
+    return bad
+
+
+def pin_dense_limit(o):
+    """With eps -> 0 every surface point becomes a control and the result is
+    the full RBF system of Eq. 9 / Eq. 10 solved densely."""
+    case = synth.airfoil_case(20, 5, displacement="bump", seed=4, R=(1.5,), eps=1e-300)
+    res = o.greedy(case.xyz_s, case.dS, case.R, case.eps)
+    bad = []
+    if sorted(res.idx[0].tolist()) != list(range(case.n_s)):
+        return ["dense limit did not select every surface point"]
+    A = phi_expanded(cdist(case.xyz_s, case.xyz_s) / 1.5)
+    a_dense = np.linalg.solve(A, case.dS)
+    a = np.zeros_like(a_dense)
+    a[res.idx[0]] = res.alpha[0]
+    if np.abs(a - a_dense).max() > 1e-8 * np.abs(a_dense).max():
+        bad.append("dense limit alpha differs from the full solve of Eq. 9")
+    dv = o.deform(res, case.xyz_s, case.R, case.xyz_v, case.d_v, k=0.0, D=2.0)
+    want = psi_ref(case.d_v.astype(np.float64) / 2.0)[:, None] * (
+        phi_expanded(cdist(case.xyz_v.astype(np.float64), case.xyz_s) / 1.5) @ a_dense
+    )
+    if np.abs(dv - want).max() > 1e-8 * np.abs(case.dS).max():
+        bad.append("dense limit volume update differs from psi * Phi_vs alpha (Eq. 10, Eq. 23)")
+    return bad
+
+
+def pin_deform(o, case):
+    """Eq. 19 / Eq. 23: zero where psi = 0 at every level; dS - E_final at
+    volume points placed on surface points with d = 0; otherwise equal to the
+    dense sum over levels of psi(d/D_l) Phi_vc alpha."""
+    res = o.greedy(case.xyz_s, case.dS, case.R, case.eps)
+    Dl = o.support_distances(res.smax, case.k, case.D)
+    bad = []
+    want_D = np.array([min(case.k * s, case.D) if case.k > 0 else case.D for s in res.smax])
+    if np.abs(Dl - want_D).max() > 0:
+        bad.append("support distances do not follow D_l = k max|dS_l| capped at D")
+    rng = np.random.default_rng(5)
+    pick = rng.choice(case.n_s, size=min(10, case.n_s), replace=False)
+    xv = np.concatenate([case.xyz_v.astype(np.float64), case.xyz_s[pick]])
+    dv_in = np.concatenate([case.d_v.astype(np.float64), np.zeros(len(pick))])
+    far = dv_in >= Dl.max()
+    out = o.deform(res, case.xyz_s, case.R, xv, dv_in, case.k, case.D)
+    if np.abs(out[far]).max(initial=0.0) != 0.0:
+        bad.append("points beyond every D_l moved")
+    want = np.zeros_like(out)
+    bound = 0.0
+    for l, R in enumerate(case.R):
+        w = psi_ref(dv_in / Dl[l]) if Dl[l] > 0 else np.zeros_like(dv_in)
+        C = res.idx[l]
+        P = phi_expanded(cdist(xv, case.xyz_s[C]) / R)
+        want += w[:, None] * (P @ res.alpha[l])
+        bound += 8 * max(len(C), 1) * U * (P @ np.abs(res.alpha[l])).max()
+    on = out[-len(pick):]
+    want_on = case.dS[pick] - res.E[pick]
+    _, _, _, tele_bound = _level_targets(case, res)
+    if np.abs(on - want_on).max() > 1e-14 * res.S0 + bound + tele_bound:
+        bad.append("volume points on the surface (d = 0) do not move by dS - E_final")
+    if np.abs(out - want).max() > 1e-14 * res.S0 + bound:
+        bad.append("volume update differs from the dense sum of Eq. 19 / Eq. 23")
+    return bad
+
+
+def all_pins(o):
+    bad = []
+    bad += pin_table1(o)
+    bad += pin_phi_expanded(o)
+    bad += pin_phi_smoothness(o)
+    bad += pin_psi(o)
+    bad += pin_cholesky(o)
+    bad += pin_eval_dense(o)
+    bad += pin_spd(o)
+    bad += pin_greedy(o, tiny_airfoil())
+    bad += pin_greedy(o, tiny_airfoil(n=60, displacement="horns", R=(1.0, 0.2), eps=1e-6))
+    bad += pin_greedy(o, tiny_wing())
+    bad += pin_dense_limit(o)
+    bad += pin_deform(o, tiny_airfoil_k5())
+    bad += pin_deform(o, tiny_wing())
+    return bad
+
+
+# ------------------------------------------------------------------ tests
+
+
+def test_table1_exact():
+    assert pin_table1(oracle) == []
+
+
+def test_phi_matches_expanded_polynomial():
+    assert pin_phi_expanded(oracle) == []
+
+
+def test_phi_smoothness():
+    assert pin_phi_smoothness(oracle) == []
+
+
+def test_psi_closed_form():
+    assert pin_psi(oracle) == []
+
+
+def test_cholesky_and_solve_vs_numpy():
+    assert pin_cholesky(oracle) == []
+
+
+def test_evaluation_vs_dense_product():
+    assert pin_eval_dense(oracle) == []
+
+
+def test_phi_cc_spd():
+    assert pin_spd(oracle) == []
+
+
+@pytest.mark.parametrize("disp", ["bump", "horns", "sinusoid", "pitch_heave"])
+def test_greedy_airfoil_single_level(disp):
+    assert pin_greedy(oracle, tiny_airfoil(n=64, displacement=disp, eps=1e-6)) == []
+
+
+def test_greedy_airfoil_two_levels():
+    assert pin_greedy(oracle, tiny_airfoil(n=80, displacement="horns", R=(1.0, 0.2), eps=1e-6)) == []
+
+
+def test_greedy_first_rule_argmax():
+    assert pin_greedy(oracle, tiny_airfoil(n=64, displacement="bump", eps=1e-5), first_rule=1) == []
+
+
+def test_greedy_wing_3d():
+    assert pin_greedy(oracle, tiny_wing()) == []
+
+
+def test_dense_limit():
+    assert pin_dense_limit(oracle) == []
+
+
+def test_deform_airfoil():
+    assert pin_deform(oracle, tiny_airfoil_k5()) == []
+
+
+def test_deform_wing():
+    assert pin_deform(oracle, tiny_wing()) == []
+
+
+def test_incremental_equals_scratch():
+    # appending one Cholesky row per control is the same arithmetic as
+    # refactorising from scratch, so the two solve modes agree bit for bit
+    c = tiny_airfoil(n=80, displacement="horns", R=(1.0, 0.2), eps=1e-6)
+    a = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, solve_mode=0)
+    b = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, solve_mode=1)
+    for l in range(2):
+        assert np.array_equal(a.idx[l], b.idx[l])
+        assert np.array_equal(a.alpha[l], b.alpha[l])
+
+
+def test_zero_displacement_gives_zero_levels():
+    c = tiny_airfoil()
+    r = oracle.greedy(c.xyz_s, np.zeros_like(c.dS), c.R, c.eps)
+    assert r.status == oracle.OK and all(len(i) == 0 for i in r.idx)
+    dv = oracle.deform(r, c.xyz_s, c.R, c.xyz_v, c.d_v, c.k, c.D)
+    assert not dv.any()
+
+
+def test_cap_reports_not_converged():
+    c = tiny_airfoil(n=64, eps=1e-8)
+    r = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, nc_cap=5)
+    assert r.status == oracle.ENOTCONV and len(r.idx[0]) == 5
+
+
+def test_duplicate_point_is_singular():
+    # two coincident surface points with different displacements make Phi_cc singular
+    c = tiny_airfoil(n=32)
+    xyz = np.concatenate([c.xyz_s, c.xyz_s[5:6]])
+    dS = np.concatenate([c.dS, c.dS[5:6] + 0.01])
+    with pytest.raises(RuntimeError, match="status 3"):
+        oracle.greedy(xyz, dS, c.R, 1e-12)
+
+
+def test_local_ice_controls_cluster_at_leading_edge():
+    # Section 5.1: for local ice the controls gather around the leading edge,
+    # for the sinusoid they spread along the chord
+    ice = synth.airfoil_case(400, 0, displacement="bump", seed=0, R=(0.5,), eps=1e-4)
+    r = oracle.greedy(ice.xyz_s, ice.dS, ice.R, ice.eps)
+    x_ice = ice.xyz_s[r.idx[0], 0]
+    sin = synth.airfoil_case(400, 0, displacement="sinusoid", seed=0, R=(0.5,), eps=1e-4)
+    r = oracle.greedy(sin.xyz_s, sin.dS, sin.R, sin.eps)
+    x_sin = sin.xyz_s[r.idx[0], 0]
+    near_le_surface = (ice.xyz_s[:, 0] < 0.1).mean()
+    assert (x_ice < 0.1).mean() > 2 * near_le_surface
+    assert (x_ice < 0.1).mean() > 2 * (x_sin < 0.1).mean()
+    assert all(((x_sin >= a) & (x_sin < a + 0.25)).any() for a in (0.0, 0.25, 0.5, 0.75))
+
+
+def test_openmp_threads_do_not_change_results():
+    c = tiny_airfoil(n=80, displacement="horns", R=(1.0, 0.2), eps=1e-6)
+    a = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, n_threads=1)
+    b = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, n_threads=4)
+    for l in range(2):
+        assert np.array_equal(a.idx[l], b.idx[l]) and np.array_equal(a.alpha[l], b.alpha[l])
+
+
+# ------------------------------------------------------------ mutation tests
+
+MUTATIONS = {
+    "drop (4 eta + 1) term": ("return (t2 * t2) * (4.0 * eta + 1.0);", "return (t2 * t2) * (4.0 * eta);"),
+    "wrong power in C2": ("return (t2 * t2) * (4.0 * eta + 1.0);", "return (t2 * t) * (4.0 * eta + 1.0);"),
+    "wrong sign in Eq. 12": ("E[i] = cur[i] - E[i];", "E[i] = cur[i] + E[i];"),
+    "psi not 1 - xi": ("return 1.0 - xi;", "return 1.0 - 0.5 * xi;"),
+    "argmax picks smallest": ("if (v > bestv) {", "if (bestv < 0.0 || v < bestv) {"),
+    "Cholesky sign": ("s = s - Lrow[k] * Lj[k];", "s = s + Lrow[k] * Lj[k];"),
+    "back substitution transposed": ("s = s - L[k * ld + i] * X[k * nrhs + r];",
+                                     "s = s - L[i * ld + k] * X[k * nrhs + r];"),
+    "next level ignores E": ("memcpy(cur, E, sizeof(double) * (size_t)(n_s * dim));\n    }",
+                             "memcpy(cur, dS, sizeof(double) * (size_t)(n_s * dim));\n    }"),
+    "support distance of level 0 only": ("double v = (k > 0.0) ? k * smax[l] : D;",
+                                         "double v = (k > 0.0) ? k * smax[0] : D;"),
+    "psi blend dropped": ("out[v * dim + k] = out[v * dim + k] + w * acc[k];",
+                          "out[v * dim + k] = out[v * dim + k] + acc[k];"),
+    "distance drops z": ("for (int k = 0; k < dim; ++k) {\n        double d = a[k] - b[k];",
+                         "for (int k = 0; k < 2; ++k) {\n        double d = a[k] - b[k];"),
+    "first control not point 0": ("int64_t first = 0;", "int64_t first = 1;"),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "rbfd_oracle.c")).read()
+    old, new = MUTATIONS[name]
+    assert src.count(old) >= 1, f"mutation anchor not found: {old!r}"
+    mutated = src.replace(old, new)
+    p = tmp_path / "mutant.c"
+    p.write_text(mutated)
+    lib = oracle.build(force=True, src=str(p), out=str(tmp_path / "libmutant.so"))
+    variant = oracle.load_variant(lib)
+    try:
+        bad = all_pins(variant)
+    except Exception as exc:  # a mutant that breaks a solve outright is caught too
+        bad = [repr(exc)]
+    assert bad, f"no pin caught the planted mistake: {name}"
+
+
+def test_unmutated_oracle_passes_every_pin():
+    assert all_pins(oracle) == []
