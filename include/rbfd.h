@@ -1,0 +1,169 @@
+/*
+ * rbfd.h -- C ABI of the GB300 library for multi-level greedy compact-support
+ * RBF mesh deformation with volume point reduction (Morelli, Bellosta,
+ * Guardone, "Efficient Radial Basis Function Mesh Deformation Methods for
+ * Aircraft Icing").
+ *
+ * The library runs every step of the method in its own CUDA kernels on one
+ * GPU.  Plain pointers and sizes only; no C++ or framework types.
+ *
+ * Conventions for every function:
+ *   - the return value is an rbfd_status; on failure rbfd_last_error() gives a
+ *     human-readable, thread-local message describing the most recent error;
+ *   - point arrays are row-major [n][dim] (x, y[, z] per point), dim 2 or 3;
+ *   - the caller owns every buffer it passes; the library copies what it keeps;
+ *   - buffers are host pointers unless rbfd_options.inputs_on_device is set
+ *     at rbfd_create, in which case every array argument of that mesh's calls
+ *     (create, deform) must be device memory of the current CUDA device;
+ *   - a mesh handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef RBFD_H
+#define RBFD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rbfd_status {
+    RBFD_OK = 0,
+    RBFD_EINVAL = 1,     /* bad argument: dim not 2/3, R <= 0, eps not in (0,1), NULL pointer, ... */
+    RBFD_ENOMEM = 2,     /* a device or host allocation failed */
+    RBFD_ESINGULAR = 3,  /* Phi_cc lost positive definiteness: coincident or near-coincident controls */
+    RBFD_ENOTCONV = 4,   /* the control cap was reached before eps; results are valid, e_max reports the error */
+    RBFD_ETIMEOUT = 5,   /* a bounded device-side or host-side wait hit its limit */
+    RBFD_EBUSY = 6,      /* serving admission refused for now (device memory); retry later */
+    RBFD_ECUDA = 7,      /* a CUDA runtime call failed (message in rbfd_last_error) */
+    RBFD_ESTATE = 8      /* call out of order (e.g. deform before greedy) */
+} rbfd_status;
+
+typedef enum rbfd_precision {
+    RBFD_FP64 = 0,  /* every step in IEEE double: the reference mode */
+    RBFD_MIXED = 1  /* evaluation sweeps on the FP32 pipe in double-float (FP32 pair)
+                       arithmetic; FP64 kept for the control-system growth, the
+                       iterative-refinement residual and the stop test */
+} rbfd_precision;
+
+typedef struct rbfd_options {
+    int precision;         /* rbfd_precision; default RBFD_MIXED */
+    int basis;             /* Wendland basis of Table 1: 0 = C0, 2 = C2 (Eq. 2, default), 4 = C4, 6 = C6 */
+    int first_point;       /* 0: surface point 0 starts every level (Section 3, default);
+                              1: the point of largest |dS_l| starts level l */
+    int inputs_on_device;  /* 0: host pointers (default); 1: device pointers */
+    int64_t nc_cap;        /* controls per level at most; 0 = min(n_s, 16384) */
+    void *stream;          /* cudaStream_t to run on; NULL = a stream the mesh creates */
+    int eps_absolute;      /* 0: eps is relative to max_i |dS_i| (default); 1: absolute length */
+    int refine_iters;      /* iterative-refinement sweeps at level close (default 3) */
+} rbfd_options;
+
+typedef struct rbfd_mesh rbfd_mesh;
+
+/* Fill *opt with the defaults listed above. */
+void rbfd_options_default(rbfd_options *opt);
+
+/*
+ * rbfd_create -- set up one surface for deformation (Section 2: surface
+ * points r_s and displacements dS = (dX_s, dY_s, dZ_s); Section 3: support
+ * radius R_l for each of the n_levels levels of the multi-level greedy
+ * selection, final tolerance eps on max_i |E_i| / max_i |dS_i|).
+ *
+ *   out      receives the new handle (set to NULL on failure)
+ *   dim      2 or 3
+ *   n_s      number of surface points, >= 1
+ *   xyz_s    [n_s][dim] surface coordinates (double)
+ *   dS       [n_s][dim] surface displacements (double)
+ *   n_levels number of greedy levels, >= 1
+ *   R        [n_levels] support radius per level, each > 0
+ *   eps      final tolerance, 0 < eps < 1 (relative unless opt->eps_absolute)
+ *   opt      options, or NULL for the defaults
+ *
+ * Copies the inputs to the device, Morton-orders the surface points and
+ * builds the point blocks the sweeps use.  Errors: RBFD_EINVAL, RBFD_ENOMEM,
+ * RBFD_ECUDA.
+ */
+int rbfd_create(rbfd_mesh **out, int dim, int64_t n_s, const double *xyz_s, const double *dS,
+                int n_levels, const double *R, double eps, const rbfd_options *opt);
+
+/*
+ * rbfd_greedy -- run the multi-level greedy surface point selection of
+ * Section 3 on the device: for each level l, start from one control, then
+ * repeatedly solve Phi_cc alpha = dS_l on the controls (Eq. 9), sweep the
+ * error E = dS_l - Phi_sc alpha over all surface points (Eq. 12), add the
+ * point of largest |E_i| until max |E_i| / max |dS_i| < eps^((l+1)/n_levels);
+ * then dS_{l+1} = E.  Blocks until done.  May be called again to re-run.
+ * Errors: RBFD_ESINGULAR, RBFD_ENOTCONV (results valid), RBFD_ETIMEOUT, RBFD_ECUDA.
+ */
+int rbfd_greedy(rbfd_mesh *m);
+
+/*
+ * rbfd_get_level -- results of level l (0-based) after rbfd_greedy.
+ *   n_c    receives the number of controls (may be NULL)
+ *   idx    [n_c] receives their surface indices in selection order (may be NULL)
+ *   alpha  [n_c][dim] receives their weights (may be NULL)
+ *   e_max  receives max_i |E_i| / max_i |dS_i| after the level (may be NULL)
+ * Call first with idx = alpha = NULL to learn n_c.  Host pointers always.
+ * Errors: RBFD_EINVAL (l out of range), RBFD_ESTATE (no greedy yet).
+ */
+int rbfd_get_level(rbfd_mesh *m, int l, int64_t *n_c, int64_t *idx, double *alpha, double *e_max);
+
+/* Number of levels the greedy produced (0 when every dS is zero). */
+int rbfd_num_levels(rbfd_mesh *m, int *n_levels);
+
+/*
+ * rbfd_level_info -- per-level scalars: R_l, max_i |dS_l,i| (the quantity the
+ * support distance D_l = k max |dS_l| of Section 4 uses) and the level's
+ * tolerance tau_l.  Any output may be NULL.
+ */
+int rbfd_level_info(rbfd_mesh *m, int l, double *R, double *smax, double *tau);
+
+typedef struct rbfd_stats {
+    double greedy_ms;        /* device time of the last rbfd_greedy (CUDA events) */
+    double deform_ms;        /* device time of the last rbfd_deform */
+    int64_t greedy_steps;    /* control additions over all levels */
+    int64_t pairs_useful;    /* greedy + deform point/control pairs with |r - r_c| < R */
+    int64_t pairs_visited;   /* pairs the kernels evaluated (a superset of the useful ones) */
+    int64_t deform_points;   /* volume points updated at least at one level (sum over levels) */
+    int64_t refine_sweeps;   /* iterative-refinement sweeps run at level close */
+    int64_t confirm_resumes; /* times a level-close confirm sweep reopened the greedy */
+} rbfd_stats;
+
+int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st);
+
+/*
+ * rbfd_deform -- volume update of Eq. 19 with the wall-distance blending of
+ * Eq. 23 (Section 4):
+ *     out_v = sum_l psi(d_v / D_l) sum_j alpha_j^(l) phi(|r_v - r_cj^(l)| / R_l)
+ * with psi(xi) = 1 - xi on [0, 1), 0 beyond, and D_l = k * max_i |dS_l,i|
+ * (capped at D when D > 0) if k > 0, else D_l = D.  Only volume points with
+ * d_v < D_l take part in level l (volume point reduction).
+ *
+ *   n_v    number of volume points (0 allowed)
+ *   xyz_v  [n_v][dim] volume coordinates (float)
+ *   d_v    [n_v] wall distance of each volume point (float, negative read as 0)
+ *   D, k   support distance and volume reduction factor (>= 0; not both 0)
+ *   out    [n_v][dim] receives the displacement of each volume point (float)
+ *
+ * Errors: RBFD_EINVAL, RBFD_ESTATE (no greedy yet), RBFD_ENOMEM, RBFD_ECUDA.
+ */
+int rbfd_deform(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v, double D, double k,
+                float *out);
+
+/* Same as rbfd_deform with double coordinates, distances and output. */
+int rbfd_deform_f64(rbfd_mesh *m, int64_t n_v, const double *xyz_v, const double *d_v, double D, double k,
+                    double *out);
+
+/* Release every device and host resource of the mesh.  NULL is allowed. */
+int rbfd_destroy(rbfd_mesh *m);
+
+/* Message of the most recent failing call on this thread ("" if none). */
+const char *rbfd_last_error(void);
+
+/* Library version string. */
+const char *rbfd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBFD_H */

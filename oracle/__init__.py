@@ -65,7 +65,7 @@ def _bind(path: str):
     lib.orc_greedy.restype = ctypes.c_int
     lib.orc_greedy.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp, ctypes.c_int, dp, ctypes.c_double,
                                ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                               i64p, i64p, dp, dp, dp, dp, dp]
+                               i64p, i64p, dp, dp, dp, dp, dp, dp]
     lib.orc_support_distances.restype = None
     lib.orc_support_distances.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp]
     lib.orc_deform.restype = ctypes.c_int
@@ -170,6 +170,7 @@ class GreedyResult:
     gap: np.ndarray  # per level: smallest relative top-2 key gap seen
     E: np.ndarray  # final error [n_s, dim]
     S0: float
+    step_gap: list = None  # per level: [nc] relative top-2 gap of the step that picked control k (k >= 1)
 
     @property
     def n_levels(self):
@@ -193,16 +194,19 @@ def greedy(xyz_s, dS, R, eps, basis="C2", nc_cap=None, first_rule=0, solve_mode=
     emax = np.zeros(L)
     gap = np.zeros(L)
     E = np.zeros((n_s, dim))
+    sg = np.ones(L * cap)
     rc = lib.orc_greedy(dim, n_s, _dp(xyz_s), _dp(dS), L, _dp(R), float(eps), BASIS[basis], cap,
                         int(first_rule), int(solve_mode), int(n_threads), _ip(nc), _ip(idx), _dp(alpha),
-                        _dp(smax), _dp(emax), _dp(E), _dp(gap))
+                        _dp(smax), _dp(emax), _dp(E), _dp(gap), _dp(sg))
     if rc in (EINVAL, ENOMEM, ESINGULAR):
         raise RuntimeError(f"oracle greedy failed with status {rc}")
     idx = idx.reshape(L, cap)
     alpha = alpha.reshape(L, cap, dim)
     S0 = float(np.sqrt((dS * dS).sum(1)).max()) if n_s else 0.0
+    sg = sg.reshape(L, cap)
     return GreedyResult(rc, [idx[l, : nc[l]].copy() for l in range(L)],
-                        [alpha[l, : nc[l]].copy() for l in range(L)], smax, emax, gap, E, S0)
+                        [alpha[l, : nc[l]].copy() for l in range(L)], smax, emax, gap, E, S0,
+                        [sg[l, : nc[l]].copy() for l in range(L)])
 
 
 def support_distances(smax, k: float, D: float, lib=None):

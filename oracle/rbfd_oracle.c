@@ -195,7 +195,10 @@ void orc_eval(int dim, int basis, double R, int64_t n_c, const double *xyz_c, co
  * smax_out[l] = max_i |dS_l,i|, emax_out[l] = max_i |E_i| / S0 after the level,
  * gap_out[l] (optional) the smallest relative gap (key1 - key2) / key1 between
  * the two largest keys over all argmax steps of the level.  E_out (optional)
- * receives the final error E after the last level.
+ * receives the final error E after the last level.  step_gap_out (optional,
+ * [n_levels * nc_cap]) receives, at [l*nc_cap + k], the relative gap between
+ * the two largest keys of the step that selected control k (k >= 1) and, at
+ * [l*nc_cap], the gap of the level's final (stopping) sweep.
  *
  * A level that reaches nc_cap controls ends there, and the next level takes
  * its error.  Returns ORC_OK, ORC_ENOTCONV (the last level's error is not
@@ -205,7 +208,7 @@ int orc_greedy(int dim, int64_t n_s, const double *xyz_s, const double *dS, int 
                const double *R, double eps, int basis, int64_t nc_cap, int first_rule,
                int solve_mode, int n_threads, int64_t *nc_out, int64_t *idx_out,
                double *alpha_out, double *smax_out, double *emax_out, double *E_out,
-               double *gap_out)
+               double *gap_out, double *step_gap_out)
 {
     if ((dim != 2 && dim != 3) || n_s < 1 || n_levels < 1 || !(eps > 0.0) || nc_cap < 1 ||
         !xyz_s || !dS || !R || !nc_out || !idx_out || !alpha_out || !smax_out || !emax_out)
@@ -296,10 +299,12 @@ int orc_greedy(int dim, int64_t n_s, const double *xyz_s, const double *dS, int 
                     second = v;
                 }
             }
+            double g = 1.0;
             if (best >= 0 && bestv > 0.0 && second >= 0.0) {
-                double g = (bestv - second) / bestv;
+                g = (bestv - second) / bestv;
                 if (g < gap_min) gap_min = g;
             }
+            if (step_gap_out) step_gap_out[(int64_t)l * nc_cap + (n < nc_cap ? n : 0)] = g;
             if (best < 0 || sqrt(bestv) / S0 < tau) break;
             if (n == nc_cap) break; /* cap reached: the level ends unconverged */
             /* append the new control: row n of Phi_cc and of its Cholesky factor */

@@ -1,0 +1,243 @@
+// common.cuh -- device helpers shared by the rbfd CUDA kernels (sm_103a).
+//
+// Contents:
+//   * status codes mirrored from include/rbfd.h;
+//   * IEEE double evaluation of the Wendland basis (Table 1, Eq. 2) with every
+//     product and sum separately rounded (no FMA contraction), so FP64 mode
+//     evaluates eta and phi exactly as the textbook formula is written;
+//   * double-float ("df") arithmetic: an unevaluated sum hi + lo of two
+//     floats carrying ~44-48 significant bits, built from the classical
+//     error-free transformations (Knuth's TwoSum, Dekker's Fast2Sum and the
+//     FMA-based TwoProduct).  It runs on the FP32 pipe, which on GB300 issues
+//     ~64x more operations per clock than the FP64 pipe;
+//   * warp / block reduction helpers and the (key, index) argmax order used
+//     by the greedy selection (largest key, then lowest surface index).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rbfd.h"
+
+namespace rbfd {
+
+constexpr int kPB = 128;      // surface / volume points per block (one per thread)
+constexpr int kTile = 128;    // controls staged in shared memory per tile
+constexpr int kMaxBasis = 6;
+
+// ------------------------------------------------------------------ FP64 path
+
+// phi(eta) of Table 1 in IEEE double, each operation rounded on its own.
+template <int BASIS>
+__device__ __forceinline__ double phi_f64(double eta) {
+    if (eta >= 1.0) return 0.0;
+    double t = __dsub_rn(1.0, eta);
+    double t2 = __dmul_rn(t, t);
+    if (BASIS == 0) return t2;
+    double t4 = __dmul_rn(t2, t2);
+    if (BASIS == 2) return __dmul_rn(t4, __dadd_rn(__dmul_rn(4.0, eta), 1.0));
+    if (BASIS == 4) {
+        double t6 = __dmul_rn(t4, t2);
+        double q = __dadd_rn(__dadd_rn(__dmul_rn(__dmul_rn(35.0 / 3.0, eta), eta), __dmul_rn(6.0, eta)), 1.0);
+        return __dmul_rn(t6, q);
+    }
+    double t8 = __dmul_rn(t4, t4);
+    double e2 = __dmul_rn(eta, eta);
+    double q = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(__dmul_rn(32.0, e2), eta), __dmul_rn(25.0, e2)),
+                                   __dmul_rn(8.0, eta)),
+                         1.0);
+    return __dmul_rn(t8, q);
+}
+
+// |a - b|_2 summed in coordinate order, no contraction.
+template <int DIM>
+__device__ __forceinline__ double dist_f64(double ax, double ay, double az, double bx, double by, double bz) {
+    double dx = __dsub_rn(ax, bx);
+    double s = __dmul_rn(dx, dx);
+    double dy = __dsub_rn(ay, by);
+    s = __dadd_rn(s, __dmul_rn(dy, dy));
+    if (DIM == 3) {
+        double dz = __dsub_rn(az, bz);
+        s = __dadd_rn(s, __dmul_rn(dz, dz));
+    }
+    return __dsqrt_rn(s);
+}
+
+// ------------------------------------------------------------ double-float
+
+struct df {
+    float hi, lo;
+};
+
+// Knuth TwoSum: s + e == a + b exactly.
+__device__ __forceinline__ df two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+// Dekker Fast2Sum (requires |a| >= |b| or a == 0).
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+
+// TwoProduct with one fused multiply-add: p + e == a * b exactly.
+__device__ __forceinline__ df two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    return {p, e};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    df t = two_sum(a.lo, b.lo);
+    float lo = __fadd_rn(s.lo, t.hi);
+    s = fast_two_sum(s.hi, lo);
+    lo = __fadd_rn(s.lo, t.lo);
+    return fast_two_sum(s.hi, lo);
+}
+
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+    df p = two_prod(a.hi, b.hi);
+    float lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+    return fast_two_sum(p.hi, lo);
+}
+
+__device__ __forceinline__ df df_sqr(df a) {
+    df p = two_prod(a.hi, a.hi);
+    float lo = __fmaf_rn(__fmul_rn(2.0f, a.hi), a.lo, p.lo);
+    return fast_two_sum(p.hi, lo);
+}
+
+// sqrt of a double-float: a single-precision estimate s = a.hi * rsqrt(a.hi),
+// then one Newton correction s + (a - s^2) / (2 s) with the residual formed
+// exactly through TwoProduct.
+__device__ __forceinline__ df df_sqrt(df a) {
+    if (!(a.hi > 0.0f)) return {0.0f, 0.0f};
+    float y = rsqrtf(a.hi);
+    float s = __fmul_rn(a.hi, y);
+    df p = two_prod(s, s);
+    float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p.hi), p.lo), a.lo);
+    float c = __fmul_rn(r, __fmul_rn(0.5f, y));
+    return fast_two_sum(s, c);
+}
+
+__device__ __forceinline__ df df_from_double(double x) {
+    float hi = __double2float_rn(x);
+    float lo = __double2float_rn(x - (double)hi);
+    return {hi, lo};
+}
+
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+// phi(eta) of Table 1 in double-float; eta >= 1 gives exactly 0.
+template <int BASIS>
+__device__ __forceinline__ df phi_df(df eta) {
+    if (!(eta.hi < 1.0f)) return {0.0f, 0.0f};
+    df t = df_add({1.0f, 0.0f}, df_neg(eta));
+    df t2 = df_sqr(t);
+    if (BASIS == 0) return t2;
+    df t4 = df_sqr(t2);
+    if (BASIS == 2) {
+        df q = df_add({__fmul_rn(4.0f, eta.hi), __fmul_rn(4.0f, eta.lo)}, {1.0f, 0.0f});
+        return df_mul(t4, q);
+    }
+    if (BASIS == 4) {
+        df t6 = df_mul(t4, t2);
+        df e2 = df_sqr(eta);
+        const df c35_3 = {11.666666984558105f, -3.1789145e-07f};  // 35/3 as hi + lo
+        df q = df_add(df_add(df_mul(c35_3, e2), {__fmul_rn(6.0f, eta.hi), __fmul_rn(6.0f, eta.lo)}), {1.0f, 0.0f});
+        return df_mul(t6, q);
+    }
+    df t8 = df_sqr(t4);
+    df e2 = df_sqr(eta);
+    df e3 = df_mul(e2, eta);
+    df q = df_add(df_add(df_add({__fmul_rn(32.0f, e3.hi), __fmul_rn(32.0f, e3.lo)},
+                                df_mul({25.0f, 0.0f}, e2)),
+                         {__fmul_rn(8.0f, eta.hi), __fmul_rn(8.0f, eta.lo)}),
+                  {1.0f, 0.0f});
+    return df_mul(t8, q);
+}
+
+// L2-coherent load of a double4 written by another block of the same launch.
+__device__ __forceinline__ double4 ldcg_d4(const double4 *p) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    double2 a = __ldcg(q), b = __ldcg(q + 1);
+    return make_double4(a.x, a.y, b.x, b.y);
+}
+
+// ------------------------------------------------------------------ argmax
+
+// Order of the greedy selection: larger key first, then lower surface index.
+__device__ __forceinline__ bool better(double ka, int ia, double kb, int ib) {
+    return (ka > kb) || (ka == kb && ia < ib && ia >= 0) || (ib < 0 && ia >= 0);
+}
+
+__device__ __forceinline__ void warp_argmax(double &k, int &i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double k2 = __shfl_xor_sync(0xffffffffu, k, o);
+        int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+        if (better(k2, i2, k, i)) {
+            k = k2;
+            i = i2;
+        }
+    }
+}
+
+// Block-wide argmax over (key, idx); every thread gets the result.
+// scratch must hold 2 * 32 entries.
+__device__ __forceinline__ void block_argmax(double &k, int &i, double *sk, int *si) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    warp_argmax(k, i);
+    __syncthreads();
+    if (lane == 0) {
+        sk[w] = k;
+        si[w] = i;
+    }
+    __syncthreads();
+    if (w == 0) {
+        k = lane < nw ? sk[lane] : -1.0;
+        i = lane < nw ? si[lane] : -1;
+        warp_argmax(k, i);
+        if (lane == 0) {
+            sk[0] = k;
+            si[0] = i;
+        }
+    }
+    __syncthreads();
+    k = sk[0];
+    i = si[0];
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------- greedy state
+
+// Device-resident state of one greedy level (lives in device memory; a
+// pinned host mirror is refreshed once per batch of steps).
+struct GreedyState {
+    int n;            // controls in the current level
+    int stop;         // 1 once the level's stop test passed or a limit was hit
+    int status;       // RBFD_OK, RBFD_ESINGULAR, RBFD_ENOTCONV
+    int best;         // sorted position of the current argmax point (-1 if none)
+    int best_orig;    // its original surface index
+    int pad;
+    double best_key;  // |E|^2 at the argmax
+    double second_key;
+    double min_gap;   // smallest (key1 - key2) / key1 seen this level
+    double emax;      // sqrt(best_key) / S0 of the last sweep
+    unsigned int pb_done;   // last-block-done counter of the sweep
+    unsigned int red_done;  // last-block-done counter of reductions
+};
+
+}  // namespace rbfd

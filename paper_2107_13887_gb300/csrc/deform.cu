@@ -1,0 +1,494 @@
+// deform.cu -- volume update with volume point reduction (Section 4, Eq. 19
+// and Eq. 23):
+//
+//   dV_v = sum_l psi(d_v / D_l) sum_j alpha_j^(l) phi(|r_v - r_cj^(l)| / R_l),
+//   psi(xi) = 1 - xi on [0, 1), 0 beyond,   D_l = k max_i |dS_l,i| (capped at D).
+//
+// Steps: (1) keep only the volume points with d < max_l D_l (stream
+// compaction); (2) Morton-sort those points so that a block of 128
+// consecutive points is spatially compact; (3) per level, compact the sorted
+// points further to d < D_l and run the fused evaluation: each block takes the
+// controls of every cell of the level's uniform grid (cell size R_l) that
+// overlaps its bounding box grown by R_l, stages them tile by tile in shared
+// memory, and accumulates alpha phi for its points; (4) scatter the blended
+// displacement back to the caller's order.
+#include <algorithm>
+#include <cmath>
+
+#include "internal.h"
+
+namespace rbfd {
+
+namespace {
+
+constexpr int kThreads = 128;
+
+inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
+
+__global__ void k_vol_pack(const void *__restrict__ xyz, const void *__restrict__ d, int64_t n, int dim, int f64,
+                           double4 *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x, y, z = 0.0, w;
+    if (f64) {
+        const double *p = static_cast<const double *>(xyz) + i * dim;
+        x = p[0];
+        y = p[1];
+        if (dim == 3) z = p[2];
+        w = static_cast<const double *>(d)[i];
+    } else {
+        const float *p = static_cast<const float *>(xyz) + i * dim;
+        x = p[0];
+        y = p[1];
+        if (dim == 3) z = p[2];
+        w = static_cast<const float *>(d)[i];
+    }
+    out[i] = make_double4(x, y, z, w < 0.0 ? 0.0 : w);
+}
+
+__global__ void k_flag_below(const double4 *__restrict__ p, const uint32_t *__restrict__ idx, int64_t n, double D,
+                             uint32_t *__restrict__ flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double d = p[idx ? idx[i] : i].w;
+    flag[i] = (d < D) ? 1u : 0u;
+}
+
+__global__ void k_compact(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pos, int64_t n,
+                          uint32_t *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (flag[i]) out[pos[i]] = (uint32_t)i;
+}
+
+__global__ void k_bbox_idx(const double4 *__restrict__ p, const uint32_t *__restrict__ idx, int64_t n,
+                           double *__restrict__ part) {
+    __shared__ double s[6][32];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double4 q = p[idx[i]];
+        lo[0] = fmin(lo[0], q.x); lo[1] = fmin(lo[1], q.y); lo[2] = fmin(lo[2], q.z);
+        hi[0] = fmax(hi[0], q.x); hi[1] = fmax(hi[1], q.y); hi[2] = fmax(hi[2], q.z);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmax(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) {
+            s[k][w] = lo[k];
+            s[3 + k][w] = hi[k];
+        }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double v = s[threadIdx.x][0];
+        for (int j = 1; j < (int)(blockDim.x >> 5); ++j)
+            v = threadIdx.x < 3 ? fmin(v, s[threadIdx.x][j]) : fmax(v, s[threadIdx.x][j]);
+        part[blockIdx.x * 6 + threadIdx.x] = v;
+    }
+}
+
+__global__ void k_bbox_reduce(const double *__restrict__ part, int nb, double *__restrict__ out) {
+    if (threadIdx.x >= 6) return;
+    double v = part[threadIdx.x];
+    for (int b = 1; b < nb; ++b) v = threadIdx.x < 3 ? fmin(v, part[b * 6 + threadIdx.x]) : fmax(v, part[b * 6 + threadIdx.x]);
+    out[threadIdx.x] = v;
+}
+
+__global__ void k_gather_vol(const double4 *__restrict__ p, const uint32_t *__restrict__ order, int64_t n,
+                             double4 *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = p[order[i]];
+}
+
+__global__ void k_gather_u32(const uint32_t *__restrict__ src, const uint32_t *__restrict__ idx, int64_t n,
+                             uint32_t *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = src[idx[i]];
+}
+
+__global__ void k_scatter_out(const double4 *__restrict__ acc, const uint32_t *__restrict__ orig, int64_t n,
+                              int dim, int f64, void *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double4 a = acc[i];
+    int64_t o = orig[i];
+    if (f64) {
+        double *q = static_cast<double *>(out) + o * dim;
+        q[0] = a.x;
+        q[1] = a.y;
+        if (dim == 3) q[2] = a.z;
+    } else {
+        float *q = static_cast<float *>(out) + o * dim;
+        q[0] = (float)a.x;
+        q[1] = (float)a.y;
+        if (dim == 3) q[2] = (float)a.z;
+    }
+}
+
+__device__ __forceinline__ uint32_t blk_excl_scan(uint32_t v, uint32_t *sw, uint32_t *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sw[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = lane < nw ? sw[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) sw[lane] = t;
+    }
+    __syncthreads();
+    uint32_t before = (w > 0 ? sw[w - 1] : 0u) + x - v;
+    *total = sw[nw - 1];
+    __syncthreads();
+    return before;
+}
+
+struct VolArgs {
+    int64_t n_list;
+    const uint32_t *list;   // sorted positions of the points with d < D_l
+    const double4 *vpos;    // sorted points (x, y, z, d)
+    double4 *vacc;          // accumulated displacement per sorted point
+    const double4 *cx, *alpha;
+    const uint32_t *cell_start, *cell_ctrl;
+    double3 g0;
+    double h, R, Dl;
+    int3 gd;
+    float invR_hi, invR_lo;
+    unsigned long long *pairs;
+};
+
+template <int DIM, int BASIS, int MODE>
+__global__ void __launch_bounds__(kThreads) k_vol_sweep(VolArgs a) {
+    __shared__ double sb[6][kThreads / 32];
+    __shared__ uint32_t s_start[kThreads], s_off[kThreads], sw[32];
+    __shared__ double t64[6][kTile];
+    __shared__ float t32[12][kTile];
+    const int tid = threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * kThreads + tid;
+    const bool valid = i < a.n_list;
+    const uint32_t s = valid ? a.list[i] : 0u;
+    const double4 P = valid ? a.vpos[s] : make_double4(0, 0, 0, 0);
+    // block bounding box
+    double lo[3] = {valid ? P.x : INFINITY, valid ? P.y : INFINITY, valid ? P.z : INFINITY};
+    double hi[3] = {valid ? P.x : -INFINITY, valid ? P.y : -INFINITY, valid ? P.z : -INFINITY};
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmax(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    if ((tid & 31) == 0)
+        for (int k = 0; k < 3; ++k) {
+            sb[k][tid >> 5] = lo[k];
+            sb[3 + k][tid >> 5] = hi[k];
+        }
+    __syncthreads();
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = sb[k][0];
+        hi[k] = sb[3 + k][0];
+        for (int q = 1; q < kThreads / 32; ++q) {
+            lo[k] = fmin(lo[k], sb[k][q]);
+            hi[k] = fmax(hi[k], sb[3 + k][q]);
+        }
+    }
+    auto cidx = [&](double v, double g, int nmax) {
+        double f = floor((v - g) / a.h);
+        f = fmin(fmax(f, 0.0), (double)(nmax - 1));
+        return (int)f;
+    };
+    const int ix0 = cidx(lo[0] - a.R, a.g0.x, a.gd.x), ix1 = cidx(hi[0] + a.R, a.g0.x, a.gd.x);
+    const int iy0 = cidx(lo[1] - a.R, a.g0.y, a.gd.y), iy1 = cidx(hi[1] + a.R, a.g0.y, a.gd.y);
+    const int iz0 = DIM == 3 ? cidx(lo[2] - a.R, a.g0.z, a.gd.z) : 0;
+    const int iz1 = DIM == 3 ? cidx(hi[2] + a.R, a.g0.z, a.gd.z) : 0;
+    const int nx = ix1 - ix0 + 1, ny = iy1 - iy0 + 1, nz = iz1 - iz0 + 1;
+    const int ncr = nx * ny * nz;
+
+    // point coordinates: FP64 absolute, or double-float relative to the box corner
+    df qx{0, 0}, qy{0, 0}, qz{0, 0};
+    if (MODE == 1) {
+        qx = df_from_double(P.x - lo[0]);
+        qy = df_from_double(P.y - lo[1]);
+        qz = df_from_double(P.z - lo[2]);
+    }
+    const df invR = {a.invR_hi, a.invR_lo};
+    double acc64[3] = {0, 0, 0};
+    df acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+    unsigned useful = 0;
+    unsigned long long visited = 0;
+    for (int cb = 0; cb < ncr; cb += kThreads) {
+        const int c = cb + tid;
+        uint32_t cnt = 0, st0 = 0;
+        if (c < ncr) {
+            int ix = ix0 + c % nx, iy = iy0 + (c / nx) % ny, iz = iz0 + c / (nx * ny);
+            int cell = (iz * a.gd.y + iy) * a.gd.x + ix;
+            st0 = a.cell_start[cell];
+            cnt = a.cell_start[cell + 1] - st0;
+        }
+        uint32_t T;
+        uint32_t off = blk_excl_scan(cnt, sw, &T);
+        s_start[tid] = st0;
+        s_off[tid] = off;
+        __syncthreads();
+        for (uint32_t w0 = 0; w0 < T; w0 += kTile) {
+            const int m = (int)min((uint32_t)kTile, T - w0);
+            if (tid < m) {
+                uint32_t q = w0 + tid;
+                int l = 0, r = kThreads;  // last k with s_off[k] <= q
+                while (r - l > 1) {
+                    int mid = (l + r) >> 1;
+                    if (s_off[mid] <= q) l = mid;
+                    else r = mid;
+                }
+                uint32_t j = a.cell_ctrl[s_start[l] + (q - s_off[l])];
+                double4 cc = a.cx[j], al = a.alpha[j];
+                if (MODE == 0) {
+                    t64[0][tid] = cc.x; t64[1][tid] = cc.y; t64[2][tid] = cc.z;
+                    t64[3][tid] = al.x; t64[4][tid] = al.y; t64[5][tid] = al.z;
+                } else {
+                    df rx = df_from_double(cc.x - lo[0]), ry = df_from_double(cc.y - lo[1]),
+                       rz = df_from_double(cc.z - lo[2]);
+                    df ax = df_from_double(al.x), ay = df_from_double(al.y), az = df_from_double(al.z);
+                    t32[0][tid] = rx.hi; t32[1][tid] = rx.lo; t32[2][tid] = ry.hi; t32[3][tid] = ry.lo;
+                    t32[4][tid] = rz.hi; t32[5][tid] = rz.lo; t32[6][tid] = ax.hi; t32[7][tid] = ax.lo;
+                    t32[8][tid] = ay.hi; t32[9][tid] = ay.lo; t32[10][tid] = az.hi; t32[11][tid] = az.lo;
+                }
+            }
+            __syncthreads();
+            if (valid) {
+                visited += m;
+                if (MODE == 0) {
+                    for (int q = 0; q < m; ++q) {
+                        double eta = __ddiv_rn(dist_f64<DIM>(P.x, P.y, P.z, t64[0][q], t64[1][q], t64[2][q]), a.R);
+                        double f = phi_f64<BASIS>(eta);
+                        useful += (eta < 1.0);
+                        acc64[0] = __dadd_rn(acc64[0], __dmul_rn(t64[3][q], f));
+                        acc64[1] = __dadd_rn(acc64[1], __dmul_rn(t64[4][q], f));
+                        if (DIM == 3) acc64[2] = __dadd_rn(acc64[2], __dmul_rn(t64[5][q], f));
+                    }
+                } else {
+                    for (int q = 0; q < m; ++q) {
+                        df dx = df_add(qx, {-t32[0][q], -t32[1][q]});
+                        df dy = df_add(qy, {-t32[2][q], -t32[3][q]});
+                        df r2 = df_add(df_sqr(dx), df_sqr(dy));
+                        if (DIM == 3) {
+                            df dz = df_add(qz, {-t32[4][q], -t32[5][q]});
+                            r2 = df_add(r2, df_sqr(dz));
+                        }
+                        df eta = df_mul(df_sqrt(r2), invR);
+                        df f = phi_df<BASIS>(eta);
+                        useful += (eta.hi < 1.0f);
+                        acc[0] = df_add(acc[0], df_mul(f, {t32[6][q], t32[7][q]}));
+                        acc[1] = df_add(acc[1], df_mul(f, {t32[8][q], t32[9][q]}));
+                        if (DIM == 3) acc[2] = df_add(acc[2], df_mul(f, {t32[10][q], t32[11][q]}));
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (MODE == 1) {
+        acc64[0] = df_to_double(acc[0]);
+        acc64[1] = df_to_double(acc[1]);
+        acc64[2] = df_to_double(acc[2]);
+    }
+    if (valid) {
+        const double w = __dsub_rn(1.0, __ddiv_rn(P.w, a.Dl));  // psi(d / D_l), d < D_l here
+        double4 v = a.vacc[s];
+        v.x = __dadd_rn(v.x, __dmul_rn(w, acc64[0]));
+        v.y = __dadd_rn(v.y, __dmul_rn(w, acc64[1]));
+        v.z = __dadd_rn(v.z, __dmul_rn(w, acc64[2]));
+        a.vacc[s] = v;
+    }
+    unsigned u = useful;
+    unsigned long long vv = visited;
+    for (int o = 16; o > 0; o >>= 1) {
+        u += __shfl_xor_sync(0xffffffffu, u, o);
+        vv += __shfl_xor_sync(0xffffffffu, vv, o);
+    }
+    if ((tid & 31) == 0) {
+        if (u) atomicAdd(&a.pairs[0], (unsigned long long)u);
+        if (vv) atomicAdd(&a.pairs[1], vv);
+    }
+}
+
+template <int DIM, int BASIS>
+void launch_vol_t(int mode, unsigned g, const VolArgs &a, cudaStream_t st) {
+    if (mode == 0) k_vol_sweep<DIM, BASIS, 0><<<g, kThreads, 0, st>>>(a);
+    else k_vol_sweep<DIM, BASIS, 1><<<g, kThreads, 0, st>>>(a);
+}
+
+void launch_vol(int dim, int basis, int mode, unsigned g, const VolArgs &a, cudaStream_t st) {
+    if (dim == 2) {
+        switch (basis) {
+        case 0: launch_vol_t<2, 0>(mode, g, a, st); break;
+        case 4: launch_vol_t<2, 4>(mode, g, a, st); break;
+        case 6: launch_vol_t<2, 6>(mode, g, a, st); break;
+        default: launch_vol_t<2, 2>(mode, g, a, st); break;
+        }
+    } else {
+        switch (basis) {
+        case 0: launch_vol_t<3, 0>(mode, g, a, st); break;
+        case 4: launch_vol_t<3, 4>(mode, g, a, st); break;
+        case 6: launch_vol_t<3, 6>(mode, g, a, st); break;
+        default: launch_vol_t<3, 2>(mode, g, a, st); break;
+        }
+    }
+}
+
+void reserve_volume(rbfd_mesh *m, size_t n) {
+    if (n <= m->vol_cap) return;
+    dfree(m->d_vin);
+    dfree(m->d_vpos);
+    dfree(m->d_vorig);
+    dfree(m->d_vflag);
+    dfree(m->d_vscan);
+    dfree(m->d_vlist);
+    dfree(m->d_vkeys);
+    dfree(m->d_vacc);
+    m->d_vin = nullptr;
+    m->vol_cap = 0;
+    m->d_vin = reinterpret_cast<float4 *>(dalloc<double4>(n, "volume points"));
+    m->d_vpos = reinterpret_cast<float4 *>(dalloc<double4>(n, "sorted volume points"));
+    m->d_vorig = dalloc<uint32_t>(n, "volume order");
+    m->d_vflag = dalloc<uint32_t>(n, "volume flags");
+    m->d_vscan = dalloc<uint32_t>(n, "volume scan");
+    m->d_vlist = dalloc<uint32_t>(n, "volume list");
+    m->d_vkeys = dalloc<uint32_t>(n, "volume keys");
+    m->d_vacc = dalloc<double4>(n, "volume displacement");
+    m->vol_cap = n;
+}
+
+}  // namespace
+
+void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64, double D, double k,
+                void *out) {
+    cudaStream_t st = m->stream;
+    const int dim = m->dim;
+    const size_t es = f64 ? sizeof(double) : sizeof(float);
+    RBFD_CUDA(cudaEventRecord(m->ev0, st));
+    const int L = (int)m->levels.size();
+    std::vector<double> Dl(L, 0.0);
+    double Dmax = 0.0;
+    for (int l = 0; l < L; ++l) {
+        double v = (k > 0.0) ? k * m->levels[l].smax : D;
+        if (k > 0.0 && D > 0.0 && v > D) v = D;
+        Dl[l] = (m->levels[l].nc > 0) ? v : 0.0;
+        Dmax = std::max(Dmax, Dl[l]);
+    }
+    const bool host = !m->opt.inputs_on_device;
+    void *dout = out;
+    const void *dx = xyz_v, *dd = d_v;
+    if (n_v > 0) {
+        reserve_volume(m, (size_t)n_v);
+        const size_t need = (size_t)n_v * dim * es * 2 + (size_t)n_v * es + 256;
+        if (host) {
+            if (need > m->vio_bytes) {
+                dfree(m->d_vio);
+                m->d_vio = nullptr;
+                m->vio_bytes = 0;
+                m->d_vio = dmalloc(need, "volume staging");
+                m->vio_bytes = need;
+            }
+            char *base = static_cast<char *>(m->d_vio);
+            void *sx = base;
+            void *sd = base + (size_t)n_v * dim * es;
+            dout = base + (size_t)n_v * dim * es + (((size_t)n_v * es + 255) / 256) * 256;
+            RBFD_CUDA(cudaMemcpyAsync(sx, xyz_v, (size_t)n_v * dim * es, cudaMemcpyHostToDevice, st));
+            RBFD_CUDA(cudaMemcpyAsync(sd, d_v, (size_t)n_v * es, cudaMemcpyHostToDevice, st));
+            dx = sx;
+            dd = sd;
+        }
+        RBFD_CUDA(cudaMemsetAsync(dout, 0, (size_t)n_v * dim * es, st));
+    }
+    double4 *vin = reinterpret_cast<double4 *>(m->d_vin);
+    double4 *vpos = reinterpret_cast<double4 *>(m->d_vpos);
+    int64_t nV = 0;
+    if (n_v > 0 && Dmax > 0.0) {
+        k_vol_pack<<<cdiv(n_v, 256), 256, 0, st>>>(dx, dd, n_v, dim, f64 ? 1 : 0, vin);
+        // (1) volume point reduction: d < max_l D_l
+        k_flag_below<<<cdiv(n_v, 256), 256, 0, st>>>(vin, nullptr, n_v, Dmax, m->d_vflag);
+        exclusive_scan_u32(m->d_vflag, m->d_vscan, (size_t)n_v, &m->d_misc[4], m->sort, st);
+        k_compact<<<cdiv(n_v, 256), 256, 0, st>>>(m->d_vflag, m->d_vscan, n_v, m->d_vlist);
+        uint32_t cnt = 0;
+        RBFD_CUDA(cudaMemcpyAsync(&cnt, &m->d_misc[4], sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        RBFD_CUDA(cudaStreamSynchronize(st));
+        nV = cnt;
+    }
+    if (nV > 0) {
+        // (2) Morton order of the kept points
+        const int nbb = std::min<int>(cdiv(nV, 256), 256);
+        k_bbox_idx<<<nbb, 256, 0, st>>>(vin, m->d_vlist, nV, m->d_red);
+        k_bbox_reduce<<<1, 32, 0, st>>>(m->d_red, nbb, m->d_bbox);
+        double bb[6];
+        RBFD_CUDA(cudaMemcpyAsync(bb, m->d_bbox, sizeof(bb), cudaMemcpyDeviceToHost, st));
+        RBFD_CUDA(cudaStreamSynchronize(st));
+        k_gather_vol<<<cdiv(nV, 256), 256, 0, st>>>(vin, m->d_vlist, nV, vpos);  // kept points, caller order
+        morton_keys_f64(vpos, nV, dim, make_double3(bb[0], bb[1], bb[2]), make_double3(bb[3], bb[4], bb[5]),
+                        m->d_vkeys, m->d_vorig, st);
+        radix_sort_pairs(m->d_vkeys, m->d_vorig, (size_t)nV, dim == 2 ? 32 : 30, m->sort, st);
+        k_gather_vol<<<cdiv(nV, 256), 256, 0, st>>>(vpos, m->d_vorig, nV, vin);  // vin := sorted points
+        // caller index of sorted point i = vlist[vorig[i]]
+        k_gather_u32<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vlist, m->d_vorig, nV, m->d_vflag);
+        RBFD_CUDA(cudaMemcpyAsync(m->d_vorig, m->d_vflag, sizeof(uint32_t) * nV, cudaMemcpyDeviceToDevice, st));
+        vpos = vin;
+        RBFD_CUDA(cudaMemsetAsync(m->d_vacc, 0, sizeof(double4) * nV, st));
+        // (3) per level: d < D_l, then the fused evaluation
+        const int mode = m->opt.precision == RBFD_FP64 ? 0 : 1;
+        for (int l = 0; l < L; ++l) {
+            const Level &Lv = m->levels[l];
+            if (Lv.nc == 0 || !(Dl[l] > 0.0)) continue;
+            k_flag_below<<<cdiv(nV, 256), 256, 0, st>>>(vpos, nullptr, nV, Dl[l], m->d_vflag);
+            exclusive_scan_u32(m->d_vflag, m->d_vscan, (size_t)nV, &m->d_misc[5], m->sort, st);
+            k_compact<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vflag, m->d_vscan, nV, m->d_vlist);
+            uint32_t nl = 0;
+            RBFD_CUDA(cudaMemcpyAsync(&nl, &m->d_misc[5], sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            RBFD_CUDA(cudaStreamSynchronize(st));
+            if (nl == 0) continue;
+            m->stats.deform_points += nl;
+            VolArgs a{};
+            a.n_list = nl;
+            a.list = m->d_vlist;
+            a.vpos = vpos;
+            a.vacc = m->d_vacc;
+            a.cx = Lv.d_cx;
+            a.alpha = Lv.d_alpha;
+            a.cell_start = Lv.d_cell_start;
+            a.cell_ctrl = Lv.d_cell_ctrl;
+            a.g0 = Lv.g0;
+            a.h = Lv.h;
+            a.gd = Lv.gdim;
+            a.R = Lv.R;
+            a.Dl = Dl[l];
+            double inv = 1.0 / Lv.R;
+            a.invR_hi = (float)inv;
+            a.invR_lo = (float)(inv - (double)a.invR_hi);
+            a.pairs = m->d_pairs;
+            launch_vol(dim, m->opt.basis, mode, cdiv(nl, kThreads), a, st);
+            RBFD_CUDA(cudaGetLastError());
+        }
+        // (4) back to the caller's order
+        k_scatter_out<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vacc, m->d_vorig, nV, dim, f64 ? 1 : 0, dout);
+        RBFD_CUDA(cudaGetLastError());
+    }
+    if (host && n_v > 0)
+        RBFD_CUDA(cudaMemcpyAsync(out, dout, (size_t)n_v * dim * es, cudaMemcpyDeviceToHost, st));
+    RBFD_CUDA(cudaEventRecord(m->ev1, st));
+    RBFD_CUDA(cudaEventSynchronize(m->ev1));
+    float ms = 0;
+    RBFD_CUDA(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
+    m->stats.deform_ms = ms;
+}
+
+}  // namespace rbfd

@@ -1,0 +1,1140 @@
+// greedy.cu -- multi-level greedy surface point selection (Section 3) on the
+// device, plus the per-mesh preparation of the surface.
+//
+// One greedy step, with n controls C = (c_0 .. c_{n-1}) selected so far:
+//
+//   sweep      E_i = dS_l,i - sum_{j in list(block(i))} alpha_j phi(|r_i - r_cj| / R)   (Eq. 12)
+//              for every surface point i; the controls a point block can reach
+//              (those within R of the block's bounding box) are kept in a
+//              per-block list that grows by at most one entry per step.  The
+//              same launch reduces max |E_i|^2 over the unselected points to
+//              the next control (last-block-done reductions, no spin waits)
+//              and applies the stop test max|E| / max|dS| < tau_l in FP64.
+//   grow       append c_n to Phi_cc = L L^T through the INVERSE factor
+//              G = L^{-1}: y = G phi(C, c_n), l = sqrt(phi(0) - y.y),
+//              G row n = [-(y^T G) / l, 1 / l], w_n = (dS_l(c_n) - y.w) / l,
+//              alpha += w_n * (G row n).  In exact arithmetic this is the
+//              bordered Cholesky solve of Eq. 9 on the control set; every
+//              product is a matrix-vector product (no sequential substitution),
+//              and alpha is updated in O(n) instead of re-solved.
+//
+// Level close: FP64 iterative refinement of alpha against the matrix-free
+// FP64 residual dS_c - Phi_cc alpha (preconditioned by G^T G), an FP64 confirm
+// sweep that stores E (the next level's target, dS_{l+1} = E), and the
+// per-level uniform cell grid of the controls for the volume update.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.h"
+
+namespace rbfd {
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kJT = 256;       // rows per tile of the column-sum kernels
+constexpr int kYWarps = 8;     // warps per block of the G*phi kernel
+constexpr int kTargetCTAs = 152 * 4;
+
+inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
+
+// ------------------------------------------------------------- prep kernels
+
+__global__ void k_unpack(const double *__restrict__ xyz, const double *__restrict__ dS, int64_t n, int dim,
+                         double4 *__restrict__ x4, double4 *__restrict__ d4) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *p = xyz + i * dim, *q = dS + i * dim;
+    x4[i] = make_double4(p[0], p[1], dim == 3 ? p[2] : 0.0, 0.0);
+    d4[i] = make_double4(q[0], q[1], dim == 3 ? q[2] : 0.0, 0.0);
+}
+
+// Two-pass bounding box of double4 points: per-block partials, then one block.
+__global__ void k_bbox_partial(const double4 *__restrict__ p, int64_t n, double *__restrict__ part) {
+    __shared__ double s[6][32];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double4 q = p[i];
+        lo[0] = fmin(lo[0], q.x); lo[1] = fmin(lo[1], q.y); lo[2] = fmin(lo[2], q.z);
+        hi[0] = fmax(hi[0], q.x); hi[1] = fmax(hi[1], q.y); hi[2] = fmax(hi[2], q.z);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmax(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) {
+            s[k][w] = lo[k];
+            s[3 + k][w] = hi[k];
+        }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double v = s[threadIdx.x][0];
+        for (int j = 1; j < (int)(blockDim.x >> 5); ++j)
+            v = threadIdx.x < 3 ? fmin(v, s[threadIdx.x][j]) : fmax(v, s[threadIdx.x][j]);
+        part[blockIdx.x * 6 + threadIdx.x] = v;
+    }
+}
+
+__global__ void k_bbox_final(const double *__restrict__ part, int nb, double *__restrict__ out) {
+    if (threadIdx.x >= 6) return;
+    double v = part[threadIdx.x];
+    for (int b = 1; b < nb; ++b) v = threadIdx.x < 3 ? fmin(v, part[b * 6 + threadIdx.x]) : fmax(v, part[b * 6 + threadIdx.x]);
+    out[threadIdx.x] = v;
+}
+
+__global__ void k_gather_sorted(const uint32_t *__restrict__ perm, int64_t n, const double4 *__restrict__ x4,
+                                const double4 *__restrict__ d4, double4 *__restrict__ xs, double4 *__restrict__ ds,
+                                uint32_t *__restrict__ inv) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t o = perm[i];
+    xs[i] = x4[o];
+    ds[i] = d4[o];
+    inv[o] = (uint32_t)i;
+}
+
+// Point blocks of kPB consecutive Morton-ordered points: bounding box, origin
+// (the box's low corner) and the points' coordinates relative to it as
+// double-float (hi, lo) pairs for the mixed-precision sweep.
+__global__ void k_point_blocks(const double4 *__restrict__ xs, int64_t n, double4 *__restrict__ lo_out,
+                               double4 *__restrict__ hi_out, double4 *__restrict__ org_out,
+                               float4 *__restrict__ xhi, float4 *__restrict__ xlo) {
+    __shared__ double s[6][kPB / 32];
+    int64_t i = (int64_t)blockIdx.x * kPB + threadIdx.x;
+    bool valid = i < n;
+    double4 q = valid ? xs[i] : make_double4(0, 0, 0, 0);
+    double lo[3] = {valid ? q.x : INFINITY, valid ? q.y : INFINITY, valid ? q.z : INFINITY};
+    double hi[3] = {valid ? q.x : -INFINITY, valid ? q.y : -INFINITY, valid ? q.z : -INFINITY};
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmax(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) {
+            s[k][w] = lo[k];
+            s[3 + k][w] = hi[k];
+        }
+    __syncthreads();
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = s[k][0];
+        hi[k] = s[3 + k][0];
+        for (int j = 1; j < kPB / 32; ++j) {
+            lo[k] = fmin(lo[k], s[k][j]);
+            hi[k] = fmax(hi[k], s[3 + k][j]);
+        }
+    }
+    if (threadIdx.x == 0) {
+        lo_out[blockIdx.x] = make_double4(lo[0], lo[1], lo[2], 0);
+        hi_out[blockIdx.x] = make_double4(hi[0], hi[1], hi[2], 0);
+        org_out[blockIdx.x] = make_double4(lo[0], lo[1], lo[2], 0);
+    }
+    if (valid) {
+        double r[3] = {q.x - lo[0], q.y - lo[1], q.z - lo[2]};
+        float h[3], l[3];
+        for (int k = 0; k < 3; ++k) {
+            h[k] = __double2float_rn(r[k]);
+            l[k] = __double2float_rn(r[k] - (double)h[k]);
+        }
+        xhi[i] = make_float4(h[0], h[1], h[2], 0.f);
+        xlo[i] = make_float4(l[0], l[1], l[2], 0.f);
+    }
+}
+
+// max_i |v_i|^2 (each square summed in coordinate order) and its argmax
+// (lowest original index on ties) over n points; last-block-done reduction.
+// out[0] = key, ((int*)(out + 1))[0] = original index of the argmax.
+__global__ void k_maxnorm(const double4 *__restrict__ v, const uint32_t *__restrict__ perm, int64_t n, int dim,
+                          double *__restrict__ bkey, int *__restrict__ bidx, unsigned int *done,
+                          double *__restrict__ out) {
+    __shared__ double sk[32];
+    __shared__ int si[32];
+    __shared__ bool last;
+    double k = -1.0;
+    int id = -1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double4 q = v[i];
+        double key = __dmul_rn(q.x, q.x);
+        key = __dadd_rn(key, __dmul_rn(q.y, q.y));
+        if (dim == 3) key = __dadd_rn(key, __dmul_rn(q.z, q.z));
+        int o = (int)perm[i];
+        if (better(key, o, k, id)) {
+            k = key;
+            id = o;
+        }
+    }
+    block_argmax(k, id, sk, si);
+    if (threadIdx.x == 0) {
+        bkey[blockIdx.x] = k;
+        bidx[blockIdx.x] = id;
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    k = -1.0;
+    id = -1;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        double kb = __ldcg(&bkey[b]);
+        int ib = __ldcg(&bidx[b]);
+        if (better(kb, ib, k, id)) {
+            k = kb;
+            id = ib;
+        }
+    }
+    block_argmax(k, id, sk, si);
+    if (threadIdx.x == 0) {
+        out[0] = k;
+        reinterpret_cast<int *>(out + 1)[0] = id;
+        *done = 0;
+    }
+}
+
+// ---------------------------------------------------------------- sweep
+
+struct SweepArgs {
+    int64_t n_s;
+    int n_pb, cap, n, chunk_len;
+    const double4 *xs;
+    const float4 *xs_hi, *xs_lo;
+    const double4 *pb_org;
+    const double4 *cur;
+    const unsigned char *sel;
+    const uint32_t *perm;
+    const uint32_t *nb_cnt, *nb_list;
+    const double4 *cx, *alpha;
+    double R, S0, tau;
+    float invR_hi, invR_lo;
+    double4 *part;
+    double4 *E_out;  // non-null: store E (confirm sweep)
+    double *pb_key;
+    int *pb_idx;
+    unsigned int *pb_done;
+    GreedyState *st;
+    unsigned long long *pairs;
+    int is_step;  // 1: greedy step (argmax over unselected + stop test); 0: confirm (max over all)
+    int dim;
+};
+
+template <int DIM, int BASIS, int MODE>
+__global__ void __launch_bounds__(kThreads) k_sweep(SweepArgs a) {
+    __shared__ double sk[32];
+    __shared__ int si[32];
+    __shared__ bool s_last;
+    // control tile: FP64 coordinates + weights (MODE 0) or double-float relative
+    // coordinates + weights (MODE 1)
+    __shared__ double t64[6][kTile];
+    __shared__ float t32[12][kTile];
+    if (a.is_step && a.st->stop) return;
+
+    const int pb = blockIdx.x, ch = blockIdx.y, nch = gridDim.y, tid = threadIdx.x;
+    const int64_t p = (int64_t)pb * kPB + tid;
+    const bool valid = p < a.n_s;
+    const uint32_t cnt = a.nb_cnt[pb];
+    const int lo = ch * a.chunk_len;
+    const int hi = min((int)cnt, lo + a.chunk_len);
+    const double4 org = a.pb_org[pb];
+
+    double acc64[3] = {0.0, 0.0, 0.0};
+    df acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    double px = 0, py = 0, pz = 0;
+    df qx{0, 0}, qy{0, 0}, qz{0, 0};
+    if (valid) {
+        if (MODE == 0) {
+            double4 q = a.xs[p];
+            px = q.x; py = q.y; pz = q.z;
+        } else {
+            float4 h = a.xs_hi[p], l = a.xs_lo[p];
+            qx = {h.x, l.x}; qy = {h.y, l.y}; qz = {h.z, l.z};
+        }
+    }
+    const df invR = {a.invR_hi, a.invR_lo};
+    unsigned useful = 0;
+    for (int t0 = lo; t0 < hi; t0 += kTile) {
+        const int m = min(kTile, hi - t0);
+        if (tid < m) {
+            uint32_t j = a.nb_list[(size_t)pb * a.cap + t0 + tid];
+            double4 c = a.cx[j], al = a.alpha[j];
+            if (MODE == 0) {
+                t64[0][tid] = c.x; t64[1][tid] = c.y; t64[2][tid] = c.z;
+                t64[3][tid] = al.x; t64[4][tid] = al.y; t64[5][tid] = al.z;
+            } else {
+                df rx = df_from_double(c.x - org.x), ry = df_from_double(c.y - org.y), rz = df_from_double(c.z - org.z);
+                df ax = df_from_double(al.x), ay = df_from_double(al.y), az = df_from_double(al.z);
+                t32[0][tid] = rx.hi; t32[1][tid] = rx.lo; t32[2][tid] = ry.hi; t32[3][tid] = ry.lo;
+                t32[4][tid] = rz.hi; t32[5][tid] = rz.lo; t32[6][tid] = ax.hi; t32[7][tid] = ax.lo;
+                t32[8][tid] = ay.hi; t32[9][tid] = ay.lo; t32[10][tid] = az.hi; t32[11][tid] = az.lo;
+            }
+        }
+        __syncthreads();
+        if (valid) {
+            if (MODE == 0) {
+                for (int q = 0; q < m; ++q) {
+                    double eta = __ddiv_rn(dist_f64<DIM>(px, py, pz, t64[0][q], t64[1][q], t64[2][q]), a.R);
+                    double f = phi_f64<BASIS>(eta);
+                    useful += (eta < 1.0);
+                    acc64[0] = __dadd_rn(acc64[0], __dmul_rn(t64[3][q], f));
+                    acc64[1] = __dadd_rn(acc64[1], __dmul_rn(t64[4][q], f));
+                    if (DIM == 3) acc64[2] = __dadd_rn(acc64[2], __dmul_rn(t64[5][q], f));
+                }
+            } else {
+                for (int q = 0; q < m; ++q) {
+                    df dx = df_add(qx, {-t32[0][q], -t32[1][q]});
+                    df dy = df_add(qy, {-t32[2][q], -t32[3][q]});
+                    df r2 = df_add(df_sqr(dx), df_sqr(dy));
+                    if (DIM == 3) {
+                        df dz = df_add(qz, {-t32[4][q], -t32[5][q]});
+                        r2 = df_add(r2, df_sqr(dz));
+                    }
+                    df eta = df_mul(df_sqrt(r2), invR);
+                    df f = phi_df<BASIS>(eta);
+                    useful += (eta.hi < 1.0f);
+                    acc[0] = df_add(acc[0], df_mul(f, {t32[6][q], t32[7][q]}));
+                    acc[1] = df_add(acc[1], df_mul(f, {t32[8][q], t32[9][q]}));
+                    if (DIM == 3) acc[2] = df_add(acc[2], df_mul(f, {t32[10][q], t32[11][q]}));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (MODE == 1) {
+        acc64[0] = df_to_double(acc[0]);
+        acc64[1] = df_to_double(acc[1]);
+        acc64[2] = df_to_double(acc[2]);
+    }
+    if (valid) a.part[(size_t)ch * a.n_s + p] = make_double4(acc64[0], acc64[1], acc64[2], 0.0);
+    // pair counters (one atomic per block)
+    {
+        unsigned u = useful;
+        for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+        if ((tid & 31) == 0 && u) atomicAdd(&a.pairs[0], (unsigned long long)u);
+        if (tid == 0 && hi > lo) {
+            unsigned long long nv = (unsigned long long)min((int64_t)kPB, a.n_s - (int64_t)pb * kPB);
+            atomicAdd(&a.pairs[1], nv * (unsigned long long)(hi - lo));
+        }
+    }
+    // last chunk-block of this point block reduces the partial sums in chunk order
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(&a.pb_done[pb], 1u) == (unsigned)(nch - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double key = -1.0;
+    int orig = -1;
+    if (valid) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        for (int c = 0; c < nch; ++c) {
+            double4 v = ldcg_d4(&a.part[(size_t)c * a.n_s + p]);
+            s0 = __dadd_rn(s0, v.x);
+            s1 = __dadd_rn(s1, v.y);
+            s2 = __dadd_rn(s2, v.z);
+        }
+        double4 cu = a.cur[p];
+        double e0 = __dsub_rn(cu.x, s0), e1 = __dsub_rn(cu.y, s1), e2 = (DIM == 3) ? __dsub_rn(cu.z, s2) : 0.0;
+        if (a.E_out) a.E_out[p] = make_double4(e0, e1, e2, 0.0);
+        double k2 = __dmul_rn(e0, e0);
+        k2 = __dadd_rn(k2, __dmul_rn(e1, e1));
+        if (DIM == 3) k2 = __dadd_rn(k2, __dmul_rn(e2, e2));
+        if (!a.is_step || !a.sel[p]) {
+            key = k2;
+            orig = (int)a.perm[p];
+        }
+    }
+    block_argmax(key, orig, sk, si);
+    if (tid == 0) {
+        a.pb_key[pb] = key;
+        a.pb_idx[pb] = orig;
+        a.pb_done[pb] = 0;
+        __threadfence();
+        s_last = atomicAdd(&a.st->pb_done, 1u) == (unsigned)(a.n_pb - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    key = -1.0;
+    orig = -1;
+    for (int b = tid; b < a.n_pb; b += kThreads) {
+        double kb = __ldcg(&a.pb_key[b]);
+        int ib = __ldcg(&a.pb_idx[b]);
+        if (better(kb, ib, key, orig)) {
+            key = kb;
+            orig = ib;
+        }
+    }
+    block_argmax(key, orig, sk, si);
+    if (tid == 0) {
+        GreedyState *st = a.st;
+        st->pb_done = 0;
+        st->best_orig = orig;
+        st->best_key = key;
+        double e = orig >= 0 ? __ddiv_rn(__dsqrt_rn(key), a.S0) : 0.0;
+        st->emax = e;
+        if (a.is_step) {
+            if (orig < 0 || e < a.tau) {
+                st->stop = 1;
+            } else if (a.n >= a.cap) {
+                st->stop = 1;
+                st->status = RBFD_ENOTCONV;
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------- growth
+
+struct GrowArgs {
+    int n, cap, n_pb, dim;
+    double R, R2;
+    const uint32_t *inv;
+    const double4 *xs;
+    const double4 *pb_lo, *pb_hi;
+    unsigned char *sel;
+    double4 *cx;
+    uint32_t *cid;
+    double *phi;
+    uint32_t *nb_cnt, *nb_list;
+    const double *G;
+    double *Gw;
+    double *y;
+    double *red;  // [blocks][4]: y.y, y.w (3)
+    int n_red;
+    double *gpart;
+    double4 *w, *alpha;
+    const double4 *cur;
+    GreedyState *st;
+};
+
+// phi(|r_cn - r_ck| / R) for k < n; list the new control in every point block
+// within R of it; record it as control n.
+template <int DIM, int BASIS>
+__global__ void k_grow_phi(GrowArgs a) {
+    if (a.st->stop) return;
+    const uint32_t c = a.inv[a.st->best_orig];
+    const double4 x = a.xs[c];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.n) {
+        double4 ck = a.cx[t];
+        a.phi[t] = phi_f64<BASIS>(__ddiv_rn(dist_f64<DIM>(x.x, x.y, x.z, ck.x, ck.y, ck.z), a.R));
+    }
+    if (t < a.n_pb) {
+        double4 l = a.pb_lo[t], h = a.pb_hi[t];
+        double dx = fmax(fmax(l.x - x.x, x.x - h.x), 0.0);
+        double dy = fmax(fmax(l.y - x.y, x.y - h.y), 0.0);
+        double dz = DIM == 3 ? fmax(fmax(l.z - x.z, x.z - h.z), 0.0) : 0.0;
+        if (dx * dx + dy * dy + dz * dz < a.R2 * (1.0 + 1e-9)) {
+            uint32_t k = a.nb_cnt[t];
+            a.nb_list[(size_t)t * a.cap + k] = (uint32_t)a.n;
+            a.nb_cnt[t] = k + 1;
+        }
+    }
+    if (t == 0) {
+        a.sel[c] = 1;
+        a.cx[a.n] = x;
+        a.cid[a.n] = c;
+    }
+}
+
+// y_j = sum_{k <= j} G_jk phi_k, one warp per row; per-block partial sums of
+// y_j^2 and y_j w_j (3 components) in fixed order.
+__global__ void k_grow_y(GrowArgs a) {
+    if (a.st->stop) return;
+    __shared__ double s[kYWarps][4];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * kYWarps + w;
+    double yy = 0, yw0 = 0, yw1 = 0, yw2 = 0;
+    if (j < a.n) {
+        const double *row = a.G + (size_t)j * a.cap;
+        double acc = 0.0;
+        for (int k = lane; k <= j; k += 32) acc = fma(row[k], a.phi[k], acc);
+        acc = warp_sum_d(acc);
+        if (lane == 0) a.y[j] = acc;
+        double4 wj = a.w[j];
+        yy = acc * acc;
+        yw0 = acc * wj.x;
+        yw1 = acc * wj.y;
+        yw2 = acc * wj.z;
+    }
+    if (lane == 0) {
+        s[w][0] = yy; s[w][1] = yw0; s[w][2] = yw1; s[w][3] = yw2;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double v = 0;
+        for (int q = 0; q < kYWarps; ++q) v += s[q][threadIdx.x];
+        a.red[blockIdx.x * 4 + threadIdx.x] = v;
+    }
+}
+
+// Partial column sums of y^T G over a tile of kJT rows: gpart[jt][k].
+__global__ void k_colsum(int n, int cap, const double *__restrict__ G, const double *__restrict__ y,
+                         double *__restrict__ gpart, const GreedyState *st) {
+    if (st && st->stop) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int jt = blockIdx.y;
+    if (k >= n) return;
+    int j0 = max(jt * kJT, k), j1 = min(n, (jt + 1) * kJT);
+    double s = 0.0;
+    for (int j = j0; j < j1; ++j) s = fma(y[j], G[(size_t)j * cap + k], s);
+    gpart[(size_t)jt * cap + k] = s;
+}
+
+// Finish the row append: l, w_n, G row n and alpha += w_n * G row n.
+__global__ void k_grow_finish(GrowArgs a, int n_jt) {
+    if (a.st->stop) return;
+    __shared__ double sh[4];
+    if (threadIdx.x < 4) {
+        double v = 0;
+        for (int b = 0; b < a.n_red; ++b) v += a.red[b * 4 + threadIdx.x];
+        sh[threadIdx.x] = v;
+    }
+    __syncthreads();
+    const double l2 = 1.0 - sh[0];  // phi(0) = 1 for every Wendland function
+    // 1 - y.y carries an absolute rounding error of about n u: a pivot below
+    // a few times that is numerically zero (coincident controls)
+    if (!(l2 > 8.0 * (a.n + 1) * 1.1102230246251565e-16)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.st->status = RBFD_ESINGULAR;
+            a.st->stop = 1;
+        }
+        return;
+    }
+    const double l = sqrt(l2);
+    const uint32_t c = a.cid[a.n];
+    const double4 b = a.cur[c];
+    const double4 wn = make_double4((b.x - sh[1]) / l, (b.y - sh[2]) / l, (b.z - sh[3]) / l, 0.0);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double *Grow = a.Gw + (size_t)a.n * a.cap;
+    if (k < a.n) {
+        double s = 0.0;
+        for (int jt = 0; jt < n_jt; ++jt) s += a.gpart[(size_t)jt * a.cap + k];
+        double g = -s / l;
+        Grow[k] = g;
+        double4 al = a.alpha[k];
+        al.x = fma(wn.x, g, al.x);
+        al.y = fma(wn.y, g, al.y);
+        al.z = fma(wn.z, g, al.z);
+        a.alpha[k] = al;
+    } else if (k == a.n) {
+        Grow[k] = 1.0 / l;
+        a.w[k] = wn;
+        a.alpha[k] = make_double4(wn.x / l, wn.y / l, wn.z / l, 0.0);
+        a.st->n = a.n + 1;
+    }
+}
+
+// Start a level: control 0, G = [1], w_0 = alpha_0 = dS_l(c_0); list it.
+__global__ void k_level_init(int first_orig_from_state, int first_orig, const uint32_t *inv, const double4 *xs,
+                             const double4 *cur, int n_pb, int cap, int dim, double R2, const double4 *pb_lo,
+                             const double4 *pb_hi, unsigned char *sel, double4 *cx, uint32_t *cid, double *G,
+                             double4 *w, double4 *alpha, uint32_t *nb_cnt, uint32_t *nb_list, const double *red_out,
+                             GreedyState *st) {
+    int o = first_orig_from_state ? reinterpret_cast<const int *>(red_out + 1)[0] : first_orig;
+    const uint32_t c = inv[o];
+    const double4 x = xs[c];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_pb) {
+        double4 l = pb_lo[t], h = pb_hi[t];
+        double dx = fmax(fmax(l.x - x.x, x.x - h.x), 0.0);
+        double dy = fmax(fmax(l.y - x.y, x.y - h.y), 0.0);
+        double dz = dim == 3 ? fmax(fmax(l.z - x.z, x.z - h.z), 0.0) : 0.0;
+        bool in = dx * dx + dy * dy + dz * dz < R2 * (1.0 + 1e-9);
+        nb_cnt[t] = in ? 1u : 0u;
+        if (in) nb_list[(size_t)t * cap] = 0u;
+    }
+    if (t == 0) {
+        sel[c] = 1;
+        cx[0] = x;
+        cid[0] = c;
+        G[0] = 1.0;
+        double4 b = cur[c];
+        w[0] = b;
+        alpha[0] = b;
+        st->n = 1;
+        st->stop = 0;
+        st->status = RBFD_OK;
+        st->best = -1;
+        st->best_orig = -1;
+        st->best_key = 0;
+        st->second_key = 0;
+        st->min_gap = 1.0;
+        st->emax = 0;
+        st->pb_done = 0;
+        st->red_done = 0;
+    }
+}
+
+// ------------------------------------------------------------ refinement
+
+// r_i = dS_l(c_i) - sum_j alpha_j phi(|r_ci - r_cj| / R) over the n controls,
+// FP64; per-block max |r| to red[block].
+template <int DIM, int BASIS>
+__global__ void __launch_bounds__(kThreads) k_resid(int n, double R, const double4 *__restrict__ cx,
+                                                    const double4 *__restrict__ alpha,
+                                                    const uint32_t *__restrict__ cid,
+                                                    const double4 *__restrict__ cur, double4 *__restrict__ r,
+                                                    double *__restrict__ red) {
+    __shared__ double t[6][kTile];
+    __shared__ double sm[32];
+    const int i = blockIdx.x * kThreads + threadIdx.x;
+    const bool valid = i < n;
+    double4 xi = valid ? cx[i] : make_double4(0, 0, 0, 0);
+    double acc[3] = {0, 0, 0};
+    for (int t0 = 0; t0 < n; t0 += kTile) {
+        int m = min(kTile, n - t0);
+        if ((int)threadIdx.x < m) {
+            double4 c = cx[t0 + threadIdx.x], al = alpha[t0 + threadIdx.x];
+            t[0][threadIdx.x] = c.x; t[1][threadIdx.x] = c.y; t[2][threadIdx.x] = c.z;
+            t[3][threadIdx.x] = al.x; t[4][threadIdx.x] = al.y; t[5][threadIdx.x] = al.z;
+        }
+        __syncthreads();
+        if (valid)
+            for (int q = 0; q < m; ++q) {
+                double f = phi_f64<BASIS>(__ddiv_rn(dist_f64<DIM>(xi.x, xi.y, xi.z, t[0][q], t[1][q], t[2][q]), R));
+                acc[0] = fma(t[3][q], f, acc[0]);
+                acc[1] = fma(t[4][q], f, acc[1]);
+                acc[2] = fma(t[5][q], f, acc[2]);
+            }
+        __syncthreads();
+    }
+    double mx = 0.0;
+    if (valid) {
+        double4 b = cur[cid[i]];
+        double4 ri = make_double4(b.x - acc[0], b.y - acc[1], DIM == 3 ? b.z - acc[2] : 0.0, 0.0);
+        r[i] = ri;
+        mx = fmax(fabs(ri.x), fmax(fabs(ri.y), fabs(ri.z)));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < kThreads / 32; ++q) mx = fmax(mx, sm[q]);
+        red[blockIdx.x] = fmax(mx, sm[0]);
+    }
+}
+
+// z_j = sum_{k <= j} G_jk r_k (3 right-hand sides), one warp per row.
+__global__ void k_lower_mv3(int n, int cap, const double *__restrict__ G, const double4 *__restrict__ r,
+                            double4 *__restrict__ z) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + w;
+    if (j >= n) return;
+    const double *row = G + (size_t)j * cap;
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int k = lane; k <= j; k += 32) {
+        double g = row[k];
+        double4 v = r[k];
+        s0 = fma(g, v.x, s0);
+        s1 = fma(g, v.y, s1);
+        s2 = fma(g, v.z, s2);
+    }
+    s0 = warp_sum_d(s0);
+    s1 = warp_sum_d(s1);
+    s2 = warp_sum_d(s2);
+    if (lane == 0) z[j] = make_double4(s0, s1, s2, 0.0);
+}
+
+// Partial column sums of z^T G for 3 right-hand sides: part[jt][k].
+__global__ void k_colsum3(int n, int cap, const double *__restrict__ G, const double4 *__restrict__ z,
+                          double4 *__restrict__ part) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int jt = blockIdx.y;
+    if (k >= n) return;
+    int j0 = max(jt * kJT, k), j1 = min(n, (jt + 1) * kJT);
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int j = j0; j < j1; ++j) {
+        double g = G[(size_t)j * cap + k];
+        double4 v = z[j];
+        s0 = fma(g, v.x, s0);
+        s1 = fma(g, v.y, s1);
+        s2 = fma(g, v.z, s2);
+    }
+    part[(size_t)jt * cap + k] = make_double4(s0, s1, s2, 0.0);
+}
+
+__global__ void k_apply_correction(int n, int cap, int n_jt, const double4 *__restrict__ part,
+                                   double4 *__restrict__ alpha) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int jt = 0; jt < n_jt; ++jt) {
+        double4 v = part[(size_t)jt * cap + k];
+        s0 += v.x;
+        s1 += v.y;
+        s2 += v.z;
+    }
+    double4 a = alpha[k];
+    alpha[k] = make_double4(a.x + s0, a.y + s1, a.z + s2, 0.0);
+}
+
+// ------------------------------------------------------------ control grid
+
+__global__ void k_orig_of_controls(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ cid, int n,
+                                   uint32_t *__restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = perm[cid[i]];
+}
+
+__global__ void k_cell_keys(const double4 *__restrict__ cx, int n, double3 g0, double inv_h, int3 gd,
+                            uint32_t *keys, uint32_t *vals) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double4 c = cx[i];
+    int ix = min(max((int)floor((c.x - g0.x) * inv_h), 0), gd.x - 1);
+    int iy = min(max((int)floor((c.y - g0.y) * inv_h), 0), gd.y - 1);
+    int iz = min(max((int)floor((c.z - g0.z) * inv_h), 0), gd.z - 1);
+    keys[i] = (uint32_t)((iz * gd.y + iy) * gd.x + ix);
+    vals[i] = (uint32_t)i;
+}
+
+// cell_start[c] = first position whose key >= c (binary search in sorted keys)
+__global__ void k_cell_start(const uint32_t *__restrict__ keys, int n, int ncell, uint32_t *__restrict__ start) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > ncell) return;
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (keys[mid] < (uint32_t)c) lo = mid + 1;
+        else hi = mid;
+    }
+    start[c] = (uint32_t)lo;
+}
+
+// ---------------------------------------------------------- dispatch helpers
+
+template <int DIM, int BASIS>
+void launch_sweep_t(int mode, dim3 grid, const SweepArgs &a, cudaStream_t st) {
+    if (mode == 0) k_sweep<DIM, BASIS, 0><<<grid, kThreads, 0, st>>>(a);
+    else k_sweep<DIM, BASIS, 1><<<grid, kThreads, 0, st>>>(a);
+}
+
+template <int DIM>
+void launch_sweep_d(int basis, int mode, dim3 grid, const SweepArgs &a, cudaStream_t st) {
+    switch (basis) {
+    case 0: launch_sweep_t<DIM, 0>(mode, grid, a, st); break;
+    case 4: launch_sweep_t<DIM, 4>(mode, grid, a, st); break;
+    case 6: launch_sweep_t<DIM, 6>(mode, grid, a, st); break;
+    default: launch_sweep_t<DIM, 2>(mode, grid, a, st); break;
+    }
+}
+
+void launch_sweep(int dim, int basis, int mode, dim3 grid, const SweepArgs &a, cudaStream_t st) {
+    if (dim == 2) launch_sweep_d<2>(basis, mode, grid, a, st);
+    else launch_sweep_d<3>(basis, mode, grid, a, st);
+}
+
+template <int DIM>
+void launch_phi_d(int basis, unsigned g, const GrowArgs &a, cudaStream_t st) {
+    switch (basis) {
+    case 0: k_grow_phi<DIM, 0><<<g, kThreads, 0, st>>>(a); break;
+    case 4: k_grow_phi<DIM, 4><<<g, kThreads, 0, st>>>(a); break;
+    case 6: k_grow_phi<DIM, 6><<<g, kThreads, 0, st>>>(a); break;
+    default: k_grow_phi<DIM, 2><<<g, kThreads, 0, st>>>(a); break;
+    }
+}
+
+template <int DIM>
+void launch_resid_d(int basis, unsigned g, int n, double R, rbfd_mesh *m, cudaStream_t st) {
+    switch (basis) {
+    case 0: k_resid<DIM, 0><<<g, kThreads, 0, st>>>(n, R, m->d_cx, m->d_alpha, m->d_cid, m->d_cur, m->d_vec, m->d_red); break;
+    case 4: k_resid<DIM, 4><<<g, kThreads, 0, st>>>(n, R, m->d_cx, m->d_alpha, m->d_cid, m->d_cur, m->d_vec, m->d_red); break;
+    case 6: k_resid<DIM, 6><<<g, kThreads, 0, st>>>(n, R, m->d_cx, m->d_alpha, m->d_cid, m->d_cur, m->d_vec, m->d_red); break;
+    default: k_resid<DIM, 2><<<g, kThreads, 0, st>>>(n, R, m->d_cx, m->d_alpha, m->d_cid, m->d_cur, m->d_vec, m->d_red); break;
+    }
+}
+
+int n_chunks_for(const rbfd_mesh *m, int n) {
+    int want = (kTargetCTAs + m->n_pb - 1) / m->n_pb;
+    int by_len = (n + 31) / 32;
+    return std::max(1, std::min(std::min(want, by_len), m->n_chunk_max));
+}
+
+SweepArgs base_sweep_args(rbfd_mesh *m, double R, double tau) {
+    SweepArgs a{};
+    a.n_s = m->n_s;
+    a.n_pb = m->n_pb;
+    a.cap = m->cap;
+    a.xs = m->d_xs;
+    a.xs_hi = m->d_xs_hi;
+    a.xs_lo = m->d_xs_lo;
+    a.pb_org = m->d_pb_org;
+    a.cur = m->d_cur;
+    a.sel = m->d_sel;
+    a.perm = m->d_perm;
+    a.nb_cnt = m->d_nb_cnt;
+    a.nb_list = m->d_nb_list;
+    a.cx = m->d_cx;
+    a.alpha = m->d_alpha;
+    a.R = R;
+    a.S0 = m->S0;
+    a.tau = tau;
+    double inv = 1.0 / R;
+    a.invR_hi = (float)inv;
+    a.invR_lo = (float)(inv - (double)a.invR_hi);
+    a.part = m->d_part;
+    a.pb_key = m->d_pb_key;
+    a.pb_idx = m->d_pb_idx;
+    a.pb_done = m->d_pb_done;
+    a.st = m->d_st;
+    a.pairs = m->d_pairs;
+    a.dim = m->dim;
+    return a;
+}
+
+void read_state(rbfd_mesh *m) {
+    RBFD_CUDA(cudaMemcpyAsync(m->h_st, m->d_st, sizeof(GreedyState), cudaMemcpyDeviceToHost, m->stream));
+    RBFD_CUDA(cudaStreamSynchronize(m->stream));
+}
+
+// max_i |v_i|^2 and its argmax over the sorted surface (FP64, exact order of
+// each squared norm); returns the key, writes the argmax's original index.
+double maxnorm(rbfd_mesh *m, const double4 *v, int *arg) {
+    const int nb = std::min<int>(cdiv(m->n_s, 256), 1024);
+    k_maxnorm<<<nb, 256, 0, m->stream>>>(v, m->d_perm, m->n_s, m->dim, m->d_pb_key, m->d_pb_idx,
+                                         &m->d_misc[0], m->d_bbox);
+    RBFD_CUDA(cudaGetLastError());
+    double h[2];
+    RBFD_CUDA(cudaMemcpyAsync(h, m->d_bbox, sizeof(h), cudaMemcpyDeviceToHost, m->stream));
+    RBFD_CUDA(cudaStreamSynchronize(m->stream));
+    if (arg) std::memcpy(arg, &h[1], sizeof(int));
+    return h[0];
+}
+
+// Uniform grid of cell size h over the level's controls (for the volume sweep).
+void build_control_grid(rbfd_mesh *m, Level &L) {
+    const int n = (int)L.nc;
+    double *part = m->d_red;
+    k_bbox_partial<<<1, 256, 0, m->stream>>>(L.d_cx, n, part);
+    k_bbox_final<<<1, 32, 0, m->stream>>>(part, 1, m->d_bbox);
+    double bb[6];
+    RBFD_CUDA(cudaMemcpyAsync(bb, m->d_bbox, sizeof(bb), cudaMemcpyDeviceToHost, m->stream));
+    RBFD_CUDA(cudaStreamSynchronize(m->stream));
+    double h = L.R;
+    auto dims = [&](double hh) {
+        int nx = std::max(1, (int)std::floor((bb[3] - bb[0]) / hh) + 1);
+        int ny = std::max(1, (int)std::floor((bb[4] - bb[1]) / hh) + 1);
+        int nz = m->dim == 3 ? std::max(1, (int)std::floor((bb[5] - bb[2]) / hh) + 1) : 1;
+        return make_int3(nx, ny, nz);
+    };
+    int3 gd = dims(h);
+    while ((double)gd.x * gd.y * gd.z > 4.0e6) {  // keep the cell table small
+        h *= 2.0;
+        gd = dims(h);
+    }
+    L.h = h;
+    L.g0 = make_double3(bb[0], bb[1], m->dim == 3 ? bb[2] : 0.0);
+    L.gdim = gd;
+    L.ncell = gd.x * gd.y * gd.z;
+    L.d_cell_start = dalloc<uint32_t>((size_t)L.ncell + 1, "control cell starts");
+    L.d_cell_ctrl = dalloc<uint32_t>((size_t)n, "control cell list");
+    uint32_t *keys = dalloc<uint32_t>((size_t)n, "control cell keys");
+    k_cell_keys<<<cdiv(n, 256), 256, 0, m->stream>>>(L.d_cx, n, L.g0, 1.0 / h, gd, keys, L.d_cell_ctrl);
+    int bits = 1;
+    while ((1u << bits) < (unsigned)L.ncell && bits < 32) ++bits;
+    radix_sort_pairs(keys, L.d_cell_ctrl, (size_t)n, bits, m->sort, m->stream);
+    k_cell_start<<<cdiv((size_t)L.ncell + 1, 256), 256, 0, m->stream>>>(keys, n, L.ncell, L.d_cell_start);
+    RBFD_CUDA(cudaGetLastError());
+    RBFD_CUDA(cudaStreamSynchronize(m->stream));
+    dfree(keys);
+}
+
+}  // namespace
+
+// ====================================================================== API
+
+void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
+    const int64_t n = m->n_s;
+    cudaStream_t st = m->stream;
+    // inputs to device (one copy each when they are host buffers)
+    const size_t bytes = sizeof(double) * (size_t)n * m->dim;
+    double *dx = nullptr, *dd = nullptr;
+    if (m->opt.inputs_on_device) {
+        dx = const_cast<double *>(xyz_s);
+        dd = const_cast<double *>(dS);
+    } else {
+        dx = dalloc<double>((size_t)n * m->dim, "surface coordinates");
+        dd = dalloc<double>((size_t)n * m->dim, "surface displacements");
+        RBFD_CUDA(cudaMemcpyAsync(dx, xyz_s, bytes, cudaMemcpyHostToDevice, st));
+        RBFD_CUDA(cudaMemcpyAsync(dd, dS, bytes, cudaMemcpyHostToDevice, st));
+    }
+    double4 *x4 = dalloc<double4>(n, "surface x4");
+    double4 *d4 = dalloc<double4>(n, "surface d4");
+    k_unpack<<<cdiv(n, 256), 256, 0, st>>>(dx, dd, n, m->dim, x4, d4);
+    RBFD_CUDA(cudaGetLastError());
+    if (!m->opt.inputs_on_device) {
+        RBFD_CUDA(cudaStreamSynchronize(st));
+        dfree(dx);
+        dfree(dd);
+    }
+    m->d_misc = dalloc<uint32_t>(16, "counters");
+    RBFD_CUDA(cudaMemsetAsync(m->d_misc, 0, 16 * sizeof(uint32_t), st));
+    m->d_bbox = dalloc<double>(8, "bbox");
+    // bounding box -> Morton keys -> stable radix sort -> permutation
+    const int nbb = std::min<int>(cdiv(n, 256), 256);
+    double *part = dalloc<double>(6 * 256, "bbox partials");
+    k_bbox_partial<<<nbb, 256, 0, st>>>(x4, n, part);
+    k_bbox_final<<<1, 32, 0, st>>>(part, nbb, m->d_bbox);
+    double bb[6];
+    RBFD_CUDA(cudaMemcpyAsync(bb, m->d_bbox, sizeof(bb), cudaMemcpyDeviceToHost, st));
+    RBFD_CUDA(cudaStreamSynchronize(st));
+    dfree(part);
+    uint32_t *keys = dalloc<uint32_t>(n, "morton keys");
+    m->d_perm = dalloc<uint32_t>(n, "permutation");
+    m->d_inv = dalloc<uint32_t>(n, "inverse permutation");
+    morton_keys_f64(x4, n, m->dim, make_double3(bb[0], bb[1], bb[2]), make_double3(bb[3], bb[4], bb[5]), keys,
+                    m->d_perm, st);
+    radix_sort_pairs(keys, m->d_perm, n, m->dim == 2 ? 32 : 30, m->sort, st);
+    m->d_xs = dalloc<double4>(n, "sorted surface");
+    m->d_dS = dalloc<double4>(n, "sorted displacement");
+    m->d_cur = dalloc<double4>(n, "level target");
+    m->d_E = dalloc<double4>(n, "surface error");
+    k_gather_sorted<<<cdiv(n, 256), 256, 0, st>>>(m->d_perm, n, x4, d4, m->d_xs, m->d_dS, m->d_inv);
+    RBFD_CUDA(cudaGetLastError());
+    // point blocks
+    m->n_pb = (int)cdiv(n, kPB);
+    m->d_pb_lo = dalloc<double4>(m->n_pb, "block lo");
+    m->d_pb_hi = dalloc<double4>(m->n_pb, "block hi");
+    m->d_pb_org = dalloc<double4>(m->n_pb, "block origin");
+    m->d_xs_hi = dalloc<float4>(n, "surface hi");
+    m->d_xs_lo = dalloc<float4>(n, "surface lo");
+    k_point_blocks<<<m->n_pb, kPB, 0, st>>>(m->d_xs, n, m->d_pb_lo, m->d_pb_hi, m->d_pb_org, m->d_xs_hi, m->d_xs_lo);
+    RBFD_CUDA(cudaGetLastError());
+    RBFD_CUDA(cudaStreamSynchronize(st));
+    dfree(keys);
+    dfree(x4);
+    dfree(d4);
+
+    // greedy workspace
+    int64_t cap = m->opt.nc_cap > 0 ? m->opt.nc_cap : 16384;
+    cap = std::min<int64_t>(cap, n);
+    m->cap = (int)cap;
+    m->d_sel = dalloc<unsigned char>(n, "selected flags");
+    m->d_G = dalloc<double>((size_t)cap * cap, "inverse factor");
+    m->d_w = dalloc<double4>(cap + 1, "w");
+    m->d_alpha = dalloc<double4>(cap + 1, "alpha");
+    m->d_cx = dalloc<double4>(cap + 1, "control coordinates");
+    m->d_cid = dalloc<uint32_t>(cap + 1, "control ids");
+    m->d_phi = dalloc<double>(cap + 1, "phi column");
+    m->d_y = dalloc<double>(cap + 1, "y");
+    const int n_red = (int)cdiv(cap + 1, kYWarps) + 8;
+    m->d_red = dalloc<double>((size_t)4 * n_red + 6 * 256, "reductions");
+    const int n_jt = (int)cdiv(cap + 1, kJT);
+    m->d_gpart = dalloc<double>((size_t)n_jt * cap + cap, "column partials");
+    m->d_vec = dalloc<double4>(cap + 1, "refinement r");
+    m->d_vec2 = dalloc<double4>(cap + 1, "refinement z");
+    m->d_v4part = dalloc<double4>((size_t)n_jt * cap + cap, "refinement partials");
+    m->d_nb_cnt = dalloc<uint32_t>(m->n_pb, "block list counts");
+    m->d_nb_list = dalloc<uint32_t>((size_t)m->n_pb * cap, "block lists");
+    m->n_chunk_max = std::max(1, (kTargetCTAs + m->n_pb - 1) / m->n_pb);
+    m->d_part = dalloc<double4>((size_t)m->n_chunk_max * n, "sweep partials");
+    m->d_pb_done = dalloc<unsigned int>(m->n_pb, "block counters");
+    RBFD_CUDA(cudaMemsetAsync(m->d_pb_done, 0, sizeof(unsigned int) * m->n_pb, st));
+    m->d_pb_key = dalloc<double>(std::max(m->n_pb, 1024), "block keys");
+    m->d_pb_idx = dalloc<int>(std::max(m->n_pb, 1024), "block argmax");
+    m->d_pairs = dalloc<unsigned long long>(2, "pair counters");
+    RBFD_CUDA(cudaMemsetAsync(m->d_pairs, 0, 2 * sizeof(unsigned long long), st));
+    m->d_st = dalloc<GreedyState>(1, "greedy state");
+    RBFD_CUDA(cudaMemsetAsync(m->d_st, 0, sizeof(GreedyState), st));
+    RBFD_CUDA(cudaMallocHost(&m->h_st, sizeof(GreedyState)));
+    RBFD_CUDA(cudaStreamSynchronize(st));
+
+    // S0 = max_i |dS_i|
+    m->S0 = std::sqrt(maxnorm(m, m->d_dS, nullptr));
+}
+
+void greedy_run(rbfd_mesh *m) {
+    cudaStream_t st = m->stream;
+    for (auto &L : m->levels) {
+        dfree(L.d_cx);
+        dfree(L.d_alpha);
+        dfree(L.d_cell_start);
+        dfree(L.d_cell_ctrl);
+    }
+    m->levels.clear();
+    m->greedy_done = false;
+    m->stats.greedy_steps = 0;
+    m->stats.refine_sweeps = 0;
+    m->stats.confirm_resumes = 0;
+    RBFD_CUDA(cudaMemsetAsync(m->d_pairs, 0, 2 * sizeof(unsigned long long), st));
+    RBFD_CUDA(cudaEventRecord(m->ev0, st));
+    if (m->S0 == 0.0) {  // nothing moves: zero levels
+        RBFD_CUDA(cudaEventRecord(m->ev1, st));
+        RBFD_CUDA(cudaEventSynchronize(m->ev1));
+        m->stats.greedy_ms = 0;
+        m->greedy_done = true;
+        return;
+    }
+    RBFD_CUDA(cudaMemcpyAsync(m->d_cur, m->d_dS, sizeof(double4) * m->n_s, cudaMemcpyDeviceToDevice, st));
+    const int Lreq = m->n_levels_req;
+    const double eps_rel = m->opt.eps_absolute ? m->eps / m->S0 : m->eps;
+    const int mode = m->opt.precision == RBFD_FP64 ? 0 : 1;
+    int final_status = RBFD_OK;
+    for (int l = 0; l < Lreq; ++l) {
+        Level L;
+        L.R = m->R[l];
+        L.tau = std::pow(eps_rel, (double)(l + 1) / (double)Lreq);
+        int arg = -1;
+        L.smax = std::sqrt(maxnorm(m, m->d_cur, &arg));
+        const double R2 = L.R * L.R;
+        RBFD_CUDA(cudaMemsetAsync(m->d_sel, 0, m->n_s, st));
+        k_level_init<<<cdiv(std::max(m->n_pb, 1), kThreads), kThreads, 0, st>>>(
+            m->opt.first_point == 1 ? 1 : 0, 0, m->d_inv, m->d_xs, m->d_cur, m->n_pb, m->cap, m->dim, R2,
+            m->d_pb_lo, m->d_pb_hi, m->d_sel, m->d_cx, m->d_cid, m->d_G, m->d_w, m->d_alpha, m->d_nb_cnt,
+            m->d_nb_list, m->d_bbox, m->d_st);
+        RBFD_CUDA(cudaGetLastError());
+
+        GrowArgs g{};
+        g.cap = m->cap;
+        g.n_pb = m->n_pb;
+        g.dim = m->dim;
+        g.R = L.R;
+        g.R2 = R2;
+        g.inv = m->d_inv;
+        g.xs = m->d_xs;
+        g.pb_lo = m->d_pb_lo;
+        g.pb_hi = m->d_pb_hi;
+        g.sel = m->d_sel;
+        g.cx = m->d_cx;
+        g.cid = m->d_cid;
+        g.phi = m->d_phi;
+        g.nb_cnt = m->d_nb_cnt;
+        g.nb_list = m->d_nb_list;
+        g.G = m->d_G;
+        g.Gw = m->d_G;
+        g.y = m->d_y;
+        g.red = m->d_red;
+        g.gpart = m->d_gpart;
+        g.w = m->d_w;
+        g.alpha = m->d_alpha;
+        g.cur = m->d_cur;
+        g.st = m->d_st;
+
+        int n = 1;
+        int resumes = 0;
+        for (;;) {
+            // ---- greedy steps, launched in batches; the device decides when to stop
+            const int kBatch = 16;
+            bool stopped = false;
+            while (!stopped) {
+                for (int s = 0; s < kBatch; ++s) {
+                    SweepArgs a = base_sweep_args(m, L.R, L.tau);
+                    a.n = n;
+                    int nch = n_chunks_for(m, n);
+                    a.chunk_len = (n + nch - 1) / nch;
+                    a.is_step = 1;
+                    a.E_out = nullptr;
+                    launch_sweep(m->dim, m->opt.basis, mode, dim3(m->n_pb, nch), a, st);
+                    if (n >= m->cap) break;  // the sweep above stops the level
+                    g.n = n;
+                    const unsigned gp = cdiv(std::max(n, m->n_pb), kThreads);
+                    if (m->dim == 2) launch_phi_d<2>(m->opt.basis, gp, g, st);
+                    else launch_phi_d<3>(m->opt.basis, gp, g, st);
+                    const int nyb = (int)cdiv(n, kYWarps);
+                    g.n_red = nyb;
+                    k_grow_y<<<nyb, kYWarps * 32, 0, st>>>(g);
+                    const int n_jt = (int)cdiv(n, kJT);
+                    k_colsum<<<dim3(cdiv(n, kThreads), n_jt), kThreads, 0, st>>>(n, m->cap, m->d_G, m->d_y,
+                                                                                 m->d_gpart, m->d_st);
+                    k_grow_finish<<<cdiv(n + 1, kThreads), kThreads, 0, st>>>(g, n_jt);
+                    RBFD_CUDA(cudaGetLastError());
+                    ++n;
+                }
+                read_state(m);
+                stopped = m->h_st->stop != 0 || n >= m->cap;
+                if (m->h_st->status == RBFD_ESINGULAR)
+                    fail(RBFD_ESINGULAR, "Phi_cc is not positive definite at level " + std::to_string(l) +
+                                             " (coincident or near-coincident controls)");
+            }
+            n = m->h_st->n;
+            // ---- level close: FP64 iterative refinement of alpha
+            for (int it = 0; it < std::max(0, m->opt.refine_iters); ++it) {
+                const unsigned nb = cdiv(n, kThreads);
+                if (m->dim == 2) launch_resid_d<2>(m->opt.basis, nb, n, L.R, m, st);
+                else launch_resid_d<3>(m->opt.basis, nb, n, L.R, m, st);
+                std::vector<double> rmax(nb);
+                RBFD_CUDA(cudaMemcpyAsync(rmax.data(), m->d_red, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+                RBFD_CUDA(cudaStreamSynchronize(st));
+                double r = 0;
+                for (double v : rmax) r = std::max(r, v);
+                if (r <= 1e-15 * m->S0) break;
+                k_lower_mv3<<<cdiv(n, 8), 256, 0, st>>>(n, m->cap, m->d_G, m->d_vec, m->d_vec2);
+                const int n_jt = (int)cdiv(n, kJT);
+                k_colsum3<<<dim3(cdiv(n, kThreads), n_jt), kThreads, 0, st>>>(n, m->cap, m->d_G, m->d_vec2,
+                                                                              m->d_v4part);
+                k_apply_correction<<<cdiv(n, kThreads), kThreads, 0, st>>>(n, m->cap, n_jt, m->d_v4part, m->d_alpha);
+                RBFD_CUDA(cudaGetLastError());
+                m->stats.refine_sweeps++;
+            }
+            // ---- confirm sweep in FP64: stores E = dS_l - Phi_sc alpha
+            {
+                SweepArgs a = base_sweep_args(m, L.R, L.tau);
+                a.n = n;
+                int nch = n_chunks_for(m, n);
+                a.chunk_len = (n + nch - 1) / nch;
+                a.is_step = 0;
+                a.E_out = m->d_E;
+                launch_sweep(m->dim, m->opt.basis, 0, dim3(m->n_pb, nch), a, st);
+                RBFD_CUDA(cudaGetLastError());
+                read_state(m);
+            }
+            const double emax = m->h_st->emax;
+            // a level stops early only if its confirmed error is below tau
+            if (emax < L.tau || n >= m->cap || resumes >= 4 || n >= m->n_s) {
+                L.emax = emax;
+                L.status = (emax < L.tau) ? RBFD_OK : RBFD_ENOTCONV;
+                break;
+            }
+            // the mixed-precision selection stopped a little early: resume
+            ++resumes;
+            m->stats.confirm_resumes++;
+            RBFD_CUDA(cudaMemsetAsync(&m->d_st->stop, 0, sizeof(int), st));
+        }
+        L.nc = n;
+        m->stats.greedy_steps += n - 1;
+        // save the level
+        L.d_cx = dalloc<double4>(n, "level controls");
+        L.d_alpha = dalloc<double4>(n, "level weights");
+        RBFD_CUDA(cudaMemcpyAsync(L.d_cx, m->d_cx, sizeof(double4) * n, cudaMemcpyDeviceToDevice, st));
+        RBFD_CUDA(cudaMemcpyAsync(L.d_alpha, m->d_alpha, sizeof(double4) * n, cudaMemcpyDeviceToDevice, st));
+        std::vector<uint32_t> orig(n);
+        std::vector<double4> al(n);
+        k_orig_of_controls<<<cdiv(n, 256), 256, 0, st>>>(m->d_perm, m->d_cid, n, reinterpret_cast<uint32_t *>(m->d_vec2));
+        RBFD_CUDA(cudaMemcpyAsync(orig.data(), m->d_vec2, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
+        RBFD_CUDA(cudaMemcpyAsync(al.data(), m->d_alpha, sizeof(double4) * n, cudaMemcpyDeviceToHost, st));
+        RBFD_CUDA(cudaStreamSynchronize(st));
+        L.idx.resize(n);
+        L.alpha.resize((size_t)n * m->dim);
+        for (int j = 0; j < n; ++j) L.idx[j] = orig[j];
+        for (int j = 0; j < n; ++j) {
+            L.alpha[(size_t)j * m->dim + 0] = al[j].x;
+            L.alpha[(size_t)j * m->dim + 1] = al[j].y;
+            if (m->dim == 3) L.alpha[(size_t)j * m->dim + 2] = al[j].z;
+        }
+        build_control_grid(m, L);
+        if (L.status != RBFD_OK) final_status = RBFD_ENOTCONV;
+        m->levels.push_back(std::move(L));
+        // multi-level subspace: the next level interpolates this level's error
+        RBFD_CUDA(cudaMemcpyAsync(m->d_cur, m->d_E, sizeof(double4) * m->n_s, cudaMemcpyDeviceToDevice, st));
+    }
+    RBFD_CUDA(cudaEventRecord(m->ev1, st));
+    RBFD_CUDA(cudaEventSynchronize(m->ev1));
+    float ms = 0;
+    RBFD_CUDA(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
+    m->stats.greedy_ms = ms;
+    unsigned long long pr[2];
+    RBFD_CUDA(cudaMemcpy(pr, m->d_pairs, sizeof(pr), cudaMemcpyDeviceToHost));
+    m->stats.pairs_useful = (int64_t)pr[0];
+    m->stats.pairs_visited = (int64_t)pr[1];
+    m->greedy_done = true;
+    if (!m->levels.empty() && !(m->levels.back().emax < eps_rel)) final_status = RBFD_ENOTCONV;
+    if (final_status != RBFD_OK) fail(final_status, "greedy selection did not reach eps before the control cap");
+}
+
+}  // namespace rbfd

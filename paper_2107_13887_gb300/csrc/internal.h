@@ -1,0 +1,162 @@
+// internal.h -- host-side state of an rbfd mesh and the launch wrappers that
+// the C ABI (api.cu) drives.  Not part of the public interface.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rbfd.h"
+#include "common.cuh"
+
+namespace rbfd {
+
+// Error carrying an rbfd_status; thrown inside the library, converted to a
+// status + thread-local message at the C boundary.
+struct Error {
+    int status;
+    std::string msg;
+};
+
+void set_last_error(const std::string &msg);
+[[noreturn]] void fail(int status, const std::string &msg);
+void check_cuda(cudaError_t e, const char *what);
+#define RBFD_CUDA(call) ::rbfd::check_cuda((call), #call)
+
+// Device allocation that reports RBFD_ENOMEM through Error.
+void *dmalloc(size_t bytes, const char *what);
+void dfree(void *p);
+
+template <typename T>
+T *dalloc(size_t n, const char *what) {
+    return static_cast<T *>(dmalloc(sizeof(T) * (n ? n : 1), what));
+}
+
+// ------------------------------------------------------------ spatial prep
+
+// Scratch for the radix sort / scan / compaction primitives (grown on demand).
+struct SortScratch {
+    uint32_t *keys_alt = nullptr;
+    uint32_t *vals_alt = nullptr;
+    uint32_t *hist = nullptr;   // 256 * n_blocks
+    uint32_t *block_sums = nullptr;
+    size_t cap_items = 0, cap_hist = 0, cap_sums = 0;
+    void reserve(size_t n_items);
+    void release();
+};
+
+// Stable LSD radix sort of (key, value) pairs by the low key_bits bits of key.
+// The sorted result ends up in keys/vals.
+void radix_sort_pairs(uint32_t *keys, uint32_t *vals, size_t n, int key_bits, SortScratch &s,
+                      cudaStream_t st);
+
+// Exclusive scan of n uint32 values (out may alias in); returns nothing,
+// total written to *total_dev if non-null.
+void exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *total_dev, SortScratch &s,
+                        cudaStream_t st);
+
+// Morton keys of points relative to a box: 2D 16 bits per axis, 3D 10 bits.
+void morton_keys_f64(const double4 *xyz, size_t n, int dim, double3 lo, double3 hi, uint32_t *keys,
+                     uint32_t *vals, cudaStream_t st);
+void morton_keys_f32(const float4 *xyzd, const uint32_t *idx, size_t n, int dim, double3 lo, double3 hi,
+                     uint32_t *keys, uint32_t *vals, cudaStream_t st);
+
+// ------------------------------------------------------------ mesh state
+
+struct Level {
+    double R = 0, tau = 0, smax = 0, emax = 0;
+    int64_t nc = 0;
+    int status = RBFD_OK;
+    std::vector<int64_t> idx;     // original surface indices, selection order
+    std::vector<double> alpha;    // [nc][dim]
+    double4 *d_cx = nullptr;      // control coordinates (FP64)
+    double4 *d_alpha = nullptr;   // weights (FP64)
+    // uniform cell grid over the controls (cell size h) for the volume sweep
+    double3 g0{0, 0, 0};
+    double h = 0;
+    int3 gdim{0, 0, 0};
+    int ncell = 0;
+    uint32_t *d_cell_start = nullptr;  // [ncell + 1]
+    uint32_t *d_cell_ctrl = nullptr;   // [nc] control ids ordered by cell
+};
+
+struct SweepBufs;  // defined in greedy.cu
+
+}  // namespace rbfd
+
+struct rbfd_mesh {
+    int dim = 3;
+    int64_t n_s = 0;
+    int n_levels_req = 0;
+    double eps = 0, S0 = 0;
+    rbfd_options opt{};
+    std::vector<double> R;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    // Morton-sorted surface
+    int n_pb = 0;
+    uint32_t *d_perm = nullptr;  // sorted position -> original index
+    uint32_t *d_inv = nullptr;   // original index -> sorted position
+    double4 *d_xs = nullptr;     // sorted coordinates (FP64, z = 0 in 2D)
+    double4 *d_dS = nullptr;     // sorted displacements
+    double4 *d_cur = nullptr;    // current level target dS_l
+    double4 *d_E = nullptr;      // error of the last confirm sweep
+    double4 *d_pb_lo = nullptr, *d_pb_hi = nullptr, *d_pb_org = nullptr;
+    float4 *d_xs_hi = nullptr, *d_xs_lo = nullptr;  // coordinates relative to the block origin (df)
+
+    // greedy workspace
+    int cap = 0;
+    unsigned char *d_sel = nullptr;
+    double *d_G = nullptr;        // inverse Cholesky factor, cap x cap, row-major lower
+    double4 *d_w = nullptr;       // L^{-1} dS_c
+    double4 *d_alpha = nullptr;   // weights of the current level
+    double4 *d_cx = nullptr;      // control coordinates
+    uint32_t *d_cid = nullptr;    // control sorted positions
+    double *d_phi = nullptr;      // phi(c_new, c_k)
+    double *d_y = nullptr;        // G phi
+    double *d_red = nullptr;      // per-block partial dot products
+    double *d_gpart = nullptr;    // per-row-tile partial column sums
+    double4 *d_vec = nullptr;     // refinement vectors
+    double4 *d_vec2 = nullptr;
+    double4 *d_v4part = nullptr;  // per-row-tile partial column sums, 4-wide
+    uint32_t *d_nb_cnt = nullptr; // controls listed per point block
+    uint32_t *d_nb_list = nullptr;// [n_pb][cap]
+    double4 *d_part = nullptr;    // sweep partial sums [n_chunk_max][n_s]
+    int n_chunk_max = 1;
+    unsigned int *d_pb_done = nullptr;
+    double *d_pb_key = nullptr;
+    int *d_pb_idx = nullptr;
+    unsigned long long *d_pairs = nullptr;  // [2]: useful, visited
+    rbfd::GreedyState *d_st = nullptr;
+    rbfd::GreedyState *h_st = nullptr;  // pinned
+
+    std::vector<rbfd::Level> levels;
+    bool greedy_done = false;
+    rbfd_stats stats{};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    rbfd::SortScratch sort;
+
+    // deform workspace (grown on demand)
+    size_t vol_cap = 0;
+    float4 *d_vin = nullptr;       // input points (x, y, z, d), caller order
+    float4 *d_vpos = nullptr;      // compacted + Morton-sorted points
+    uint32_t *d_vorig = nullptr;   // their caller indices
+    uint32_t *d_vflag = nullptr, *d_vscan = nullptr, *d_vlist = nullptr, *d_vkeys = nullptr;
+    double4 *d_vacc = nullptr;     // accumulated displacement per sorted point
+    void *d_vio = nullptr;         // staging for host inputs/outputs
+    size_t vio_bytes = 0;
+    uint32_t *d_misc = nullptr;    // small counters
+    double *d_bbox = nullptr;      // 8 doubles
+};
+
+namespace rbfd {
+void greedy_run(rbfd_mesh *m);
+void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64, double D, double k,
+                void *out);
+void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS);
+void mesh_free(rbfd_mesh *m);
+}  // namespace rbfd

@@ -1,0 +1,245 @@
+"""ctypes binding of the rbfd C ABI (``include/rbfd.h``).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``_build/librbfd.so``.  The functions keep the C names; ``Mesh`` wraps a handle.
+Host arrays are numpy arrays; device arrays are torch CUDA tensors (pass
+``inputs_on_device=True`` at creation).  If the library cannot be built or
+loaded, every call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ESINGULAR, ENOTCONV, ETIMEOUT, EBUSY, ECUDA, ESTATE = range(9)
+FP64, MIXED = 0, 1
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ESINGULAR", 4: "ENOTCONV", 5: "ETIMEOUT", 6: "EBUSY",
+                7: "ECUDA", 8: "ESTATE"}
+
+
+class RbfdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class rbfd_options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("basis", ctypes.c_int),
+        ("first_point", ctypes.c_int),
+        ("inputs_on_device", ctypes.c_int),
+        ("nc_cap", ctypes.c_int64),
+        ("stream", ctypes.c_void_p),
+        ("eps_absolute", ctypes.c_int),
+        ("refine_iters", ctypes.c_int),
+    ]
+
+
+class rbfd_stats(ctypes.Structure):
+    _fields_ = [
+        ("greedy_ms", ctypes.c_double),
+        ("deform_ms", ctypes.c_double),
+        ("greedy_steps", ctypes.c_int64),
+        ("pairs_useful", ctypes.c_int64),
+        ("pairs_visited", ctypes.c_int64),
+        ("deform_points", ctypes.c_int64),
+        ("refine_sweeps", ctypes.c_int64),
+        ("confirm_resumes", ctypes.c_int64),
+    ]
+
+
+# (name, restype, argtypes) of every function include/rbfd.h declares
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_d = ctypes.c_double
+SIGNATURES = [
+    ("rbfd_options_default", None, [ctypes.POINTER(rbfd_options)]),
+    ("rbfd_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i64, _vp, _vp, ctypes.c_int, _vp, _d,
+                                   ctypes.POINTER(rbfd_options)]),
+    ("rbfd_greedy", ctypes.c_int, [_vp]),
+    ("rbfd_get_level", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_i64), _vp, _vp, ctypes.POINTER(_d)]),
+    ("rbfd_num_levels", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    ("rbfd_level_info", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_d), ctypes.POINTER(_d),
+                                       ctypes.POINTER(_d)]),
+    ("rbfd_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(rbfd_stats)]),
+    ("rbfd_deform", ctypes.c_int, [_vp, _i64, _vp, _vp, _d, _d, _vp]),
+    ("rbfd_deform_f64", ctypes.c_int, [_vp, _i64, _vp, _vp, _d, _d, _vp]),
+    ("rbfd_destroy", ctypes.c_int, [_vp]),
+    ("rbfd_last_error", ctypes.c_char_p, []),
+    ("rbfd_version", ctypes.c_char_p, []),
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load (building first if needed) the CUDA library; raises on failure."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"rbfd CUDA library missing: {_build.LIB} (run paper_2107_13887_gb300.build)")
+        lib = ctypes.CDLL(_build.LIB)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != OK:
+        msg = load().rbfd_last_error().decode(errors="replace")
+        raise RbfdError(rc, msg)
+
+
+def rbfd_last_error() -> str:
+    return load().rbfd_last_error().decode(errors="replace")
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or a torch tensor."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _is_torch_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def default_options() -> rbfd_options:
+    o = rbfd_options()
+    load().rbfd_options_default(ctypes.byref(o))
+    return o
+
+
+@dataclasses.dataclass
+class LevelResult:
+    idx: np.ndarray
+    alpha: np.ndarray
+    e_max: float
+    R: float
+    smax: float
+    tau: float
+
+
+class Mesh:
+    """One surface set up for deformation: ``rbfd_create`` on construction,
+    ``rbfd_destroy`` on ``close()`` / garbage collection."""
+
+    def __init__(self, xyz_s, dS, R, eps, precision=MIXED, basis=2, first_point=0, nc_cap=0, stream=None,
+                 eps_absolute=False, refine_iters=3):
+        lib = load()
+        self._lib = lib
+        on_dev = _is_torch_cuda(xyz_s)
+        if on_dev:
+            import torch
+
+            xyz_s = xyz_s.to(torch.float64).contiguous()
+            dS = dS.to(torch.float64).contiguous()
+            n_s, dim = xyz_s.shape
+        else:
+            xyz_s = np.ascontiguousarray(xyz_s, dtype=np.float64)
+            dS = np.ascontiguousarray(dS, dtype=np.float64)
+            n_s, dim = xyz_s.shape
+        self._keep = (xyz_s, dS)
+        self.dim = int(dim)
+        self.n_s = int(n_s)
+        Rv = np.ascontiguousarray(np.atleast_1d(R), dtype=np.float64)
+        o = default_options()
+        o.precision = int(precision)
+        o.basis = int(basis)
+        o.first_point = int(first_point)
+        o.inputs_on_device = 1 if on_dev else 0
+        o.nc_cap = int(nc_cap)
+        o.stream = stream
+        o.eps_absolute = 1 if eps_absolute else 0
+        o.refine_iters = int(refine_iters)
+        self.on_device = on_dev
+        h = ctypes.c_void_p()
+        _check(lib.rbfd_create(ctypes.byref(h), self.dim, self.n_s, _ptr(xyz_s), _ptr(dS), len(Rv),
+                               _ptr(Rv), float(eps), ctypes.byref(o)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.rbfd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def greedy(self, allow_not_converged: bool = True) -> int:
+        rc = self._lib.rbfd_greedy(self.h)
+        if rc == ENOTCONV and allow_not_converged:
+            return rc
+        _check(rc)
+        return rc
+
+    def num_levels(self) -> int:
+        n = ctypes.c_int()
+        _check(self._lib.rbfd_num_levels(self.h, ctypes.byref(n)))
+        return n.value
+
+    def level(self, l: int) -> LevelResult:
+        nc = ctypes.c_int64()
+        e = ctypes.c_double()
+        _check(self._lib.rbfd_get_level(self.h, l, ctypes.byref(nc), None, None, ctypes.byref(e)))
+        idx = np.zeros(nc.value, dtype=np.int64)
+        al = np.zeros((nc.value, self.dim))
+        _check(self._lib.rbfd_get_level(self.h, l, ctypes.byref(nc), _ptr(idx), _ptr(al), ctypes.byref(e)))
+        R, sm, tau = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(self._lib.rbfd_level_info(self.h, l, ctypes.byref(R), ctypes.byref(sm), ctypes.byref(tau)))
+        return LevelResult(idx, al, e.value, R.value, sm.value, tau.value)
+
+    def levels(self):
+        return [self.level(l) for l in range(self.num_levels())]
+
+    def stats(self) -> dict:
+        s = rbfd_stats()
+        _check(self._lib.rbfd_get_stats(self.h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in rbfd_stats._fields_}
+
+    def deform(self, xyz_v, d_v, D: float, k: float, out=None):
+        """Volume update (Eq. 19 / Eq. 23).  numpy in -> numpy out (host
+        pointers); torch CUDA tensors in -> tensor out (device pointers)."""
+        if self.on_device:
+            import torch
+
+            f64 = xyz_v.dtype == torch.float64
+            n_v = xyz_v.shape[0]
+            if out is None:
+                out = torch.empty((n_v, self.dim), dtype=xyz_v.dtype, device=xyz_v.device)
+        else:
+            f64 = np.asarray(xyz_v).dtype == np.float64
+            dt = np.float64 if f64 else np.float32
+            xyz_v = np.ascontiguousarray(xyz_v, dtype=dt)
+            d_v = np.ascontiguousarray(d_v, dtype=dt)
+            n_v = xyz_v.shape[0]
+            if out is None:
+                out = np.empty((n_v, self.dim), dtype=dt)
+        fn = self._lib.rbfd_deform_f64 if f64 else self._lib.rbfd_deform
+        _check(fn(self.h, int(n_v), _ptr(xyz_v), _ptr(d_v), float(D), float(k), _ptr(out)))
+        return out

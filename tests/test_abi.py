@@ -1,0 +1,85 @@
+"""The C-ABI library builds, loads, and exports every function include/rbfd.h
+declares; the ctypes mirrors of its structs match the C layout.  No GPU
+needed: nothing here launches a kernel."""
+import ctypes
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+from paper_2107_13887_gb300 import build as B
+from paper_2107_13887_gb300 import rbfd
+
+HEADER = os.path.join(B.ROOT, "include", "rbfd.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^[A-Za-z_][\w \*]*?\b(rbfd_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    B.build()
+    return ctypes.CDLL(B.LIB)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for need in ["rbfd_create", "rbfd_greedy", "rbfd_get_level", "rbfd_deform", "rbfd_deform_f64",
+                 "rbfd_destroy", "rbfd_last_error", "rbfd_options_default"]:
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_binding_covers_every_declared_symbol():
+    bound = {name for name, _, _ in rbfd.SIGNATURES}
+    assert set(declared_functions()) <= bound
+
+
+def test_exports_are_plain_c(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    for n in declared_functions():
+        assert n in exported  # unmangled
+
+
+def test_version_and_defaults_without_gpu(lib):
+    L = rbfd.load()
+    assert L.rbfd_version().startswith(b"rbfd")
+    o = rbfd.default_options()
+    assert o.precision == rbfd.MIXED and o.basis == 2 and o.refine_iters == 3
+
+
+def test_struct_layout_matches_header(tmp_path):
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "rbfd.h"\n'
+        "int main(void){\n"
+        'printf("%zu %zu %zu %zu\\n", sizeof(rbfd_options), offsetof(rbfd_options, nc_cap),'
+        " offsetof(rbfd_options, stream), offsetof(rbfd_options, refine_iters));\n"
+        'printf("%zu %zu\\n", sizeof(rbfd_stats), offsetof(rbfd_stats, confirm_resumes));\n'
+        "return 0;}\n"
+    )
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
+    so, onc, ost, ori = map(int, a.split())
+    ss, ocr = map(int, b.split())
+    assert so == ctypes.sizeof(rbfd.rbfd_options)
+    assert onc == rbfd.rbfd_options.nc_cap.offset
+    assert ost == rbfd.rbfd_options.stream.offset
+    assert ori == rbfd.rbfd_options.refine_iters.offset
+    assert ss == ctypes.sizeof(rbfd.rbfd_stats)
+    assert ocr == rbfd.rbfd_stats.confirm_resumes.offset

@@ -1,0 +1,274 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Greedy: the selected control sequence must equal the oracle's exactly up to
+the first step where the oracle's two largest error keys are within rounding
+of each other (relative gap below TIE); past such a near-tie both answers are
+correct, so the rest is checked for validity instead (every level below its
+tolerance, weights solving Eq. 9 on the GPU's own controls).
+
+Volume: FP64 mode within 1e-10 max|dS| of the oracle, mixed mode within
+1e-5 max|dS| (both when the control sequences agree in full).
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial.distance import cdist
+
+import oracle
+from paper_2107_13887_gb300 import rbfd, synth
+
+pytestmark = pytest.mark.gpu
+
+NT = os.cpu_count() or 1
+TIE = 1e-7
+C2 = [4.0, -15.0, 20.0, -10.0, 0.0, 1.0]
+
+
+def phi_np(eta):
+    return np.where(eta < 1.0, np.polyval(C2, np.minimum(eta, 1.0)), 0.0)
+
+
+def run_gpu(c, precision, **kw):
+    m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, **kw)
+    rc = m.greedy()
+    return m, rc
+
+
+def check_sequences(ref, levels, strict_full=False):
+    """Exact match up to the first near-tie; returns True if every level matched in full."""
+    assert len(levels) == ref.n_levels
+    full = True
+    for l, lv in enumerate(levels):
+        r_idx = ref.idx[l]
+        g_idx = lv.idx
+        gaps = ref.step_gap[l]
+        k_tie = next((k for k in range(1, len(r_idx)) if gaps[k] < TIE), len(r_idx))
+        n = min(len(r_idx), len(g_idx), k_tie)
+        mism = np.nonzero(r_idx[:n] != g_idx[:n])[0]
+        assert mism.size == 0, f"level {l}: first mismatch at step {mism[0]} (tie at {k_tie})"
+        if not (len(r_idx) == len(g_idx) and np.array_equal(r_idx, g_idx)):
+            full = False
+            assert k_tie < len(r_idx), f"level {l}: lengths differ ({len(g_idx)} vs {len(r_idx)}) with no near-tie"
+    if strict_full:
+        assert full
+    return full
+
+
+def check_valid(c, levels, S0):
+    """Validity of any correct answer: each level's weights solve Eq. 9 on its
+    own controls, the level error is below tau_l, levels telescope."""
+    cur = c.dS.copy()
+    L = len(c.R)
+    for l, lv in enumerate(levels):
+        C = lv.idx
+        A = phi_np(cdist(c.xyz_s[C], c.xyz_s[C]) / c.R[l])
+        res = A @ lv.alpha - cur[C]
+        assert np.abs(res).max() <= 1e-9 * S0 + 1e-12 * np.abs(lv.alpha).max(), f"level {l}: Eq. 9 residual"
+        E = cur - phi_np(cdist(c.xyz_s, c.xyz_s[C]) / c.R[l]) @ lv.alpha
+        e = np.sqrt((E**2).sum(1)).max() / S0
+        tau = c.eps ** ((l + 1) / L)
+        assert e < tau * (1 + 1e-9), f"level {l}: error {e} above tau {tau}"
+        assert abs(e - lv.e_max) <= 1e-6 * tau + 1e-12, f"level {l}: reported e_max {lv.e_max} vs {e}"
+        cur = E
+
+
+def small_cases():
+    return {
+        "airfoil_bump_333": synth.airfoil_case(333, 7, displacement="bump", seed=1, R=(0.5,), eps=1e-4, D=2.0, k=0.0),
+        "airfoil_horns_2lvl": synth.airfoil_case(600, 9, displacement="horns", seed=2, R=(1.0, 0.2), eps=1e-5,
+                                                 D=2.0, k=5.0),
+        "airfoil_pitch_2lvl": synth.airfoil_case(500, 9, displacement="pitch_heave", seed=0, R=(1.0, 0.2),
+                                                 eps=1e-5, D=2.0, k=5.0),
+        "wing_ridge_2lvl": synth.wing_case(40, 15, 6, displacement="ridge", seed=3, R=(1.5, 0.4), eps=1e-3,
+                                           D=1.0, k=4.0),
+        "wing_sinusoid": synth.wing_case(30, 12, 5, displacement="sinusoid", seed=0, R=(1.5,), eps=1e-3,
+                                         D=1.0, k=4.0),
+    }
+
+
+CASES = small_cases()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
+def test_greedy_and_deform_parity(name, precision):
+    c = CASES[name]
+    ref = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, n_threads=NT)
+    m, rc = run_gpu(c, precision)
+    levels = m.levels()
+    full = check_sequences(ref, levels)
+    check_valid(c, levels, ref.S0)
+    for l, lv in enumerate(levels):
+        assert abs(lv.smax - ref.smax[l]) <= 1e-12 * ref.S0 + (0 if full else 1e-6 * ref.S0)
+        if full and l == 0:
+            amax = np.abs(ref.alpha[l]).max()
+            assert np.abs(lv.alpha - ref.alpha[l]).max() <= 1e-6 * amax
+    if not full:
+        return
+    dv_ref = oracle.deform(ref, c.xyz_s, c.R, c.xyz_v, c.d_v, c.k, c.D, n_threads=NT)
+    dv = m.deform(c.xyz_v, c.d_v, c.D, c.k)
+    tol = 1e-10 if precision == rbfd.FP64 else 1e-5
+    err = np.abs(dv.astype(np.float64) - dv_ref).max()
+    # float32 output: add half an ulp of the largest displacement
+    assert err <= tol * ref.S0 + np.abs(dv_ref).max() * 2.0**-24, f"volume error {err / ref.S0:g} S0"
+    dv64 = m.deform(c.xyz_v.astype(np.float64), c.d_v.astype(np.float64), c.D, c.k)
+    assert np.abs(dv64 - dv_ref).max() <= tol * ref.S0
+    st = m.stats()
+    assert 0 < st["pairs_useful"] <= st["pairs_visited"]
+    m.close()
+
+
+@pytest.mark.parametrize("basis", ["C0", "C4", "C6"])
+def test_other_wendland_bases_fp64(basis):
+    c = synth.airfoil_case(256, 6, displacement="bump", seed=0, R=(0.6,), eps=1e-3, D=2.0, k=0.0)
+    ref = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, basis=basis, n_threads=NT)
+    m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=rbfd.FP64, basis=oracle.BASIS[basis])
+    m.greedy()
+    full = check_sequences(ref, m.levels())
+    if full:
+        dv_ref = oracle.deform(ref, c.xyz_s, c.R, c.xyz_v, c.d_v, c.k, c.D, basis=basis, n_threads=NT)
+        dv = m.deform(c.xyz_v.astype(np.float64), c.d_v.astype(np.float64), c.D, c.k)
+        assert np.abs(dv - dv_ref).max() <= 1e-10 * ref.S0
+
+
+@pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
+def test_first_point_argmax_rule(precision):
+    c = synth.airfoil_case(300, 5, displacement="horns", seed=5, R=(1.0, 0.2), eps=1e-4, D=2.0, k=5.0)
+    ref = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, first_rule=1, n_threads=NT)
+    m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, first_point=1)
+    m.greedy()
+    check_sequences(ref, m.levels())
+
+
+def test_naca0012_400_full_fp64_and_mixed():
+    c = synth.make_config("naca0012_400s_40kv_bump")
+    ref = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, n_threads=NT)
+    dv_ref = oracle.deform(ref, c.xyz_s, c.R, c.xyz_v, c.d_v, c.k, c.D, n_threads=NT)
+    for precision, tol in ((rbfd.FP64, 1e-10), (rbfd.MIXED, 1e-5)):
+        m, _ = run_gpu(c, precision)
+        assert check_sequences(ref, m.levels(), strict_full=True)
+        dv = m.deform(c.xyz_v, c.d_v, c.D, c.k).astype(np.float64)
+        assert np.abs(dv - dv_ref).max() <= tol * ref.S0 + np.abs(dv_ref).max() * 2.0**-24
+
+
+@pytest.mark.parametrize("disp", ["horns", "pitch_heave"])
+def test_naca0012_4000_1m_full_mixed(disp):
+    c = synth.make_config(f"naca0012_4000s_1mv_{disp}")
+    ref = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, n_threads=NT)
+    m, _ = run_gpu(c, rbfd.MIXED)
+    levels = m.levels()
+    full = check_sequences(ref, levels)
+    check_valid(c, levels, ref.S0)
+    dv = m.deform(c.xyz_v, c.d_v, c.D, c.k).astype(np.float64)
+    if full:
+        dv_ref = oracle.deform(ref, c.xyz_s, c.R, c.xyz_v, c.d_v, c.k, c.D, n_threads=NT)
+        assert np.abs(dv - dv_ref).max() <= 1e-5 * ref.S0 + np.abs(dv_ref).max() * 2.0**-24
+
+
+# ---------------------------------------------------------------- edge cases
+
+
+def test_single_surface_point():
+    xyz = np.array([[0.3, 0.1]])
+    dS = np.array([[0.01, -0.02]])
+    m = rbfd.Mesh(xyz, dS, [0.5], 1e-3, precision=rbfd.MIXED)
+    m.greedy()
+    lv = m.levels()
+    assert len(lv) == 1 and lv[0].idx.tolist() == [0]
+    np.testing.assert_allclose(lv[0].alpha, dS, rtol=0, atol=1e-15)
+    xv = np.array([[0.3, 0.1], [0.3, 0.35], [5.0, 5.0]], dtype=np.float32)
+    dv = np.array([0.0, 0.25, 7.0], dtype=np.float32)
+    out = m.deform(xv, dv, D=1.0, k=0.0)
+    ref = oracle.greedy(xyz, dS, [0.5], 1e-3)
+    want = oracle.deform(ref, xyz, [0.5], xv, dv, 0.0, 1.0)
+    np.testing.assert_allclose(out, want, rtol=0, atol=1e-7)
+
+
+def test_zero_displacement_gives_zero_levels():
+    c = synth.airfoil_case(200, 4, displacement="bump", seed=0)
+    m = rbfd.Mesh(c.xyz_s, np.zeros_like(c.dS), c.R, c.eps)
+    m.greedy()
+    assert m.num_levels() == 0
+    out = m.deform(c.xyz_v, c.d_v, 2.0, 0.0)
+    assert not out.any()
+
+
+def test_empty_and_out_of_reach_volumes():
+    c = synth.airfoil_case(200, 4, displacement="bump", seed=0)
+    m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps)
+    m.greedy()
+    out = m.deform(np.zeros((0, 2), np.float32), np.zeros(0, np.float32), 2.0, 0.0)
+    assert out.shape == (0, 2)
+    far = np.full((1000, 2), 50.0, np.float32)
+    out = m.deform(far, np.full(1000, 30.0, np.float32), 2.0, 0.0)
+    assert not out.any()
+
+
+def test_cap_reports_not_converged():
+    c = synth.airfoil_case(300, 0, displacement="bump", seed=0, eps=1e-8)
+    m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, nc_cap=7)
+    rc = m.greedy()
+    assert rc == rbfd.ENOTCONV
+    lv = m.levels()
+    assert len(lv[0].idx) == 7
+    ref = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, nc_cap=7)
+    assert ref.status == oracle.ENOTCONV
+    assert np.array_equal(ref.idx[0], lv[0].idx)
+
+
+def test_duplicate_point_is_singular():
+    c = synth.airfoil_case(64, 0, displacement="bump", seed=0)
+    xyz = np.concatenate([c.xyz_s, c.xyz_s[5:6]])
+    dS = np.concatenate([c.dS, c.dS[5:6] + 0.01])
+    m = rbfd.Mesh(xyz, dS, c.R, 1e-12, precision=rbfd.FP64)
+    with pytest.raises(rbfd.RbfdError) as ei:
+        m.greedy(allow_not_converged=False)
+    assert ei.value.status == rbfd.ESINGULAR
+
+
+def test_invalid_arguments():
+    xyz = np.zeros((4, 2))
+    for kw in (dict(R=[0.0], eps=1e-3), dict(R=[1.0], eps=0.0), dict(R=[1.0], eps=2.0)):
+        with pytest.raises(rbfd.RbfdError) as ei:
+            rbfd.Mesh(xyz, xyz, kw["R"], kw["eps"])
+        assert ei.value.status == rbfd.EINVAL
+    with pytest.raises(rbfd.RbfdError):
+        rbfd.Mesh(np.zeros((4, 4)), np.zeros((4, 4)), [1.0], 1e-3)
+
+
+def test_deform_before_greedy_is_a_state_error():
+    c = synth.airfoil_case(100, 2, displacement="bump", seed=0)
+    m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps)
+    with pytest.raises(rbfd.RbfdError) as ei:
+        m.deform(c.xyz_v, c.d_v, 2.0, 0.0)
+    assert ei.value.status == rbfd.ESTATE
+
+
+def test_device_pointers_match_host_pointers():
+    torch = pytest.importorskip("torch")
+    c = synth.airfoil_case(500, 8, displacement="horns", seed=7, R=(1.0, 0.2), eps=1e-4, D=2.0, k=5.0)
+    mh = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps)
+    mh.greedy()
+    outh = mh.deform(c.xyz_v, c.d_v, c.D, c.k)
+    dev = torch.device("cuda:0")
+    md = rbfd.Mesh(torch.from_numpy(c.xyz_s).to(dev), torch.from_numpy(c.dS).to(dev), c.R, c.eps)
+    md.greedy()
+    for a, b in zip(mh.levels(), md.levels()):
+        assert np.array_equal(a.idx, b.idx) and np.array_equal(a.alpha, b.alpha)
+    outd = md.deform(torch.from_numpy(c.xyz_v).to(dev), torch.from_numpy(c.d_v).to(dev), c.D, c.k)
+    assert np.array_equal(outd.cpu().numpy(), outh)
+
+
+def test_repeat_greedy_is_deterministic():
+    c = CASES["airfoil_horns_2lvl"]
+    m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps)
+    m.greedy()
+    a = m.levels()
+    o1 = m.deform(c.xyz_v, c.d_v, c.D, c.k)
+    m.greedy()
+    b = m.levels()
+    o2 = m.deform(c.xyz_v, c.d_v, c.D, c.k)
+    for x, y in zip(a, b):
+        assert np.array_equal(x.idx, y.idx) and np.array_equal(x.alpha, y.alpha)
+    assert np.array_equal(o1, o2)
