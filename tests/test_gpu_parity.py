@@ -36,23 +36,26 @@ def run_gpu(c, precision, **kw):
 
 
 def check_sequences(ref, levels, strict_full=False):
-    """Exact match up to the first near-tie; returns True if every level matched in full."""
+    """Element-by-element equality of the control sequences.  The first
+    mismatch is allowed only at a step where the oracle's two largest keys are
+    within TIE of each other (both choices are correct there); from that point
+    on the runs interpolate different targets and only validity is checked.
+    Returns True if every level matched in full."""
     assert len(levels) == ref.n_levels
-    full = True
     for l, lv in enumerate(levels):
-        r_idx = ref.idx[l]
-        g_idx = lv.idx
-        gaps = ref.step_gap[l]
-        k_tie = next((k for k in range(1, len(r_idx)) if gaps[k] < TIE), len(r_idx))
-        n = min(len(r_idx), len(g_idx), k_tie)
+        r_idx, g_idx, gaps = ref.idx[l], lv.idx, ref.step_gap[l]
+        n = min(len(r_idx), len(g_idx))
         mism = np.nonzero(r_idx[:n] != g_idx[:n])[0]
-        assert mism.size == 0, f"level {l}: first mismatch at step {mism[0]} (tie at {k_tie})"
-        if not (len(r_idx) == len(g_idx) and np.array_equal(r_idx, g_idx)):
-            full = False
-            assert k_tie < len(r_idx), f"level {l}: lengths differ ({len(g_idx)} vs {len(r_idx)}) with no near-tie"
-    if strict_full:
-        assert full
-    return full
+        if mism.size:
+            k = int(mism[0])
+            assert gaps[k] < TIE, f"level {l}: control {k} differs ({g_idx[k]} vs {r_idx[k]}) with gap {gaps[k]:g}"
+            assert not strict_full
+            return False
+        if len(r_idx) != len(g_idx):
+            # same controls, different stopping step: the stop test sat on its threshold
+            assert not strict_full, f"level {l}: {len(g_idx)} controls vs {len(r_idx)}"
+            return False
+    return True
 
 
 def check_valid(c, levels, S0):
