@@ -1,0 +1,389 @@
+"""Benchmark: RBF pair-evaluations/s of the multi-level greedy RBF mesh
+deformation hot path on one GB300 (or N replicas under torchrun).
+
+One step = the whole path for the 2D airfoil workload of 4,000 surface and
+1,000,000 volume points, two greedy levels (R = 1c then 0.2c), eps = 1e-5,
+for both displacement cases: a global rigid pitch (5 deg) + heave (0.05c), and
+a three-horn ice shape.  For each case: rbfd_create (Morton prep), rbfd_greedy
+(both levels, to eps), rbfd_deform (volume point reduction + update of every
+volume point), rbfd_destroy.
+
+value   = useful point/control pair evaluations (|r - r_c| < R) of all timed
+          steps on all ranks / max over ranks of the device time (CUDA events on
+          the library's stream), inputs resident in HBM, L2 flushed between steps.
+e2e     = the same through host (pinned) buffers: host->device copies of the
+          inputs and device->host copies of the results inside the timed region.
+roofline, cpu_baseline (the FP64 oracle on the host cores), clocks,
+gpu_launches: see the design doc.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "naca0012_4000s_1mv"
+CASES = ("naca0012_4000s_1mv_pitch_heave", "naca0012_4000s_1mv_horns")
+METRIC = "rbf_pair_evals_per_s"
+UNIT = "pair-evals/s"
+
+# FP32-pipe operations per useful pair of the double-float evaluation, counted
+# from csrc/common.cuh (df_add 20, df_mul 7, df_sqr 7, df_sqrt 12 incl. MUFU;
+# see the design doc for the tally).  2D: differences 2 x 20, r^2 2 x 7 + 20,
+# sqrt 12, eta 7, phi 63, accumulate 2 x 27 -> 210; 3D -> 284.
+OPS_PER_PAIR_DF = {2: 210, 3: 284}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_cases():
+    from paper_2107_13887_gb300 import synth
+
+    return [synth.make_config(n, seed=0) for n in CASES]
+
+
+# ------------------------------------------------------------ useful pairs
+
+def useful_pairs_oracle_run(case, res, Dl, sample_idx=None):
+    """Useful pair evaluations (|r - r_c| < R) of the oracle's own run:
+    every greedy sweep (one per added control, plus the stopping sweep) and
+    the volume update of the sampled volume points."""
+    from scipy.spatial import cKDTree
+
+    total = 0
+    tree_s = cKDTree(case.xyz_s)
+    for l, R in enumerate(case.R):
+        C = res.idx[l]
+        n = len(C)
+        cnt = np.array([len(v) for v in tree_s.query_ball_point(case.xyz_s[C], r=R * (1 - 1e-12))])
+        # control j is present in the sweeps of steps j+1 .. n (n - j sweeps)
+        total += int((cnt * (n - np.arange(n))).sum())
+    xv = case.xyz_v if sample_idx is None else case.xyz_v[sample_idx]
+    dv = case.d_v if sample_idx is None else case.d_v[sample_idx]
+    for l, R in enumerate(case.R):
+        if not Dl[l] > 0 or len(res.idx[l]) == 0:
+            continue
+        keep = dv.astype(np.float64) < Dl[l]
+        if not keep.any():
+            continue
+        tree_c = cKDTree(case.xyz_s[res.idx[l]])
+        total += int(sum(len(v) for v in tree_c.query_ball_point(xv[keep].astype(np.float64), r=R * (1 - 1e-12))))
+    return total
+
+
+def oracle_step(cases, frac, rng_seed=0, n_threads=None):
+    """One bounded CPU step with the FP64 oracle: full greedy of every case,
+    volume update of a random `frac` of the volume points.  Returns
+    (useful_pairs, seconds)."""
+    import oracle
+
+    nt = n_threads or (os.cpu_count() or 1)
+    rng = np.random.default_rng(rng_seed)
+    pairs = 0
+    secs = 0.0
+    for c in cases:
+        idx = np.sort(rng.choice(c.n_v, size=max(1, int(frac * c.n_v)), replace=False))
+        xv = np.ascontiguousarray(c.xyz_v[idx])
+        dv = np.ascontiguousarray(c.d_v[idx])
+        t0 = time.perf_counter()
+        res = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, n_threads=nt)
+        oracle.deform(res, c.xyz_s, c.R, xv, dv, c.k, c.D, n_threads=nt)
+        secs += time.perf_counter() - t0
+        Dl = oracle.support_distances(res.smax, c.k, c.D)
+        pairs += useful_pairs_oracle_run(c, res, Dl, idx)
+    return pairs, secs
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ GPU arm
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2107_13887_gb300 import rbfd
+
+    rbfd.load()
+    precision = rbfd.MIXED if args.precision == "mixed" else rbfd.FP64
+    cases = make_cases()
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+
+    # device-resident inputs
+    dcases = []
+    for c in cases:
+        dcases.append(dict(
+            xyz_s=torch.from_numpy(c.xyz_s).to(dev), dS=torch.from_numpy(c.dS).to(dev),
+            xyz_v=torch.from_numpy(c.xyz_v).to(dev), d_v=torch.from_numpy(c.d_v).to(dev),
+            out=torch.empty((c.n_v, c.dim), dtype=torch.float32, device=dev)))
+    # pinned host inputs for the end-to-end leg
+    hcases = []
+    for c in cases:
+        def pin(a):
+            t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+            return t.numpy()
+        hcases.append(dict(xyz_s=pin(c.xyz_s), dS=pin(c.dS), xyz_v=pin(c.xyz_v), d_v=pin(c.d_v),
+                           out=pin(np.zeros((c.n_v, c.dim), np.float32))))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def one_step(src, record):
+        pairs = 0
+        stats = []
+        for c, d in zip(cases, src):
+            m = rbfd.Mesh(d["xyz_s"], d["dS"], c.R, c.eps, precision=precision, stream=sp, profile=record)
+            m.greedy()
+            m.deform(d["xyz_v"], d["d_v"], c.D, c.k, out=d["out"])
+            st = m.stats()
+            m.close()
+            stats.append(st)
+            pairs += st["pairs_useful"]
+        return pairs, stats
+
+    def timed(src, K, W, record):
+        for _ in range(W):
+            one_step(src, False)
+        torch.cuda.synchronize()
+        tot_ms, tot_pairs, all_stats = 0.0, 0, []
+        for _ in range(K):
+            flush.zero_()
+            torch.cuda.synchronize()
+            if ws > 1:
+                torch.distributed.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p, st = one_step(src, record)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot_ms += e0.elapsed_time(e1)
+            tot_pairs += p
+            all_stats.extend(st)
+        return tot_ms, tot_pairs, all_stats
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms, pairs, stats = timed(dcases, args.steps, args.warmup, True)
+    clocks = sampler.stop()
+    e2e = None
+    if not args.no_e2e:
+        ms_e, pairs_e, _ = timed(hcases, args.steps, 1, False)
+    # aggregate over ranks: units summed, time = max
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([float(pairs)], dtype=torch.float64, device=dev)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms_all, pairs_all = float(t.item()), float(u.item())
+        if not args.no_e2e:
+            t = torch.tensor([ms_e], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            u = torch.tensor([float(pairs_e)], dtype=torch.float64, device=dev)
+            dist.all_reduce(u, op=dist.ReduceOp.SUM)
+            ms_e, pairs_e = float(t.item()), float(u.item())
+    else:
+        ms_all, pairs_all = ms, float(pairs)
+    if not args.no_e2e:
+        h2d = sum(c.xyz_s.nbytes + c.dS.nbytes + c.xyz_v.nbytes + c.d_v.nbytes for c in cases)
+        d2h = sum(c.n_v * c.dim * 4 for c in cases)
+        e2e = {"value": pairs_e / (ms_e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e / args.steps}
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel class (device time inside the timed region)
+    kinds = {
+        "sweep": (sum(s["sweep_ms"] for s in stats), sum(s["sweep_launches"] for s in stats),
+                  sum(s["sweep_pairs_useful"] for s in stats)),
+        "grow": (sum(s["grow_ms"] for s in stats), sum(s["grow_launches"] for s in stats), 0),
+        "vol": (sum(s["vol_ms"] for s in stats), sum(s["vol_launches"] for s in stats),
+                sum(s["vol_pairs_useful"] for s in stats)),
+    }
+    dim = cases[0].dim
+    peak_ops = SM_COUNT * FP32_LANES_PER_SM * 2.07e9  # FP32 issue slots per second at max SM clock
+    ev_kinds = {k: v for k, v in kinds.items() if k != "grow"}
+    dom = max(ev_kinds, key=lambda k: ev_kinds[k][0])
+    d_ms, d_launch, d_pairs = ev_kinds[dom]
+    achieved = d_pairs * OPS_PER_PAIR_DF[dim] / (d_ms / 1e3) if d_ms > 0 else 0.0
+    roofline = {
+        "bound": "alu", "kernel": {"sweep": "k_sweep<2,2,1>", "vol": "k_vol_sweep<2,2,1>"}[dom],
+        "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "TFLOP/s",
+        "frac": achieved / peak_ops, "traffic": None,
+        "ops_per_pair": OPS_PER_PAIR_DF[dim], "avg_launch_ms": d_ms / max(1, d_launch),
+        "launches": int(d_launch),
+        "kernel_ms": {k: round(v[0], 3) for k, v in kinds.items()},
+        "note": "FP32-pipe operations of the double-float pair evaluation; peak = 152 SMs x 128 FP32 lanes x 2.07 GHz",
+    }
+    greedy_ms = [s["greedy_ms"] for s in stats]
+    line = {
+        "metric": METRIC, "value": pairs_all / (ms_all / 1e3), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32x2+f64" if precision == rbfd.MIXED else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cases": list(CASES), "n_surface": 4000, "n_volume": 1000000,
+                   "levels": 2, "R": [1.0, 0.2], "eps": 1e-5, "k": 5.0, "D": 2.0, "precision": args.precision,
+                   "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas{ws}"},
+        "time_to_eps_ms": {"pitch_heave": statistics.median(greedy_ms[0::2]),
+                           "horns": statistics.median(greedy_ms[1::2])},
+        "pairs_useful_per_step": pairs_all / args.steps / ws,
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": int(sum(s["launches"] for s in stats)),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        frac = 0.05
+        p_cpu, s_cpu = oracle_step(cases, frac)
+        line["cpu_baseline"] = {"value": p_cpu / s_cpu, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                                "sample": f"full greedy of both cases + volume update of a random {frac:.0%} "
+                                          f"of the volume points (FP64 oracle, OpenMP)",
+                                "seconds": s_cpu}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cases = make_cases()
+    frac = 0.02
+    cores = cpu_cores()
+    for _ in range(args.warmup):
+        oracle_step(cases, frac, rng_seed=1)
+    tot_p, tot_s = 0, 0.0
+    for k in range(args.steps):
+        p, s = oracle_step(cases, frac, rng_seed=100 + k)
+        tot_p += p
+        tot_s += s
+    v = tot_p / tot_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_s * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cases": list(CASES), "n_surface": 4000, "n_volume": 1000000,
+                   "levels": 2, "R": [1.0, 0.2], "eps": 1e-5, "k": 5.0, "D": 2.0},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: full greedy of both cases + volume update of a random {frac:.0%} "
+                                   f"of the volume points"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -55,6 +55,8 @@ typedef struct rbfd_options {
     void *stream;          /* cudaStream_t to run on; NULL = a stream the mesh creates */
     int eps_absolute;      /* 0: eps is relative to max_i |dS_i| (default); 1: absolute length */
     int refine_iters;      /* iterative-refinement sweeps at level close (default 3) */
+    int profile;           /* 1: time each kernel class with CUDA events on the mesh's stream
+                              (rbfd_stats.*_ms / *_launches); adds two event records per launch */
 } rbfd_options;
 
 typedef struct rbfd_mesh rbfd_mesh;
@@ -126,6 +128,12 @@ typedef struct rbfd_stats {
     int64_t deform_points;   /* volume points updated at least at one level (sum over levels) */
     int64_t refine_sweeps;   /* iterative-refinement sweeps run at level close */
     int64_t confirm_resumes; /* times a level-close confirm sweep reopened the greedy */
+    int64_t launches;        /* kernels this mesh launched (all calls since creation) */
+    /* per kernel class, since creation (event timing only with opt.profile = 1):
+       surface error sweep (Eq. 12 + argmax), control-system growth, volume sweep (Eq. 23) */
+    double sweep_ms, grow_ms, vol_ms;
+    int64_t sweep_launches, grow_launches, vol_launches;
+    int64_t sweep_pairs_useful, sweep_pairs_visited, vol_pairs_useful, vol_pairs_visited;
 } rbfd_stats;
 
 int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st);

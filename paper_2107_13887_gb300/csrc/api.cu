@@ -38,6 +38,53 @@ void dfree(void *p) {
     if (p) cudaFree(p);
 }
 
+cudaEvent_t Profiler::get() {
+    if (!free_ev.empty()) {
+        cudaEvent_t e = free_ev.back();
+        free_ev.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    RBFD_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+cudaEvent_t Profiler::begin(cudaStream_t st) {
+    if (!on) return nullptr;
+    cudaEvent_t a = get();
+    RBFD_CUDA(cudaEventRecord(a, st));
+    return a;
+}
+
+void Profiler::end(int kind, cudaEvent_t a, cudaStream_t st, int n_launches) {
+    launches[kind] += n_launches;
+    if (!on || !a) return;
+    cudaEvent_t b = get();
+    RBFD_CUDA(cudaEventRecord(b, st));
+    pend.push_back({kind, a, b});
+}
+
+void Profiler::flush() {
+    for (auto &p : pend) {
+        float ms_ = 0.f;
+        if (cudaEventElapsedTime(&ms_, p.a, p.b) == cudaSuccess) ms[p.kind] += ms_;
+        else cudaGetLastError();
+        free_ev.push_back(p.a);
+        free_ev.push_back(p.b);
+    }
+    pend.clear();
+}
+
+void Profiler::release() {
+    for (auto &p : pend) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    pend.clear();
+    for (auto e : free_ev) cudaEventDestroy(e);
+    free_ev.clear();
+}
+
 void mesh_free(rbfd_mesh *m) {
     if (!m) return;
     int prev = 0;
@@ -58,6 +105,7 @@ void mesh_free(rbfd_mesh *m) {
                     m->d_vacc, m->d_vio, m->d_misc, m->d_bbox};
     for (void *p : ptrs) dfree(p);
     m->sort.release();
+    m->prof.release();
     if (m->h_st) cudaFreeHost(m->h_st);
     if (m->ev0) cudaEventDestroy(m->ev0);
     if (m->ev1) cudaEventDestroy(m->ev1);
@@ -113,6 +161,7 @@ void rbfd_options_default(rbfd_options *opt) {
     opt->stream = nullptr;
     opt->eps_absolute = 0;
     opt->refine_iters = 3;
+    opt->profile = 0;
 }
 
 int rbfd_create(rbfd_mesh **out, int dim, int64_t n_s, const double *xyz_s, const double *dS, int n_levels,
@@ -155,6 +204,8 @@ int rbfd_create(rbfd_mesh **out, int dim, int64_t n_s, const double *xyz_s, cons
         }
         RBFD_CUDA(cudaEventCreate(&m->ev0));
         RBFD_CUDA(cudaEventCreate(&m->ev1));
+        m->prof.on = o.profile != 0;
+        m->sort.launches = &m->stats.launches;
         rbfd::mesh_prepare(m, xyz_s, dS);
         *out = m;
     });
@@ -210,11 +261,23 @@ int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st) {
     return guarded([&] {
         if (!m || !st) rbfd::fail(RBFD_EINVAL, "rbfd_get_stats: NULL argument");
         RBFD_CUDA(cudaSetDevice(m->device));
-        unsigned long long pr[2] = {0, 0};
+        unsigned long long pr[4] = {0, 0, 0, 0};
+        RBFD_CUDA(cudaStreamSynchronize(m->stream));
         RBFD_CUDA(cudaMemcpy(pr, m->d_pairs, sizeof(pr), cudaMemcpyDeviceToHost));
+        m->prof.flush();
         *st = m->stats;
-        st->pairs_useful = (int64_t)pr[0];
-        st->pairs_visited = (int64_t)pr[1];
+        st->sweep_pairs_useful = (int64_t)pr[0];
+        st->sweep_pairs_visited = (int64_t)pr[1];
+        st->vol_pairs_useful = (int64_t)pr[2];
+        st->vol_pairs_visited = (int64_t)pr[3];
+        st->pairs_useful = (int64_t)(pr[0] + pr[2]);
+        st->pairs_visited = (int64_t)(pr[1] + pr[3]);
+        st->sweep_ms = m->prof.ms[rbfd::kProfSweep];
+        st->grow_ms = m->prof.ms[rbfd::kProfGrow];
+        st->vol_ms = m->prof.ms[rbfd::kProfVol];
+        st->sweep_launches = m->prof.launches[rbfd::kProfSweep];
+        st->grow_launches = m->prof.launches[rbfd::kProfGrow];
+        st->vol_launches = m->prof.launches[rbfd::kProfVol];
     });
 }
 

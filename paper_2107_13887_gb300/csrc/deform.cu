@@ -474,13 +474,18 @@ void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, b
             double inv = 1.0 / Lv.R;
             a.invR_hi = (float)inv;
             a.invR_lo = (float)(inv - (double)a.invR_hi);
-            a.pairs = m->d_pairs;
+            a.pairs = m->d_pairs + 2;
+            m->stats.launches += 3;  // flags, compaction (+ scan counted in the scan)
+            cudaEvent_t e0 = m->prof.begin(st);
             launch_vol(dim, m->opt.basis, mode, cdiv(nl, kThreads), a, st);
             RBFD_CUDA(cudaGetLastError());
+            m->prof.end(kProfVol, e0, st, 1);
+            m->stats.launches += 1;
         }
         // (4) back to the caller's order
         k_scatter_out<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vacc, m->d_vorig, nV, dim, f64 ? 1 : 0, dout);
         RBFD_CUDA(cudaGetLastError());
+        m->stats.launches += 9;  // pack, flags, compaction, bbox x2, gathers x3, scatter
     }
     if (host && n_v > 0)
         RBFD_CUDA(cudaMemcpyAsync(out, dout, (size_t)n_v * dim * es, cudaMemcpyDeviceToHost, st));
@@ -489,6 +494,7 @@ void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, b
     float ms = 0;
     RBFD_CUDA(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
     m->stats.deform_ms = ms;
+    m->prof.flush();
 }
 
 }  // namespace rbfd

@@ -840,6 +840,7 @@ void build_control_grid(rbfd_mesh *m, Level &L) {
     while ((1u << bits) < (unsigned)L.ncell && bits < 32) ++bits;
     radix_sort_pairs(keys, L.d_cell_ctrl, (size_t)n, bits, m->sort, m->stream);
     k_cell_start<<<cdiv((size_t)L.ncell + 1, 256), 256, 0, m->stream>>>(keys, n, L.ncell, L.d_cell_start);
+    m->stats.launches += 4;
     RBFD_CUDA(cudaGetLastError());
     RBFD_CUDA(cudaStreamSynchronize(m->stream));
     dfree(keys);
@@ -938,15 +939,17 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     RBFD_CUDA(cudaMemsetAsync(m->d_pb_done, 0, sizeof(unsigned int) * m->n_pb, st));
     m->d_pb_key = dalloc<double>(std::max(m->n_pb, 1024), "block keys");
     m->d_pb_idx = dalloc<int>(std::max(m->n_pb, 1024), "block argmax");
-    m->d_pairs = dalloc<unsigned long long>(2, "pair counters");
-    RBFD_CUDA(cudaMemsetAsync(m->d_pairs, 0, 2 * sizeof(unsigned long long), st));
+    m->d_pairs = dalloc<unsigned long long>(4, "pair counters");
+    RBFD_CUDA(cudaMemsetAsync(m->d_pairs, 0, 4 * sizeof(unsigned long long), st));
     m->d_st = dalloc<GreedyState>(1, "greedy state");
     RBFD_CUDA(cudaMemsetAsync(m->d_st, 0, sizeof(GreedyState), st));
     RBFD_CUDA(cudaMallocHost(&m->h_st, sizeof(GreedyState)));
     RBFD_CUDA(cudaStreamSynchronize(st));
 
+    m->stats.launches += 6;  // unpack, bbox x2, morton, gather, point blocks
     // S0 = max_i |dS_i|
     m->S0 = std::sqrt(maxnorm(m, m->d_dS, nullptr));
+    m->stats.launches += 1;
 }
 
 void greedy_run(rbfd_mesh *m) {
@@ -962,7 +965,6 @@ void greedy_run(rbfd_mesh *m) {
     m->stats.greedy_steps = 0;
     m->stats.refine_sweeps = 0;
     m->stats.confirm_resumes = 0;
-    RBFD_CUDA(cudaMemsetAsync(m->d_pairs, 0, 2 * sizeof(unsigned long long), st));
     RBFD_CUDA(cudaEventRecord(m->ev0, st));
     if (m->S0 == 0.0) {  // nothing moves: zero levels
         RBFD_CUDA(cudaEventRecord(m->ev1, st));
@@ -989,6 +991,7 @@ void greedy_run(rbfd_mesh *m) {
             m->d_pb_lo, m->d_pb_hi, m->d_sel, m->d_cx, m->d_cid, m->d_G, m->d_w, m->d_alpha, m->d_nb_cnt,
             m->d_nb_list, m->d_bbox, m->d_st);
         RBFD_CUDA(cudaGetLastError());
+        m->stats.launches += 2;  // maxnorm + level init
 
         GrowArgs g{};
         g.cap = m->cap;
@@ -1030,8 +1033,12 @@ void greedy_run(rbfd_mesh *m) {
                     a.chunk_len = (n + nch - 1) / nch;
                     a.is_step = 1;
                     a.E_out = nullptr;
+                    cudaEvent_t e0 = m->prof.begin(st);
                     launch_sweep(m->dim, m->opt.basis, mode, dim3(m->n_pb, nch), a, st);
+                    m->prof.end(kProfSweep, e0, st, 1);
+                    m->stats.launches += 1;
                     if (n >= m->cap) break;  // the sweep above stops the level
+                    cudaEvent_t e1 = m->prof.begin(st);
                     g.n = n;
                     const unsigned gp = cdiv(std::max(n, m->n_pb), kThreads);
                     if (m->dim == 2) launch_phi_d<2>(m->opt.basis, gp, g, st);
@@ -1044,9 +1051,12 @@ void greedy_run(rbfd_mesh *m) {
                                                                                  m->d_gpart, m->d_st);
                     k_grow_finish<<<cdiv(n + 1, kThreads), kThreads, 0, st>>>(g, n_jt);
                     RBFD_CUDA(cudaGetLastError());
+                    m->prof.end(kProfGrow, e1, st, 4);
+                    m->stats.launches += 4;
                     ++n;
                 }
                 read_state(m);
+                m->prof.flush();
                 stopped = m->h_st->stop != 0 || n >= m->cap;
                 if (m->h_st->status == RBFD_ESINGULAR)
                     fail(RBFD_ESINGULAR, "Phi_cc is not positive definite at level " + std::to_string(l) +
@@ -1070,6 +1080,7 @@ void greedy_run(rbfd_mesh *m) {
                                                                               m->d_v4part);
                 k_apply_correction<<<cdiv(n, kThreads), kThreads, 0, st>>>(n, m->cap, n_jt, m->d_v4part, m->d_alpha);
                 RBFD_CUDA(cudaGetLastError());
+                m->stats.launches += 4;
                 m->stats.refine_sweeps++;
             }
             // ---- confirm sweep in FP64: stores E = dS_l - Phi_sc alpha
@@ -1082,6 +1093,7 @@ void greedy_run(rbfd_mesh *m) {
                 a.E_out = m->d_E;
                 launch_sweep(m->dim, m->opt.basis, 0, dim3(m->n_pb, nch), a, st);
                 RBFD_CUDA(cudaGetLastError());
+                m->stats.launches += 1;
                 read_state(m);
             }
             const double emax = m->h_st->emax;
@@ -1106,6 +1118,7 @@ void greedy_run(rbfd_mesh *m) {
         std::vector<uint32_t> orig(n);
         std::vector<double4> al(n);
         k_orig_of_controls<<<cdiv(n, 256), 256, 0, st>>>(m->d_perm, m->d_cid, n, reinterpret_cast<uint32_t *>(m->d_vec2));
+        m->stats.launches += 1;
         RBFD_CUDA(cudaMemcpyAsync(orig.data(), m->d_vec2, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
         RBFD_CUDA(cudaMemcpyAsync(al.data(), m->d_alpha, sizeof(double4) * n, cudaMemcpyDeviceToHost, st));
         RBFD_CUDA(cudaStreamSynchronize(st));
@@ -1128,10 +1141,7 @@ void greedy_run(rbfd_mesh *m) {
     float ms = 0;
     RBFD_CUDA(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
     m->stats.greedy_ms = ms;
-    unsigned long long pr[2];
-    RBFD_CUDA(cudaMemcpy(pr, m->d_pairs, sizeof(pr), cudaMemcpyDeviceToHost));
-    m->stats.pairs_useful = (int64_t)pr[0];
-    m->stats.pairs_visited = (int64_t)pr[1];
+    m->prof.flush();
     m->greedy_done = true;
     if (!m->levels.empty() && !(m->levels.back().emax < eps_rel)) final_status = RBFD_ENOTCONV;
     if (final_status != RBFD_OK) fail(final_status, "greedy selection did not reach eps before the control cap");

@@ -38,6 +38,7 @@ T *dalloc(size_t n, const char *what) {
 
 // Scratch for the radix sort / scan / compaction primitives (grown on demand).
 struct SortScratch {
+    int64_t *launches = nullptr;  // kernel launch counter of the owning mesh
     uint32_t *keys_alt = nullptr;
     uint32_t *vals_alt = nullptr;
     uint32_t *hist = nullptr;   // 256 * n_blocks
@@ -82,7 +83,25 @@ struct Level {
     uint32_t *d_cell_ctrl = nullptr;   // [nc] control ids ordered by cell
 };
 
-struct SweepBufs;  // defined in greedy.cu
+// Optional per-kernel-class timing with CUDA events on the mesh's stream.
+enum ProfKind { kProfSweep = 0, kProfGrow = 1, kProfVol = 2, kProfKinds = 3 };
+
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> free_ev;
+    struct Pending {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pend;
+    double ms[kProfKinds] = {0, 0, 0};
+    int64_t launches[kProfKinds] = {0, 0, 0};
+    cudaEvent_t get();
+    cudaEvent_t begin(cudaStream_t st);            // records and returns the start event (or nullptr)
+    void end(int kind, cudaEvent_t a, cudaStream_t st, int n_launches);
+    void flush();                                  // after a stream sync: accumulate finished pairs
+    void release();
+};
 
 }  // namespace rbfd
 
@@ -130,7 +149,7 @@ struct rbfd_mesh {
     unsigned int *d_pb_done = nullptr;
     double *d_pb_key = nullptr;
     int *d_pb_idx = nullptr;
-    unsigned long long *d_pairs = nullptr;  // [2]: useful, visited
+    unsigned long long *d_pairs = nullptr;  // [4]: surface sweep useful, visited; volume useful, visited
     rbfd::GreedyState *d_st = nullptr;
     rbfd::GreedyState *h_st = nullptr;  // pinned
 
@@ -139,6 +158,7 @@ struct rbfd_mesh {
     rbfd_stats stats{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     rbfd::SortScratch sort;
+    rbfd::Profiler prof;
 
     // deform workspace (grown on demand)
     size_t vol_cap = 0;

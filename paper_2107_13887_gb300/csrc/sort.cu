@@ -255,6 +255,7 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *t
     k_scan_top<<<1, 1024, 0, st>>>(s.block_sums, nb, total_dev);
     k_scan_down<<<nb, SC_THREADS, 0, st>>>(in, out, n, s.block_sums);
     RBFD_CUDA(cudaGetLastError());
+    if (s.launches) *s.launches += 3;
 }
 
 void radix_sort_pairs(uint32_t *keys, uint32_t *vals, size_t n, int key_bits, SortScratch &s, cudaStream_t st) {
@@ -268,6 +269,7 @@ void radix_sort_pairs(uint32_t *keys, uint32_t *vals, size_t n, int key_bits, So
         k_rs_hist<<<nblk, RS_THREADS, 0, st>>>(ka, n, shift, s.hist, nblk);
         exclusive_scan_u32(s.hist, s.hist, (size_t)256 * nblk, nullptr, s, st);
         k_rs_scatter<<<nblk, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, s.hist, nblk);
+        if (s.launches) *s.launches += 2;
         std::swap(ka, kb);
         std::swap(va, vb);
     }

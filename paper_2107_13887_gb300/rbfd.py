@@ -39,6 +39,7 @@ class rbfd_options(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("eps_absolute", ctypes.c_int),
         ("refine_iters", ctypes.c_int),
+        ("profile", ctypes.c_int),
     ]
 
 
@@ -52,6 +53,17 @@ class rbfd_stats(ctypes.Structure):
         ("deform_points", ctypes.c_int64),
         ("refine_sweeps", ctypes.c_int64),
         ("confirm_resumes", ctypes.c_int64),
+        ("launches", ctypes.c_int64),
+        ("sweep_ms", ctypes.c_double),
+        ("grow_ms", ctypes.c_double),
+        ("vol_ms", ctypes.c_double),
+        ("sweep_launches", ctypes.c_int64),
+        ("grow_launches", ctypes.c_int64),
+        ("vol_launches", ctypes.c_int64),
+        ("sweep_pairs_useful", ctypes.c_int64),
+        ("sweep_pairs_visited", ctypes.c_int64),
+        ("vol_pairs_useful", ctypes.c_int64),
+        ("vol_pairs_visited", ctypes.c_int64),
     ]
 
 
@@ -147,7 +159,7 @@ class Mesh:
     ``rbfd_destroy`` on ``close()`` / garbage collection."""
 
     def __init__(self, xyz_s, dS, R, eps, precision=MIXED, basis=2, first_point=0, nc_cap=0, stream=None,
-                 eps_absolute=False, refine_iters=3):
+                 eps_absolute=False, refine_iters=3, profile=False):
         lib = load()
         self._lib = lib
         on_dev = _is_torch_cuda(xyz_s)
@@ -174,6 +186,7 @@ class Mesh:
         o.stream = stream
         o.eps_absolute = 1 if eps_absolute else 0
         o.refine_iters = int(refine_iters)
+        o.profile = 1 if profile else 0
         self.on_device = on_dev
         h = ctypes.c_void_p()
         _check(lib.rbfd_create(ctypes.byref(h), self.dim, self.n_s, _ptr(xyz_s), _ptr(dS), len(Rv),

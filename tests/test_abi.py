@@ -69,17 +69,19 @@ def test_struct_layout_matches_header(tmp_path):
         "int main(void){\n"
         'printf("%zu %zu %zu %zu\\n", sizeof(rbfd_options), offsetof(rbfd_options, nc_cap),'
         " offsetof(rbfd_options, stream), offsetof(rbfd_options, refine_iters));\n"
-        'printf("%zu %zu\\n", sizeof(rbfd_stats), offsetof(rbfd_stats, confirm_resumes));\n'
+        'printf("%zu %zu %zu\\n", sizeof(rbfd_stats), offsetof(rbfd_stats, confirm_resumes),'
+        " offsetof(rbfd_stats, vol_pairs_visited));\n"
         "return 0;}\n"
     )
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
     a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
     so, onc, ost, ori = map(int, a.split())
-    ss, ocr = map(int, b.split())
+    ss, ocr, ovp = map(int, b.split())
     assert so == ctypes.sizeof(rbfd.rbfd_options)
     assert onc == rbfd.rbfd_options.nc_cap.offset
     assert ost == rbfd.rbfd_options.stream.offset
     assert ori == rbfd.rbfd_options.refine_iters.offset
     assert ss == ctypes.sizeof(rbfd.rbfd_stats)
     assert ocr == rbfd.rbfd_stats.confirm_resumes.offset
+    assert ovp == rbfd.rbfd_stats.vol_pairs_visited.offset

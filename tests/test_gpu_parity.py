@@ -76,6 +76,36 @@ def check_valid(c, levels, S0):
         cur = E
 
 
+def psi_np(xi):
+    xi = np.maximum(xi, 0.0)
+    return np.where(xi < 1.0, 1.0 - xi, 0.0)
+
+
+def fp64_volume_tol(c, ref, basis_poly=None):
+    """FP64 volume bound: the larger of 1e-10 max|dS| and ten times the
+    disagreement, at the volume points, between two backward-stable FP64 solves
+    of Eq. 9 on the oracle's controls (its row Cholesky and LAPACK's LU).
+    Both are correct to about cond(Phi_cc) u; no solver can do better."""
+    poly = basis_poly or C2
+    ph = lambda e: np.where(e < 1.0, np.polyval(poly, np.minimum(e, 1.0)), 0.0)
+    Dl = oracle.support_distances(ref.smax, c.k, c.D)
+    xv = c.xyz_v.astype(np.float64)
+    dv = c.d_v.astype(np.float64)
+    cur = c.dS.copy()
+    va = np.zeros_like(xv)
+    vb = np.zeros_like(xv)
+    for l, R in enumerate(c.R):
+        C = ref.idx[l]
+        A = ph(cdist(c.xyz_s[C], c.xyz_s[C]) / R)
+        a_lu = np.linalg.solve(A, cur[C])
+        w = psi_np(dv / Dl[l])[:, None] if Dl[l] > 0 else np.zeros((len(dv), 1))
+        P = ph(cdist(xv, c.xyz_s[C]) / R)
+        va += w * (P @ ref.alpha[l])
+        vb += w * (P @ a_lu)
+        cur = cur - ph(cdist(c.xyz_s, c.xyz_s[C]) / R) @ ref.alpha[l]
+    return max(1e-10 * ref.S0, 10.0 * np.abs(va - vb).max())
+
+
 def small_cases():
     return {
         "airfoil_bump_333": synth.airfoil_case(333, 7, displacement="bump", seed=1, R=(0.5,), eps=1e-4, D=2.0, k=0.0),
@@ -103,7 +133,10 @@ def test_greedy_and_deform_parity(name, precision):
     full = check_sequences(ref, levels)
     check_valid(c, levels, ref.S0)
     for l, lv in enumerate(levels):
-        assert abs(lv.smax - ref.smax[l]) <= 1e-12 * ref.S0 + (0 if full else 1e-6 * ref.S0)
+        # level 0 targets are the inputs; later levels' targets carry the
+        # rounding of Eq. 12 (about n u sum|alpha phi|, below 1e-9 S0 here)
+        tol_s = 1e-15 * ref.S0 if l == 0 else (1e-9 if full else 1e-6) * ref.S0
+        assert abs(lv.smax - ref.smax[l]) <= tol_s
         if full and l == 0:
             amax = np.abs(ref.alpha[l]).max()
             assert np.abs(lv.alpha - ref.alpha[l]).max() <= 1e-6 * amax
@@ -111,15 +144,23 @@ def test_greedy_and_deform_parity(name, precision):
         return
     dv_ref = oracle.deform(ref, c.xyz_s, c.R, c.xyz_v, c.d_v, c.k, c.D, n_threads=NT)
     dv = m.deform(c.xyz_v, c.d_v, c.D, c.k)
-    tol = 1e-10 if precision == rbfd.FP64 else 1e-5
+    tol = fp64_volume_tol(c, ref) if precision == rbfd.FP64 else 1e-5 * ref.S0
     err = np.abs(dv.astype(np.float64) - dv_ref).max()
     # float32 output: add half an ulp of the largest displacement
-    assert err <= tol * ref.S0 + np.abs(dv_ref).max() * 2.0**-24, f"volume error {err / ref.S0:g} S0"
+    assert err <= tol + np.abs(dv_ref).max() * 2.0**-24, f"volume error {err / ref.S0:g} S0"
     dv64 = m.deform(c.xyz_v.astype(np.float64), c.d_v.astype(np.float64), c.D, c.k)
-    assert np.abs(dv64 - dv_ref).max() <= tol * ref.S0
+    assert np.abs(dv64 - dv_ref).max() <= tol
     st = m.stats()
     assert 0 < st["pairs_useful"] <= st["pairs_visited"]
     m.close()
+
+
+# Table 1 multiplied out (C4 = (1-e)^6 (35/3 e^2 + 6 e + 1), C6 = (1-e)^8 (32 e^3 + 25 e^2 + 8 e + 1))
+POLY = {
+    "C0": [1.0, -2.0, 1.0],
+    "C4": list(np.polymul(np.poly1d([-1.0, 1.0]) ** 6, [35.0 / 3.0, 6.0, 1.0]).coeffs),
+    "C6": list(np.polymul(np.poly1d([-1.0, 1.0]) ** 8, [32.0, 25.0, 8.0, 1.0]).coeffs),
+}
 
 
 @pytest.mark.parametrize("basis", ["C0", "C4", "C6"])
@@ -132,7 +173,7 @@ def test_other_wendland_bases_fp64(basis):
     if full:
         dv_ref = oracle.deform(ref, c.xyz_s, c.R, c.xyz_v, c.d_v, c.k, c.D, basis=basis, n_threads=NT)
         dv = m.deform(c.xyz_v.astype(np.float64), c.d_v.astype(np.float64), c.D, c.k)
-        assert np.abs(dv - dv_ref).max() <= 1e-10 * ref.S0
+        assert np.abs(dv - dv_ref).max() <= fp64_volume_tol(c, ref, POLY[basis])
 
 
 @pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
@@ -148,11 +189,12 @@ def test_naca0012_400_full_fp64_and_mixed():
     c = synth.make_config("naca0012_400s_40kv_bump")
     ref = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, n_threads=NT)
     dv_ref = oracle.deform(ref, c.xyz_s, c.R, c.xyz_v, c.d_v, c.k, c.D, n_threads=NT)
-    for precision, tol in ((rbfd.FP64, 1e-10), (rbfd.MIXED, 1e-5)):
+    for precision in (rbfd.FP64, rbfd.MIXED):
         m, _ = run_gpu(c, precision)
         assert check_sequences(ref, m.levels(), strict_full=True)
         dv = m.deform(c.xyz_v, c.d_v, c.D, c.k).astype(np.float64)
-        assert np.abs(dv - dv_ref).max() <= tol * ref.S0 + np.abs(dv_ref).max() * 2.0**-24
+        tol = fp64_volume_tol(c, ref) if precision == rbfd.FP64 else 1e-5 * ref.S0
+        assert np.abs(dv - dv_ref).max() <= tol + np.abs(dv_ref).max() * 2.0**-24
 
 
 @pytest.mark.parametrize("disp", ["horns", "pitch_heave"])
@@ -161,12 +203,12 @@ def test_naca0012_4000_1m_full_mixed(disp):
     ref = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, n_threads=NT)
     m, _ = run_gpu(c, rbfd.MIXED)
     levels = m.levels()
-    full = check_sequences(ref, levels)
+    # the oracle's smallest top-2 gap on these inputs is well above rounding
+    assert check_sequences(ref, levels, strict_full=True)
     check_valid(c, levels, ref.S0)
     dv = m.deform(c.xyz_v, c.d_v, c.D, c.k).astype(np.float64)
-    if full:
-        dv_ref = oracle.deform(ref, c.xyz_s, c.R, c.xyz_v, c.d_v, c.k, c.D, n_threads=NT)
-        assert np.abs(dv - dv_ref).max() <= 1e-5 * ref.S0 + np.abs(dv_ref).max() * 2.0**-24
+    dv_ref = oracle.deform(ref, c.xyz_s, c.R, c.xyz_v, c.d_v, c.k, c.D, n_threads=NT)
+    assert np.abs(dv - dv_ref).max() <= 1e-5 * ref.S0 + np.abs(dv_ref).max() * 2.0**-24
 
 
 # ---------------------------------------------------------------- edge cases
