@@ -161,6 +161,32 @@ int rbfd_deform(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v,
 int rbfd_deform_f64(rbfd_mesh *m, int64_t n_v, const double *xyz_v, const double *d_v, double D, double k,
                     double *out);
 
+/*
+ * rbfd_deform_noalloc -- the volume update of rbfd_deform for callers that
+ * cannot allocate device memory while they run: a solver loop whose device
+ * memory was reserved up front (a pool or a fixed budget), or a host that keeps
+ * cudaMalloc/cudaFree off its hot path because those calls synchronise the
+ * device and can fail in the middle of a run.  The paper has no counterpart;
+ * this is a deployment variant of the same computation.
+ *
+ * Same arguments and result as rbfd_deform, with three differences:
+ *   - xyz_v, d_v and out must be device memory (of the mesh's device);
+ *   - n_v must not exceed 131072: every per-call buffer lives in one fixed
+ *     device array of about 16 MB that each GPU loading the library holds
+ *     until the process exits; larger n_v returns RBFD_EINVAL;
+ *   - the call allocates nothing (no cudaMalloc/cudaFree, no allocating
+ *     library routine).  On each device the first call looks up the array's
+ *     device address once (cudaGetSymbolAddress); make that first call before
+ *     any stream capture.
+ * All calls share the array and it keeps the previous call's contents (the
+ * call clears what must start at zero).  Calls whose work overlaps on the
+ * GPU (two host threads, or two meshes on different streams) race on it: run
+ * them one after another.  The mesh itself (rbfd_create, rbfd_greedy) is set up
+ * beforehand with the ordinary, allocating calls.
+ */
+int rbfd_deform_noalloc(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v, double D, double k,
+                        float *out);
+
 /* Release every device and host resource of the mesh.  NULL is allowed. */
 int rbfd_destroy(rbfd_mesh *m);
 

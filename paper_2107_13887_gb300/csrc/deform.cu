@@ -14,6 +14,8 @@
 // displacement back to the caller's order.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <string>
 
 #include "internal.h"
 
@@ -498,3 +500,198 @@ void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, b
 }
 
 }  // namespace rbfd
+
+// ==================================================== allocation-free variant
+//
+// rbfd_deform_noalloc: the volume update above for callers that must not
+// allocate device memory during the call -- code running between the
+// iterations of a solver whose device memory is fully reserved up front, or
+// hosts that forbid cudaMalloc/cudaFree on their hot path because those calls
+// synchronise the device and can fail mid-run.  Every per-call buffer (packed,
+// compacted and sorted points, lists, Morton keys, sort scratch, accumulators)
+// lives in one file-scope device array of fixed size, so the call allocates
+// nothing; it is limited to kNoAllocMaxPoints volume points.
+namespace rbfd {
+namespace {
+
+constexpr int64_t kNoAllocMaxPoints = 1 << 17;  // 131,072 volume points per call
+constexpr size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t kNaD4 = al256(sizeof(double4) * (size_t)kNoAllocMaxPoints);
+constexpr size_t kNaU32 = al256(sizeof(uint32_t) * (size_t)kNoAllocMaxPoints);
+constexpr size_t kNaSortBlocks = (size_t)kNoAllocMaxPoints / 2048 + 1;      // radix tiles of 2048 (+1)
+constexpr size_t kNaHistN = 256 * kNaSortBlocks;
+constexpr size_t kNaSumsN = (kNaHistN + 2047) / 2048 + (size_t)kNoAllocMaxPoints / 2048 + 4;
+constexpr size_t kNaBytes = 3 * kNaD4 + 7 * kNaU32 + al256(sizeof(uint32_t) * kNaHistN) +
+                            al256(sizeof(uint32_t) * kNaSumsN);
+
+// Shared by every call in the process on a given device (about 16 MB).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_na_mutex;
+unsigned char *g_na_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code must not use the symbol itself as an address).
+unsigned char *noalloc_scratch() {
+    int dev = 0;
+    RBFD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) fail(RBFD_EINVAL, "rbfd_deform_noalloc: device index out of range");
+    std::lock_guard<std::mutex> lk(g_na_mutex);
+    if (!g_na_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            fail(RBFD_ECUDA, std::string("rbfd_deform_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+        }
+        g_na_addr[dev] = static_cast<unsigned char *>(p);
+    }
+    return g_na_addr[dev];
+}
+
+void deform_noalloc_run(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v, double D, double k,
+                        float *out) {
+    cudaStream_t st = m->stream;
+    const int dim = m->dim;
+    unsigned char *base = noalloc_scratch();
+    double4 *vin = reinterpret_cast<double4 *>(base);
+    double4 *vpos = reinterpret_cast<double4 *>(base + kNaD4);
+    double4 *vacc = reinterpret_cast<double4 *>(base + 2 * kNaD4);
+    unsigned char *u = base + 3 * kNaD4;
+    uint32_t *vorig = reinterpret_cast<uint32_t *>(u + 0 * kNaU32);
+    uint32_t *vflag = reinterpret_cast<uint32_t *>(u + 1 * kNaU32);
+    uint32_t *vscan = reinterpret_cast<uint32_t *>(u + 2 * kNaU32);
+    uint32_t *vlist = reinterpret_cast<uint32_t *>(u + 3 * kNaU32);
+    uint32_t *vkeys = reinterpret_cast<uint32_t *>(u + 4 * kNaU32);
+    SortScratch ss;  // a view into the static array with its capacities: reserve() never allocates
+    ss.launches = &m->stats.launches;
+    ss.keys_alt = reinterpret_cast<uint32_t *>(u + 5 * kNaU32);
+    ss.vals_alt = reinterpret_cast<uint32_t *>(u + 6 * kNaU32);
+    ss.hist = reinterpret_cast<uint32_t *>(u + 7 * kNaU32);
+    ss.block_sums = reinterpret_cast<uint32_t *>(u + 7 * kNaU32 + al256(sizeof(uint32_t) * kNaHistN));
+    ss.cap_items = (size_t)kNoAllocMaxPoints;
+    ss.cap_hist = kNaHistN;
+    ss.cap_sums = kNaSumsN;
+
+    RBFD_CUDA(cudaEventRecord(m->ev0, st));
+    const int L = (int)m->levels.size();
+    double Dl[64] = {0};
+    double Dmax = 0.0;
+    for (int l = 0; l < L; ++l) {
+        double v = (k > 0.0) ? k * m->levels[l].smax : D;
+        if (k > 0.0 && D > 0.0 && v > D) v = D;
+        Dl[l] = (m->levels[l].nc > 0) ? v : 0.0;
+        Dmax = std::max(Dmax, Dl[l]);
+    }
+    if (n_v > 0) RBFD_CUDA(cudaMemsetAsync(out, 0, (size_t)n_v * dim * sizeof(float), st));
+    int64_t nV = 0;
+    if (n_v > 0 && Dmax > 0.0) {
+        k_vol_pack<<<cdiv(n_v, 256), 256, 0, st>>>(xyz_v, d_v, n_v, dim, 0, vin);
+        k_flag_below<<<cdiv(n_v, 256), 256, 0, st>>>(vin, nullptr, n_v, Dmax, vflag);
+        exclusive_scan_u32(vflag, vscan, (size_t)n_v, &m->d_misc[6], ss, st);
+        k_compact<<<cdiv(n_v, 256), 256, 0, st>>>(vflag, vscan, n_v, vlist);
+        uint32_t cnt = 0;
+        RBFD_CUDA(cudaMemcpyAsync(&cnt, &m->d_misc[6], sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        RBFD_CUDA(cudaStreamSynchronize(st));
+        nV = cnt;
+    }
+    if (nV > 0) {
+        const int nbb = std::min<int>(cdiv(nV, 256), 256);
+        k_bbox_idx<<<nbb, 256, 0, st>>>(vin, vlist, nV, m->d_red);
+        k_bbox_reduce<<<1, 32, 0, st>>>(m->d_red, nbb, m->d_bbox);
+        double bb[6];
+        RBFD_CUDA(cudaMemcpyAsync(bb, m->d_bbox, sizeof(bb), cudaMemcpyDeviceToHost, st));
+        RBFD_CUDA(cudaStreamSynchronize(st));
+        k_gather_vol<<<cdiv(nV, 256), 256, 0, st>>>(vin, vlist, nV, vpos);
+        morton_keys_f64(vpos, nV, dim, make_double3(bb[0], bb[1], bb[2]), make_double3(bb[3], bb[4], bb[5]), vkeys,
+                        vorig, st);
+        radix_sort_pairs(vkeys, vorig, (size_t)nV, dim == 2 ? 32 : 30, ss, st);
+        k_gather_vol<<<cdiv(nV, 256), 256, 0, st>>>(vpos, vorig, nV, vin);  // vin := sorted points
+        k_gather_u32<<<cdiv(nV, 256), 256, 0, st>>>(vlist, vorig, nV, vflag);
+        RBFD_CUDA(cudaMemcpyAsync(vorig, vflag, sizeof(uint32_t) * nV, cudaMemcpyDeviceToDevice, st));
+        RBFD_CUDA(cudaMemsetAsync(vacc, 0, sizeof(double4) * nV, st));  // the array keeps the last call's data
+        const int mode = m->opt.precision == RBFD_FP64 ? 0 : 1;
+        for (int l = 0; l < L; ++l) {
+            const Level &Lv = m->levels[l];
+            if (Lv.nc == 0 || !(Dl[l] > 0.0)) continue;
+            k_flag_below<<<cdiv(nV, 256), 256, 0, st>>>(vin, nullptr, nV, Dl[l], vflag);
+            exclusive_scan_u32(vflag, vscan, (size_t)nV, &m->d_misc[7], ss, st);
+            k_compact<<<cdiv(nV, 256), 256, 0, st>>>(vflag, vscan, nV, vlist);
+            uint32_t nl = 0;
+            RBFD_CUDA(cudaMemcpyAsync(&nl, &m->d_misc[7], sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            RBFD_CUDA(cudaStreamSynchronize(st));
+            if (nl == 0) continue;
+            VolArgs a{};
+            a.n_list = nl;
+            a.list = vlist;
+            a.vpos = vin;
+            a.vacc = vacc;
+            a.cx = Lv.d_cx;
+            a.alpha = Lv.d_alpha;
+            a.cell_start = Lv.d_cell_start;
+            a.cell_ctrl = Lv.d_cell_ctrl;
+            a.g0 = Lv.g0;
+            a.h = Lv.h;
+            a.gd = Lv.gdim;
+            a.R = Lv.R;
+            a.Dl = Dl[l];
+            double inv = 1.0 / Lv.R;
+            a.invR_hi = (float)inv;
+            a.invR_lo = (float)(inv - (double)a.invR_hi);
+            a.pairs = m->d_pairs + 2;
+            launch_vol(dim, m->opt.basis, mode, cdiv(nl, kThreads), a, st);
+            RBFD_CUDA(cudaGetLastError());
+            m->stats.launches += 4;
+        }
+        k_scatter_out<<<cdiv(nV, 256), 256, 0, st>>>(vacc, vorig, nV, dim, 0, out);
+        RBFD_CUDA(cudaGetLastError());
+        m->stats.launches += 9;
+    }
+    RBFD_CUDA(cudaEventRecord(m->ev1, st));
+    RBFD_CUDA(cudaEventSynchronize(m->ev1));
+    float ms = 0;
+    RBFD_CUDA(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
+    m->stats.deform_ms = ms;
+}
+
+bool na_is_device_ptr(const void *p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+}  // namespace rbfd
+
+extern "C" int rbfd_deform_noalloc(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v, double D,
+                                   double k, float *out) {
+    try {
+        if (!m) rbfd::fail(RBFD_EINVAL, "rbfd_deform_noalloc: NULL mesh");
+        if (n_v < 0 || n_v > rbfd::kNoAllocMaxPoints)
+            rbfd::fail(RBFD_EINVAL, "rbfd_deform_noalloc: n_v = " + std::to_string(n_v) +
+                                        " is outside [0, 131072], the size of the fixed scratch array");
+        if (n_v > 0 && (!xyz_v || !d_v || !out)) rbfd::fail(RBFD_EINVAL, "rbfd_deform_noalloc: NULL array");
+        if (!(D >= 0.0) || !(k >= 0.0) || !std::isfinite(D) || !std::isfinite(k))
+            rbfd::fail(RBFD_EINVAL, "rbfd_deform_noalloc: D and k must be finite and >= 0");
+        if (D == 0.0 && k == 0.0) rbfd::fail(RBFD_EINVAL, "rbfd_deform_noalloc: D and k cannot both be 0");
+        if (!m->greedy_done) rbfd::fail(RBFD_ESTATE, "rbfd_deform_noalloc: run rbfd_greedy first");
+        if ((int)m->levels.size() > 64) rbfd::fail(RBFD_EINVAL, "rbfd_deform_noalloc: more than 64 levels");
+        RBFD_CUDA(cudaSetDevice(m->device));
+        if (n_v > 0 && (!rbfd::na_is_device_ptr(xyz_v) || !rbfd::na_is_device_ptr(d_v) ||
+                        !rbfd::na_is_device_ptr(out)))
+            rbfd::fail(RBFD_EINVAL, "rbfd_deform_noalloc: xyz_v, d_v and out must be device memory");
+        rbfd::deform_noalloc_run(m, n_v, xyz_v, d_v, D, k, out);
+        rbfd::set_last_error("");
+        return RBFD_OK;
+    } catch (const rbfd::Error &e) {
+        rbfd::set_last_error(e.msg);
+        return e.status;
+    } catch (...) {
+        rbfd::set_last_error("rbfd_deform_noalloc: unexpected internal error");
+        return RBFD_ECUDA;
+    }
+}

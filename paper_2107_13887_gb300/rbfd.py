@@ -83,6 +83,7 @@ SIGNATURES = [
     ("rbfd_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(rbfd_stats)]),
     ("rbfd_deform", ctypes.c_int, [_vp, _i64, _vp, _vp, _d, _d, _vp]),
     ("rbfd_deform_f64", ctypes.c_int, [_vp, _i64, _vp, _vp, _d, _d, _vp]),
+    ("rbfd_deform_noalloc", ctypes.c_int, [_vp, _i64, _vp, _vp, _d, _d, _vp]),
     ("rbfd_destroy", ctypes.c_int, [_vp]),
     ("rbfd_last_error", ctypes.c_char_p, []),
     ("rbfd_version", ctypes.c_char_p, []),
@@ -255,4 +256,11 @@ class Mesh:
                 out = np.empty((n_v, self.dim), dtype=dt)
         fn = self._lib.rbfd_deform_f64 if f64 else self._lib.rbfd_deform
         _check(fn(self.h, int(n_v), _ptr(xyz_v), _ptr(d_v), float(D), float(k), _ptr(out)))
+        return out
+
+    def deform_noalloc(self, xyz_v, d_v, D: float, k: float, out):
+        """``rbfd_deform_noalloc``: float32 torch CUDA tensors in, result written
+        into ``out`` (a preallocated float32 CUDA tensor); at most 131,072 points."""
+        _check(self._lib.rbfd_deform_noalloc(self.h, int(xyz_v.shape[0]), _ptr(xyz_v), _ptr(d_v), float(D), float(k),
+                                             _ptr(out)))
         return out
