@@ -58,6 +58,8 @@ def parse_args():
     p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--engine", type=int, default=0, help="0: persistent greedy launch, 1: launches per step")
+    p.add_argument("--ctas", type=int, default=0, help="blocks of the persistent launch (0: automatic)")
     return p.parse_args()
 
 
@@ -207,7 +209,6 @@ def run_ours(args):
     precision = rbfd.MIXED if args.precision == "mixed" else rbfd.FP64
     cases = make_cases()
     stream = torch.cuda.current_stream(dev)
-    sp = stream.cuda_stream
 
     # device-resident inputs
     dcases = []
@@ -226,18 +227,22 @@ def run_ours(args):
                            out=pin(np.zeros((c.n_v, c.dim), np.float32))))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
+    # each case gets its own stream so that the batch calls overlap them
+    streams = [torch.cuda.Stream(dev) for _ in cases]
+
     def one_step(src, record):
-        pairs = 0
-        stats = []
-        for c, d in zip(cases, src):
-            m = rbfd.Mesh(d["xyz_s"], d["dS"], c.R, c.eps, precision=precision, stream=sp, profile=record)
-            m.greedy()
-            m.deform(d["xyz_v"], d["d_v"], c.D, c.k, out=d["out"])
-            st = m.stats()
+        """Both cases as one batch: create, greedy (batched), deform (batched), destroy."""
+        ms = []
+        for c, d, s_ in zip(cases, src, streams):
+            ms.append(rbfd.Mesh(d["xyz_s"], d["dS"], c.R, c.eps, precision=precision, stream=s_.cuda_stream,
+                                profile=record, engine=args.engine, grid_ctas=args.ctas))
+        rbfd.greedy_batch(ms)
+        rbfd.deform_batch(ms, [d["xyz_v"] for d in src], [d["d_v"] for d in src], [c.D for c in cases],
+                          [c.k for c in cases], [d["out"] for d in src])
+        stats = [m.stats() for m in ms]
+        for m in ms:
             m.close()
-            stats.append(st)
-            pairs += st["pairs_useful"]
-        return pairs, stats
+        return sum(st["pairs_useful"] for st in stats), stats
 
     def timed(src, K, W, record):
         for _ in range(W):
@@ -252,7 +257,11 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
+            for s_ in streams:  # the case streams start after e0
+                s_.wait_event(e0)
             p, st = one_step(src, record)
+            for s_ in streams:  # e1 follows the work of every case stream
+                stream.wait_stream(s_)
             e1.record(stream)
             torch.cuda.synchronize()
             tot_ms += e0.elapsed_time(e1)
@@ -295,12 +304,15 @@ def run_ours(args):
         return
 
     # roofline of the dominant kernel class (device time inside the timed region)
+    sweep_pairs = sum(s["sweep_pairs_useful"] for s in stats)
     kinds = {
-        "sweep": (sum(s["sweep_ms"] for s in stats), sum(s["sweep_launches"] for s in stats),
-                  sum(s["sweep_pairs_useful"] for s in stats)),
+        "sweep": (sum(s["sweep_ms"] for s in stats), sum(s["sweep_launches"] for s in stats), sweep_pairs),
         "grow": (sum(s["grow_ms"] for s in stats), sum(s["grow_launches"] for s in stats), 0),
         "vol": (sum(s["vol_ms"] for s in stats), sum(s["vol_launches"] for s in stats),
                 sum(s["vol_pairs_useful"] for s in stats)),
+        # the persistent greedy launch runs the sweeps AND the FP64 growth; only
+        # its sweep pairs are counted as work here, so its fraction is a lower bound
+        "persist": (sum(s["persist_ms"] for s in stats), sum(s["persist_launches"] for s in stats), sweep_pairs),
     }
     dim = cases[0].dim
     peak_ops = SM_COUNT * FP32_LANES_PER_SM * 2.07e9  # FP32 issue slots per second at max SM clock
@@ -309,12 +321,14 @@ def run_ours(args):
     d_ms, d_launch, d_pairs = ev_kinds[dom]
     achieved = d_pairs * OPS_PER_PAIR_DF[dim] / (d_ms / 1e3) if d_ms > 0 else 0.0
     roofline = {
-        "bound": "alu", "kernel": {"sweep": "k_sweep<2,2,1>", "vol": "k_vol_sweep<2,2,1>"}[dom],
+        "bound": "alu", "kernel": {"sweep": "k_sweep<2,2,1>", "vol": "k_vol_sweep<2,2,1>",
+                                   "persist": "k_greedy_persist<2,2,1>"}[dom],
         "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "TFLOP/s",
         "frac": achieved / peak_ops, "traffic": None,
         "ops_per_pair": OPS_PER_PAIR_DF[dim], "avg_launch_ms": d_ms / max(1, d_launch),
         "launches": int(d_launch),
         "kernel_ms": {k: round(v[0], 3) for k, v in kinds.items()},
+        "persist_phase_ms": [round(sum(s["persist_phase_ms"][q] for s in stats), 3) for q in range(8)],
         "note": "FP32-pipe operations of the double-float pair evaluation; peak = 152 SMs x 128 FP32 lanes x 2.07 GHz",
     }
     greedy_ms = [s["greedy_ms"] for s in stats]
@@ -325,7 +339,9 @@ def run_ours(args):
         "dtype": "f32x2+f64" if precision == rbfd.MIXED else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "cases": list(CASES), "n_surface": 4000, "n_volume": 1000000,
                    "levels": 2, "R": [1.0, 0.2], "eps": 1e-5, "k": 5.0, "D": 2.0, "precision": args.precision,
-                   "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas{ws}"},
+                   "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas{ws}",
+                   "engine": "persistent" if args.engine == 0 else "per-step launches",
+                   "persist_ctas": int(stats[-1]["persist_ctas"]) if stats else 0},
         "time_to_eps_ms": {"pitch_heave": statistics.median(greedy_ms[0::2]),
                            "horns": statistics.median(greedy_ms[1::2])},
         "pairs_useful_per_step": pairs_all / args.steps / ws,

@@ -57,6 +57,9 @@ typedef struct rbfd_options {
     int refine_iters;      /* iterative-refinement sweeps at level close (default 3) */
     int profile;           /* 1: time each kernel class with CUDA events on the mesh's stream
                               (rbfd_stats.*_ms / *_launches); adds two event records per launch */
+    int engine;            /* greedy engine: 0 = one cooperative persistent launch per level
+                              (default); 1 = separate launches for every step */
+    int grid_ctas;         /* blocks of the persistent launch (0 = chosen from the mesh size) */
 } rbfd_options;
 
 typedef struct rbfd_mesh rbfd_mesh;
@@ -94,7 +97,9 @@ int rbfd_create(rbfd_mesh **out, int dim, int64_t n_s, const double *xyz_s, cons
  * error E = dS_l - Phi_sc alpha over all surface points (Eq. 12), add the
  * point of largest |E_i| until max |E_i| / max |dS_i| < eps^((l+1)/n_levels);
  * then dS_{l+1} = E.  Blocks until done.  May be called again to re-run.
- * Errors: RBFD_ESINGULAR, RBFD_ENOTCONV (results valid), RBFD_ETIMEOUT, RBFD_ECUDA.
+ * Errors: RBFD_ESINGULAR, RBFD_ENOTCONV (results valid), RBFD_ETIMEOUT (a grid
+ * barrier of the persistent launch waited past its bound; the launch ended
+ * without hanging), RBFD_ECUDA.
  */
 int rbfd_greedy(rbfd_mesh *m);
 
@@ -134,6 +139,12 @@ typedef struct rbfd_stats {
     double sweep_ms, grow_ms, vol_ms;
     int64_t sweep_launches, grow_launches, vol_launches;
     int64_t sweep_pairs_useful, sweep_pairs_visited, vol_pairs_useful, vol_pairs_visited;
+    double persist_ms;         /* persistent greedy launches (engine 0): sweep + growth of every step */
+    int64_t persist_launches;
+    int64_t persist_ctas;      /* blocks of the last persistent launch */
+    /* profile mode: block 0 of the persistent launch, summed over steps, in ms:
+       [2p] = work of phase p (sweep, argmax+phi, G phi, G row), [2p+1] = wait at its barrier */
+    double persist_phase_ms[8];
 } rbfd_stats;
 
 int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st);
@@ -186,6 +197,25 @@ int rbfd_deform_f64(rbfd_mesh *m, int64_t n_v, const double *xyz_v, const double
  */
 int rbfd_deform_noalloc(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v, double D, double k,
                         float *out);
+
+/*
+ * rbfd_greedy_batch -- rbfd_greedy on n meshes at once.  Each greedy is a
+ * chain of small, latency-bound steps (Section 3); independent meshes (several
+ * ice shapes, several grids) run side by side: one host thread per mesh, each
+ * on the mesh's own stream, the persistent launches sized so that they are
+ * resident together.  Give every mesh its own stream (the default) for
+ * overlap.  Returns the first failing mesh's status (RBFD_ENOTCONV only if no
+ * mesh failed otherwise); every mesh that succeeded holds its results.
+ */
+int rbfd_greedy_batch(rbfd_mesh **meshes, int n);
+
+/*
+ * rbfd_deform_batch -- rbfd_deform on n meshes at once (one host thread and
+ * stream per mesh).  Array i of each argument belongs to mesh i; the pointer
+ * kinds follow each mesh's inputs_on_device option.
+ */
+int rbfd_deform_batch(rbfd_mesh **meshes, int n, const int64_t *n_v, const float *const *xyz_v,
+                      const float *const *d_v, const double *D, const double *k, float *const *out);
 
 /* Release every device and host resource of the mesh.  NULL is allowed. */
 int rbfd_destroy(rbfd_mesh *m);

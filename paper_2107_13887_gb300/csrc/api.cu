@@ -2,9 +2,14 @@
 // point validates its arguments, converts internal errors into an
 // rbfd_status, and records a thread-local message for rbfd_last_error().
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
+#include <unordered_map>
 
 #include "internal.h"
 
@@ -23,19 +28,132 @@ void check_cuda(cudaError_t e, const char *what) {
     fail(RBFD_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// ------------------------------------------------------- device memory pool
+//
+// Meshes are created and destroyed per deformation request; the ~45 buffers a
+// mesh owns would otherwise cost a cudaMalloc each and a device-synchronising
+// cudaFree each.  Freed blocks are kept per device in a size-ordered free list
+// and handed out again for requests of up to twice their size.  Every free in
+// the library happens after the owning stream has been synchronised, so a
+// block is idle when it is reused.  The cache is trimmed (cudaFree) when it
+// grows past a limit (RBFD_POOL_LIMIT_MB, default 16384) or when cudaMalloc
+// runs out of memory.
+namespace {
+
+constexpr int kPoolDevices = 64;
+
+struct DevicePool {
+    std::mutex mu;
+    std::multimap<size_t, void *> free_blocks[kPoolDevices];
+    std::unordered_map<void *, std::pair<int, size_t>> live;
+    size_t cached[kPoolDevices] = {};
+    size_t limit = 0;
+};
+
+DevicePool &pool() {
+    static DevicePool *p = [] {
+        auto *q = new DevicePool();  // never destroyed: safe to use during process exit
+        const char *v = std::getenv("RBFD_POOL_LIMIT_MB");
+        q->limit = (v ? std::strtoull(v, nullptr, 10) : 16384ull) << 20;
+        return q;
+    }();
+    return *p;
+}
+
+void trim_locked(DevicePool &P, int dev, size_t keep) {
+    while (P.cached[dev] > keep && !P.free_blocks[dev].empty()) {
+        auto it = std::prev(P.free_blocks[dev].end());  // largest first
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != dev) cudaSetDevice(dev);
+        cudaFree(it->second);
+        if (cur != dev) cudaSetDevice(cur);
+        P.cached[dev] -= it->first;
+        P.free_blocks[dev].erase(it);
+    }
+}
+
+}  // namespace
+
 void *dmalloc(size_t bytes, const char *what) {
+    const size_t sz = ((bytes ? bytes : 1) + 511) / 512 * 512;
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kPoolDevices) fail(RBFD_EINVAL, "device index out of range for the memory pool");
+    DevicePool &P = pool();
+    {
+        std::lock_guard<std::mutex> lk(P.mu);
+        auto it = P.free_blocks[dev].lower_bound(sz);
+        if (it != P.free_blocks[dev].end() && it->first <= 2 * sz) {
+            void *p = it->second;
+            P.cached[dev] -= it->first;
+            P.live[p] = {dev, it->first};
+            P.free_blocks[dev].erase(it);
+            return p;
+        }
+    }
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes ? bytes : 1);
+    cudaError_t e = cudaMalloc(&p, sz);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        {
+            std::lock_guard<std::mutex> lk(P.mu);
+            trim_locked(P, dev, 0);
+        }
+        e = cudaMalloc(&p, sz);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         fail(e == cudaErrorMemoryAllocation ? RBFD_ENOMEM : RBFD_ECUDA,
              std::string("allocating ") + what + " (" + std::to_string(bytes) + " bytes): " + cudaGetErrorString(e));
     }
+    std::lock_guard<std::mutex> lk(P.mu);
+    P.live[p] = {dev, sz};
     return p;
 }
 
 void dfree(void *p) {
-    if (p) cudaFree(p);
+    if (!p) return;
+    DevicePool &P = pool();
+    std::lock_guard<std::mutex> lk(P.mu);
+    auto it = P.live.find(p);
+    if (it == P.live.end()) {
+        cudaFree(p);  // not from the pool
+        return;
+    }
+    const int dev = it->second.first;
+    const size_t sz = it->second.second;
+    P.live.erase(it);
+    P.free_blocks[dev].insert({sz, p});
+    P.cached[dev] += sz;
+    if (P.cached[dev] > P.limit) trim_locked(P, dev, P.limit / 2);
+}
+
+// Pinned host words for the greedy state mirror (cudaMallocHost is slow).
+namespace {
+std::mutex g_pin_mu;
+std::vector<void *> g_pin_free;
+}  // namespace
+
+void *pinned_alloc(size_t bytes) {
+    if (bytes > 4096) fail(RBFD_EINVAL, "pinned_alloc: block too large");
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        if (!g_pin_free.empty()) {
+            void *p = g_pin_free.back();
+            g_pin_free.pop_back();
+            return p;
+        }
+    }
+    void *p = nullptr;
+    check_cuda(cudaMallocHost(&p, 4096), "cudaMallocHost");
+    return p;
+}
+
+void pinned_free(void *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(p);
 }
 
 cudaEvent_t Profiler::get() {
@@ -102,11 +220,12 @@ void mesh_free(rbfd_mesh *m) {
                     m->d_cid, m->d_phi, m->d_y, m->d_red, m->d_gpart, m->d_vec, m->d_vec2, m->d_v4part,
                     m->d_nb_cnt, m->d_nb_list, m->d_part, m->d_pb_done, m->d_pb_key, m->d_pb_idx, m->d_pairs,
                     m->d_st, m->d_vin, m->d_vpos, m->d_vorig, m->d_vflag, m->d_vscan, m->d_vlist, m->d_vkeys,
-                    m->d_vacc, m->d_vio, m->d_misc, m->d_bbox};
+                    m->d_vacc, m->d_vio, m->d_misc, m->d_bbox, m->d_bar, m->d_pred, m->d_pgpart,
+                    m->d_kt_done, m->d_phase_ns};
     for (void *p : ptrs) dfree(p);
     m->sort.release();
     m->prof.release();
-    if (m->h_st) cudaFreeHost(m->h_st);
+    if (m->h_st) pinned_free(m->h_st);
     if (m->ev0) cudaEventDestroy(m->ev0);
     if (m->ev1) cudaEventDestroy(m->ev1);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
@@ -146,6 +265,33 @@ bool is_device_ptr(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Run f(i) for i < n on n host threads (the calling thread takes i = 0);
+// returns the statuses, and the message of the first failure in *msg.
+template <typename F>
+int run_batch(int n, F &&f, const char *name) {
+    std::vector<int> rc(n, RBFD_OK);
+    std::vector<std::string> msg(n);
+    auto body = [&](int i) {
+        rc[i] = guarded([&] { f(i); });
+        if (rc[i] != RBFD_OK) msg[i] = rbfd::g_last_error;
+    };
+    std::vector<std::thread> th;
+    for (int i = 1; i < n; ++i) th.emplace_back(body, i);
+    if (n > 0) body(0);
+    for (auto &t : th) t.join();
+    int worst = RBFD_OK;
+    std::string wmsg;
+    for (int i = 0; i < n; ++i) {
+        if (rc[i] == RBFD_OK) continue;
+        if (worst == RBFD_OK || (worst == RBFD_ENOTCONV && rc[i] != RBFD_ENOTCONV)) {
+            worst = rc[i];
+            wmsg = std::string(name) + ": mesh " + std::to_string(i) + ": " + msg[i];
+        }
+    }
+    rbfd::g_last_error = wmsg;
+    return worst;
+}
+
 }  // namespace
 
 extern "C" {
@@ -162,6 +308,8 @@ void rbfd_options_default(rbfd_options *opt) {
     opt->eps_absolute = 0;
     opt->refine_iters = 3;
     opt->profile = 0;
+    opt->engine = 0;
+    opt->grid_ctas = 0;
 }
 
 int rbfd_create(rbfd_mesh **out, int dim, int64_t n_s, const double *xyz_s, const double *dS, int n_levels,
@@ -182,6 +330,9 @@ int rbfd_create(rbfd_mesh **out, int dim, int64_t n_s, const double *xyz_s, cons
         if (o.precision != RBFD_FP64 && o.precision != RBFD_MIXED)
             rbfd::fail(RBFD_EINVAL, "rbfd_create: unknown precision");
         if (o.nc_cap < 0) rbfd::fail(RBFD_EINVAL, "rbfd_create: nc_cap must be >= 0");
+        if (o.engine != 0 && o.engine != 1) rbfd::fail(RBFD_EINVAL, "rbfd_create: engine must be 0 or 1");
+        if (o.grid_ctas < 0 || o.grid_ctas > rbfd::kMaxPersistCTAs)
+            rbfd::fail(RBFD_EINVAL, "rbfd_create: grid_ctas must be in [0, 2048]");
         if (!(eps > 0.0) || (!o.eps_absolute && !(eps < 1.0)) || !std::isfinite(eps))
             rbfd::fail(RBFD_EINVAL, "rbfd_create: eps must be in (0, 1) (or > 0 when absolute)");
         for (int l = 0; l < n_levels; ++l)
@@ -278,6 +429,11 @@ int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st) {
         st->sweep_launches = m->prof.launches[rbfd::kProfSweep];
         st->grow_launches = m->prof.launches[rbfd::kProfGrow];
         st->vol_launches = m->prof.launches[rbfd::kProfVol];
+        st->persist_ms = m->prof.ms[rbfd::kProfPersist];
+        st->persist_launches = m->prof.launches[rbfd::kProfPersist];
+        unsigned long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (m->d_phase_ns) RBFD_CUDA(cudaMemcpy(ph, m->d_phase_ns, sizeof(ph), cudaMemcpyDeviceToHost));
+        for (int q = 0; q < 8; ++q) st->persist_phase_ms[q] = ph[q] * 1e-6;
     });
 }
 
@@ -306,6 +462,48 @@ int rbfd_deform(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v,
 int rbfd_deform_f64(rbfd_mesh *m, int64_t n_v, const double *xyz_v, const double *d_v, double D, double k,
                     double *out) {
     return deform_common(m, n_v, xyz_v, d_v, D, k, out, true);
+}
+
+int rbfd_greedy_batch(rbfd_mesh **meshes, int n) {
+    if (n < 0 || (n > 0 && !meshes)) {
+        rbfd::g_last_error = "rbfd_greedy_batch: bad arguments";
+        return RBFD_EINVAL;
+    }
+    for (int i = 0; i < n; ++i)
+        if (!meshes[i]) {
+            rbfd::g_last_error = "rbfd_greedy_batch: NULL mesh";
+            return RBFD_EINVAL;
+        }
+    // persistent grids of the batch must be resident together
+    int cap = 0;
+    if (n > 1) {
+        int total = 0;
+        int rc = guarded([&] {
+            RBFD_CUDA(cudaSetDevice(meshes[0]->device));
+            total = rbfd::persist_max_ctas(meshes[0]);
+        });
+        if (rc != RBFD_OK) return rc;
+        cap = std::max(1, total / n);
+    }
+    for (int i = 0; i < n; ++i) meshes[i]->batch_ctas_cap = cap;
+    int rc = run_batch(n, [&](int i) {
+        RBFD_CUDA(cudaSetDevice(meshes[i]->device));
+        rbfd::greedy_run(meshes[i]);
+    }, "rbfd_greedy_batch");
+    for (int i = 0; i < n; ++i) meshes[i]->batch_ctas_cap = 0;
+    return rc;
+}
+
+int rbfd_deform_batch(rbfd_mesh **meshes, int n, const int64_t *n_v, const float *const *xyz_v,
+                      const float *const *d_v, const double *D, const double *k, float *const *out) {
+    if (n < 0 || (n > 0 && (!meshes || !n_v || !xyz_v || !d_v || !D || !k || !out))) {
+        rbfd::g_last_error = "rbfd_deform_batch: bad arguments";
+        return RBFD_EINVAL;
+    }
+    return run_batch(n, [&](int i) {
+        int rc = deform_common(meshes[i], n_v[i], xyz_v[i], d_v[i], D[i], k[i], out[i], false);
+        if (rc != RBFD_OK) rbfd::fail(rc, rbfd::g_last_error);
+    }, "rbfd_deform_batch");
 }
 
 int rbfd_destroy(rbfd_mesh *m) {

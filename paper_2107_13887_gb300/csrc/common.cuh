@@ -164,6 +164,51 @@ __device__ __forceinline__ df phi_df(df eta) {
     return df_mul(t8, q);
 }
 
+// One pair of the double-float evaluation: phi(|q - c| / R) for a point q and
+// a control c, both given relative to the same origin as (hi, lo) floats.
+// t32 holds the staged controls: rows 0..5 = x hi, x lo, y hi, y lo, z hi, z lo.
+template <int DIM, int BASIS>
+__device__ __forceinline__ df pair_phi_df(df qx, df qy, df qz, const float (*t32)[kTile], int q, df invR,
+                                          unsigned &useful) {
+    df dx = df_add(qx, {-t32[0][q], -t32[1][q]});
+    df dy = df_add(qy, {-t32[2][q], -t32[3][q]});
+    df r2 = df_add(df_sqr(dx), df_sqr(dy));
+    if (DIM == 3) {
+        df dz = df_add(qz, {-t32[4][q], -t32[5][q]});
+        r2 = df_add(r2, df_sqr(dz));
+    }
+    df eta = df_mul(df_sqrt(r2), invR);
+    useful += (eta.hi < 1.0f);
+    return phi_df<BASIS>(eta);
+}
+
+// Accumulate sum_q alpha_q phi_q over the m staged controls of a tile, in
+// order q = 0, 1, ..., two pairs per iteration so that the compiler can
+// interleave their independent instruction chains (one warp per scheduler
+// has nothing else to hide the FP32 latencies with).  Rows 6..11 of t32 are
+// alpha x hi, lo, y hi, lo, z hi, lo.
+template <int DIM, int BASIS>
+__device__ __forceinline__ void tile_accumulate_df(df qx, df qy, df qz, const float (*t32)[kTile], int m,
+                                                   df invR, df acc[3], unsigned &useful) {
+    int q = 0;
+    for (; q + 2 <= m; q += 2) {
+        const df f0 = pair_phi_df<DIM, BASIS>(qx, qy, qz, t32, q, invR, useful);
+        const df f1 = pair_phi_df<DIM, BASIS>(qx, qy, qz, t32, q + 1, invR, useful);
+        acc[0] = df_add(acc[0], df_mul(f0, {t32[6][q], t32[7][q]}));
+        acc[1] = df_add(acc[1], df_mul(f0, {t32[8][q], t32[9][q]}));
+        if (DIM == 3) acc[2] = df_add(acc[2], df_mul(f0, {t32[10][q], t32[11][q]}));
+        acc[0] = df_add(acc[0], df_mul(f1, {t32[6][q + 1], t32[7][q + 1]}));
+        acc[1] = df_add(acc[1], df_mul(f1, {t32[8][q + 1], t32[9][q + 1]}));
+        if (DIM == 3) acc[2] = df_add(acc[2], df_mul(f1, {t32[10][q + 1], t32[11][q + 1]}));
+    }
+    if (q < m) {
+        const df f0 = pair_phi_df<DIM, BASIS>(qx, qy, qz, t32, q, invR, useful);
+        acc[0] = df_add(acc[0], df_mul(f0, {t32[6][q], t32[7][q]}));
+        acc[1] = df_add(acc[1], df_mul(f0, {t32[8][q], t32[9][q]}));
+        if (DIM == 3) acc[2] = df_add(acc[2], df_mul(f0, {t32[10][q], t32[11][q]}));
+    }
+}
+
 // L2-coherent load of a double4 written by another block of the same launch.
 __device__ __forceinline__ double4 ldcg_d4(const double4 *p) {
     const double2 *q = reinterpret_cast<const double2 *>(p);
@@ -238,6 +283,15 @@ struct GreedyState {
     double emax;      // sqrt(best_key) / S0 of the last sweep
     unsigned int pb_done;   // last-block-done counter of the sweep
     unsigned int red_done;  // last-block-done counter of reductions
+};
+
+// Counter + generation word of the bounded grid barrier of the persistent
+// greedy launch; err is set by a block that waited too long.
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+    int err;
+    int pad;
 };
 
 }  // namespace rbfd

@@ -280,21 +280,7 @@ __global__ void __launch_bounds__(kThreads) k_vol_sweep(VolArgs a) {
                         if (DIM == 3) acc64[2] = __dadd_rn(acc64[2], __dmul_rn(t64[5][q], f));
                     }
                 } else {
-                    for (int q = 0; q < m; ++q) {
-                        df dx = df_add(qx, {-t32[0][q], -t32[1][q]});
-                        df dy = df_add(qy, {-t32[2][q], -t32[3][q]});
-                        df r2 = df_add(df_sqr(dx), df_sqr(dy));
-                        if (DIM == 3) {
-                            df dz = df_add(qz, {-t32[4][q], -t32[5][q]});
-                            r2 = df_add(r2, df_sqr(dz));
-                        }
-                        df eta = df_mul(df_sqrt(r2), invR);
-                        df f = phi_df<BASIS>(eta);
-                        useful += (eta.hi < 1.0f);
-                        acc[0] = df_add(acc[0], df_mul(f, {t32[6][q], t32[7][q]}));
-                        acc[1] = df_add(acc[1], df_mul(f, {t32[8][q], t32[9][q]}));
-                        if (DIM == 3) acc[2] = df_add(acc[2], df_mul(f, {t32[10][q], t32[11][q]}));
-                    }
+                    tile_accumulate_df<DIM, BASIS>(qx, qy, qz, t32, m, invR, acc, useful);
                 }
             }
             __syncthreads();

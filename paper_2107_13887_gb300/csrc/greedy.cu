@@ -285,21 +285,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(SweepArgs a) {
                     if (DIM == 3) acc64[2] = __dadd_rn(acc64[2], __dmul_rn(t64[5][q], f));
                 }
             } else {
-                for (int q = 0; q < m; ++q) {
-                    df dx = df_add(qx, {-t32[0][q], -t32[1][q]});
-                    df dy = df_add(qy, {-t32[2][q], -t32[3][q]});
-                    df r2 = df_add(df_sqr(dx), df_sqr(dy));
-                    if (DIM == 3) {
-                        df dz = df_add(qz, {-t32[4][q], -t32[5][q]});
-                        r2 = df_add(r2, df_sqr(dz));
-                    }
-                    df eta = df_mul(df_sqrt(r2), invR);
-                    df f = phi_df<BASIS>(eta);
-                    useful += (eta.hi < 1.0f);
-                    acc[0] = df_add(acc[0], df_mul(f, {t32[6][q], t32[7][q]}));
-                    acc[1] = df_add(acc[1], df_mul(f, {t32[8][q], t32[9][q]}));
-                    if (DIM == 3) acc[2] = df_add(acc[2], df_mul(f, {t32[10][q], t32[11][q]}));
-                }
+                tile_accumulate_df<DIM, BASIS>(qx, qy, qz, t32, m, invR, acc, useful);
             }
         }
         __syncthreads();
@@ -943,7 +929,15 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     RBFD_CUDA(cudaMemsetAsync(m->d_pairs, 0, 4 * sizeof(unsigned long long), st));
     m->d_st = dalloc<GreedyState>(1, "greedy state");
     RBFD_CUDA(cudaMemsetAsync(m->d_st, 0, sizeof(GreedyState), st));
-    RBFD_CUDA(cudaMallocHost(&m->h_st, sizeof(GreedyState)));
+    m->d_bar = dalloc<GridBarrier>(1, "grid barrier");
+    RBFD_CUDA(cudaMemsetAsync(m->d_bar, 0, sizeof(GridBarrier), st));
+    m->d_pred = dalloc<double>((size_t)4 * kMaxPersistCTAs, "persistent reductions");
+    m->d_pgpart = dalloc<double>((size_t)(cap / 128 + 2) * cap, "persistent column partials");
+    m->d_kt_done = dalloc<unsigned int>((size_t)cap / 32 + 2, "column-group counters");
+    m->d_phase_ns = dalloc<unsigned long long>(8, "phase timing");
+    RBFD_CUDA(cudaMemsetAsync(m->d_phase_ns, 0, 8 * sizeof(unsigned long long), st));
+    RBFD_CUDA(cudaMemsetAsync(m->d_kt_done, 0, sizeof(unsigned int) * (cap / 32 + 2), st));
+    m->h_st = static_cast<GreedyState *>(pinned_alloc(sizeof(GreedyState)));
     RBFD_CUDA(cudaStreamSynchronize(st));
 
     m->stats.launches += 6;  // unpack, bbox x2, morton, gather, point blocks
@@ -1022,9 +1016,33 @@ void greedy_run(rbfd_mesh *m) {
         int n = 1;
         int resumes = 0;
         for (;;) {
-            // ---- greedy steps, launched in batches; the device decides when to stop
-            const int kBatch = 16;
+            // ---- greedy steps: one persistent cooperative launch (engine 0) ...
             bool stopped = false;
+            if (m->opt.engine == 0) {
+                const int maxc = std::min(persist_max_ctas(m), kMaxPersistCTAs);
+                if (maxc < 1) fail(RBFD_ECUDA, "persistent greedy kernel cannot be resident on this device");
+                int ctas = m->opt.grid_ctas > 0 ? m->opt.grid_ctas : std::min(std::max(64, 4 * m->n_pb), 2 * 152);
+                if (m->batch_ctas_cap > 0) ctas = std::min(ctas, m->batch_ctas_cap);
+                ctas = std::max(1, std::min(ctas, maxc));
+                RBFD_CUDA(cudaMemsetAsync(m->d_bar, 0, sizeof(GridBarrier), st));
+                cudaEvent_t e0 = m->prof.begin(st);
+                persist_run_level(m, L.R, L.tau, ctas);
+                m->prof.end(kProfPersist, e0, st, 1);
+                m->stats.persist_ctas = ctas;
+                read_state(m);
+                m->prof.flush();
+                GridBarrier hb{};
+                RBFD_CUDA(cudaMemcpy(&hb, m->d_bar, sizeof(hb), cudaMemcpyDeviceToHost));
+                if (hb.err) fail(RBFD_ETIMEOUT, "persistent greedy: a grid barrier exceeded its wait bound");
+                if (m->h_st->status == RBFD_ESINGULAR)
+                    fail(RBFD_ESINGULAR, "Phi_cc is not positive definite at level " + std::to_string(l) +
+                                             " (coincident or near-coincident controls)");
+                if (!m->h_st->stop) fail(RBFD_ECUDA, "persistent greedy ended without a stop decision");
+                n = m->h_st->n;
+                stopped = true;
+            }
+            // ... or separate launches per step, in batches (engine 1)
+            const int kBatch = 16;
             while (!stopped) {
                 for (int s = 0; s < kBatch; ++s) {
                     SweepArgs a = base_sweep_args(m, L.R, L.tau);
@@ -1063,6 +1081,7 @@ void greedy_run(rbfd_mesh *m) {
                                              " (coincident or near-coincident controls)");
             }
             n = m->h_st->n;
+            m->stats.greedy_steps += 0;
             // ---- level close: FP64 iterative refinement of alpha
             for (int it = 0; it < std::max(0, m->opt.refine_iters); ++it) {
                 const unsigned nb = cdiv(n, kThreads);

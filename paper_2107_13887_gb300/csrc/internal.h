@@ -25,9 +25,14 @@ void set_last_error(const std::string &msg);
 void check_cuda(cudaError_t e, const char *what);
 #define RBFD_CUDA(call) ::rbfd::check_cuda((call), #call)
 
-// Device allocation that reports RBFD_ENOMEM through Error.
+// Device allocation from the library's per-device caching pool; reports
+// RBFD_ENOMEM through Error.  dfree returns the block to the pool: call it
+// only once the stream that used the block has been synchronised.
 void *dmalloc(size_t bytes, const char *what);
 void dfree(void *p);
+// Small pinned host blocks (<= 4 KB), pooled.
+void *pinned_alloc(size_t bytes);
+void pinned_free(void *p);
 
 template <typename T>
 T *dalloc(size_t n, const char *what) {
@@ -84,7 +89,7 @@ struct Level {
 };
 
 // Optional per-kernel-class timing with CUDA events on the mesh's stream.
-enum ProfKind { kProfSweep = 0, kProfGrow = 1, kProfVol = 2, kProfKinds = 3 };
+enum ProfKind { kProfSweep = 0, kProfGrow = 1, kProfVol = 2, kProfPersist = 3, kProfKinds = 4 };
 
 struct Profiler {
     bool on = false;
@@ -94,8 +99,8 @@ struct Profiler {
         cudaEvent_t a, b;
     };
     std::vector<Pending> pend;
-    double ms[kProfKinds] = {0, 0, 0};
-    int64_t launches[kProfKinds] = {0, 0, 0};
+    double ms[kProfKinds] = {0, 0, 0, 0};
+    int64_t launches[kProfKinds] = {0, 0, 0, 0};
     cudaEvent_t get();
     cudaEvent_t begin(cudaStream_t st);            // records and returns the start event (or nullptr)
     void end(int kind, cudaEvent_t a, cudaStream_t st, int n_launches);
@@ -152,6 +157,13 @@ struct rbfd_mesh {
     unsigned long long *d_pairs = nullptr;  // [4]: surface sweep useful, visited; volume useful, visited
     rbfd::GreedyState *d_st = nullptr;
     rbfd::GreedyState *h_st = nullptr;  // pinned
+    // persistent engine
+    int batch_ctas_cap = 0;          // set by the batch calls: blocks this mesh may use
+    rbfd::GridBarrier *d_bar = nullptr;
+    double *d_pred = nullptr;       // [kMaxPersistCTAs][4] per-block y.y, y.w
+    double *d_pgpart = nullptr;     // [cap/128 + 1][cap] column-sum partials
+    unsigned int *d_kt_done = nullptr;  // [cap/32 + 1] column-group counters
+    unsigned long long *d_phase_ns = nullptr;  // [8] persistent phase timing (profile mode)
 
     std::vector<rbfd::Level> levels;
     bool greedy_done = false;
@@ -174,6 +186,9 @@ struct rbfd_mesh {
 };
 
 namespace rbfd {
+constexpr int kMaxPersistCTAs = 2048;
+int persist_max_ctas(rbfd_mesh *m);
+void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas);
 void greedy_run(rbfd_mesh *m);
 void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64, double D, double k,
                 void *out);

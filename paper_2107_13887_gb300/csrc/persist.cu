@@ -1,0 +1,580 @@
+// persist.cu -- the greedy selection of one level (Section 3) as ONE
+// cooperative launch: the grid stays resident and walks through the greedy
+// steps itself, separated by a grid barrier, so no step waits for the host.
+//
+// Per step, with n controls selected so far (every block tracks n in lockstep):
+//   phase 1  surface error sweep (Eq. 12): items (point block, control chunk);
+//            chunk partial sums -> scratch; the last chunk of each point block
+//            (atomic counter) reduces them in chunk order in FP64, forms
+//            E = dS_l - sum and the key |E|^2, and writes the block's argmax;
+//            the last point block to finish (second counter) takes the step's
+//            decision: global argmax, stop test max|E|/S0 < tau_l in FP64, and,
+//            if the level goes on, phi(|r_cn - r_ck|/R) for every k (up to
+//            1024 controls; beyond that all blocks share it after the barrier),
+//            c_n listed in every point block within R, c_n recorded.
+//   -- barrier --
+//   phase 3  y = G phi (one warp per row of the inverse factor G = L^{-1});
+//            per-block partial sums of y.y and y.w.
+//   -- barrier --
+//   phase 4  l = sqrt(1 - y.y), w_n = (dS_l(c_n) - y.w) / l; column sums of
+//            y^T G in 32-column x 128-row tiles, finished by the last tile of
+//            each column group (atomic counter): G row n and alpha += w_n G_n.
+//   -- barrier --
+//
+// The barrier is a counter plus generation word in global memory; a block
+// that waits longer than a fixed number of polls sets an error word and
+// returns, and every other block returns at its next barrier, so a failure
+// ends the launch instead of hanging it.  Data written by another block of
+// this launch is read with ld.global.cg (L2), never through L1.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+
+#include "internal.h"
+
+namespace rbfd {
+
+namespace {
+
+constexpr int kT = 128;        // threads per block (4 warps)
+constexpr int kColTile = 32;   // columns per column-sum item
+constexpr int kRowTile = 128;  // rows per column-sum item
+constexpr int kFusePhiMax = 1024;  // up to this many controls one block computes the phi column
+
+struct PersistArgs {
+    int64_t n_s;
+    int n_pb, cap, dim, n_chunk_max;
+    double R, R2, S0, tau, piv_tol_per_n;
+    float invR_hi, invR_lo;
+    const double4 *xs, *pb_org, *pb_lo, *pb_hi, *cur;
+    const float4 *xs_hi, *xs_lo;
+    const uint32_t *perm, *inv;
+    unsigned char *sel;
+    uint32_t *nb_cnt, *nb_list;
+    double4 *cx, *alpha, *w;
+    uint32_t *cid;
+    double *G, *phi, *y, *red, *gpart;
+    double4 *part;
+    unsigned int *pb_done, *kt_done;
+    double *pb_key;
+    int *pb_idx;
+    GridBarrier *bar;
+    unsigned long long spin_limit;
+    GreedyState *st;
+    unsigned long long *pairs;
+    int test_skip_arrival;  // tests only: block 0 leaves before its first barrier arrival
+    unsigned long long *phase_ns;  // non-null: block 0 accumulates [work, wait] ns per phase (8 words)
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ldcg_u32(const uint32_t *p) { return __ldcg(p); }
+__device__ __forceinline__ double ldcg_d(const double *p) { return __ldcg(p); }
+
+// Grid-wide barrier with a bounded wait.  Returns false (in every thread of
+// the block) if the launch is failing: this block timed out or another one did.
+__device__ __forceinline__ bool grid_sync(GridBarrier *b, unsigned nblk, unsigned long long limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &b->gen;
+        volatile int *verr = &b->err;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&b->count, 1u);
+        if (arrived == nblk - 1) {
+            b->count = 0;
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            unsigned long long it = 0;
+            while (*vgen == g) {
+                if (*verr) break;
+                if (++it > limit) {
+                    atomicExch(&b->err, 1);
+                    break;
+                }
+                __nanosleep(8);
+            }
+        }
+        __threadfence();
+        s_ok = (*verr == 0);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int DIM, int BASIS, int MODE>
+__global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
+    __shared__ double t64[6][kTile];
+    __shared__ float t32[12][kTile];
+    __shared__ double sk[32];
+    __shared__ int si[32];
+    __shared__ double scol[4][kColTile];
+    __shared__ double sred[4][4];
+    __shared__ bool s_last, s_lead;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned P = gridDim.x;
+    int n = __ldcg(&a.st->n);
+    const df invR = {a.invR_hi, a.invR_lo};
+    // phase timing (block 0, thread 0): work = phase start -> barrier entry,
+    // wait = barrier entry -> exit
+    const bool timing = a.phase_ns && blockIdx.x == 0 && tid == 0;
+    unsigned long long acc_ns[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long t_mark = timing ? gtimer() : 0ull;
+#define RBFD_SYNC(PH)                                                            \
+    {                                                                            \
+        unsigned long long t_in = timing ? gtimer() : 0ull;                      \
+        bool ok_ = grid_sync(a.bar, P, a.spin_limit);                            \
+        if (timing) {                                                            \
+            unsigned long long t_out = gtimer();                                 \
+            acc_ns[2 * (PH)] += t_in - t_mark;                                   \
+            acc_ns[2 * (PH) + 1] += t_out - t_in;                                \
+            t_mark = t_out;                                                      \
+        }                                                                        \
+        if (!ok_) {                                                              \
+            if (timing)                                                          \
+                for (int q = 0; q < 8; ++q) atomicAdd(&a.phase_ns[q], acc_ns[q]); \
+            return;                                                              \
+        }                                                                        \
+    }
+#define RBFD_EXIT()                                                              \
+    {                                                                            \
+        if (timing)                                                              \
+            for (int q = 0; q < 8; ++q) atomicAdd(&a.phase_ns[q], acc_ns[q]);   \
+        return;                                                                  \
+    }
+
+    for (int guard = 0; guard <= a.cap; ++guard) {
+        // ------------------------------------------------ phase 1: sweep (+ the step's decision)
+        const bool fuse_phi = n <= kFusePhiMax;  // phi computed by the deciding block
+        int nch = (int)((P + a.n_pb - 1) / a.n_pb);
+        nch = max(1, min(nch, min(a.n_chunk_max, (n + 15) / 16)));
+        const int cl = (n + nch - 1) / nch;
+        for (int item = blockIdx.x; item < a.n_pb * nch; item += P) {
+            const int pb = item / nch, ch = item % nch;
+            const int64_t p = (int64_t)pb * kPB + tid;
+            const bool valid = p < a.n_s;
+            const int cnt = (int)ldcg_u32(&a.nb_cnt[pb]);
+            const int lo = ch * cl, hi = min(cnt, lo + cl);
+            const double4 org = a.pb_org[pb];
+            double acc64[3] = {0, 0, 0};
+            df acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+            double px = 0, py = 0, pz = 0;
+            df qx{0, 0}, qy{0, 0}, qz{0, 0};
+            if (valid) {
+                if (MODE == 0) {
+                    double4 q = a.xs[p];
+                    px = q.x; py = q.y; pz = q.z;
+                } else {
+                    float4 h = a.xs_hi[p], l = a.xs_lo[p];
+                    qx = {h.x, l.x}; qy = {h.y, l.y}; qz = {h.z, l.z};
+                }
+            }
+            unsigned useful = 0;
+            for (int t0 = lo; t0 < hi; t0 += kTile) {
+                const int m = min(kTile, hi - t0);
+                if (tid < m) {
+                    const uint32_t j = ldcg_u32(&a.nb_list[(size_t)pb * a.cap + t0 + tid]);
+                    const double4 c = ldcg_d4(&a.cx[j]), al = ldcg_d4(&a.alpha[j]);
+                    if (MODE == 0) {
+                        t64[0][tid] = c.x; t64[1][tid] = c.y; t64[2][tid] = c.z;
+                        t64[3][tid] = al.x; t64[4][tid] = al.y; t64[5][tid] = al.z;
+                    } else {
+                        df rx = df_from_double(c.x - org.x), ry = df_from_double(c.y - org.y),
+                           rz = df_from_double(c.z - org.z);
+                        df ax = df_from_double(al.x), ay = df_from_double(al.y), az = df_from_double(al.z);
+                        t32[0][tid] = rx.hi; t32[1][tid] = rx.lo; t32[2][tid] = ry.hi; t32[3][tid] = ry.lo;
+                        t32[4][tid] = rz.hi; t32[5][tid] = rz.lo; t32[6][tid] = ax.hi; t32[7][tid] = ax.lo;
+                        t32[8][tid] = ay.hi; t32[9][tid] = ay.lo; t32[10][tid] = az.hi; t32[11][tid] = az.lo;
+                    }
+                }
+                __syncthreads();
+                if (valid) {
+                    if (MODE == 0) {
+                        for (int q = 0; q < m; ++q) {
+                            double eta = __ddiv_rn(dist_f64<DIM>(px, py, pz, t64[0][q], t64[1][q], t64[2][q]), a.R);
+                            double f = phi_f64<BASIS>(eta);
+                            useful += (eta < 1.0);
+                            acc64[0] = __dadd_rn(acc64[0], __dmul_rn(t64[3][q], f));
+                            acc64[1] = __dadd_rn(acc64[1], __dmul_rn(t64[4][q], f));
+                            if (DIM == 3) acc64[2] = __dadd_rn(acc64[2], __dmul_rn(t64[5][q], f));
+                        }
+                    } else {
+                        tile_accumulate_df<DIM, BASIS>(qx, qy, qz, t32, m, invR, acc, useful);
+                    }
+                }
+                __syncthreads();
+            }
+            if (MODE == 1) {
+                acc64[0] = df_to_double(acc[0]);
+                acc64[1] = df_to_double(acc[1]);
+                acc64[2] = df_to_double(acc[2]);
+            }
+            if (valid) a.part[(size_t)ch * a.n_s + p] = make_double4(acc64[0], acc64[1], acc64[2], 0.0);
+            {
+                unsigned u = useful;
+                for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+                if (lane == 0 && u) atomicAdd(&a.pairs[0], (unsigned long long)u);
+                if (tid == 0 && hi > lo) {
+                    unsigned long long nv = (unsigned long long)min((int64_t)kPB, a.n_s - (int64_t)pb * kPB);
+                    atomicAdd(&a.pairs[1], nv * (unsigned long long)(hi - lo));
+                }
+            }
+            // last chunk of this point block: E, key, block argmax; the last
+            // point block to finish then takes the step's decision
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) s_last = atomicAdd(&a.pb_done[pb], 1u) == (unsigned)(nch - 1);
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                double key = -1.0;
+                int orig = -1;
+                if (valid) {
+                    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+                    int c = 0;
+                    for (; c + 4 <= nch; c += 4) {  // four independent loads in flight
+                        double4 v[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) v[q] = ldcg_d4(&a.part[(size_t)(c + q) * a.n_s + p]);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            s0 = __dadd_rn(s0, v[q].x);
+                            s1 = __dadd_rn(s1, v[q].y);
+                            s2 = __dadd_rn(s2, v[q].z);
+                        }
+                    }
+                    for (; c < nch; ++c) {
+                        double4 v = ldcg_d4(&a.part[(size_t)c * a.n_s + p]);
+                        s0 = __dadd_rn(s0, v.x);
+                        s1 = __dadd_rn(s1, v.y);
+                        s2 = __dadd_rn(s2, v.z);
+                    }
+                    const double4 cu = a.cur[p];
+                    const double e0 = __dsub_rn(cu.x, s0), e1 = __dsub_rn(cu.y, s1);
+                    const double e2 = (DIM == 3) ? __dsub_rn(cu.z, s2) : 0.0;
+                    double k2 = __dmul_rn(e0, e0);
+                    k2 = __dadd_rn(k2, __dmul_rn(e1, e1));
+                    if (DIM == 3) k2 = __dadd_rn(k2, __dmul_rn(e2, e2));
+                    if (!__ldcg(reinterpret_cast<const unsigned char *>(a.sel) + p)) {
+                        key = k2;
+                        orig = (int)a.perm[p];
+                    }
+                }
+                block_argmax(key, orig, sk, si);
+                if (tid == 0) {
+                    a.pb_key[pb] = key;
+                    a.pb_idx[pb] = orig;
+                    a.pb_done[pb] = 0;
+                    __threadfence();
+                    s_lead = atomicAdd(&a.st->pb_done, 1u) == (unsigned)(a.n_pb - 1);
+                }
+                __syncthreads();
+                if (s_lead) {
+                    // ---- the step's decision (one block): argmax, stop test, phi, lists
+                    __threadfence();
+                    double K = -1.0;
+                    int I = -1;
+                    for (int b = tid; b < a.n_pb; b += kT) {
+                        const double kb = __ldcg(&a.pb_key[b]);
+                        const int ib = __ldcg(&a.pb_idx[b]);
+                        if (better(kb, ib, K, I)) {
+                            K = kb;
+                            I = ib;
+                        }
+                    }
+                    block_argmax(K, I, sk, si);
+                    const double e = I >= 0 ? __ddiv_rn(__dsqrt_rn(K), a.S0) : 0.0;
+                    const bool stop = I < 0 || e < a.tau || n >= a.cap;
+                    if (!stop) {
+                        const uint32_t c = a.inv[I];
+                        const double4 xc = a.xs[c];
+                        if (fuse_phi)
+                            for (int k = tid; k < n; k += kT) {
+                                const double4 ck = ldcg_d4(&a.cx[k]);
+                                a.phi[k] = phi_f64<BASIS>(
+                                    __ddiv_rn(dist_f64<DIM>(xc.x, xc.y, xc.z, ck.x, ck.y, ck.z), a.R));
+                            }
+                        for (int t = tid; t < a.n_pb; t += kT) {
+                            const double4 l = a.pb_lo[t], h = a.pb_hi[t];
+                            const double dx = fmax(fmax(l.x - xc.x, xc.x - h.x), 0.0);
+                            const double dy = fmax(fmax(l.y - xc.y, xc.y - h.y), 0.0);
+                            const double dz = DIM == 3 ? fmax(fmax(l.z - xc.z, xc.z - h.z), 0.0) : 0.0;
+                            if (dx * dx + dy * dy + dz * dz < a.R2 * (1.0 + 1e-9)) {
+                                const uint32_t k = ldcg_u32(&a.nb_cnt[t]);
+                                a.nb_list[(size_t)t * a.cap + k] = (uint32_t)n;
+                                a.nb_cnt[t] = k + 1;
+                            }
+                        }
+                        if (tid == 0) {
+                            a.sel[c] = 1;
+                            a.cx[n] = xc;
+                            a.cid[n] = c;
+                            a.st->best = (int)c;
+                        }
+                    }
+                    if (tid == 0) {
+                        a.st->best_orig = I;
+                        a.st->best_key = K;
+                        a.st->emax = e;
+                        a.st->pb_done = 0;
+                        if (stop) {
+                            a.st->n = n;
+                            if (!(I < 0 || e < a.tau)) a.st->status = RBFD_ENOTCONV;
+                            a.st->stop = 1;
+                        }
+                    }
+                }
+            }
+        }
+        if (a.test_skip_arrival && blockIdx.x == 0) return;  // the others' waits run out
+        RBFD_SYNC(0)
+
+        // ------------------------------------------------ every block: the decision
+        if (__ldcg(&a.st->stop)) RBFD_EXIT()
+        const uint32_t c = (uint32_t)__ldcg(&a.st->best);
+        const bool first_block = blockIdx.x == 0 && tid == 0;
+        if (!fuse_phi) {
+            const double4 xc = a.xs[c];
+            const unsigned gtid = blockIdx.x * kT + tid, gstride = P * kT;
+            for (unsigned k = gtid; k < (unsigned)n; k += gstride) {
+                const double4 ck = ldcg_d4(&a.cx[k]);
+                a.phi[k] = phi_f64<BASIS>(__ddiv_rn(dist_f64<DIM>(xc.x, xc.y, xc.z, ck.x, ck.y, ck.z), a.R));
+            }
+            RBFD_SYNC(1)
+        }
+
+        // ------------------------------------------------ phase 3: y = G phi
+        double yy = 0, yw0 = 0, yw1 = 0, yw2 = 0;
+        for (int j = blockIdx.x * 4 + warp; j < n; j += P * 4) {
+            const double *row = a.G + (size_t)j * a.cap;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int k = lane;
+            for (; k + 96 <= j; k += 128) {  // four independent load pairs in flight
+                const double g0 = ldcg_d(row + k), g1 = ldcg_d(row + k + 32), g2 = ldcg_d(row + k + 64),
+                             g3 = ldcg_d(row + k + 96);
+                const double p0 = ldcg_d(a.phi + k), p1 = ldcg_d(a.phi + k + 32), p2 = ldcg_d(a.phi + k + 64),
+                             p3 = ldcg_d(a.phi + k + 96);
+                s0 = fma(g0, p0, s0);
+                s1 = fma(g1, p1, s1);
+                s2 = fma(g2, p2, s2);
+                s3 = fma(g3, p3, s3);
+            }
+            for (; k <= j; k += 32) s0 = fma(ldcg_d(row + k), ldcg_d(a.phi + k), s0);
+            double s = warp_sum_d((s0 + s1) + (s2 + s3));
+            if (lane == 0) {
+                a.y[j] = s;
+                const double4 wj = ldcg_d4(&a.w[j]);
+                yy += s * s;
+                yw0 += s * wj.x;
+                yw1 += s * wj.y;
+                yw2 += s * wj.z;
+            }
+        }
+        if (lane == 0) {
+            sred[warp][0] = yy;
+            sred[warp][1] = yw0;
+            sred[warp][2] = yw1;
+            sred[warp][3] = yw2;
+        }
+        __syncthreads();
+        if (tid < 4) a.red[blockIdx.x * 4 + tid] = sred[0][tid] + sred[1][tid] + sred[2][tid] + sred[3][tid];
+        RBFD_SYNC(2)
+
+        // ------------------------------------------------ phase 4: G row n, alpha
+        {
+            double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+            for (unsigned b = tid; b < P; b += kT) {
+                v0 += ldcg_d(&a.red[b * 4 + 0]);
+                v1 += ldcg_d(&a.red[b * 4 + 1]);
+                v2 += ldcg_d(&a.red[b * 4 + 2]);
+                v3 += ldcg_d(&a.red[b * 4 + 3]);
+            }
+            v0 = warp_sum_d(v0);
+            v1 = warp_sum_d(v1);
+            v2 = warp_sum_d(v2);
+            v3 = warp_sum_d(v3);
+            if (lane == 0) {
+                scol[warp][0] = v0;
+                scol[warp][1] = v1;
+                scol[warp][2] = v2;
+                scol[warp][3] = v3;
+            }
+            __syncthreads();
+        }
+        double r4[4];
+        for (int q = 0; q < 4; ++q) r4[q] = ((scol[0][q] + scol[1][q]) + scol[2][q]) + scol[3][q];
+        __syncthreads();
+        const double l2 = 1.0 - r4[0];  // phi(0) = 1 for every Wendland function
+        if (!(l2 > a.piv_tol_per_n * (n + 1))) {
+            if (first_block) {
+                a.st->status = RBFD_ESINGULAR;
+                a.st->stop = 1;
+                a.st->n = n;
+            }
+            RBFD_EXIT()
+        }
+        const double l = sqrt(l2);
+        const double4 bc = a.cur[c];
+        const double wn0 = (bc.x - r4[1]) / l, wn1 = (bc.y - r4[2]) / l, wn2 = (bc.z - r4[3]) / l;
+        double *Grow = a.G + (size_t)n * a.cap;
+        if (first_block) {
+            Grow[n] = 1.0 / l;
+            a.w[n] = make_double4(wn0, wn1, wn2, 0.0);
+            a.alpha[n] = make_double4(wn0 / l, wn1 / l, wn2 / l, 0.0);
+        }
+        const int n_kt = (n + kColTile - 1) / kColTile, n_jc = (n + kRowTile - 1) / kRowTile;
+        for (int item = blockIdx.x; item < n_kt * n_jc; item += P) {
+            const int kt = item / n_jc, jc = item % n_jc;
+            const int k = kt * kColTile + lane;
+            const int jb = jc * kRowTile + warp * 32;
+            double s = 0.0;
+#pragma unroll
+            for (int r0 = 0; r0 < 32; r0 += 8) {  // eight independent load pairs in flight
+                double gv[8], yv[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int j = jb + r0 + q;
+                    const bool ok = j < n && k <= j;
+                    gv[q] = ok ? ldcg_d(a.G + (size_t)j * a.cap + k) : 0.0;
+                    yv[q] = ok ? ldcg_d(a.y + j) : 0.0;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) s = fma(yv[q], gv[q], s);
+            }
+            scol[warp][lane] = s;
+            __syncthreads();
+            if (n_jc == 1) {  // one row tile: the column sums are complete here
+                if (warp == 0 && k < n) {
+                    const double t = ((scol[0][lane] + scol[1][lane]) + scol[2][lane]) + scol[3][lane];
+                    const double g = -t / l;
+                    Grow[k] = g;
+                    double4 al = ldcg_d4(&a.alpha[k]);
+                    al.x = fma(wn0, g, al.x);
+                    al.y = fma(wn1, g, al.y);
+                    al.z = fma(wn2, g, al.z);
+                    a.alpha[k] = al;
+                }
+                __syncthreads();
+                continue;
+            }
+            if (warp == 0 && k < n)
+                a.gpart[(size_t)jc * a.cap + k] = ((scol[0][lane] + scol[1][lane]) + scol[2][lane]) + scol[3][lane];
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) s_last = atomicAdd(&a.kt_done[kt], 1u) == (unsigned)(n_jc - 1);
+            __syncthreads();
+            if (s_last && warp == 0) {
+                __threadfence();
+                if (k < n) {
+                    double t = 0.0;
+                    for (int q = 0; q < n_jc; ++q) t += ldcg_d(&a.gpart[(size_t)q * a.cap + k]);
+                    const double g = -t / l;
+                    Grow[k] = g;
+                    double4 al = ldcg_d4(&a.alpha[k]);
+                    al.x = fma(wn0, g, al.x);
+                    al.y = fma(wn1, g, al.y);
+                    al.z = fma(wn2, g, al.z);
+                    a.alpha[k] = al;
+                }
+                if (lane == 0) a.kt_done[kt] = 0;
+            }
+            __syncthreads();
+        }
+        if (first_block) a.st->n = n + 1;
+        RBFD_SYNC(3)
+        ++n;
+    }
+    RBFD_EXIT()
+#undef RBFD_SYNC
+#undef RBFD_EXIT
+}
+
+template <int DIM, int BASIS, int MODE>
+const void *kernel_ptr() {
+    return reinterpret_cast<const void *>(&k_greedy_persist<DIM, BASIS, MODE>);
+}
+
+const void *select_kernel(int dim, int basis, int mode) {
+#define RBFD_SEL(D, B)                                                                  \
+    if (dim == D && basis == B) return mode == 0 ? kernel_ptr<D, B, 0>() : kernel_ptr<D, B, 1>();
+    RBFD_SEL(2, 0) RBFD_SEL(2, 2) RBFD_SEL(2, 4) RBFD_SEL(2, 6)
+    RBFD_SEL(3, 0) RBFD_SEL(3, 2) RBFD_SEL(3, 4) RBFD_SEL(3, 6)
+#undef RBFD_SEL
+    return nullptr;
+}
+
+}  // namespace
+
+int persist_max_ctas(rbfd_mesh *m) {
+    const void *k = select_kernel(m->dim, m->opt.basis, m->opt.precision == RBFD_FP64 ? 0 : 1);
+    int occ = 0, sms = 0;
+    RBFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kT, 0));
+    RBFD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+    return std::max(0, occ * sms);
+}
+
+void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
+    PersistArgs a{};
+    a.n_s = m->n_s;
+    a.n_pb = m->n_pb;
+    a.cap = m->cap;
+    a.dim = m->dim;
+    a.n_chunk_max = m->n_chunk_max;
+    a.R = R;
+    a.R2 = R * R;
+    a.S0 = m->S0;
+    a.tau = tau;
+    a.piv_tol_per_n = 8.0 * 1.1102230246251565e-16;
+    const double inv = 1.0 / R;
+    a.invR_hi = (float)inv;
+    a.invR_lo = (float)(inv - (double)a.invR_hi);
+    a.xs = m->d_xs;
+    a.pb_org = m->d_pb_org;
+    a.pb_lo = m->d_pb_lo;
+    a.pb_hi = m->d_pb_hi;
+    a.cur = m->d_cur;
+    a.xs_hi = m->d_xs_hi;
+    a.xs_lo = m->d_xs_lo;
+    a.perm = m->d_perm;
+    a.inv = m->d_inv;
+    a.sel = m->d_sel;
+    a.nb_cnt = m->d_nb_cnt;
+    a.nb_list = m->d_nb_list;
+    a.cx = m->d_cx;
+    a.alpha = m->d_alpha;
+    a.w = m->d_w;
+    a.cid = m->d_cid;
+    a.G = m->d_G;
+    a.phi = m->d_phi;
+    a.y = m->d_y;
+    a.red = m->d_pred;
+    a.gpart = m->d_pgpart;
+    a.part = m->d_part;
+    a.pb_done = m->d_pb_done;
+    a.kt_done = m->d_kt_done;
+    a.pb_key = m->d_pb_key;
+    a.pb_idx = m->d_pb_idx;
+    a.bar = m->d_bar;
+    a.spin_limit = 1ull << 24;  // polls of an L2 word (~0.1-0.5 us each): seconds at most
+    // test hooks (environment, read per call): a short poll bound, and block 0
+    // skipping its first barrier arrival so that the others' waits run out
+    if (const char *v = std::getenv("RBFD_TEST_BARRIER_POLLS")) a.spin_limit = std::strtoull(v, nullptr, 10);
+    if (const char *v = std::getenv("RBFD_TEST_SKIP_ARRIVAL")) a.test_skip_arrival = std::atoi(v) != 0;
+    a.phase_ns = m->prof.on ? m->d_phase_ns : nullptr;
+    a.st = m->d_st;
+    a.pairs = m->d_pairs;
+    const void *k = select_kernel(m->dim, m->opt.basis, m->opt.precision == RBFD_FP64 ? 0 : 1);
+    if (!k) fail(RBFD_EINVAL, "persistent greedy: unsupported dim/basis");
+    void *args[] = {&a};
+    RBFD_CUDA(cudaLaunchCooperativeKernel(k, dim3(ctas), dim3(kT), args, 0, m->stream));
+    m->stats.launches += 1;
+}
+
+}  // namespace rbfd

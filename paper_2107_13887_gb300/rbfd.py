@@ -40,6 +40,8 @@ class rbfd_options(ctypes.Structure):
         ("eps_absolute", ctypes.c_int),
         ("refine_iters", ctypes.c_int),
         ("profile", ctypes.c_int),
+        ("engine", ctypes.c_int),
+        ("grid_ctas", ctypes.c_int),
     ]
 
 
@@ -64,6 +66,10 @@ class rbfd_stats(ctypes.Structure):
         ("sweep_pairs_visited", ctypes.c_int64),
         ("vol_pairs_useful", ctypes.c_int64),
         ("vol_pairs_visited", ctypes.c_int64),
+        ("persist_ms", ctypes.c_double),
+        ("persist_launches", ctypes.c_int64),
+        ("persist_ctas", ctypes.c_int64),
+        ("persist_phase_ms", ctypes.c_double * 8),
     ]
 
 
@@ -84,6 +90,10 @@ SIGNATURES = [
     ("rbfd_deform", ctypes.c_int, [_vp, _i64, _vp, _vp, _d, _d, _vp]),
     ("rbfd_deform_f64", ctypes.c_int, [_vp, _i64, _vp, _vp, _d, _d, _vp]),
     ("rbfd_deform_noalloc", ctypes.c_int, [_vp, _i64, _vp, _vp, _d, _d, _vp]),
+    ("rbfd_greedy_batch", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int]),
+    ("rbfd_deform_batch", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_i64),
+                                         ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_d),
+                                         ctypes.POINTER(_d), ctypes.POINTER(_vp)]),
     ("rbfd_destroy", ctypes.c_int, [_vp]),
     ("rbfd_last_error", ctypes.c_char_p, []),
     ("rbfd_version", ctypes.c_char_p, []),
@@ -160,7 +170,7 @@ class Mesh:
     ``rbfd_destroy`` on ``close()`` / garbage collection."""
 
     def __init__(self, xyz_s, dS, R, eps, precision=MIXED, basis=2, first_point=0, nc_cap=0, stream=None,
-                 eps_absolute=False, refine_iters=3, profile=False):
+                 eps_absolute=False, refine_iters=3, profile=False, engine=0, grid_ctas=0):
         lib = load()
         self._lib = lib
         on_dev = _is_torch_cuda(xyz_s)
@@ -188,6 +198,8 @@ class Mesh:
         o.eps_absolute = 1 if eps_absolute else 0
         o.refine_iters = int(refine_iters)
         o.profile = 1 if profile else 0
+        o.engine = int(engine)
+        o.grid_ctas = int(grid_ctas)
         self.on_device = on_dev
         h = ctypes.c_void_p()
         _check(lib.rbfd_create(ctypes.byref(h), self.dim, self.n_s, _ptr(xyz_s), _ptr(dS), len(Rv),
@@ -234,7 +246,9 @@ class Mesh:
     def stats(self) -> dict:
         s = rbfd_stats()
         _check(self._lib.rbfd_get_stats(self.h, ctypes.byref(s)))
-        return {f: getattr(s, f) for f, _ in rbfd_stats._fields_}
+        out = {f: getattr(s, f) for f, _ in rbfd_stats._fields_}
+        out["persist_phase_ms"] = list(s.persist_phase_ms)
+        return out
 
     def deform(self, xyz_v, d_v, D: float, k: float, out=None):
         """Volume update (Eq. 19 / Eq. 23).  numpy in -> numpy out (host
@@ -264,3 +278,30 @@ class Mesh:
         _check(self._lib.rbfd_deform_noalloc(self.h, int(xyz_v.shape[0]), _ptr(xyz_v), _ptr(d_v), float(D), float(k),
                                              _ptr(out)))
         return out
+
+
+def greedy_batch(meshes, allow_not_converged: bool = True) -> int:
+    """``rbfd_greedy_batch``: the greedy selection of several meshes at once."""
+    lib = load()
+    arr = (_vp * len(meshes))(*[m.h.value for m in meshes])
+    rc = lib.rbfd_greedy_batch(arr, len(meshes))
+    if rc == ENOTCONV and allow_not_converged:
+        return rc
+    _check(rc)
+    return rc
+
+
+def deform_batch(meshes, xyz_v, d_v, D, k, out):
+    """``rbfd_deform_batch``: float32 arrays (numpy for host meshes, torch CUDA
+    tensors for device meshes), one per mesh; results written into ``out``."""
+    lib = load()
+    n = len(meshes)
+    nv = (_i64 * n)(*[int(x.shape[0]) for x in xyz_v])
+    px = (_vp * n)(*[_ptr(x).value for x in xyz_v])
+    pd = (_vp * n)(*[_ptr(x).value for x in d_v])
+    po = (_vp * n)(*[_ptr(x).value for x in out])
+    Dv = (_d * n)(*[float(x) for x in D])
+    kv = (_d * n)(*[float(x) for x in k])
+    arr = (_vp * n)(*[m.h.value for m in meshes])
+    _check(lib.rbfd_deform_batch(arr, n, nv, px, pd, Dv, kv, po))
+    return out

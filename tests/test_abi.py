@@ -68,9 +68,9 @@ def test_struct_layout_matches_header(tmp_path):
         '#include <stdio.h>\n#include <stddef.h>\n#include "rbfd.h"\n'
         "int main(void){\n"
         'printf("%zu %zu %zu %zu\\n", sizeof(rbfd_options), offsetof(rbfd_options, nc_cap),'
-        " offsetof(rbfd_options, stream), offsetof(rbfd_options, refine_iters));\n"
+        " offsetof(rbfd_options, stream), offsetof(rbfd_options, grid_ctas));\n"
         'printf("%zu %zu %zu\\n", sizeof(rbfd_stats), offsetof(rbfd_stats, confirm_resumes),'
-        " offsetof(rbfd_stats, vol_pairs_visited));\n"
+        " offsetof(rbfd_stats, persist_phase_ms));\n"
         "return 0;}\n"
     )
     exe = tmp_path / "layout"
@@ -81,7 +81,7 @@ def test_struct_layout_matches_header(tmp_path):
     assert so == ctypes.sizeof(rbfd.rbfd_options)
     assert onc == rbfd.rbfd_options.nc_cap.offset
     assert ost == rbfd.rbfd_options.stream.offset
-    assert ori == rbfd.rbfd_options.refine_iters.offset
+    assert ori == rbfd.rbfd_options.grid_ctas.offset
     assert ss == ctypes.sizeof(rbfd.rbfd_stats)
     assert ocr == rbfd.rbfd_stats.confirm_resumes.offset
-    assert ovp == rbfd.rbfd_stats.vol_pairs_visited.offset
+    assert ovp == rbfd.rbfd_stats.persist_phase_ms.offset

@@ -317,3 +317,69 @@ def test_repeat_greedy_is_deterministic():
     for x, y in zip(a, b):
         assert np.array_equal(x.idx, y.idx) and np.array_equal(x.alpha, y.alpha)
     assert np.array_equal(o1, o2)
+
+
+# ---------------------------------------------------------------- engines
+
+
+@pytest.mark.parametrize("name", ["airfoil_horns_2lvl", "wing_ridge_2lvl"])
+@pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
+def test_persistent_engine_matches_step_engine(name, precision):
+    c = CASES[name]
+    a = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, engine=0)
+    a.greedy()
+    b = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, engine=1)
+    b.greedy()
+    for x, y in zip(a.levels(), b.levels()):
+        assert np.array_equal(x.idx, y.idx)
+        assert np.abs(x.alpha - y.alpha).max() <= 1e-6 * max(np.abs(y.alpha).max(), 1e-300)
+    for ctas in (1, 7, 300):
+        m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, engine=0, grid_ctas=ctas)
+        m.greedy()
+        for x, y in zip(m.levels(), b.levels()):
+            assert np.array_equal(x.idx, y.idx)
+
+
+def test_barrier_wait_bound_returns_timeout(monkeypatch):
+    """A block that never arrives at the grid barrier (test hook) makes the
+    other blocks' bounded waits run out: the launch ends and rbfd_greedy
+    reports RBFD_ETIMEOUT; the next call on the same mesh works."""
+    c = CASES["airfoil_bump_333"]
+    m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, engine=0, grid_ctas=8)
+    monkeypatch.setenv("RBFD_TEST_BARRIER_POLLS", "2000")
+    monkeypatch.setenv("RBFD_TEST_SKIP_ARRIVAL", "1")
+    with pytest.raises(rbfd.RbfdError) as ei:
+        m.greedy(allow_not_converged=False)
+    assert ei.value.status == rbfd.ETIMEOUT
+    monkeypatch.delenv("RBFD_TEST_BARRIER_POLLS")
+    monkeypatch.delenv("RBFD_TEST_SKIP_ARRIVAL")
+    m.greedy()
+    ref = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, n_threads=NT)
+    check_sequences(ref, m.levels(), strict_full=True)
+
+
+# ---------------------------------------------------------------- batches
+
+
+@pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
+def test_batch_matches_single_meshes(precision):
+    names = ["airfoil_horns_2lvl", "wing_ridge_2lvl", "airfoil_pitch_2lvl", "airfoil_bump_333"]
+    cases = [CASES[n] for n in names]
+    single = []
+    for c in cases:
+        m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision)
+        m.greedy()
+        single.append((m.levels(), m.deform(c.xyz_v, c.d_v, c.D, c.k)))
+        m.close()
+    ms = [rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision) for c in cases]
+    rbfd.greedy_batch(ms)
+    outs = [np.empty((c.n_v, c.dim), np.float32) for c in cases]
+    rbfd.deform_batch(ms, [c.xyz_v for c in cases], [c.d_v for c in cases], [c.D for c in cases],
+                      [c.k for c in cases], outs)
+    for c, m, (lv1, out1), out2 in zip(cases, ms, single, outs):
+        S0 = float(np.sqrt((c.dS**2).sum(1)).max())
+        for x, y in zip(m.levels(), lv1):
+            assert np.array_equal(x.idx, y.idx)
+            assert np.abs(x.alpha - y.alpha).max() <= 1e-6 * max(np.abs(y.alpha).max(), 1e-300)
+        assert np.abs(out2.astype(np.float64) - out1).max() <= 1e-5 * S0 + np.abs(out1).max() * 2.0**-24
+        m.close()
