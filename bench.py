@@ -60,6 +60,8 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--engine", type=int, default=0, help="0: persistent greedy launch, 1: launches per step")
     p.add_argument("--ctas", type=int, default=0, help="blocks of the persistent launch (0: automatic)")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving leg (p50/p99 latency)")
+    p.add_argument("--serve-requests", type=int, default=200)
     return p.parse_args()
 
 
@@ -357,9 +359,73 @@ def run_ours(args):
                                 "sample": f"full greedy of both cases + volume update of a random {frac:.0%} "
                                           f"of the volume points (FP64 oracle, OpenMP)",
                                 "seconds": s_cpu}
+    if not args.no_serve:
+        line["serving"] = run_serving(n_requests=args.serve_requests)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------ serving leg
+
+def serving_meshes():
+    """Eight meshes drawn from the 2D and 3D workload families (20k to 1M
+    volume points), each with its base ice shape."""
+    from paper_2107_13887_gb300 import synth
+
+    return [
+        synth.make_config("naca0012_400s_40kv_bump", seed=0),
+        synth.airfoil_case(1000, 100, displacement="horns", seed=1, R=(1.0, 0.2), eps=1e-5, D=2.0, k=5.0),
+        synth.airfoil_case(2000, 150, displacement="horns", seed=2, R=(1.0, 0.2), eps=1e-5, D=2.0, k=5.0),
+        synth.make_config("naca0012_4000s_1mv_horns", seed=0),
+        synth.make_config("naca0012_4000s_1mv_pitch_heave", seed=0),
+        synth.airfoil_case(800, 25, displacement="bump", seed=3, R=(0.5,), eps=1e-4, D=2.0, k=0.0),
+        synth.wing_case(60, 20, 20, displacement="ridge", seed=4, R=(1.5, 0.4), eps=1e-3, D=1.0, k=4.0),
+        synth.wing_case(80, 30, 25, displacement="ridge", seed=5, R=(1.5, 0.4), eps=1e-3, D=1.0, k=4.0),
+    ]
+
+
+def run_serving(n_requests=200, rate=50.0, slots=4, seed=0):
+    """Requests with Poisson arrivals at `rate`/s, each one time step of an
+    ice-growth sequence (displacement scaled up linearly with the step) on one
+    of the meshes; submitted in real time to the request loop.  Returns the
+    latency percentiles (submit to done) and the throughput."""
+    from paper_2107_13887_gb300 import rbfd
+
+    meshes = serving_meshes()
+    srv = rbfd.Server(slots=slots)
+    ids = [srv.add_mesh(c.xyz_s, c.xyz_v, c.d_v, c.R, c.eps, c.D, c.k) for c in meshes]
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+    which = rng.integers(0, len(meshes), size=n_requests)
+    steps = np.zeros(len(meshes), dtype=int)
+    per_mesh = np.bincount(which, minlength=len(meshes))
+    # warm each mesh once (resident instances, code paths) outside the measured stream
+    for mid, c in zip(ids, meshes):
+        srv.wait(srv.submit(mid, c.dS * 0.5), timeout_s=600.0)
+    tickets = []
+    t0 = time.perf_counter()
+    for a, w in zip(arrivals, which):
+        now = time.perf_counter() - t0
+        if a > now:
+            time.sleep(a - now)
+        c = meshes[w]
+        growth = 0.2 + 0.8 * (steps[w] + 1) / per_mesh[w]
+        steps[w] += 1
+        tickets.append(srv.submit(ids[w], c.dS * growth))
+    for t in tickets:
+        srv.wait(t, timeout_s=600.0)
+    wall = time.perf_counter() - t0
+    tot = np.array([srv.times(t)[2] for t in tickets])
+    que = np.array([srv.times(t)[0] for t in tickets])
+    srv.close()
+    return {
+        "requests": n_requests, "arrival_rate_per_s": rate, "slots": slots, "meshes": len(meshes),
+        "volume_points": [int(c.n_v) for c in meshes],
+        "latency_ms_p50": float(np.percentile(tot, 50)), "latency_ms_p99": float(np.percentile(tot, 99)),
+        "queue_ms_p50": float(np.percentile(que, 50)), "queue_ms_p99": float(np.percentile(que, 99)),
+        "throughput_req_per_s": n_requests / wall, "wall_s": wall,
+    }
 
 
 # ------------------------------------------------------------ reference arm

@@ -168,6 +168,23 @@ int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st);
 int rbfd_deform(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v, double D, double k,
                 float *out);
 
+/*
+ * Time stepping on one surface (an ice shape growing step by step): the
+ * surface points and the volume mesh stay the same, the displacement changes.
+ *
+ * rbfd_set_displacement -- replace dS ([n_s][dim], caller order) of a mesh;
+ *   keeps the Morton order, point blocks and workspace; the previous greedy
+ *   results are dropped (run rbfd_greedy again).
+ * rbfd_set_volume -- register a volume mesh ([n_v][dim] float coordinates,
+ *   [n_v] wall distances) once; it is packed and Morton-sorted on the device
+ *   and kept until the next call or rbfd_destroy.
+ * rbfd_deform_volume -- rbfd_deform on the registered volume: out [n_v][dim].
+ * Pointer kinds follow inputs_on_device.  Errors as for rbfd_deform.
+ */
+int rbfd_set_displacement(rbfd_mesh *m, const double *dS);
+int rbfd_set_volume(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v);
+int rbfd_deform_volume(rbfd_mesh *m, double D, double k, float *out);
+
 /* Same as rbfd_deform with double coordinates, distances and output. */
 int rbfd_deform_f64(rbfd_mesh *m, int64_t n_v, const double *xyz_v, const double *d_v, double D, double k,
                     double *out);
@@ -216,6 +233,70 @@ int rbfd_greedy_batch(rbfd_mesh **meshes, int n);
  */
 int rbfd_deform_batch(rbfd_mesh **meshes, int n, const int64_t *n_v, const float *const *xyz_v,
                       const float *const *d_v, const double *D, const double *k, float *const *out);
+
+/* ------------------------------------------------------------- serving ---
+ *
+ * A request loop for deformation requests as icing time steps produce them:
+ * each request is a new surface displacement on a registered mesh (2D or 3D,
+ * any size).  Up to `slots` requests run at once, each on its own worker
+ * thread and CUDA stream, so their GPU work overlaps; requests arriving
+ * meanwhile wait in a FIFO queue and start as soon as a slot is free and the
+ * device memory their mesh needs fits the budget (admission by footprint).
+ * Each mesh keeps resident instances (sorted surface and volume, workspace)
+ * on the device between time steps.  A request's result does not depend on
+ * which other requests run beside it (up to the rounding of the growth
+ * reductions, far below the stated tolerances).
+ */
+typedef struct rbfd_server rbfd_server;
+
+typedef struct rbfd_server_options {
+    int slots;                 /* requests in flight at most (default 4) */
+    int precision;             /* rbfd_precision of every request (default RBFD_MIXED) */
+    int64_t mem_budget_bytes;  /* device memory the resident instances may hold (0 = 80% of free memory) */
+    int64_t max_queue;         /* queued requests at most; rbfd_submit returns RBFD_EBUSY beyond (default 4096) */
+} rbfd_server_options;
+
+typedef struct rbfd_request {
+    const double *dS;  /* [n_s][dim] host displacement of the registered surface; copied by rbfd_submit */
+    float *out;        /* [n_v][dim] host buffer; written when the request completes, untouched before */
+} rbfd_request;
+
+typedef enum rbfd_request_state {
+    RBFD_REQ_QUEUED = 0,
+    RBFD_REQ_RUNNING = 1,
+    RBFD_REQ_DONE = 2,   /* out holds the result (status RBFD_OK or RBFD_ENOTCONV) */
+    RBFD_REQ_FAILED = 3  /* rbfd_poll returns the error status */
+} rbfd_request_state;
+
+void rbfd_server_options_default(rbfd_server_options *opt);
+
+/* Start the worker threads on the current CUDA device. */
+int rbfd_server_create(rbfd_server **out, const rbfd_server_options *opt);
+
+/*
+ * Register a mesh: surface points xyz_s [n_s][dim] (double), volume points
+ * xyz_v [n_v][dim] with wall distances d_v [n_v] (float), the greedy levels
+ * (R [n_levels], eps) and the support distance rule (D, k) of rbfd_deform.
+ * Host pointers; the server copies them.  *mesh_id names the mesh in rbfd_submit.
+ */
+int rbfd_server_add_mesh(rbfd_server *s, int dim, int64_t n_s, const double *xyz_s, int64_t n_v, const float *xyz_v,
+                         const float *d_v, int n_levels, const double *R, double eps, double D, double k,
+                         int *mesh_id);
+
+/* Queue one request; *ticket identifies it.  RBFD_EBUSY if the queue is full. */
+int rbfd_submit(rbfd_server *s, int mesh_id, const rbfd_request *req, uint64_t *ticket);
+
+/* Non-blocking: *state = rbfd_request_state; returns the request's status once done. */
+int rbfd_poll(rbfd_server *s, uint64_t ticket, int *state);
+
+/* Block until the request is done or timeout_s passes (<= 0: no limit; RBFD_ETIMEOUT). */
+int rbfd_wait(rbfd_server *s, uint64_t ticket, double timeout_s, int *state);
+
+/* Host-clock times of a finished request: queued, running, and submit-to-done. */
+int rbfd_request_times(rbfd_server *s, uint64_t ticket, double *queue_ms, double *run_ms, double *total_ms);
+
+/* Finish the running requests, drop the queued ones, free everything. */
+int rbfd_server_destroy(rbfd_server *s);
 
 /* Release every device and host resource of the mesh.  NULL is allowed. */
 int rbfd_destroy(rbfd_mesh *m);

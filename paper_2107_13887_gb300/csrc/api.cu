@@ -221,7 +221,7 @@ void mesh_free(rbfd_mesh *m) {
                     m->d_nb_cnt, m->d_nb_list, m->d_part, m->d_pb_done, m->d_pb_key, m->d_pb_idx, m->d_pairs,
                     m->d_st, m->d_vin, m->d_vpos, m->d_vorig, m->d_vflag, m->d_vscan, m->d_vlist, m->d_vkeys,
                     m->d_vacc, m->d_vio, m->d_misc, m->d_bbox, m->d_bar, m->d_pred, m->d_pgpart,
-                    m->d_kt_done, m->d_phase_ns};
+                    m->d_kt_done, m->d_phase_ns, m->d_vreg, m->d_vreg_orig};
     for (void *p : ptrs) dfree(p);
     m->sort.release();
     m->prof.release();
@@ -452,6 +452,42 @@ static int deform_common(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const voi
             (!is_device_ptr(xyz_v) || !is_device_ptr(d_v) || !is_device_ptr(out)))
             rbfd::fail(RBFD_EINVAL, "rbfd_deform: inputs_on_device set but arrays are not device memory");
         rbfd::deform_run(m, n_v, xyz_v, d_v, f64, D, k, out);
+    });
+}
+
+int rbfd_set_displacement(rbfd_mesh *m, const double *dS) {
+    return guarded([&] {
+        if (!m || !dS) rbfd::fail(RBFD_EINVAL, "rbfd_set_displacement: NULL argument");
+        RBFD_CUDA(cudaSetDevice(m->device));
+        if (m->opt.inputs_on_device && !is_device_ptr(dS))
+            rbfd::fail(RBFD_EINVAL, "rbfd_set_displacement: inputs_on_device set but dS is not device memory");
+        rbfd::mesh_set_displacement(m, dS);
+    });
+}
+
+int rbfd_set_volume(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v) {
+    return guarded([&] {
+        if (!m) rbfd::fail(RBFD_EINVAL, "rbfd_set_volume: NULL mesh");
+        if (n_v < 0 || n_v > ((int64_t)1 << 31) - 1) rbfd::fail(RBFD_EINVAL, "rbfd_set_volume: n_v out of range");
+        if (n_v > 0 && (!xyz_v || !d_v)) rbfd::fail(RBFD_EINVAL, "rbfd_set_volume: NULL array");
+        RBFD_CUDA(cudaSetDevice(m->device));
+        if (m->opt.inputs_on_device && n_v > 0 && (!is_device_ptr(xyz_v) || !is_device_ptr(d_v)))
+            rbfd::fail(RBFD_EINVAL, "rbfd_set_volume: inputs_on_device set but arrays are not device memory");
+        rbfd::volume_register(m, n_v, xyz_v, d_v);
+    });
+}
+
+int rbfd_deform_volume(rbfd_mesh *m, double D, double k, float *out) {
+    return guarded([&] {
+        if (!m) rbfd::fail(RBFD_EINVAL, "rbfd_deform_volume: NULL mesh");
+        if (!(D >= 0.0) || !(k >= 0.0) || !std::isfinite(D) || !std::isfinite(k) || (D == 0.0 && k == 0.0))
+            rbfd::fail(RBFD_EINVAL, "rbfd_deform_volume: D and k must be finite, >= 0 and not both 0");
+        if (!m->greedy_done) rbfd::fail(RBFD_ESTATE, "rbfd_deform_volume: run rbfd_greedy first");
+        if (m->vreg_n > 0 && !out) rbfd::fail(RBFD_EINVAL, "rbfd_deform_volume: NULL out");
+        RBFD_CUDA(cudaSetDevice(m->device));
+        if (m->opt.inputs_on_device && m->vreg_n > 0 && !is_device_ptr(out))
+            rbfd::fail(RBFD_EINVAL, "rbfd_deform_volume: inputs_on_device set but out is not device memory");
+        rbfd::deform_registered(m, D, k, out);
     });
 }
 

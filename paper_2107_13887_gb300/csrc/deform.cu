@@ -92,6 +92,34 @@ __global__ void k_bbox_idx(const double4 *__restrict__ p, const uint32_t *__rest
     }
 }
 
+__global__ void k_bbox_partial_v(const double4 *__restrict__ p, int64_t n, double *__restrict__ part) {
+    __shared__ double s[6][32];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double4 q = p[i];
+        lo[0] = fmin(lo[0], q.x); lo[1] = fmin(lo[1], q.y); lo[2] = fmin(lo[2], q.z);
+        hi[0] = fmax(hi[0], q.x); hi[1] = fmax(hi[1], q.y); hi[2] = fmax(hi[2], q.z);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmax(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) {
+            s[k][w] = lo[k];
+            s[3 + k][w] = hi[k];
+        }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double v = s[threadIdx.x][0];
+        for (int j = 1; j < (int)(blockDim.x >> 5); ++j)
+            v = threadIdx.x < 3 ? fmin(v, s[threadIdx.x][j]) : fmax(v, s[threadIdx.x][j]);
+        part[blockIdx.x * 6 + threadIdx.x] = v;
+    }
+}
+
 __global__ void k_bbox_reduce(const double *__restrict__ part, int nb, double *__restrict__ out) {
     if (threadIdx.x >= 6) return;
     double v = part[threadIdx.x];
@@ -358,6 +386,57 @@ void reserve_volume(rbfd_mesh *m, size_t n) {
     m->vol_cap = n;
 }
 
+// Steps (3) and (4) of the volume update for nV Morton-sorted points vpos
+// (caller indices vorig): per level, compaction to d < D_l and the fused
+// evaluation into the accumulator; then the scatter into dout (caller order).
+void deform_levels(rbfd_mesh *m, int64_t nV, const double4 *vpos, const uint32_t *vorig, const double *Dl, int L,
+                   void *dout, bool f64) {
+    cudaStream_t st = m->stream;
+    const int dim = m->dim;
+    RBFD_CUDA(cudaMemsetAsync(m->d_vacc, 0, sizeof(double4) * nV, st));
+    // (3) per level: d < D_l, then the fused evaluation
+    const int mode = m->opt.precision == RBFD_FP64 ? 0 : 1;
+    for (int l = 0; l < L; ++l) {
+        const Level &Lv = m->levels[l];
+        if (Lv.nc == 0 || !(Dl[l] > 0.0)) continue;
+        k_flag_below<<<cdiv(nV, 256), 256, 0, st>>>(vpos, nullptr, nV, Dl[l], m->d_vflag);
+        exclusive_scan_u32(m->d_vflag, m->d_vscan, (size_t)nV, &m->d_misc[5], m->sort, st);
+        k_compact<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vflag, m->d_vscan, nV, m->d_vlist);
+        uint32_t nl = 0;
+        RBFD_CUDA(cudaMemcpyAsync(&nl, &m->d_misc[5], sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        RBFD_CUDA(cudaStreamSynchronize(st));
+        if (nl == 0) continue;
+        m->stats.deform_points += nl;
+        VolArgs a{};
+        a.n_list = nl;
+        a.list = m->d_vlist;
+        a.vpos = vpos;
+        a.vacc = m->d_vacc;
+        a.cx = Lv.d_cx;
+        a.alpha = Lv.d_alpha;
+        a.cell_start = Lv.d_cell_start;
+        a.cell_ctrl = Lv.d_cell_ctrl;
+        a.g0 = Lv.g0;
+        a.h = Lv.h;
+        a.gd = Lv.gdim;
+        a.R = Lv.R;
+        a.Dl = Dl[l];
+        double inv = 1.0 / Lv.R;
+        a.invR_hi = (float)inv;
+        a.invR_lo = (float)(inv - (double)a.invR_hi);
+        a.pairs = m->d_pairs + 2;
+        m->stats.launches += 3;  // flags, compaction (+ scan counted in the scan)
+        cudaEvent_t e0 = m->prof.begin(st);
+        launch_vol(dim, m->opt.basis, mode, cdiv(nl, kThreads), a, st);
+        RBFD_CUDA(cudaGetLastError());
+        m->prof.end(kProfVol, e0, st, 1);
+        m->stats.launches += 1;
+    }
+    // (4) back to the caller's order
+    k_scatter_out<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vacc, vorig, nV, dim, f64 ? 1 : 0, dout);
+    RBFD_CUDA(cudaGetLastError());
+}
+
 }  // namespace
 
 void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64, double D, double k,
@@ -431,52 +510,91 @@ void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, b
         k_gather_u32<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vlist, m->d_vorig, nV, m->d_vflag);
         RBFD_CUDA(cudaMemcpyAsync(m->d_vorig, m->d_vflag, sizeof(uint32_t) * nV, cudaMemcpyDeviceToDevice, st));
         vpos = vin;
-        RBFD_CUDA(cudaMemsetAsync(m->d_vacc, 0, sizeof(double4) * nV, st));
-        // (3) per level: d < D_l, then the fused evaluation
-        const int mode = m->opt.precision == RBFD_FP64 ? 0 : 1;
-        for (int l = 0; l < L; ++l) {
-            const Level &Lv = m->levels[l];
-            if (Lv.nc == 0 || !(Dl[l] > 0.0)) continue;
-            k_flag_below<<<cdiv(nV, 256), 256, 0, st>>>(vpos, nullptr, nV, Dl[l], m->d_vflag);
-            exclusive_scan_u32(m->d_vflag, m->d_vscan, (size_t)nV, &m->d_misc[5], m->sort, st);
-            k_compact<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vflag, m->d_vscan, nV, m->d_vlist);
-            uint32_t nl = 0;
-            RBFD_CUDA(cudaMemcpyAsync(&nl, &m->d_misc[5], sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-            RBFD_CUDA(cudaStreamSynchronize(st));
-            if (nl == 0) continue;
-            m->stats.deform_points += nl;
-            VolArgs a{};
-            a.n_list = nl;
-            a.list = m->d_vlist;
-            a.vpos = vpos;
-            a.vacc = m->d_vacc;
-            a.cx = Lv.d_cx;
-            a.alpha = Lv.d_alpha;
-            a.cell_start = Lv.d_cell_start;
-            a.cell_ctrl = Lv.d_cell_ctrl;
-            a.g0 = Lv.g0;
-            a.h = Lv.h;
-            a.gd = Lv.gdim;
-            a.R = Lv.R;
-            a.Dl = Dl[l];
-            double inv = 1.0 / Lv.R;
-            a.invR_hi = (float)inv;
-            a.invR_lo = (float)(inv - (double)a.invR_hi);
-            a.pairs = m->d_pairs + 2;
-            m->stats.launches += 3;  // flags, compaction (+ scan counted in the scan)
-            cudaEvent_t e0 = m->prof.begin(st);
-            launch_vol(dim, m->opt.basis, mode, cdiv(nl, kThreads), a, st);
-            RBFD_CUDA(cudaGetLastError());
-            m->prof.end(kProfVol, e0, st, 1);
-            m->stats.launches += 1;
-        }
-        // (4) back to the caller's order
-        k_scatter_out<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vacc, m->d_vorig, nV, dim, f64 ? 1 : 0, dout);
-        RBFD_CUDA(cudaGetLastError());
+        deform_levels(m, nV, vpos, m->d_vorig, Dl.data(), L, dout, f64);
         m->stats.launches += 9;  // pack, flags, compaction, bbox x2, gathers x3, scatter
     }
     if (host && n_v > 0)
         RBFD_CUDA(cudaMemcpyAsync(out, dout, (size_t)n_v * dim * es, cudaMemcpyDeviceToHost, st));
+    RBFD_CUDA(cudaEventRecord(m->ev1, st));
+    RBFD_CUDA(cudaEventSynchronize(m->ev1));
+    float ms = 0;
+    RBFD_CUDA(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
+    m->stats.deform_ms = ms;
+    m->prof.flush();
+}
+
+// Register a volume mesh for repeated updates (rbfd_set_volume): its points
+// are packed and Morton-sorted once; deform_registered then runs only the
+// per-level compaction, evaluation and scatter for each new displacement.
+void volume_register(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v) {
+    cudaStream_t st = m->stream;
+    const int dim = m->dim;
+    dfree(m->d_vreg);
+    dfree(m->d_vreg_orig);
+    m->d_vreg = nullptr;
+    m->d_vreg_orig = nullptr;
+    m->vreg_n = 0;
+    if (n_v == 0) return;
+    reserve_volume(m, (size_t)n_v);
+    const void *dx = xyz_v, *dd = d_v;
+    float *stage = nullptr;
+    if (!m->opt.inputs_on_device) {
+        stage = dalloc<float>((size_t)n_v * (dim + 1), "volume staging");
+        RBFD_CUDA(cudaMemcpyAsync(stage, xyz_v, sizeof(float) * n_v * dim, cudaMemcpyHostToDevice, st));
+        RBFD_CUDA(cudaMemcpyAsync(stage + (size_t)n_v * dim, d_v, sizeof(float) * n_v, cudaMemcpyHostToDevice, st));
+        dx = stage;
+        dd = stage + (size_t)n_v * dim;
+    }
+    double4 *vin = reinterpret_cast<double4 *>(m->d_vin);
+    k_vol_pack<<<cdiv(n_v, 256), 256, 0, st>>>(dx, dd, n_v, dim, 0, vin);
+    const int nbb = std::min<int>(cdiv(n_v, 256), 256);
+    k_bbox_partial_v<<<nbb, 256, 0, st>>>(vin, n_v, m->d_red);
+    k_bbox_reduce<<<1, 32, 0, st>>>(m->d_red, nbb, m->d_bbox);
+    double bb[6];
+    RBFD_CUDA(cudaMemcpyAsync(bb, m->d_bbox, sizeof(bb), cudaMemcpyDeviceToHost, st));
+    RBFD_CUDA(cudaStreamSynchronize(st));
+    m->d_vreg = dalloc<double4>((size_t)n_v, "registered volume");
+    m->d_vreg_orig = dalloc<uint32_t>((size_t)n_v, "registered volume order");
+    morton_keys_f64(vin, n_v, dim, make_double3(bb[0], bb[1], bb[2]), make_double3(bb[3], bb[4], bb[5]), m->d_vkeys,
+                    m->d_vreg_orig, st);
+    radix_sort_pairs(m->d_vkeys, m->d_vreg_orig, (size_t)n_v, dim == 2 ? 32 : 30, m->sort, st);
+    k_gather_vol<<<cdiv(n_v, 256), 256, 0, st>>>(vin, m->d_vreg_orig, n_v, m->d_vreg);
+    RBFD_CUDA(cudaGetLastError());
+    RBFD_CUDA(cudaStreamSynchronize(st));
+    dfree(stage);
+    m->vreg_n = n_v;
+    m->stats.launches += 5;
+}
+
+void deform_registered(rbfd_mesh *m, double D, double k, float *out) {
+    cudaStream_t st = m->stream;
+    const int dim = m->dim;
+    const int64_t n_v = m->vreg_n;
+    RBFD_CUDA(cudaEventRecord(m->ev0, st));
+    const int L = (int)m->levels.size();
+    std::vector<double> Dl(L, 0.0);
+    for (int l = 0; l < L; ++l) {
+        double v = (k > 0.0) ? k * m->levels[l].smax : D;
+        if (k > 0.0 && D > 0.0 && v > D) v = D;
+        Dl[l] = (m->levels[l].nc > 0) ? v : 0.0;
+    }
+    float *dout = out;
+    if (!m->opt.inputs_on_device && n_v > 0) {
+        const size_t need = sizeof(float) * (size_t)n_v * dim;
+        if (need > m->vio_bytes) {
+            dfree(m->d_vio);
+            m->d_vio = nullptr;
+            m->vio_bytes = 0;
+            m->d_vio = dmalloc(need, "volume output staging");
+            m->vio_bytes = need;
+        }
+        dout = static_cast<float *>(m->d_vio);
+    }
+    if (n_v > 0) {
+        RBFD_CUDA(cudaMemsetAsync(dout, 0, sizeof(float) * n_v * dim, st));
+        deform_levels(m, n_v, m->d_vreg, m->d_vreg_orig, Dl.data(), L, dout, false);
+        if (dout != out) RBFD_CUDA(cudaMemcpyAsync(out, dout, sizeof(float) * n_v * dim, cudaMemcpyDeviceToHost, st));
+    }
     RBFD_CUDA(cudaEventRecord(m->ev1, st));
     RBFD_CUDA(cudaEventSynchronize(m->ev1));
     float ms = 0;

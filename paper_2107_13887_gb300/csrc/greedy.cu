@@ -946,6 +946,45 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     m->stats.launches += 1;
 }
 
+namespace {
+__global__ void k_gather_disp(const double *__restrict__ dS, const uint32_t *__restrict__ perm, int64_t n, int dim,
+                              double4 *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *q = dS + (int64_t)perm[i] * dim;
+    out[i] = make_double4(q[0], q[1], dim == 3 ? q[2] : 0.0, 0.0);
+}
+}  // namespace
+
+// New surface displacement on a prepared mesh: the Morton order, point blocks
+// and workspace are kept; the greedy results of the previous displacement are
+// dropped.
+void mesh_set_displacement(rbfd_mesh *m, const double *dS) {
+    cudaStream_t st = m->stream;
+    const int64_t n = m->n_s;
+    const double *dd = dS;
+    double *tmp = nullptr;
+    if (!m->opt.inputs_on_device) {
+        tmp = dalloc<double>((size_t)n * m->dim, "surface displacements");
+        RBFD_CUDA(cudaMemcpyAsync(tmp, dS, sizeof(double) * n * m->dim, cudaMemcpyHostToDevice, st));
+        dd = tmp;
+    }
+    k_gather_disp<<<cdiv(n, 256), 256, 0, st>>>(dd, m->d_perm, n, m->dim, m->d_dS);
+    RBFD_CUDA(cudaGetLastError());
+    m->stats.launches += 1;
+    m->S0 = std::sqrt(maxnorm(m, m->d_dS, nullptr));  // synchronises the stream
+    m->stats.launches += 1;
+    dfree(tmp);
+    for (auto &L : m->levels) {
+        dfree(L.d_cx);
+        dfree(L.d_alpha);
+        dfree(L.d_cell_start);
+        dfree(L.d_cell_ctrl);
+    }
+    m->levels.clear();
+    m->greedy_done = false;
+}
+
 void greedy_run(rbfd_mesh *m) {
     cudaStream_t st = m->stream;
     for (auto &L : m->levels) {

@@ -181,6 +181,10 @@ struct rbfd_mesh {
     double4 *d_vacc = nullptr;     // accumulated displacement per sorted point
     void *d_vio = nullptr;         // staging for host inputs/outputs
     size_t vio_bytes = 0;
+    // registered volume (rbfd_set_volume): Morton-sorted once, deformed per displacement
+    int64_t vreg_n = 0;
+    double4 *d_vreg = nullptr;     // sorted points (x, y, z, d)
+    uint32_t *d_vreg_orig = nullptr;
     uint32_t *d_misc = nullptr;    // small counters
     double *d_bbox = nullptr;      // 8 doubles
 };
@@ -193,5 +197,8 @@ void greedy_run(rbfd_mesh *m);
 void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64, double D, double k,
                 void *out);
 void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS);
+void mesh_set_displacement(rbfd_mesh *m, const double *dS);
+void volume_register(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v);
+void deform_registered(rbfd_mesh *m, double D, double k, float *out);
 void mesh_free(rbfd_mesh *m);
 }  // namespace rbfd

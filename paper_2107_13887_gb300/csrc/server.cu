@@ -1,0 +1,374 @@
+// server.cu -- continuous-batching request loop for deformation requests
+// (rbfd_server_* / rbfd_submit / rbfd_poll in include/rbfd.h).
+//
+// A request is one time step of an icing computation: a new surface
+// displacement dS on a registered mesh.  The server runs up to `slots`
+// requests at a time, each on a worker thread with its own CUDA stream, so
+// the greedy launches of different requests overlap on the GPU (their
+// persistent grids are sized to be resident together).  Requests that arrive
+// while others run wait in a FIFO queue and are admitted as soon as a slot is
+// free and their device-memory footprint fits the budget; a request whose
+// mesh is already busy can still start on a second resident instance of that
+// mesh if memory allows.  Each registered mesh keeps its resident instances
+// (Morton-ordered surface, point blocks, workspace, sorted volume) on the
+// device between time steps: a new step only uploads dS, runs the greedy
+// selection (Section 3) and the volume update (Section 4).
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <functional>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+struct MeshSpec {
+    int dim = 2;
+    int64_t n_s = 0, n_v = 0;
+    std::vector<double> xyz_s, R;
+    std::vector<float> xyz_v, d_v;
+    double eps = 0, D = 0, k = 0;
+    size_t footprint = 0;
+    std::vector<rbfd_mesh *> idle;  // resident instances not running a request
+    int instances = 0;
+};
+
+struct Request {
+    int mesh = -1;
+    std::vector<double> dS;
+    float *out = nullptr;
+    int state = RBFD_REQ_QUEUED;
+    int status = RBFD_OK;
+    std::string msg;
+    clk::time_point t_submit, t_start, t_done;
+};
+
+}  // namespace
+
+struct rbfd_server {
+    rbfd_server_options opt{};
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::vector<std::unique_ptr<MeshSpec>> meshes;
+    std::map<uint64_t, Request> reqs;
+    std::deque<uint64_t> queue;
+    uint64_t next_ticket = 1;
+    size_t used_bytes = 0;
+    int running = 0;
+    bool shutdown = false;
+    std::vector<std::thread> workers;
+};
+
+namespace rbfd {
+
+// Device bytes one resident instance of a mesh holds (greedy workspace, the
+// inverse factor, block lists, sorted surface and volume, deform buffers).
+size_t mesh_footprint(int dim, int64_t n_s, int64_t n_v, int64_t cap) {
+    (void)dim;
+    const int64_t n_pb = (n_s + kPB - 1) / kPB;
+    const int64_t nch = std::max<int64_t>(1, (608 + n_pb - 1) / n_pb);
+    size_t b = 0;
+    b += 8ull * cap * cap;                          // G
+    b += 4ull * n_pb * cap;                         // block lists
+    b += (size_t)n_s * (4 * 32 + 2 * 16 + 16);      // sorted surface, targets, error, df coords, perms
+    b += (size_t)nch * n_s * 32;                    // sweep partials
+    b += (size_t)cap * (6 * 32 + 8 * 8) + 8ull * (cap / 128 + 2) * cap + 32ull * (cap / 256 + 2) * cap;
+    b += (size_t)n_v * (32 * 3 + 4 * 6);            // registered + working volume buffers
+    return b + (64ull << 20);                       // small buffers and pool rounding
+}
+
+// Run one admitted request.  inst is an idle resident instance of its mesh,
+// or nullptr when a new instance (already counted in used_bytes) is to be made.
+static void run_request(rbfd_server *S, uint64_t ticket, rbfd_mesh *inst) {
+    int mesh_id;
+    std::vector<double> dS;
+    float *out;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        Request &r = S->reqs[ticket];
+        mesh_id = r.mesh;
+        dS.swap(r.dS);
+        out = r.out;
+    }
+    MeshSpec &M = *S->meshes[mesh_id];
+    const bool fresh = inst == nullptr;
+    int status = RBFD_OK;
+    std::string msg;
+    try {
+        RBFD_CUDA(cudaSetDevice(S->device));
+        if (fresh) {
+            rbfd_options o;
+            rbfd_options_default(&o);
+            o.precision = S->opt.precision;
+            int rc = rbfd_create(&inst, M.dim, M.n_s, M.xyz_s.data(), dS.data(), (int)M.R.size(), M.R.data(), M.eps,
+                                 &o);
+            if (rc != RBFD_OK) fail(rc, std::string("server: creating a mesh instance: ") + rbfd_last_error());
+            volume_register(inst, M.n_v, M.xyz_v.data(), M.d_v.data());
+        } else {
+            mesh_set_displacement(inst, dS.data());
+        }
+        // the persistent grids of all slots must be resident together
+        inst->batch_ctas_cap = std::max(1, persist_max_ctas(inst) / std::max(1, S->opt.slots));
+        try {
+            greedy_run(inst);
+        } catch (const Error &e) {
+            if (e.status != RBFD_ENOTCONV) throw;
+            status = RBFD_ENOTCONV;  // results valid
+            msg = e.msg;
+        }
+        deform_registered(inst, M.D, M.k, out);
+    } catch (const Error &e) {
+        status = e.status;
+        msg = e.msg;
+    } catch (...) {
+        status = RBFD_ECUDA;
+        msg = "server: unexpected internal error";
+    }
+    const bool ok = status == RBFD_OK || status == RBFD_ENOTCONV;
+    if (!ok && inst) {  // a failed instance is not reused
+        rbfd_destroy(inst);
+        inst = nullptr;
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    Request &r = S->reqs[ticket];
+    r.status = status;
+    r.msg = msg;
+    r.state = ok ? RBFD_REQ_DONE : RBFD_REQ_FAILED;
+    r.t_done = clk::now();
+    if (inst) {
+        M.idle.push_back(inst);
+    } else {  // the instance is gone (or was never made): release its share
+        M.instances--;
+        S->used_bytes -= M.footprint;
+    }
+    S->running--;
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+}
+
+// First queued request that can start now: its mesh has an idle instance, or a
+// new instance fits the memory budget.  Called with the lock held.
+static bool pick_request(rbfd_server *S, uint64_t &ticket, rbfd_mesh *&inst) {
+    for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
+        Request &r = S->reqs[*it];
+        MeshSpec &M = *S->meshes[r.mesh];
+        bool ok = false;
+        if (!M.idle.empty()) {
+            inst = M.idle.back();
+            M.idle.pop_back();
+            ok = true;
+        } else if (S->used_bytes + M.footprint <= (size_t)S->opt.mem_budget_bytes) {
+            inst = nullptr;  // reserve for a new instance
+            S->used_bytes += M.footprint;
+            M.instances++;
+            ok = true;
+        }
+        if (ok) {
+            ticket = *it;
+            S->queue.erase(it);
+            r.state = RBFD_REQ_RUNNING;
+            r.t_start = clk::now();
+            S->running++;
+            return true;
+        }
+    }
+    return false;
+}
+
+static void worker(rbfd_server *S) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        uint64_t ticket = 0;
+        rbfd_mesh *inst = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait(lk, [&] { return S->shutdown || (!S->queue.empty() && pick_request(S, ticket, inst)); });
+            if (ticket == 0) {
+                if (S->shutdown) return;
+                continue;
+            }
+        }
+        run_request(S, ticket, inst);
+    }
+}
+
+}  // namespace rbfd
+
+namespace {
+
+int guarded_srv(const std::function<void()> &f) {
+    try {
+        f();
+        rbfd::set_last_error("");
+        return RBFD_OK;
+    } catch (const rbfd::Error &e) {
+        rbfd::set_last_error(e.msg);
+        return e.status;
+    } catch (...) {
+        rbfd::set_last_error("server: unexpected internal error");
+        return RBFD_ECUDA;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void rbfd_server_options_default(rbfd_server_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->slots = 4;
+    o->mem_budget_bytes = 0;
+    o->precision = RBFD_MIXED;
+    o->max_queue = 4096;
+}
+
+int rbfd_server_create(rbfd_server **out, const rbfd_server_options *opt) {
+    if (out) *out = nullptr;
+    return guarded_srv([&] {
+        if (!out) rbfd::fail(RBFD_EINVAL, "rbfd_server_create: out is NULL");
+        rbfd_server_options o;
+        rbfd_server_options_default(&o);
+        if (opt) o = *opt;
+        if (o.slots < 1 || o.slots > 64) rbfd::fail(RBFD_EINVAL, "rbfd_server_create: slots must be in [1, 64]");
+        if (o.max_queue < 1) rbfd::fail(RBFD_EINVAL, "rbfd_server_create: max_queue must be >= 1");
+        auto *S = new rbfd_server();
+        S->opt = o;
+        RBFD_CUDA(cudaGetDevice(&S->device));
+        if (S->opt.mem_budget_bytes <= 0) {
+            size_t fr = 0, tot = 0;
+            RBFD_CUDA(cudaMemGetInfo(&fr, &tot));
+            S->opt.mem_budget_bytes = (int64_t)(0.8 * (double)fr);
+        }
+        for (int i = 0; i < o.slots; ++i) S->workers.emplace_back(rbfd::worker, S);
+        *out = S;
+    });
+}
+
+int rbfd_server_add_mesh(rbfd_server *S, int dim, int64_t n_s, const double *xyz_s, int64_t n_v, const float *xyz_v,
+                         const float *d_v, int n_levels, const double *R, double eps, double D, double k,
+                         int *mesh_id) {
+    return guarded_srv([&] {
+        if (!S || !mesh_id) rbfd::fail(RBFD_EINVAL, "rbfd_server_add_mesh: NULL argument");
+        if (dim != 2 && dim != 3) rbfd::fail(RBFD_EINVAL, "rbfd_server_add_mesh: dim must be 2 or 3");
+        if (n_s < 1 || !xyz_s || n_levels < 1 || n_levels > 64 || !R || !(eps > 0.0 && eps < 1.0))
+            rbfd::fail(RBFD_EINVAL, "rbfd_server_add_mesh: bad surface or level arguments");
+        if (n_v < 0 || (n_v > 0 && (!xyz_v || !d_v))) rbfd::fail(RBFD_EINVAL, "rbfd_server_add_mesh: bad volume");
+        if (!(D >= 0.0) || !(k >= 0.0) || (D == 0.0 && k == 0.0))
+            rbfd::fail(RBFD_EINVAL, "rbfd_server_add_mesh: D and k must be >= 0 and not both 0");
+        for (int l = 0; l < n_levels; ++l)
+            if (!(R[l] > 0.0)) rbfd::fail(RBFD_EINVAL, "rbfd_server_add_mesh: every R must be > 0");
+        auto M = std::make_unique<MeshSpec>();
+        M->dim = dim;
+        M->n_s = n_s;
+        M->n_v = n_v;
+        M->xyz_s.assign(xyz_s, xyz_s + n_s * dim);
+        M->R.assign(R, R + n_levels);
+        M->xyz_v.assign(xyz_v, xyz_v + n_v * dim);
+        M->d_v.assign(d_v, d_v + n_v);
+        M->eps = eps;
+        M->D = D;
+        M->k = k;
+        M->footprint = rbfd::mesh_footprint(dim, n_s, n_v, std::min<int64_t>(n_s, 16384));
+        if (M->footprint > (size_t)S->opt.mem_budget_bytes)
+            rbfd::fail(RBFD_ENOMEM, "rbfd_server_add_mesh: one instance of this mesh exceeds the memory budget");
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->meshes.push_back(std::move(M));
+        *mesh_id = (int)S->meshes.size() - 1;
+    });
+}
+
+int rbfd_submit(rbfd_server *S, int mesh_id, const rbfd_request *req, uint64_t *ticket) {
+    return guarded_srv([&] {
+        if (!S || !req || !ticket || !req->dS || !req->out) rbfd::fail(RBFD_EINVAL, "rbfd_submit: NULL argument");
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (mesh_id < 0 || mesh_id >= (int)S->meshes.size()) rbfd::fail(RBFD_EINVAL, "rbfd_submit: unknown mesh");
+        if ((int64_t)S->queue.size() >= S->opt.max_queue) rbfd::fail(RBFD_EBUSY, "rbfd_submit: queue full");
+        const MeshSpec &M = *S->meshes[mesh_id];
+        Request r;
+        r.mesh = mesh_id;
+        r.dS.assign(req->dS, req->dS + M.n_s * M.dim);
+        r.out = req->out;
+        r.t_submit = clk::now();
+        const uint64_t t = S->next_ticket++;
+        S->reqs.emplace(t, std::move(r));
+        S->queue.push_back(t);
+        *ticket = t;
+        S->cv_work.notify_one();
+    });
+}
+
+int rbfd_poll(rbfd_server *S, uint64_t ticket, int *state) {
+    if (!S || !state) return RBFD_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) {
+        rbfd::set_last_error("rbfd_poll: unknown ticket");
+        return RBFD_EINVAL;
+    }
+    *state = it->second.state;
+    if (it->second.state == RBFD_REQ_FAILED) rbfd::set_last_error(it->second.msg);
+    return it->second.state >= RBFD_REQ_DONE ? it->second.status : RBFD_OK;
+}
+
+int rbfd_wait(rbfd_server *S, uint64_t ticket, double timeout_s, int *state) {
+    if (!S || !state) return RBFD_EINVAL;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) {
+        rbfd::set_last_error("rbfd_wait: unknown ticket");
+        return RBFD_EINVAL;
+    }
+    const bool done = S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 1e9),
+                                          [&] { return it->second.state >= RBFD_REQ_DONE; });
+    *state = it->second.state;
+    if (!done) {
+        rbfd::set_last_error("rbfd_wait: timed out");
+        return RBFD_ETIMEOUT;
+    }
+    if (it->second.state == RBFD_REQ_FAILED) rbfd::set_last_error(it->second.msg);
+    return it->second.status;
+}
+
+int rbfd_request_times(rbfd_server *S, uint64_t ticket, double *queue_ms, double *run_ms, double *total_ms) {
+    if (!S) return RBFD_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end() || it->second.state < RBFD_REQ_DONE) {
+        rbfd::set_last_error("rbfd_request_times: unknown or unfinished ticket");
+        return RBFD_EINVAL;
+    }
+    const Request &r = it->second;
+    auto ms = [](clk::duration d) { return std::chrono::duration<double, std::milli>(d).count(); };
+    if (queue_ms) *queue_ms = ms(r.t_start - r.t_submit);
+    if (run_ms) *run_ms = ms(r.t_done - r.t_start);
+    if (total_ms) *total_ms = ms(r.t_done - r.t_submit);
+    return RBFD_OK;
+}
+
+int rbfd_server_destroy(rbfd_server *S) {
+    if (!S) return RBFD_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->shutdown = true;
+        S->queue.clear();
+        S->cv_work.notify_all();
+    }
+    for (auto &t : S->workers) t.join();
+    for (auto &M : S->meshes)
+        for (rbfd_mesh *m : M->idle) rbfd_destroy(m);
+    delete S;
+    return RBFD_OK;
+}
+
+}  // extern "C"

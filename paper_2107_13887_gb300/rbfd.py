@@ -73,6 +73,21 @@ class rbfd_stats(ctypes.Structure):
     ]
 
 
+class rbfd_server_options(ctypes.Structure):
+    _fields_ = [
+        ("slots", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("mem_budget_bytes", ctypes.c_int64),
+        ("max_queue", ctypes.c_int64),
+    ]
+
+
+class rbfd_request(ctypes.Structure):
+    _fields_ = [("dS", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
 # (name, restype, argtypes) of every function include/rbfd.h declares
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -90,11 +105,24 @@ SIGNATURES = [
     ("rbfd_deform", ctypes.c_int, [_vp, _i64, _vp, _vp, _d, _d, _vp]),
     ("rbfd_deform_f64", ctypes.c_int, [_vp, _i64, _vp, _vp, _d, _d, _vp]),
     ("rbfd_deform_noalloc", ctypes.c_int, [_vp, _i64, _vp, _vp, _d, _d, _vp]),
+    ("rbfd_set_displacement", ctypes.c_int, [_vp, _vp]),
+    ("rbfd_set_volume", ctypes.c_int, [_vp, _i64, _vp, _vp]),
+    ("rbfd_deform_volume", ctypes.c_int, [_vp, _d, _d, _vp]),
     ("rbfd_greedy_batch", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int]),
     ("rbfd_deform_batch", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_i64),
                                          ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_d),
                                          ctypes.POINTER(_d), ctypes.POINTER(_vp)]),
     ("rbfd_destroy", ctypes.c_int, [_vp]),
+    ("rbfd_server_options_default", None, [ctypes.POINTER(rbfd_server_options)]),
+    ("rbfd_server_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(rbfd_server_options)]),
+    ("rbfd_server_add_mesh", ctypes.c_int, [_vp, ctypes.c_int, _i64, _vp, _i64, _vp, _vp, ctypes.c_int, _vp, _d,
+                                            _d, _d, ctypes.POINTER(ctypes.c_int)]),
+    ("rbfd_submit", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(rbfd_request), ctypes.POINTER(ctypes.c_uint64)]),
+    ("rbfd_poll", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
+    ("rbfd_wait", ctypes.c_int, [_vp, ctypes.c_uint64, _d, ctypes.POINTER(ctypes.c_int)]),
+    ("rbfd_request_times", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(_d), ctypes.POINTER(_d),
+                                          ctypes.POINTER(_d)]),
+    ("rbfd_server_destroy", ctypes.c_int, [_vp]),
     ("rbfd_last_error", ctypes.c_char_p, []),
     ("rbfd_version", ctypes.c_char_p, []),
 ]
@@ -272,6 +300,37 @@ class Mesh:
         _check(fn(self.h, int(n_v), _ptr(xyz_v), _ptr(d_v), float(D), float(k), _ptr(out)))
         return out
 
+    def set_displacement(self, dS):
+        """``rbfd_set_displacement``: a new surface displacement on the same surface."""
+        if self.on_device:
+            import torch
+
+            dS = dS.to(torch.float64).contiguous()
+        else:
+            dS = np.ascontiguousarray(dS, dtype=np.float64)
+        self._keep_dS = dS
+        _check(self._lib.rbfd_set_displacement(self.h, _ptr(dS)))
+
+    def set_volume(self, xyz_v, d_v):
+        """``rbfd_set_volume``: register a float32 volume mesh for repeated updates."""
+        if not self.on_device:
+            xyz_v = np.ascontiguousarray(xyz_v, dtype=np.float32)
+            d_v = np.ascontiguousarray(d_v, dtype=np.float32)
+        self.n_v_reg = int(xyz_v.shape[0])
+        _check(self._lib.rbfd_set_volume(self.h, self.n_v_reg, _ptr(xyz_v), _ptr(d_v)))
+
+    def deform_volume(self, D: float, k: float, out=None):
+        """``rbfd_deform_volume`` on the registered volume."""
+        if out is None:
+            if self.on_device:
+                import torch
+
+                out = torch.empty((self.n_v_reg, self.dim), dtype=torch.float32, device="cuda")
+            else:
+                out = np.empty((self.n_v_reg, self.dim), dtype=np.float32)
+        _check(self._lib.rbfd_deform_volume(self.h, float(D), float(k), _ptr(out)))
+        return out
+
     def deform_noalloc(self, xyz_v, d_v, D: float, k: float, out):
         """``rbfd_deform_noalloc``: float32 torch CUDA tensors in, result written
         into ``out`` (a preallocated float32 CUDA tensor); at most 131,072 points."""
@@ -305,3 +364,77 @@ def deform_batch(meshes, xyz_v, d_v, D, k, out):
     arr = (_vp * n)(*[m.h.value for m in meshes])
     _check(lib.rbfd_deform_batch(arr, n, nv, px, pd, Dv, kv, po))
     return out
+
+
+class Server:
+    """The request loop of ``rbfd_server_*``: register meshes, submit
+    displacements (host numpy arrays), poll / wait for the volume results."""
+
+    def __init__(self, slots=4, precision=MIXED, mem_budget_bytes=0, max_queue=4096):
+        lib = load()
+        self._lib = lib
+        o = rbfd_server_options()
+        lib.rbfd_server_options_default(ctypes.byref(o))
+        o.slots = int(slots)
+        o.precision = int(precision)
+        o.mem_budget_bytes = int(mem_budget_bytes)
+        o.max_queue = int(max_queue)
+        h = ctypes.c_void_p()
+        _check(lib.rbfd_server_create(ctypes.byref(h), ctypes.byref(o)))
+        self.h = h
+        self.meshes = {}
+        self._live = {}
+
+    def add_mesh(self, xyz_s, xyz_v, d_v, R, eps, D, k) -> int:
+        xyz_s = np.ascontiguousarray(xyz_s, dtype=np.float64)
+        xyz_v = np.ascontiguousarray(xyz_v, dtype=np.float32)
+        d_v = np.ascontiguousarray(d_v, dtype=np.float32)
+        Rv = np.ascontiguousarray(np.atleast_1d(R), dtype=np.float64)
+        mid = ctypes.c_int()
+        _check(self._lib.rbfd_server_add_mesh(self.h, xyz_s.shape[1], xyz_s.shape[0], _ptr(xyz_s), xyz_v.shape[0],
+                                              _ptr(xyz_v), _ptr(d_v), len(Rv), _ptr(Rv), float(eps), float(D),
+                                              float(k), ctypes.byref(mid)))
+        self.meshes[mid.value] = (xyz_s.shape[0], xyz_v.shape[0], xyz_s.shape[1])
+        return mid.value
+
+    def submit(self, mesh_id: int, dS, out=None):
+        if mesh_id not in self.meshes:
+            raise RbfdError(EINVAL, f"rbfd_submit: unknown mesh {mesh_id}")
+        n_s, n_v, dim = self.meshes[mesh_id]
+        dS = np.ascontiguousarray(dS, dtype=np.float64)
+        if out is None:
+            out = np.empty((n_v, dim), dtype=np.float32)
+        req = rbfd_request(_ptr(dS).value, _ptr(out).value)
+        t = ctypes.c_uint64()
+        _check(self._lib.rbfd_submit(self.h, int(mesh_id), ctypes.byref(req), ctypes.byref(t)))
+        self._live[t.value] = out  # the server writes it when the request completes
+        return t.value
+
+    def poll(self, ticket: int) -> int:
+        st = ctypes.c_int()
+        _check(self._lib.rbfd_poll(self.h, ticket, ctypes.byref(st)))
+        return st.value
+
+    def wait(self, ticket: int, timeout_s: float = 0.0):
+        """Block until done; returns (status, result array)."""
+        st = ctypes.c_int()
+        rc = self._lib.rbfd_wait(self.h, ticket, float(timeout_s), ctypes.byref(st))
+        if rc not in (OK, ENOTCONV):
+            raise RbfdError(rc, rbfd_last_error())
+        return rc, self._live.pop(ticket)
+
+    def times(self, ticket: int):
+        q, r, t = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(self._lib.rbfd_request_times(self.h, ticket, ctypes.byref(q), ctypes.byref(r), ctypes.byref(t)))
+        return q.value, r.value, t.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.rbfd_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
