@@ -51,7 +51,8 @@ typedef struct rbfd_options {
     int first_point;       /* 0: surface point 0 starts every level (Section 3, default);
                               1: the point of largest |dS_l| starts level l */
     int inputs_on_device;  /* 0: host pointers (default); 1: device pointers */
-    int64_t nc_cap;        /* controls per level at most; 0 = min(n_s, 16384) */
+    int64_t nc_cap;        /* controls per level at most; 0 = min(n_s, 32768).  Device memory grows
+                              as 16 * nc_cap^2 bytes (the inverse factor and its transpose) */
     void *stream;          /* cudaStream_t to run on; NULL = a stream the mesh creates */
     int eps_absolute;      /* 0: eps is relative to max_i |dS_i| (default); 1: absolute length */
     int refine_iters;      /* iterative-refinement sweeps at level close (default 3) */

@@ -217,11 +217,11 @@ void mesh_free(rbfd_mesh *m) {
     }
     void *ptrs[] = {m->d_perm, m->d_inv, m->d_xs, m->d_dS, m->d_cur, m->d_E, m->d_pb_lo, m->d_pb_hi,
                     m->d_pb_org, m->d_xs_hi, m->d_xs_lo, m->d_sel, m->d_G, m->d_w, m->d_alpha, m->d_cx,
-                    m->d_cid, m->d_phi, m->d_y, m->d_red, m->d_gpart, m->d_vec, m->d_vec2, m->d_v4part,
+                    m->d_cdf, m->d_cid, m->d_phi, m->d_y, m->d_red, m->d_gpart, m->d_vec, m->d_vec2, m->d_v4part,
                     m->d_nb_cnt, m->d_nb_list, m->d_part, m->d_pb_done, m->d_pb_key, m->d_pb_idx, m->d_pairs,
                     m->d_st, m->d_vin, m->d_vpos, m->d_vorig, m->d_vflag, m->d_vscan, m->d_vlist, m->d_vkeys,
-                    m->d_vacc, m->d_vio, m->d_misc, m->d_bbox, m->d_bar, m->d_pred, m->d_pgpart,
-                    m->d_kt_done, m->d_phase_ns, m->d_vreg, m->d_vreg_orig};
+                    m->d_vacc, m->d_vio, m->d_misc, m->d_bbox, m->d_bar, m->d_pred, m->d_Gt,
+                    m->d_nz_k, m->d_nz_v, m->d_phase_ns, m->d_vreg, m->d_vreg_orig};
     for (void *p : ptrs) dfree(p);
     m->sort.release();
     m->prof.release();

@@ -209,6 +209,80 @@ __device__ __forceinline__ void tile_accumulate_df(df qx, df qy, df qz, const fl
     }
 }
 
+// Bounding box of the warp's valid points (coordinates relative to the block
+// origin, hi parts), for the per-warp control filter below.
+__device__ __forceinline__ void warp_box(bool valid, float x, float y, float z, float3 &lo, float3 &hi) {
+    lo = valid ? make_float3(x, y, z) : make_float3(INFINITY, INFINITY, INFINITY);
+    hi = valid ? make_float3(x, y, z) : make_float3(-INFINITY, -INFINITY, -INFINITY);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
+        lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
+        lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
+        hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
+        hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
+        hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
+    }
+}
+
+// Indices of the staged controls (of m) that lie within R of the warp's box
+// (squared box distance below R2m, which carries a safety margin): a
+// warp-uniform filter, so the warp skips controls none of its points can
+// reach.  Writes them in order into hits[] and returns how many.
+template <int DIM>
+__device__ __forceinline__ int warp_hits(const float (*t32)[kTile], int m, float3 lo, float3 hi, float R2m,
+                                         unsigned char *hits) {
+    const int lane = threadIdx.x & 31;
+    int cnt = 0;
+    for (int base = 0; base < m; base += 32) {
+        const int q = base + lane;
+        bool in = false;
+        if (q < m) {
+            const float cx = t32[0][q], cy = t32[2][q];
+            const float dx = fmaxf(fmaxf(lo.x - cx, cx - hi.x), 0.0f);
+            const float dy = fmaxf(fmaxf(lo.y - cy, cy - hi.y), 0.0f);
+            float d2 = dx * dx + dy * dy;
+            if (DIM == 3) {
+                const float cz = t32[4][q];
+                const float dz = fmaxf(fmaxf(lo.z - cz, cz - hi.z), 0.0f);
+                d2 += dz * dz;
+            }
+            in = d2 < R2m;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, in);
+        if (in) hits[cnt + __popc(b & ((1u << lane) - 1u))] = (unsigned char)q;
+        cnt += __popc(b);
+    }
+    __syncwarp();
+    return cnt;
+}
+
+// tile_accumulate_df over the filtered controls hits[0..cnt) of a tile.
+template <int DIM, int BASIS>
+__device__ __forceinline__ void hits_accumulate_df(df qx, df qy, df qz, const float (*t32)[kTile],
+                                                   const unsigned char *hits, int cnt, df invR, df acc[3],
+                                                   unsigned &useful) {
+    int i = 0;
+    for (; i + 2 <= cnt; i += 2) {
+        const int q0 = hits[i], q1 = hits[i + 1];
+        const df f0 = pair_phi_df<DIM, BASIS>(qx, qy, qz, t32, q0, invR, useful);
+        const df f1 = pair_phi_df<DIM, BASIS>(qx, qy, qz, t32, q1, invR, useful);
+        acc[0] = df_add(acc[0], df_mul(f0, {t32[6][q0], t32[7][q0]}));
+        acc[1] = df_add(acc[1], df_mul(f0, {t32[8][q0], t32[9][q0]}));
+        if (DIM == 3) acc[2] = df_add(acc[2], df_mul(f0, {t32[10][q0], t32[11][q0]}));
+        acc[0] = df_add(acc[0], df_mul(f1, {t32[6][q1], t32[7][q1]}));
+        acc[1] = df_add(acc[1], df_mul(f1, {t32[8][q1], t32[9][q1]}));
+        if (DIM == 3) acc[2] = df_add(acc[2], df_mul(f1, {t32[10][q1], t32[11][q1]}));
+    }
+    if (i < cnt) {
+        const int q0 = hits[i];
+        const df f0 = pair_phi_df<DIM, BASIS>(qx, qy, qz, t32, q0, invR, useful);
+        acc[0] = df_add(acc[0], df_mul(f0, {t32[6][q0], t32[7][q0]}));
+        acc[1] = df_add(acc[1], df_mul(f0, {t32[8][q0], t32[9][q0]}));
+        if (DIM == 3) acc[2] = df_add(acc[2], df_mul(f0, {t32[10][q0], t32[11][q0]}));
+    }
+}
+
 // L2-coherent load of a double4 written by another block of the same launch.
 __device__ __forceinline__ double4 ldcg_d4(const double4 *p) {
     const double2 *q = reinterpret_cast<const double2 *>(p);
@@ -266,6 +340,34 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
+// Block-wide exclusive scan of one unsigned per thread (blockDim a multiple
+// of 32); *total receives the block sum.  sw: 32 words of shared scratch.
+__device__ __forceinline__ unsigned block_excl_scan_u32(unsigned v, unsigned *sw, unsigned *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sw[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned t = lane < nw ? sw[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) sw[lane] = t;
+    }
+    __syncthreads();
+    const unsigned before = (w > 0 ? sw[w - 1] : 0u) + x - v;
+    *total = sw[nw - 1];
+    __syncthreads();
+    return before;
+}
+
 // ---------------------------------------------------------- greedy state
 
 // Device-resident state of one greedy level (lives in device memory; a
@@ -283,6 +385,8 @@ struct GreedyState {
     double emax;      // sqrt(best_key) / S0 of the last sweep
     unsigned int pb_done;   // last-block-done counter of the sweep
     unsigned int red_done;  // last-block-done counter of reductions
+    int max_cnt;            // longest per-block control list (persistent engine)
+    int nnz;                // nonzeros of the phi column of the newest control
 };
 
 // Counter + generation word of the bounded grid barrier of the persistent

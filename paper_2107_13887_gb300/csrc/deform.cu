@@ -206,6 +206,7 @@ __global__ void __launch_bounds__(kThreads) k_vol_sweep(VolArgs a) {
     __shared__ uint32_t s_start[kThreads], s_off[kThreads], sw[32];
     __shared__ double t64[6][kTile];
     __shared__ float t32[12][kTile];
+    __shared__ unsigned char s_hits[4][kTile];
     const int tid = threadIdx.x;
     const int64_t i = (int64_t)blockIdx.x * kThreads + tid;
     const bool valid = i < a.n_list;
@@ -257,6 +258,9 @@ __global__ void __launch_bounds__(kThreads) k_vol_sweep(VolArgs a) {
     df acc[3] = {{0, 0}, {0, 0}, {0, 0}};
     unsigned useful = 0;
     unsigned long long visited = 0;
+    float3 wlo, whi;
+    if (MODE == 1) warp_box(valid, qx.hi, qy.hi, qz.hi, wlo, whi);
+    const float R2m = (float)(1.002 * a.R) * (float)(1.002 * a.R);  // filter margin
     for (int cb = 0; cb < ncr; cb += kThreads) {
         const int c = cb + tid;
         uint32_t cnt = 0, st0 = 0;
@@ -296,9 +300,9 @@ __global__ void __launch_bounds__(kThreads) k_vol_sweep(VolArgs a) {
                 }
             }
             __syncthreads();
-            if (valid) {
-                visited += m;
-                if (MODE == 0) {
+            if (MODE == 0) {
+                if (valid) {
+                    visited += m;
                     for (int q = 0; q < m; ++q) {
                         double eta = __ddiv_rn(dist_f64<DIM>(P.x, P.y, P.z, t64[0][q], t64[1][q], t64[2][q]), a.R);
                         double f = phi_f64<BASIS>(eta);
@@ -307,8 +311,13 @@ __global__ void __launch_bounds__(kThreads) k_vol_sweep(VolArgs a) {
                         acc64[1] = __dadd_rn(acc64[1], __dmul_rn(t64[4][q], f));
                         if (DIM == 3) acc64[2] = __dadd_rn(acc64[2], __dmul_rn(t64[5][q], f));
                     }
-                } else {
-                    tile_accumulate_df<DIM, BASIS>(qx, qy, qz, t32, m, invR, acc, useful);
+                }
+            } else {
+                // the whole warp takes part in the filter; lanes with a point accumulate
+                const int nh = warp_hits<DIM>(t32, m, wlo, whi, R2m, s_hits[tid >> 5]);
+                if (valid) {
+                    visited += nh;
+                    hits_accumulate_df<DIM, BASIS>(qx, qy, qz, t32, s_hits[tid >> 5], nh, invR, acc, useful);
                 }
             }
             __syncthreads();

@@ -232,6 +232,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(SweepArgs a) {
     // coordinates + weights (MODE 1)
     __shared__ double t64[6][kTile];
     __shared__ float t32[12][kTile];
+    __shared__ unsigned char s_hits[4][kTile];
     if (a.is_step && a.st->stop) return;
 
     const int pb = blockIdx.x, ch = blockIdx.y, nch = gridDim.y, tid = threadIdx.x;
@@ -257,6 +258,9 @@ __global__ void __launch_bounds__(kThreads) k_sweep(SweepArgs a) {
     }
     const df invR = {a.invR_hi, a.invR_lo};
     unsigned useful = 0;
+    float3 wlo, whi;
+    if (MODE == 1) warp_box(valid, qx.hi, qy.hi, qz.hi, wlo, whi);
+    const float R2m = (float)(1.002 * a.R) * (float)(1.002 * a.R);  // filter margin
     for (int t0 = lo; t0 < hi; t0 += kTile) {
         const int m = min(kTile, hi - t0);
         if (tid < m) {
@@ -274,8 +278,8 @@ __global__ void __launch_bounds__(kThreads) k_sweep(SweepArgs a) {
             }
         }
         __syncthreads();
-        if (valid) {
-            if (MODE == 0) {
+        if (MODE == 0) {
+            if (valid)
                 for (int q = 0; q < m; ++q) {
                     double eta = __ddiv_rn(dist_f64<DIM>(px, py, pz, t64[0][q], t64[1][q], t64[2][q]), a.R);
                     double f = phi_f64<BASIS>(eta);
@@ -284,9 +288,10 @@ __global__ void __launch_bounds__(kThreads) k_sweep(SweepArgs a) {
                     acc64[1] = __dadd_rn(acc64[1], __dmul_rn(t64[4][q], f));
                     if (DIM == 3) acc64[2] = __dadd_rn(acc64[2], __dmul_rn(t64[5][q], f));
                 }
-            } else {
-                tile_accumulate_df<DIM, BASIS>(qx, qy, qz, t32, m, invR, acc, useful);
-            }
+        } else {
+            // the whole warp takes part in the filter; lanes with a point accumulate
+            const int nh = warp_hits<DIM>(t32, m, wlo, whi, R2m, s_hits[tid >> 5]);
+            if (valid) hits_accumulate_df<DIM, BASIS>(qx, qy, qz, t32, s_hits[tid >> 5], nh, invR, acc, useful);
         }
         __syncthreads();
     }
@@ -389,6 +394,7 @@ struct GrowArgs {
     uint32_t *nb_cnt, *nb_list;
     const double *G;
     double *Gw;
+    double *Gt;
     double *y;
     double *red;  // [blocks][4]: y.y, y.w (3)
     int n_red;
@@ -503,6 +509,7 @@ __global__ void k_grow_finish(GrowArgs a, int n_jt) {
         for (int jt = 0; jt < n_jt; ++jt) s += a.gpart[(size_t)jt * a.cap + k];
         double g = -s / l;
         Grow[k] = g;
+        a.Gt[(size_t)k * a.cap + a.n] = g;
         double4 al = a.alpha[k];
         al.x = fma(wn.x, g, al.x);
         al.y = fma(wn.y, g, al.y);
@@ -510,6 +517,7 @@ __global__ void k_grow_finish(GrowArgs a, int n_jt) {
         a.alpha[k] = al;
     } else if (k == a.n) {
         Grow[k] = 1.0 / l;
+        a.Gt[(size_t)k * a.cap + k] = 1.0 / l;
         a.w[k] = wn;
         a.alpha[k] = make_double4(wn.x / l, wn.y / l, wn.z / l, 0.0);
         a.st->n = a.n + 1;
@@ -519,9 +527,10 @@ __global__ void k_grow_finish(GrowArgs a, int n_jt) {
 // Start a level: control 0, G = [1], w_0 = alpha_0 = dS_l(c_0); list it.
 __global__ void k_level_init(int first_orig_from_state, int first_orig, const uint32_t *inv, const double4 *xs,
                              const double4 *cur, int n_pb, int cap, int dim, double R2, const double4 *pb_lo,
-                             const double4 *pb_hi, unsigned char *sel, double4 *cx, uint32_t *cid, double *G,
-                             double4 *w, double4 *alpha, uint32_t *nb_cnt, uint32_t *nb_list, const double *red_out,
-                             GreedyState *st) {
+                             const double4 *pb_hi, unsigned char *sel, double4 *cx, float4 *cdf, uint32_t *cid,
+                             double *G,
+                             double *Gt, double4 *w, double4 *alpha, uint32_t *nb_cnt, uint32_t *nb_list,
+                             const double *red_out, GreedyState *st) {
     int o = first_orig_from_state ? reinterpret_cast<const int *>(red_out + 1)[0] : first_orig;
     const uint32_t c = inv[o];
     const double4 x = xs[c];
@@ -538,8 +547,13 @@ __global__ void k_level_init(int first_orig_from_state, int first_orig, const ui
     if (t == 0) {
         sel[c] = 1;
         cx[0] = x;
+        const float hx = __double2float_rn(x.x), hy = __double2float_rn(x.y), hz = __double2float_rn(x.z);
+        cdf[0] = make_float4(hx, hy, hz, 0.f);
+        cdf[cap + 1] = make_float4(__double2float_rn(x.x - (double)hx), __double2float_rn(x.y - (double)hy),
+                                   __double2float_rn(x.z - (double)hz), 0.f);
         cid[0] = c;
         G[0] = 1.0;
+        Gt[0] = 1.0;
         double4 b = cur[c];
         w[0] = b;
         alpha[0] = b;
@@ -554,55 +568,60 @@ __global__ void k_level_init(int first_orig_from_state, int first_orig, const ui
         st->emax = 0;
         st->pb_done = 0;
         st->red_done = 0;
+        st->max_cnt = 1;
+        st->nnz = 0;
     }
 }
 
 // ------------------------------------------------------------ refinement
 
-// r_i = dS_l(c_i) - sum_j alpha_j phi(|r_ci - r_cj| / R) over the n controls,
-// FP64; per-block max |r| to red[block].
+// r_i = dS_l(c_i) - sum_j alpha_j phi(|r_ci - r_cj| / R), FP64, one warp per
+// control i; the sum runs over the controls listed for the point block that
+// holds c_i (every control within R of it is listed, so the omitted ones
+// contribute exactly 0).  Per-block max |r| to red[block].
 template <int DIM, int BASIS>
-__global__ void __launch_bounds__(kThreads) k_resid(int n, double R, const double4 *__restrict__ cx,
+__global__ void __launch_bounds__(kThreads) k_resid(int n, double R, int cap, const double4 *__restrict__ cx,
                                                     const double4 *__restrict__ alpha,
                                                     const uint32_t *__restrict__ cid,
+                                                    const uint32_t *__restrict__ nb_cnt,
+                                                    const uint32_t *__restrict__ nb_list,
                                                     const double4 *__restrict__ cur, double4 *__restrict__ r,
                                                     double *__restrict__ red) {
-    __shared__ double t[6][kTile];
-    __shared__ double sm[32];
-    const int i = blockIdx.x * kThreads + threadIdx.x;
-    const bool valid = i < n;
-    double4 xi = valid ? cx[i] : make_double4(0, 0, 0, 0);
-    double acc[3] = {0, 0, 0};
-    for (int t0 = 0; t0 < n; t0 += kTile) {
-        int m = min(kTile, n - t0);
-        if ((int)threadIdx.x < m) {
-            double4 c = cx[t0 + threadIdx.x], al = alpha[t0 + threadIdx.x];
-            t[0][threadIdx.x] = c.x; t[1][threadIdx.x] = c.y; t[2][threadIdx.x] = c.z;
-            t[3][threadIdx.x] = al.x; t[4][threadIdx.x] = al.y; t[5][threadIdx.x] = al.z;
-        }
-        __syncthreads();
-        if (valid)
-            for (int q = 0; q < m; ++q) {
-                double f = phi_f64<BASIS>(__ddiv_rn(dist_f64<DIM>(xi.x, xi.y, xi.z, t[0][q], t[1][q], t[2][q]), R));
-                acc[0] = fma(t[3][q], f, acc[0]);
-                acc[1] = fma(t[4][q], f, acc[1]);
-                acc[2] = fma(t[5][q], f, acc[2]);
-            }
-        __syncthreads();
-    }
+    __shared__ double sm[kThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * (kThreads / 32) + w;
     double mx = 0.0;
-    if (valid) {
-        double4 b = cur[cid[i]];
-        double4 ri = make_double4(b.x - acc[0], b.y - acc[1], DIM == 3 ? b.z - acc[2] : 0.0, 0.0);
-        r[i] = ri;
-        mx = fmax(fabs(ri.x), fmax(fabs(ri.y), fabs(ri.z)));
+    if (i < n) {
+        const uint32_t ci = cid[i];
+        const double4 xi = cx[i];
+        const int pb = (int)(ci / kPB);
+        const int cnt = (int)nb_cnt[pb];
+        const uint32_t *list = nb_list + (size_t)pb * cap;
+        double a0 = 0, a1 = 0, a2 = 0;
+        for (int q = lane; q < cnt; q += 32) {
+            const uint32_t j = list[q];
+            const double4 c = cx[j], al = alpha[j];
+            const double f = phi_f64<BASIS>(__ddiv_rn(dist_f64<DIM>(xi.x, xi.y, xi.z, c.x, c.y, c.z), R));
+            a0 = fma(al.x, f, a0);
+            a1 = fma(al.y, f, a1);
+            a2 = fma(al.z, f, a2);
+        }
+        a0 = warp_sum_d(a0);
+        a1 = warp_sum_d(a1);
+        a2 = warp_sum_d(a2);
+        if (lane == 0) {
+            const double4 b = cur[ci];
+            const double4 ri = make_double4(b.x - a0, b.y - a1, DIM == 3 ? b.z - a2 : 0.0, 0.0);
+            r[i] = ri;
+            mx = fmax(fabs(ri.x), fmax(fabs(ri.y), fabs(ri.z)));
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+    if (lane == 0) sm[w] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int q = 1; q < kThreads / 32; ++q) mx = fmax(mx, sm[q]);
-        red[blockIdx.x] = fmax(mx, sm[0]);
+        double v = sm[0];
+        for (int q = 1; q < kThreads / 32; ++q) v = fmax(v, sm[q]);
+        red[blockIdx.x] = v;
     }
 }
 
@@ -728,12 +747,16 @@ void launch_phi_d(int basis, unsigned g, const GrowArgs &a, cudaStream_t st) {
 
 template <int DIM>
 void launch_resid_d(int basis, unsigned g, int n, double R, rbfd_mesh *m, cudaStream_t st) {
+#define RBFD_RESID(B)                                                                                           \
+    k_resid<DIM, B><<<g, kThreads, 0, st>>>(n, R, m->cap, m->d_cx, m->d_alpha, m->d_cid, m->d_nb_cnt,           \
+                                            m->d_nb_list, m->d_cur, m->d_vec, m->d_red)
     switch (basis) {
-    case 0: k_resid<DIM, 0><<<g, kThreads, 0, st>>>(n, R, m->d_cx, m->d_alpha, m->d_cid, m->d_cur, m->d_vec, m->d_red); break;
-    case 4: k_resid<DIM, 4><<<g, kThreads, 0, st>>>(n, R, m->d_cx, m->d_alpha, m->d_cid, m->d_cur, m->d_vec, m->d_red); break;
-    case 6: k_resid<DIM, 6><<<g, kThreads, 0, st>>>(n, R, m->d_cx, m->d_alpha, m->d_cid, m->d_cur, m->d_vec, m->d_red); break;
-    default: k_resid<DIM, 2><<<g, kThreads, 0, st>>>(n, R, m->d_cx, m->d_alpha, m->d_cid, m->d_cur, m->d_vec, m->d_red); break;
+    case 0: RBFD_RESID(0); break;
+    case 4: RBFD_RESID(4); break;
+    case 6: RBFD_RESID(6); break;
+    default: RBFD_RESID(2); break;
     }
+#undef RBFD_RESID
 }
 
 int n_chunks_for(const rbfd_mesh *m, int n) {
@@ -899,7 +922,7 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     dfree(d4);
 
     // greedy workspace
-    int64_t cap = m->opt.nc_cap > 0 ? m->opt.nc_cap : 16384;
+    int64_t cap = m->opt.nc_cap > 0 ? m->opt.nc_cap : 32768;
     cap = std::min<int64_t>(cap, n);
     m->cap = (int)cap;
     m->d_sel = dalloc<unsigned char>(n, "selected flags");
@@ -907,6 +930,7 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     m->d_w = dalloc<double4>(cap + 1, "w");
     m->d_alpha = dalloc<double4>(cap + 1, "alpha");
     m->d_cx = dalloc<double4>(cap + 1, "control coordinates");
+    m->d_cdf = dalloc<float4>(2 * (cap + 1), "control coordinates, double-float");
     m->d_cid = dalloc<uint32_t>(cap + 1, "control ids");
     m->d_phi = dalloc<double>(cap + 1, "phi column");
     m->d_y = dalloc<double>(cap + 1, "y");
@@ -919,7 +943,7 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     m->d_v4part = dalloc<double4>((size_t)n_jt * cap + cap, "refinement partials");
     m->d_nb_cnt = dalloc<uint32_t>(m->n_pb, "block list counts");
     m->d_nb_list = dalloc<uint32_t>((size_t)m->n_pb * cap, "block lists");
-    m->n_chunk_max = std::max(1, (kTargetCTAs + m->n_pb - 1) / m->n_pb);
+    m->n_chunk_max = std::max(128, (kTargetCTAs + m->n_pb - 1) / m->n_pb);
     m->d_part = dalloc<double4>((size_t)m->n_chunk_max * n, "sweep partials");
     m->d_pb_done = dalloc<unsigned int>(m->n_pb, "block counters");
     RBFD_CUDA(cudaMemsetAsync(m->d_pb_done, 0, sizeof(unsigned int) * m->n_pb, st));
@@ -932,11 +956,11 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     m->d_bar = dalloc<GridBarrier>(1, "grid barrier");
     RBFD_CUDA(cudaMemsetAsync(m->d_bar, 0, sizeof(GridBarrier), st));
     m->d_pred = dalloc<double>((size_t)4 * kMaxPersistCTAs, "persistent reductions");
-    m->d_pgpart = dalloc<double>((size_t)(cap / 128 + 2) * cap, "persistent column partials");
-    m->d_kt_done = dalloc<unsigned int>((size_t)cap / 32 + 2, "column-group counters");
+    m->d_Gt = dalloc<double>((size_t)cap * cap, "inverse factor, transposed");
+    m->d_nz_k = dalloc<uint32_t>(cap + 1, "phi nonzero ids");
+    m->d_nz_v = dalloc<double>(cap + 1, "phi nonzero values");
     m->d_phase_ns = dalloc<unsigned long long>(8, "phase timing");
     RBFD_CUDA(cudaMemsetAsync(m->d_phase_ns, 0, 8 * sizeof(unsigned long long), st));
-    RBFD_CUDA(cudaMemsetAsync(m->d_kt_done, 0, sizeof(unsigned int) * (cap / 32 + 2), st));
     m->h_st = static_cast<GreedyState *>(pinned_alloc(sizeof(GreedyState)));
     RBFD_CUDA(cudaStreamSynchronize(st));
 
@@ -1021,7 +1045,7 @@ void greedy_run(rbfd_mesh *m) {
         RBFD_CUDA(cudaMemsetAsync(m->d_sel, 0, m->n_s, st));
         k_level_init<<<cdiv(std::max(m->n_pb, 1), kThreads), kThreads, 0, st>>>(
             m->opt.first_point == 1 ? 1 : 0, 0, m->d_inv, m->d_xs, m->d_cur, m->n_pb, m->cap, m->dim, R2,
-            m->d_pb_lo, m->d_pb_hi, m->d_sel, m->d_cx, m->d_cid, m->d_G, m->d_w, m->d_alpha, m->d_nb_cnt,
+            m->d_pb_lo, m->d_pb_hi, m->d_sel, m->d_cx, m->d_cdf, m->d_cid, m->d_G, m->d_Gt, m->d_w, m->d_alpha, m->d_nb_cnt,
             m->d_nb_list, m->d_bbox, m->d_st);
         RBFD_CUDA(cudaGetLastError());
         m->stats.launches += 2;  // maxnorm + level init
@@ -1044,6 +1068,7 @@ void greedy_run(rbfd_mesh *m) {
         g.nb_list = m->d_nb_list;
         g.G = m->d_G;
         g.Gw = m->d_G;
+        g.Gt = m->d_Gt;
         g.y = m->d_y;
         g.red = m->d_red;
         g.gpart = m->d_gpart;
@@ -1060,7 +1085,10 @@ void greedy_run(rbfd_mesh *m) {
             if (m->opt.engine == 0) {
                 const int maxc = std::min(persist_max_ctas(m), kMaxPersistCTAs);
                 if (maxc < 1) fail(RBFD_ECUDA, "persistent greedy kernel cannot be resident on this device");
-                int ctas = m->opt.grid_ctas > 0 ? m->opt.grid_ctas : std::min(std::max(64, 4 * m->n_pb), 2 * 152);
+                // small meshes: few blocks keep the barriers cheap; large ones fill the GPU
+                int ctas = m->opt.grid_ctas > 0 ? m->opt.grid_ctas
+                                                : (m->n_pb <= 128 ? std::min(std::max(64, 4 * m->n_pb), 2 * 152)
+                                                                  : std::min(4 * m->n_pb, 8 * 152));
                 if (m->batch_ctas_cap > 0) ctas = std::min(ctas, m->batch_ctas_cap);
                 ctas = std::max(1, std::min(ctas, maxc));
                 RBFD_CUDA(cudaMemsetAsync(m->d_bar, 0, sizeof(GridBarrier), st));
@@ -1123,7 +1151,7 @@ void greedy_run(rbfd_mesh *m) {
             m->stats.greedy_steps += 0;
             // ---- level close: FP64 iterative refinement of alpha
             for (int it = 0; it < std::max(0, m->opt.refine_iters); ++it) {
-                const unsigned nb = cdiv(n, kThreads);
+                const unsigned nb = cdiv(n, kThreads / 32);  // one warp per control
                 if (m->dim == 2) launch_resid_d<2>(m->opt.basis, nb, n, L.R, m, st);
                 else launch_resid_d<3>(m->opt.basis, nb, n, L.R, m, st);
                 std::vector<double> rmax(nb);

@@ -136,9 +136,13 @@ struct rbfd_mesh {
     int cap = 0;
     unsigned char *d_sel = nullptr;
     double *d_G = nullptr;        // inverse Cholesky factor, cap x cap, row-major lower
+    double *d_Gt = nullptr;       // its transpose, row-major (row k = column k of G)
+    uint32_t *d_nz_k = nullptr;   // nonzeros of the newest phi column: control ids
+    double *d_nz_v = nullptr;     //   and values
     double4 *d_w = nullptr;       // L^{-1} dS_c
     double4 *d_alpha = nullptr;   // weights of the current level
     double4 *d_cx = nullptr;      // control coordinates
+    float4 *d_cdf = nullptr;      // the same split into double-float hi [0..cap] and lo [cap+1..]
     uint32_t *d_cid = nullptr;    // control sorted positions
     double *d_phi = nullptr;      // phi(c_new, c_k)
     double *d_y = nullptr;        // G phi
@@ -161,8 +165,6 @@ struct rbfd_mesh {
     int batch_ctas_cap = 0;          // set by the batch calls: blocks this mesh may use
     rbfd::GridBarrier *d_bar = nullptr;
     double *d_pred = nullptr;       // [kMaxPersistCTAs][4] per-block y.y, y.w
-    double *d_pgpart = nullptr;     // [cap/128 + 1][cap] column-sum partials
-    unsigned int *d_kt_done = nullptr;  // [cap/32 + 1] column-group counters
     unsigned long long *d_phase_ns = nullptr;  // [8] persistent phase timing (profile mode)
 
     std::vector<rbfd::Level> levels;

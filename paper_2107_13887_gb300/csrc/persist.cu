@@ -3,22 +3,26 @@
 // steps itself, separated by a grid barrier, so no step waits for the host.
 //
 // Per step, with n controls selected so far (every block tracks n in lockstep):
-//   phase 1  surface error sweep (Eq. 12): items (point block, control chunk);
-//            chunk partial sums -> scratch; the last chunk of each point block
-//            (atomic counter) reduces them in chunk order in FP64, forms
+//   phase 1  surface error sweep (Eq. 12): items (point block, chunk of its
+//            control list), the chunk length set by the longest list so that
+//            heavy blocks near the ice spread over many blocks; chunk partial
+//            sums -> scratch; the last chunk of each point block (atomic
+//            counter) reduces them in chunk order in FP64, forms
 //            E = dS_l - sum and the key |E|^2, and writes the block's argmax;
 //            the last point block to finish (second counter) takes the step's
-//            decision: global argmax, stop test max|E|/S0 < tau_l in FP64, and,
-//            if the level goes on, phi(|r_cn - r_ck|/R) for every k (up to
-//            1024 controls; beyond that all blocks share it after the barrier),
-//            c_n listed in every point block within R, c_n recorded.
+//            decision: global argmax, stop test max|E|/S0 < tau_l in FP64,
+//            and, if the level goes on, the nonzeros of phi(|r_cn - r_ck|/R)
+//            (only controls on c_n's block list can be within R) and c_n.
 //   -- barrier --
-//   phase 3  y = G phi (one warp per row of the inverse factor G = L^{-1});
-//            per-block partial sums of y.y and y.w.
+//   phase 3  c_n listed in every point block within R of it (after the
+//            barrier: no sweep reads the lists any more); y = G phi over the
+//            nonzeros of phi (one warp per row of the inverse factor
+//            G = L^{-1}); per-block partial sums of y.y, y.w.
 //   -- barrier --
-//   phase 4  l = sqrt(1 - y.y), w_n = (dS_l(c_n) - y.w) / l; column sums of
-//            y^T G in 32-column x 128-row tiles, finished by the last tile of
-//            each column group (atomic counter): G row n and alpha += w_n G_n.
+//   phase 4  l = sqrt(1 - y.y), w_n = (dS_l(c_n) - y.w) / l; the new row
+//            g = -(y^T G) / l as one warp per column over the rows of the
+//            transposed copy G^T (contiguous reads); G row n, G^T column n,
+//            alpha += w_n g.
 //   -- barrier --
 //
 // The barrier is a counter plus generation word in global memory; a block
@@ -37,9 +41,7 @@ namespace rbfd {
 namespace {
 
 constexpr int kT = 128;        // threads per block (4 warps)
-constexpr int kColTile = 32;   // columns per column-sum item
-constexpr int kRowTile = 128;  // rows per column-sum item
-constexpr int kFusePhiMax = 1024;  // up to this many controls one block computes the phi column
+
 
 struct PersistArgs {
     int64_t n_s;
@@ -52,10 +54,13 @@ struct PersistArgs {
     unsigned char *sel;
     uint32_t *nb_cnt, *nb_list;
     double4 *cx, *alpha, *w;
+    float4 *cdf;  // control coordinates split hi [0, cap] / lo [cap + 1, 2 cap + 1] (double-float)
     uint32_t *cid;
-    double *G, *phi, *y, *red, *gpart;
+    double *G, *Gt, *phi, *y, *red;
+    uint32_t *nz_k;
+    double *nz_v;
     double4 *part;
-    unsigned int *pb_done, *kt_done;
+    unsigned int *pb_done;
     double *pb_key;
     int *pb_idx;
     GridBarrier *bar;
@@ -74,6 +79,7 @@ __device__ __forceinline__ unsigned long long gtimer() {
 
 __device__ __forceinline__ uint32_t ldcg_u32(const uint32_t *p) { return __ldcg(p); }
 __device__ __forceinline__ double ldcg_d(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ float4 ldcg_f4(const float4 *p) { return __ldcg(p); }
 
 // Grid-wide barrier with a bounded wait.  Returns false (in every thread of
 // the block) if the launch is failing: this block timed out or another one did.
@@ -114,9 +120,11 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
     __shared__ float t32[12][kTile];
     __shared__ double sk[32];
     __shared__ int si[32];
-    __shared__ double scol[4][kColTile];
+    __shared__ double scol[4][32];
     __shared__ double sred[4][4];
     __shared__ bool s_last, s_lead;
+    __shared__ unsigned s_scan[32];
+    __shared__ unsigned char s_hits[4][kTile];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned P = gridDim.x;
@@ -152,16 +160,20 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
 
     for (int guard = 0; guard <= a.cap; ++guard) {
         // ------------------------------------------------ phase 1: sweep (+ the step's decision)
-        const bool fuse_phi = n <= kFusePhiMax;  // phi computed by the deciding block
-        int nch = (int)((P + a.n_pb - 1) / a.n_pb);
-        nch = max(1, min(nch, min(a.n_chunk_max, (n + 15) / 16)));
-        const int cl = (n + nch - 1) / nch;
+        // every block list is cut into chunks of at most cl controls, cl set by
+        // the longest list, so that no point block holds the step back
+        const int max_cnt = max(1, (int)__ldcg(&a.st->max_cnt));
+        int nch = max((int)((P + a.n_pb - 1) / a.n_pb), (max_cnt + 127) / 128);
+        nch = max(1, min(nch, min(a.n_chunk_max, (max_cnt + 15) / 16)));
+        const int cl = (max_cnt + nch - 1) / nch;
         for (int item = blockIdx.x; item < a.n_pb * nch; item += P) {
             const int pb = item / nch, ch = item % nch;
+            const int cnt = (int)ldcg_u32(&a.nb_cnt[pb]);
+            const int used = min(nch, max(1, (cnt + cl - 1) / cl));  // chunks this block's list occupies
+            if (ch >= used) continue;                                // same decision in every thread
             const int64_t p = (int64_t)pb * kPB + tid;
             const bool valid = p < a.n_s;
-            const int cnt = (int)ldcg_u32(&a.nb_cnt[pb]);
-            const int lo = ch * cl, hi = min(cnt, lo + cl);
+            const int lo = ch * cl, hi = (ch == used - 1) ? cnt : min(cnt, lo + cl);  // the last takes the rest
             const double4 org = a.pb_org[pb];
             double acc64[3] = {0, 0, 0};
             df acc[3] = {{0, 0}, {0, 0}, {0, 0}};
@@ -177,6 +189,9 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
                 }
             }
             unsigned useful = 0;
+            float3 wlo, whi;
+            if (MODE == 1) warp_box(valid, qx.hi, qy.hi, qz.hi, wlo, whi);
+            const float R2m = (float)(1.002 * a.R) * (float)(1.002 * a.R);  // filter margin
             for (int t0 = lo; t0 < hi; t0 += kTile) {
                 const int m = min(kTile, hi - t0);
                 if (tid < m) {
@@ -195,8 +210,8 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
                     }
                 }
                 __syncthreads();
-                if (valid) {
-                    if (MODE == 0) {
+                if (MODE == 0) {
+                    if (valid)
                         for (int q = 0; q < m; ++q) {
                             double eta = __ddiv_rn(dist_f64<DIM>(px, py, pz, t64[0][q], t64[1][q], t64[2][q]), a.R);
                             double f = phi_f64<BASIS>(eta);
@@ -205,9 +220,12 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
                             acc64[1] = __dadd_rn(acc64[1], __dmul_rn(t64[4][q], f));
                             if (DIM == 3) acc64[2] = __dadd_rn(acc64[2], __dmul_rn(t64[5][q], f));
                         }
-                    } else {
-                        tile_accumulate_df<DIM, BASIS>(qx, qy, qz, t32, m, invR, acc, useful);
-                    }
+                } else {
+                    // every lane of the warp takes part in the filter, then only
+                    // the lanes with a point accumulate
+                    const int nh = warp_hits<DIM>(t32, m, wlo, whi, R2m, s_hits[warp]);
+                    if (valid)
+                        hits_accumulate_df<DIM, BASIS>(qx, qy, qz, t32, s_hits[warp], nh, invR, acc, useful);
                 }
                 __syncthreads();
             }
@@ -230,7 +248,7 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
             // point block to finish then takes the step's decision
             __threadfence();
             __syncthreads();
-            if (tid == 0) s_last = atomicAdd(&a.pb_done[pb], 1u) == (unsigned)(nch - 1);
+            if (tid == 0) s_last = atomicAdd(&a.pb_done[pb], 1u) == (unsigned)(used - 1);
             __syncthreads();
             if (s_last) {
                 __threadfence();
@@ -239,18 +257,18 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
                 if (valid) {
                     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
                     int c = 0;
-                    for (; c + 4 <= nch; c += 4) {  // four independent loads in flight
-                        double4 v[4];
+                    for (; c + 8 <= used; c += 8) {  // eight independent loads in flight
+                        double4 v[8];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) v[q] = ldcg_d4(&a.part[(size_t)(c + q) * a.n_s + p]);
+                        for (int q = 0; q < 8; ++q) v[q] = ldcg_d4(&a.part[(size_t)(c + q) * a.n_s + p]);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
+                        for (int q = 0; q < 8; ++q) {
                             s0 = __dadd_rn(s0, v[q].x);
                             s1 = __dadd_rn(s1, v[q].y);
                             s2 = __dadd_rn(s2, v[q].z);
                         }
                     }
-                    for (; c < nch; ++c) {
+                    for (; c < used; ++c) {
                         double4 v = ldcg_d4(&a.part[(size_t)c * a.n_s + p]);
                         s0 = __dadd_rn(s0, v.x);
                         s1 = __dadd_rn(s1, v.y);
@@ -277,7 +295,7 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
                 }
                 __syncthreads();
                 if (s_lead) {
-                    // ---- the step's decision (one block): argmax, stop test, phi, lists
+                    // ---- the step's decision (one block): argmax, stop test, phi column, lists
                     __threadfence();
                     double K = -1.0;
                     int I = -1;
@@ -295,26 +313,52 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
                     if (!stop) {
                         const uint32_t c = a.inv[I];
                         const double4 xc = a.xs[c];
-                        if (fuse_phi)
-                            for (int k = tid; k < n; k += kT) {
+                        const df xcx = df_from_double(xc.x), xcy = df_from_double(xc.y), xcz = df_from_double(xc.z);
+                        // phi(|r_cn - r_ck| / R) is nonzero only for controls within R of
+                        // c_n, all of which are on the list of c_n's point block; keep
+                        // the nonzeros in list (= control) order
+                        const int pbc = (int)(c / kPB);
+                        const int cntc = (int)ldcg_u32(&a.nb_cnt[pbc]);
+                        const uint32_t *lst = a.nb_list + (size_t)pbc * a.cap;
+                        // each thread evaluates a contiguous stretch of the list (values
+                        // parked in phi[]), then one block scan places the nonzeros in order
+                        const int per = (cntc + kT - 1) / kT;
+                        const int q0 = min(cntc, tid * per), q1 = min(cntc, q0 + per);
+                        unsigned mine = 0;
+                        for (int q = q0; q < q1; ++q) {
+                            const uint32_t k = ldcg_u32(lst + q);
+                            double f;
+                            if (MODE == 0) {
                                 const double4 ck = ldcg_d4(&a.cx[k]);
-                                a.phi[k] = phi_f64<BASIS>(
-                                    __ddiv_rn(dist_f64<DIM>(xc.x, xc.y, xc.z, ck.x, ck.y, ck.z), a.R));
+                                f = phi_f64<BASIS>(__ddiv_rn(dist_f64<DIM>(xc.x, xc.y, xc.z, ck.x, ck.y, ck.z), a.R));
+                            } else {  // double-float on the FP32 pipe from the split coordinates
+                                const float4 h = ldcg_f4(&a.cdf[k]), l = ldcg_f4(&a.cdf[a.cap + 1 + k]);
+                                const df dx = df_add({h.x, l.x}, df_neg(xcx)), dy = df_add({h.y, l.y}, df_neg(xcy));
+                                df r2 = df_add(df_sqr(dx), df_sqr(dy));
+                                if (DIM == 3) r2 = df_add(r2, df_sqr(df_add({h.z, l.z}, df_neg(xcz))));
+                                f = df_to_double(phi_df<BASIS>(df_mul(df_sqrt(r2), invR)));
                             }
-                        for (int t = tid; t < a.n_pb; t += kT) {
-                            const double4 l = a.pb_lo[t], h = a.pb_hi[t];
-                            const double dx = fmax(fmax(l.x - xc.x, xc.x - h.x), 0.0);
-                            const double dy = fmax(fmax(l.y - xc.y, xc.y - h.y), 0.0);
-                            const double dz = DIM == 3 ? fmax(fmax(l.z - xc.z, xc.z - h.z), 0.0) : 0.0;
-                            if (dx * dx + dy * dy + dz * dz < a.R2 * (1.0 + 1e-9)) {
-                                const uint32_t k = ldcg_u32(&a.nb_cnt[t]);
-                                a.nb_list[(size_t)t * a.cap + k] = (uint32_t)n;
-                                a.nb_cnt[t] = k + 1;
+                            a.phi[q] = f;
+                            mine += (f != 0.0);
+                        }
+                        unsigned nnz;
+                        unsigned pos = block_excl_scan_u32(mine, s_scan, &nnz);
+                        for (int q = q0; q < q1; ++q) {
+                            const double f = a.phi[q];  // written by this thread above
+                            if (f != 0.0) {
+                                a.nz_k[pos] = ldcg_u32(lst + q);
+                                a.nz_v[pos] = f;
+                                ++pos;
                             }
                         }
+                        // (the block lists get c_n after the barrier: other blocks may
+                        // still be deciding their items of this step from the counts)
                         if (tid == 0) {
+                            a.st->nnz = (int)nnz;
                             a.sel[c] = 1;
                             a.cx[n] = xc;
+                            a.cdf[n] = make_float4(xcx.hi, xcy.hi, xcz.hi, 0.f);
+                            a.cdf[a.cap + 1 + n] = make_float4(xcx.lo, xcy.lo, xcz.lo, 0.f);
                             a.cid[n] = c;
                             a.st->best = (int)c;
                         }
@@ -340,34 +384,45 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
         if (__ldcg(&a.st->stop)) RBFD_EXIT()
         const uint32_t c = (uint32_t)__ldcg(&a.st->best);
         const bool first_block = blockIdx.x == 0 && tid == 0;
-        if (!fuse_phi) {
-            const double4 xc = a.xs[c];
-            const unsigned gtid = blockIdx.x * kT + tid, gstride = P * kT;
-            for (unsigned k = gtid; k < (unsigned)n; k += gstride) {
-                const double4 ck = ldcg_d4(&a.cx[k]);
-                a.phi[k] = phi_f64<BASIS>(__ddiv_rn(dist_f64<DIM>(xc.x, xc.y, xc.z, ck.x, ck.y, ck.z), a.R));
-            }
-            RBFD_SYNC(1)
-        }
+        const int nnz = __ldcg(&a.st->nnz);
+        const int k0 = nnz > 0 ? (int)ldcg_u32(a.nz_k) : n;  // y_j = 0 for j < k0
 
-        // ------------------------------------------------ phase 3: y = G phi
+        // ------------------------------------------------ phase 3: lists, y = G phi (phi sparse)
+        {
+            // list c_n in every point block within R of it; the next sweep
+            // chunks the lists by the longest one
+            const double4 xc = a.xs[c];
+            for (int t = blockIdx.x * kT + tid; t < a.n_pb; t += P * kT) {
+                const double4 l = a.pb_lo[t], h = a.pb_hi[t];
+                const double dx = fmax(fmax(l.x - xc.x, xc.x - h.x), 0.0);
+                const double dy = fmax(fmax(l.y - xc.y, xc.y - h.y), 0.0);
+                const double dz = DIM == 3 ? fmax(fmax(l.z - xc.z, xc.z - h.z), 0.0) : 0.0;
+                if (dx * dx + dy * dy + dz * dz < a.R2 * (1.0 + 1e-9)) {
+                    const uint32_t k = ldcg_u32(&a.nb_cnt[t]);
+                    a.nb_list[(size_t)t * a.cap + k] = (uint32_t)n;
+                    a.nb_cnt[t] = k + 1;
+                    atomicMax(&a.st->max_cnt, (int)(k + 1));
+                }
+            }
+        }
         double yy = 0, yw0 = 0, yw1 = 0, yw2 = 0;
         for (int j = blockIdx.x * 4 + warp; j < n; j += P * 4) {
-            const double *row = a.G + (size_t)j * a.cap;
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            int k = lane;
-            for (; k + 96 <= j; k += 128) {  // four independent load pairs in flight
-                const double g0 = ldcg_d(row + k), g1 = ldcg_d(row + k + 32), g2 = ldcg_d(row + k + 64),
-                             g3 = ldcg_d(row + k + 96);
-                const double p0 = ldcg_d(a.phi + k), p1 = ldcg_d(a.phi + k + 32), p2 = ldcg_d(a.phi + k + 64),
-                             p3 = ldcg_d(a.phi + k + 96);
-                s0 = fma(g0, p0, s0);
-                s1 = fma(g1, p1, s1);
-                s2 = fma(g2, p2, s2);
-                s3 = fma(g3, p3, s3);
+            double s0 = 0.0, s1 = 0.0;
+            if (j >= k0) {
+                const double *row = a.G + (size_t)j * a.cap;
+                int q = lane;
+                for (; q + 32 < nnz; q += 64) {
+                    const uint32_t ka = ldcg_u32(a.nz_k + q), kb = ldcg_u32(a.nz_k + q + 32);
+                    const double va = ldcg_d(a.nz_v + q), vb = ldcg_d(a.nz_v + q + 32);
+                    if ((int)ka <= j) s0 = fma(ldcg_d(row + ka), va, s0);
+                    if ((int)kb <= j) s1 = fma(ldcg_d(row + kb), vb, s1);
+                }
+                for (; q < nnz; q += 32) {
+                    const uint32_t ka = ldcg_u32(a.nz_k + q);
+                    if ((int)ka <= j) s0 = fma(ldcg_d(row + ka), ldcg_d(a.nz_v + q), s0);
+                }
             }
-            for (; k <= j; k += 32) s0 = fma(ldcg_d(row + k), ldcg_d(a.phi + k), s0);
-            double s = warp_sum_d((s0 + s1) + (s2 + s3));
+            const double s = warp_sum_d(s0 + s1);
             if (lane == 0) {
                 a.y[j] = s;
                 const double4 wj = ldcg_d4(&a.w[j]);
@@ -387,7 +442,7 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
         if (tid < 4) a.red[blockIdx.x * 4 + tid] = sred[0][tid] + sred[1][tid] + sred[2][tid] + sred[3][tid];
         RBFD_SYNC(2)
 
-        // ------------------------------------------------ phase 4: G row n, alpha
+        // ------------------------------------------------ phase 4: G row n (= G^T column n), alpha
         {
             double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
             for (unsigned b = tid; b < P; b += kT) {
@@ -426,66 +481,37 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
         double *Grow = a.G + (size_t)n * a.cap;
         if (first_block) {
             Grow[n] = 1.0 / l;
+            a.Gt[(size_t)n * a.cap + n] = 1.0 / l;
             a.w[n] = make_double4(wn0, wn1, wn2, 0.0);
             a.alpha[n] = make_double4(wn0 / l, wn1 / l, wn2 / l, 0.0);
         }
-        const int n_kt = (n + kColTile - 1) / kColTile, n_jc = (n + kRowTile - 1) / kRowTile;
-        for (int item = blockIdx.x; item < n_kt * n_jc; item += P) {
-            const int kt = item / n_jc, jc = item % n_jc;
-            const int k = kt * kColTile + lane;
-            const int jb = jc * kRowTile + warp * 32;
-            double s = 0.0;
-#pragma unroll
-            for (int r0 = 0; r0 < 32; r0 += 8) {  // eight independent load pairs in flight
-                double gv[8], yv[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int j = jb + r0 + q;
-                    const bool ok = j < n && k <= j;
-                    gv[q] = ok ? ldcg_d(a.G + (size_t)j * a.cap + k) : 0.0;
-                    yv[q] = ok ? ldcg_d(a.y + j) : 0.0;
-                }
-#pragma unroll
-                for (int q = 0; q < 8; ++q) s = fma(yv[q], gv[q], s);
+        // g_k = -(sum_{j >= k} y_j G_jk) / l, one warp per k over row k of G^T
+        for (int k = blockIdx.x * 4 + warp; k < n; k += P * 4) {
+            const double *trow = a.Gt + (size_t)k * a.cap;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int j = max(k, k0) + lane;
+            for (; j + 96 < n; j += 128) {
+                const double g0 = ldcg_d(trow + j), g1 = ldcg_d(trow + j + 32), g2 = ldcg_d(trow + j + 64),
+                             g3 = ldcg_d(trow + j + 96);
+                const double y0 = ldcg_d(a.y + j), y1 = ldcg_d(a.y + j + 32), y2 = ldcg_d(a.y + j + 64),
+                             y3 = ldcg_d(a.y + j + 96);
+                s0 = fma(g0, y0, s0);
+                s1 = fma(g1, y1, s1);
+                s2 = fma(g2, y2, s2);
+                s3 = fma(g3, y3, s3);
             }
-            scol[warp][lane] = s;
-            __syncthreads();
-            if (n_jc == 1) {  // one row tile: the column sums are complete here
-                if (warp == 0 && k < n) {
-                    const double t = ((scol[0][lane] + scol[1][lane]) + scol[2][lane]) + scol[3][lane];
-                    const double g = -t / l;
-                    Grow[k] = g;
-                    double4 al = ldcg_d4(&a.alpha[k]);
-                    al.x = fma(wn0, g, al.x);
-                    al.y = fma(wn1, g, al.y);
-                    al.z = fma(wn2, g, al.z);
-                    a.alpha[k] = al;
-                }
-                __syncthreads();
-                continue;
+            for (; j < n; j += 32) s0 = fma(ldcg_d(trow + j), ldcg_d(a.y + j), s0);
+            const double t = warp_sum_d((s0 + s1) + (s2 + s3));
+            if (lane == 0) {
+                const double g = -t / l;
+                Grow[k] = g;
+                a.Gt[(size_t)k * a.cap + n] = g;
+                double4 al = ldcg_d4(&a.alpha[k]);
+                al.x = fma(wn0, g, al.x);
+                al.y = fma(wn1, g, al.y);
+                al.z = fma(wn2, g, al.z);
+                a.alpha[k] = al;
             }
-            if (warp == 0 && k < n)
-                a.gpart[(size_t)jc * a.cap + k] = ((scol[0][lane] + scol[1][lane]) + scol[2][lane]) + scol[3][lane];
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) s_last = atomicAdd(&a.kt_done[kt], 1u) == (unsigned)(n_jc - 1);
-            __syncthreads();
-            if (s_last && warp == 0) {
-                __threadfence();
-                if (k < n) {
-                    double t = 0.0;
-                    for (int q = 0; q < n_jc; ++q) t += ldcg_d(&a.gpart[(size_t)q * a.cap + k]);
-                    const double g = -t / l;
-                    Grow[k] = g;
-                    double4 al = ldcg_d4(&a.alpha[k]);
-                    al.x = fma(wn0, g, al.x);
-                    al.y = fma(wn1, g, al.y);
-                    al.z = fma(wn2, g, al.z);
-                    a.alpha[k] = al;
-                }
-                if (lane == 0) a.kt_done[kt] = 0;
-            }
-            __syncthreads();
         }
         if (first_block) a.st->n = n + 1;
         RBFD_SYNC(3)
@@ -548,17 +574,19 @@ void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
     a.nb_cnt = m->d_nb_cnt;
     a.nb_list = m->d_nb_list;
     a.cx = m->d_cx;
+    a.cdf = m->d_cdf;
     a.alpha = m->d_alpha;
     a.w = m->d_w;
     a.cid = m->d_cid;
     a.G = m->d_G;
+    a.Gt = m->d_Gt;
     a.phi = m->d_phi;
     a.y = m->d_y;
     a.red = m->d_pred;
-    a.gpart = m->d_pgpart;
+    a.nz_k = m->d_nz_k;
+    a.nz_v = m->d_nz_v;
     a.part = m->d_part;
     a.pb_done = m->d_pb_done;
-    a.kt_done = m->d_kt_done;
     a.pb_key = m->d_pb_key;
     a.pb_idx = m->d_pb_idx;
     a.bar = m->d_bar;

@@ -76,13 +76,13 @@ namespace rbfd {
 size_t mesh_footprint(int dim, int64_t n_s, int64_t n_v, int64_t cap) {
     (void)dim;
     const int64_t n_pb = (n_s + kPB - 1) / kPB;
-    const int64_t nch = std::max<int64_t>(1, (608 + n_pb - 1) / n_pb);
+    const int64_t nch = std::max<int64_t>(128, (608 + n_pb - 1) / n_pb);
     size_t b = 0;
-    b += 8ull * cap * cap;                          // G
+    b += 16ull * cap * cap;                         // G and its transpose
     b += 4ull * n_pb * cap;                         // block lists
     b += (size_t)n_s * (4 * 32 + 2 * 16 + 16);      // sorted surface, targets, error, df coords, perms
     b += (size_t)nch * n_s * 32;                    // sweep partials
-    b += (size_t)cap * (6 * 32 + 8 * 8) + 8ull * (cap / 128 + 2) * cap + 32ull * (cap / 256 + 2) * cap;
+    b += (size_t)cap * (6 * 32 + 8 * 8) + 32ull * (cap / 256 + 2) * cap;
     b += (size_t)n_v * (32 * 3 + 4 * 6);            // registered + working volume buffers
     return b + (64ull << 20);                       // small buffers and pool rounding
 }
@@ -279,7 +279,7 @@ int rbfd_server_add_mesh(rbfd_server *S, int dim, int64_t n_s, const double *xyz
         M->eps = eps;
         M->D = D;
         M->k = k;
-        M->footprint = rbfd::mesh_footprint(dim, n_s, n_v, std::min<int64_t>(n_s, 16384));
+        M->footprint = rbfd::mesh_footprint(dim, n_s, n_v, std::min<int64_t>(n_s, 32768));
         if (M->footprint > (size_t)S->opt.mem_budget_bytes)
             rbfd::fail(RBFD_ENOMEM, "rbfd_server_add_mesh: one instance of this mesh exceeds the memory budget");
         std::lock_guard<std::mutex> lk(S->mu);
