@@ -73,6 +73,8 @@ def _bind(path: str):
                                ctypes.c_int64, dp, ctypes.c_int64, dp, dp, dp, ctypes.c_int]
     lib.orc_max_threads.restype = ctypes.c_int
     lib.orc_max_threads.argtypes = []
+    lib.orc_wall_distance.restype = None
+    lib.orc_wall_distance.argtypes = [ctypes.c_int, ctypes.c_int64, dp, ctypes.c_int64, dp, dp, ctypes.c_int]
     return lib
 
 
@@ -243,6 +245,17 @@ def deform(res: GreedyResult, xyz_s, R, xyz_v, d_v, k: float, D: float, basis="C
     if rc != OK:
         raise RuntimeError(f"oracle deform failed with status {rc}")
     return out
+
+
+def wall_distance(xyz_s, xyz_v, n_threads=1, lib=None):
+    """Distance from each volume point to its nearest surface point (brute force)."""
+    lib = lib or _load()
+    xyz_s = _f64(xyz_s)
+    xyz_v = _f64(xyz_v)
+    d = np.zeros(xyz_v.shape[0])
+    lib.orc_wall_distance(xyz_s.shape[1], xyz_s.shape[0], _dp(xyz_s), xyz_v.shape[0], _dp(xyz_v), _dp(d),
+                          int(n_threads))
+    return d
 
 
 class Variant:

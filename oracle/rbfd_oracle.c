@@ -427,3 +427,25 @@ int orc_max_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------ wall distance */
+
+/* d(r) of Section 4 for each volume point: the distance to the nearest surface
+ * point (the paper takes d as given; this is its plainest definition on a
+ * point cloud), by brute force over every surface point. */
+void orc_wall_distance(int dim, int64_t n_s, const double *xyz_s, int64_t n_v, const double *xyz_v, double *d,
+                       int n_threads)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(n_threads > 0 ? n_threads : 1)
+#endif
+    for (int64_t v = 0; v < n_v; ++v) {
+        double best = INFINITY;
+        for (int64_t i = 0; i < n_s; ++i) {
+            double r = dist(xyz_v + v * dim, xyz_s + i * dim, dim);
+            if (r < best) best = r;
+        }
+        d[v] = best;
+    }
+    (void)n_threads;
+}

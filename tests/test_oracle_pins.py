@@ -290,6 +290,26 @@ def pin_deform(o, case):
     return bad
 
 
+def pin_wall_distance(o):
+    """Brute-force nearest-surface-point distance against a k-d tree (scipy)
+    and against a closed form: points on a regular polygon inscribed in the
+    unit circle seen from the centre are all at distance 1."""
+    from scipy.spatial import cKDTree
+
+    bad = []
+    for dim, case in ((2, tiny_airfoil(n=64, layers=8)), (3, tiny_wing())):
+        d = o.wall_distance(case.xyz_s, case.xyz_v.astype(np.float64))
+        want, _ = cKDTree(case.xyz_s).query(case.xyz_v.astype(np.float64))
+        if np.abs(d - want).max() > 1e-12:
+            bad.append(f"{dim}D wall distance differs from the k-d tree")
+    t = np.linspace(0, 2 * np.pi, 17)[:-1]
+    ring = np.stack([np.cos(t), np.sin(t)], axis=1)
+    d = o.wall_distance(ring, np.zeros((1, 2)))
+    if abs(d[0] - 1.0) > 1e-15:
+        bad.append("distance from the centre of a unit ring is not 1")
+    return bad
+
+
 def all_pins(o):
     bad = []
     bad += pin_table1(o)
@@ -305,6 +325,7 @@ def all_pins(o):
     bad += pin_dense_limit(o)
     bad += pin_deform(o, tiny_airfoil_k5())
     bad += pin_deform(o, tiny_wing())
+    bad += pin_wall_distance(o)
     return bad
 
 
@@ -366,6 +387,10 @@ def test_deform_airfoil():
 
 def test_deform_wing():
     assert pin_deform(oracle, tiny_wing()) == []
+
+
+def test_wall_distance_vs_kdtree_and_closed_form():
+    assert pin_wall_distance(oracle) == []
 
 
 def test_incremental_equals_scratch():
@@ -445,6 +470,8 @@ MUTATIONS = {
     "distance drops z": ("for (int k = 0; k < dim; ++k) {\n        double d = a[k] - b[k];",
                          "for (int k = 0; k < 2; ++k) {\n        double d = a[k] - b[k];"),
     "first control not point 0": ("int64_t first = 0;", "int64_t first = 1;"),
+    "wall distance skips the last point": ("for (int64_t i = 0; i < n_s; ++i) {\n            double r = dist(",
+                                           "for (int64_t i = 0; i < n_s - 1; ++i) {\n            double r = dist("),
 }
 
 
