@@ -146,6 +146,11 @@ typedef struct rbfd_stats {
     /* profile mode: block 0 of the persistent launch, summed over steps, in ms:
        [2p] = work of phase p (sweep, argmax+phi, G phi, G row), [2p+1] = wait at its barrier */
     double persist_phase_ms[8];
+    /* wall distance queries (rbfd_wall_distance, or deform/set_volume without d_v) */
+    double wall_ms;              /* event time of the query kernels (opt.profile = 1) */
+    int64_t wall_launches;
+    int64_t wall_pairs_search;   /* point pairs scanned by the FP32 search pass */
+    int64_t wall_pairs_exact;    /* point pairs scanned by the exact pass */
 } rbfd_stats;
 
 int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st);
@@ -160,7 +165,9 @@ int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st);
  *
  *   n_v    number of volume points (0 allowed)
  *   xyz_v  [n_v][dim] volume coordinates (float)
- *   d_v    [n_v] wall distance of each volume point (float, negative read as 0)
+ *   d_v    [n_v] wall distance of each volume point (float, negative read as 0),
+ *          or NULL: the library computes it (as rbfd_wall_distance, needed
+ *          and computed only below max_l D_l)
  *   D, k   support distance and volume reduction factor (>= 0; not both 0)
  *   out    [n_v][dim] receives the displacement of each volume point (float)
  *
@@ -177,7 +184,8 @@ int rbfd_deform(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v,
  *   keeps the Morton order, point blocks and workspace; the previous greedy
  *   results are dropped (run rbfd_greedy again).
  * rbfd_set_volume -- register a volume mesh ([n_v][dim] float coordinates,
- *   [n_v] wall distances) once; it is packed and Morton-sorted on the device
+ *   [n_v] wall distances, or NULL to compute them once with
+ *   rbfd_wall_distance) once; it is packed and Morton-sorted on the device
  *   and kept until the next call or rbfd_destroy.
  * rbfd_deform_volume -- rbfd_deform on the registered volume: out [n_v][dim].
  * Pointer kinds follow inputs_on_device.  Errors as for rbfd_deform.
@@ -186,9 +194,29 @@ int rbfd_set_displacement(rbfd_mesh *m, const double *dS);
 int rbfd_set_volume(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v);
 int rbfd_deform_volume(rbfd_mesh *m, double D, double k, float *out);
 
-/* Same as rbfd_deform with double coordinates, distances and output. */
+/* Same as rbfd_deform with double coordinates, distances (or NULL) and output. */
 int rbfd_deform_f64(rbfd_mesh *m, int64_t n_v, const double *xyz_v, const double *d_v, double D, double k,
                     double *out);
+
+/*
+ * rbfd_wall_distance -- the wall distance d of Section 4 (the distance of a
+ * volume point from the surface, the argument of psi in Eq. 23, which the
+ * paper takes as given): for each volume point r_v,
+ *     d_out[v] = min_i |r_v - r_s,i|
+ * over the mesh's n_s surface points (as passed to rbfd_create), with the
+ * distance evaluated in FP64 as sqrt(dx*dx + dy*dy (+ dz*dz)), each operation
+ * rounded once, in axis order.  The result is exact in that sense: the same
+ * value as a plain brute-force minimum in FP64, bit for bit.  Needs no greedy.
+ *
+ *   n_v    number of volume points (0 allowed)
+ *   xyz_v  [n_v][dim] coordinates: float (rbfd_wall_distance) or double
+ *          (rbfd_wall_distance_f64); host or device per inputs_on_device
+ *   d_out  [n_v] result (double), caller order
+ *
+ * Errors: RBFD_EINVAL (NULL arrays, n_v < 0 or >= 2^31), RBFD_ENOMEM, RBFD_ECUDA.
+ */
+int rbfd_wall_distance(rbfd_mesh *m, int64_t n_v, const float *xyz_v, double *d_out);
+int rbfd_wall_distance_f64(rbfd_mesh *m, int64_t n_v, const double *xyz_v, double *d_out);
 
 /*
  * rbfd_deform_noalloc -- the volume update of rbfd_deform for callers that
@@ -276,7 +304,8 @@ int rbfd_server_create(rbfd_server **out, const rbfd_server_options *opt);
 
 /*
  * Register a mesh: surface points xyz_s [n_s][dim] (double), volume points
- * xyz_v [n_v][dim] with wall distances d_v [n_v] (float), the greedy levels
+ * xyz_v [n_v][dim] with wall distances d_v [n_v] (float; NULL: computed on the
+ * device when an instance is made), the greedy levels
  * (R [n_levels], eps) and the support distance rule (D, k) of rbfd_deform.
  * Host pointers; the server copies them.  *mesh_id names the mesh in rbfd_submit.
  */

@@ -221,7 +221,7 @@ void mesh_free(rbfd_mesh *m) {
                     m->d_nb_cnt, m->d_nb_list, m->d_part, m->d_pb_done, m->d_pb_key, m->d_pb_idx, m->d_pairs,
                     m->d_st, m->d_vin, m->d_vpos, m->d_vorig, m->d_vflag, m->d_vscan, m->d_vlist, m->d_vkeys,
                     m->d_vacc, m->d_vio, m->d_misc, m->d_bbox, m->d_bar, m->d_pred, m->d_Gt,
-                    m->d_nz_k, m->d_nz_v, m->d_phase_ns, m->d_vreg, m->d_vreg_orig};
+                    m->d_nz_k, m->d_nz_v, m->d_phase_ns, m->d_vreg, m->d_vreg_orig, m->d_pb_fbox};
     for (void *p : ptrs) dfree(p);
     m->sort.release();
     m->prof.release();
@@ -412,7 +412,7 @@ int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st) {
     return guarded([&] {
         if (!m || !st) rbfd::fail(RBFD_EINVAL, "rbfd_get_stats: NULL argument");
         RBFD_CUDA(cudaSetDevice(m->device));
-        unsigned long long pr[4] = {0, 0, 0, 0};
+        unsigned long long pr[6] = {0, 0, 0, 0, 0, 0};
         RBFD_CUDA(cudaStreamSynchronize(m->stream));
         RBFD_CUDA(cudaMemcpy(pr, m->d_pairs, sizeof(pr), cudaMemcpyDeviceToHost));
         m->prof.flush();
@@ -431,6 +431,10 @@ int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st) {
         st->vol_launches = m->prof.launches[rbfd::kProfVol];
         st->persist_ms = m->prof.ms[rbfd::kProfPersist];
         st->persist_launches = m->prof.launches[rbfd::kProfPersist];
+        st->wall_ms = m->prof.ms[rbfd::kProfWall];
+        st->wall_launches = m->prof.launches[rbfd::kProfWall];
+        st->wall_pairs_search = (int64_t)pr[4];
+        st->wall_pairs_exact = (int64_t)pr[5];
         unsigned long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         if (m->d_phase_ns) RBFD_CUDA(cudaMemcpy(ph, m->d_phase_ns, sizeof(ph), cudaMemcpyDeviceToHost));
         for (int q = 0; q < 8; ++q) st->persist_phase_ms[q] = ph[q] * 1e-6;
@@ -442,14 +446,14 @@ static int deform_common(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const voi
     return guarded([&] {
         if (!m) rbfd::fail(RBFD_EINVAL, "rbfd_deform: NULL mesh");
         if (n_v < 0 || n_v > ((int64_t)1 << 31) - 1) rbfd::fail(RBFD_EINVAL, "rbfd_deform: n_v out of range");
-        if (n_v > 0 && (!xyz_v || !d_v || !out)) rbfd::fail(RBFD_EINVAL, "rbfd_deform: NULL array");
+        if (n_v > 0 && (!xyz_v || !out)) rbfd::fail(RBFD_EINVAL, "rbfd_deform: NULL array");
         if (!(D >= 0.0) || !(k >= 0.0) || !std::isfinite(D) || !std::isfinite(k))
             rbfd::fail(RBFD_EINVAL, "rbfd_deform: D and k must be finite and >= 0");
         if (D == 0.0 && k == 0.0) rbfd::fail(RBFD_EINVAL, "rbfd_deform: D and k cannot both be 0");
         if (!m->greedy_done) rbfd::fail(RBFD_ESTATE, "rbfd_deform: run rbfd_greedy first");
         RBFD_CUDA(cudaSetDevice(m->device));
         if (m->opt.inputs_on_device && n_v > 0 &&
-            (!is_device_ptr(xyz_v) || !is_device_ptr(d_v) || !is_device_ptr(out)))
+            (!is_device_ptr(xyz_v) || (d_v && !is_device_ptr(d_v)) || !is_device_ptr(out)))
             rbfd::fail(RBFD_EINVAL, "rbfd_deform: inputs_on_device set but arrays are not device memory");
         rbfd::deform_run(m, n_v, xyz_v, d_v, f64, D, k, out);
     });
@@ -469,9 +473,9 @@ int rbfd_set_volume(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *
     return guarded([&] {
         if (!m) rbfd::fail(RBFD_EINVAL, "rbfd_set_volume: NULL mesh");
         if (n_v < 0 || n_v > ((int64_t)1 << 31) - 1) rbfd::fail(RBFD_EINVAL, "rbfd_set_volume: n_v out of range");
-        if (n_v > 0 && (!xyz_v || !d_v)) rbfd::fail(RBFD_EINVAL, "rbfd_set_volume: NULL array");
+        if (n_v > 0 && !xyz_v) rbfd::fail(RBFD_EINVAL, "rbfd_set_volume: NULL array");
         RBFD_CUDA(cudaSetDevice(m->device));
-        if (m->opt.inputs_on_device && n_v > 0 && (!is_device_ptr(xyz_v) || !is_device_ptr(d_v)))
+        if (m->opt.inputs_on_device && n_v > 0 && (!is_device_ptr(xyz_v) || (d_v && !is_device_ptr(d_v))))
             rbfd::fail(RBFD_EINVAL, "rbfd_set_volume: inputs_on_device set but arrays are not device memory");
         rbfd::volume_register(m, n_v, xyz_v, d_v);
     });
@@ -489,6 +493,26 @@ int rbfd_deform_volume(rbfd_mesh *m, double D, double k, float *out) {
             rbfd::fail(RBFD_EINVAL, "rbfd_deform_volume: inputs_on_device set but out is not device memory");
         rbfd::deform_registered(m, D, k, out);
     });
+}
+
+static int wall_common(rbfd_mesh *m, int64_t n_v, const void *xyz_v, double *d_out, bool f64) {
+    return guarded([&] {
+        if (!m) rbfd::fail(RBFD_EINVAL, "rbfd_wall_distance: NULL mesh");
+        if (n_v < 0 || n_v > ((int64_t)1 << 31) - 1) rbfd::fail(RBFD_EINVAL, "rbfd_wall_distance: n_v out of range");
+        if (n_v > 0 && (!xyz_v || !d_out)) rbfd::fail(RBFD_EINVAL, "rbfd_wall_distance: NULL array");
+        RBFD_CUDA(cudaSetDevice(m->device));
+        if (m->opt.inputs_on_device && n_v > 0 && (!is_device_ptr(xyz_v) || !is_device_ptr(d_out)))
+            rbfd::fail(RBFD_EINVAL, "rbfd_wall_distance: inputs_on_device set but arrays are not device memory");
+        rbfd::wall_distance_run(m, n_v, xyz_v, f64, d_out);
+    });
+}
+
+int rbfd_wall_distance(rbfd_mesh *m, int64_t n_v, const float *xyz_v, double *d_out) {
+    return wall_common(m, n_v, xyz_v, d_out, false);
+}
+
+int rbfd_wall_distance_f64(rbfd_mesh *m, int64_t n_v, const double *xyz_v, double *d_out) {
+    return wall_common(m, n_v, xyz_v, d_out, true);
 }
 
 int rbfd_deform(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v, double D, double k, float *out) {

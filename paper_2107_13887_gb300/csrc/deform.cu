@@ -37,13 +37,13 @@ __global__ void k_vol_pack(const void *__restrict__ xyz, const void *__restrict_
         x = p[0];
         y = p[1];
         if (dim == 3) z = p[2];
-        w = static_cast<const double *>(d)[i];
+        w = d ? static_cast<const double *>(d)[i] : 0.0;
     } else {
         const float *p = static_cast<const float *>(xyz) + i * dim;
         x = p[0];
         y = p[1];
         if (dim == 3) z = p[2];
-        w = static_cast<const float *>(d)[i];
+        w = d ? static_cast<const float *>(d)[i] : 0.0;
     }
     out[i] = make_double4(x, y, z, w < 0.0 ? 0.0 : w);
 }
@@ -139,6 +139,13 @@ __global__ void k_gather_u32(const uint32_t *__restrict__ src, const uint32_t *_
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     out[i] = src[idx[i]];
+}
+
+__global__ void k_scatter_d(const double *__restrict__ d, const uint32_t *__restrict__ orig, int64_t n,
+                            double *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[orig[i]] = d[i];
 }
 
 __global__ void k_scatter_out(const double4 *__restrict__ acc, const uint32_t *__restrict__ orig, int64_t n,
@@ -395,6 +402,25 @@ void reserve_volume(rbfd_mesh *m, size_t n) {
     m->vol_cap = n;
 }
 
+// Morton order of n packed points vin: sorted copy into vsorted, caller
+// index of each sorted point into orig.  Uses the mesh's key buffer.
+void morton_order(rbfd_mesh *m, int64_t n, const double4 *vin, double4 *vsorted, uint32_t *orig) {
+    cudaStream_t st = m->stream;
+    const int dim = m->dim;
+    const int nbb = std::min<int>(cdiv(n, 256), 256);
+    k_bbox_partial_v<<<nbb, 256, 0, st>>>(vin, n, m->d_red);
+    k_bbox_reduce<<<1, 32, 0, st>>>(m->d_red, nbb, m->d_bbox);
+    double bb[6];
+    RBFD_CUDA(cudaMemcpyAsync(bb, m->d_bbox, sizeof(bb), cudaMemcpyDeviceToHost, st));
+    RBFD_CUDA(cudaStreamSynchronize(st));
+    morton_keys_f64(vin, n, dim, make_double3(bb[0], bb[1], bb[2]), make_double3(bb[3], bb[4], bb[5]), m->d_vkeys,
+                    orig, st);
+    radix_sort_pairs(m->d_vkeys, orig, (size_t)n, dim == 2 ? 32 : 30, m->sort, st);
+    k_gather_vol<<<cdiv(n, 256), 256, 0, st>>>(vin, orig, n, vsorted);
+    RBFD_CUDA(cudaGetLastError());
+    m->stats.launches += 4;
+}
+
 // Steps (3) and (4) of the volume update for nV Morton-sorted points vpos
 // (caller indices vorig): per level, compaction to d < D_l and the fused
 // evaluation into the accumulator; then the scatter into dout (caller order).
@@ -482,16 +508,37 @@ void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, b
             void *sd = base + (size_t)n_v * dim * es;
             dout = base + (size_t)n_v * dim * es + (((size_t)n_v * es + 255) / 256) * 256;
             RBFD_CUDA(cudaMemcpyAsync(sx, xyz_v, (size_t)n_v * dim * es, cudaMemcpyHostToDevice, st));
-            RBFD_CUDA(cudaMemcpyAsync(sd, d_v, (size_t)n_v * es, cudaMemcpyHostToDevice, st));
+            if (d_v) RBFD_CUDA(cudaMemcpyAsync(sd, d_v, (size_t)n_v * es, cudaMemcpyHostToDevice, st));
             dx = sx;
-            dd = sd;
+            dd = d_v ? sd : nullptr;
         }
         RBFD_CUDA(cudaMemsetAsync(dout, 0, (size_t)n_v * dim * es, st));
     }
     double4 *vin = reinterpret_cast<double4 *>(m->d_vin);
     double4 *vpos = reinterpret_cast<double4 *>(m->d_vpos);
     int64_t nV = 0;
-    if (n_v > 0 && Dmax > 0.0) {
+    if (n_v > 0 && Dmax > 0.0 && !dd) {
+        // No wall distances given: Morton-sort every point, compute d(r) on
+        // the device (needed only below max_l D_l, so capped there), then
+        // keep d < max_l D_l in Morton order (steps (1) and (2) in one).
+        k_vol_pack<<<cdiv(n_v, 256), 256, 0, st>>>(dx, nullptr, n_v, dim, f64 ? 1 : 0, vin);
+        morton_order(m, n_v, vin, vpos, m->d_vorig);
+        wall_distance_sorted(m, n_v, vpos, Dmax, nullptr);
+        k_flag_below<<<cdiv(n_v, 256), 256, 0, st>>>(vpos, nullptr, n_v, Dmax, m->d_vflag);
+        exclusive_scan_u32(m->d_vflag, m->d_vscan, (size_t)n_v, &m->d_misc[4], m->sort, st);
+        k_compact<<<cdiv(n_v, 256), 256, 0, st>>>(m->d_vflag, m->d_vscan, n_v, m->d_vlist);
+        uint32_t cnt = 0;
+        RBFD_CUDA(cudaMemcpyAsync(&cnt, &m->d_misc[4], sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        RBFD_CUDA(cudaStreamSynchronize(st));
+        const int64_t nk = cnt;
+        if (nk > 0) {
+            k_gather_vol<<<cdiv(nk, 256), 256, 0, st>>>(vpos, m->d_vlist, nk, vin);  // kept points, sorted
+            k_gather_u32<<<cdiv(nk, 256), 256, 0, st>>>(m->d_vorig, m->d_vlist, nk, m->d_vflag);
+            RBFD_CUDA(cudaMemcpyAsync(m->d_vorig, m->d_vflag, sizeof(uint32_t) * nk, cudaMemcpyDeviceToDevice, st));
+            deform_levels(m, nk, vin, m->d_vorig, Dl.data(), L, dout, f64);
+        }
+        m->stats.launches += 6;  // pack, flags, compaction, gathers x2, scatter
+    } else if (n_v > 0 && Dmax > 0.0) {
         k_vol_pack<<<cdiv(n_v, 256), 256, 0, st>>>(dx, dd, n_v, dim, f64 ? 1 : 0, vin);
         // (1) volume point reduction: d < max_l D_l
         k_flag_below<<<cdiv(n_v, 256), 256, 0, st>>>(vin, nullptr, n_v, Dmax, m->d_vflag);
@@ -550,29 +597,58 @@ void volume_register(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float 
     if (!m->opt.inputs_on_device) {
         stage = dalloc<float>((size_t)n_v * (dim + 1), "volume staging");
         RBFD_CUDA(cudaMemcpyAsync(stage, xyz_v, sizeof(float) * n_v * dim, cudaMemcpyHostToDevice, st));
-        RBFD_CUDA(cudaMemcpyAsync(stage + (size_t)n_v * dim, d_v, sizeof(float) * n_v, cudaMemcpyHostToDevice, st));
+        if (d_v)
+            RBFD_CUDA(cudaMemcpyAsync(stage + (size_t)n_v * dim, d_v, sizeof(float) * n_v, cudaMemcpyHostToDevice,
+                                      st));
         dx = stage;
-        dd = stage + (size_t)n_v * dim;
+        dd = d_v ? stage + (size_t)n_v * dim : nullptr;
     }
     double4 *vin = reinterpret_cast<double4 *>(m->d_vin);
     k_vol_pack<<<cdiv(n_v, 256), 256, 0, st>>>(dx, dd, n_v, dim, 0, vin);
-    const int nbb = std::min<int>(cdiv(n_v, 256), 256);
-    k_bbox_partial_v<<<nbb, 256, 0, st>>>(vin, n_v, m->d_red);
-    k_bbox_reduce<<<1, 32, 0, st>>>(m->d_red, nbb, m->d_bbox);
-    double bb[6];
-    RBFD_CUDA(cudaMemcpyAsync(bb, m->d_bbox, sizeof(bb), cudaMemcpyDeviceToHost, st));
-    RBFD_CUDA(cudaStreamSynchronize(st));
     m->d_vreg = dalloc<double4>((size_t)n_v, "registered volume");
     m->d_vreg_orig = dalloc<uint32_t>((size_t)n_v, "registered volume order");
-    morton_keys_f64(vin, n_v, dim, make_double3(bb[0], bb[1], bb[2]), make_double3(bb[3], bb[4], bb[5]), m->d_vkeys,
-                    m->d_vreg_orig, st);
-    radix_sort_pairs(m->d_vkeys, m->d_vreg_orig, (size_t)n_v, dim == 2 ? 32 : 30, m->sort, st);
-    k_gather_vol<<<cdiv(n_v, 256), 256, 0, st>>>(vin, m->d_vreg_orig, n_v, m->d_vreg);
-    RBFD_CUDA(cudaGetLastError());
+    morton_order(m, n_v, vin, m->d_vreg, m->d_vreg_orig);
+    // no wall distances given: d(r) of every point, computed once (later
+    // displacements may need any D_l)
+    if (!dd) wall_distance_sorted(m, n_v, m->d_vreg, INFINITY, nullptr);
     RBFD_CUDA(cudaStreamSynchronize(st));
     dfree(stage);
     m->vreg_n = n_v;
-    m->stats.launches += 5;
+    m->stats.launches += 1;
+}
+
+// rbfd_wall_distance: pack, Morton-sort, query, scatter back to the caller's order.
+void wall_distance_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, bool f64, double *out) {
+    cudaStream_t st = m->stream;
+    const int dim = m->dim;
+    if (n_v == 0) return;
+    RBFD_CUDA(cudaEventRecord(m->ev0, st));
+    reserve_volume(m, (size_t)n_v);
+    const size_t es = f64 ? sizeof(double) : sizeof(float);
+    const void *dx = xyz_v;
+    double *dout = out;
+    void *stage = nullptr;
+    if (!m->opt.inputs_on_device) {
+        const size_t xb = ((size_t)n_v * dim * es + 255) / 256 * 256;
+        stage = dmalloc(xb + sizeof(double) * (size_t)n_v, "wall distance staging");
+        RBFD_CUDA(cudaMemcpyAsync(stage, xyz_v, (size_t)n_v * dim * es, cudaMemcpyHostToDevice, st));
+        dx = stage;
+        dout = reinterpret_cast<double *>(static_cast<char *>(stage) + xb);
+    }
+    double4 *vin = reinterpret_cast<double4 *>(m->d_vin);
+    double4 *vpos = reinterpret_cast<double4 *>(m->d_vpos);
+    k_vol_pack<<<cdiv(n_v, 256), 256, 0, st>>>(dx, nullptr, n_v, dim, f64 ? 1 : 0, vin);
+    morton_order(m, n_v, vin, vpos, m->d_vorig);
+    double *dsorted = reinterpret_cast<double *>(m->d_vacc);
+    wall_distance_sorted(m, n_v, vpos, INFINITY, dsorted);
+    k_scatter_d<<<cdiv(n_v, 256), 256, 0, st>>>(dsorted, m->d_vorig, n_v, dout);
+    RBFD_CUDA(cudaGetLastError());
+    m->stats.launches += 2;
+    if (dout != out) RBFD_CUDA(cudaMemcpyAsync(out, dout, sizeof(double) * n_v, cudaMemcpyDeviceToHost, st));
+    RBFD_CUDA(cudaEventRecord(m->ev1, st));
+    RBFD_CUDA(cudaEventSynchronize(m->ev1));
+    dfree(stage);
+    m->prof.flush();
 }
 
 void deform_registered(rbfd_mesh *m, double D, double k, float *out) {

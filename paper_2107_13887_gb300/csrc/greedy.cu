@@ -949,8 +949,8 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     RBFD_CUDA(cudaMemsetAsync(m->d_pb_done, 0, sizeof(unsigned int) * m->n_pb, st));
     m->d_pb_key = dalloc<double>(std::max(m->n_pb, 1024), "block keys");
     m->d_pb_idx = dalloc<int>(std::max(m->n_pb, 1024), "block argmax");
-    m->d_pairs = dalloc<unsigned long long>(4, "pair counters");
-    RBFD_CUDA(cudaMemsetAsync(m->d_pairs, 0, 4 * sizeof(unsigned long long), st));
+    m->d_pairs = dalloc<unsigned long long>(6, "pair counters");
+    RBFD_CUDA(cudaMemsetAsync(m->d_pairs, 0, 6 * sizeof(unsigned long long), st));
     m->d_st = dalloc<GreedyState>(1, "greedy state");
     RBFD_CUDA(cudaMemsetAsync(m->d_st, 0, sizeof(GreedyState), st));
     m->d_bar = dalloc<GridBarrier>(1, "grid barrier");

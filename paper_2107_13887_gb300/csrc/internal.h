@@ -89,7 +89,7 @@ struct Level {
 };
 
 // Optional per-kernel-class timing with CUDA events on the mesh's stream.
-enum ProfKind { kProfSweep = 0, kProfGrow = 1, kProfVol = 2, kProfPersist = 3, kProfKinds = 4 };
+enum ProfKind { kProfSweep = 0, kProfGrow = 1, kProfVol = 2, kProfPersist = 3, kProfWall = 4, kProfKinds = 5 };
 
 struct Profiler {
     bool on = false;
@@ -99,8 +99,8 @@ struct Profiler {
         cudaEvent_t a, b;
     };
     std::vector<Pending> pend;
-    double ms[kProfKinds] = {0, 0, 0, 0};
-    int64_t launches[kProfKinds] = {0, 0, 0, 0};
+    double ms[kProfKinds] = {};
+    int64_t launches[kProfKinds] = {};
     cudaEvent_t get();
     cudaEvent_t begin(cudaStream_t st);            // records and returns the start event (or nullptr)
     void end(int kind, cudaEvent_t a, cudaStream_t st, int n_launches);
@@ -131,6 +131,7 @@ struct rbfd_mesh {
     double4 *d_E = nullptr;      // error of the last confirm sweep
     double4 *d_pb_lo = nullptr, *d_pb_hi = nullptr, *d_pb_org = nullptr;
     float4 *d_xs_hi = nullptr, *d_xs_lo = nullptr;  // coordinates relative to the block origin (df)
+    float4 *d_pb_fbox = nullptr;  // [4][n_pb] FP32 block boxes for the wall distance (made on first use)
 
     // greedy workspace
     int cap = 0;
@@ -158,7 +159,8 @@ struct rbfd_mesh {
     unsigned int *d_pb_done = nullptr;
     double *d_pb_key = nullptr;
     int *d_pb_idx = nullptr;
-    unsigned long long *d_pairs = nullptr;  // [4]: surface sweep useful, visited; volume useful, visited
+    unsigned long long *d_pairs = nullptr;  // [6]: surface sweep useful, visited; volume useful, visited;
+                                            //     wall distance search, exact pass
     rbfd::GreedyState *d_st = nullptr;
     rbfd::GreedyState *h_st = nullptr;  // pinned
     // persistent engine
@@ -203,4 +205,8 @@ void mesh_set_displacement(rbfd_mesh *m, const double *dS);
 void volume_register(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v);
 void deform_registered(rbfd_mesh *m, double D, double k, float *out);
 void mesh_free(rbfd_mesh *m);
+// wall distance of n Morton-sorted points: min(d, cap) into d_out (sorted
+// order) or, with d_out null, into vpos[i].w
+void wall_distance_sorted(rbfd_mesh *m, int64_t n, double4 *vpos, double cap, double *d_out);
+void wall_distance_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, bool f64, double *out);
 }  // namespace rbfd

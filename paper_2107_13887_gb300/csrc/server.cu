@@ -113,7 +113,7 @@ static void run_request(rbfd_server *S, uint64_t ticket, rbfd_mesh *inst) {
             int rc = rbfd_create(&inst, M.dim, M.n_s, M.xyz_s.data(), dS.data(), (int)M.R.size(), M.R.data(), M.eps,
                                  &o);
             if (rc != RBFD_OK) fail(rc, std::string("server: creating a mesh instance: ") + rbfd_last_error());
-            volume_register(inst, M.n_v, M.xyz_v.data(), M.d_v.data());
+            volume_register(inst, M.n_v, M.xyz_v.data(), M.d_v.empty() ? nullptr : M.d_v.data());
         } else {
             mesh_set_displacement(inst, dS.data());
         }
@@ -263,7 +263,7 @@ int rbfd_server_add_mesh(rbfd_server *S, int dim, int64_t n_s, const double *xyz
         if (dim != 2 && dim != 3) rbfd::fail(RBFD_EINVAL, "rbfd_server_add_mesh: dim must be 2 or 3");
         if (n_s < 1 || !xyz_s || n_levels < 1 || n_levels > 64 || !R || !(eps > 0.0 && eps < 1.0))
             rbfd::fail(RBFD_EINVAL, "rbfd_server_add_mesh: bad surface or level arguments");
-        if (n_v < 0 || (n_v > 0 && (!xyz_v || !d_v))) rbfd::fail(RBFD_EINVAL, "rbfd_server_add_mesh: bad volume");
+        if (n_v < 0 || (n_v > 0 && !xyz_v)) rbfd::fail(RBFD_EINVAL, "rbfd_server_add_mesh: bad volume");
         if (!(D >= 0.0) || !(k >= 0.0) || (D == 0.0 && k == 0.0))
             rbfd::fail(RBFD_EINVAL, "rbfd_server_add_mesh: D and k must be >= 0 and not both 0");
         for (int l = 0; l < n_levels; ++l)
@@ -275,7 +275,7 @@ int rbfd_server_add_mesh(rbfd_server *S, int dim, int64_t n_s, const double *xyz
         M->xyz_s.assign(xyz_s, xyz_s + n_s * dim);
         M->R.assign(R, R + n_levels);
         M->xyz_v.assign(xyz_v, xyz_v + n_v * dim);
-        M->d_v.assign(d_v, d_v + n_v);
+        if (d_v) M->d_v.assign(d_v, d_v + n_v);  // empty: wall distance computed on the device
         M->eps = eps;
         M->D = D;
         M->k = k;

@@ -70,6 +70,10 @@ class rbfd_stats(ctypes.Structure):
         ("persist_launches", ctypes.c_int64),
         ("persist_ctas", ctypes.c_int64),
         ("persist_phase_ms", ctypes.c_double * 8),
+        ("wall_ms", ctypes.c_double),
+        ("wall_launches", ctypes.c_int64),
+        ("wall_pairs_search", ctypes.c_int64),
+        ("wall_pairs_exact", ctypes.c_int64),
     ]
 
 
@@ -105,6 +109,8 @@ SIGNATURES = [
     ("rbfd_deform", ctypes.c_int, [_vp, _i64, _vp, _vp, _d, _d, _vp]),
     ("rbfd_deform_f64", ctypes.c_int, [_vp, _i64, _vp, _vp, _d, _d, _vp]),
     ("rbfd_deform_noalloc", ctypes.c_int, [_vp, _i64, _vp, _vp, _d, _d, _vp]),
+    ("rbfd_wall_distance", ctypes.c_int, [_vp, _i64, _vp, _vp]),
+    ("rbfd_wall_distance_f64", ctypes.c_int, [_vp, _i64, _vp, _vp]),
     ("rbfd_set_displacement", ctypes.c_int, [_vp, _vp]),
     ("rbfd_set_volume", ctypes.c_int, [_vp, _i64, _vp, _vp]),
     ("rbfd_deform_volume", ctypes.c_int, [_vp, _d, _d, _vp]),
@@ -280,7 +286,8 @@ class Mesh:
 
     def deform(self, xyz_v, d_v, D: float, k: float, out=None):
         """Volume update (Eq. 19 / Eq. 23).  numpy in -> numpy out (host
-        pointers); torch CUDA tensors in -> tensor out (device pointers)."""
+        pointers); torch CUDA tensors in -> tensor out (device pointers).
+        ``d_v=None``: the wall distances are computed on the device."""
         if self.on_device:
             import torch
 
@@ -292,7 +299,8 @@ class Mesh:
             f64 = np.asarray(xyz_v).dtype == np.float64
             dt = np.float64 if f64 else np.float32
             xyz_v = np.ascontiguousarray(xyz_v, dtype=dt)
-            d_v = np.ascontiguousarray(d_v, dtype=dt)
+            if d_v is not None:
+                d_v = np.ascontiguousarray(d_v, dtype=dt)
             n_v = xyz_v.shape[0]
             if out is None:
                 out = np.empty((n_v, self.dim), dtype=dt)
@@ -315,7 +323,8 @@ class Mesh:
         """``rbfd_set_volume``: register a float32 volume mesh for repeated updates."""
         if not self.on_device:
             xyz_v = np.ascontiguousarray(xyz_v, dtype=np.float32)
-            d_v = np.ascontiguousarray(d_v, dtype=np.float32)
+            if d_v is not None:
+                d_v = np.ascontiguousarray(d_v, dtype=np.float32)
         self.n_v_reg = int(xyz_v.shape[0])
         _check(self._lib.rbfd_set_volume(self.h, self.n_v_reg, _ptr(xyz_v), _ptr(d_v)))
 
@@ -329,6 +338,27 @@ class Mesh:
             else:
                 out = np.empty((self.n_v_reg, self.dim), dtype=np.float32)
         _check(self._lib.rbfd_deform_volume(self.h, float(D), float(k), _ptr(out)))
+        return out
+
+    def wall_distance(self, xyz_v, out=None):
+        """``rbfd_wall_distance``: distance of each volume point from the
+        nearest surface point, FP64.  float32 or float64 coordinates; numpy in
+        -> numpy out, torch CUDA tensors in -> tensor out."""
+        if self.on_device:
+            import torch
+
+            f64 = xyz_v.dtype == torch.float64
+            n_v = xyz_v.shape[0]
+            if out is None:
+                out = torch.empty((n_v,), dtype=torch.float64, device=xyz_v.device)
+        else:
+            f64 = np.asarray(xyz_v).dtype == np.float64
+            xyz_v = np.ascontiguousarray(xyz_v, dtype=np.float64 if f64 else np.float32)
+            n_v = xyz_v.shape[0]
+            if out is None:
+                out = np.empty((n_v,), dtype=np.float64)
+        fn = self._lib.rbfd_wall_distance_f64 if f64 else self._lib.rbfd_wall_distance
+        _check(fn(self.h, int(n_v), _ptr(xyz_v), _ptr(out)))
         return out
 
     def deform_noalloc(self, xyz_v, d_v, D: float, k: float, out):
@@ -357,7 +387,7 @@ def deform_batch(meshes, xyz_v, d_v, D, k, out):
     n = len(meshes)
     nv = (_i64 * n)(*[int(x.shape[0]) for x in xyz_v])
     px = (_vp * n)(*[_ptr(x).value for x in xyz_v])
-    pd = (_vp * n)(*[_ptr(x).value for x in d_v])
+    pd = (_vp * n)(*[None if x is None else _ptr(x).value for x in d_v])
     po = (_vp * n)(*[_ptr(x).value for x in out])
     Dv = (_d * n)(*[float(x) for x in D])
     kv = (_d * n)(*[float(x) for x in k])
@@ -388,7 +418,8 @@ class Server:
     def add_mesh(self, xyz_s, xyz_v, d_v, R, eps, D, k) -> int:
         xyz_s = np.ascontiguousarray(xyz_s, dtype=np.float64)
         xyz_v = np.ascontiguousarray(xyz_v, dtype=np.float32)
-        d_v = np.ascontiguousarray(d_v, dtype=np.float32)
+        if d_v is not None:  # None: wall distances computed on the device
+            d_v = np.ascontiguousarray(d_v, dtype=np.float32)
         Rv = np.ascontiguousarray(np.atleast_1d(R), dtype=np.float64)
         mid = ctypes.c_int()
         _check(self._lib.rbfd_server_add_mesh(self.h, xyz_s.shape[1], xyz_s.shape[0], _ptr(xyz_s), xyz_v.shape[0],

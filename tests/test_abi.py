@@ -69,15 +69,15 @@ def test_struct_layout_matches_header(tmp_path):
         "int main(void){\n"
         'printf("%zu %zu %zu %zu\\n", sizeof(rbfd_options), offsetof(rbfd_options, nc_cap),'
         " offsetof(rbfd_options, stream), offsetof(rbfd_options, grid_ctas));\n"
-        'printf("%zu %zu %zu\\n", sizeof(rbfd_stats), offsetof(rbfd_stats, confirm_resumes),'
-        " offsetof(rbfd_stats, persist_phase_ms));\n"
+        'printf("%zu %zu %zu %zu\\n", sizeof(rbfd_stats), offsetof(rbfd_stats, confirm_resumes),'
+        " offsetof(rbfd_stats, persist_phase_ms), offsetof(rbfd_stats, wall_pairs_exact));\n"
         "return 0;}\n"
     )
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
     a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
     so, onc, ost, ori = map(int, a.split())
-    ss, ocr, ovp = map(int, b.split())
+    ss, ocr, ovp, owp = map(int, b.split())
     assert so == ctypes.sizeof(rbfd.rbfd_options)
     assert onc == rbfd.rbfd_options.nc_cap.offset
     assert ost == rbfd.rbfd_options.stream.offset
@@ -85,3 +85,4 @@ def test_struct_layout_matches_header(tmp_path):
     assert ss == ctypes.sizeof(rbfd.rbfd_stats)
     assert ocr == rbfd.rbfd_stats.confirm_resumes.offset
     assert ovp == rbfd.rbfd_stats.persist_phase_ms.offset
+    assert owp == rbfd.rbfd_stats.wall_pairs_exact.offset
