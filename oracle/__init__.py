@@ -73,6 +73,10 @@ def _bind(path: str):
                                ctypes.c_int64, dp, ctypes.c_int64, dp, dp, dp, ctypes.c_int]
     lib.orc_max_threads.restype = ctypes.c_int
     lib.orc_max_threads.argtypes = []
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.orc_orthogonality.restype = ctypes.c_int
+    lib.orc_orthogonality.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                      dp, dp, fp, fp, dp, dp]
     lib.orc_wall_distance.restype = None
     lib.orc_wall_distance.argtypes = [ctypes.c_int, ctypes.c_int64, dp, ctypes.c_int64, dp, dp, ctypes.c_int]
     return lib
@@ -256,6 +260,41 @@ def wall_distance(xyz_s, xyz_v, n_threads=1, lib=None):
     lib.orc_wall_distance(xyz_s.shape[1], xyz_s.shape[0], _dp(xyz_s), xyz_v.shape[0], _dp(xyz_v), _dp(d),
                           int(n_threads))
     return d
+
+
+@dataclasses.dataclass
+class Quality:
+    theta: np.ndarray     # per cell, degrees in [0, 90]
+    min_deg: float
+    mean_deg: float
+    argmin: int
+    cells: int
+    tangled: int
+    hist: np.ndarray      # cells per 10-degree bin
+
+
+def orthogonality(wall, vol, n_layers, periodic_i=True, wall_disp=None, vol_disp=None, n_k=1, lib=None):
+    """Orthogonality angle of each cell of the structured grid grown off the
+    surface: ``wall`` [n_k * n_i][dim] (FP64), ``vol`` [n_k * n_i * n_layers][dim]
+    (FP32, wall-normal index fastest), displacements optional."""
+    lib = lib or _load()
+    wall = _f64(wall)
+    dim = wall.shape[1]
+    n_i = wall.shape[0] // n_k
+    vol = np.ascontiguousarray(vol, dtype=np.float32)
+    wd = None if wall_disp is None else _f64(wall_disp)
+    vd = None if vol_disp is None else np.ascontiguousarray(vol_disp, dtype=np.float32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    fptr = lambda a: None if a is None else a.ctypes.data_as(fp)
+    n_ci = n_i if periodic_i else n_i - 1
+    n_ck = n_k - 1 if dim == 3 else 1
+    theta = np.zeros(max(n_ck * n_ci * n_layers, 0))
+    summ = np.zeros(14)
+    rc = lib.orc_orthogonality(dim, n_i, n_k, n_layers, 1 if periodic_i else 0, _dp(wall),
+                               None if wd is None else _dp(wd), fptr(vol), fptr(vd), _dp(theta), _dp(summ))
+    if rc != OK:
+        raise ValueError(f"oracle orthogonality: bad arguments (status {rc})")
+    return Quality(theta, summ[0], summ[1], int(summ[2]), int(summ[3]), int(summ[4]), summ[5:].astype(np.int64))
 
 
 class Variant:

@@ -35,7 +35,13 @@
  *     lowest surface index; the comparison key is Ex*Ex + Ey*Ey (+ Ez*Ez);
  *   - psi applies at every level; if k > 0, D_l = k * max_i |dS_l,i|, capped
  *     at D when D > 0; if k == 0, D_l = D; a D_l of 0 leaves points fixed;
- *     d < 0 is clamped to 0.
+ *     d < 0 is clamped to 0;
+ *   - wall distance d (Section 4, taken as given by the paper): the distance
+ *     to the nearest surface point;
+ *   - mesh quality (Section 5, "orthogonality angle"): per cell of a
+ *     structured grid, the smallest angle between two grid lines meeting at
+ *     a corner, folded into [0, 90] degrees (90 = orthogonal); a cell whose
+ *     corners disagree in orientation is counted as tangled.
  *
  * Compiled with -O2 -ffp-contract=off so that every product and sum is a
  * separately rounded IEEE double operation.
@@ -448,4 +454,149 @@ void orc_wall_distance(int dim, int64_t n_s, const double *xyz_s, int64_t n_v, c
         d[v] = best;
     }
     (void)n_threads;
+}
+
+/* ------------------------------------------------------------ mesh quality */
+
+/* Node (i, k, j) of a structured grid grown off the surface: layer j = 0 is
+ * the wall (surface point (k, i) moved by its displacement), layers j >= 1 are
+ * volume points (k, i, j - 1) moved by theirs.  Every coordinate is the FP64
+ * sum of the stored value and its displacement. */
+typedef struct {
+    int dim;
+    int64_t n_i, n_k, n_layers;
+    const double *wall, *wall_disp;
+    const float *vol, *vol_disp;
+} orc_grid;
+
+static void grid_node(const orc_grid *g, int64_t i, int64_t k, int64_t j, double *p)
+{
+    for (int c = 0; c < 3; ++c) p[c] = 0.0;
+    for (int c = 0; c < g->dim; ++c) {
+        if (j == 0) {
+            int64_t q = (k * g->n_i + i) * g->dim + c;
+            p[c] = g->wall[q] + (g->wall_disp ? g->wall_disp[q] : 0.0);
+        } else {
+            int64_t q = ((k * g->n_i + i) * g->n_layers + (j - 1)) * g->dim + c;
+            p[c] = (double)g->vol[q] + (g->vol_disp ? (double)g->vol_disp[q] : 0.0);
+        }
+    }
+}
+
+/* Angle between the grid lines a and b at a corner, folded into [0, 90]
+ * degrees: atan2(|a x b|, |a . b|). */
+static double folded_angle_deg(const double *a, const double *b, int dim)
+{
+    double dot = a[0] * b[0] + a[1] * b[1] + (dim == 3 ? a[2] * b[2] : 0.0);
+    double cr;
+    if (dim == 2) {
+        cr = fabs(a[0] * b[1] - a[1] * b[0]);
+    } else {
+        double c0 = a[1] * b[2] - a[2] * b[1];
+        double c1 = a[2] * b[0] - a[0] * b[2];
+        double c2 = a[0] * b[1] - a[1] * b[0];
+        cr = sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+    }
+    return atan2(cr, fabs(dot)) * (180.0 / 3.14159265358979323846);
+}
+
+static void sub3(const double *a, const double *b, double *out)
+{
+    for (int c = 0; c < 3; ++c) out[c] = a[c] - b[c];
+}
+
+/* Orthogonality angle of every cell of the grid and a summary.
+ *   2D: cells (i, j) between wall-normal lines i, i+1 and layers j, j+1;
+ *       theta index i * n_layers + j.
+ *   3D: cells (k, i, j) with the span direction k; index (k * n_ci + i) * n_layers + j.
+ * n_ci = n_i if the i direction closes on itself (periodic), else n_i - 1.
+ * Orientation at a corner: 2D, the cross product of the edges to the next and
+ * the previous corner going round the cell; 3D, the triple product of the
+ * three edges leaving the corner, sign-corrected by the corner's parity.  A
+ * cell with both positive and negative orientations is tangled.
+ * summary: [0] min angle, [1] mean angle, [2] argmin (lowest index on ties),
+ *          [3] cells, [4] tangled cells, [5..13] cells per 10-degree bin. */
+int orc_orthogonality(int dim, int64_t n_i, int64_t n_k, int64_t n_layers, int periodic_i, const double *wall,
+                      const double *wall_disp, const float *vol, const float *vol_disp, double *theta,
+                      double *summary)
+{
+    if ((dim != 2 && dim != 3) || n_i < 2 || n_layers < 1 || (dim == 3 && n_k < 2) || !wall || !vol)
+        return ORC_EINVAL;
+    if (dim == 2) n_k = 1;
+    orc_grid g = {dim, n_i, n_k, n_layers, wall, wall_disp, vol, vol_disp};
+    int64_t n_ci = periodic_i ? n_i : n_i - 1;
+    int64_t n_ck = dim == 3 ? n_k - 1 : 1;
+    int64_t cells = n_ck * n_ci * n_layers;
+    double mn = INFINITY, sum = 0.0;
+    int64_t argmin = -1, tangled = 0, hist[9] = {0};
+    for (int64_t k = 0; k < n_ck; ++k)
+        for (int64_t i = 0; i < n_ci; ++i)
+            for (int64_t j = 0; j < n_layers; ++j) {
+                int64_t i1 = (i + 1) % n_i;
+                double th = INFINITY;
+                int pos = 0, neg = 0;
+                if (dim == 2) {
+                    /* corners in order round the cell */
+                    double P[4][3], e0[3], e1[3];
+                    grid_node(&g, i, 0, j, P[0]);
+                    grid_node(&g, i1, 0, j, P[1]);
+                    grid_node(&g, i1, 0, j + 1, P[2]);
+                    grid_node(&g, i, 0, j + 1, P[3]);
+                    for (int q = 0; q < 4; ++q) {
+                        sub3(P[(q + 1) % 4], P[q], e0);
+                        sub3(P[(q + 3) % 4], P[q], e1);
+                        double a = folded_angle_deg(e0, e1, 2);
+                        if (a < th) th = a;
+                        double o = e0[0] * e1[1] - e0[1] * e1[0];
+                        pos |= o > 0.0;
+                        neg |= o < 0.0;
+                    }
+                } else {
+                    double P[2][2][2][3]; /* [di][dk][dj] */
+                    for (int di = 0; di < 2; ++di)
+                        for (int dk = 0; dk < 2; ++dk)
+                            for (int dj = 0; dj < 2; ++dj)
+                                grid_node(&g, di ? i1 : i, k + dk, j + dj, P[di][dk][dj]);
+                    for (int di = 0; di < 2; ++di)
+                        for (int dk = 0; dk < 2; ++dk)
+                            for (int dj = 0; dj < 2; ++dj) {
+                                double ei[3], ek[3], ej[3];
+                                const double *c = P[di][dk][dj];
+                                sub3(P[1 - di][dk][dj], c, ei);
+                                sub3(P[di][1 - dk][dj], c, ek);
+                                sub3(P[di][dk][1 - dj], c, ej);
+                                double a = folded_angle_deg(ei, ek, 3);
+                                if (a < th) th = a;
+                                a = folded_angle_deg(ei, ej, 3);
+                                if (a < th) th = a;
+                                a = folded_angle_deg(ek, ej, 3);
+                                if (a < th) th = a;
+                                /* ei . (ek x ej), times -1 for odd corners */
+                                double x0 = ek[1] * ej[2] - ek[2] * ej[1];
+                                double x1 = ek[2] * ej[0] - ek[0] * ej[2];
+                                double x2 = ek[0] * ej[1] - ek[1] * ej[0];
+                                double o = ei[0] * x0 + ei[1] * x1 + ei[2] * x2;
+                                if ((di + dk + dj) & 1) o = -o;
+                                pos |= o > 0.0;
+                                neg |= o < 0.0;
+                            }
+                }
+                int64_t idx = (k * n_ci + i) * n_layers + j;
+                if (theta) theta[idx] = th;
+                if (th < mn) {
+                    mn = th;
+                    argmin = idx;
+                }
+                sum += th;
+                tangled += (pos && neg);
+                int b = (int)(th / 10.0);
+                hist[b < 0 ? 0 : (b > 8 ? 8 : b)]++;
+            }
+    summary[0] = mn;
+    summary[1] = cells ? sum / (double)cells : 0.0;
+    summary[2] = (double)argmin;
+    summary[3] = (double)cells;
+    summary[4] = (double)tangled;
+    for (int b = 0; b < 9; ++b) summary[5 + b] = (double)hist[b];
+    return ORC_OK;
 }

@@ -310,6 +310,80 @@ def pin_wall_distance(o):
     return bad
 
 
+def _cart_grid_2d(nx, ny, hx=0.25, hy=0.5, shear=0.0):
+    """Cartesian nx x (ny + 1) grid, row 0 the wall, x' = x + shear * y (dyadic
+    values: exact in FP32)."""
+    xs = np.arange(nx) * hx
+    ys = np.arange(ny + 1) * hy
+    X, Y = np.meshgrid(xs, ys, indexing="ij")
+    P = np.stack([X + shear * Y, Y], axis=-1)  # [i][j]
+    return P[:, 0, :].copy(), P[:, 1:, :].reshape(-1, 2).copy()
+
+
+def _cart_grid_3d(nx, nz, ny, shear_k=0.0):
+    """Box grid: i along x, k along z (span), j along y (wall normal);
+    x' = x + shear_k * z."""
+    xs, zs, ys = np.arange(nx) * 0.25, np.arange(nz) * 0.5, np.arange(ny + 1) * 0.125
+    Z, X, Y = np.meshgrid(zs, xs, ys, indexing="ij")  # [k][i][j]
+    P = np.stack([X + shear_k * Z, Y, Z], axis=-1)
+    return P[:, :, 0, :].reshape(-1, 3).copy(), P[:, :, 1:, :].reshape(-1, 3).copy()
+
+
+def pin_orthogonality(o):
+    """Closed forms of the orthogonality angle (mesh quality, Section 5):
+    right angles on a Cartesian grid; atan(1/s) on a grid sheared by s; on a
+    polar O-grid with n rays every cell is an isosceles trapezoid whose acute
+    corner is 90 - 180/n degrees (this includes the cell that closes the
+    ring); a node pushed through its neighbour tangles the cells around it; a
+    collapsed edge gives 0."""
+    bad = []
+    wall, vol = _cart_grid_2d(6, 4)
+    q = o.orthogonality(wall, vol, 4, periodic_i=False)
+    if q.cells != 20 or np.abs(q.theta - 90.0).max() > 1e-12 or q.tangled:
+        bad.append("Cartesian 2D grid is not orthogonal")
+    wall, vol = _cart_grid_2d(6, 4, shear=0.5)
+    q = o.orthogonality(wall, vol, 4, periodic_i=False)
+    if np.abs(q.theta - np.degrees(np.arctan(2.0))).max() > 1e-12 or q.tangled:
+        bad.append("sheared 2D grid angle is not atan(1/s)")
+    if q.hist.sum() != q.cells or q.hist[6] != q.cells or abs(q.mean_deg - q.theta.mean()) > 1e-12:
+        bad.append("histogram or mean inconsistent")
+    n, r = 16, np.array([1.0, 1.5, 2.25, 3.0])
+    ph = 2 * np.pi * np.arange(n) / n
+    ring = np.stack([np.cos(ph), np.sin(ph)], 1)
+    vol = (ring[:, None, :] * r[None, 1:, None]).reshape(-1, 2)
+    q = o.orthogonality(ring * r[0], vol, 3, periodic_i=True)
+    # FP32 volume coordinates move the corners by up to 2^-24 |r|: a few 1e-5 degrees here
+    if q.cells != n * 3 or np.abs(q.theta - (90.0 - 180.0 / n)).max() > 1e-4 or q.tangled:
+        bad.append("polar O-grid angle is not 90 - 180/n")
+    wall, vol = _cart_grid_2d(5, 3)
+    v = vol.reshape(5, 3, 2)
+    v[2, 1, 1] = v[2, 1, 1] + 1.0  # through the node above it
+    q = o.orthogonality(wall, v.reshape(-1, 2), 3, periodic_i=False)
+    if q.tangled < 1:
+        bad.append("a folded cell is not counted as tangled")
+    wall, vol = _cart_grid_2d(5, 3)
+    wd = np.zeros_like(wall)
+    wd[2] = [0.25, 0.0]  # wall node 2 onto wall node 3: a zero-length edge
+    q = o.orthogonality(wall, vol, 3, periodic_i=False, wall_disp=wd)
+    if q.min_deg != 0.0 or q.argmin != 2 * 3 + 0:
+        bad.append("collapsed edge does not give angle 0 at its cell")
+    # one general quad whose only smallest corner is the last one round the cell:
+    # edges (1.25, 0.25) and (0.25, -1) there, angle atan2(1.1875, 0.5625)
+    q = o.orthogonality(np.array([[0.0, 0.0], [1.0, 0.0]]), np.array([[-0.25, 1.0], [1.0, 0.75]]), 1,
+                        periodic_i=False)
+    if abs(q.min_deg - np.degrees(np.arctan2(1.1875, 0.5625))) > 1e-12:
+        bad.append("single quad: smallest corner angle wrong")
+    wall, vol = _cart_grid_3d(5, 4, 3)
+    q = o.orthogonality(wall, vol, 3, periodic_i=False, n_k=4)
+    if q.cells != 4 * 3 * 3 or np.abs(q.theta - 90.0).max() > 1e-12 or q.tangled:
+        bad.append("Cartesian 3D grid is not orthogonal or counted tangled")
+    wall, vol = _cart_grid_3d(5, 4, 3, shear_k=0.25)
+    q = o.orthogonality(wall, vol, 3, periodic_i=False, n_k=4)
+    if np.abs(q.theta - np.degrees(np.arctan(1.0 / 0.25))).max() > 1e-12 or q.tangled:
+        bad.append("sheared 3D grid angle is not atan(1/s)")
+    return bad
+
+
 def all_pins(o):
     bad = []
     bad += pin_table1(o)
@@ -326,6 +400,7 @@ def all_pins(o):
     bad += pin_deform(o, tiny_airfoil_k5())
     bad += pin_deform(o, tiny_wing())
     bad += pin_wall_distance(o)
+    bad += pin_orthogonality(o)
     return bad
 
 
@@ -391,6 +466,10 @@ def test_deform_wing():
 
 def test_wall_distance_vs_kdtree_and_closed_form():
     assert pin_wall_distance(oracle) == []
+
+
+def test_orthogonality_closed_forms():
+    assert pin_orthogonality(oracle) == []
 
 
 def test_incremental_equals_scratch():
@@ -472,6 +551,13 @@ MUTATIONS = {
     "first control not point 0": ("int64_t first = 0;", "int64_t first = 1;"),
     "wall distance skips the last point": ("for (int64_t i = 0; i < n_s; ++i) {\n            double r = dist(",
                                            "for (int64_t i = 0; i < n_s - 1; ++i) {\n            double r = dist("),
+    "orthogonality drops the ring-closing cell": ("int64_t n_ci = periodic_i ? n_i : n_i - 1;",
+                                                  "int64_t n_ci = n_i - 1;"),
+    "orthogonality volume layer off by one": ("int64_t q = ((k * g->n_i + i) * g->n_layers + (j - 1)) * g->dim + c;",
+                                              "int64_t q = ((k * g->n_i + i) * g->n_layers + j) * g->dim + c;"),
+    "orthogonality ignores corner parity": ("if ((di + dk + dj) & 1) o = -o;", ""),
+    "orthogonality skips one corner": ("for (int q = 0; q < 4; ++q) {\n                        sub3(P[(q + 1) % 4]",
+                                       "for (int q = 0; q < 3; ++q) {\n                        sub3(P[(q + 1) % 4]"),
 }
 
 
