@@ -219,6 +219,49 @@ int rbfd_wall_distance(rbfd_mesh *m, int64_t n_v, const float *xyz_v, double *d_
 int rbfd_wall_distance_f64(rbfd_mesh *m, int64_t n_v, const double *xyz_v, double *d_out);
 
 /*
+ * rbfd_orthogonality -- mesh quality of a deformed structured grid, the
+ * orthogonality angle by which Section 5 judges the deformations.  The grid
+ * grows off the surface: node layer j = 0 is the wall, layers j = 1..n_layers
+ * are volume points; i runs round the section (periodic_i = 1 when it closes
+ * on itself, as an O-mesh does), k along the span (3D only).
+ *
+ *   wall       [n_k][n_i][dim] wall node coordinates (double)
+ *   wall_disp  same shape, added to wall (double), or NULL
+ *   vol        [n_k][n_i][n_layers][dim] volume node coordinates (float);
+ *              the layout rbfd_deform's xyz_v has for these meshes
+ *   vol_disp   same shape, added to vol (float; rbfd_deform's out), or NULL
+ *   theta      per cell, the angle in degrees (float), or NULL; 2D cells
+ *              (i, j) at i * n_layers + j, 3D cells (k, i, j) at
+ *              (k * n_ci + i) * n_layers + j, n_ci = n_i if periodic_i else
+ *              n_i - 1, k < n_k - 1, j < n_layers
+ *   q          summary (below), or NULL
+ *   on_device  1: every array is device memory of the current device; 0: host
+ *   stream     cudaStream_t to run on, or NULL for the per-thread default stream
+ *
+ * Each node is the FP64 sum of its coordinate and its displacement.  The
+ * orthogonality angle of a cell is the smallest angle between two grid lines
+ * (cell edges) meeting at a corner, folded into [0, 90] degrees: 90 for a
+ * rectangular cell, 0 for a collapsed one.  A cell whose corners disagree in
+ * orientation (2D: the cross product of the edges round the cell; 3D: the
+ * triple product of the three edges at a corner) is tangled.  Angles are
+ * within 1e-4 degrees of an FP64 evaluation; tangled decisions equal it.
+ * Errors: RBFD_EINVAL (dim not 2 or 3, n_i < 2, n_layers < 1, n_k < 2 in 3D,
+ * NULL wall or vol), RBFD_ENOMEM, RBFD_ECUDA.
+ */
+typedef struct rbfd_quality {
+    double min_deg;   /* smallest cell angle */
+    double mean_deg;  /* mean cell angle */
+    int64_t argmin;   /* cell of the smallest angle (lowest index on ties) */
+    int64_t cells;
+    int64_t tangled;  /* tangled cells */
+    int64_t hist[9];  /* cells per 10-degree bin: [0,10), [10,20), ..., [80,90] */
+} rbfd_quality;
+
+int rbfd_orthogonality(int dim, int64_t n_i, int64_t n_k, int64_t n_layers, int periodic_i, const double *wall,
+                       const double *wall_disp, const float *vol, const float *vol_disp, float *theta,
+                       rbfd_quality *q, int on_device, void *stream);
+
+/*
  * rbfd_deform_noalloc -- the volume update of rbfd_deform for callers that
  * cannot allocate device memory while they run: a solver loop whose device
  * memory was reserved up front (a pool or a fixed budget), or a host that keeps

@@ -515,6 +515,28 @@ int rbfd_wall_distance_f64(rbfd_mesh *m, int64_t n_v, const double *xyz_v, doubl
     return wall_common(m, n_v, xyz_v, d_out, true);
 }
 
+int rbfd_orthogonality(int dim, int64_t n_i, int64_t n_k, int64_t n_layers, int periodic_i, const double *wall,
+                       const double *wall_disp, const float *vol, const float *vol_disp, float *theta,
+                       rbfd_quality *q, int on_device, void *stream) {
+    return guarded([&] {
+        if (dim != 2 && dim != 3) rbfd::fail(RBFD_EINVAL, "rbfd_orthogonality: dim must be 2 or 3");
+        if (dim == 2) n_k = 1;
+        if (n_i < 2 || n_layers < 1 || n_k < 1 || (dim == 3 && n_k < 2))
+            rbfd::fail(RBFD_EINVAL, "rbfd_orthogonality: grid too small");
+        if (n_k * n_i * (n_layers + 1) > ((int64_t)1 << 40)) rbfd::fail(RBFD_EINVAL, "rbfd_orthogonality: grid too large");
+        if (!wall || !vol) rbfd::fail(RBFD_EINVAL, "rbfd_orthogonality: NULL wall or vol");
+        if (on_device) {
+            const void *ptrs[] = {wall, wall_disp, vol, vol_disp, theta};
+            for (const void *p : ptrs)
+                if (p && !is_device_ptr(p))
+                    rbfd::fail(RBFD_EINVAL, "rbfd_orthogonality: on_device set but an array is not device memory");
+        }
+        cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : cudaStreamPerThread;
+        rbfd::orthogonality_run(dim, n_i, n_k, n_layers, periodic_i, wall, wall_disp, vol, vol_disp, on_device != 0,
+                                st, theta, q);
+    });
+}
+
 int rbfd_deform(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v, double D, double k, float *out) {
     return deform_common(m, n_v, xyz_v, d_v, D, k, out, false);
 }

@@ -209,4 +209,7 @@ void mesh_free(rbfd_mesh *m);
 // order) or, with d_out null, into vpos[i].w
 void wall_distance_sorted(rbfd_mesh *m, int64_t n, double4 *vpos, double cap, double *d_out);
 void wall_distance_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, bool f64, double *out);
+void orthogonality_run(int dim, int64_t n_i, int64_t n_k, int64_t n_layers, int periodic_i, const double *wall,
+                       const double *wall_disp, const float *vol, const float *vol_disp, bool on_device,
+                       cudaStream_t st, float *theta, rbfd_quality *q);
 }  // namespace rbfd

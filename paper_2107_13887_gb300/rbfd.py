@@ -77,6 +77,17 @@ class rbfd_stats(ctypes.Structure):
     ]
 
 
+class rbfd_quality(ctypes.Structure):
+    _fields_ = [
+        ("min_deg", ctypes.c_double),
+        ("mean_deg", ctypes.c_double),
+        ("argmin", ctypes.c_int64),
+        ("cells", ctypes.c_int64),
+        ("tangled", ctypes.c_int64),
+        ("hist", ctypes.c_int64 * 9),
+    ]
+
+
 class rbfd_server_options(ctypes.Structure):
     _fields_ = [
         ("slots", ctypes.c_int),
@@ -110,6 +121,8 @@ SIGNATURES = [
     ("rbfd_deform_f64", ctypes.c_int, [_vp, _i64, _vp, _vp, _d, _d, _vp]),
     ("rbfd_deform_noalloc", ctypes.c_int, [_vp, _i64, _vp, _vp, _d, _d, _vp]),
     ("rbfd_wall_distance", ctypes.c_int, [_vp, _i64, _vp, _vp]),
+    ("rbfd_orthogonality", ctypes.c_int, [ctypes.c_int, _i64, _i64, _i64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp,
+                                          ctypes.POINTER(rbfd_quality), ctypes.c_int, _vp]),
     ("rbfd_wall_distance_f64", ctypes.c_int, [_vp, _i64, _vp, _vp]),
     ("rbfd_set_displacement", ctypes.c_int, [_vp, _vp]),
     ("rbfd_set_volume", ctypes.c_int, [_vp, _i64, _vp, _vp]),
@@ -367,6 +380,45 @@ class Mesh:
         _check(self._lib.rbfd_deform_noalloc(self.h, int(xyz_v.shape[0]), _ptr(xyz_v), _ptr(d_v), float(D), float(k),
                                              _ptr(out)))
         return out
+
+
+def orthogonality(wall, vol, n_layers, periodic_i=True, wall_disp=None, vol_disp=None, n_k=1, theta=True,
+                  stream=None):
+    """``rbfd_orthogonality``: orthogonality angle (degrees) of each cell of
+    the structured grid grown off the surface, and a summary dict.  ``wall``
+    [n_k * n_i][dim] (float64), ``vol`` [n_k * n_i * n_layers][dim] (float32),
+    displacements optional; numpy arrays (host) or torch CUDA tensors (device)."""
+    lib = load()
+    on_dev = _is_torch_cuda(vol)
+    if on_dev:
+        import torch
+
+        wall = wall.to(torch.float64).contiguous()
+        vol = vol.to(torch.float32).contiguous()
+        wall_disp = None if wall_disp is None else wall_disp.to(torch.float64).contiguous()
+        vol_disp = None if vol_disp is None else vol_disp.to(torch.float32).contiguous()
+    else:
+        wall = np.ascontiguousarray(wall, dtype=np.float64)
+        vol = np.ascontiguousarray(vol, dtype=np.float32)
+        wall_disp = None if wall_disp is None else np.ascontiguousarray(wall_disp, dtype=np.float64)
+        vol_disp = None if vol_disp is None else np.ascontiguousarray(vol_disp, dtype=np.float32)
+    dim = int(wall.shape[1])
+    n_i = int(wall.shape[0]) // (n_k if dim == 3 else 1)
+    n_ci = n_i if periodic_i else n_i - 1
+    cells = max(0, (n_k - 1 if dim == 3 else 1) * n_ci * int(n_layers))
+    th = None
+    if theta:
+        if on_dev:
+            th = torch.empty(cells, dtype=torch.float32, device=vol.device)
+        else:
+            th = np.empty(cells, dtype=np.float32)
+    q = rbfd_quality()
+    _check(lib.rbfd_orthogonality(dim, n_i, n_k if dim == 3 else 1, int(n_layers), 1 if periodic_i else 0,
+                                  _ptr(wall), _ptr(wall_disp), _ptr(vol), _ptr(vol_disp), _ptr(th),
+                                  ctypes.byref(q), 1 if on_dev else 0, stream))
+    summ = {f: getattr(q, f) for f, _ in rbfd_quality._fields_}
+    summ["hist"] = list(q.hist)
+    return th, summ
 
 
 def greedy_batch(meshes, allow_not_converged: bool = True) -> int:

@@ -140,20 +140,26 @@ def _wall_distance(xyz_v: np.ndarray, xyz_s: np.ndarray) -> np.ndarray:
     return d
 
 
-def _o_mesh(xy, nrm, n_layers, radius, h1=1e-5):
+def _o_mesh(xy, nrm, n_layers, radius, h1=1e-5, reach=0.5):
     """Structured O-mesh: each surface point marched out in ``n_layers`` layers.
 
-    Near the wall the layers follow the surface normal; they blend into rays to
-    a far-field circle of ``radius`` about mid-chord.
+    Near the wall the layers follow the surface normal; further out they blend
+    (smoothstep over the first ``reach`` of the radius) into rays to a
+    far-field circle of ``radius`` about mid-chord, on which the surface
+    points are spread evenly by arc length, so neighbouring rays never meet
+    (the blunt trailing edge included).  Layout [surface point][layer].
     """
     h = _geometric_heights(n_layers, h1, radius)
     centre = np.array([0.5, 0.0])
-    ang = np.arctan2(xy[:, 1] - centre[1], xy[:, 0] - centre[0])
+    seg = np.linalg.norm(np.roll(xy, -1, axis=0) - xy, axis=1)
+    s = np.concatenate([[0.0], np.cumsum(seg)[:-1]])
+    ang = 2.0 * math.pi * s / seg.sum() + math.atan2(xy[0, 1] - centre[1], xy[0, 0] - centre[0])
     far = centre + radius * np.stack([np.cos(ang), np.sin(ang)], axis=1)
     w = (h / radius)[None, :, None]  # 0 at wall .. 1 at far field
     near = xy[:, None, :] + nrm[:, None, :] * h[None, :, None]
     ray = xy[:, None, :] + (far - xy)[:, None, :] * w
-    blend = np.clip(w * 10.0, 0.0, 1.0)  # normal-following in the first 10% of the radius
+    x = np.clip(w / reach, 0.0, 1.0)
+    blend = x * x * (3.0 - 2.0 * x)
     pts = (1.0 - blend) * near + blend * ray
     return pts.reshape(-1, 2)
 
@@ -277,9 +283,11 @@ def wing_case(
 ) -> Case:
     """3D swept (30 deg), tapered (0.5) wing of NACA0012 sections, span 3 chords.
 
-    The volume is the surface extruded along its normals in ``n_layers``
-    geometric layers (first height 1e-5, last ``radius``), an O-H topology that
-    stands in for the paper's unstructured C-H mesh.
+    The volume is an O-H grid standing in for the paper's unstructured C-H
+    mesh: at every span station the section's points carry ``n_layers``
+    geometric layers (first height 1e-5, last ``radius``) that follow the
+    normals near the wall and blend into rays to a far-field circle, the
+    layers of the unit-chord section's O-mesh.  Layout [span][chord][layer].
 
     displacement:
       ``ridge``     leading-edge ice ridge, height growing linearly from 0.01
@@ -305,8 +313,12 @@ def wing_case(
     else:
         raise ValueError(displacement)
     if n_layers > 0:
-        hgt = _geometric_heights(n_layers, 1e-5, radius)
-        xv = (pts[:, None, :] + nrm[:, None, :] * hgt[None, :, None]).reshape(-1, 3)
+        # every span station carries the layers of the unit-chord section's
+        # O-mesh, as offsets from its surface points
+        xy2, nrm2, _ = naca0012_surface(n_chord)
+        off = _o_mesh(xy2, nrm2, n_layers, radius).reshape(n_chord, n_layers, 2) - xy2[:, None, :]
+        off3 = np.concatenate([off, np.zeros((n_chord, n_layers, 1))], axis=2)
+        xv = (pts.reshape(n_span, n_chord, 1, 3) + off3[None]).reshape(-1, 3)
         d = _wall_distance(xv, pts)
     else:
         xv = np.zeros((0, 3))

@@ -71,11 +71,12 @@ def test_struct_layout_matches_header(tmp_path):
         " offsetof(rbfd_options, stream), offsetof(rbfd_options, grid_ctas));\n"
         'printf("%zu %zu %zu %zu\\n", sizeof(rbfd_stats), offsetof(rbfd_stats, confirm_resumes),'
         " offsetof(rbfd_stats, persist_phase_ms), offsetof(rbfd_stats, wall_pairs_exact));\n"
+        'printf("%zu %zu\\n", sizeof(rbfd_quality), offsetof(rbfd_quality, hist));\n'
         "return 0;}\n"
     )
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
-    a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
+    a, b, c = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:3]
     so, onc, ost, ori = map(int, a.split())
     ss, ocr, ovp, owp = map(int, b.split())
     assert so == ctypes.sizeof(rbfd.rbfd_options)
@@ -86,3 +87,5 @@ def test_struct_layout_matches_header(tmp_path):
     assert ocr == rbfd.rbfd_stats.confirm_resumes.offset
     assert ovp == rbfd.rbfd_stats.persist_phase_ms.offset
     assert owp == rbfd.rbfd_stats.wall_pairs_exact.offset
+    sq, oh = map(int, c.split())
+    assert sq == ctypes.sizeof(rbfd.rbfd_quality) and oh == rbfd.rbfd_quality.hist.offset
