@@ -58,8 +58,11 @@ typedef struct rbfd_options {
     int refine_iters;      /* iterative-refinement sweeps at level close (default 3) */
     int profile;           /* 1: time each kernel class with CUDA events on the mesh's stream
                               (rbfd_stats.*_ms / *_launches); adds two event records per launch */
-    int engine;            /* greedy engine: 0 = one cooperative persistent launch per level
-                              (default); 1 = separate launches for every step */
+    int engine;            /* greedy engine: 0 (default) = persistent cooperative launches: a
+                              level starts in the Newton basis (one FP64 update per point
+                              and step) and goes on with the control-list sweep once that
+                              is cheaper; 2 = the persistent list sweep only; 1 = separate
+                              launches for every step */
     int grid_ctas;         /* blocks of the persistent launch (0 = chosen from the mesh size) */
 } rbfd_options;
 
@@ -151,6 +154,7 @@ typedef struct rbfd_stats {
     int64_t wall_launches;
     int64_t wall_pairs_search;   /* point pairs scanned by the FP32 search pass */
     int64_t wall_pairs_exact;    /* point pairs scanned by the exact pass */
+    int64_t newton_steps;        /* greedy steps taken in the Newton basis (engine 0) */
 } rbfd_stats;
 
 int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st);

@@ -21,7 +21,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "librbfd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "greedy.cu", "persist.cu", "deform.cu", "sort.cu", "server.cu", "walldist.cu", "quality.cu"]
+SOURCES = ["api.cu", "greedy.cu", "persist.cu", "deform.cu", "sort.cu", "server.cu", "walldist.cu", "quality.cu", "newton.cu"]
 
 
 def nvcc_path() -> str:

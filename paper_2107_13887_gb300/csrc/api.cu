@@ -221,7 +221,8 @@ void mesh_free(rbfd_mesh *m) {
                     m->d_nb_cnt, m->d_nb_list, m->d_part, m->d_pb_done, m->d_pb_key, m->d_pb_idx, m->d_pairs,
                     m->d_st, m->d_vin, m->d_vpos, m->d_vorig, m->d_vflag, m->d_vscan, m->d_vlist, m->d_vkeys,
                     m->d_vacc, m->d_vio, m->d_misc, m->d_bbox, m->d_bar, m->d_pred, m->d_Gt,
-                    m->d_nz_k, m->d_nz_v, m->d_phase_ns, m->d_vreg, m->d_vreg_orig, m->d_pb_fbox};
+                    m->d_nz_k, m->d_nz_v, m->d_phase_ns, m->d_vreg, m->d_vreg_orig, m->d_pb_fbox,
+                    m->d_V, m->d_nrec, m->d_nycol};
     for (void *p : ptrs) dfree(p);
     m->sort.release();
     m->prof.release();
@@ -330,7 +331,7 @@ int rbfd_create(rbfd_mesh **out, int dim, int64_t n_s, const double *xyz_s, cons
         if (o.precision != RBFD_FP64 && o.precision != RBFD_MIXED)
             rbfd::fail(RBFD_EINVAL, "rbfd_create: unknown precision");
         if (o.nc_cap < 0) rbfd::fail(RBFD_EINVAL, "rbfd_create: nc_cap must be >= 0");
-        if (o.engine != 0 && o.engine != 1) rbfd::fail(RBFD_EINVAL, "rbfd_create: engine must be 0 or 1");
+        if (o.engine < 0 || o.engine > 2) rbfd::fail(RBFD_EINVAL, "rbfd_create: engine must be 0, 1 or 2");
         if (o.grid_ctas < 0 || o.grid_ctas > rbfd::kMaxPersistCTAs)
             rbfd::fail(RBFD_EINVAL, "rbfd_create: grid_ctas must be in [0, 2048]");
         if (!(eps > 0.0) || (!o.eps_absolute && !(eps < 1.0)) || !std::isfinite(eps))
@@ -567,12 +568,18 @@ int rbfd_greedy_batch(rbfd_mesh **meshes, int n) {
         if (rc != RBFD_OK) return rc;
         cap = std::max(1, total / n);
     }
-    for (int i = 0; i < n; ++i) meshes[i]->batch_ctas_cap = cap;
+    for (int i = 0; i < n; ++i) {
+        meshes[i]->batch_ctas_cap = cap;
+        meshes[i]->batch_share = n;
+    }
     int rc = run_batch(n, [&](int i) {
         RBFD_CUDA(cudaSetDevice(meshes[i]->device));
         rbfd::greedy_run(meshes[i]);
     }, "rbfd_greedy_batch");
-    for (int i = 0; i < n; ++i) meshes[i]->batch_ctas_cap = 0;
+    for (int i = 0; i < n; ++i) {
+        meshes[i]->batch_ctas_cap = 0;
+        meshes[i]->batch_share = 0;
+    }
     return rc;
 }
 

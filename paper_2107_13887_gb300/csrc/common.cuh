@@ -387,6 +387,9 @@ struct GreedyState {
     unsigned int red_done;  // last-block-done counter of reductions
     int max_cnt;            // longest per-block control list (persistent engine)
     int nnz;                // nonzeros of the phi column of the newest control
+    int handoff;            // Newton-basis launch ended to let the list sweep go on
+    int pad2;
+    unsigned long long nnz_tot;  // nonzeros of Phi_sc for the level's controls so far (Newton launch)
 };
 
 // Counter + generation word of the bounded grid barrier of the persistent
@@ -397,5 +400,89 @@ struct GridBarrier {
     int err;
     int pad;
 };
+
+// Global nanosecond timer (phase timing of the persistent launches).
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier with a bounded wait.  Returns false (in every thread of
+// the block) if the launch is failing: this block timed out or another one did.
+__device__ __forceinline__ bool grid_sync(GridBarrier *b, unsigned nblk, unsigned long long limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &b->gen;
+        volatile int *verr = &b->err;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&b->count, 1u);
+        if (arrived == nblk - 1) {
+            b->count = 0;
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            unsigned long long it = 0;
+            while (*vgen == g) {
+                if (*verr) break;
+                if (++it > limit) {
+                    atomicExch(&b->err, 1);
+                    break;
+                }
+                __nanosleep(8);
+            }
+        }
+        __threadfence();
+        s_ok = (*verr == 0);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// The same barrier in two halves, so that a block can do work that no other
+// block waits for between its arrival and its wait.  grid_arrive returns the
+// generation observed before arriving (to pass to grid_wait).
+__device__ __forceinline__ unsigned grid_arrive(GridBarrier *b, unsigned nblk) {
+    __shared__ unsigned s_gen;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &b->gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&b->count, 1u);
+        if (arrived == nblk - 1) {
+            b->count = 0;
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        }
+        s_gen = g;
+    }
+    __syncthreads();
+    return s_gen;
+}
+
+__device__ __forceinline__ bool grid_wait(GridBarrier *b, unsigned g, unsigned long long limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &b->gen;
+        volatile int *verr = &b->err;
+        unsigned long long it = 0;
+        while (*vgen == g) {
+            if (*verr) break;
+            if (++it > limit) {
+                atomicExch(&b->err, 1);
+                break;
+            }
+            __nanosleep(8);
+        }
+        __threadfence();
+        s_ok = (*verr == 0);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
 
 }  // namespace rbfd

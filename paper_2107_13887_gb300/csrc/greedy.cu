@@ -24,6 +24,7 @@
 // per-level uniform cell grid of the controls for the volume update.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 
@@ -1009,6 +1010,12 @@ void mesh_set_displacement(rbfd_mesh *m, const double *dS) {
     m->greedy_done = false;
 }
 
+// RBFD_NEWTON=0 in the environment turns the Newton-basis start of a level off.
+static bool newton_enabled() {
+    const char *v = std::getenv("RBFD_NEWTON");
+    return !(v && v[0] == '0');
+}
+
 void greedy_run(rbfd_mesh *m) {
     cudaStream_t st = m->stream;
     for (auto &L : m->levels) {
@@ -1020,6 +1027,7 @@ void greedy_run(rbfd_mesh *m) {
     m->levels.clear();
     m->greedy_done = false;
     m->stats.greedy_steps = 0;
+    m->stats.newton_steps = 0;
     m->stats.refine_sweeps = 0;
     m->stats.confirm_resumes = 0;
     RBFD_CUDA(cudaEventRecord(m->ev0, st));
@@ -1082,7 +1090,41 @@ void greedy_run(rbfd_mesh *m) {
         for (;;) {
             // ---- greedy steps: one persistent cooperative launch (engine 0) ...
             bool stopped = false;
-            if (m->opt.engine == 0) {
+            // a level starts in the Newton basis (engine 0) while that pays; the
+            // list sweep below takes over where it hands the level on
+            if (m->opt.engine == 0 && resumes == 0 && newton_enabled()) {
+                newton_reserve(m);
+                if (m->newton_cols >= 2) {
+                    // one block per 32 surface points, as far as they fit (newton_shape)
+                    int ctas = m->opt.grid_ctas > 0 ? m->opt.grid_ctas : kMaxPersistCTAs;
+                    if (m->batch_ctas_cap > 0) ctas = std::min(ctas, m->batch_ctas_cap);
+                    ctas = std::max(1, ctas);
+                    RBFD_CUDA(cudaMemsetAsync(&m->d_st->handoff, 0, sizeof(int), st));
+                    RBFD_CUDA(cudaMemsetAsync(&m->d_st->nnz_tot, 0, sizeof(unsigned long long), st));
+                    RBFD_CUDA(cudaMemsetAsync(m->d_bar, 0, sizeof(GridBarrier), st));
+                    cudaEvent_t e0 = m->prof.begin(st);
+                    newton_run_level(m, L.R, L.tau, ctas);
+                    m->prof.end(kProfPersist, e0, st, 1);
+                    read_state(m);
+                    m->prof.flush();
+                    GridBarrier hb{};
+                    RBFD_CUDA(cudaMemcpy(&hb, m->d_bar, sizeof(hb), cudaMemcpyDeviceToHost));
+                    if (hb.err) fail(RBFD_ETIMEOUT, "Newton greedy: a grid barrier exceeded its wait bound");
+                    if (m->h_st->status == RBFD_ESINGULAR)
+                        fail(RBFD_ESINGULAR, "Phi_cc is not positive definite at level " + std::to_string(l) +
+                                                 " (coincident or near-coincident controls)");
+                    if (!m->h_st->stop) fail(RBFD_ECUDA, "Newton greedy ended without a stop decision");
+                    n = m->h_st->n;
+                    m->stats.newton_steps += n - 1;
+                    if (m->h_st->handoff) {
+                        RBFD_CUDA(cudaMemsetAsync(&m->d_st->stop, 0, sizeof(int), st));
+                        RBFD_CUDA(cudaMemsetAsync(&m->d_st->handoff, 0, sizeof(int), st));
+                    } else {
+                        stopped = true;
+                    }
+                }
+            }
+            if (!stopped && (m->opt.engine == 0 || m->opt.engine == 2)) {
                 const int maxc = std::min(persist_max_ctas(m), kMaxPersistCTAs);
                 if (maxc < 1) fail(RBFD_ECUDA, "persistent greedy kernel cannot be resident on this device");
                 // small meshes: few blocks keep the barriers cheap; large ones fill the GPU

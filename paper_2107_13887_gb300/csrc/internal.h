@@ -165,8 +165,15 @@ struct rbfd_mesh {
     rbfd::GreedyState *h_st = nullptr;  // pinned
     // persistent engine
     int batch_ctas_cap = 0;          // set by the batch calls: blocks this mesh may use
+    int batch_share = 0;             // meshes whose greedy runs beside this one (batch calls, server)
     rbfd::GridBarrier *d_bar = nullptr;
     double *d_pred = nullptr;       // [kMaxPersistCTAs][4] per-block y.y, y.w
+    // Newton-basis launch (made on first use): V[k][i] = v_k(x_i) for k < newton_cols
+    int newton_cols = 0;
+    double *d_V = nullptr;
+    int newton_rec_rows = 0;        // blocks the records below are sized for
+    double4 *d_nrec = nullptr;      // [blocks][3] per-block candidate records
+    double *d_nycol = nullptr;      // [blocks][newton_cols + 1] their columns of V
     unsigned long long *d_phase_ns = nullptr;  // [8] persistent phase timing (profile mode)
 
     std::vector<rbfd::Level> levels;
@@ -195,6 +202,10 @@ struct rbfd_mesh {
 
 namespace rbfd {
 constexpr int kMaxPersistCTAs = 2048;
+constexpr int kNewtonCols = 4096;  // most controls a Newton-basis launch carries (y staged in shared memory)
+int newton_columns(rbfd_mesh *m);
+void newton_reserve(rbfd_mesh *m);
+void newton_run_level(rbfd_mesh *m, double R, double tau, int ctas);
 int persist_max_ctas(rbfd_mesh *m);
 void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas);
 void greedy_run(rbfd_mesh *m);

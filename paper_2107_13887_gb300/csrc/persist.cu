@@ -71,48 +71,9 @@ struct PersistArgs {
     unsigned long long *phase_ns;  // non-null: block 0 accumulates [work, wait] ns per phase (8 words)
 };
 
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 __device__ __forceinline__ uint32_t ldcg_u32(const uint32_t *p) { return __ldcg(p); }
 __device__ __forceinline__ double ldcg_d(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ float4 ldcg_f4(const float4 *p) { return __ldcg(p); }
-
-// Grid-wide barrier with a bounded wait.  Returns false (in every thread of
-// the block) if the launch is failing: this block timed out or another one did.
-__device__ __forceinline__ bool grid_sync(GridBarrier *b, unsigned nblk, unsigned long long limit) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned *vgen = &b->gen;
-        volatile int *verr = &b->err;
-        const unsigned g = *vgen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(&b->count, 1u);
-        if (arrived == nblk - 1) {
-            b->count = 0;
-            __threadfence();
-            atomicAdd(&b->gen, 1u);
-        } else {
-            unsigned long long it = 0;
-            while (*vgen == g) {
-                if (*verr) break;
-                if (++it > limit) {
-                    atomicExch(&b->err, 1);
-                    break;
-                }
-                __nanosleep(8);
-            }
-        }
-        __threadfence();
-        s_ok = (*verr == 0);
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
 
 template <int DIM, int BASIS, int MODE>
 __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {

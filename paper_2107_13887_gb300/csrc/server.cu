@@ -84,6 +84,8 @@ size_t mesh_footprint(int dim, int64_t n_s, int64_t n_v, int64_t cap) {
     b += (size_t)nch * n_s * 32;                    // sweep partials
     b += (size_t)cap * (6 * 32 + 8 * 8) + 32ull * (cap / 256 + 2) * cap;
     b += (size_t)n_v * (32 * 3 + 4 * 6);            // registered + working volume buffers
+    // Newton-basis values V: n_s doubles per column, at most kNewtonCols columns and 1 GB
+    b += std::min<size_t>((size_t)n_s * 8 * std::min<int64_t>(cap, kNewtonCols), (size_t)1 << 30);
     return b + (64ull << 20);                       // small buffers and pool rounding
 }
 
@@ -119,6 +121,7 @@ static void run_request(rbfd_server *S, uint64_t ticket, rbfd_mesh *inst) {
         }
         // the persistent grids of all slots must be resident together
         inst->batch_ctas_cap = std::max(1, persist_max_ctas(inst) / std::max(1, S->opt.slots));
+        inst->batch_share = S->opt.slots;
         try {
             greedy_run(inst);
         } catch (const Error &e) {

@@ -74,6 +74,7 @@ class rbfd_stats(ctypes.Structure):
         ("wall_launches", ctypes.c_int64),
         ("wall_pairs_search", ctypes.c_int64),
         ("wall_pairs_exact", ctypes.c_int64),
+        ("newton_steps", ctypes.c_int64),
     ]
 
 

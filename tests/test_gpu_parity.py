@@ -340,6 +340,36 @@ def test_persistent_engine_matches_step_engine(name, precision):
             assert np.array_equal(x.idx, y.idx)
 
 
+@pytest.mark.parametrize("name", ["airfoil_horns_2lvl", "wing_ridge_2lvl", "airfoil_bump_333"])
+@pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
+def test_newton_start_matches_list_sweep(name, precision, monkeypatch):
+    """Engine 0 starts every level in the Newton basis (E updated by one basis
+    function per step) and hands over to the list sweep; engine 2 runs the
+    list sweep alone.  Both pick the oracle's controls; a forced hand-over
+    after 8 Newton steps (V capped at 8 columns) does too."""
+    c = CASES[name]
+    ref = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, n_threads=NT)
+    S0 = np.sqrt((c.dS**2).sum(1)).max()
+    a = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, engine=0)
+    a.greedy()
+    assert a.stats()["newton_steps"] > 0
+    check_sequences(ref, a.levels())
+    check_valid(c, a.levels(), S0)
+    b = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, engine=2)
+    b.greedy()
+    assert b.stats()["newton_steps"] == 0
+    for x, y in zip(a.levels(), b.levels()):
+        assert np.array_equal(x.idx, y.idx)
+        assert np.abs(x.alpha - y.alpha).max() <= 1e-6 * max(np.abs(y.alpha).max(), 1e-300)
+    monkeypatch.setenv("RBFD_NEWTON_COLS", "8")
+    h = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, engine=0)
+    h.greedy()
+    st = h.stats()
+    assert 0 < st["newton_steps"] <= 7 * len(c.R)
+    for x, y in zip(h.levels(), b.levels()):
+        assert np.array_equal(x.idx, y.idx)
+
+
 def test_barrier_wait_bound_returns_timeout(monkeypatch):
     """A block that never arrives at the grid barrier (test hook) makes the
     other blocks' bounded waits run out: the launch ends and rbfd_greedy
