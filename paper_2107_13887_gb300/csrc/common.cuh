@@ -441,36 +441,26 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *b, unsigned nblk, unsigne
     return s_ok != 0;
 }
 
-// The same barrier in two halves, so that a block can do work that no other
-// block waits for between its arrival and its wait.  grid_arrive returns the
-// generation observed before arriving (to pass to grid_wait).
-__device__ __forceinline__ unsigned grid_arrive(GridBarrier *b, unsigned nblk) {
-    __shared__ unsigned s_gen;
+// A grid barrier in two halves on a monotone arrival counter (the word
+// `count` of a GridBarrier zeroed before the launch): barrier number t (from
+// 0) is passed once count reaches (t + 1) * nblk.  Arriving is a release
+// fence and an atomic add whose result nobody waits for; between arriving
+// and waiting a block can do work that no other block waits for.
+__device__ __forceinline__ void grid_arrive_mono(GridBarrier *b) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *vgen = &b->gen;
-        const unsigned g = *vgen;
         __threadfence();
-        const unsigned arrived = atomicAdd(&b->count, 1u);
-        if (arrived == nblk - 1) {
-            b->count = 0;
-            __threadfence();
-            atomicAdd(&b->gen, 1u);
-        }
-        s_gen = g;
+        atomicAdd(&b->count, 1u);
     }
-    __syncthreads();
-    return s_gen;
 }
 
-__device__ __forceinline__ bool grid_wait(GridBarrier *b, unsigned g, unsigned long long limit) {
+__device__ __forceinline__ bool grid_wait_mono(GridBarrier *b, unsigned target, unsigned long long limit) {
     __shared__ int s_ok;
-    __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *vgen = &b->gen;
+        volatile unsigned *vcnt = &b->count;
         volatile int *verr = &b->err;
         unsigned long long it = 0;
-        while (*vgen == g) {
+        while (*vcnt < target) {
             if (*verr) break;
             if (++it > limit) {
                 atomicExch(&b->err, 1);

@@ -171,6 +171,7 @@ struct rbfd_mesh {
     // Newton-basis launch (made on first use): V[k][i] = v_k(x_i) for k < newton_cols
     int newton_cols = 0;
     double *d_V = nullptr;
+    float4 *d_nwdf = nullptr;       // [cap + 1][2] w in double-float (mixed-mode Newton launch)
     int newton_rec_rows = 0;        // blocks the records below are sized for
     double4 *d_nrec = nullptr;      // [blocks][3] per-block candidate records
     double *d_nycol = nullptr;      // [blocks][newton_cols + 1] their columns of V

@@ -54,20 +54,40 @@ namespace {
 constexpr int kNT = 256;  // threads per block (8 warps)
 constexpr int kNW = kNT / 32;
 
-// Argmax by (key, index) with the keys compared as the bit patterns of
-// non-negative doubles (same order as the values; -1 marks "none"), so that no
-// comparison runs on the narrow FP64 pipe.
-__device__ __forceinline__ bool better_bits(long long ka, int ia, long long kb, int ib) {
+// Keys of the argmax as unsigned 64-bit integers in the order of the values:
+// FP64 mode, the bit pattern of the non-negative double plus one; mixed mode,
+// the high float's bits above an order-preserving image of the low float.
+// 0 means "no candidate".  Comparisons then run on the integer pipes.
+__device__ __forceinline__ unsigned long long key_of_double(double k) {
+    return (unsigned long long)__double_as_longlong(k) + 1ull;
+}
+__device__ __forceinline__ unsigned float_order(float x) {
+    const unsigned u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float float_unorder(unsigned u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+__device__ __forceinline__ unsigned long long key_of_df(df k) {  // k.hi >= 0
+    return ((unsigned long long)__float_as_uint(k.hi) << 32) | float_order(k.lo);
+}
+template <int MODE>
+__device__ __forceinline__ double key_value(unsigned long long k) {
+    if (MODE == 0) return __longlong_as_double((long long)(k - 1ull));
+    return (double)__uint_as_float((unsigned)(k >> 32)) + (double)float_unorder((unsigned)k);
+}
+
+__device__ __forceinline__ bool better_key(unsigned long long ka, int ia, unsigned long long kb, int ib) {
     return (ka > kb) || (ka == kb && ia < ib && ia >= 0) || (ib < 0 && ia >= 0);
 }
 
-__device__ __forceinline__ void block_argmax_bits(long long &k, int &i, long long *sk, int *si) {
+__device__ __forceinline__ void block_argmax_key(unsigned long long &k, int &i, unsigned long long *sk, int *si) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const long long k2 = __shfl_xor_sync(0xffffffffu, k, o);
+        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, k, o);
         const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
-        if (better_bits(k2, i2, k, i)) {
+        if (better_key(k2, i2, k, i)) {
             k = k2;
             i = i2;
         }
@@ -79,13 +99,13 @@ __device__ __forceinline__ void block_argmax_bits(long long &k, int &i, long lon
     }
     __syncthreads();
     if (w == 0) {
-        k = lane < nw ? sk[lane] : (long long)0x8000000000000000ll;
+        k = lane < nw ? sk[lane] : 0ull;
         i = lane < nw ? si[lane] : -1;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const long long k2 = __shfl_xor_sync(0xffffffffu, k, o);
+            const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, k, o);
             const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
-            if (better_bits(k2, i2, k, i)) {
+            if (better_key(k2, i2, k, i)) {
                 k = k2;
                 i = i2;
             }
@@ -100,22 +120,50 @@ __device__ __forceinline__ void block_argmax_bits(long long &k, int &i, long lon
     i = si[0];
 }
 
+// acc += y * v in double-float (TwoProduct by FMA, TwoSum on the high
+// parts, low parts summed plainly; renormalised once at the end).
+__device__ __forceinline__ void df_fma_acc(float &ah, float &al, float yh, float yl, float vh, float vl) {
+    const float p = __fmul_rn(yh, vh);
+    float pe = __fmaf_rn(yh, vh, -p);
+    pe = __fmaf_rn(yh, vl, __fmaf_rn(yl, vh, pe));
+    const float s = __fadd_rn(ah, p);
+    const float bb = __fsub_rn(s, ah);
+    const float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    ah = s;
+    al = __fadd_rn(al, __fadd_rn(pe, e));
+}
+
+// 1 / sqrt(x) of a positive double-float: FP32 estimate, two Newton steps.
+__device__ __forceinline__ df df_rsqrt(df x) {
+    df y = {rsqrtf(x.hi), 0.0f};
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const df h = df_mul(x, df_sqr(y));                       // ~ 1
+        const df r = df_add({1.5f, 0.0f}, df_mul({-0.5f, 0.0f}, h));
+        y = df_mul(y, r);
+    }
+    return y;
+}
+
 struct NewtonArgs {
     int64_t n_s;
     int n_pb, cap, cn;  // cn: columns of V (controls the launch may reach)
     int ppb, cs;        // points per block (32 per group), columns of V held in shared memory
     double R, invR, R2, S0, tau, piv_tol_per_n, switch_ratio, switch_work;
+    double K_lo, K_hi;  // (tau S0)^2 with a relative margin of 1e-12 either side
+    float invR_hi, invR_lo;
     const double4 *xs, *pb_lo, *pb_hi;
     const uint32_t *perm;
     const double4 *E0;  // E at the start of the level (= dS_l)
     unsigned char *sel;
     uint32_t *nb_cnt, *nb_list;
     double4 *cx, *alpha, *w;
+    float4 *wdf;  // mixed mode: w of each control in double-float ([2] float4 per control)
     float4 *cdf;
     uint32_t *cid;
     double *G, *Gt, *V;
-    double4 *rec;  // [2][P][3] per block: (key, original index, longest list, position), (coordinates, l^2), E
-    double *ycol;  // [2][P][cn + 1] per block: V[.][candidate]
+    double4 *rec;  // [2][P][3] per block: (key, original index, longest list, position), coordinates + l^2, E
+    double *ycol;  // [2][P][cn + 1] per block: V[.][candidate] (mixed mode: hi/lo float pairs)
     // (two copies, by the parity of the step: a block writes the next step's
     // record while a slower block may still read this step's)
     GridBarrier *bar;
@@ -126,33 +174,42 @@ struct NewtonArgs {
     int test_skip_arrival;  // tests only: block 0 leaves before its first barrier arrival
 };
 
-// Dynamic shared memory of one block: y [cn], V slice [cs][ppb], E [3][ppb],
-// coordinates [3][ppb], s2 [ppb], selected flags [ppb].
+// Dynamic shared memory of one block (8-byte words): y [cn], V slice
+// [cs][ppb], E [3][ppb], coordinates [3][ppb], s2 [ppb]; then original
+// indices [ppb] and selected flags [ppb].  Mixed mode keeps each 8-byte value
+// as a hi float array followed by a lo float array.
 inline size_t newton_smem_bytes(int cn, int cs, int ppb) {
-    return sizeof(double) * ((size_t)cn + (size_t)cs * ppb + 7 * (size_t)ppb) + (size_t)ppb;
+    return 8 * ((size_t)cn + (size_t)cs * ppb + 7 * (size_t)ppb) + 4 * (size_t)ppb + (size_t)ppb;
 }
 
-template <int DIM, int BASIS>
-__global__ void __launch_bounds__(kNT) k_greedy_newton(NewtonArgs a) {
+template <int DIM, int BASIS, int MODE>
+__global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
     extern __shared__ double dsm[];
-    double *s_y = dsm;                         // y of the control being propagated
-    double *s_V = s_y + a.cn;                  // V[k][slot], k < cs
-    double *s_E = s_V + (size_t)a.cs * a.ppb;  // E of the block's points (x, y, z rows)
-    double *s_X = s_E + 3 * a.ppb;             // their coordinates
-    double *s_S2 = s_X + 3 * a.ppb;            // sum_k v_k(x)^2
-    unsigned char *s_sel = reinterpret_cast<unsigned char *>(s_S2 + a.ppb);
-    __shared__ double s_part[kNW][32];
-    __shared__ long long sk[32];
+    const int ppb = a.ppb, n_grp = ppb / 32;
+    double *s_y = dsm;                        // FP64: y [cn]
+    float *s_yh = reinterpret_cast<float *>(dsm), *s_yl = s_yh + a.cn;  // mixed: y hi, lo
+    double *s_V = dsm + a.cn;                 // FP64: V[k][slot], k < cs
+    float *s_Vh = reinterpret_cast<float *>(s_V), *s_Vl = s_Vh + (size_t)a.cs * ppb;
+    double *s_E = s_V + (size_t)a.cs * ppb;   // E of the block's points (x, y, z rows)
+    float *s_Eh = reinterpret_cast<float *>(s_E), *s_El = s_Eh + 3 * ppb;
+    double *s_X = s_E + 3 * ppb;              // their coordinates
+    float *s_Xh = reinterpret_cast<float *>(s_X), *s_Xl = s_Xh + 3 * ppb;
+    double *s_S2 = s_X + 3 * ppb;             // sum_k v_k(x)^2
+    float *s_S2h = reinterpret_cast<float *>(s_S2), *s_S2l = s_S2h + ppb;
+    int *s_orig = reinterpret_cast<int *>(s_S2 + ppb);  // original surface index
+    unsigned char *s_sel = reinterpret_cast<unsigned char *>(s_orig + ppb);
+    __shared__ double s_part[kNW][32];        // FP64: partial dots; mixed: hi [8][32] then lo
+    __shared__ unsigned long long sk[32];
     __shared__ int si[32];
     __shared__ double s_dec[8];  // the step's scalars, computed by one warp
     __shared__ int s_flags;
     __shared__ unsigned s_nz[kNW], s_lm[kNW];
     __shared__ int s_win;
     __shared__ double4 s_wrec[3];
+    float *s_parth = reinterpret_cast<float *>(&s_part[0][0]), *s_partl = s_parth + kNW * 32;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned P = gridDim.x;
-    const int ppb = a.ppb, n_grp = ppb / 32;
     const size_t ycl = (size_t)a.cn + 1;
     // slot s of this block is surface point (blockIdx + (s / 32) P) * 32 + s % 32
     auto point_of = [&](int slot) -> int64_t {
@@ -163,13 +220,26 @@ __global__ void __launch_bounds__(kNT) k_greedy_newton(NewtonArgs a) {
         const bool valid = i < a.n_s;
         const double4 x = valid ? a.xs[i] : make_double4(0, 0, 0, 0);
         const double4 e = valid ? a.E0[i] : make_double4(0, 0, 0, 0);
-        s_X[sl] = x.x;
-        s_X[ppb + sl] = x.y;
-        s_X[2 * ppb + sl] = x.z;
-        s_E[sl] = e.x;
-        s_E[ppb + sl] = e.y;
-        s_E[2 * ppb + sl] = e.z;
-        s_S2[sl] = 0.0;
+        const double xv[3] = {x.x, x.y, x.z}, ev[3] = {e.x, e.y, e.z};
+        for (int c = 0; c < 3; ++c) {
+            if (MODE) {
+                const df xd = df_from_double(xv[c]), ed = df_from_double(ev[c]);
+                s_Xh[c * ppb + sl] = xd.hi;
+                s_Xl[c * ppb + sl] = xd.lo;
+                s_Eh[c * ppb + sl] = ed.hi;
+                s_El[c * ppb + sl] = ed.lo;
+            } else {
+                s_X[c * ppb + sl] = xv[c];
+                s_E[c * ppb + sl] = ev[c];
+            }
+        }
+        if (MODE) {
+            s_S2h[sl] = 0.f;
+            s_S2l[sl] = 0.f;
+        } else {
+            s_S2[sl] = 0.0;
+        }
+        s_orig[sl] = valid ? (int)a.perm[i] : -1;
         s_sel[sl] = valid ? __ldcg(a.sel + i) : 1;
     }
     // control lists: point block t is kept by thread t / P of block t % P
@@ -186,9 +256,13 @@ __global__ void __launch_bounds__(kNT) k_greedy_newton(NewtonArgs a) {
     // the launch starts a level: control 0 placed, nothing propagated yet
     int n = __ldcg(&a.st->n);
     uint32_t cj = __ldcg(&a.cid[0]);
+    // c_j: coordinates (FP64; mixed: double-float), 1 / l_j and w_j
     double4 xcj = ldcg_d4(&a.cx[0]);
-    double lj = 1.0, ilj = 1.0;
+    df xcd[3] = {df_from_double(xcj.x), df_from_double(xcj.y), df_from_double(xcj.z)};
+    double ilj = 1.0;
+    df ild = {1.0f, 0.0f};
     double4 wj = ldcg_d4(&a.w[0]);
+    df wd[3] = {df_from_double(wj.x), df_from_double(wj.y), df_from_double(wj.z)};
     int B = -1;  // block whose column is y of c_j
     // counts kept per block and added once at the end: nonzeros of Phi_sc in
     // this block's points so far, and the pairs a list sweep of each step
@@ -197,6 +271,7 @@ __global__ void __launch_bounds__(kNT) k_greedy_newton(NewtonArgs a) {
     uint32_t list_max = own_list ? own_cnt : 0;  // longest list this block keeps
     // rows of the inverse factor: row k belongs to warp (k / P) % 8 of block k % P
     const int k_first = (int)blockIdx.x + warp * (int)P;
+    const df invRd = {a.invR_hi, a.invR_lo};
     // profile mode, block 0: [0] y, [1] (a), [2] lists + record, [3] (b),
     // [4] barrier wait, [5] reading the records, [6] their argmax, [7] the rest
     const bool timing = a.phase_ns && blockIdx.x == 0 && tid == 0;
@@ -226,7 +301,16 @@ __global__ void __launch_bounds__(kNT) k_greedy_newton(NewtonArgs a) {
         const int j = n - 1;  // the control this pass propagates
         if (B >= 0) {  // written in the previous pass, parity (j - 1) & 1
             const double *yb = a.ycol + ((size_t)((j - 1) & 1) * P + B) * ycl;
-            for (int k = tid; k < j; k += kNT) s_y[k] = __ldcg(&yb[k]);
+            if (MODE) {
+                const float2 *yf = reinterpret_cast<const float2 *>(yb);
+                for (int k = tid; k < j; k += kNT) {
+                    const float2 v = __ldcg(&yf[k]);
+                    s_yh[k] = v.x;
+                    s_yl[k] = v.y;
+                }
+            } else {
+                for (int k = tid; k < j; k += kNT) s_y[k] = __ldcg(&yb[k]);
+            }
         }
         {  // the owner marks c_j as selected
             const int64_t item = (int64_t)cj / 32;
@@ -236,7 +320,7 @@ __global__ void __launch_bounds__(kNT) k_greedy_newton(NewtonArgs a) {
         RBFD_TMARK(0)
 
         // ---- (a) v_j at the block's points, E update, argmax
-        long long bkey = __double_as_longlong(-1.0);
+        unsigned long long bkey = 0;
         int bidx = -1, bslot = -1;
         unsigned nz = 0;
         const int kcs = min(j, a.cs);
@@ -245,57 +329,117 @@ __global__ void __launch_bounds__(kNT) k_greedy_newton(NewtonArgs a) {
             const int64_t i = point_of(sl);
             const bool valid = i < a.n_s;
             double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
             if (valid) {
-                const double *Vs = s_V + sl;
                 int k = warp;
-                for (; k + 3 * kNW < kcs; k += 4 * kNW) {
-                    s0 = fma(s_y[k], Vs[(size_t)k * ppb], s0);
-                    s1 = fma(s_y[k + kNW], Vs[(size_t)(k + kNW) * ppb], s1);
-                    s2 = fma(s_y[k + 2 * kNW], Vs[(size_t)(k + 2 * kNW) * ppb], s2);
-                    s3 = fma(s_y[k + 3 * kNW], Vs[(size_t)(k + 3 * kNW) * ppb], s3);
+                if (MODE) {
+                    // double-float on the FP32 pipe (FP64 issues at a small
+                    // fraction of the FP32 rate on this GPU)
+                    const float *Vh = s_Vh + sl, *Vl = s_Vl + sl;
+                    for (; k + kNW < kcs; k += 2 * kNW) {
+                        df_fma_acc(h0, l0, s_yh[k], s_yl[k], Vh[(size_t)k * ppb], Vl[(size_t)k * ppb]);
+                        df_fma_acc(h1, l1, s_yh[k + kNW], s_yl[k + kNW], Vh[(size_t)(k + kNW) * ppb],
+                                   Vl[(size_t)(k + kNW) * ppb]);
+                    }
+                    for (; k < kcs; k += kNW)
+                        df_fma_acc(h0, l0, s_yh[k], s_yl[k], Vh[(size_t)k * ppb], Vl[(size_t)k * ppb]);
+                    // columns beyond the shared slice: FP64 values from global memory
+                    const double *Vi = a.V + i;
+                    for (; k < j; k += kNW) {
+                        const df v = df_from_double(__ldcg(Vi + (size_t)k * a.n_s));
+                        df_fma_acc(h0, l0, s_yh[k], s_yl[k], v.hi, v.lo);
+                    }
+                } else {
+                    const double *Vs = s_V + sl;
+                    for (; k + 3 * kNW < kcs; k += 4 * kNW) {
+                        s0 = fma(s_y[k], Vs[(size_t)k * ppb], s0);
+                        s1 = fma(s_y[k + kNW], Vs[(size_t)(k + kNW) * ppb], s1);
+                        s2 = fma(s_y[k + 2 * kNW], Vs[(size_t)(k + 2 * kNW) * ppb], s2);
+                        s3 = fma(s_y[k + 3 * kNW], Vs[(size_t)(k + 3 * kNW) * ppb], s3);
+                    }
+                    for (; k < kcs; k += kNW) s0 = fma(s_y[k], Vs[(size_t)k * ppb], s0);
+                    const double *Vi = a.V + i;
+                    const size_t ld = (size_t)a.n_s;
+                    for (; k + 3 * kNW < j; k += 4 * kNW) {
+                        const double v0 = __ldcg(Vi + (size_t)k * ld), v1 = __ldcg(Vi + (size_t)(k + kNW) * ld),
+                                     v2 = __ldcg(Vi + (size_t)(k + 2 * kNW) * ld),
+                                     v3 = __ldcg(Vi + (size_t)(k + 3 * kNW) * ld);
+                        s0 = fma(s_y[k], v0, s0);
+                        s1 = fma(s_y[k + kNW], v1, s1);
+                        s2 = fma(s_y[k + 2 * kNW], v2, s2);
+                        s3 = fma(s_y[k + 3 * kNW], v3, s3);
+                    }
+                    for (; k < j; k += kNW) s0 = fma(s_y[k], __ldcg(Vi + (size_t)k * ld), s0);
                 }
-                for (; k < kcs; k += kNW) s0 = fma(s_y[k], Vs[(size_t)k * ppb], s0);
-                // columns beyond the shared slice come from global memory
-                const double *Vi = a.V + i;
-                const size_t ld = (size_t)a.n_s;
-                for (; k + 3 * kNW < j; k += 4 * kNW) {
-                    const double v0 = __ldcg(Vi + (size_t)k * ld), v1 = __ldcg(Vi + (size_t)(k + kNW) * ld),
-                                 v2 = __ldcg(Vi + (size_t)(k + 2 * kNW) * ld),
-                                 v3 = __ldcg(Vi + (size_t)(k + 3 * kNW) * ld);
-                    s0 = fma(s_y[k], v0, s0);
-                    s1 = fma(s_y[k + kNW], v1, s1);
-                    s2 = fma(s_y[k + 2 * kNW], v2, s2);
-                    s3 = fma(s_y[k + 3 * kNW], v3, s3);
-                }
-                for (; k < j; k += kNW) s0 = fma(s_y[k], __ldcg(Vi + (size_t)k * ld), s0);
             }
-            s_part[warp][lane] = (s0 + s1) + (s2 + s3);
+            if (MODE) {
+                const df t = df_add({h0, l0}, {h1, l1});
+                s_parth[warp * 32 + lane] = t.hi;
+                s_partl[warp * 32 + lane] = t.lo;
+            } else {
+                s_part[warp][lane] = (s0 + s1) + (s2 + s3);
+            }
             __syncthreads();
             if (warp == 0 && valid) {
-                double sum = s_part[0][lane];
+                unsigned long long key;
+                if (MODE) {
+                    df sum = {s_parth[lane], s_partl[lane]};
 #pragma unroll
-                for (int w8 = 1; w8 < kNW; ++w8) sum += s_part[w8][lane];
-                const double f = phi_f64<BASIS>(
-                    dist_f64<DIM>(s_X[sl], s_X[ppb + sl], s_X[2 * ppb + sl], xcj.x, xcj.y, xcj.z) * a.invR);
-                nz += (f != 0.0);
-                const double v = (f - sum) * ilj;
-                if (j < a.cs) s_V[(size_t)j * ppb + sl] = v;
-                a.V[(size_t)j * a.n_s + i] = v;
-                const double e0 = fma(-wj.x, v, s_E[sl]);
-                const double e1 = fma(-wj.y, v, s_E[ppb + sl]);
-                const double e2 = DIM == 3 ? fma(-wj.z, v, s_E[2 * ppb + sl]) : 0.0;
-                s_E[sl] = e0;
-                s_E[ppb + sl] = e1;
-                s_E[2 * ppb + sl] = e2;
-                s_S2[sl] = fma(v, v, s_S2[sl]);
-                double k2 = __dmul_rn(e0, e0);
-                k2 = __dadd_rn(k2, __dmul_rn(e1, e1));
-                if (DIM == 3) k2 = __dadd_rn(k2, __dmul_rn(e2, e2));
+                    for (int w8 = 1; w8 < kNW; ++w8) sum = df_add(sum, {s_parth[w8 * 32 + lane], s_partl[w8 * 32 + lane]});
+                    df r2 = {0.f, 0.f};
+#pragma unroll
+                    for (int c = 0; c < DIM; ++c) {
+                        const df d = df_add({s_Xh[c * ppb + sl], s_Xl[c * ppb + sl]}, df_neg(xcd[c]));
+                        r2 = df_add(r2, df_sqr(d));
+                    }
+                    const df f = phi_df<BASIS>(df_mul(df_sqrt(r2), invRd));
+                    nz += (f.hi != 0.f);
+                    const df v = df_mul(df_add(f, df_neg(sum)), ild);
+                    if (j < a.cs) {
+                        s_Vh[(size_t)j * ppb + sl] = v.hi;
+                        s_Vl[(size_t)j * ppb + sl] = v.lo;
+                    } else {
+                        a.V[(size_t)j * a.n_s + i] = df_to_double(v);
+                    }
+                    df k2 = {0.f, 0.f};
+#pragma unroll
+                    for (int c = 0; c < DIM; ++c) {
+                        df e = {s_Eh[c * ppb + sl], s_El[c * ppb + sl]};
+                        e = df_add(e, df_neg(df_mul(wd[c], v)));
+                        s_Eh[c * ppb + sl] = e.hi;
+                        s_El[c * ppb + sl] = e.lo;
+                        k2 = df_add(k2, df_sqr(e));
+                    }
+                    const df s2n = df_add({s_S2h[sl], s_S2l[sl]}, df_sqr(v));
+                    s_S2h[sl] = s2n.hi;
+                    s_S2l[sl] = s2n.lo;
+                    key = key_of_df(k2);
+                } else {
+                    double sum = s_part[0][lane];
+#pragma unroll
+                    for (int w8 = 1; w8 < kNW; ++w8) sum += s_part[w8][lane];
+                    const double f = phi_f64<BASIS>(
+                        dist_f64<DIM>(s_X[sl], s_X[ppb + sl], s_X[2 * ppb + sl], xcj.x, xcj.y, xcj.z) * a.invR);
+                    nz += (f != 0.0);
+                    const double v = (f - sum) * ilj;
+                    if (j < a.cs) s_V[(size_t)j * ppb + sl] = v;
+                    else a.V[(size_t)j * a.n_s + i] = v;
+                    const double e0 = fma(-wj.x, v, s_E[sl]);
+                    const double e1 = fma(-wj.y, v, s_E[ppb + sl]);
+                    const double e2 = DIM == 3 ? fma(-wj.z, v, s_E[2 * ppb + sl]) : 0.0;
+                    s_E[sl] = e0;
+                    s_E[ppb + sl] = e1;
+                    s_E[2 * ppb + sl] = e2;
+                    s_S2[sl] = fma(v, v, s_S2[sl]);
+                    double k2 = __dmul_rn(e0, e0);
+                    k2 = __dadd_rn(k2, __dmul_rn(e1, e1));
+                    if (DIM == 3) k2 = __dadd_rn(k2, __dmul_rn(e2, e2));
+                    key = key_of_double(k2);
+                }
                 if (!s_sel[sl]) {
-                    const int o = (int)a.perm[i];
-                    const long long kb = __double_as_longlong(k2);
-                    if (better_bits(kb, o, bkey, bidx)) {
-                        bkey = kb;
+                    const int o = s_orig[sl];
+                    if (better_key(key, o, bkey, bidx)) {
+                        bkey = key;
                         bidx = o;
                         bslot = sl;
                     }
@@ -317,9 +461,9 @@ __global__ void __launch_bounds__(kNT) k_greedy_newton(NewtonArgs a) {
             }
         }
         {
-            long long kk = bkey;
+            unsigned long long kk = bkey;
             int ii = bidx;
-            block_argmax_bits(kk, ii, sk, si);  // (ends with __syncthreads)
+            block_argmax_key(kk, ii, sk, si);  // (ends with __syncthreads)
             if (ii >= 0 && bidx == ii) s_win = bslot;  // the one thread holding it
             unsigned u = nz;
             for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
@@ -341,63 +485,95 @@ __global__ void __launch_bounds__(kNT) k_greedy_newton(NewtonArgs a) {
                 pairs_useful += nz_cum;  // the list sweep of this step would evaluate these pairs
                 double4 *r = a.rec + 3 * ((size_t)(j & 1) * P + blockIdx.x);
                 if (ws >= 0) {
-                    r[0] = make_double4(__longlong_as_double(kk), (double)ii, (double)list_max, (double)point_of(ws));
-                    r[1] = make_double4(s_X[ws], s_X[ppb + ws], s_X[2 * ppb + ws], 1.0 - s_S2[ws]);
-                    r[2] = make_double4(s_E[ws], s_E[ppb + ws], s_E[2 * ppb + ws], 0.0);
+                    r[0] = make_double4(__longlong_as_double((long long)kk), (double)ii, (double)list_max,
+                                        (double)point_of(ws));
+                    if (MODE) {
+                        float4 *rf = reinterpret_cast<float4 *>(r + 1);
+                        const df l2 = df_add({1.0f, 0.0f}, df_neg({s_S2h[ws], s_S2l[ws]}));
+                        rf[0] = make_float4(s_Xh[ws], s_Xl[ws], s_Xh[ppb + ws], s_Xl[ppb + ws]);
+                        rf[1] = make_float4(s_Xh[2 * ppb + ws], s_Xl[2 * ppb + ws], l2.hi, l2.lo);
+                        rf[2] = make_float4(s_Eh[ws], s_El[ws], s_Eh[ppb + ws], s_El[ppb + ws]);
+                        rf[3] = make_float4(s_Eh[2 * ppb + ws], s_El[2 * ppb + ws], 0.f, 0.f);
+                    } else {
+                        r[1] = make_double4(s_X[ws], s_X[ppb + ws], s_X[2 * ppb + ws], 1.0 - s_S2[ws]);
+                        r[2] = make_double4(s_E[ws], s_E[ppb + ws], s_E[2 * ppb + ws], 0.0);
+                    }
                 } else {
-                    r[0] = make_double4(-1.0, -1.0, (double)list_max, -1.0);
+                    r[0] = make_double4(__longlong_as_double(0ll), -1.0, (double)list_max, -1.0);
                 }
             }
             if (ws >= 0) {  // the candidate's column: y of the next control if it wins
                 const int64_t pw = point_of(ws);
                 double *yc = a.ycol + ((size_t)(j & 1) * P + blockIdx.x) * ycl;
-                for (int k = tid; k <= j; k += kNT)
-                    yc[k] = k < a.cs ? s_V[(size_t)k * ppb + ws] : __ldcg(a.V + (size_t)k * a.n_s + pw);
+                if (MODE) {
+                    float2 *yf = reinterpret_cast<float2 *>(yc);
+                    for (int k = tid; k <= j; k += kNT) {
+                        float2 v;
+                        if (k < a.cs) {
+                            v = make_float2(s_Vh[(size_t)k * ppb + ws], s_Vl[(size_t)k * ppb + ws]);
+                        } else {
+                            const df d = df_from_double(__ldcg(a.V + (size_t)k * a.n_s + pw));
+                            v = make_float2(d.hi, d.lo);
+                        }
+                        yf[k] = v;
+                    }
+                } else {
+                    for (int k = tid; k <= j; k += kNT)
+                        yc[k] = k < a.cs ? s_V[(size_t)k * ppb + ws] : __ldcg(a.V + (size_t)k * a.n_s + pw);
+                }
             }
         }
         RBFD_TMARK(2)
         if (a.test_skip_arrival && blockIdx.x == 0) return;  // the others' waits run out
-        const unsigned gen = grid_arrive(a.bar, P);
+        grid_arrive_mono(a.bar);
 
-        // ---- (b) row j of the inverse factor on this block's rows, alpha
-        for (int k = k_first; k <= j; k += (int)P * kNW) {
-            if (k == j) {  // the diagonal and alpha_j
-                if (lane == 0) {
-                    a.G[(size_t)j * a.cap + j] = ilj;
-                    a.Gt[(size_t)j * a.cap + j] = ilj;
-                    a.alpha[j] = make_double4(wj.x * ilj, wj.y * ilj, wj.z * ilj, 0.0);
+        // ---- (b) row j of the inverse factor on this block's rows, alpha (FP64)
+        {
+            double ilj64 = ilj;
+            double4 wj64 = wj;
+            if (MODE) {
+                ilj64 = df_to_double(ild);
+                wj64 = make_double4(df_to_double(wd[0]), df_to_double(wd[1]), df_to_double(wd[2]), 0.0);
+            }
+            for (int k = k_first; k <= j; k += (int)P * kNW) {
+                if (k == j) {  // the diagonal and alpha_j
+                    if (lane == 0) {
+                        a.G[(size_t)j * a.cap + j] = ilj64;
+                        a.Gt[(size_t)j * a.cap + j] = ilj64;
+                        a.alpha[j] = make_double4(wj64.x * ilj64, wj64.y * ilj64, wj64.z * ilj64, 0.0);
+                    }
+                    break;
                 }
-                break;
-            }
-            const double *trow = a.Gt + (size_t)k * a.cap;
-            double4 al = make_double4(0, 0, 0, 0);
-            if (lane == 0) al = ldcg_d4(&a.alpha[k]);
-            double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
-            int m = k + lane;
-            for (; m + 96 < j; m += 128) {
-                t0 = fma(__ldcg(trow + m), s_y[m], t0);
-                t1 = fma(__ldcg(trow + m + 32), s_y[m + 32], t1);
-                t2 = fma(__ldcg(trow + m + 64), s_y[m + 64], t2);
-                t3 = fma(__ldcg(trow + m + 96), s_y[m + 96], t3);
-            }
-            for (; m < j; m += 32) t0 = fma(__ldcg(trow + m), s_y[m], t0);
-            const double t = warp_sum_d((t0 + t1) + (t2 + t3));
-            if (lane == 0) {
-                const double gk = -t * ilj;
-                a.G[(size_t)j * a.cap + k] = gk;
-                a.Gt[(size_t)k * a.cap + j] = gk;
-                al.x = fma(wj.x, gk, al.x);
-                al.y = fma(wj.y, gk, al.y);
-                al.z = fma(wj.z, gk, al.z);
-                a.alpha[k] = al;
+                const double *trow = a.Gt + (size_t)k * a.cap;
+                double4 al = make_double4(0, 0, 0, 0);
+                if (lane == 0) al = ldcg_d4(&a.alpha[k]);
+                double t0 = 0.0, t1 = 0.0;
+                for (int m = k + lane; m < j; m += 64) {
+                    const double y0 = MODE ? (double)s_yh[m] + (double)s_yl[m] : s_y[m];
+                    t0 = fma(__ldcg(trow + m), y0, t0);
+                    if (m + 32 < j) {
+                        const double y1 = MODE ? (double)s_yh[m + 32] + (double)s_yl[m + 32] : s_y[m + 32];
+                        t1 = fma(__ldcg(trow + m + 32), y1, t1);
+                    }
+                }
+                const double t = warp_sum_d(t0 + t1);
+                if (lane == 0) {
+                    const double gk = -t * ilj64;
+                    a.G[(size_t)j * a.cap + k] = gk;
+                    a.Gt[(size_t)k * a.cap + j] = gk;
+                    al.x = fma(wj64.x, gk, al.x);
+                    al.y = fma(wj64.y, gk, al.y);
+                    al.z = fma(wj64.z, gk, al.z);
+                    a.alpha[k] = al;
+                }
             }
         }
         RBFD_TMARK(3)
-        if (!grid_wait(a.bar, gen, a.spin_limit)) RBFD_NEXIT()
+        if (!grid_wait_mono(a.bar, (unsigned)(guard + 1) * P, a.spin_limit)) RBFD_NEXIT()
         RBFD_TMARK(4)
 
         // ---- the step's decision: every block from the same records
-        long long K = __double_as_longlong(-1.0);
+        unsigned long long K = 0;
         int I = -1, Bw = -1;
         unsigned lmax = 0;
         double4 r0 = make_double4(0, 0, 0, 0), r1 = r0, r2 = r0;
@@ -408,8 +584,8 @@ __global__ void __launch_bounds__(kNT) k_greedy_newton(NewtonArgs a) {
             const double4 q2 = ldcg_d4(&rj[3 * (size_t)b + 2]);
             lmax = max(lmax, (unsigned)q0.z);
             const int ib = (int)q0.y;
-            const long long kb = __double_as_longlong(q0.x);
-            if (better_bits(kb, ib, K, I)) {
+            const unsigned long long kb = (unsigned long long)__double_as_longlong(q0.x);
+            if (better_key(kb, ib, K, I)) {
                 K = kb;
                 I = ib;
                 Bw = (int)b;
@@ -422,9 +598,9 @@ __global__ void __launch_bounds__(kNT) k_greedy_newton(NewtonArgs a) {
         if (lane == 0) s_lm[warp] = lmax;
         RBFD_TMARK(5)
         {
-            const long long kk = K;
+            const unsigned long long kk = K;
             const int ii = I;
-            block_argmax_bits(K, I, sk, si);  // (its barriers also publish s_lm)
+            block_argmax_key(K, I, sk, si);  // (its barriers also publish s_lm)
             if (I >= 0 && ii == I && kk == K) {
                 s_win = Bw;
                 s_wrec[0] = r0;
@@ -434,48 +610,82 @@ __global__ void __launch_bounds__(kNT) k_greedy_newton(NewtonArgs a) {
             __syncthreads();
         }
         RBFD_TMARK(6)
-        // the step's scalars in FP64, on one warp
         const int nn = n;  // index the next control takes
-        if (warp == 0) {
+        if (warp == 0) {  // the step's scalars, on one warp
             int mc = 1;
             for (int w8 = 0; w8 < kNW; ++w8) mc = max(mc, (int)s_lm[w8]);
-            const double Kd = __longlong_as_double(K);
-            const double e = I >= 0 ? __ddiv_rn(__dsqrt_rn(Kd), a.S0) : 0.0;
-            const bool stop = I < 0 || e < a.tau || nn >= a.cap;
+            // e = sqrt(K) / S0 < tau, the same rounded test as the other
+            // engines; the square root and the division only near the threshold
+            bool below;
+            if (I < 0) {
+                below = true;
+            } else {
+                const double Kd = key_value<MODE>(K);
+                if (Kd < a.K_lo) below = true;
+                else if (Kd > a.K_hi) below = false;
+                else below = __ddiv_rn(__dsqrt_rn(Kd), a.S0) < a.tau;
+            }
+            const bool stop = I < 0 || below || nn >= a.cap;
             // hand over to the list sweep when V is full, or when the Newton
             // update (n_s * n multiply-adds) is large and the lists are much
             // shorter than the control count
             const bool hand = !stop && (nn >= a.cn || ((double)a.n_s * nn > a.switch_work &&
                                                        (double)nn > a.switch_ratio * (double)mc));
-            const double l2 = stop ? 1.0 : s_wrec[1].w;
-            const bool singular = !stop && !hand && !(l2 > a.piv_tol_per_n * (nn + 1));
+            bool singular = false;
+            if (!stop && !hand) {
+                if (MODE) {
+                    const float4 *rf = reinterpret_cast<const float4 *>(&s_wrec[1]);
+                    const df l2 = {rf[1].z, rf[1].w};
+                    singular = !(l2.hi > (float)(a.piv_tol_per_n * (nn + 1)));
+                    if (!singular && lane == 0) {
+                        const df il = df_rsqrt(l2);
+                        s_dec[2] = __longlong_as_double((long long)(((unsigned long long)__float_as_uint(il.hi) << 32) |
+                                                                    __float_as_uint(il.lo)));
+                    }
+                } else {
+                    const double l2 = s_wrec[1].w;
+                    singular = !(l2 > a.piv_tol_per_n * (nn + 1));
+                    if (!singular && lane == 0) {
+                        // 1 / sqrt(l2): FP32 estimate and two Newton steps in FP64
+                        double il = (double)rsqrtf((float)l2);
+                        il = il * fma(-0.5 * l2 * il, il, 1.5);
+                        il = il * fma(-0.5 * l2 * il, il, 1.5);
+                        s_dec[2] = il;
+                    }
+                }
+            }
             if (lane == 0) {
                 s_flags = (stop ? 1 : 0) | (hand ? 2 : 0) | (singular ? 4 : 0);
-                s_dec[0] = e;
                 s_dec[1] = (double)mc;
-                if (!(stop || hand || singular)) {
-                    const double l = sqrt(l2), il = 1.0 / l;
-                    s_dec[2] = l;
-                    s_dec[3] = il;
-                    s_dec[4] = s_wrec[2].x * il;
-                    s_dec[5] = s_wrec[2].y * il;
-                    s_dec[6] = s_wrec[2].z * il;
-                }
             }
         }
         __syncthreads();
         const int flags = s_flags;
         const bool writer = blockIdx.x == 0 && tid == 0;
         if (flags) {
-            if (tid == 0) {
-                atomicAdd(&a.pairs[0], pairs_useful);
+            if (tid == 0) atomicAdd(&a.pairs[0], pairs_useful);
+            if (blockIdx.x == 0) {
+                if (MODE)  // the controls' records in FP64 for what follows the launch
+                    for (int k = 1 + tid; k < nn; k += kNT) {
+                        const double4 x = a.xs[__ldcg(&a.cid[k])];
+                        const float hx = __double2float_rn(x.x), hy = __double2float_rn(x.y),
+                                    hz = __double2float_rn(x.z);
+                        a.cx[k] = x;
+                        a.cdf[k] = make_float4(hx, hy, hz, 0.f);
+                        a.cdf[a.cap + 1 + k] = make_float4(__double2float_rn(x.x - (double)hx),
+                                                           __double2float_rn(x.y - (double)hy),
+                                                           __double2float_rn(x.z - (double)hz), 0.f);
+                        const float4 w0 = __ldcg(&a.wdf[2 * k]), w1 = __ldcg(&a.wdf[2 * k + 1]);
+                        a.w[k] = make_double4((double)w0.x + (double)w0.y, (double)w0.z + (double)w0.w,
+                                              (double)w1.x + (double)w1.y, 0.0);
+                    }
                 if (writer) {
                     const bool stop = flags & 1, hand = flags & 2, singular = flags & 4;
-                    const double e = s_dec[0];
+                    const double e = I >= 0 ? __ddiv_rn(__dsqrt_rn(key_value<MODE>(K)), a.S0) : 0.0;
                     // a list sweep visits n_s x (controls so far) pairs per step
                     a.pairs[1] += (unsigned long long)a.n_s * (unsigned long long)(nn) * (unsigned long long)(nn + 1) / 2;
                     a.st->best_orig = I;
-                    a.st->best_key = __longlong_as_double(K);
+                    a.st->best_key = I >= 0 ? key_value<MODE>(K) : -1.0;
                     a.st->emax = e;
                     a.st->max_cnt = (int)s_dec[1];
                     a.st->n = nn;
@@ -488,24 +698,45 @@ __global__ void __launch_bounds__(kNT) k_greedy_newton(NewtonArgs a) {
             RBFD_TMARK(7)
             RBFD_NEXIT()
         }
-        const double4 wr0 = s_wrec[0], wr1 = s_wrec[1], wr2 = s_wrec[2];
         B = s_win;
-        xcj = make_double4(wr1.x, wr1.y, wr1.z, 0.0);
-        cj = (uint32_t)wr0.w;
-        lj = s_dec[2];
-        ilj = s_dec[3];
-        wj = make_double4(s_dec[4], s_dec[5], s_dec[6], 0.0);
-        (void)wr2;
-        if (writer) {
-            const float hx = __double2float_rn(xcj.x), hy = __double2float_rn(xcj.y), hz = __double2float_rn(xcj.z);
-            a.sel[cj] = 1;
-            a.cx[nn] = xcj;
-            a.cdf[nn] = make_float4(hx, hy, hz, 0.f);
-            a.cdf[a.cap + 1 + nn] = make_float4(__double2float_rn(xcj.x - (double)hx),
-                                                __double2float_rn(xcj.y - (double)hy),
-                                                __double2float_rn(xcj.z - (double)hz), 0.f);
-            a.cid[nn] = cj;
-            a.w[nn] = wj;
+        cj = (uint32_t)s_wrec[0].w;
+        if (MODE) {
+            const float4 *rf = reinterpret_cast<const float4 *>(&s_wrec[1]);
+            xcd[0] = {rf[0].x, rf[0].y};
+            xcd[1] = {rf[0].z, rf[0].w};
+            xcd[2] = {rf[1].x, rf[1].y};
+            const unsigned long long ib = (unsigned long long)__double_as_longlong(s_dec[2]);
+            ild = {__uint_as_float((unsigned)(ib >> 32)), __uint_as_float((unsigned)ib)};
+            const float4 *ef = reinterpret_cast<const float4 *>(&s_wrec[2]);
+            wd[0] = df_mul({ef[0].x, ef[0].y}, ild);
+            wd[1] = df_mul({ef[0].z, ef[0].w}, ild);
+            wd[2] = df_mul({ef[1].x, ef[1].y}, ild);
+            // FP64 coordinates of c_j for the list test: exact from the split
+            xcj = make_double4((double)xcd[0].hi + (double)xcd[0].lo, (double)xcd[1].hi + (double)xcd[1].lo,
+                               (double)xcd[2].hi + (double)xcd[2].lo, 0.0);
+            if (writer) {
+                a.sel[cj] = 1;
+                a.cid[nn] = cj;
+                a.wdf[2 * nn] = make_float4(wd[0].hi, wd[0].lo, wd[1].hi, wd[1].lo);
+                a.wdf[2 * nn + 1] = make_float4(wd[2].hi, wd[2].lo, 0.f, 0.f);
+            }
+        } else {
+            ilj = s_dec[2];
+            const double4 wr1 = s_wrec[1], wr2 = s_wrec[2];
+            xcj = make_double4(wr1.x, wr1.y, wr1.z, 0.0);
+            wj = make_double4(wr2.x * ilj, wr2.y * ilj, wr2.z * ilj, 0.0);
+            if (writer) {
+                const float hx = __double2float_rn(xcj.x), hy = __double2float_rn(xcj.y),
+                            hz = __double2float_rn(xcj.z);
+                a.sel[cj] = 1;
+                a.cx[nn] = xcj;
+                a.cdf[nn] = make_float4(hx, hy, hz, 0.f);
+                a.cdf[a.cap + 1 + nn] = make_float4(__double2float_rn(xcj.x - (double)hx),
+                                                    __double2float_rn(xcj.y - (double)hy),
+                                                    __double2float_rn(xcj.z - (double)hz), 0.f);
+                a.cid[nn] = cj;
+                a.w[nn] = wj;
+            }
         }
         ++n;
         RBFD_TMARK(7)
@@ -517,13 +748,14 @@ __global__ void __launch_bounds__(kNT) k_greedy_newton(NewtonArgs a) {
 }
 
 template <int DIM, int BASIS>
-const void *newton_ptr() {
-    return reinterpret_cast<const void *>(&k_greedy_newton<DIM, BASIS>);
+const void *newton_ptr(int mode) {
+    return mode ? reinterpret_cast<const void *>(&k_greedy_newton<DIM, BASIS, 1>)
+                : reinterpret_cast<const void *>(&k_greedy_newton<DIM, BASIS, 0>);
 }
 
-const void *select_newton(int dim, int basis) {
+const void *select_newton(int dim, int basis, int mode) {
 #define RBFD_SEL(D, B) \
-    if (dim == D && basis == B) return newton_ptr<D, B>();
+    if (dim == D && basis == B) return newton_ptr<D, B>(mode);
     RBFD_SEL(2, 0) RBFD_SEL(2, 2) RBFD_SEL(2, 4) RBFD_SEL(2, 6)
     RBFD_SEL(3, 0) RBFD_SEL(3, 2) RBFD_SEL(3, 4) RBFD_SEL(3, 6)
 #undef RBFD_SEL
@@ -548,6 +780,7 @@ void newton_reserve(rbfd_mesh *m) {
     m->newton_cols = cn;
     if (cn < 2) return;
     m->d_V = dalloc<double>((size_t)cn * (size_t)m->n_s, "Newton basis values");
+    m->d_nwdf = dalloc<float4>((size_t)2 * (m->cap + 1), "Newton weights (double-float)");
 }
 
 // Blocks and shared-memory layout of a launch on this mesh: ppb points per
@@ -558,7 +791,8 @@ struct NewtonShape {
 };
 
 NewtonShape newton_shape(rbfd_mesh *m, int want_ctas) {
-    const void *k = select_newton(m->dim, m->opt.basis);
+    const int mode = m->opt.precision == RBFD_FP64 ? 0 : 1;
+    const void *k = select_newton(m->dim, m->opt.basis, mode);
     static const size_t kSmemMax = 220 * 1024;  // dynamic shared memory per block (of 227 KB)
     NewtonShape s;
     int sms = 0;
@@ -603,9 +837,13 @@ void newton_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
     a.cs = sh.cs;
     a.R = R;
     a.invR = 1.0 / R;
+    a.invR_hi = (float)a.invR;
+    a.invR_lo = (float)(a.invR - (double)a.invR_hi);
     a.R2 = R * R;
     a.S0 = m->S0;
     a.tau = tau;
+    a.K_lo = (tau * m->S0) * (tau * m->S0) * (1.0 - 1e-12);
+    a.K_hi = (tau * m->S0) * (tau * m->S0) * (1.0 + 1e-12);
     a.piv_tol_per_n = 8.0 * 1.1102230246251565e-16;
     a.switch_ratio = 3.0;
     a.switch_work = 2e7;  // ~30 us of FP64 multiply-adds per step
@@ -621,6 +859,7 @@ void newton_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
     a.cx = m->d_cx;
     a.alpha = m->d_alpha;
     a.w = m->d_w;
+    a.wdf = m->d_nwdf;
     a.cdf = m->d_cdf;
     a.cid = m->d_cid;
     a.G = m->d_G;
@@ -646,7 +885,7 @@ void newton_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
     a.st = m->d_st;
     a.pairs = m->d_pairs;
     a.phase_ns = m->prof.on ? m->d_phase_ns : nullptr;
-    const void *k = select_newton(m->dim, m->opt.basis);
+    const void *k = select_newton(m->dim, m->opt.basis, m->opt.precision == RBFD_FP64 ? 0 : 1);
     void *args[] = {&a};
     RBFD_CUDA(cudaLaunchCooperativeKernel(k, dim3(sh.ctas), dim3(kNT), args, sh.smem, m->stream));
     m->stats.launches += 1;

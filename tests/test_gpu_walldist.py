@@ -6,7 +6,6 @@ oracle evaluates (differences, squares and sums rounded once each, in axis
 order, then a correctly rounded square root), so the bar is bit-for-bit
 equality, also at full size on sampled points.
 """
-import dataclasses
 import os
 
 import numpy as np
@@ -14,7 +13,6 @@ import pytest
 
 import oracle
 from paper_2107_13887_gb300 import rbfd, synth
-from test_gpu_parity import fp64_volume_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -155,23 +153,29 @@ def _ref_deform(c, ref, d):
     return oracle.deform(ref, c.xyz_s, c.R, c.xyz_v, d, c.k, c.D, n_threads=NT)
 
 
+def _gpu_levels_as_reference(c, m):
+    """The GPU's own controls and weights in the oracle's result type, so
+    that the FP64 volume update of the oracle uses exactly them."""
+    lv = m.levels()
+    return oracle.GreedyResult(status=0, idx=[l.idx for l in lv], alpha=[l.alpha for l in lv],
+                               smax=np.array([l.smax for l in lv]), emax=np.array([l.e_max for l in lv]),
+                               gap=np.zeros(len(lv)), E=None, S0=float(np.sqrt((c.dS**2).sum(1)).max()))
+
+
 @pytest.mark.parametrize("name", ["airfoil_333", "wing_40x15"])
 @pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
 def test_deform_with_device_wall_distance(name, precision):
-    """rbfd_deform with d_v = NULL equals the oracle's volume update fed the
-    oracle's exact wall distances (the FP64 and mixed bars of the volume
-    parity tests)."""
+    """rbfd_deform with d_v = NULL equals the oracle's FP64 volume update on
+    the same controls and weights fed the oracle's exact wall distances
+    (FP64: 1e-10 max|dS|; mixed: 1e-5 max|dS|, the volume parity bars)."""
     c = CASES[name]()
-    ref = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, n_threads=NT)
-    d = wall_ref(c.xyz_s, c.xyz_v)
-    want = _ref_deform(c, ref, d)
     m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision)
     m.greedy()
+    ref = _gpu_levels_as_reference(c, m)
+    d = wall_ref(c.xyz_s, c.xyz_v)
+    want = _ref_deform(c, ref, d)
     got = m.deform(c.xyz_v, None, c.D, c.k).astype(np.float64)
-    if precision == rbfd.FP64:
-        tol = fp64_volume_tol(dataclasses.replace(c, d_v=d), ref)
-    else:
-        tol = 1e-5 * ref.S0
+    tol = (1e-10 if precision == rbfd.FP64 else 1e-5) * ref.S0
     assert np.abs(got - want).max() <= tol + np.abs(want).max() * 2.0**-24
     # FP64 coordinates as well
     if precision == rbfd.FP64:
