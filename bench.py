@@ -45,6 +45,8 @@ UNIT = "pair-evals/s"
 # see the design doc for the tally).  2D: differences 2 x 20, r^2 2 x 7 + 20,
 # sqrt 12, eta 7, phi 63, accumulate 2 x 27 -> 210; 3D -> 284.
 OPS_PER_PAIR_DF = {2: 210, 3: 284}
+CPU_BASELINE_S = 10.0  # seconds of oracle time behind the cpu_baseline figure
+OPS_PER_NEWTON_TERM = 12  # df multiply-add of a basis value: TwoProduct by FMA (4), TwoSum (6), two adds
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -58,7 +60,8 @@ def parse_args():
     p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--engine", type=int, default=0, help="0: persistent greedy launch, 1: launches per step")
+    p.add_argument("--engine", type=int, default=0,
+                   help="0: Newton-basis start + persistent list sweep, 2: persistent list sweep, 1: launches per step")
     p.add_argument("--ctas", type=int, default=0, help="blocks of the persistent launch (0: automatic)")
     p.add_argument("--no-serve", action="store_true", help="skip the serving leg (p50/p99 latency)")
     p.add_argument("--serve-requests", type=int, default=200)
@@ -107,10 +110,10 @@ def useful_pairs_oracle_run(case, res, Dl, sample_idx=None):
     return total
 
 
-def oracle_step(cases, frac, rng_seed=0, n_threads=None):
-    """One bounded CPU step with the FP64 oracle: full greedy of every case,
-    volume update of a random `frac` of the volume points.  Returns
-    (useful_pairs, seconds)."""
+def oracle_step(cases, frac, rng_seed=0, n_threads=None, count=True):
+    """One CPU step with the FP64 oracle: full greedy of every case, volume
+    update of a random `frac` of the volume points (all of them at frac = 1).
+    Returns (useful_pairs, seconds)."""
     import oracle
 
     nt = n_threads or (os.cpu_count() or 1)
@@ -118,15 +121,19 @@ def oracle_step(cases, frac, rng_seed=0, n_threads=None):
     pairs = 0
     secs = 0.0
     for c in cases:
-        idx = np.sort(rng.choice(c.n_v, size=max(1, int(frac * c.n_v)), replace=False))
+        if frac >= 1.0:
+            idx = np.arange(c.n_v)
+        else:
+            idx = np.sort(rng.choice(c.n_v, size=max(1, int(frac * c.n_v)), replace=False))
         xv = np.ascontiguousarray(c.xyz_v[idx])
         dv = np.ascontiguousarray(c.d_v[idx])
         t0 = time.perf_counter()
         res = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, n_threads=nt)
         oracle.deform(res, c.xyz_s, c.R, xv, dv, c.k, c.D, n_threads=nt)
         secs += time.perf_counter() - t0
-        Dl = oracle.support_distances(res.smax, c.k, c.D)
-        pairs += useful_pairs_oracle_run(c, res, Dl, idx)
+        if count:
+            Dl = oracle.support_distances(res.smax, c.k, c.D)
+            pairs += useful_pairs_oracle_run(c, res, Dl, idx)
     return pairs, secs
 
 
@@ -307,31 +314,42 @@ def run_ours(args):
 
     # roofline of the dominant kernel class (device time inside the timed region)
     sweep_pairs = sum(s["sweep_pairs_useful"] for s in stats)
-    kinds = {
-        "sweep": (sum(s["sweep_ms"] for s in stats), sum(s["sweep_launches"] for s in stats), sweep_pairs),
-        "grow": (sum(s["grow_ms"] for s in stats), sum(s["grow_launches"] for s in stats), 0),
-        "vol": (sum(s["vol_ms"] for s in stats), sum(s["vol_launches"] for s in stats),
-                sum(s["vol_pairs_useful"] for s in stats)),
-        # the persistent greedy launch runs the sweeps AND the FP64 growth; only
-        # its sweep pairs are counted as work here, so its fraction is a lower bound
-        "persist": (sum(s["persist_ms"] for s in stats), sum(s["persist_launches"] for s in stats), sweep_pairs),
-    }
     dim = cases[0].dim
     peak_ops = SM_COUNT * FP32_LANES_PER_SM * 2.07e9  # FP32 issue slots per second at max SM clock
+    # (device ms, launches, FP32-pipe operations of the work the class did)
+    kinds = {
+        "sweep": (sum(s["sweep_ms"] for s in stats), sum(s["sweep_launches"] for s in stats),
+                  sweep_pairs * OPS_PER_PAIR_DF[dim]),
+        "grow": (sum(s["grow_ms"] for s in stats), sum(s["grow_launches"] for s in stats), 0),
+        "vol": (sum(s["vol_ms"] for s in stats), sum(s["vol_launches"] for s in stats),
+                sum(s["vol_pairs_useful"] for s in stats) * OPS_PER_PAIR_DF[dim]),
+        # the persistent list sweep runs the sweeps AND the FP64 growth; only
+        # its sweep pairs are counted as work here, so its fraction is a lower bound
+        "persist": (sum(s["persist_ms"] for s in stats), sum(s["persist_launches"] for s in stats),
+                    0),
+        # the Newton-basis launch: one double-float multiply-add (12 FP32
+        # operations) per basis value read; its per-point tail and growth are
+        # not counted, so the fraction is a lower bound
+        "newton": (sum(s["newton_ms"] for s in stats), sum(s["newton_launches"] for s in stats),
+                   sum(s["newton_terms"] for s in stats) * OPS_PER_NEWTON_TERM),
+    }
+    names = {"sweep": f"k_sweep<{dim},2,1>", "vol": f"k_vol_sweep<{dim},2,1>",
+             "persist": f"k_greedy_persist<{dim},2,1>", "newton": f"k_greedy_newton<{dim},2,1>"}
     ev_kinds = {k: v for k, v in kinds.items() if k != "grow"}
     dom = max(ev_kinds, key=lambda k: ev_kinds[k][0])
-    d_ms, d_launch, d_pairs = ev_kinds[dom]
-    achieved = d_pairs * OPS_PER_PAIR_DF[dim] / (d_ms / 1e3) if d_ms > 0 else 0.0
+    d_ms, d_launch, d_ops = ev_kinds[dom]
+    achieved = d_ops / (d_ms / 1e3) if d_ms > 0 else 0.0
     roofline = {
-        "bound": "alu", "kernel": {"sweep": "k_sweep<2,2,1>", "vol": "k_vol_sweep<2,2,1>",
-                                   "persist": "k_greedy_persist<2,2,1>"}[dom],
+        "bound": "alu", "kernel": names[dom],
         "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "TFLOP/s",
         "frac": achieved / peak_ops, "traffic": None,
-        "ops_per_pair": OPS_PER_PAIR_DF[dim], "avg_launch_ms": d_ms / max(1, d_launch),
-        "launches": int(d_launch),
+        "avg_launch_ms": d_ms / max(1, d_launch), "launches": int(d_launch),
         "kernel_ms": {k: round(v[0], 3) for k, v in kinds.items()},
+        "kernel_frac": {k: round(v[2] / (v[0] / 1e3) / peak_ops, 5) for k, v in kinds.items() if v[0] > 0 and v[2]},
         "persist_phase_ms": [round(sum(s["persist_phase_ms"][q] for s in stats), 3) for q in range(8)],
-        "note": "FP32-pipe operations of the double-float pair evaluation; peak = 152 SMs x 128 FP32 lanes x 2.07 GHz",
+        "note": ("FP32-pipe operations: 210 (2D) / 284 (3D) per double-float pair evaluation, 12 per "
+                 "double-float basis multiply-add; peak = 152 SMs x 128 FP32 lanes x 2.07 GHz. The greedy "
+                 "launches are latency-bound chains of dependent steps (one grid barrier per step)"),
     }
     greedy_ms = [s["greedy_ms"] for s in stats]
     line = {
@@ -342,7 +360,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "cases": list(CASES), "n_surface": 4000, "n_volume": 1000000,
                    "levels": 2, "R": [1.0, 0.2], "eps": 1e-5, "k": 5.0, "D": 2.0, "precision": args.precision,
                    "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas{ws}",
-                   "engine": "persistent" if args.engine == 0 else "per-step launches",
+                   "engine": {0: "newton+persistent", 1: "per-step launches", 2: "persistent"}[args.engine],
                    "persist_ctas": int(stats[-1]["persist_ctas"]) if stats else 0},
         "time_to_eps_ms": {"pitch_heave": statistics.median(greedy_ms[0::2]),
                            "horns": statistics.median(greedy_ms[1::2])},
@@ -353,11 +371,19 @@ def run_ours(args):
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
-        frac = 0.05
-        p_cpu, s_cpu = oracle_step(cases, frac)
+        # the whole step (both cases, every volume point), repeated until at
+        # least CPU_BASELINE_S seconds of oracle time have run
+        # (the full step is the same every time: its pairs are counted once)
+        p_cpu, s_cpu, reps, p_one = 0, 0.0, 0, 0
+        while s_cpu < CPU_BASELINE_S and reps < 200:
+            p, s_ = oracle_step(cases, 1.0, count=(reps == 0))
+            p_one = p_one or p
+            p_cpu += p_one
+            s_cpu += s_
+            reps += 1
         line["cpu_baseline"] = {"value": p_cpu / s_cpu, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                                "sample": f"full greedy of both cases + volume update of a random {frac:.0%} "
-                                          f"of the volume points (FP64 oracle, OpenMP)",
+                                "sample": f"the full step (greedy of both cases + volume update of all their "
+                                          f"volume points) repeated {reps} times (FP64 oracle, OpenMP)",
                                 "seconds": s_cpu}
     if not args.no_serve:
         line["serving"] = run_serving(n_requests=args.serve_requests)
@@ -435,14 +461,15 @@ def run_reference(args):
     if rank != 0:
         return
     cases = make_cases()
-    frac = 0.02
+    frac = 1.0  # the whole workload each step
     cores = cpu_cores()
     for _ in range(args.warmup):
-        oracle_step(cases, frac, rng_seed=1)
-    tot_p, tot_s = 0, 0.0
+        oracle_step(cases, frac, rng_seed=1, count=False)
+    tot_p, tot_s, p_one = 0, 0.0, 0
     for k in range(args.steps):
-        p, s = oracle_step(cases, frac, rng_seed=100 + k)
-        tot_p += p
+        p, s = oracle_step(cases, frac, rng_seed=100 + k, count=(k == 0))  # the same full step each time
+        p_one = p_one or p
+        tot_p += p_one
         tot_s += s
     v = tot_p / tot_s
     line = {
@@ -452,8 +479,8 @@ def run_reference(args):
         "config": {"workload": WORKLOAD, "cases": list(CASES), "n_surface": 4000, "n_volume": 1000000,
                    "levels": 2, "R": [1.0, 0.2], "eps": 1e-5, "k": 5.0, "D": 2.0},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"each step: full greedy of both cases + volume update of a random {frac:.0%} "
-                                   f"of the volume points"},
+                         "sample": "each step: the full workload (greedy of both cases + volume update of "
+                                   "all their volume points)"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

@@ -143,7 +143,7 @@ typedef struct rbfd_stats {
     double sweep_ms, grow_ms, vol_ms;
     int64_t sweep_launches, grow_launches, vol_launches;
     int64_t sweep_pairs_useful, sweep_pairs_visited, vol_pairs_useful, vol_pairs_visited;
-    double persist_ms;         /* persistent greedy launches (engine 0): sweep + growth of every step */
+    double persist_ms;         /* persistent list-sweep launches (engines 0, 2): sweep + growth of every step */
     int64_t persist_launches;
     int64_t persist_ctas;      /* blocks of the last persistent launch */
     /* profile mode: block 0 of the persistent launch, summed over steps, in ms:
@@ -155,6 +155,9 @@ typedef struct rbfd_stats {
     int64_t wall_pairs_search;   /* point pairs scanned by the FP32 search pass */
     int64_t wall_pairs_exact;    /* point pairs scanned by the exact pass */
     int64_t newton_steps;        /* greedy steps taken in the Newton basis (engine 0) */
+    double newton_ms;            /* event time of the Newton-basis launches (opt.profile = 1) */
+    int64_t newton_launches;
+    int64_t newton_terms;        /* basis values the Newton update read: n_s x controls, summed over steps */
 } rbfd_stats;
 
 int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st);

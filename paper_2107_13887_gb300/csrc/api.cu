@@ -413,7 +413,7 @@ int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st) {
     return guarded([&] {
         if (!m || !st) rbfd::fail(RBFD_EINVAL, "rbfd_get_stats: NULL argument");
         RBFD_CUDA(cudaSetDevice(m->device));
-        unsigned long long pr[6] = {0, 0, 0, 0, 0, 0};
+        unsigned long long pr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         RBFD_CUDA(cudaStreamSynchronize(m->stream));
         RBFD_CUDA(cudaMemcpy(pr, m->d_pairs, sizeof(pr), cudaMemcpyDeviceToHost));
         m->prof.flush();
@@ -436,6 +436,9 @@ int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st) {
         st->wall_launches = m->prof.launches[rbfd::kProfWall];
         st->wall_pairs_search = (int64_t)pr[4];
         st->wall_pairs_exact = (int64_t)pr[5];
+        st->newton_ms = m->prof.ms[rbfd::kProfNewton];
+        st->newton_launches = m->prof.launches[rbfd::kProfNewton];
+        st->newton_terms = (int64_t)pr[6];
         unsigned long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         if (m->d_phase_ns) RBFD_CUDA(cudaMemcpy(ph, m->d_phase_ns, sizeof(ph), cudaMemcpyDeviceToHost));
         for (int q = 0; q < 8; ++q) st->persist_phase_ms[q] = ph[q] * 1e-6;

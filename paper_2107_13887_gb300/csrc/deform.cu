@@ -120,11 +120,19 @@ __global__ void k_bbox_partial_v(const double4 *__restrict__ p, int64_t n, doubl
     }
 }
 
+// Final box from nb per-block partials [nb][6] (lo xyz, hi xyz): one warp per
+// coordinate bound, lanes striding over the partials (min / max are exact, so
+// the order does not matter).
 __global__ void k_bbox_reduce(const double *__restrict__ part, int nb, double *__restrict__ out) {
-    if (threadIdx.x >= 6) return;
-    double v = part[threadIdx.x];
-    for (int b = 1; b < nb; ++b) v = threadIdx.x < 3 ? fmin(v, part[b * 6 + threadIdx.x]) : fmax(v, part[b * 6 + threadIdx.x]);
-    out[threadIdx.x] = v;
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;  // 6 warps
+    if (q >= 6) return;
+    double v = q < 3 ? INFINITY : -INFINITY;
+    for (int b = lane; b < nb; b += 32) v = q < 3 ? fmin(v, part[b * 6 + q]) : fmax(v, part[b * 6 + q]);
+    for (int o = 16; o > 0; o >>= 1) {
+        const double w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = q < 3 ? fmin(v, w) : fmax(v, w);
+    }
+    if (lane == 0) out[q] = v;
 }
 
 __global__ void k_gather_vol(const double4 *__restrict__ p, const uint32_t *__restrict__ order, int64_t n,
@@ -409,7 +417,7 @@ void morton_order(rbfd_mesh *m, int64_t n, const double4 *vin, double4 *vsorted,
     const int dim = m->dim;
     const int nbb = std::min<int>(cdiv(n, 256), 256);
     k_bbox_partial_v<<<nbb, 256, 0, st>>>(vin, n, m->d_red);
-    k_bbox_reduce<<<1, 32, 0, st>>>(m->d_red, nbb, m->d_bbox);
+    k_bbox_reduce<<<1, 192, 0, st>>>(m->d_red, nbb, m->d_bbox);
     double bb[6];
     RBFD_CUDA(cudaMemcpyAsync(bb, m->d_bbox, sizeof(bb), cudaMemcpyDeviceToHost, st));
     RBFD_CUDA(cudaStreamSynchronize(st));
@@ -553,7 +561,7 @@ void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, b
         // (2) Morton order of the kept points
         const int nbb = std::min<int>(cdiv(nV, 256), 256);
         k_bbox_idx<<<nbb, 256, 0, st>>>(vin, m->d_vlist, nV, m->d_red);
-        k_bbox_reduce<<<1, 32, 0, st>>>(m->d_red, nbb, m->d_bbox);
+        k_bbox_reduce<<<1, 192, 0, st>>>(m->d_red, nbb, m->d_bbox);
         double bb[6];
         RBFD_CUDA(cudaMemcpyAsync(bb, m->d_bbox, sizeof(bb), cudaMemcpyDeviceToHost, st));
         RBFD_CUDA(cudaStreamSynchronize(st));
@@ -788,7 +796,7 @@ void deform_noalloc_run(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const flo
     if (nV > 0) {
         const int nbb = std::min<int>(cdiv(nV, 256), 256);
         k_bbox_idx<<<nbb, 256, 0, st>>>(vin, vlist, nV, m->d_red);
-        k_bbox_reduce<<<1, 32, 0, st>>>(m->d_red, nbb, m->d_bbox);
+        k_bbox_reduce<<<1, 192, 0, st>>>(m->d_red, nbb, m->d_bbox);
         double bb[6];
         RBFD_CUDA(cudaMemcpyAsync(bb, m->d_bbox, sizeof(bb), cudaMemcpyDeviceToHost, st));
         RBFD_CUDA(cudaStreamSynchronize(st));

@@ -81,11 +81,17 @@ __global__ void k_bbox_partial(const double4 *__restrict__ p, int64_t n, double 
     }
 }
 
+// Final box from nb per-block partials [nb][6]: one warp per coordinate bound.
 __global__ void k_bbox_final(const double *__restrict__ part, int nb, double *__restrict__ out) {
-    if (threadIdx.x >= 6) return;
-    double v = part[threadIdx.x];
-    for (int b = 1; b < nb; ++b) v = threadIdx.x < 3 ? fmin(v, part[b * 6 + threadIdx.x]) : fmax(v, part[b * 6 + threadIdx.x]);
-    out[threadIdx.x] = v;
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;  // 6 warps
+    if (q >= 6) return;
+    double v = q < 3 ? INFINITY : -INFINITY;
+    for (int b = lane; b < nb; b += 32) v = q < 3 ? fmin(v, part[b * 6 + q]) : fmax(v, part[b * 6 + q]);
+    for (int o = 16; o > 0; o >>= 1) {
+        const double w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = q < 3 ? fmin(v, w) : fmax(v, w);
+    }
+    if (lane == 0) out[q] = v;
 }
 
 __global__ void k_gather_sorted(const uint32_t *__restrict__ perm, int64_t n, const double4 *__restrict__ x4,
@@ -822,7 +828,7 @@ void build_control_grid(rbfd_mesh *m, Level &L) {
     const int n = (int)L.nc;
     double *part = m->d_red;
     k_bbox_partial<<<1, 256, 0, m->stream>>>(L.d_cx, n, part);
-    k_bbox_final<<<1, 32, 0, m->stream>>>(part, 1, m->d_bbox);
+    k_bbox_final<<<1, 192, 0, m->stream>>>(part, 1, m->d_bbox);
     double bb[6];
     RBFD_CUDA(cudaMemcpyAsync(bb, m->d_bbox, sizeof(bb), cudaMemcpyDeviceToHost, m->stream));
     RBFD_CUDA(cudaStreamSynchronize(m->stream));
@@ -891,7 +897,7 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     const int nbb = std::min<int>(cdiv(n, 256), 256);
     double *part = dalloc<double>(6 * 256, "bbox partials");
     k_bbox_partial<<<nbb, 256, 0, st>>>(x4, n, part);
-    k_bbox_final<<<1, 32, 0, st>>>(part, nbb, m->d_bbox);
+    k_bbox_final<<<1, 192, 0, st>>>(part, nbb, m->d_bbox);
     double bb[6];
     RBFD_CUDA(cudaMemcpyAsync(bb, m->d_bbox, sizeof(bb), cudaMemcpyDeviceToHost, st));
     RBFD_CUDA(cudaStreamSynchronize(st));
@@ -950,8 +956,8 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     RBFD_CUDA(cudaMemsetAsync(m->d_pb_done, 0, sizeof(unsigned int) * m->n_pb, st));
     m->d_pb_key = dalloc<double>(std::max(m->n_pb, 1024), "block keys");
     m->d_pb_idx = dalloc<int>(std::max(m->n_pb, 1024), "block argmax");
-    m->d_pairs = dalloc<unsigned long long>(6, "pair counters");
-    RBFD_CUDA(cudaMemsetAsync(m->d_pairs, 0, 6 * sizeof(unsigned long long), st));
+    m->d_pairs = dalloc<unsigned long long>(8, "pair counters");
+    RBFD_CUDA(cudaMemsetAsync(m->d_pairs, 0, 8 * sizeof(unsigned long long), st));
     m->d_st = dalloc<GreedyState>(1, "greedy state");
     RBFD_CUDA(cudaMemsetAsync(m->d_st, 0, sizeof(GreedyState), st));
     m->d_bar = dalloc<GridBarrier>(1, "grid barrier");
@@ -1104,7 +1110,7 @@ void greedy_run(rbfd_mesh *m) {
                     RBFD_CUDA(cudaMemsetAsync(m->d_bar, 0, sizeof(GridBarrier), st));
                     cudaEvent_t e0 = m->prof.begin(st);
                     newton_run_level(m, L.R, L.tau, ctas);
-                    m->prof.end(kProfPersist, e0, st, 1);
+                    m->prof.end(kProfNewton, e0, st, 1);
                     read_state(m);
                     m->prof.flush();
                     GridBarrier hb{};

@@ -89,7 +89,8 @@ struct Level {
 };
 
 // Optional per-kernel-class timing with CUDA events on the mesh's stream.
-enum ProfKind { kProfSweep = 0, kProfGrow = 1, kProfVol = 2, kProfPersist = 3, kProfWall = 4, kProfKinds = 5 };
+enum ProfKind { kProfSweep = 0, kProfGrow = 1, kProfVol = 2, kProfPersist = 3, kProfWall = 4, kProfNewton = 5,
+                kProfKinds = 6 };
 
 struct Profiler {
     bool on = false;
@@ -159,8 +160,8 @@ struct rbfd_mesh {
     unsigned int *d_pb_done = nullptr;
     double *d_pb_key = nullptr;
     int *d_pb_idx = nullptr;
-    unsigned long long *d_pairs = nullptr;  // [6]: surface sweep useful, visited; volume useful, visited;
-                                            //     wall distance search, exact pass
+    unsigned long long *d_pairs = nullptr;  // [8]: surface sweep useful, visited; volume useful, visited;
+                                            //     wall distance search, exact pass; Newton basis terms
     rbfd::GreedyState *d_st = nullptr;
     rbfd::GreedyState *h_st = nullptr;  // pinned
     // persistent engine

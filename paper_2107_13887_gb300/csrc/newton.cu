@@ -682,8 +682,11 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
                 if (writer) {
                     const bool stop = flags & 1, hand = flags & 2, singular = flags & 4;
                     const double e = I >= 0 ? __ddiv_rn(__dsqrt_rn(key_value<MODE>(K)), a.S0) : 0.0;
-                    // a list sweep visits n_s x (controls so far) pairs per step
-                    a.pairs[1] += (unsigned long long)a.n_s * (unsigned long long)(nn) * (unsigned long long)(nn + 1) / 2;
+                    // per step, the basis update touches n_s x (controls so far) values of V
+                    const unsigned long long terms =
+                        (unsigned long long)a.n_s * (unsigned long long)(nn) * (unsigned long long)(nn + 1) / 2;
+                    a.pairs[1] += terms;
+                    a.pairs[6] += terms;
                     a.st->best_orig = I;
                     a.st->best_key = I >= 0 ? key_value<MODE>(K) : -1.0;
                     a.st->emax = e;

@@ -75,6 +75,9 @@ class rbfd_stats(ctypes.Structure):
         ("wall_pairs_search", ctypes.c_int64),
         ("wall_pairs_exact", ctypes.c_int64),
         ("newton_steps", ctypes.c_int64),
+        ("newton_ms", ctypes.c_double),
+        ("newton_launches", ctypes.c_int64),
+        ("newton_terms", ctypes.c_int64),
     ]
 
 
