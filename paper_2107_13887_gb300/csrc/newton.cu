@@ -161,7 +161,7 @@ struct NewtonArgs {
     float4 *wdf;  // mixed mode: w of each control in double-float ([2] float4 per control)
     float4 *cdf;
     uint32_t *cid;
-    double *G, *Gt, *V;
+    double *G, *Gt, *V;  // V: FP64, or hi/lo float pairs in mixed mode
     double4 *rec;  // [2][P][3] per block: (key, original index, longest list, position), coordinates + l^2, E
     double *ycol;  // [2][P][cn + 1] per block: V[.][candidate] (mixed mode: hi/lo float pairs)
     // (two copies, by the parity of the step: a block writes the next step's
@@ -343,11 +343,16 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
                     }
                     for (; k < kcs; k += kNW)
                         df_fma_acc(h0, l0, s_yh[k], s_yl[k], Vh[(size_t)k * ppb], Vl[(size_t)k * ppb]);
-                    // columns beyond the shared slice: FP64 values from global memory
-                    const double *Vi = a.V + i;
+                    // columns beyond the shared slice: hi/lo pairs from global memory
+                    const float2 *Vi = reinterpret_cast<const float2 *>(a.V) + i;
+                    for (; k + kNW < j; k += 2 * kNW) {
+                        const float2 v0 = __ldcg(Vi + (size_t)k * a.n_s), v1 = __ldcg(Vi + (size_t)(k + kNW) * a.n_s);
+                        df_fma_acc(h0, l0, s_yh[k], s_yl[k], v0.x, v0.y);
+                        df_fma_acc(h1, l1, s_yh[k + kNW], s_yl[k + kNW], v1.x, v1.y);
+                    }
                     for (; k < j; k += kNW) {
-                        const df v = df_from_double(__ldcg(Vi + (size_t)k * a.n_s));
-                        df_fma_acc(h0, l0, s_yh[k], s_yl[k], v.hi, v.lo);
+                        const float2 v = __ldcg(Vi + (size_t)k * a.n_s);
+                        df_fma_acc(h0, l0, s_yh[k], s_yl[k], v.x, v.y);
                     }
                 } else {
                     const double *Vs = s_V + sl;
@@ -399,7 +404,7 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
                         s_Vh[(size_t)j * ppb + sl] = v.hi;
                         s_Vl[(size_t)j * ppb + sl] = v.lo;
                     } else {
-                        a.V[(size_t)j * a.n_s + i] = df_to_double(v);
+                        reinterpret_cast<float2 *>(a.V)[(size_t)j * a.n_s + i] = make_float2(v.hi, v.lo);
                     }
                     df k2 = {0.f, 0.f};
 #pragma unroll
@@ -509,12 +514,10 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
                     float2 *yf = reinterpret_cast<float2 *>(yc);
                     for (int k = tid; k <= j; k += kNT) {
                         float2 v;
-                        if (k < a.cs) {
+                        if (k < a.cs)
                             v = make_float2(s_Vh[(size_t)k * ppb + ws], s_Vl[(size_t)k * ppb + ws]);
-                        } else {
-                            const df d = df_from_double(__ldcg(a.V + (size_t)k * a.n_s + pw));
-                            v = make_float2(d.hi, d.lo);
-                        }
+                        else
+                            v = __ldcg(reinterpret_cast<const float2 *>(a.V) + (size_t)k * a.n_s + pw);
                         yf[k] = v;
                     }
                 } else {
