@@ -240,14 +240,14 @@ def run_ours(args):
     streams = [torch.cuda.Stream(dev) for _ in cases]
 
     def one_step(src, record):
-        """Both cases as one batch: create, greedy (batched), deform (batched), destroy."""
+        """Both cases as one batch: create, greedy + deform (each case on its own
+        host thread and stream, side by side), destroy."""
         ms = []
         for c, d, s_ in zip(cases, src, streams):
             ms.append(rbfd.Mesh(d["xyz_s"], d["dS"], c.R, c.eps, precision=precision, stream=s_.cuda_stream,
                                 profile=record, engine=args.engine, grid_ctas=args.ctas))
-        rbfd.greedy_batch(ms)
-        rbfd.deform_batch(ms, [d["xyz_v"] for d in src], [d["d_v"] for d in src], [c.D for c in cases],
-                          [c.k for c in cases], [d["out"] for d in src])
+        rbfd.greedy_deform_batch(ms, [d["xyz_v"] for d in src], [d["d_v"] for d in src], [c.D for c in cases],
+                                 [c.k for c in cases], [d["out"] for d in src])
         stats = [m.stats() for m in ms]
         for m in ms:
             m.close()

@@ -313,6 +313,17 @@ int rbfd_greedy_batch(rbfd_mesh **meshes, int n);
 int rbfd_deform_batch(rbfd_mesh **meshes, int n, const int64_t *n_v, const float *const *xyz_v,
                       const float *const *d_v, const double *D, const double *k, float *const *out);
 
+/*
+ * rbfd_greedy_deform_batch -- rbfd_greedy then rbfd_deform for each of n
+ * meshes, mesh i's two calls one after the other on its own host thread and
+ * stream, so that one mesh's volume update overlaps another's greedy.
+ * Arguments as rbfd_deform_batch (d_v may be NULL, or any d_v[i], to compute
+ * wall distances).  Returns RBFD_ENOTCONV, after deforming with the valid
+ * levels, if a greedy hit its control cap; otherwise the worst status.
+ */
+int rbfd_greedy_deform_batch(rbfd_mesh **meshes, int n, const int64_t *n_v, const float *const *xyz_v,
+                             const float *const *d_v, const double *D, const double *k, float *const *out);
+
 /* ------------------------------------------------------------- serving ---
  *
  * A request loop for deformation requests as icing time steps produce them:

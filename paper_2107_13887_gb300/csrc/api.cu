@@ -293,6 +293,33 @@ int run_batch(int n, F &&f, const char *name) {
     return worst;
 }
 
+// Meshes whose greedy runs side by side: their persistent grids must be
+// resident together, so each takes a share of the blocks.
+int share_grid(rbfd_mesh **meshes, int n) {
+    int cap = 0;
+    if (n > 1) {
+        int total = 0;
+        int rc = guarded([&] {
+            RBFD_CUDA(cudaSetDevice(meshes[0]->device));
+            total = rbfd::persist_max_ctas(meshes[0]);
+        });
+        if (rc != RBFD_OK) return rc;
+        cap = std::max(1, total / n);
+    }
+    for (int i = 0; i < n; ++i) {
+        meshes[i]->batch_ctas_cap = cap;
+        meshes[i]->batch_share = n;
+    }
+    return RBFD_OK;
+}
+
+void unshare_grid(rbfd_mesh **meshes, int n) {
+    for (int i = 0; i < n; ++i) {
+        meshes[i]->batch_ctas_cap = 0;
+        meshes[i]->batch_share = 0;
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -560,29 +587,44 @@ int rbfd_greedy_batch(rbfd_mesh **meshes, int n) {
             rbfd::g_last_error = "rbfd_greedy_batch: NULL mesh";
             return RBFD_EINVAL;
         }
-    // persistent grids of the batch must be resident together
-    int cap = 0;
-    if (n > 1) {
-        int total = 0;
-        int rc = guarded([&] {
-            RBFD_CUDA(cudaSetDevice(meshes[0]->device));
-            total = rbfd::persist_max_ctas(meshes[0]);
-        });
-        if (rc != RBFD_OK) return rc;
-        cap = std::max(1, total / n);
-    }
-    for (int i = 0; i < n; ++i) {
-        meshes[i]->batch_ctas_cap = cap;
-        meshes[i]->batch_share = n;
-    }
-    int rc = run_batch(n, [&](int i) {
+    int rc = share_grid(meshes, n);
+    if (rc != RBFD_OK) return rc;
+    rc = run_batch(n, [&](int i) {
         RBFD_CUDA(cudaSetDevice(meshes[i]->device));
         rbfd::greedy_run(meshes[i]);
     }, "rbfd_greedy_batch");
-    for (int i = 0; i < n; ++i) {
-        meshes[i]->batch_ctas_cap = 0;
-        meshes[i]->batch_share = 0;
+    unshare_grid(meshes, n);
+    return rc;
+}
+
+int rbfd_greedy_deform_batch(rbfd_mesh **meshes, int n, const int64_t *n_v, const float *const *xyz_v,
+                             const float *const *d_v, const double *D, const double *k, float *const *out) {
+    if (n < 0 || (n > 0 && (!meshes || !n_v || !xyz_v || !D || !k || !out))) {
+        rbfd::g_last_error = "rbfd_greedy_deform_batch: bad arguments";
+        return RBFD_EINVAL;
     }
+    for (int i = 0; i < n; ++i)
+        if (!meshes[i]) {
+            rbfd::g_last_error = "rbfd_greedy_deform_batch: NULL mesh";
+            return RBFD_EINVAL;
+        }
+    int rc = share_grid(meshes, n);
+    if (rc != RBFD_OK) return rc;
+    rc = run_batch(n, [&](int i) {
+        rbfd_mesh *m = meshes[i];
+        RBFD_CUDA(cudaSetDevice(m->device));
+        bool notconv = false;
+        try {
+            rbfd::greedy_run(m);
+        } catch (const Error &e) {
+            if (e.status != RBFD_ENOTCONV) throw;
+            notconv = true;  // the levels are valid: deform with them, report it after
+        }
+        const int drc = deform_common(m, n_v[i], xyz_v[i], d_v ? d_v[i] : nullptr, D[i], k[i], out[i], false);
+        if (drc != RBFD_OK) rbfd::fail(drc, rbfd::g_last_error);
+        if (notconv) rbfd::fail(RBFD_ENOTCONV, "greedy selection did not reach eps before the control cap");
+    }, "rbfd_greedy_deform_batch");
+    unshare_grid(meshes, n);
     return rc;
 }
 

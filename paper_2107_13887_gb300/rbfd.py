@@ -135,6 +135,9 @@ SIGNATURES = [
     ("rbfd_deform_batch", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_i64),
                                          ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_d),
                                          ctypes.POINTER(_d), ctypes.POINTER(_vp)]),
+    ("rbfd_greedy_deform_batch", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_i64),
+                                                ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_d),
+                                                ctypes.POINTER(_d), ctypes.POINTER(_vp)]),
     ("rbfd_destroy", ctypes.c_int, [_vp]),
     ("rbfd_server_options_default", None, [ctypes.POINTER(rbfd_server_options)]),
     ("rbfd_server_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(rbfd_server_options)]),
@@ -450,6 +453,26 @@ def deform_batch(meshes, xyz_v, d_v, D, k, out):
     arr = (_vp * n)(*[m.h.value for m in meshes])
     _check(lib.rbfd_deform_batch(arr, n, nv, px, pd, Dv, kv, po))
     return out
+
+
+def greedy_deform_batch(meshes, xyz_v, d_v, D, k, out, allow_not_converged: bool = True) -> int:
+    """``rbfd_greedy_deform_batch``: greedy then volume update per mesh, the
+    meshes side by side; float32 arrays as in ``deform_batch`` (``d_v`` may be
+    None, or hold None entries, to compute wall distances)."""
+    lib = load()
+    n = len(meshes)
+    arr = (_vp * n)(*[m.h.value for m in meshes])
+    nv = (_i64 * n)(*[int(x.shape[0]) for x in xyz_v])
+    px = (_vp * n)(*[_ptr(x).value for x in xyz_v])
+    pd = None if d_v is None else (_vp * n)(*[None if x is None else _ptr(x).value for x in d_v])
+    Dv = (_d * n)(*[float(x) for x in D])
+    kv = (_d * n)(*[float(x) for x in k])
+    po = (_vp * n)(*[_ptr(x).value for x in out])
+    rc = lib.rbfd_greedy_deform_batch(arr, n, nv, px, pd, Dv, kv, po)
+    if rc == ENOTCONV and allow_not_converged:
+        return rc
+    _check(rc)
+    return rc
 
 
 class Server:

@@ -430,3 +430,18 @@ def test_batch_matches_single_meshes(precision):
             assert np.abs(x.alpha - y.alpha).max() <= 1e-6 * max(np.abs(y.alpha).max(), 1e-300)
         assert np.abs(out2.astype(np.float64) - out1).max() <= 1e-5 * S0 + np.abs(out1).max() * 2.0**-24
         m.close()
+    # greedy then volume update per mesh, meshes side by side: the same as
+    # the two batch calls one after the other, bit for bit
+    ms2 = [rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision) for c in cases]
+    outs2 = [np.empty((c.n_v, c.dim), np.float32) for c in cases]
+    rbfd.greedy_deform_batch(ms2, [c.xyz_v for c in cases], [c.d_v for c in cases], [c.D for c in cases],
+                             [c.k for c in cases], outs2)
+    for c, m, o1, o2 in zip(cases, ms2, outs, outs2):
+        assert np.array_equal(o1, o2)
+    # with the wall distances computed on the device
+    outs3 = [np.empty((c.n_v, c.dim), np.float32) for c in cases]
+    rbfd.greedy_deform_batch(ms2, [c.xyz_v for c in cases], None, [c.D for c in cases], [c.k for c in cases], outs3)
+    for c, m, o1, o3 in zip(cases, ms2, outs, outs3):
+        S0 = float(np.sqrt((c.dS**2).sum(1)).max())
+        assert np.abs(o3.astype(np.float64) - o1).max() <= 1e-5 * S0
+        m.close()
