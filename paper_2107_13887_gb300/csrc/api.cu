@@ -222,11 +222,13 @@ void mesh_free(rbfd_mesh *m) {
                     m->d_st, m->d_vin, m->d_vpos, m->d_vorig, m->d_vflag, m->d_vscan, m->d_vlist, m->d_vkeys,
                     m->d_vacc, m->d_vio, m->d_misc, m->d_bbox, m->d_bar, m->d_pred, m->d_Gt,
                     m->d_nz_k, m->d_nz_v, m->d_phase_ns, m->d_vreg, m->d_vreg_orig, m->d_pb_fbox,
-                    m->d_V, m->d_nrec, m->d_nycol, m->d_nwdf};
+                    m->d_V, m->d_nrec, m->d_nycol, m->d_nwdf, m->d_lvl, m->d_ckeys};
     for (void *p : ptrs) dfree(p);
     m->sort.release();
     m->prof.release();
     if (m->h_st) pinned_free(m->h_st);
+    if (m->h_bar) pinned_free(m->h_bar);
+    if (m->h_lvl) pinned_free(m->h_lvl);
     if (m->ev0) cudaEventDestroy(m->ev0);
     if (m->ev1) cudaEventDestroy(m->ev1);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);

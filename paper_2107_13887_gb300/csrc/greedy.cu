@@ -593,7 +593,8 @@ __global__ void __launch_bounds__(kThreads) k_resid(int n, double R, int cap, co
                                                     const uint32_t *__restrict__ nb_cnt,
                                                     const uint32_t *__restrict__ nb_list,
                                                     const double4 *__restrict__ cur, double4 *__restrict__ r,
-                                                    double *__restrict__ red) {
+                                                    double *__restrict__ red, const double *__restrict__ done) {
+    if (*done != 0.0) return;  // refinement already converged
     __shared__ double sm[kThreads / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i = blockIdx.x * (kThreads / 32) + w;
@@ -633,8 +634,29 @@ __global__ void __launch_bounds__(kThreads) k_resid(int n, double R, int cap, co
 }
 
 // z_j = sum_{k <= j} G_jk r_k (3 right-hand sides), one warp per row.
+// Convergence test of the iterative refinement on the device (no host round
+// trip): once the largest residual of a sweep is at most tol, lvl[2] is set
+// and the remaining sweeps of this level close do nothing; lvl[3] counts the
+// corrections applied.
+__global__ void k_ir_check(const double *__restrict__ rmax, int nb, double tol, double *__restrict__ lvl) {
+    __shared__ double sm[32];
+    if (lvl[2] != 0.0) return;
+    double r = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) r = fmax(r, rmax[b]);
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, sm[w]);
+        r = fmax(r, sm[0]);
+        if (r <= tol) lvl[2] = 1.0;
+        else lvl[3] += 1.0;
+    }
+}
+
 __global__ void k_lower_mv3(int n, int cap, const double *__restrict__ G, const double4 *__restrict__ r,
-                            double4 *__restrict__ z) {
+                            double4 *__restrict__ z, const double *__restrict__ done) {
+    if (*done != 0.0) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = blockIdx.x * (blockDim.x >> 5) + w;
     if (j >= n) return;
@@ -655,7 +677,8 @@ __global__ void k_lower_mv3(int n, int cap, const double *__restrict__ G, const 
 
 // Partial column sums of z^T G for 3 right-hand sides: part[jt][k].
 __global__ void k_colsum3(int n, int cap, const double *__restrict__ G, const double4 *__restrict__ z,
-                          double4 *__restrict__ part) {
+                          double4 *__restrict__ part, const double *__restrict__ done) {
+    if (*done != 0.0) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int jt = blockIdx.y;
     if (k >= n) return;
@@ -672,7 +695,8 @@ __global__ void k_colsum3(int n, int cap, const double *__restrict__ G, const do
 }
 
 __global__ void k_apply_correction(int n, int cap, int n_jt, const double4 *__restrict__ part,
-                                   double4 *__restrict__ alpha) {
+                                   double4 *__restrict__ alpha, const double *__restrict__ done) {
+    if (*done != 0.0) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     double s0 = 0, s1 = 0, s2 = 0;
@@ -756,7 +780,7 @@ template <int DIM>
 void launch_resid_d(int basis, unsigned g, int n, double R, rbfd_mesh *m, cudaStream_t st) {
 #define RBFD_RESID(B)                                                                                           \
     k_resid<DIM, B><<<g, kThreads, 0, st>>>(n, R, m->cap, m->d_cx, m->d_alpha, m->d_cid, m->d_nb_cnt,           \
-                                            m->d_nb_list, m->d_cur, m->d_vec, m->d_red)
+                                            m->d_nb_list, m->d_cur, m->d_vec, m->d_red, m->d_lvl + 2)
     switch (basis) {
     case 0: RBFD_RESID(0); break;
     case 4: RBFD_RESID(4); break;
@@ -809,6 +833,21 @@ void read_state(rbfd_mesh *m) {
     RBFD_CUDA(cudaStreamSynchronize(m->stream));
 }
 
+// The state and the grid barrier after a persistent launch, in one round trip.
+void read_state_bar(rbfd_mesh *m) {
+    RBFD_CUDA(cudaMemcpyAsync(m->h_st, m->d_st, sizeof(GreedyState), cudaMemcpyDeviceToHost, m->stream));
+    RBFD_CUDA(cudaMemcpyAsync(m->h_bar, m->d_bar, sizeof(GridBarrier), cudaMemcpyDeviceToHost, m->stream));
+    RBFD_CUDA(cudaStreamSynchronize(m->stream));
+}
+
+// max_i |v_i|^2 and its argmax (original index, as int bits in out[1]) into
+// out on the device, without waiting for it.
+void maxnorm_async(rbfd_mesh *m, const double4 *v, double *out) {
+    const int nb = std::min<int>(cdiv(m->n_s, 256), 1024);
+    k_maxnorm<<<nb, 256, 0, m->stream>>>(v, m->d_perm, m->n_s, m->dim, m->d_pb_key, m->d_pb_idx, &m->d_misc[0], out);
+    RBFD_CUDA(cudaGetLastError());
+}
+
 // max_i |v_i|^2 and its argmax over the sorted surface (FP64, exact order of
 // each squared norm); returns the key, writes the argmax's original index.
 double maxnorm(rbfd_mesh *m, const double4 *v, int *arg) {
@@ -823,15 +862,10 @@ double maxnorm(rbfd_mesh *m, const double4 *v, int *arg) {
     return h[0];
 }
 
-// Uniform grid of cell size h over the level's controls (for the volume sweep).
-void build_control_grid(rbfd_mesh *m, Level &L) {
+// Uniform grid of cell size h over the level's controls (for the volume
+// sweep); bb = the controls' box (lo xyz, hi xyz), known on the host.
+void build_control_grid(rbfd_mesh *m, Level &L, const double *bb) {
     const int n = (int)L.nc;
-    double *part = m->d_red;
-    k_bbox_partial<<<1, 256, 0, m->stream>>>(L.d_cx, n, part);
-    k_bbox_final<<<1, 192, 0, m->stream>>>(part, 1, m->d_bbox);
-    double bb[6];
-    RBFD_CUDA(cudaMemcpyAsync(bb, m->d_bbox, sizeof(bb), cudaMemcpyDeviceToHost, m->stream));
-    RBFD_CUDA(cudaStreamSynchronize(m->stream));
     double h = L.R;
     auto dims = [&](double hh) {
         int nx = std::max(1, (int)std::floor((bb[3] - bb[0]) / hh) + 1);
@@ -850,16 +884,15 @@ void build_control_grid(rbfd_mesh *m, Level &L) {
     L.ncell = gd.x * gd.y * gd.z;
     L.d_cell_start = dalloc<uint32_t>((size_t)L.ncell + 1, "control cell starts");
     L.d_cell_ctrl = dalloc<uint32_t>((size_t)n, "control cell list");
-    uint32_t *keys = dalloc<uint32_t>((size_t)n, "control cell keys");
+    if (!m->d_ckeys) m->d_ckeys = dalloc<uint32_t>((size_t)m->cap + 1, "control cell keys");
+    uint32_t *keys = m->d_ckeys;
     k_cell_keys<<<cdiv(n, 256), 256, 0, m->stream>>>(L.d_cx, n, L.g0, 1.0 / h, gd, keys, L.d_cell_ctrl);
     int bits = 1;
     while ((1u << bits) < (unsigned)L.ncell && bits < 32) ++bits;
     radix_sort_pairs(keys, L.d_cell_ctrl, (size_t)n, bits, m->sort, m->stream);
     k_cell_start<<<cdiv((size_t)L.ncell + 1, 256), 256, 0, m->stream>>>(keys, n, L.ncell, L.d_cell_start);
-    m->stats.launches += 4;
+    m->stats.launches += 2;
     RBFD_CUDA(cudaGetLastError());
-    RBFD_CUDA(cudaStreamSynchronize(m->stream));
-    dfree(keys);
 }
 
 }  // namespace
@@ -969,6 +1002,10 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     m->d_phase_ns = dalloc<unsigned long long>(8, "phase timing");
     RBFD_CUDA(cudaMemsetAsync(m->d_phase_ns, 0, 8 * sizeof(unsigned long long), st));
     m->h_st = static_cast<GreedyState *>(pinned_alloc(sizeof(GreedyState)));
+    m->h_bar = static_cast<GridBarrier *>(pinned_alloc(sizeof(GridBarrier)));
+    m->h_lvl = static_cast<double *>(pinned_alloc(8 * sizeof(double)));
+    m->d_lvl = dalloc<double>(8, "level scalars");
+    RBFD_CUDA(cudaMemsetAsync(m->d_lvl, 0, 8 * sizeof(double), st));
     RBFD_CUDA(cudaStreamSynchronize(st));
 
     m->stats.launches += 6;  // unpack, bbox x2, morton, gather, point blocks
@@ -1053,14 +1090,15 @@ void greedy_run(rbfd_mesh *m) {
         Level L;
         L.R = m->R[l];
         L.tau = std::pow(eps_rel, (double)(l + 1) / (double)Lreq);
-        int arg = -1;
-        L.smax = std::sqrt(maxnorm(m, m->d_cur, &arg));
+        // max |dS_l| (read with the level's results; the first-point rule reads it on the device)
+        RBFD_CUDA(cudaMemsetAsync(m->d_lvl, 0, 8 * sizeof(double), st));
+        maxnorm_async(m, m->d_cur, m->d_lvl);
         const double R2 = L.R * L.R;
         RBFD_CUDA(cudaMemsetAsync(m->d_sel, 0, m->n_s, st));
         k_level_init<<<cdiv(std::max(m->n_pb, 1), kThreads), kThreads, 0, st>>>(
             m->opt.first_point == 1 ? 1 : 0, 0, m->d_inv, m->d_xs, m->d_cur, m->n_pb, m->cap, m->dim, R2,
             m->d_pb_lo, m->d_pb_hi, m->d_sel, m->d_cx, m->d_cdf, m->d_cid, m->d_G, m->d_Gt, m->d_w, m->d_alpha, m->d_nb_cnt,
-            m->d_nb_list, m->d_bbox, m->d_st);
+            m->d_nb_list, m->d_lvl, m->d_st);
         RBFD_CUDA(cudaGetLastError());
         m->stats.launches += 2;  // maxnorm + level init
 
@@ -1111,11 +1149,9 @@ void greedy_run(rbfd_mesh *m) {
                     cudaEvent_t e0 = m->prof.begin(st);
                     newton_run_level(m, L.R, L.tau, ctas);
                     m->prof.end(kProfNewton, e0, st, 1);
-                    read_state(m);
+                    read_state_bar(m);
                     m->prof.flush();
-                    GridBarrier hb{};
-                    RBFD_CUDA(cudaMemcpy(&hb, m->d_bar, sizeof(hb), cudaMemcpyDeviceToHost));
-                    if (hb.err) fail(RBFD_ETIMEOUT, "Newton greedy: a grid barrier exceeded its wait bound");
+                    if (m->h_bar->err) fail(RBFD_ETIMEOUT, "Newton greedy: a grid barrier exceeded its wait bound");
                     if (m->h_st->status == RBFD_ESINGULAR)
                         fail(RBFD_ESINGULAR, "Phi_cc is not positive definite at level " + std::to_string(l) +
                                                  " (coincident or near-coincident controls)");
@@ -1144,11 +1180,9 @@ void greedy_run(rbfd_mesh *m) {
                 persist_run_level(m, L.R, L.tau, ctas);
                 m->prof.end(kProfPersist, e0, st, 1);
                 m->stats.persist_ctas = ctas;
-                read_state(m);
+                read_state_bar(m);
                 m->prof.flush();
-                GridBarrier hb{};
-                RBFD_CUDA(cudaMemcpy(&hb, m->d_bar, sizeof(hb), cudaMemcpyDeviceToHost));
-                if (hb.err) fail(RBFD_ETIMEOUT, "persistent greedy: a grid barrier exceeded its wait bound");
+                if (m->h_bar->err) fail(RBFD_ETIMEOUT, "persistent greedy: a grid barrier exceeded its wait bound");
                 if (m->h_st->status == RBFD_ESINGULAR)
                     fail(RBFD_ESINGULAR, "Phi_cc is not positive definite at level " + std::to_string(l) +
                                              " (coincident or near-coincident controls)");
@@ -1197,25 +1231,23 @@ void greedy_run(rbfd_mesh *m) {
             }
             n = m->h_st->n;
             m->stats.greedy_steps += 0;
-            // ---- level close: FP64 iterative refinement of alpha
+            // ---- level close: FP64 iterative refinement of alpha; the
+            // convergence test runs on the device (k_ir_check), so the sweeps
+            // after convergence are launched but do nothing
+            RBFD_CUDA(cudaMemsetAsync(m->d_lvl + 2, 0, sizeof(double), st));
             for (int it = 0; it < std::max(0, m->opt.refine_iters); ++it) {
                 const unsigned nb = cdiv(n, kThreads / 32);  // one warp per control
                 if (m->dim == 2) launch_resid_d<2>(m->opt.basis, nb, n, L.R, m, st);
                 else launch_resid_d<3>(m->opt.basis, nb, n, L.R, m, st);
-                std::vector<double> rmax(nb);
-                RBFD_CUDA(cudaMemcpyAsync(rmax.data(), m->d_red, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-                RBFD_CUDA(cudaStreamSynchronize(st));
-                double r = 0;
-                for (double v : rmax) r = std::max(r, v);
-                if (r <= 1e-15 * m->S0) break;
-                k_lower_mv3<<<cdiv(n, 8), 256, 0, st>>>(n, m->cap, m->d_G, m->d_vec, m->d_vec2);
+                k_ir_check<<<1, 256, 0, st>>>(m->d_red, (int)nb, 1e-15 * m->S0, m->d_lvl);
+                k_lower_mv3<<<cdiv(n, 8), 256, 0, st>>>(n, m->cap, m->d_G, m->d_vec, m->d_vec2, m->d_lvl + 2);
                 const int n_jt = (int)cdiv(n, kJT);
                 k_colsum3<<<dim3(cdiv(n, kThreads), n_jt), kThreads, 0, st>>>(n, m->cap, m->d_G, m->d_vec2,
-                                                                              m->d_v4part);
-                k_apply_correction<<<cdiv(n, kThreads), kThreads, 0, st>>>(n, m->cap, n_jt, m->d_v4part, m->d_alpha);
+                                                                              m->d_v4part, m->d_lvl + 2);
+                k_apply_correction<<<cdiv(n, kThreads), kThreads, 0, st>>>(n, m->cap, n_jt, m->d_v4part, m->d_alpha,
+                                                                           m->d_lvl + 2);
                 RBFD_CUDA(cudaGetLastError());
-                m->stats.launches += 4;
-                m->stats.refine_sweeps++;
+                m->stats.launches += 5;
             }
             // ---- confirm sweep in FP64: stores E = dS_l - Phi_sc alpha
             {
@@ -1250,21 +1282,31 @@ void greedy_run(rbfd_mesh *m) {
         RBFD_CUDA(cudaMemcpyAsync(L.d_cx, m->d_cx, sizeof(double4) * n, cudaMemcpyDeviceToDevice, st));
         RBFD_CUDA(cudaMemcpyAsync(L.d_alpha, m->d_alpha, sizeof(double4) * n, cudaMemcpyDeviceToDevice, st));
         std::vector<uint32_t> orig(n);
-        std::vector<double4> al(n);
+        std::vector<double4> al(n), cxh(n);
         k_orig_of_controls<<<cdiv(n, 256), 256, 0, st>>>(m->d_perm, m->d_cid, n, reinterpret_cast<uint32_t *>(m->d_vec2));
         m->stats.launches += 1;
         RBFD_CUDA(cudaMemcpyAsync(orig.data(), m->d_vec2, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
         RBFD_CUDA(cudaMemcpyAsync(al.data(), m->d_alpha, sizeof(double4) * n, cudaMemcpyDeviceToHost, st));
+        RBFD_CUDA(cudaMemcpyAsync(cxh.data(), m->d_cx, sizeof(double4) * n, cudaMemcpyDeviceToHost, st));
+        RBFD_CUDA(cudaMemcpyAsync(m->h_lvl, m->d_lvl, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
         RBFD_CUDA(cudaStreamSynchronize(st));
+        L.smax = std::sqrt(m->h_lvl[0]);
+        m->stats.refine_sweeps += (int64_t)m->h_lvl[3];
         L.idx.resize(n);
         L.alpha.resize((size_t)n * m->dim);
-        for (int j = 0; j < n; ++j) L.idx[j] = orig[j];
+        double bb[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
         for (int j = 0; j < n; ++j) {
+            L.idx[j] = orig[j];
             L.alpha[(size_t)j * m->dim + 0] = al[j].x;
             L.alpha[(size_t)j * m->dim + 1] = al[j].y;
             if (m->dim == 3) L.alpha[(size_t)j * m->dim + 2] = al[j].z;
+            const double c3[3] = {cxh[j].x, cxh[j].y, cxh[j].z};
+            for (int q = 0; q < 3; ++q) {
+                bb[q] = std::min(bb[q], c3[q]);
+                bb[3 + q] = std::max(bb[3 + q], c3[q]);
+            }
         }
-        build_control_grid(m, L);
+        build_control_grid(m, L, bb);
         if (L.status != RBFD_OK) final_status = RBFD_ENOTCONV;
         m->levels.push_back(std::move(L));
         // multi-level subspace: the next level interpolates this level's error

@@ -164,6 +164,10 @@ struct rbfd_mesh {
                                             //     wall distance search, exact pass; Newton basis terms
     rbfd::GreedyState *d_st = nullptr;
     rbfd::GreedyState *h_st = nullptr;  // pinned
+    rbfd::GridBarrier *h_bar = nullptr; // pinned
+    double *d_lvl = nullptr;            // [8] level scalars: max|dS_l|^2, its argmax, refinement flag and count
+    double *h_lvl = nullptr;            // pinned copy
+    uint32_t *d_ckeys = nullptr;        // [cap + 1] control cell keys
     // persistent engine
     int batch_ctas_cap = 0;          // set by the batch calls: blocks this mesh may use
     int batch_share = 0;             // meshes whose greedy runs beside this one (batch calls, server)
