@@ -178,6 +178,9 @@ struct rbfd_mesh {
     double *d_V = nullptr;
     float4 *d_nwdf = nullptr;       // [cap + 1][2] w in double-float (mixed-mode Newton launch)
     int newton_rec_rows = 0;        // blocks the records below are sized for
+    int newton_shape_key = -1;      // launch shape of the Newton kernel, cached per (blocks asked, sharing)
+    int newton_ctas = 0, newton_ppb = 0, newton_cs = 0;
+    size_t newton_smem = 0;
     double4 *d_nrec = nullptr;      // [blocks][3] per-block candidate records
     double *d_nycol = nullptr;      // [blocks][newton_cols + 1] their columns of V
     unsigned long long *d_phase_ns = nullptr;  // [8] persistent phase timing (profile mode)

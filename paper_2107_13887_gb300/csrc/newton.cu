@@ -44,6 +44,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "internal.h"
 
@@ -799,41 +802,76 @@ struct NewtonShape {
 NewtonShape newton_shape(rbfd_mesh *m, int want_ctas) {
     const int mode = m->opt.precision == RBFD_FP64 ? 0 : 1;
     const void *k = select_newton(m->dim, m->opt.basis, mode);
-    static const size_t kSmemMax = 220 * 1024;  // dynamic shared memory per block (of 227 KB)
+    static const size_t kSmemMax = 220 * 1024;   // dynamic shared memory per block (of 227 KB)
+    static const size_t kSmemPerSM = 228 * 1024;  // shared memory of one SM
+    static const size_t kPerBlockReserve = 4 * 1024;  // static shared memory and the system's share
     NewtonShape s;
     int sms = 0;
     RBFD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
     const int64_t items = (m->n_s + 31) / 32;
+    const int share = std::max(1, m->batch_share);
     int ctas = (int)std::max<int64_t>(1, std::min<int64_t>(want_ctas, items));
     // meshes running side by side (batch calls, server slots) share the SMs:
-    // one block per SM each, so that their launches stay resident together
-    if (m->batch_share > 1) ctas = std::min(ctas, std::max(1, sms / m->batch_share));
+    // their blocks should fit on the GPU together
+    ctas = std::min(ctas, std::max(1, 2 * sms / share));
     // one value for every launch: the attribute belongs to the kernel, and
     // meshes on other host threads launch it concurrently
     RBFD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax));
     for (;;) {
         const int ppb = (int)(32 * ((items + ctas - 1) / ctas));
+        // blocks each SM must hold when every sharing mesh runs this shape
+        const int per_sm = (int)std::max<int64_t>(1, ((int64_t)ctas * share + sms - 1) / sms);
+        const size_t budget = std::min(kSmemMax, kSmemPerSM / per_sm - kPerBlockReserve);
         const size_t fixed = newton_smem_bytes(m->newton_cols, 0, ppb);
-        if (fixed > kSmemMax) fail(RBFD_ENOMEM, "Newton greedy: block state exceeds shared memory");
-        const int cs = (int)std::min<size_t>((size_t)m->newton_cols, (kSmemMax - fixed) / (sizeof(double) * ppb));
-        const size_t smem = newton_smem_bytes(m->newton_cols, cs, ppb);
-        int occ = 0;
-        RBFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kNT, smem));
-        const int maxc = std::min(occ * sms, kMaxPersistCTAs);
-        if (maxc < 1) fail(RBFD_ECUDA, "Newton greedy kernel cannot be resident on this device");
-        if (ctas <= maxc) {
-            s.ctas = ctas;
-            s.ppb = ppb;
-            s.cs = cs;
-            s.smem = smem;
-            return s;
+        if (fixed + 8 * 32 * (size_t)ppb <= budget) {  // at least 32 columns in shared memory
+            const int cs = (int)std::min<size_t>((size_t)m->newton_cols, (budget - fixed) / (sizeof(double) * ppb));
+            const size_t smem = newton_smem_bytes(m->newton_cols, cs, ppb);
+            int occ = 0;
+            RBFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kNT, smem));
+            if (occ >= per_sm && ctas <= std::min(occ * sms, kMaxPersistCTAs)) {
+                s.ctas = ctas;
+                s.ppb = ppb;
+                s.cs = cs;
+                s.smem = smem;
+                return s;
+            }
         }
-        ctas = maxc;  // fewer blocks, more points each
+        if (ctas == 1) fail(RBFD_ENOMEM, "Newton greedy: block state exceeds shared memory");
+        ctas = std::max(1, ctas * 3 / 4);  // fewer blocks, more points each
     }
 }
 
 void newton_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
-    const NewtonShape sh = newton_shape(m, ctas);
+    // the shape depends on the mesh, the request and the co-running meshes only
+    const int key = ctas * 64 + std::min(m->batch_share, 63);
+    if (m->newton_shape_key != key) {
+        // shapes are shared by meshes of the same size and kind (the queries behind them are host calls)
+        static std::mutex mu;
+        static std::map<std::tuple<int, int, int, int, int64_t, int, int, int>, NewtonShape> cache;
+        const auto ck = std::make_tuple(m->device, m->dim, m->opt.basis, m->opt.precision, m->n_s, m->newton_cols,
+                                        ctas, m->batch_share);
+        NewtonShape s;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            auto it = cache.find(ck);
+            if (it != cache.end()) s = it->second;
+        }
+        if (s.ctas == 0) {
+            s = newton_shape(m, ctas);
+            std::lock_guard<std::mutex> lk(mu);
+            cache[ck] = s;
+        }
+        m->newton_shape_key = key;
+        m->newton_ctas = s.ctas;
+        m->newton_ppb = s.ppb;
+        m->newton_cs = s.cs;
+        m->newton_smem = s.smem;
+    }
+    NewtonShape sh;
+    sh.ctas = m->newton_ctas;
+    sh.ppb = m->newton_ppb;
+    sh.cs = m->newton_cs;
+    sh.smem = m->newton_smem;
     NewtonArgs a{};
     a.n_s = m->n_s;
     a.n_pb = m->n_pb;
