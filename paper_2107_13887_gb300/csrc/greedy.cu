@@ -918,10 +918,11 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     double4 *d4 = dalloc<double4>(n, "surface d4");
     k_unpack<<<cdiv(n, 256), 256, 0, st>>>(dx, dd, n, m->dim, x4, d4);
     RBFD_CUDA(cudaGetLastError());
+    // temporaries are returned to the pool after the one synchronisation below
+    std::vector<void *> temps = {x4, d4};
     if (!m->opt.inputs_on_device) {
-        RBFD_CUDA(cudaStreamSynchronize(st));
-        dfree(dx);
-        dfree(dd);
+        temps.push_back(dx);
+        temps.push_back(dd);
     }
     m->d_misc = dalloc<uint32_t>(16, "counters");
     RBFD_CUDA(cudaMemsetAsync(m->d_misc, 0, 16 * sizeof(uint32_t), st));
@@ -931,15 +932,12 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     double *part = dalloc<double>(6 * 256, "bbox partials");
     k_bbox_partial<<<nbb, 256, 0, st>>>(x4, n, part);
     k_bbox_final<<<1, 192, 0, st>>>(part, nbb, m->d_bbox);
-    double bb[6];
-    RBFD_CUDA(cudaMemcpyAsync(bb, m->d_bbox, sizeof(bb), cudaMemcpyDeviceToHost, st));
-    RBFD_CUDA(cudaStreamSynchronize(st));
-    dfree(part);
+    temps.push_back(part);
     uint32_t *keys = dalloc<uint32_t>(n, "morton keys");
+    temps.push_back(keys);
     m->d_perm = dalloc<uint32_t>(n, "permutation");
     m->d_inv = dalloc<uint32_t>(n, "inverse permutation");
-    morton_keys_f64(x4, n, m->dim, make_double3(bb[0], bb[1], bb[2]), make_double3(bb[3], bb[4], bb[5]), keys,
-                    m->d_perm, st);
+    morton_keys_f64_dev(x4, n, m->dim, m->d_bbox, keys, m->d_perm, st);
     radix_sort_pairs(keys, m->d_perm, n, m->dim == 2 ? 32 : 30, m->sort, st);
     m->d_xs = dalloc<double4>(n, "sorted surface");
     m->d_dS = dalloc<double4>(n, "sorted displacement");
@@ -956,10 +954,6 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     m->d_xs_lo = dalloc<float4>(n, "surface lo");
     k_point_blocks<<<m->n_pb, kPB, 0, st>>>(m->d_xs, n, m->d_pb_lo, m->d_pb_hi, m->d_pb_org, m->d_xs_hi, m->d_xs_lo);
     RBFD_CUDA(cudaGetLastError());
-    RBFD_CUDA(cudaStreamSynchronize(st));
-    dfree(keys);
-    dfree(x4);
-    dfree(d4);
 
     // greedy workspace
     int64_t cap = m->opt.nc_cap > 0 ? m->opt.nc_cap : 32768;
@@ -1006,12 +1000,12 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     m->h_lvl = static_cast<double *>(pinned_alloc(8 * sizeof(double)));
     m->d_lvl = dalloc<double>(8, "level scalars");
     RBFD_CUDA(cudaMemsetAsync(m->d_lvl, 0, 8 * sizeof(double), st));
-    RBFD_CUDA(cudaStreamSynchronize(st));
 
     m->stats.launches += 6;  // unpack, bbox x2, morton, gather, point blocks
-    // S0 = max_i |dS_i|
+    // S0 = max_i |dS_i| (the one synchronisation of the set-up)
     m->S0 = std::sqrt(maxnorm(m, m->d_dS, nullptr));
     m->stats.launches += 1;
+    for (void *p : temps) dfree(p);
 }
 
 namespace {

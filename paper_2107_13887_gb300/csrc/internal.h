@@ -66,6 +66,8 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *t
 // Morton keys of points relative to a box: 2D 16 bits per axis, 3D 10 bits.
 void morton_keys_f64(const double4 *xyz, size_t n, int dim, double3 lo, double3 hi, uint32_t *keys,
                      uint32_t *vals, cudaStream_t st);
+void morton_keys_f64_dev(const double4 *xyz, size_t n, int dim, const double *bbox, uint32_t *keys, uint32_t *vals,
+                         cudaStream_t st);
 void morton_keys_f32(const float4 *xyzd, const uint32_t *idx, size_t n, int dim, double3 lo, double3 hi,
                      uint32_t *keys, uint32_t *vals, cudaStream_t st);
 

@@ -193,6 +193,20 @@ __global__ void k_morton_f64(const double4 *__restrict__ p, size_t n, int dim, d
     vals[i] = (uint32_t)i;
 }
 
+// The same with the box read from device memory (lo xyz, hi xyz), so that no
+// host round trip separates the box reduction from the keys.
+__global__ void k_morton_f64_dev(const double4 *__restrict__ p, size_t n, int dim, const double *__restrict__ bb,
+                                 uint32_t *keys, uint32_t *vals) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    auto f = [](double a, double b) { return (b > a) ? 1.0 / (b - a) : 0.0; };
+    const double3 lo = make_double3(bb[0], bb[1], bb[2]);
+    const double3 inv = make_double3(f(bb[0], bb[3]), f(bb[1], bb[4]), f(bb[2], bb[5]));
+    double4 q = p[i];
+    keys[i] = morton(q.x, q.y, q.z, dim, lo, inv);
+    vals[i] = (uint32_t)i;
+}
+
 __global__ void k_morton_f32(const float4 *__restrict__ p, const uint32_t *__restrict__ idx, size_t n, int dim,
                              double3 lo, double3 inv, uint32_t *keys, uint32_t *vals) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -284,6 +298,13 @@ void morton_keys_f64(const double4 *xyz, size_t n, int dim, double3 lo, double3 
                      uint32_t *vals, cudaStream_t st) {
     if (!n) return;
     k_morton_f64<<<grid1(n, 256), 256, 0, st>>>(xyz, n, dim, lo, inv_extent(lo, hi), keys, vals);
+    RBFD_CUDA(cudaGetLastError());
+}
+
+void morton_keys_f64_dev(const double4 *xyz, size_t n, int dim, const double *bbox, uint32_t *keys, uint32_t *vals,
+                         cudaStream_t st) {
+    if (!n) return;
+    k_morton_f64_dev<<<grid1(n, 256), 256, 0, st>>>(xyz, n, dim, bbox, keys, vals);
     RBFD_CUDA(cudaGetLastError());
 }
 
