@@ -212,6 +212,8 @@ void mesh_free(rbfd_mesh *m) {
     for (auto &L : m->levels) {
         dfree(L.d_cx);
         dfree(L.d_alpha);
+        dfree(L.d_cdf);
+        dfree(L.d_adf);
         dfree(L.d_cell_start);
         dfree(L.d_cell_ctrl);
     }
@@ -222,7 +224,7 @@ void mesh_free(rbfd_mesh *m) {
                     m->d_st, m->d_vin, m->d_vpos, m->d_vorig, m->d_vflag, m->d_vscan, m->d_vlist, m->d_vkeys,
                     m->d_vacc, m->d_vio, m->d_misc, m->d_bbox, m->d_bar, m->d_pred, m->d_Gt,
                     m->d_nz_k, m->d_nz_v, m->d_phase_ns, m->d_vreg, m->d_vreg_orig, m->d_pb_fbox,
-                    m->d_V, m->d_nrec, m->d_nycol, m->d_nwdf, m->d_lvl, m->d_ckeys};
+                    m->d_V, m->d_nrec, m->d_nycol, m->d_nwdf, m->d_lvl, m->d_ckeys, m->d_vpos4};
     for (void *p : ptrs) dfree(p);
     m->sort.release();
     m->prof.release();
@@ -447,6 +449,7 @@ int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st) {
         RBFD_CUDA(cudaMemcpy(pr, m->d_pairs, sizeof(pr), cudaMemcpyDeviceToHost));
         m->prof.flush();
         *st = m->stats;
+        st->deform_points += (int64_t)pr[7];
         st->sweep_pairs_useful = (int64_t)pr[0];
         st->sweep_pairs_visited = (int64_t)pr[1];
         st->vol_pairs_useful = (int64_t)pr[2];

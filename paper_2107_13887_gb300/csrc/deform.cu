@@ -203,9 +203,10 @@ __device__ __forceinline__ uint32_t blk_excl_scan(uint32_t v, uint32_t *sw, uint
 
 struct VolArgs {
     int64_t n_list;
+    const uint32_t *n_list_dev;  // if set: the list length in device memory (n_list is then an upper bound)
     const uint32_t *list;   // sorted positions of the points with d < D_l
     const double4 *vpos;    // sorted points (x, y, z, d)
-    double4 *vacc;          // accumulated displacement per sorted point
+    double4 *vacc;          // accumulated displacement per sorted point (FP32-input path: double-float)
     const double4 *cx, *alpha;
     const uint32_t *cell_start, *cell_ctrl;
     double3 g0;
@@ -213,6 +214,12 @@ struct VolArgs {
     int3 gd;
     float invR_hi, invR_lo;
     unsigned long long *pairs;
+    // FP32-input path (mode 2): the same points as float4, the level's controls
+    // and weights as double-float, the grid in FP32
+    const float4 *vp4;
+    const float4 *cdf;      // [2n]: coordinates hi, lo
+    const float4 *adf;      // [2n]: (ax hi, ax lo, ay hi, ay lo), (az hi, az lo, -, -)
+    float g0f[3], hf, Rf, invDlf;
 };
 
 template <int DIM, int BASIS, int MODE>
@@ -223,8 +230,10 @@ __global__ void __launch_bounds__(kThreads) k_vol_sweep(VolArgs a) {
     __shared__ float t32[12][kTile];
     __shared__ unsigned char s_hits[4][kTile];
     const int tid = threadIdx.x;
+    const int64_t n_list = a.n_list_dev ? (int64_t)*a.n_list_dev : a.n_list;
+    if ((int64_t)blockIdx.x * kThreads >= n_list) return;  // (block-uniform)
     const int64_t i = (int64_t)blockIdx.x * kThreads + tid;
-    const bool valid = i < a.n_list;
+    const bool valid = i < n_list;
     const uint32_t s = valid ? a.list[i] : 0u;
     const double4 P = valid ? a.vpos[s] : make_double4(0, 0, 0, 0);
     // block bounding box
@@ -363,10 +372,163 @@ __global__ void __launch_bounds__(kThreads) k_vol_sweep(VolArgs a) {
     }
 }
 
+// The volume update for FP32 volume inputs in mixed precision: the same
+// double-float pair evaluation as mode 1, with every per-point and per-tile
+// step off the FP64 pipe (one FP64 warp instruction costs 64 cycles per SM
+// sub-partition on this GPU): FP32 block box and cell range (one guard cell
+// each side), block-relative coordinates by exact FP32 TwoSum, controls and
+// weights pre-split per level, psi in FP32, double-float accumulator.
+template <int DIM, int BASIS>
+__global__ void __launch_bounds__(kThreads) k_vol_sweep_f32(VolArgs a) {
+    __shared__ float sb[6][kThreads / 32];
+    __shared__ uint32_t s_start[kThreads], s_off[kThreads], sw[32];
+    __shared__ float t32[12][kTile];
+    __shared__ unsigned char s_hits[4][kTile];
+    const int tid = threadIdx.x;
+    const int64_t n_list = a.n_list_dev ? (int64_t)*a.n_list_dev : a.n_list;
+    if ((int64_t)blockIdx.x * kThreads >= n_list) return;  // (block-uniform)
+    const int64_t i = (int64_t)blockIdx.x * kThreads + tid;
+    const bool valid = i < n_list;
+    const uint32_t s = valid ? a.list[i] : 0u;
+    const float4 P = valid ? a.vp4[s] : make_float4(0, 0, 0, 0);
+    float lo[3] = {valid ? P.x : INFINITY, valid ? P.y : INFINITY, valid ? P.z : INFINITY};
+    float hi[3] = {valid ? P.x : -INFINITY, valid ? P.y : -INFINITY, valid ? P.z : -INFINITY};
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    if ((tid & 31) == 0)
+        for (int k = 0; k < 3; ++k) {
+            sb[k][tid >> 5] = lo[k];
+            sb[3 + k][tid >> 5] = hi[k];
+        }
+    __syncthreads();
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = sb[k][0];
+        hi[k] = sb[3 + k][0];
+        for (int q = 1; q < kThreads / 32; ++q) {
+            lo[k] = fminf(lo[k], sb[k][q]);
+            hi[k] = fmaxf(hi[k], sb[3 + k][q]);
+        }
+    }
+    // cell range of the box grown by R, one guard cell each side against FP32 rounding
+    auto cidx = [&](float v, float g, int nmax, int guard) {
+        float f = floorf((v - g) / a.hf) + (float)guard;
+        f = fminf(fmaxf(f, 0.0f), (float)(nmax - 1));
+        return (int)f;
+    };
+    const int ix0 = cidx(lo[0] - a.Rf, a.g0f[0], a.gd.x, -1), ix1 = cidx(hi[0] + a.Rf, a.g0f[0], a.gd.x, 1);
+    const int iy0 = cidx(lo[1] - a.Rf, a.g0f[1], a.gd.y, -1), iy1 = cidx(hi[1] + a.Rf, a.g0f[1], a.gd.y, 1);
+    const int iz0 = DIM == 3 ? cidx(lo[2] - a.Rf, a.g0f[2], a.gd.z, -1) : 0;
+    const int iz1 = DIM == 3 ? cidx(hi[2] + a.Rf, a.g0f[2], a.gd.z, 1) : 0;
+    const int nx = ix1 - ix0 + 1, ny = iy1 - iy0 + 1, nz = iz1 - iz0 + 1;
+    const int ncr = nx * ny * nz;
+    // point relative to the box corner: exact as a double-float (both are floats)
+    const df qx = two_sum(P.x, -lo[0]), qy = two_sum(P.y, -lo[1]), qz = two_sum(P.z, -lo[2]);
+    const df invR = {a.invR_hi, a.invR_lo};
+    df acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+    unsigned useful = 0;
+    unsigned long long visited = 0;
+    float3 wlo, whi;
+    warp_box(valid, qx.hi, qy.hi, qz.hi, wlo, whi);
+    const float R2m = (1.002f * a.Rf) * (1.002f * a.Rf);  // filter margin
+    for (int cb = 0; cb < ncr; cb += kThreads) {
+        const int c = cb + tid;
+        uint32_t cnt = 0, st0 = 0;
+        if (c < ncr) {
+            int ix = ix0 + c % nx, iy = iy0 + (c / nx) % ny, iz = iz0 + c / (nx * ny);
+            int cell = (iz * a.gd.y + iy) * a.gd.x + ix;
+            st0 = a.cell_start[cell];
+            cnt = a.cell_start[cell + 1] - st0;
+        }
+        uint32_t T;
+        uint32_t off = blk_excl_scan(cnt, sw, &T);
+        s_start[tid] = st0;
+        s_off[tid] = off;
+        __syncthreads();
+        for (uint32_t w0 = 0; w0 < T; w0 += kTile) {
+            const int m = (int)min((uint32_t)kTile, T - w0);
+            if (tid < m) {
+                uint32_t q = w0 + tid;
+                int l = 0, r = kThreads;  // last k with s_off[k] <= q
+                while (r - l > 1) {
+                    int mid = (l + r) >> 1;
+                    if (s_off[mid] <= q) l = mid;
+                    else r = mid;
+                }
+                const uint32_t j = a.cell_ctrl[s_start[l] + (q - s_off[l])];
+                const float4 ch = a.cdf[2 * j], cl = a.cdf[2 * j + 1];
+                const df rx = df_add({ch.x, cl.x}, {-lo[0], 0.f}), ry = df_add({ch.y, cl.y}, {-lo[1], 0.f}),
+                         rz = df_add({ch.z, cl.z}, {-lo[2], 0.f});
+                const float4 a0 = a.adf[2 * j], a1 = a.adf[2 * j + 1];
+                t32[0][tid] = rx.hi; t32[1][tid] = rx.lo; t32[2][tid] = ry.hi; t32[3][tid] = ry.lo;
+                t32[4][tid] = rz.hi; t32[5][tid] = rz.lo; t32[6][tid] = a0.x; t32[7][tid] = a0.y;
+                t32[8][tid] = a0.z; t32[9][tid] = a0.w; t32[10][tid] = a1.x; t32[11][tid] = a1.y;
+            }
+            __syncthreads();
+            // the whole warp takes part in the filter; lanes with a point accumulate
+            const int nh = warp_hits<DIM>(t32, m, wlo, whi, R2m, s_hits[tid >> 5]);
+            if (valid) {
+                visited += nh;
+                hits_accumulate_df<DIM, BASIS>(qx, qy, qz, t32, s_hits[tid >> 5], nh, invR, acc, useful);
+            }
+            __syncthreads();
+        }
+    }
+    if (valid) {
+        const float w = 1.0f - P.w * a.invDlf;  // psi(d / D_l), d < D_l here
+        float4 *va = reinterpret_cast<float4 *>(a.vacc + s);
+        const float4 v0 = va[0], v1 = va[1];
+        const df sx = df_add({v0.x, v0.y}, df_mul(acc[0], {w, 0.f}));
+        const df sy = df_add({v0.z, v0.w}, df_mul(acc[1], {w, 0.f}));
+        const df sz = df_add({v1.x, v1.y}, df_mul(acc[2], {w, 0.f}));
+        va[0] = make_float4(sx.hi, sx.lo, sy.hi, sy.lo);
+        va[1] = make_float4(sz.hi, sz.lo, 0.f, 0.f);
+    }
+    unsigned u = useful;
+    unsigned long long vv = visited;
+    for (int o = 16; o > 0; o >>= 1) {
+        u += __shfl_xor_sync(0xffffffffu, u, o);
+        vv += __shfl_xor_sync(0xffffffffu, vv, o);
+    }
+    if ((tid & 31) == 0) {
+        if (u) atomicAdd(&a.pairs[0], (unsigned long long)u);
+        if (vv) atomicAdd(&a.pairs[1], vv);
+    }
+}
+
+// Volume points taking part in a level, summed on the device (statistics).
+__global__ void k_count_points(const uint32_t *__restrict__ n, unsigned long long *__restrict__ total) {
+    if (threadIdx.x == 0) *total += *n;
+}
+
+// Sorted points as float4 for the FP32-input path.
+__global__ void k_to_f4(const double4 *__restrict__ p, int64_t n, float4 *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double4 q = p[i];
+    out[i] = make_float4((float)q.x, (float)q.y, (float)q.z, (float)q.w);
+}
+
+// The double-float accumulator of the FP32-input path to the caller's order.
+__global__ void k_scatter_out_df(const double4 *__restrict__ acc, const uint32_t *__restrict__ orig, int64_t n,
+                                 int dim, float *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 *va = reinterpret_cast<const float4 *>(acc + i);
+    const float4 v0 = va[0], v1 = va[1];
+    float *q = out + (int64_t)orig[i] * dim;
+    q[0] = v0.x + v0.y;
+    q[1] = v0.z + v0.w;
+    if (dim == 3) q[2] = v1.x + v1.y;
+}
+
 template <int DIM, int BASIS>
 void launch_vol_t(int mode, unsigned g, const VolArgs &a, cudaStream_t st) {
     if (mode == 0) k_vol_sweep<DIM, BASIS, 0><<<g, kThreads, 0, st>>>(a);
-    else k_vol_sweep<DIM, BASIS, 1><<<g, kThreads, 0, st>>>(a);
+    else if (mode == 1) k_vol_sweep<DIM, BASIS, 1><<<g, kThreads, 0, st>>>(a);
+    else k_vol_sweep_f32<DIM, BASIS><<<g, kThreads, 0, st>>>(a);
 }
 
 void launch_vol(int dim, int basis, int mode, unsigned g, const VolArgs &a, cudaStream_t st) {
@@ -407,6 +569,9 @@ void reserve_volume(rbfd_mesh *m, size_t n) {
     m->d_vlist = dalloc<uint32_t>(n, "volume list");
     m->d_vkeys = dalloc<uint32_t>(n, "volume keys");
     m->d_vacc = dalloc<double4>(n, "volume displacement");
+    dfree(m->d_vpos4);
+    m->d_vpos4 = nullptr;
+    m->d_vpos4 = dalloc<float4>(n, "sorted volume points (FP32)");
     m->vol_cap = n;
 }
 
@@ -437,21 +602,25 @@ void deform_levels(rbfd_mesh *m, int64_t nV, const double4 *vpos, const uint32_t
     cudaStream_t st = m->stream;
     const int dim = m->dim;
     RBFD_CUDA(cudaMemsetAsync(m->d_vacc, 0, sizeof(double4) * nV, st));
-    // (3) per level: d < D_l, then the fused evaluation
-    const int mode = m->opt.precision == RBFD_FP64 ? 0 : 1;
+    // mixed precision with FP32 inputs: the FP32-input sweep on a float4 copy
+    const bool fast = m->opt.precision != RBFD_FP64 && !f64 && m->d_vpos4;
+    if (fast) {
+        k_to_f4<<<cdiv(nV, 256), 256, 0, st>>>(vpos, nV, m->d_vpos4);
+        m->stats.launches += 1;
+    }
+    const int mode = m->opt.precision == RBFD_FP64 ? 0 : (fast ? 2 : 1);
+    // (3) per level: d < D_l, then the fused evaluation; the list length
+    // stays on the device (the sweep reads it), so no level waits for the host
     for (int l = 0; l < L; ++l) {
         const Level &Lv = m->levels[l];
         if (Lv.nc == 0 || !(Dl[l] > 0.0)) continue;
         k_flag_below<<<cdiv(nV, 256), 256, 0, st>>>(vpos, nullptr, nV, Dl[l], m->d_vflag);
         exclusive_scan_u32(m->d_vflag, m->d_vscan, (size_t)nV, &m->d_misc[5], m->sort, st);
         k_compact<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vflag, m->d_vscan, nV, m->d_vlist);
-        uint32_t nl = 0;
-        RBFD_CUDA(cudaMemcpyAsync(&nl, &m->d_misc[5], sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-        RBFD_CUDA(cudaStreamSynchronize(st));
-        if (nl == 0) continue;
-        m->stats.deform_points += nl;
+        k_count_points<<<1, 32, 0, st>>>(&m->d_misc[5], m->d_pairs + 7);
         VolArgs a{};
-        a.n_list = nl;
+        a.n_list = nV;  // upper bound; the exact count is read on the device
+        a.n_list_dev = &m->d_misc[5];
         a.list = m->d_vlist;
         a.vpos = vpos;
         a.vacc = m->d_vacc;
@@ -468,15 +637,29 @@ void deform_levels(rbfd_mesh *m, int64_t nV, const double4 *vpos, const uint32_t
         a.invR_hi = (float)inv;
         a.invR_lo = (float)(inv - (double)a.invR_hi);
         a.pairs = m->d_pairs + 2;
-        m->stats.launches += 3;  // flags, compaction (+ scan counted in the scan)
+        if (fast) {
+            a.vp4 = m->d_vpos4;
+            a.cdf = Lv.d_cdf;
+            a.adf = Lv.d_adf;
+            a.g0f[0] = (float)Lv.g0.x;
+            a.g0f[1] = (float)Lv.g0.y;
+            a.g0f[2] = (float)Lv.g0.z;
+            a.hf = (float)Lv.h;
+            a.Rf = (float)Lv.R;
+            a.invDlf = (float)(1.0 / Dl[l]);
+        }
+        m->stats.launches += 4;  // flags, compaction, count (+ scan counted in the scan)
         cudaEvent_t e0 = m->prof.begin(st);
-        launch_vol(dim, m->opt.basis, mode, cdiv(nl, kThreads), a, st);
+        launch_vol(dim, m->opt.basis, mode, cdiv(nV, kThreads), a, st);
         RBFD_CUDA(cudaGetLastError());
         m->prof.end(kProfVol, e0, st, 1);
         m->stats.launches += 1;
     }
     // (4) back to the caller's order
-    k_scatter_out<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vacc, vorig, nV, dim, f64 ? 1 : 0, dout);
+    if (fast)
+        k_scatter_out_df<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vacc, vorig, nV, dim, static_cast<float *>(dout));
+    else
+        k_scatter_out<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vacc, vorig, nV, dim, f64 ? 1 : 0, dout);
     RBFD_CUDA(cudaGetLastError());
 }
 

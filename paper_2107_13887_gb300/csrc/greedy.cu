@@ -862,6 +862,20 @@ double maxnorm(rbfd_mesh *m, const double4 *v, int *arg) {
     return h[0];
 }
 
+// A level's controls and weights as double-float pairs (FP32-input volume sweep).
+__global__ void k_level_split(const double4 *__restrict__ cx, const double4 *__restrict__ al, int n,
+                              float4 *__restrict__ cdf, float4 *__restrict__ adf) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double4 c = cx[j], a = al[j];
+    const df x = df_from_double(c.x), y = df_from_double(c.y), z = df_from_double(c.z);
+    const df ax = df_from_double(a.x), ay = df_from_double(a.y), az = df_from_double(a.z);
+    cdf[2 * j] = make_float4(x.hi, y.hi, z.hi, 0.f);
+    cdf[2 * j + 1] = make_float4(x.lo, y.lo, z.lo, 0.f);
+    adf[2 * j] = make_float4(ax.hi, ax.lo, ay.hi, ay.lo);
+    adf[2 * j + 1] = make_float4(az.hi, az.lo, 0.f, 0.f);
+}
+
 // Uniform grid of cell size h over the level's controls (for the volume
 // sweep); bb = the controls' box (lo xyz, hi xyz), known on the host.
 void build_control_grid(rbfd_mesh *m, Level &L, const double *bb) {
@@ -1040,6 +1054,8 @@ void mesh_set_displacement(rbfd_mesh *m, const double *dS) {
     for (auto &L : m->levels) {
         dfree(L.d_cx);
         dfree(L.d_alpha);
+        dfree(L.d_cdf);
+        dfree(L.d_adf);
         dfree(L.d_cell_start);
         dfree(L.d_cell_ctrl);
     }
@@ -1058,6 +1074,8 @@ void greedy_run(rbfd_mesh *m) {
     for (auto &L : m->levels) {
         dfree(L.d_cx);
         dfree(L.d_alpha);
+        dfree(L.d_cdf);
+        dfree(L.d_adf);
         dfree(L.d_cell_start);
         dfree(L.d_cell_ctrl);
     }
@@ -1275,6 +1293,10 @@ void greedy_run(rbfd_mesh *m) {
         L.d_alpha = dalloc<double4>(n, "level weights");
         RBFD_CUDA(cudaMemcpyAsync(L.d_cx, m->d_cx, sizeof(double4) * n, cudaMemcpyDeviceToDevice, st));
         RBFD_CUDA(cudaMemcpyAsync(L.d_alpha, m->d_alpha, sizeof(double4) * n, cudaMemcpyDeviceToDevice, st));
+        L.d_cdf = dalloc<float4>((size_t)2 * n, "level controls (double-float)");
+        L.d_adf = dalloc<float4>((size_t)2 * n, "level weights (double-float)");
+        k_level_split<<<cdiv(n, 256), 256, 0, st>>>(m->d_cx, m->d_alpha, n, L.d_cdf, L.d_adf);
+        m->stats.launches += 1;
         std::vector<uint32_t> orig(n);
         std::vector<double4> al(n), cxh(n);
         k_orig_of_controls<<<cdiv(n, 256), 256, 0, st>>>(m->d_perm, m->d_cid, n, reinterpret_cast<uint32_t *>(m->d_vec2));

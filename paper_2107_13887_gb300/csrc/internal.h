@@ -81,6 +81,8 @@ struct Level {
     std::vector<double> alpha;    // [nc][dim]
     double4 *d_cx = nullptr;      // control coordinates (FP64)
     double4 *d_alpha = nullptr;   // weights (FP64)
+    float4 *d_cdf = nullptr;      // [2 nc] the coordinates as double-float (hi xyz, lo xyz)
+    float4 *d_adf = nullptr;      // [2 nc] the weights as double-float ((ax, ay) hi/lo pairs, az pair)
     // uniform cell grid over the controls (cell size h) for the volume sweep
     double3 g0{0, 0, 0};
     double h = 0;
@@ -198,6 +200,7 @@ struct rbfd_mesh {
     size_t vol_cap = 0;
     float4 *d_vin = nullptr;       // input points (x, y, z, d), caller order
     float4 *d_vpos = nullptr;      // compacted + Morton-sorted points
+    float4 *d_vpos4 = nullptr;     // the same as float4 (FP32-input volume sweep)
     uint32_t *d_vorig = nullptr;   // their caller indices
     uint32_t *d_vflag = nullptr, *d_vscan = nullptr, *d_vlist = nullptr, *d_vkeys = nullptr;
     double4 *d_vacc = nullptr;     // accumulated displacement per sorted point
