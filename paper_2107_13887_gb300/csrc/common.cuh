@@ -394,7 +394,7 @@ struct GreedyState {
 
 // Counter + generation word of the bounded grid barrier of the persistent
 // greedy launch; err is set by a block that waited too long.
-struct GridBarrier {
+struct alignas(16) GridBarrier {
     unsigned int count;
     unsigned int gen;
     int err;
@@ -449,27 +449,33 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *b, unsigned nblk, unsigne
 __device__ __forceinline__ void grid_arrive_mono(GridBarrier *b) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(&b->count, 1u);
+        // release: the block's writes (ordered before this thread by the
+        // block barrier) become visible to a block that observes the count
+        asm volatile("fence.acq_rel.gpu;\n\tred.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(&b->count) : "memory");
     }
 }
 
 __device__ __forceinline__ bool grid_wait_mono(GridBarrier *b, unsigned target, unsigned long long limit) {
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
-        volatile unsigned *vcnt = &b->count;
-        volatile int *verr = &b->err;
+        // one 16-byte load per poll reads the count and the error word together
         unsigned long long it = 0;
-        while (*vcnt < target) {
-            if (*verr) break;
+        unsigned cnt, gen, err, pad;
+        for (;;) {
+            asm volatile("ld.relaxed.gpu.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(cnt), "=r"(gen), "=r"(err), "=r"(pad)
+                         : "l"(b)
+                         : "memory");
+            if (cnt >= target || err) break;
             if (++it > limit) {
                 atomicExch(&b->err, 1);
+                err = 1;
                 break;
             }
             __nanosleep(8);
         }
-        __threadfence();
-        s_ok = (*verr == 0);
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");  // acquire: pairs with the arrivals' release
+        s_ok = (err == 0);
     }
     __syncthreads();
     return s_ok != 0;

@@ -583,12 +583,8 @@ void morton_order(rbfd_mesh *m, int64_t n, const double4 *vin, double4 *vsorted,
     const int nbb = std::min<int>(cdiv(n, 256), 256);
     k_bbox_partial_v<<<nbb, 256, 0, st>>>(vin, n, m->d_red);
     k_bbox_reduce<<<1, 192, 0, st>>>(m->d_red, nbb, m->d_bbox);
-    double bb[6];
-    RBFD_CUDA(cudaMemcpyAsync(bb, m->d_bbox, sizeof(bb), cudaMemcpyDeviceToHost, st));
-    RBFD_CUDA(cudaStreamSynchronize(st));
-    morton_keys_f64(vin, n, dim, make_double3(bb[0], bb[1], bb[2]), make_double3(bb[3], bb[4], bb[5]), m->d_vkeys,
-                    orig, st);
-    radix_sort_pairs(m->d_vkeys, orig, (size_t)n, dim == 2 ? 32 : 30, m->sort, st);
+    morton_keys_f64_dev(vin, n, dim, m->d_bbox, m->d_vkeys, orig, st, vol_key_shift(dim));
+    radix_sort_pairs(m->d_vkeys, orig, (size_t)n, kVolKeyBits, m->sort, st);
     k_gather_vol<<<cdiv(n, 256), 256, 0, st>>>(vin, orig, n, vsorted);
     RBFD_CUDA(cudaGetLastError());
     m->stats.launches += 4;
@@ -745,13 +741,9 @@ void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, b
         const int nbb = std::min<int>(cdiv(nV, 256), 256);
         k_bbox_idx<<<nbb, 256, 0, st>>>(vin, m->d_vlist, nV, m->d_red);
         k_bbox_reduce<<<1, 192, 0, st>>>(m->d_red, nbb, m->d_bbox);
-        double bb[6];
-        RBFD_CUDA(cudaMemcpyAsync(bb, m->d_bbox, sizeof(bb), cudaMemcpyDeviceToHost, st));
-        RBFD_CUDA(cudaStreamSynchronize(st));
         k_gather_vol<<<cdiv(nV, 256), 256, 0, st>>>(vin, m->d_vlist, nV, vpos);  // kept points, caller order
-        morton_keys_f64(vpos, nV, dim, make_double3(bb[0], bb[1], bb[2]), make_double3(bb[3], bb[4], bb[5]),
-                        m->d_vkeys, m->d_vorig, st);
-        radix_sort_pairs(m->d_vkeys, m->d_vorig, (size_t)nV, dim == 2 ? 32 : 30, m->sort, st);
+        morton_keys_f64_dev(vpos, nV, dim, m->d_bbox, m->d_vkeys, m->d_vorig, st, vol_key_shift(dim));
+        radix_sort_pairs(m->d_vkeys, m->d_vorig, (size_t)nV, kVolKeyBits, m->sort, st);
         k_gather_vol<<<cdiv(nV, 256), 256, 0, st>>>(vpos, m->d_vorig, nV, vin);  // vin := sorted points
         // caller index of sorted point i = vlist[vorig[i]]
         k_gather_u32<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vlist, m->d_vorig, nV, m->d_vflag);
@@ -980,13 +972,9 @@ void deform_noalloc_run(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const flo
         const int nbb = std::min<int>(cdiv(nV, 256), 256);
         k_bbox_idx<<<nbb, 256, 0, st>>>(vin, vlist, nV, m->d_red);
         k_bbox_reduce<<<1, 192, 0, st>>>(m->d_red, nbb, m->d_bbox);
-        double bb[6];
-        RBFD_CUDA(cudaMemcpyAsync(bb, m->d_bbox, sizeof(bb), cudaMemcpyDeviceToHost, st));
-        RBFD_CUDA(cudaStreamSynchronize(st));
         k_gather_vol<<<cdiv(nV, 256), 256, 0, st>>>(vin, vlist, nV, vpos);
-        morton_keys_f64(vpos, nV, dim, make_double3(bb[0], bb[1], bb[2]), make_double3(bb[3], bb[4], bb[5]), vkeys,
-                        vorig, st);
-        radix_sort_pairs(vkeys, vorig, (size_t)nV, dim == 2 ? 32 : 30, ss, st);
+        morton_keys_f64_dev(vpos, nV, dim, m->d_bbox, vkeys, vorig, st, vol_key_shift(dim));
+        radix_sort_pairs(vkeys, vorig, (size_t)nV, kVolKeyBits, ss, st);
         k_gather_vol<<<cdiv(nV, 256), 256, 0, st>>>(vpos, vorig, nV, vin);  // vin := sorted points
         k_gather_u32<<<cdiv(nV, 256), 256, 0, st>>>(vlist, vorig, nV, vflag);
         RBFD_CUDA(cudaMemcpyAsync(vorig, vflag, sizeof(uint32_t) * nV, cudaMemcpyDeviceToDevice, st));

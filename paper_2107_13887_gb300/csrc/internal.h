@@ -63,11 +63,14 @@ void radix_sort_pairs(uint32_t *keys, uint32_t *vals, size_t n, int key_bits, So
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *total_dev, SortScratch &s,
                         cudaStream_t st);
 
-// Morton keys of points relative to a box: 2D 16 bits per axis, 3D 10 bits.
-void morton_keys_f64(const double4 *xyz, size_t n, int dim, double3 lo, double3 hi, uint32_t *keys,
-                     uint32_t *vals, cudaStream_t st);
+// Morton keys of points relative to the box bbox[6] in device memory: 2D 16
+// bits per axis, 3D 10 bits, shifted right by `shift` bits (coarser keys,
+// fewer radix passes).
 void morton_keys_f64_dev(const double4 *xyz, size_t n, int dim, const double *bbox, uint32_t *keys, uint32_t *vals,
-                         cudaStream_t st);
+                         cudaStream_t st, int shift = 0);
+// Volume points: 24-bit Morton keys (12 bits per axis in 2D, 8 in 3D), three radix passes.
+constexpr int kVolKeyBits = 24;
+inline int vol_key_shift(int dim) { return dim == 2 ? 32 - kVolKeyBits : 30 - kVolKeyBits; }
 void morton_keys_f32(const float4 *xyzd, const uint32_t *idx, size_t n, int dim, double3 lo, double3 hi,
                      uint32_t *keys, uint32_t *vals, cudaStream_t st);
 

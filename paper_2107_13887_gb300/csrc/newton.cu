@@ -27,8 +27,8 @@
 // point therefore knows l^2 = 1 - s2 and w = E / l of its own, and a block
 // publishes a complete record of its best candidate (key, position,
 // coordinates, l^2, E) plus its column y = V[.][candidate].  Per pass, for the
-// control c_j decided in the previous pass:
-//   y <- the winner's published column;
+// control c_j decided in the previous pass (y = the winner's published
+// column, loaded during that decision):
 //   (a) v_j at the block's points: V[j][i], E_i -= w_j v_j(x_i), s2_i += v_j^2,
 //       the block's argmax of |E_i|^2 over unselected points -> its record;
 //       c_j appended to the control lists of the point blocks within R;
@@ -40,10 +40,13 @@
 //   -- wait --
 //   every block reads the P records and takes the same decision: global
 //   argmax, stop test |E|max / S0 < tau_l in FP64, pivot test, the next
-//   control; block 0 records it.
+//   control; block 0 records it.  One warp computes the step's scalars
+//   while the others load the winner's column.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -56,6 +59,8 @@ namespace {
 
 constexpr int kNT = 256;  // threads per block (8 warps)
 constexpr int kNW = kNT / 32;
+constexpr int kRound = 2;     // point groups per round of (a)
+constexpr int kRowChunk = 8;  // entries per lane of a row of (b) loaded together
 
 // Keys of the argmax as unsigned 64-bit integers in the order of the values:
 // FP64 mode, the bit pattern of the non-negative double plus one; mixed mode,
@@ -153,8 +158,11 @@ struct NewtonArgs {
     int n_pb, cap, cn;  // cn: columns of V (controls the launch may reach)
     int ppb, cs;        // points per block (32 per group), columns of V held in shared memory
     double R, invR, R2, S0, tau, piv_tol_per_n, switch_ratio, switch_work;
-    double K_lo, K_hi;  // (tau S0)^2 with a relative margin of 1e-12 either side
+    // the stop test's bracket as argmax keys: key < key_lo is below the
+    // threshold, key >= key_hi above it, keys between are tested exactly
+    unsigned long long key_lo, key_hi;
     float invR_hi, invR_lo;
+    float Rlist;  // R (1 + 1e-9), rounded up to FP32: the list test's radius
     const double4 *xs, *pb_lo, *pb_hi;
     const uint32_t *perm;
     const double4 *E0;  // E at the start of the level (= dS_l)
@@ -165,7 +173,7 @@ struct NewtonArgs {
     float4 *cdf;
     uint32_t *cid;
     double *G, *Gt, *V;  // V: FP64, or hi/lo float pairs in mixed mode
-    double4 *rec;  // [2][P][3] per block: (key, original index, longest list, position), coordinates + l^2, E
+    double4 *rec;  // [2][P][3] per block: integers (key, original index, longest list, position), coordinates + l^2, E
     double *ycol;  // [2][P][cn + 1] per block: V[.][candidate] (mixed mode: hi/lo float pairs)
     // (two copies, by the parity of the step: a block writes the next step's
     // record while a slower block may still read this step's)
@@ -179,8 +187,9 @@ struct NewtonArgs {
 
 // Dynamic shared memory of one block (8-byte words): y [cn], V slice
 // [cs][ppb], E [3][ppb], coordinates [3][ppb], s2 [ppb]; then original
-// indices [ppb] and selected flags [ppb].  Mixed mode keeps each 8-byte value
-// as a hi float array followed by a lo float array.
+// indices [ppb] and selected flags [ppb].  Mixed mode keeps y as (hi, lo)
+// float pairs and each other 8-byte value as a hi float array followed by a
+// lo float array.
 inline size_t newton_smem_bytes(int cn, int cs, int ppb) {
     return 8 * ((size_t)cn + (size_t)cs * ppb + 7 * (size_t)ppb) + 4 * (size_t)ppb + (size_t)ppb;
 }
@@ -189,8 +198,8 @@ template <int DIM, int BASIS, int MODE>
 __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
     extern __shared__ double dsm[];
     const int ppb = a.ppb, n_grp = ppb / 32;
-    double *s_y = dsm;                        // FP64: y [cn]
-    float *s_yh = reinterpret_cast<float *>(dsm), *s_yl = s_yh + a.cn;  // mixed: y hi, lo
+    double *s_y = dsm;                        // y [cn] (mixed: as FP64 only during (b))
+    float2 *s_y2 = reinterpret_cast<float2 *>(dsm);  // mixed: y as (hi, lo) pairs in the same words
     double *s_V = dsm + a.cn;                 // FP64: V[k][slot], k < cs
     float *s_Vh = reinterpret_cast<float *>(s_V), *s_Vl = s_Vh + (size_t)a.cs * ppb;
     double *s_E = s_V + (size_t)a.cs * ppb;   // E of the block's points (x, y, z rows)
@@ -201,15 +210,18 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
     float *s_S2h = reinterpret_cast<float *>(s_S2), *s_S2l = s_S2h + ppb;
     int *s_orig = reinterpret_cast<int *>(s_S2 + ppb);  // original surface index
     unsigned char *s_sel = reinterpret_cast<unsigned char *>(s_orig + ppb);
-    __shared__ double s_part[kNW][32];        // FP64: partial dots; mixed: hi [8][32] then lo
+    // partial dots of the two groups of a round of (a), [group][warp][lane]
+    // (FP64; mixed: hi [8][32] then lo [8][32] per group)
+    __shared__ double s_part[kRound][kNW][32];
     __shared__ unsigned long long sk[32];
     __shared__ int si[32];
-    __shared__ double s_dec[8];  // the step's scalars, computed by one warp
-    __shared__ int s_flags;
+    // the step's scalars, computed by one warp: [2] 1 / l_j (mixed: its
+    // double-float bits), [3] 1 / l_j and [4..6] w_j in FP64 for (b)
+    __shared__ double s_dec[8];
+    __shared__ int s_flags, s_mc;
     __shared__ unsigned s_nz[kNW], s_lm[kNW];
     __shared__ int s_win;
     __shared__ double4 s_wrec[3];
-    float *s_parth = reinterpret_cast<float *>(&s_part[0][0]), *s_partl = s_parth + kNW * 32;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned P = gridDim.x;
@@ -249,11 +261,15 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
     // (box and count in registers: appends never read back)
     const int t_own = (int)blockIdx.x + tid * (int)P;
     const bool own_list = t_own < a.n_pb;
-    double4 own_lo = make_double4(0, 0, 0, 0), own_hi = own_lo;
+    // the block box rounded outward to FP32: the list test below runs in
+    // FP32 with a radius that covers its rounding, so it keeps every control
+    // within R of the box (and a few just beyond it, which add zero terms)
+    float3 own_lo = make_float3(0.f, 0.f, 0.f), own_hi = own_lo;
     uint32_t own_cnt = 0;
     if (own_list) {
-        own_lo = a.pb_lo[t_own];
-        own_hi = a.pb_hi[t_own];
+        const double4 lo = a.pb_lo[t_own], hi = a.pb_hi[t_own];
+        own_lo = make_float3(__double2float_rd(lo.x), __double2float_rd(lo.y), __double2float_rd(lo.z));
+        own_hi = make_float3(__double2float_ru(hi.x), __double2float_ru(hi.y), __double2float_ru(hi.z));
         own_cnt = __ldcg(&a.nb_cnt[t_own]);
     }
     // the launch starts a level: control 0 placed, nothing propagated yet
@@ -266,7 +282,12 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
     df ild = {1.0f, 0.0f};
     double4 wj = ldcg_d4(&a.w[0]);
     df wd[3] = {df_from_double(wj.x), df_from_double(wj.y), df_from_double(wj.z)};
-    int B = -1;  // block whose column is y of c_j
+    if (tid == 0) {  // (b) of control 0: l_0 = 1
+        s_dec[3] = 1.0;
+        s_dec[4] = wj.x;
+        s_dec[5] = wj.y;
+        s_dec[6] = wj.z;
+    }
     // counts kept per block and added once at the end: nonzeros of Phi_sc in
     // this block's points so far, and the pairs a list sweep of each step
     // would have evaluated there
@@ -275,8 +296,9 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
     // rows of the inverse factor: row k belongs to warp (k / P) % 8 of block k % P
     const int k_first = (int)blockIdx.x + warp * (int)P;
     const df invRd = {a.invR_hi, a.invR_lo};
-    // profile mode, block 0: [0] y, [1] (a), [2] lists + record, [3] (b),
-    // [4] barrier wait, [5] reading the records, [6] their argmax, [7] the rest
+    // profile mode, block 0: [0] marking c_j, [1] (a), [2] lists + record, [3] (b),
+    // [4] barrier wait, [5] reading the records, [6] their argmax, [7] scalars
+    // and the next y
     const bool timing = a.phase_ns && blockIdx.x == 0 && tid == 0;
     unsigned long long acc_ns[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     unsigned long long t_mark = timing ? gtimer() : 0ull;
@@ -300,26 +322,32 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
         RBFD_NEXIT()
     }
 
+    __syncthreads();  // the block's state is in shared memory
+    // Block barriers per pass: two per group of (a), two in the record, one
+    // after the grid barrier's arrival (mixed mode), one in the wait, three in
+    // the decision.  The first of (a) orders the marking below and the
+    // previous decision's shared writes before their readers.
     for (int guard = 0; guard <= a.cap; ++guard) {
         const int j = n - 1;  // the control this pass propagates
-        if (B >= 0) {  // written in the previous pass, parity (j - 1) & 1
-            const double *yb = a.ycol + ((size_t)((j - 1) & 1) * P + B) * ycl;
-            if (MODE) {
-                const float2 *yf = reinterpret_cast<const float2 *>(yb);
-                for (int k = tid; k < j; k += kNT) {
-                    const float2 v = __ldcg(&yf[k]);
-                    s_yh[k] = v.x;
-                    s_yl[k] = v.y;
-                }
-            } else {
-                for (int k = tid; k < j; k += kNT) s_y[k] = __ldcg(&yb[k]);
-            }
-        }
+        // (y of c_j was loaded by the previous pass's decision)
         {  // the owner marks c_j as selected
             const int64_t item = (int64_t)cj / 32;
             if (tid == 0 && item % P == blockIdx.x) s_sel[(int)(item / P) * 32 + (int)(cj % 32)] = 1;
         }
-        __syncthreads();
+        // this warp's first row of the inverse factor for (b): its entries
+        // before column j are final (this warp wrote them), so the loads
+        // start now and arrive during (a)
+        double gpre[kRowChunk];
+        double4 apre = make_double4(0, 0, 0, 0);
+        if (k_first < j) {
+            const double *trow = a.Gt + (size_t)k_first * a.cap;
+#pragma unroll
+            for (int q = 0; q < kRowChunk; ++q) {
+                const int m = k_first + lane + 32 * q;
+                gpre[q] = m < j ? __ldcg(trow + m) : 0.0;
+            }
+            if (lane == 0) apre = ldcg_d4(&a.alpha[k_first]);
+        }
         RBFD_TMARK(0)
 
         // ---- (a) v_j at the block's points, E update, argmax
@@ -327,129 +355,148 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
         int bidx = -1, bslot = -1;
         unsigned nz = 0;
         const int kcs = min(j, a.cs);
-        for (int g = 0; g < n_grp; ++g) {
-            const int sl = g * 32 + lane;
-            const int64_t i = point_of(sl);
-            const bool valid = i < a.n_s;
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-            if (valid) {
-                int k = warp;
-                if (MODE) {
-                    // double-float on the FP32 pipe (FP64 issues at a small
-                    // fraction of the FP32 rate on this GPU)
-                    const float *Vh = s_Vh + sl, *Vl = s_Vl + sl;
-                    for (; k + kNW < kcs; k += 2 * kNW) {
-                        df_fma_acc(h0, l0, s_yh[k], s_yl[k], Vh[(size_t)k * ppb], Vl[(size_t)k * ppb]);
-                        df_fma_acc(h1, l1, s_yh[k + kNW], s_yl[k + kNW], Vh[(size_t)(k + kNW) * ppb],
-                                   Vl[(size_t)(k + kNW) * ppb]);
+        // rounds of up to kRound groups: every warp computes its slice of the
+        // dot (columns k = warp mod 8) for each group of the round, then warp
+        // g of the block finishes group g; the per-point arithmetic does not
+        // depend on the number of groups
+        for (int g0 = 0; g0 < n_grp; g0 += kRound) {
+            const int ng = min(kRound, n_grp - g0);
+            for (int gg = 0; gg < ng; ++gg) {
+                const int g = g0 + gg;
+                const int sl = g * 32 + lane;
+                const int64_t i = point_of(sl);
+                const bool valid = i < a.n_s;
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+                if (valid) {
+                    int k = warp;
+                    if (MODE) {
+                        // double-float on the FP32 pipe (FP64 issues at a small
+                        // fraction of the FP32 rate on this GPU)
+                        const float *Vh = s_Vh + sl, *Vl = s_Vl + sl;
+                        for (; k + kNW < kcs; k += 2 * kNW) {
+                            const float2 y0 = s_y2[k], y1 = s_y2[k + kNW];
+                            df_fma_acc(h0, l0, y0.x, y0.y, Vh[(size_t)k * ppb], Vl[(size_t)k * ppb]);
+                            df_fma_acc(h1, l1, y1.x, y1.y, Vh[(size_t)(k + kNW) * ppb], Vl[(size_t)(k + kNW) * ppb]);
+                        }
+                        for (; k < kcs; k += kNW) {
+                            const float2 y0 = s_y2[k];
+                            df_fma_acc(h0, l0, y0.x, y0.y, Vh[(size_t)k * ppb], Vl[(size_t)k * ppb]);
+                        }
+                        // columns beyond the shared slice: hi/lo pairs from global memory
+                        const float2 *Vi = reinterpret_cast<const float2 *>(a.V) + i;
+                        for (; k + kNW < j; k += 2 * kNW) {
+                            const float2 v0 = __ldcg(Vi + (size_t)k * a.n_s), v1 = __ldcg(Vi + (size_t)(k + kNW) * a.n_s);
+                            const float2 y0 = s_y2[k], y1 = s_y2[k + kNW];
+                            df_fma_acc(h0, l0, y0.x, y0.y, v0.x, v0.y);
+                            df_fma_acc(h1, l1, y1.x, y1.y, v1.x, v1.y);
+                        }
+                        for (; k < j; k += kNW) {
+                            const float2 v = __ldcg(Vi + (size_t)k * a.n_s), y0 = s_y2[k];
+                            df_fma_acc(h0, l0, y0.x, y0.y, v.x, v.y);
+                        }
+                    } else {
+                        const double *Vs = s_V + sl;
+                        for (; k + 3 * kNW < kcs; k += 4 * kNW) {
+                            s0 = fma(s_y[k], Vs[(size_t)k * ppb], s0);
+                            s1 = fma(s_y[k + kNW], Vs[(size_t)(k + kNW) * ppb], s1);
+                            s2 = fma(s_y[k + 2 * kNW], Vs[(size_t)(k + 2 * kNW) * ppb], s2);
+                            s3 = fma(s_y[k + 3 * kNW], Vs[(size_t)(k + 3 * kNW) * ppb], s3);
+                        }
+                        for (; k < kcs; k += kNW) s0 = fma(s_y[k], Vs[(size_t)k * ppb], s0);
+                        const double *Vi = a.V + i;
+                        const size_t ld = (size_t)a.n_s;
+                        for (; k + 3 * kNW < j; k += 4 * kNW) {
+                            const double v0 = __ldcg(Vi + (size_t)k * ld), v1 = __ldcg(Vi + (size_t)(k + kNW) * ld),
+                                         v2 = __ldcg(Vi + (size_t)(k + 2 * kNW) * ld),
+                                         v3 = __ldcg(Vi + (size_t)(k + 3 * kNW) * ld);
+                            s0 = fma(s_y[k], v0, s0);
+                            s1 = fma(s_y[k + kNW], v1, s1);
+                            s2 = fma(s_y[k + 2 * kNW], v2, s2);
+                            s3 = fma(s_y[k + 3 * kNW], v3, s3);
+                        }
+                        for (; k < j; k += kNW) s0 = fma(s_y[k], __ldcg(Vi + (size_t)k * ld), s0);
                     }
-                    for (; k < kcs; k += kNW)
-                        df_fma_acc(h0, l0, s_yh[k], s_yl[k], Vh[(size_t)k * ppb], Vl[(size_t)k * ppb]);
-                    // columns beyond the shared slice: hi/lo pairs from global memory
-                    const float2 *Vi = reinterpret_cast<const float2 *>(a.V) + i;
-                    for (; k + kNW < j; k += 2 * kNW) {
-                        const float2 v0 = __ldcg(Vi + (size_t)k * a.n_s), v1 = __ldcg(Vi + (size_t)(k + kNW) * a.n_s);
-                        df_fma_acc(h0, l0, s_yh[k], s_yl[k], v0.x, v0.y);
-                        df_fma_acc(h1, l1, s_yh[k + kNW], s_yl[k + kNW], v1.x, v1.y);
-                    }
-                    for (; k < j; k += kNW) {
-                        const float2 v = __ldcg(Vi + (size_t)k * a.n_s);
-                        df_fma_acc(h0, l0, s_yh[k], s_yl[k], v.x, v.y);
-                    }
-                } else {
-                    const double *Vs = s_V + sl;
-                    for (; k + 3 * kNW < kcs; k += 4 * kNW) {
-                        s0 = fma(s_y[k], Vs[(size_t)k * ppb], s0);
-                        s1 = fma(s_y[k + kNW], Vs[(size_t)(k + kNW) * ppb], s1);
-                        s2 = fma(s_y[k + 2 * kNW], Vs[(size_t)(k + 2 * kNW) * ppb], s2);
-                        s3 = fma(s_y[k + 3 * kNW], Vs[(size_t)(k + 3 * kNW) * ppb], s3);
-                    }
-                    for (; k < kcs; k += kNW) s0 = fma(s_y[k], Vs[(size_t)k * ppb], s0);
-                    const double *Vi = a.V + i;
-                    const size_t ld = (size_t)a.n_s;
-                    for (; k + 3 * kNW < j; k += 4 * kNW) {
-                        const double v0 = __ldcg(Vi + (size_t)k * ld), v1 = __ldcg(Vi + (size_t)(k + kNW) * ld),
-                                     v2 = __ldcg(Vi + (size_t)(k + 2 * kNW) * ld),
-                                     v3 = __ldcg(Vi + (size_t)(k + 3 * kNW) * ld);
-                        s0 = fma(s_y[k], v0, s0);
-                        s1 = fma(s_y[k + kNW], v1, s1);
-                        s2 = fma(s_y[k + 2 * kNW], v2, s2);
-                        s3 = fma(s_y[k + 3 * kNW], v3, s3);
-                    }
-                    for (; k < j; k += kNW) s0 = fma(s_y[k], __ldcg(Vi + (size_t)k * ld), s0);
                 }
-            }
-            if (MODE) {
-                const df t = df_add({h0, l0}, {h1, l1});
-                s_parth[warp * 32 + lane] = t.hi;
-                s_partl[warp * 32 + lane] = t.lo;
-            } else {
-                s_part[warp][lane] = (s0 + s1) + (s2 + s3);
+                if (MODE) {
+                    const df t = df_add({h0, l0}, {h1, l1});
+                    float *ph = reinterpret_cast<float *>(&s_part[gg][0][0]);
+                    ph[warp * 32 + lane] = t.hi;
+                    ph[kNW * 32 + warp * 32 + lane] = t.lo;
+                } else {
+                    s_part[gg][warp][lane] = (s0 + s1) + (s2 + s3);
+                }
             }
             __syncthreads();
-            if (warp == 0 && valid) {
-                unsigned long long key;
-                if (MODE) {
-                    df sum = {s_parth[lane], s_partl[lane]};
+            if (warp < ng) {
+                const int g = g0 + warp;
+                const int sl = g * 32 + lane;
+                const int64_t i = point_of(sl);
+                if (i < a.n_s) {
+                    unsigned long long key;
+                    if (MODE) {
+                        const float *ph = reinterpret_cast<const float *>(&s_part[warp][0][0]);
+                        const float *pl = ph + kNW * 32;
+                        df sum = {ph[lane], pl[lane]};
 #pragma unroll
-                    for (int w8 = 1; w8 < kNW; ++w8) sum = df_add(sum, {s_parth[w8 * 32 + lane], s_partl[w8 * 32 + lane]});
-                    df r2 = {0.f, 0.f};
+                        for (int w8 = 1; w8 < kNW; ++w8) sum = df_add(sum, {ph[w8 * 32 + lane], pl[w8 * 32 + lane]});
+                        df r2 = {0.f, 0.f};
 #pragma unroll
-                    for (int c = 0; c < DIM; ++c) {
-                        const df d = df_add({s_Xh[c * ppb + sl], s_Xl[c * ppb + sl]}, df_neg(xcd[c]));
-                        r2 = df_add(r2, df_sqr(d));
-                    }
-                    const df f = phi_df<BASIS>(df_mul(df_sqrt(r2), invRd));
-                    nz += (f.hi != 0.f);
-                    const df v = df_mul(df_add(f, df_neg(sum)), ild);
-                    if (j < a.cs) {
-                        s_Vh[(size_t)j * ppb + sl] = v.hi;
-                        s_Vl[(size_t)j * ppb + sl] = v.lo;
+                        for (int c = 0; c < DIM; ++c) {
+                            const df d = df_add({s_Xh[c * ppb + sl], s_Xl[c * ppb + sl]}, df_neg(xcd[c]));
+                            r2 = df_add(r2, df_sqr(d));
+                        }
+                        const df f = phi_df<BASIS>(df_mul(df_sqrt(r2), invRd));
+                        nz += (f.hi != 0.f);
+                        const df v = df_mul(df_add(f, df_neg(sum)), ild);
+                        if (j < a.cs) {
+                            s_Vh[(size_t)j * ppb + sl] = v.hi;
+                            s_Vl[(size_t)j * ppb + sl] = v.lo;
+                        } else {
+                            reinterpret_cast<float2 *>(a.V)[(size_t)j * a.n_s + i] = make_float2(v.hi, v.lo);
+                        }
+                        df k2 = {0.f, 0.f};
+#pragma unroll
+                        for (int c = 0; c < DIM; ++c) {
+                            df e = {s_Eh[c * ppb + sl], s_El[c * ppb + sl]};
+                            e = df_add(e, df_neg(df_mul(wd[c], v)));
+                            s_Eh[c * ppb + sl] = e.hi;
+                            s_El[c * ppb + sl] = e.lo;
+                            k2 = df_add(k2, df_sqr(e));
+                        }
+                        const df s2n = df_add({s_S2h[sl], s_S2l[sl]}, df_sqr(v));
+                        s_S2h[sl] = s2n.hi;
+                        s_S2l[sl] = s2n.lo;
+                        key = key_of_df(k2);
                     } else {
-                        reinterpret_cast<float2 *>(a.V)[(size_t)j * a.n_s + i] = make_float2(v.hi, v.lo);
-                    }
-                    df k2 = {0.f, 0.f};
+                        double sum = s_part[warp][0][lane];
 #pragma unroll
-                    for (int c = 0; c < DIM; ++c) {
-                        df e = {s_Eh[c * ppb + sl], s_El[c * ppb + sl]};
-                        e = df_add(e, df_neg(df_mul(wd[c], v)));
-                        s_Eh[c * ppb + sl] = e.hi;
-                        s_El[c * ppb + sl] = e.lo;
-                        k2 = df_add(k2, df_sqr(e));
+                        for (int w8 = 1; w8 < kNW; ++w8) sum += s_part[warp][w8][lane];
+                        const double f = phi_f64<BASIS>(
+                            dist_f64<DIM>(s_X[sl], s_X[ppb + sl], s_X[2 * ppb + sl], xcj.x, xcj.y, xcj.z) * a.invR);
+                        nz += (f != 0.0);
+                        const double v = (f - sum) * ilj;
+                        if (j < a.cs) s_V[(size_t)j * ppb + sl] = v;
+                        else a.V[(size_t)j * a.n_s + i] = v;
+                        const double e0 = fma(-wj.x, v, s_E[sl]);
+                        const double e1 = fma(-wj.y, v, s_E[ppb + sl]);
+                        const double e2 = DIM == 3 ? fma(-wj.z, v, s_E[2 * ppb + sl]) : 0.0;
+                        s_E[sl] = e0;
+                        s_E[ppb + sl] = e1;
+                        s_E[2 * ppb + sl] = e2;
+                        s_S2[sl] = fma(v, v, s_S2[sl]);
+                        double k2 = __dmul_rn(e0, e0);
+                        k2 = __dadd_rn(k2, __dmul_rn(e1, e1));
+                        if (DIM == 3) k2 = __dadd_rn(k2, __dmul_rn(e2, e2));
+                        key = key_of_double(k2);
                     }
-                    const df s2n = df_add({s_S2h[sl], s_S2l[sl]}, df_sqr(v));
-                    s_S2h[sl] = s2n.hi;
-                    s_S2l[sl] = s2n.lo;
-                    key = key_of_df(k2);
-                } else {
-                    double sum = s_part[0][lane];
-#pragma unroll
-                    for (int w8 = 1; w8 < kNW; ++w8) sum += s_part[w8][lane];
-                    const double f = phi_f64<BASIS>(
-                        dist_f64<DIM>(s_X[sl], s_X[ppb + sl], s_X[2 * ppb + sl], xcj.x, xcj.y, xcj.z) * a.invR);
-                    nz += (f != 0.0);
-                    const double v = (f - sum) * ilj;
-                    if (j < a.cs) s_V[(size_t)j * ppb + sl] = v;
-                    else a.V[(size_t)j * a.n_s + i] = v;
-                    const double e0 = fma(-wj.x, v, s_E[sl]);
-                    const double e1 = fma(-wj.y, v, s_E[ppb + sl]);
-                    const double e2 = DIM == 3 ? fma(-wj.z, v, s_E[2 * ppb + sl]) : 0.0;
-                    s_E[sl] = e0;
-                    s_E[ppb + sl] = e1;
-                    s_E[2 * ppb + sl] = e2;
-                    s_S2[sl] = fma(v, v, s_S2[sl]);
-                    double k2 = __dmul_rn(e0, e0);
-                    k2 = __dadd_rn(k2, __dmul_rn(e1, e1));
-                    if (DIM == 3) k2 = __dadd_rn(k2, __dmul_rn(e2, e2));
-                    key = key_of_double(k2);
-                }
-                if (!s_sel[sl]) {
-                    const int o = s_orig[sl];
-                    if (better_key(key, o, bkey, bidx)) {
-                        bkey = key;
-                        bidx = o;
-                        bslot = sl;
+                    if (!s_sel[sl]) {
+                        const int o = s_orig[sl];
+                        if (better_key(key, o, bkey, bidx)) {
+                            bkey = key;
+                            bidx = o;
+                            bslot = sl;
+                        }
                     }
                 }
             }
@@ -459,10 +506,27 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
 
         // ---- lists (control 0: listed at level start), nonzero count, the block's record
         if (j > 0 && own_list) {
-            const double dx = fmax(fmax(own_lo.x - xcj.x, xcj.x - own_hi.x), 0.0);
-            const double dy = fmax(fmax(own_lo.y - xcj.y, xcj.y - own_hi.y), 0.0);
-            const double dz = DIM == 3 ? fmax(fmax(own_lo.z - xcj.z, xcj.z - own_hi.z), 0.0) : 0.0;
-            if (dx * dx + dy * dy + dz * dz < a.R2 * (1.0 + 1e-9)) {
+            // c_j rounded to FP32 (u = 2^-24 relative); with the box rounded
+            // outward each gap exceeds the exact one by at most u |c| (1 + u)
+            // and the sum of squares carries (1 + u)^5, which the radius
+            // (R (1 + 1e-9) + 2.5 u max|c|)^2 (1 + 2^-21), rounded up, covers
+            float xf, yf, zf;
+            if (MODE) {
+                xf = xcd[0].hi;
+                yf = xcd[1].hi;
+                zf = xcd[2].hi;
+            } else {
+                xf = __double2float_rn(xcj.x);
+                yf = __double2float_rn(xcj.y);
+                zf = __double2float_rn(xcj.z);
+            }
+            const float mx = fmaxf(fmaxf(fabsf(xf), fabsf(yf)), DIM == 3 ? fabsf(zf) : 0.f);
+            const float rr = __fadd_ru(a.Rlist, __fmul_ru(mx, 1.4901161193847656e-7f));
+            const float r2 = __fmul_ru(__fmul_ru(rr, rr), 1.0f + 4.76837158203125e-7f);
+            const float dx = fmaxf(fmaxf(own_lo.x - xf, xf - own_hi.x), 0.f);
+            const float dy = fmaxf(fmaxf(own_lo.y - yf, yf - own_hi.y), 0.f);
+            const float dz = DIM == 3 ? fmaxf(fmaxf(own_lo.z - zf, zf - own_hi.z), 0.f) : 0.f;
+            if (dx * dx + dy * dy + dz * dz < r2) {
                 a.nb_list[(size_t)t_own * a.cap + own_cnt] = (uint32_t)j;
                 ++own_cnt;
                 a.nb_cnt[t_own] = own_cnt;
@@ -492,9 +556,10 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
                 nz_cum += bnz;
                 pairs_useful += nz_cum;  // the list sweep of this step would evaluate these pairs
                 double4 *r = a.rec + 3 * ((size_t)(j & 1) * P + blockIdx.x);
+                ulonglong2 *ri = reinterpret_cast<ulonglong2 *>(r);
                 if (ws >= 0) {
-                    r[0] = make_double4(__longlong_as_double((long long)kk), (double)ii, (double)list_max,
-                                        (double)point_of(ws));
+                    ri[0] = make_ulonglong2(kk, (unsigned long long)(long long)ii);
+                    ri[1] = make_ulonglong2((unsigned long long)list_max, (unsigned long long)point_of(ws));
                     if (MODE) {
                         float4 *rf = reinterpret_cast<float4 *>(r + 1);
                         const df l2 = df_add({1.0f, 0.0f}, df_neg({s_S2h[ws], s_S2l[ws]}));
@@ -507,7 +572,8 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
                         r[2] = make_double4(s_E[ws], s_E[ppb + ws], s_E[2 * ppb + ws], 0.0);
                     }
                 } else {
-                    r[0] = make_double4(__longlong_as_double(0ll), -1.0, (double)list_max, -1.0);
+                    ri[0] = make_ulonglong2(0ull, ~0ull);  // key 0, index -1
+                    ri[1] = make_ulonglong2((unsigned long long)list_max, ~0ull);
                 }
             }
             if (ws >= 0) {  // the candidate's column: y of the next control if it wins
@@ -535,12 +601,15 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
 
         // ---- (b) row j of the inverse factor on this block's rows, alpha (FP64)
         {
-            double ilj64 = ilj;
-            double4 wj64 = wj;
-            if (MODE) {
-                ilj64 = df_to_double(ild);
-                wj64 = make_double4(df_to_double(wd[0]), df_to_double(wd[1]), df_to_double(wd[2]), 0.0);
+            if (MODE) {  // y to FP64 once per block, in place (each pair becomes its double)
+                for (int m = tid; m < j; m += kNT) {
+                    const float2 v = s_y2[m];
+                    s_y[m] = (double)v.x + (double)v.y;
+                }
+                __syncthreads();
             }
+            const double ilj64 = s_dec[3];
+            const double4 wj64 = make_double4(s_dec[4], s_dec[5], s_dec[6], 0.0);
             for (int k = k_first; k <= j; k += (int)P * kNW) {
                 if (k == j) {  // the diagonal and alpha_j
                     if (lane == 0) {
@@ -552,14 +621,38 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
                 }
                 const double *trow = a.Gt + (size_t)k * a.cap;
                 double4 al = make_double4(0, 0, 0, 0);
-                if (lane == 0) al = ldcg_d4(&a.alpha[k]);
+                // t0 sums the entries m = k + lane + 64 i, t1 those 32 further on,
+                // in chunks of 32 kRowChunk entries whose loads are issued together
                 double t0 = 0.0, t1 = 0.0;
-                for (int m = k + lane; m < j; m += 64) {
-                    const double y0 = MODE ? (double)s_yh[m] + (double)s_yl[m] : s_y[m];
-                    t0 = fma(__ldcg(trow + m), y0, t0);
-                    if (m + 32 < j) {
-                        const double y1 = MODE ? (double)s_yh[m + 32] + (double)s_yl[m + 32] : s_y[m + 32];
-                        t1 = fma(__ldcg(trow + m + 32), y1, t1);
+                int m0 = k + lane;
+                if (k == k_first) {  // (loaded at the start of the pass)
+                    al = apre;
+#pragma unroll
+                    for (int q = 0; q < kRowChunk; ++q) {
+                        const int m = m0 + 32 * q;
+                        if (m < j) {
+                            if (q & 1) t1 = fma(gpre[q], s_y[m], t1);
+                            else t0 = fma(gpre[q], s_y[m], t0);
+                        }
+                    }
+                    m0 += 32 * kRowChunk;
+                } else if (lane == 0) {
+                    al = ldcg_d4(&a.alpha[k]);
+                }
+                for (; m0 < j; m0 += 32 * kRowChunk) {
+                    double g[kRowChunk];
+#pragma unroll
+                    for (int q = 0; q < kRowChunk; ++q) {
+                        const int m = m0 + 32 * q;
+                        g[q] = m < j ? __ldcg(trow + m) : 0.0;
+                    }
+#pragma unroll
+                    for (int q = 0; q < kRowChunk; ++q) {
+                        const int m = m0 + 32 * q;
+                        if (m < j) {
+                            if (q & 1) t1 = fma(g[q], s_y[m], t1);
+                            else t0 = fma(g[q], s_y[m], t0);
+                        }
                     }
                 }
                 const double t = warp_sum_d(t0 + t1);
@@ -585,12 +678,15 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
         double4 r0 = make_double4(0, 0, 0, 0), r1 = r0, r2 = r0;
         const double4 *rj = a.rec + 3 * (size_t)(j & 1) * P;
         for (unsigned b = tid; b < P; b += kNT) {
-            const double4 q0 = ldcg_d4(&rj[3 * (size_t)b]);
+            const ulonglong2 *qi = reinterpret_cast<const ulonglong2 *>(&rj[3 * (size_t)b]);
+            const ulonglong2 i0 = __ldcg(qi), i1 = __ldcg(qi + 1);
+            const double4 q0 = make_double4(__longlong_as_double((long long)i0.x), __longlong_as_double((long long)i0.y),
+                                            __longlong_as_double((long long)i1.x), __longlong_as_double((long long)i1.y));
             const double4 q1 = ldcg_d4(&rj[3 * (size_t)b + 1]);
             const double4 q2 = ldcg_d4(&rj[3 * (size_t)b + 2]);
-            lmax = max(lmax, (unsigned)q0.z);
-            const int ib = (int)q0.y;
-            const unsigned long long kb = (unsigned long long)__double_as_longlong(q0.x);
+            lmax = max(lmax, (unsigned)i1.x);
+            const int ib = (int)(long long)i0.y;
+            const unsigned long long kb = i0.x;
             if (better_key(kb, ib, K, I)) {
                 K = kb;
                 I = ib;
@@ -623,14 +719,10 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
             // e = sqrt(K) / S0 < tau, the same rounded test as the other
             // engines; the square root and the division only near the threshold
             bool below;
-            if (I < 0) {
-                below = true;
-            } else {
-                const double Kd = key_value<MODE>(K);
-                if (Kd < a.K_lo) below = true;
-                else if (Kd > a.K_hi) below = false;
-                else below = __ddiv_rn(__dsqrt_rn(Kd), a.S0) < a.tau;
-            }
+            if (I < 0) below = true;
+            else if (K < a.key_lo) below = true;
+            else if (K >= a.key_hi) below = false;
+            else below = __ddiv_rn(__dsqrt_rn(key_value<MODE>(K)), a.S0) < a.tau;
             const bool stop = I < 0 || below || nn >= a.cap;
             // hand over to the list sweep when V is full, or when the Newton
             // update (n_s * n multiply-adds) is large and the lists are much
@@ -639,30 +731,49 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
                                                        (double)nn > a.switch_ratio * (double)mc));
             bool singular = false;
             if (!stop && !hand) {
+                // 1 / l_j, and w_j = E(c_j) / l_j in FP64 for (b): lanes 0-2
+                // take w_j's components, lane 3 takes 1 / l_j
                 if (MODE) {
                     const float4 *rf = reinterpret_cast<const float4 *>(&s_wrec[1]);
                     const df l2 = {rf[1].z, rf[1].w};
                     singular = !(l2.hi > (float)(a.piv_tol_per_n * (nn + 1)));
-                    if (!singular && lane == 0) {
+                    if (!singular) {
                         const df il = df_rsqrt(l2);
-                        s_dec[2] = __longlong_as_double((long long)(((unsigned long long)__float_as_uint(il.hi) << 32) |
-                                                                    __float_as_uint(il.lo)));
+                        const float *ef = reinterpret_cast<const float *>(&s_wrec[2]);
+                        const df q = lane < 3 ? df_mul({ef[2 * lane], ef[2 * lane + 1]}, il) : il;
+                        if (lane < 4) s_dec[lane < 3 ? 4 + lane : 3] = (double)q.hi + (double)q.lo;
+                        if (lane == 0)
+                            s_dec[2] = __longlong_as_double(
+                                (long long)(((unsigned long long)__float_as_uint(il.hi) << 32) | __float_as_uint(il.lo)));
                     }
                 } else {
                     const double l2 = s_wrec[1].w;
                     singular = !(l2 > a.piv_tol_per_n * (nn + 1));
-                    if (!singular && lane == 0) {
+                    if (!singular) {
                         // 1 / sqrt(l2): FP32 estimate and two Newton steps in FP64
                         double il = (double)rsqrtf((float)l2);
                         il = il * fma(-0.5 * l2 * il, il, 1.5);
                         il = il * fma(-0.5 * l2 * il, il, 1.5);
-                        s_dec[2] = il;
+                        const double *er = reinterpret_cast<const double *>(&s_wrec[2]);
+                        if (lane < 3) s_dec[4 + lane] = er[lane] * il;
+                        if (lane == 3) s_dec[3] = il;
                     }
                 }
             }
             if (lane == 0) {
                 s_flags = (stop ? 1 : 0) | (hand ? 2 : 0) | (singular ? 4 : 0);
-                s_dec[1] = (double)mc;
+                s_mc = mc;
+            }
+        } else if (I >= 0) {
+            // meanwhile the other warps load the winner's column, y of the
+            // next pass (written before this step's barrier, parity j & 1;
+            // unused if the level stops here)
+            const double *yb = a.ycol + ((size_t)(j & 1) * P + s_win) * ycl;
+            if (MODE) {
+                const float2 *yf = reinterpret_cast<const float2 *>(yb);
+                for (int k = tid - 32; k < nn; k += kNT - 32) s_y2[k] = __ldcg(&yf[k]);
+            } else {
+                for (int k = tid - 32; k < nn; k += kNT - 32) s_y[k] = __ldcg(&yb[k]);
             }
         }
         __syncthreads();
@@ -696,7 +807,7 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
                     a.st->best_orig = I;
                     a.st->best_key = I >= 0 ? key_value<MODE>(K) : -1.0;
                     a.st->emax = e;
-                    a.st->max_cnt = (int)s_dec[1];
+                    a.st->max_cnt = s_mc;
                     a.st->n = nn;
                     if (singular) a.st->status = RBFD_ESINGULAR;
                     else if (stop && !(I < 0 || e < a.tau)) a.st->status = RBFD_ENOTCONV;
@@ -707,8 +818,7 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
             RBFD_TMARK(7)
             RBFD_NEXIT()
         }
-        B = s_win;
-        cj = (uint32_t)s_wrec[0].w;
+        cj = (uint32_t)reinterpret_cast<const ulonglong2 *>(&s_wrec[0])[1].y;
         if (MODE) {
             const float4 *rf = reinterpret_cast<const float4 *>(&s_wrec[1]);
             xcd[0] = {rf[0].x, rf[0].y};
@@ -720,9 +830,6 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
             wd[0] = df_mul({ef[0].x, ef[0].y}, ild);
             wd[1] = df_mul({ef[0].z, ef[0].w}, ild);
             wd[2] = df_mul({ef[1].x, ef[1].y}, ild);
-            // FP64 coordinates of c_j for the list test: exact from the split
-            xcj = make_double4((double)xcd[0].hi + (double)xcd[0].lo, (double)xcd[1].hi + (double)xcd[1].lo,
-                               (double)xcd[2].hi + (double)xcd[2].lo, 0.0);
             if (writer) {
                 a.sel[cj] = 1;
                 a.cid[nn] = cj;
@@ -730,10 +837,10 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
                 a.wdf[2 * nn + 1] = make_float4(wd[2].hi, wd[2].lo, 0.f, 0.f);
             }
         } else {
-            ilj = s_dec[2];
-            const double4 wr1 = s_wrec[1], wr2 = s_wrec[2];
+            ilj = s_dec[3];
+            const double4 wr1 = s_wrec[1];
             xcj = make_double4(wr1.x, wr1.y, wr1.z, 0.0);
-            wj = make_double4(wr2.x * ilj, wr2.y * ilj, wr2.z * ilj, 0.0);
+            wj = make_double4(s_dec[4], s_dec[5], s_dec[6], 0.0);
             if (writer) {
                 const float hx = __double2float_rn(xcj.x), hy = __double2float_rn(xcj.y),
                             hz = __double2float_rn(xcj.z);
@@ -749,7 +856,6 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
         }
         ++n;
         RBFD_TMARK(7)
-        __syncthreads();  // shared scratch is reused
     }
     RBFD_NEXIT()
 #undef RBFD_NEXIT
@@ -772,6 +878,37 @@ const void *select_newton(int dim, int basis, int mode) {
 }
 
 }  // namespace
+
+// The argmax keys that bracket the stop threshold (the keys order the
+// values of |E|^2).  FP64 keys are the bit pattern plus one: key < bits(K_lo)
+// + 1 is exactly value < K_lo, key >= bits(K_hi) + 2 exactly value > K_hi.
+// Mixed-mode keys put the high float's bits above the low float's: with
+// h the largest float <= K_lo, a key below (bits(h) << 32) has hi < h and so
+// a value below h <= K_lo; with h' the smallest float >= K_hi, a key from
+// (bits(next(next(h'))) << 32) on has a value above next(h') - ulp / 2 >= h'.
+unsigned long long stop_key(double K, bool mixed, bool upper) {
+    if (!mixed) {
+        unsigned long long b;
+        std::memcpy(&b, &K, sizeof(b));
+        return b + (upper ? 2ull : 1ull);
+    }
+    if (!upper) {
+        if (!(K > 0.0)) return 0ull;
+        float h = K >= (double)FLT_MAX ? FLT_MAX : (float)K;
+        if ((double)h > K) h = std::nextafter(h, 0.0f);
+        unsigned u;
+        std::memcpy(&u, &h, sizeof(u));
+        return (unsigned long long)u << 32;
+    }
+    if (!(K < (double)FLT_MAX)) return ~0ull;
+    float h = K > 0.0 ? (float)K : 0.0f;
+    if ((double)h < K) h = std::nextafter(h, HUGE_VALF);
+    h = std::nextafter(std::nextafter(h, HUGE_VALF), HUGE_VALF);
+    if (std::isinf(h)) return ~0ull;
+    unsigned u;
+    std::memcpy(&u, &h, sizeof(u));
+    return (unsigned long long)u << 32;
+}
 
 int newton_columns(rbfd_mesh *m) {
     // V holds n_s doubles per column; at most kNewtonCols columns, at most
@@ -804,7 +941,7 @@ NewtonShape newton_shape(rbfd_mesh *m, int want_ctas) {
     const void *k = select_newton(m->dim, m->opt.basis, mode);
     static const size_t kSmemMax = 220 * 1024;   // dynamic shared memory per block (of 227 KB)
     static const size_t kSmemPerSM = 228 * 1024;  // shared memory of one SM
-    static const size_t kPerBlockReserve = 4 * 1024;  // static shared memory and the system's share
+    static const size_t kPerBlockReserve = 6 * 1024;  // static shared memory and the system's share
     NewtonShape s;
     int sms = 0;
     RBFD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
@@ -886,8 +1023,16 @@ void newton_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
     a.R2 = R * R;
     a.S0 = m->S0;
     a.tau = tau;
-    a.K_lo = (tau * m->S0) * (tau * m->S0) * (1.0 - 1e-12);
-    a.K_hi = (tau * m->S0) * (tau * m->S0) * (1.0 + 1e-12);
+    {
+        float rl = (float)(R * (1.0 + 1e-9));
+        if ((double)rl < R * (1.0 + 1e-9)) rl = std::nextafter(rl, HUGE_VALF);
+        a.Rlist = rl;
+        const bool mixed = m->opt.precision != RBFD_FP64;
+        const double K_lo = (tau * m->S0) * (tau * m->S0) * (1.0 - 1e-12);
+        const double K_hi = (tau * m->S0) * (tau * m->S0) * (1.0 + 1e-12);
+        a.key_lo = stop_key(K_lo, mixed, false);
+        a.key_hi = stop_key(K_hi, mixed, true);
+    }
     a.piv_tol_per_n = 8.0 * 1.1102230246251565e-16;
     a.switch_ratio = 3.0;
     a.switch_work = 2e7;  // ~30 us of FP64 multiply-adds per step

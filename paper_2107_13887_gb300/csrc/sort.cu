@@ -184,26 +184,17 @@ __device__ __forceinline__ uint32_t morton(double x, double y, double z, int dim
            spread3(quant(x, lo.x, inv.x, 0x3ffu));
 }
 
-__global__ void k_morton_f64(const double4 *__restrict__ p, size_t n, int dim, double3 lo, double3 inv,
-                             uint32_t *keys, uint32_t *vals) {
-    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double4 q = p[i];
-    keys[i] = morton(q.x, q.y, q.z, dim, lo, inv);
-    vals[i] = (uint32_t)i;
-}
-
-// The same with the box read from device memory (lo xyz, hi xyz), so that no
-// host round trip separates the box reduction from the keys.
+// Morton keys with the box read from device memory (lo xyz, hi xyz), so that
+// no host round trip separates the box reduction from the keys.
 __global__ void k_morton_f64_dev(const double4 *__restrict__ p, size_t n, int dim, const double *__restrict__ bb,
-                                 uint32_t *keys, uint32_t *vals) {
+                                 int shift, uint32_t *keys, uint32_t *vals) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     auto f = [](double a, double b) { return (b > a) ? 1.0 / (b - a) : 0.0; };
     const double3 lo = make_double3(bb[0], bb[1], bb[2]);
     const double3 inv = make_double3(f(bb[0], bb[3]), f(bb[1], bb[4]), f(bb[2], bb[5]));
     double4 q = p[i];
-    keys[i] = morton(q.x, q.y, q.z, dim, lo, inv);
+    keys[i] = morton(q.x, q.y, q.z, dim, lo, inv) >> shift;
     vals[i] = (uint32_t)i;
 }
 
@@ -294,17 +285,10 @@ void radix_sort_pairs(uint32_t *keys, uint32_t *vals, size_t n, int key_bits, So
     RBFD_CUDA(cudaGetLastError());
 }
 
-void morton_keys_f64(const double4 *xyz, size_t n, int dim, double3 lo, double3 hi, uint32_t *keys,
-                     uint32_t *vals, cudaStream_t st) {
-    if (!n) return;
-    k_morton_f64<<<grid1(n, 256), 256, 0, st>>>(xyz, n, dim, lo, inv_extent(lo, hi), keys, vals);
-    RBFD_CUDA(cudaGetLastError());
-}
-
 void morton_keys_f64_dev(const double4 *xyz, size_t n, int dim, const double *bbox, uint32_t *keys, uint32_t *vals,
-                         cudaStream_t st) {
+                         cudaStream_t st, int shift) {
     if (!n) return;
-    k_morton_f64_dev<<<grid1(n, 256), 256, 0, st>>>(xyz, n, dim, bbox, keys, vals);
+    k_morton_f64_dev<<<grid1(n, 256), 256, 0, st>>>(xyz, n, dim, bbox, shift, keys, vals);
     RBFD_CUDA(cudaGetLastError());
 }
 
