@@ -158,6 +158,11 @@ typedef struct rbfd_stats {
     double newton_ms;            /* event time of the Newton-basis launches (opt.profile = 1) */
     int64_t newton_launches;
     int64_t newton_terms;        /* basis values the Newton update read: n_s x controls, summed over steps */
+    /* host wall time of the last rbfd_greedy by part, in ms, summed over levels:
+       [0] level start, [1] greedy steps (launches and their waits),
+       [2] level close (refinement, confirm sweep), [3] level save (results to
+       the host, control grid) */
+    double greedy_host_ms[4];
 } rbfd_stats;
 
 int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st);

@@ -209,17 +209,10 @@ void mesh_free(rbfd_mesh *m) {
     cudaGetDevice(&prev);
     cudaSetDevice(m->device);
     if (m->stream) cudaStreamSynchronize(m->stream);
-    for (auto &L : m->levels) {
-        dfree(L.d_cx);
-        dfree(L.d_alpha);
-        dfree(L.d_cdf);
-        dfree(L.d_adf);
-        dfree(L.d_cell_start);
-        dfree(L.d_cell_ctrl);
-    }
+    for (auto &L : m->levels) rbfd::level_free(L);
     void *ptrs[] = {m->d_perm, m->d_inv, m->d_xs, m->d_dS, m->d_cur, m->d_E, m->d_pb_lo, m->d_pb_hi,
                     m->d_pb_org, m->d_xs_hi, m->d_xs_lo, m->d_sel, m->d_G, m->d_w, m->d_alpha, m->d_cx,
-                    m->d_cdf, m->d_cid, m->d_phi, m->d_y, m->d_red, m->d_gpart, m->d_vec, m->d_vec2, m->d_v4part,
+                    m->d_cdf, m->d_cid, m->d_phi, m->d_y, m->d_red, m->d_gpart, m->d_vec, m->d_vec2,
                     m->d_nb_cnt, m->d_nb_list, m->d_part, m->d_pb_done, m->d_pb_key, m->d_pb_idx, m->d_pairs,
                     m->d_st, m->d_vin, m->d_vpos, m->d_vorig, m->d_vflag, m->d_vscan, m->d_vlist, m->d_vkeys,
                     m->d_vacc, m->d_vio, m->d_misc, m->d_bbox, m->d_bar, m->d_pred, m->d_Gt,
@@ -420,7 +413,8 @@ int rbfd_get_level(rbfd_mesh *m, int l, int64_t *n_c, int64_t *idx, double *alph
         if (!m) rbfd::fail(RBFD_EINVAL, "rbfd_get_level: NULL mesh");
         if (!m->greedy_done) rbfd::fail(RBFD_ESTATE, "rbfd_get_level: run rbfd_greedy first");
         if (l < 0 || l >= (int)m->levels.size()) rbfd::fail(RBFD_EINVAL, "rbfd_get_level: level out of range");
-        const rbfd::Level &L = m->levels[l];
+        rbfd::Level &L = m->levels[l];
+        if (idx || alpha) rbfd::level_fetch(m, L);
         if (n_c) *n_c = L.nc;
         if (idx) std::memcpy(idx, L.idx.data(), sizeof(int64_t) * L.idx.size());
         if (alpha) std::memcpy(alpha, L.alpha.data(), sizeof(double) * L.alpha.size());

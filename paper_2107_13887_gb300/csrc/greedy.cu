@@ -23,6 +23,7 @@
 // sweep that stores E (the next level's target, dS_{l+1} = E), and the
 // per-level uniform cell grid of the controls for the volume update.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <cstdio>
@@ -585,7 +586,10 @@ __global__ void k_level_init(int first_orig_from_state, int first_orig, const ui
 // r_i = dS_l(c_i) - sum_j alpha_j phi(|r_ci - r_cj| / R), FP64, one warp per
 // control i; the sum runs over the controls listed for the point block that
 // holds c_i (every control within R of it is listed, so the omitted ones
-// contribute exactly 0).  Per-block max |r| to red[block].
+// contribute exactly 0).  Per-block max |r| to red[block]; the last block to
+// finish (a counter in cnt, reset by that block) tests the largest residual
+// against tol on the device: once it is at most tol, lvl[2] is set and the
+// rest of this level close does nothing; lvl[3] counts the corrections.
 template <int DIM, int BASIS>
 __global__ void __launch_bounds__(kThreads) k_resid(int n, double R, int cap, const double4 *__restrict__ cx,
                                                     const double4 *__restrict__ alpha,
@@ -593,9 +597,11 @@ __global__ void __launch_bounds__(kThreads) k_resid(int n, double R, int cap, co
                                                     const uint32_t *__restrict__ nb_cnt,
                                                     const uint32_t *__restrict__ nb_list,
                                                     const double4 *__restrict__ cur, double4 *__restrict__ r,
-                                                    double *__restrict__ red, const double *__restrict__ done) {
-    if (*done != 0.0) return;  // refinement already converged
+                                                    double *__restrict__ red, double tol, double *__restrict__ lvl,
+                                                    unsigned *__restrict__ cnt) {
+    if (lvl[2] != 0.0) return;  // refinement already converged
     __shared__ double sm[kThreads / 32];
+    __shared__ bool s_last;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i = blockIdx.x * (kThreads / 32) + w;
     double mx = 0.0;
@@ -630,30 +636,27 @@ __global__ void __launch_bounds__(kThreads) k_resid(int n, double R, int cap, co
         double v = sm[0];
         for (int q = 1; q < kThreads / 32; ++q) v = fmax(v, sm[q]);
         red[blockIdx.x] = v;
+        __threadfence();
+        s_last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double v = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) v = fmax(v, __ldcg(&red[b]));
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) sm[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < kThreads / 32; ++q) v = fmax(v, sm[q]);
+        if (v <= tol) lvl[2] = 1.0;
+        else lvl[3] += 1.0;
+        *cnt = 0;
     }
 }
 
 // z_j = sum_{k <= j} G_jk r_k (3 right-hand sides), one warp per row.
-// Convergence test of the iterative refinement on the device (no host round
-// trip): once the largest residual of a sweep is at most tol, lvl[2] is set
-// and the remaining sweeps of this level close do nothing; lvl[3] counts the
-// corrections applied.
-__global__ void k_ir_check(const double *__restrict__ rmax, int nb, double tol, double *__restrict__ lvl) {
-    __shared__ double sm[32];
-    if (lvl[2] != 0.0) return;
-    double r = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) r = fmax(r, rmax[b]);
-    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = r;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, sm[w]);
-        r = fmax(r, sm[0]);
-        if (r <= tol) lvl[2] = 1.0;
-        else lvl[3] += 1.0;
-    }
-}
-
 __global__ void k_lower_mv3(int n, int cap, const double *__restrict__ G, const double4 *__restrict__ r,
                             double4 *__restrict__ z, const double *__restrict__ done) {
     if (*done != 0.0) return;
@@ -675,39 +678,30 @@ __global__ void k_lower_mv3(int n, int cap, const double *__restrict__ G, const 
     if (lane == 0) z[j] = make_double4(s0, s1, s2, 0.0);
 }
 
-// Partial column sums of z^T G for 3 right-hand sides: part[jt][k].
-__global__ void k_colsum3(int n, int cap, const double *__restrict__ G, const double4 *__restrict__ z,
-                          double4 *__restrict__ part, const double *__restrict__ done) {
+// alpha_k += sum_{j >= k} G_jk z_j (3 right-hand sides), one warp per k over
+// row k of the transposed copy G^T (contiguous).
+__global__ void k_upper_mv3_add(int n, int cap, const double *__restrict__ Gt, const double4 *__restrict__ z,
+                                double4 *__restrict__ alpha, const double *__restrict__ done) {
     if (*done != 0.0) return;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int jt = blockIdx.y;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = blockIdx.x * (blockDim.x >> 5) + w;
     if (k >= n) return;
-    int j0 = max(jt * kJT, k), j1 = min(n, (jt + 1) * kJT);
+    const double *row = Gt + (size_t)k * cap;
     double s0 = 0, s1 = 0, s2 = 0;
-    for (int j = j0; j < j1; ++j) {
-        double g = G[(size_t)j * cap + k];
-        double4 v = z[j];
+    for (int j = k + lane; j < n; j += 32) {
+        const double g = row[j];
+        const double4 v = z[j];
         s0 = fma(g, v.x, s0);
         s1 = fma(g, v.y, s1);
         s2 = fma(g, v.z, s2);
     }
-    part[(size_t)jt * cap + k] = make_double4(s0, s1, s2, 0.0);
-}
-
-__global__ void k_apply_correction(int n, int cap, int n_jt, const double4 *__restrict__ part,
-                                   double4 *__restrict__ alpha, const double *__restrict__ done) {
-    if (*done != 0.0) return;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    double s0 = 0, s1 = 0, s2 = 0;
-    for (int jt = 0; jt < n_jt; ++jt) {
-        double4 v = part[(size_t)jt * cap + k];
-        s0 += v.x;
-        s1 += v.y;
-        s2 += v.z;
+    s0 = warp_sum_d(s0);
+    s1 = warp_sum_d(s1);
+    s2 = warp_sum_d(s2);
+    if (lane == 0) {
+        const double4 a = alpha[k];
+        alpha[k] = make_double4(a.x + s0, a.y + s1, a.z + s2, 0.0);
     }
-    double4 a = alpha[k];
-    alpha[k] = make_double4(a.x + s0, a.y + s1, a.z + s2, 0.0);
 }
 
 // ------------------------------------------------------------ control grid
@@ -780,7 +774,8 @@ template <int DIM>
 void launch_resid_d(int basis, unsigned g, int n, double R, rbfd_mesh *m, cudaStream_t st) {
 #define RBFD_RESID(B)                                                                                           \
     k_resid<DIM, B><<<g, kThreads, 0, st>>>(n, R, m->cap, m->d_cx, m->d_alpha, m->d_cid, m->d_nb_cnt,           \
-                                            m->d_nb_list, m->d_cur, m->d_vec, m->d_red, m->d_lvl + 2)
+                                            m->d_nb_list, m->d_cur, m->d_vec, m->d_red, 1e-15 * m->S0, m->d_lvl, \
+                                            &m->d_misc[8])
     switch (basis) {
     case 0: RBFD_RESID(0); break;
     case 4: RBFD_RESID(4); break;
@@ -850,16 +845,19 @@ void maxnorm_async(rbfd_mesh *m, const double4 *v, double *out) {
 
 // max_i |v_i|^2 and its argmax over the sorted surface (FP64, exact order of
 // each squared norm); returns the key, writes the argmax's original index.
-double maxnorm(rbfd_mesh *m, const double4 *v, int *arg) {
+// The result goes to slots 6, 7 of the box array; with box given, the box
+// in slots 0-5 comes back in the same copy.
+double maxnorm(rbfd_mesh *m, const double4 *v, int *arg, double *box = nullptr) {
     const int nb = std::min<int>(cdiv(m->n_s, 256), 1024);
     k_maxnorm<<<nb, 256, 0, m->stream>>>(v, m->d_perm, m->n_s, m->dim, m->d_pb_key, m->d_pb_idx,
-                                         &m->d_misc[0], m->d_bbox);
+                                         &m->d_misc[0], m->d_bbox + 6);
     RBFD_CUDA(cudaGetLastError());
-    double h[2];
+    double h[8];
     RBFD_CUDA(cudaMemcpyAsync(h, m->d_bbox, sizeof(h), cudaMemcpyDeviceToHost, m->stream));
     RBFD_CUDA(cudaStreamSynchronize(m->stream));
-    if (arg) std::memcpy(arg, &h[1], sizeof(int));
-    return h[0];
+    if (arg) std::memcpy(arg, &h[7], sizeof(int));
+    if (box) std::memcpy(box, h, 6 * sizeof(double));
+    return h[6];
 }
 
 // A level's controls and weights as double-float pairs (FP32-input volume sweep).
@@ -988,7 +986,6 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     m->d_gpart = dalloc<double>((size_t)n_jt * cap + cap, "column partials");
     m->d_vec = dalloc<double4>(cap + 1, "refinement r");
     m->d_vec2 = dalloc<double4>(cap + 1, "refinement z");
-    m->d_v4part = dalloc<double4>((size_t)n_jt * cap + cap, "refinement partials");
     m->d_nb_cnt = dalloc<uint32_t>(m->n_pb, "block list counts");
     m->d_nb_list = dalloc<uint32_t>((size_t)m->n_pb * cap, "block lists");
     m->n_chunk_max = std::max(128, (kTargetCTAs + m->n_pb - 1) / m->n_pb);
@@ -1016,8 +1013,8 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     RBFD_CUDA(cudaMemsetAsync(m->d_lvl, 0, 8 * sizeof(double), st));
 
     m->stats.launches += 6;  // unpack, bbox x2, morton, gather, point blocks
-    // S0 = max_i |dS_i| (the one synchronisation of the set-up)
-    m->S0 = std::sqrt(maxnorm(m, m->d_dS, nullptr));
+    // S0 = max_i |dS_i| and the surface box (the one synchronisation of the set-up)
+    m->S0 = std::sqrt(maxnorm(m, m->d_dS, nullptr, m->h_sbox));
     m->stats.launches += 1;
     for (void *p : temps) dfree(p);
 }
@@ -1051,14 +1048,7 @@ void mesh_set_displacement(rbfd_mesh *m, const double *dS) {
     m->S0 = std::sqrt(maxnorm(m, m->d_dS, nullptr));  // synchronises the stream
     m->stats.launches += 1;
     dfree(tmp);
-    for (auto &L : m->levels) {
-        dfree(L.d_cx);
-        dfree(L.d_alpha);
-        dfree(L.d_cdf);
-        dfree(L.d_adf);
-        dfree(L.d_cell_start);
-        dfree(L.d_cell_ctrl);
-    }
+    for (auto &L : m->levels) level_free(L);
     m->levels.clear();
     m->greedy_done = false;
 }
@@ -1069,19 +1059,56 @@ static bool newton_enabled() {
     return !(v && v[0] == '0');
 }
 
+void level_free(Level &L) {
+    dfree(L.d_cx);
+    dfree(L.d_alpha);
+    dfree(L.d_cdf);
+    dfree(L.d_adf);
+    dfree(L.d_orig);
+    dfree(L.d_cell_start);
+    dfree(L.d_cell_ctrl);
+    pinned_free(L.h_scal);
+    L.d_cx = L.d_alpha = nullptr;
+    L.d_cdf = L.d_adf = nullptr;
+    L.d_orig = L.d_cell_start = L.d_cell_ctrl = nullptr;
+    L.h_scal = nullptr;
+}
+
+void level_fetch(rbfd_mesh *m, Level &L) {
+    if (L.fetched) return;
+    const int64_t n = L.nc;
+    std::vector<uint32_t> orig((size_t)n);
+    std::vector<double4> al((size_t)n);
+    if (n > 0) {
+        RBFD_CUDA(cudaMemcpyAsync(orig.data(), L.d_orig, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, m->stream));
+        RBFD_CUDA(cudaMemcpyAsync(al.data(), L.d_alpha, sizeof(double4) * n, cudaMemcpyDeviceToHost, m->stream));
+        RBFD_CUDA(cudaStreamSynchronize(m->stream));
+    }
+    L.idx.resize((size_t)n);
+    L.alpha.resize((size_t)n * m->dim);
+    for (int64_t j = 0; j < n; ++j) {
+        L.idx[j] = orig[j];
+        L.alpha[(size_t)j * m->dim + 0] = al[j].x;
+        L.alpha[(size_t)j * m->dim + 1] = al[j].y;
+        if (m->dim == 3) L.alpha[(size_t)j * m->dim + 2] = al[j].z;
+    }
+    L.fetched = true;
+}
+
 void greedy_run(rbfd_mesh *m) {
     cudaStream_t st = m->stream;
-    for (auto &L : m->levels) {
-        dfree(L.d_cx);
-        dfree(L.d_alpha);
-        dfree(L.d_cdf);
-        dfree(L.d_adf);
-        dfree(L.d_cell_start);
-        dfree(L.d_cell_ctrl);
-    }
+    for (auto &L : m->levels) level_free(L);
     m->levels.clear();
     m->greedy_done = false;
     m->stats.greedy_steps = 0;
+    // host wall time by part of the level (rbfd_stats.greedy_host_ms)
+    for (double &v : m->stats.greedy_host_ms) v = 0.0;
+    auto t_host = std::chrono::steady_clock::now();
+    auto host_mark = [&](int part) {
+        const auto t = std::chrono::steady_clock::now();
+        m->stats.greedy_host_ms[part] += std::chrono::duration<double, std::milli>(t - t_host).count();
+        t_host = t;
+    };
     m->stats.newton_steps = 0;
     m->stats.refine_sweeps = 0;
     m->stats.confirm_resumes = 0;
@@ -1099,6 +1126,7 @@ void greedy_run(rbfd_mesh *m) {
     const int mode = m->opt.precision == RBFD_FP64 ? 0 : 1;
     int final_status = RBFD_OK;
     for (int l = 0; l < Lreq; ++l) {
+        host_mark(3);  // (the set-up before the first level counts with the saves)
         Level L;
         L.R = m->R[l];
         L.tau = std::pow(eps_rel, (double)(l + 1) / (double)Lreq);
@@ -1143,6 +1171,7 @@ void greedy_run(rbfd_mesh *m) {
 
         int n = 1;
         int resumes = 0;
+        host_mark(0);
         for (;;) {
             // ---- greedy steps: one persistent cooperative launch (engine 0) ...
             bool stopped = false;
@@ -1243,29 +1272,32 @@ void greedy_run(rbfd_mesh *m) {
             }
             n = m->h_st->n;
             m->stats.greedy_steps += 0;
-            // ---- level close: FP64 iterative refinement of alpha; the
-            // convergence test runs on the device (k_ir_check), so the sweeps
-            // after convergence are launched but do nothing
+            host_mark(1);
+            // ---- level close: FP64 iterative refinement of alpha,
+            // alpha += G^T G (dS_l - Phi_cc alpha) at the controls; the
+            // convergence test runs on the device (in k_resid), so the
+            // sweeps after convergence are launched but do nothing
             RBFD_CUDA(cudaMemsetAsync(m->d_lvl + 2, 0, sizeof(double), st));
+            RBFD_CUDA(cudaMemsetAsync(&m->d_misc[8], 0, sizeof(uint32_t), st));  // k_resid's block counter
             for (int it = 0; it < std::max(0, m->opt.refine_iters); ++it) {
                 const unsigned nb = cdiv(n, kThreads / 32);  // one warp per control
                 if (m->dim == 2) launch_resid_d<2>(m->opt.basis, nb, n, L.R, m, st);
                 else launch_resid_d<3>(m->opt.basis, nb, n, L.R, m, st);
-                k_ir_check<<<1, 256, 0, st>>>(m->d_red, (int)nb, 1e-15 * m->S0, m->d_lvl);
                 k_lower_mv3<<<cdiv(n, 8), 256, 0, st>>>(n, m->cap, m->d_G, m->d_vec, m->d_vec2, m->d_lvl + 2);
-                const int n_jt = (int)cdiv(n, kJT);
-                k_colsum3<<<dim3(cdiv(n, kThreads), n_jt), kThreads, 0, st>>>(n, m->cap, m->d_G, m->d_vec2,
-                                                                              m->d_v4part, m->d_lvl + 2);
-                k_apply_correction<<<cdiv(n, kThreads), kThreads, 0, st>>>(n, m->cap, n_jt, m->d_v4part, m->d_alpha,
-                                                                           m->d_lvl + 2);
+                k_upper_mv3_add<<<cdiv(n, 8), 256, 0, st>>>(n, m->cap, m->d_Gt, m->d_vec2, m->d_alpha, m->d_lvl + 2);
                 RBFD_CUDA(cudaGetLastError());
-                m->stats.launches += 5;
+                m->stats.launches += 3;
             }
-            // ---- confirm sweep in FP64: stores E = dS_l - Phi_sc alpha
+            // ---- confirm sweep in FP64: stores E = dS_l - Phi_sc alpha.
+            // Each pair costs about 40 FP64 instructions, which issue at one
+            // warp instruction per 64 cycles per SM sub-partition: the lists
+            // are cut into chunks of 8 controls or more, so that the blocks
+            // cover the SMs several times over
             {
                 SweepArgs a = base_sweep_args(m, L.R, L.tau);
                 a.n = n;
-                int nch = n_chunks_for(m, n);
+                const int want = (4 * kTargetCTAs + m->n_pb - 1) / m->n_pb;
+                const int nch = std::max(1, std::min({want, (n + 7) / 8, m->n_chunk_max}));
                 a.chunk_len = (n + nch - 1) / nch;
                 a.is_step = 0;
                 a.E_out = m->d_E;
@@ -1274,6 +1306,7 @@ void greedy_run(rbfd_mesh *m) {
                 m->stats.launches += 1;
                 read_state(m);
             }
+            host_mark(2);
             const double emax = m->h_st->emax;
             // a level stops early only if its confirmed error is below tau
             if (emax < L.tau || n >= m->cap || resumes >= 4 || n >= m->n_s) {
@@ -1296,33 +1329,14 @@ void greedy_run(rbfd_mesh *m) {
         L.d_cdf = dalloc<float4>((size_t)2 * n, "level controls (double-float)");
         L.d_adf = dalloc<float4>((size_t)2 * n, "level weights (double-float)");
         k_level_split<<<cdiv(n, 256), 256, 0, st>>>(m->d_cx, m->d_alpha, n, L.d_cdf, L.d_adf);
-        m->stats.launches += 1;
-        std::vector<uint32_t> orig(n);
-        std::vector<double4> al(n), cxh(n);
-        k_orig_of_controls<<<cdiv(n, 256), 256, 0, st>>>(m->d_perm, m->d_cid, n, reinterpret_cast<uint32_t *>(m->d_vec2));
-        m->stats.launches += 1;
-        RBFD_CUDA(cudaMemcpyAsync(orig.data(), m->d_vec2, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, st));
-        RBFD_CUDA(cudaMemcpyAsync(al.data(), m->d_alpha, sizeof(double4) * n, cudaMemcpyDeviceToHost, st));
-        RBFD_CUDA(cudaMemcpyAsync(cxh.data(), m->d_cx, sizeof(double4) * n, cudaMemcpyDeviceToHost, st));
-        RBFD_CUDA(cudaMemcpyAsync(m->h_lvl, m->d_lvl, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
-        RBFD_CUDA(cudaStreamSynchronize(st));
-        L.smax = std::sqrt(m->h_lvl[0]);
-        m->stats.refine_sweeps += (int64_t)m->h_lvl[3];
-        L.idx.resize(n);
-        L.alpha.resize((size_t)n * m->dim);
-        double bb[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
-        for (int j = 0; j < n; ++j) {
-            L.idx[j] = orig[j];
-            L.alpha[(size_t)j * m->dim + 0] = al[j].x;
-            L.alpha[(size_t)j * m->dim + 1] = al[j].y;
-            if (m->dim == 3) L.alpha[(size_t)j * m->dim + 2] = al[j].z;
-            const double c3[3] = {cxh[j].x, cxh[j].y, cxh[j].z};
-            for (int q = 0; q < 3; ++q) {
-                bb[q] = std::min(bb[q], c3[q]);
-                bb[3 + q] = std::max(bb[3 + q], c3[q]);
-            }
-        }
-        build_control_grid(m, L, bb);
+        L.d_orig = dalloc<uint32_t>(n, "level control indices");
+        k_orig_of_controls<<<cdiv(n, 256), 256, 0, st>>>(m->d_perm, m->d_cid, n, L.d_orig);
+        m->stats.launches += 2;
+        // the level's scalars reach the host with the final wait of the
+        // greedy; indices and weights are copied only when asked for
+        L.h_scal = static_cast<double *>(pinned_alloc(4 * sizeof(double)));
+        RBFD_CUDA(cudaMemcpyAsync(L.h_scal, m->d_lvl, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        build_control_grid(m, L, m->h_sbox);
         if (L.status != RBFD_OK) final_status = RBFD_ENOTCONV;
         m->levels.push_back(std::move(L));
         // multi-level subspace: the next level interpolates this level's error
@@ -1330,6 +1344,11 @@ void greedy_run(rbfd_mesh *m) {
     }
     RBFD_CUDA(cudaEventRecord(m->ev1, st));
     RBFD_CUDA(cudaEventSynchronize(m->ev1));
+    for (auto &L : m->levels) {
+        L.smax = std::sqrt(L.h_scal[0]);
+        m->stats.refine_sweeps += (int64_t)L.h_scal[3];
+    }
+    host_mark(3);
     float ms = 0;
     RBFD_CUDA(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
     m->stats.greedy_ms = ms;

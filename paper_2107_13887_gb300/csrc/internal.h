@@ -80,13 +80,18 @@ struct Level {
     double R = 0, tau = 0, smax = 0, emax = 0;
     int64_t nc = 0;
     int status = RBFD_OK;
-    std::vector<int64_t> idx;     // original surface indices, selection order
-    std::vector<double> alpha;    // [nc][dim]
+    // host copies of the original surface indices (selection order) and the
+    // weights [nc][dim], fetched from the device on first request
+    std::vector<int64_t> idx;
+    std::vector<double> alpha;
+    bool fetched = false;
+    uint32_t *d_orig = nullptr;   // original surface indices (device)
+    double *h_scal = nullptr;     // pinned: the level's scalars (max |dS_l|^2, ..., corrections)
     double4 *d_cx = nullptr;      // control coordinates (FP64)
     double4 *d_alpha = nullptr;   // weights (FP64)
     float4 *d_cdf = nullptr;      // [2 nc] the coordinates as double-float (hi xyz, lo xyz)
     float4 *d_adf = nullptr;      // [2 nc] the weights as double-float ((ax, ay) hi/lo pairs, az pair)
-    // uniform cell grid over the controls (cell size h) for the volume sweep
+    // uniform cell grid over the surface's box (cell size h) for the volume sweep
     double3 g0{0, 0, 0};
     double h = 0;
     int3 gdim{0, 0, 0};
@@ -123,6 +128,7 @@ struct rbfd_mesh {
     int64_t n_s = 0;
     int n_levels_req = 0;
     double eps = 0, S0 = 0;
+    double h_sbox[6] = {0, 0, 0, 0, 0, 0};  // box of the surface points (lo xyz, hi xyz)
     rbfd_options opt{};
     std::vector<double> R;
     int device = 0;
@@ -159,7 +165,6 @@ struct rbfd_mesh {
     double *d_gpart = nullptr;    // per-row-tile partial column sums
     double4 *d_vec = nullptr;     // refinement vectors
     double4 *d_vec2 = nullptr;
-    double4 *d_v4part = nullptr;  // per-row-tile partial column sums, 4-wide
     uint32_t *d_nb_cnt = nullptr; // controls listed per point block
     uint32_t *d_nb_list = nullptr;// [n_pb][cap]
     double4 *d_part = nullptr;    // sweep partial sums [n_chunk_max][n_s]
@@ -226,6 +231,10 @@ void newton_run_level(rbfd_mesh *m, double R, double tau, int ctas);
 int persist_max_ctas(rbfd_mesh *m);
 void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas);
 void greedy_run(rbfd_mesh *m);
+// a level's device and pinned buffers back to the pools (its stream synchronised)
+void level_free(Level &L);
+// the host copies of a level's indices and weights (one synchronised copy, first call only)
+void level_fetch(rbfd_mesh *m, Level &L);
 void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64, double D, double k,
                 void *out);
 void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS);

@@ -78,6 +78,7 @@ class rbfd_stats(ctypes.Structure):
         ("newton_ms", ctypes.c_double),
         ("newton_launches", ctypes.c_int64),
         ("newton_terms", ctypes.c_int64),
+        ("greedy_host_ms", ctypes.c_double * 4),
     ]
 
 
@@ -302,6 +303,7 @@ class Mesh:
         _check(self._lib.rbfd_get_stats(self.h, ctypes.byref(s)))
         out = {f: getattr(s, f) for f, _ in rbfd_stats._fields_}
         out["persist_phase_ms"] = list(s.persist_phase_ms)
+        out["greedy_host_ms"] = list(s.greedy_host_ms)
         return out
 
     def deform(self, xyz_v, d_v, D: float, k: float, out=None):
