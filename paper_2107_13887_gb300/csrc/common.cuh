@@ -49,9 +49,9 @@ __device__ __forceinline__ double phi_f64(double eta) {
     return __dmul_rn(t8, q);
 }
 
-// |a - b|_2 summed in coordinate order, no contraction.
+// |a - b|_2^2 summed in coordinate order, no contraction.
 template <int DIM>
-__device__ __forceinline__ double dist_f64(double ax, double ay, double az, double bx, double by, double bz) {
+__device__ __forceinline__ double dist2_f64(double ax, double ay, double az, double bx, double by, double bz) {
     double dx = __dsub_rn(ax, bx);
     double s = __dmul_rn(dx, dx);
     double dy = __dsub_rn(ay, by);
@@ -60,7 +60,13 @@ __device__ __forceinline__ double dist_f64(double ax, double ay, double az, doub
         double dz = __dsub_rn(az, bz);
         s = __dadd_rn(s, __dmul_rn(dz, dz));
     }
-    return __dsqrt_rn(s);
+    return s;
+}
+
+// |a - b|_2 (the square root of dist2_f64).
+template <int DIM>
+__device__ __forceinline__ double dist_f64(double ax, double ay, double az, double bx, double by, double bz) {
+    return __dsqrt_rn(dist2_f64<DIM>(ax, ay, az, bx, by, bz));
 }
 
 // ------------------------------------------------------------ double-float

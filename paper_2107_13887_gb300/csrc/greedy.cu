@@ -229,6 +229,11 @@ struct SweepArgs {
     unsigned long long *pairs;
     int is_step;  // 1: greedy step (argmax over unselected + stop test); 0: confirm (max over all)
     int dim;
+    // confirm: n from this state when given (no sweep if its launch handed
+    // the level on); the lists are cut into min(ceil(n / 8), chunk_cap)
+    // chunks of equal length, the launch's other chunk blocks are idle
+    const GreedyState *n_from;
+    int chunk_cap;
 };
 
 template <int DIM, int BASIS, int MODE>
@@ -242,13 +247,22 @@ __global__ void __launch_bounds__(kThreads) k_sweep(SweepArgs a) {
     __shared__ float t32[12][kTile];
     __shared__ unsigned char s_hits[4][kTile];
     if (a.is_step && a.st->stop) return;
+    int n_c = a.n, nch = gridDim.y, chunk_len = a.chunk_len;
+    if (!a.is_step) {
+        if (a.n_from) {
+            if (a.n_from->handoff) return;
+            n_c = a.n_from->n;
+        }
+        nch = max(1, min((n_c + 7) / 8, a.chunk_cap));
+        chunk_len = (n_c + nch - 1) / nch;
+    }
 
-    const int pb = blockIdx.x, ch = blockIdx.y, nch = gridDim.y, tid = threadIdx.x;
+    const int pb = blockIdx.x, ch = blockIdx.y, tid = threadIdx.x;
     const int64_t p = (int64_t)pb * kPB + tid;
     const bool valid = p < a.n_s;
     const uint32_t cnt = a.nb_cnt[pb];
-    const int lo = ch * a.chunk_len;
-    const int hi = min((int)cnt, lo + a.chunk_len);
+    const int lo = ch < nch ? ch * chunk_len : 0;
+    const int hi = ch < nch ? min((int)cnt, lo + chunk_len) : 0;
     const double4 org = a.pb_org[pb];
 
     double acc64[3] = {0.0, 0.0, 0.0};
@@ -287,15 +301,24 @@ __global__ void __launch_bounds__(kThreads) k_sweep(SweepArgs a) {
         }
         __syncthreads();
         if (MODE == 0) {
-            if (valid)
-                for (int q = 0; q < m; ++q) {
-                    double eta = __ddiv_rn(dist_f64<DIM>(px, py, pz, t64[0][q], t64[1][q], t64[2][q]), a.R);
+            // A warp skips a control farther than R from all its points: there
+            // eta = |r - r_c| / R rounds to at least 1 and phi is exactly 0,
+            // so the sums do not change.  (FP64 issues at one warp
+            // instruction per 64 cycles per SM sub-partition, and the root,
+            // the division and phi are most of a pair's instructions.)
+            const double R2hi = __dmul_rn(__dmul_rn(a.R, a.R), 1.0 + 1e-12);
+            for (int q = 0; q < m; ++q) {
+                const double s2 = dist2_f64<DIM>(px, py, pz, t64[0][q], t64[1][q], t64[2][q]);
+                if (!__any_sync(0xffffffffu, valid && s2 <= R2hi)) continue;
+                if (valid) {
+                    double eta = __ddiv_rn(__dsqrt_rn(s2), a.R);
                     double f = phi_f64<BASIS>(eta);
                     useful += (eta < 1.0);
                     acc64[0] = __dadd_rn(acc64[0], __dmul_rn(t64[3][q], f));
                     acc64[1] = __dadd_rn(acc64[1], __dmul_rn(t64[4][q], f));
                     if (DIM == 3) acc64[2] = __dadd_rn(acc64[2], __dmul_rn(t64[5][q], f));
                 }
+            }
         } else {
             // the whole warp takes part in the filter; lanes with a point accumulate
             const int nh = warp_hits<DIM>(t32, m, wlo, whi, R2m, s_hits[tid >> 5]);
@@ -322,7 +345,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(SweepArgs a) {
     // last chunk-block of this point block reduces the partial sums in chunk order
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = atomicAdd(&a.pb_done[pb], 1u) == (unsigned)(nch - 1);
+    if (tid == 0) s_last = atomicAdd(&a.pb_done[pb], 1u) == gridDim.y - 1;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
@@ -586,12 +609,25 @@ __global__ void k_level_init(int first_orig_from_state, int first_orig, const ui
 // r_i = dS_l(c_i) - sum_j alpha_j phi(|r_ci - r_cj| / R), FP64, one warp per
 // control i; the sum runs over the controls listed for the point block that
 // holds c_i (every control within R of it is listed, so the omitted ones
-// contribute exactly 0).  Per-block max |r| to red[block]; the last block to
-// finish (a counter in cnt, reset by that block) tests the largest residual
-// against tol on the device: once it is at most tol, lvl[2] is set and the
-// rest of this level close does nothing; lvl[3] counts the corrections.
+// contribute exactly 0).  Per block, max |r| and whether any residual is above
+// its rounding level to red[2 block], red[2 block + 1]; the last block to
+// finish (a counter in cnt, reset by that block) tests them on the device:
+// once the largest residual is at most tol, or every residual is at the
+// rounding level of its evaluation, lvl[2] is set and the rest of this level
+// close does nothing; lvl[3] counts the corrections.
+// The level-close kernels take n from nfrom when it is given (a close queued
+// behind the greedy launch before the host has read n) and then do nothing
+// if that launch handed the level on; warps stride over the rows.
+__device__ __forceinline__ bool close_rows(const GreedyState *nfrom, int &n) {
+    if (!nfrom) return true;
+    if (nfrom->handoff) return false;
+    n = nfrom->n;
+    return true;
+}
+
 template <int DIM, int BASIS>
-__global__ void __launch_bounds__(kThreads) k_resid(int n, double R, int cap, const double4 *__restrict__ cx,
+__global__ void __launch_bounds__(kThreads) k_resid(int n, const GreedyState *__restrict__ nfrom, double R, int cap,
+                                                    const double4 *__restrict__ cx,
                                                     const double4 *__restrict__ alpha,
                                                     const uint32_t *__restrict__ cid,
                                                     const uint32_t *__restrict__ nb_cnt,
@@ -599,19 +635,20 @@ __global__ void __launch_bounds__(kThreads) k_resid(int n, double R, int cap, co
                                                     const double4 *__restrict__ cur, double4 *__restrict__ r,
                                                     double *__restrict__ red, double tol, double *__restrict__ lvl,
                                                     unsigned *__restrict__ cnt) {
-    if (lvl[2] != 0.0) return;  // refinement already converged
-    __shared__ double sm[kThreads / 32];
+    if (lvl[2] != 0.0 || !close_rows(nfrom, n)) return;  // converged, or no close for this launch
+    __shared__ double sm[kThreads / 32], sb[kThreads / 32];
+    __shared__ bool sa[kThreads / 32];
     __shared__ bool s_last;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int i = blockIdx.x * (kThreads / 32) + w;
     double mx = 0.0;
-    if (i < n) {
+    bool above = false;
+    for (int i = blockIdx.x * (kThreads / 32) + w; i < n; i += gridDim.x * (kThreads / 32)) {
         const uint32_t ci = cid[i];
         const double4 xi = cx[i];
         const int pb = (int)(ci / kPB);
         const int cnt = (int)nb_cnt[pb];
         const uint32_t *list = nb_list + (size_t)pb * cap;
-        double a0 = 0, a1 = 0, a2 = 0;
+        double a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;
         for (int q = lane; q < cnt; q += 32) {
             const uint32_t j = list[q];
             const double4 c = cx[j], al = alpha[j];
@@ -619,50 +656,81 @@ __global__ void __launch_bounds__(kThreads) k_resid(int n, double R, int cap, co
             a0 = fma(al.x, f, a0);
             a1 = fma(al.y, f, a1);
             a2 = fma(al.z, f, a2);
+            b0 = fma(fabs(al.x), f, b0);  // (f >= 0)
+            b1 = fma(fabs(al.y), f, b1);
+            b2 = fma(fabs(al.z), f, b2);
         }
         a0 = warp_sum_d(a0);
         a1 = warp_sum_d(a1);
         a2 = warp_sum_d(a2);
+        b0 = warp_sum_d(b0);
+        b1 = warp_sum_d(b1);
+        b2 = warp_sum_d(b2);
         if (lane == 0) {
             const double4 b = cur[ci];
             const double4 ri = make_double4(b.x - a0, b.y - a1, DIM == 3 ? b.z - a2 : 0.0, 0.0);
             r[i] = ri;
-            mx = fmax(fabs(ri.x), fmax(fabs(ri.y), fabs(ri.z)));
+            mx = fmax(mx, fmax(fabs(ri.x), fmax(fabs(ri.y), fabs(ri.z))));
+            // at the rounding level of its own evaluation: 32 u (|b| + sum |alpha phi|)
+            const double u32 = 32.0 * 1.1102230246251565e-16;
+            above |= fabs(ri.x) > u32 * (fabs(b.x) + b0) || fabs(ri.y) > u32 * (fabs(b.y) + b1) ||
+                     (DIM == 3 && fabs(ri.z) > u32 * (fabs(b.z) + b2));
         }
     }
-    if (lane == 0) sm[w] = mx;
+    if (lane == 0) {
+        sm[w] = mx;
+        sa[w] = above;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         double v = sm[0];
-        for (int q = 1; q < kThreads / 32; ++q) v = fmax(v, sm[q]);
-        red[blockIdx.x] = v;
+        bool ab = sa[0];
+        for (int q = 1; q < kThreads / 32; ++q) {
+            v = fmax(v, sm[q]);
+            ab = ab || sa[q];
+        }
+        red[2 * blockIdx.x] = v;
+        red[2 * blockIdx.x + 1] = ab ? 1.0 : 0.0;
         __threadfence();
         s_last = atomicAdd(cnt, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    double v = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) v = fmax(v, __ldcg(&red[b]));
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    double v = 0.0, ab = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+        v = fmax(v, __ldcg(&red[2 * b]));
+        ab = fmax(ab, __ldcg(&red[2 * b + 1]));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        ab = fmax(ab, __shfl_xor_sync(0xffffffffu, ab, o));
+    }
     __syncthreads();
-    if (lane == 0) sm[w] = v;
+    if (lane == 0) {
+        sm[w] = v;
+        sb[w] = ab;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int q = 1; q < kThreads / 32; ++q) v = fmax(v, sm[q]);
-        if (v <= tol) lvl[2] = 1.0;
+        for (int q = 1; q < kThreads / 32; ++q) {
+            v = fmax(v, sm[q]);
+            ab = fmax(ab, sb[q]);
+        }
+        // converged: below tol, or every residual at its rounding level
+        // (further corrections cannot lower it)
+        if (v <= tol || ab == 0.0) lvl[2] = 1.0;
         else lvl[3] += 1.0;
         *cnt = 0;
     }
 }
 
 // z_j = sum_{k <= j} G_jk r_k (3 right-hand sides), one warp per row.
-__global__ void k_lower_mv3(int n, int cap, const double *__restrict__ G, const double4 *__restrict__ r,
-                            double4 *__restrict__ z, const double *__restrict__ done) {
-    if (*done != 0.0) return;
+__global__ void k_lower_mv3(int n, const GreedyState *__restrict__ nfrom, int cap, const double *__restrict__ G,
+                            const double4 *__restrict__ r, double4 *__restrict__ z, const double *__restrict__ done) {
+    if (*done != 0.0 || !close_rows(nfrom, n)) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = blockIdx.x * (blockDim.x >> 5) + w;
-    if (j >= n) return;
+    for (int j = blockIdx.x * (blockDim.x >> 5) + w; j < n; j += gridDim.x * (blockDim.x >> 5)) {
     const double *row = G + (size_t)j * cap;
     double s0 = 0, s1 = 0, s2 = 0;
     for (int k = lane; k <= j; k += 32) {
@@ -676,16 +744,17 @@ __global__ void k_lower_mv3(int n, int cap, const double *__restrict__ G, const 
     s1 = warp_sum_d(s1);
     s2 = warp_sum_d(s2);
     if (lane == 0) z[j] = make_double4(s0, s1, s2, 0.0);
+    }
 }
 
 // alpha_k += sum_{j >= k} G_jk z_j (3 right-hand sides), one warp per k over
 // row k of the transposed copy G^T (contiguous).
-__global__ void k_upper_mv3_add(int n, int cap, const double *__restrict__ Gt, const double4 *__restrict__ z,
-                                double4 *__restrict__ alpha, const double *__restrict__ done) {
-    if (*done != 0.0) return;
+__global__ void k_upper_mv3_add(int n, const GreedyState *__restrict__ nfrom, int cap, const double *__restrict__ Gt,
+                                const double4 *__restrict__ z, double4 *__restrict__ alpha,
+                                const double *__restrict__ done) {
+    if (*done != 0.0 || !close_rows(nfrom, n)) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = blockIdx.x * (blockDim.x >> 5) + w;
-    if (k >= n) return;
+    for (int k = blockIdx.x * (blockDim.x >> 5) + w; k < n; k += gridDim.x * (blockDim.x >> 5)) {
     const double *row = Gt + (size_t)k * cap;
     double s0 = 0, s1 = 0, s2 = 0;
     for (int j = k + lane; j < n; j += 32) {
@@ -701,6 +770,7 @@ __global__ void k_upper_mv3_add(int n, int cap, const double *__restrict__ Gt, c
     if (lane == 0) {
         const double4 a = alpha[k];
         alpha[k] = make_double4(a.x + s0, a.y + s1, a.z + s2, 0.0);
+    }
     }
 }
 
@@ -771,9 +841,10 @@ void launch_phi_d(int basis, unsigned g, const GrowArgs &a, cudaStream_t st) {
 }
 
 template <int DIM>
-void launch_resid_d(int basis, unsigned g, int n, double R, rbfd_mesh *m, cudaStream_t st) {
+void launch_resid_d(int basis, unsigned g, int n, const GreedyState *nfrom, double R, rbfd_mesh *m,
+                    cudaStream_t st) {
 #define RBFD_RESID(B)                                                                                           \
-    k_resid<DIM, B><<<g, kThreads, 0, st>>>(n, R, m->cap, m->d_cx, m->d_alpha, m->d_cid, m->d_nb_cnt,           \
+    k_resid<DIM, B><<<g, kThreads, 0, st>>>(n, nfrom, R, m->cap, m->d_cx, m->d_alpha, m->d_cid, m->d_nb_cnt,    \
                                             m->d_nb_list, m->d_cur, m->d_vec, m->d_red, 1e-15 * m->S0, m->d_lvl, \
                                             &m->d_misc[8])
     switch (basis) {
@@ -1171,8 +1242,49 @@ void greedy_run(rbfd_mesh *m) {
 
         int n = 1;
         int resumes = 0;
+        // ---- level close: FP64 iterative refinement of alpha, alpha +=
+        // G^T G (dS_l - Phi_cc alpha) at the controls, then the FP64 confirm
+        // sweep E = dS_l - Phi_sc alpha.  The convergence test of the
+        // refinement runs on the device (in k_resid), so the sweeps after
+        // convergence are launched but do nothing.  With from_state the
+        // kernels read n from the greedy state (a close queued behind the
+        // greedy launch before the host has read it, n_max bounding it) and
+        // do nothing if that launch handed the level on.
+        auto enqueue_close = [&](int n_max, bool from_state) {
+            const GreedyState *nfrom = from_state ? m->d_st : nullptr;
+            RBFD_CUDA(cudaMemsetAsync(m->d_lvl + 2, 0, sizeof(double), st));
+            RBFD_CUDA(cudaMemsetAsync(&m->d_misc[8], 0, sizeof(uint32_t), st));  // k_resid's block counter
+            // one warp per control (strided over a grid of at most 4 blocks per SM)
+            const unsigned nb = (unsigned)std::min<int64_t>(cdiv(n_max, kThreads / 32), 4 * 152);
+            const unsigned nb8 = (unsigned)std::min<int64_t>(cdiv(n_max, 8), 4 * 152);
+            for (int it = 0; it < std::max(0, m->opt.refine_iters); ++it) {
+                if (m->dim == 2) launch_resid_d<2>(m->opt.basis, nb, n_max, nfrom, L.R, m, st);
+                else launch_resid_d<3>(m->opt.basis, nb, n_max, nfrom, L.R, m, st);
+                k_lower_mv3<<<nb8, 256, 0, st>>>(n_max, nfrom, m->cap, m->d_G, m->d_vec, m->d_vec2, m->d_lvl + 2);
+                k_upper_mv3_add<<<nb8, 256, 0, st>>>(n_max, nfrom, m->cap, m->d_Gt, m->d_vec2, m->d_alpha,
+                                                     m->d_lvl + 2);
+                RBFD_CUDA(cudaGetLastError());
+                m->stats.launches += 3;
+            }
+            // Each confirm pair costs about 40 FP64 instructions, which issue
+            // at one warp instruction per 64 cycles per SM sub-partition: the
+            // lists are cut into chunks of 8 controls or more, so that the
+            // blocks cover the SMs several times over
+            SweepArgs a = base_sweep_args(m, L.R, L.tau);
+            a.n = n_max;
+            a.n_from = nfrom;
+            a.chunk_cap = std::max(1, std::min((4 * kTargetCTAs + m->n_pb - 1) / m->n_pb, m->n_chunk_max));
+            const int nch = std::max(1, std::min((n_max + 7) / 8, a.chunk_cap));
+            a.chunk_len = 0;  // (from n in the kernel)
+            a.is_step = 0;
+            a.E_out = m->d_E;
+            launch_sweep(m->dim, m->opt.basis, 0, dim3(m->n_pb, nch), a, st);
+            RBFD_CUDA(cudaGetLastError());
+            m->stats.launches += 1;
+        };
         host_mark(0);
         for (;;) {
+            bool closed = false;
             // ---- greedy steps: one persistent cooperative launch (engine 0) ...
             bool stopped = false;
             // a level starts in the Newton basis (engine 0) while that pays; the
@@ -1190,6 +1302,7 @@ void greedy_run(rbfd_mesh *m) {
                     cudaEvent_t e0 = m->prof.begin(st);
                     newton_run_level(m, L.R, L.tau, ctas);
                     m->prof.end(kProfNewton, e0, st, 1);
+                    enqueue_close(std::min(m->newton_cols, m->cap), true);
                     read_state_bar(m);
                     m->prof.flush();
                     if (m->h_bar->err) fail(RBFD_ETIMEOUT, "Newton greedy: a grid barrier exceeded its wait bound");
@@ -1204,6 +1317,7 @@ void greedy_run(rbfd_mesh *m) {
                         RBFD_CUDA(cudaMemsetAsync(&m->d_st->handoff, 0, sizeof(int), st));
                     } else {
                         stopped = true;
+                        closed = true;  // (the state read above follows the close)
                     }
                 }
             }
@@ -1273,37 +1387,8 @@ void greedy_run(rbfd_mesh *m) {
             n = m->h_st->n;
             m->stats.greedy_steps += 0;
             host_mark(1);
-            // ---- level close: FP64 iterative refinement of alpha,
-            // alpha += G^T G (dS_l - Phi_cc alpha) at the controls; the
-            // convergence test runs on the device (in k_resid), so the
-            // sweeps after convergence are launched but do nothing
-            RBFD_CUDA(cudaMemsetAsync(m->d_lvl + 2, 0, sizeof(double), st));
-            RBFD_CUDA(cudaMemsetAsync(&m->d_misc[8], 0, sizeof(uint32_t), st));  // k_resid's block counter
-            for (int it = 0; it < std::max(0, m->opt.refine_iters); ++it) {
-                const unsigned nb = cdiv(n, kThreads / 32);  // one warp per control
-                if (m->dim == 2) launch_resid_d<2>(m->opt.basis, nb, n, L.R, m, st);
-                else launch_resid_d<3>(m->opt.basis, nb, n, L.R, m, st);
-                k_lower_mv3<<<cdiv(n, 8), 256, 0, st>>>(n, m->cap, m->d_G, m->d_vec, m->d_vec2, m->d_lvl + 2);
-                k_upper_mv3_add<<<cdiv(n, 8), 256, 0, st>>>(n, m->cap, m->d_Gt, m->d_vec2, m->d_alpha, m->d_lvl + 2);
-                RBFD_CUDA(cudaGetLastError());
-                m->stats.launches += 3;
-            }
-            // ---- confirm sweep in FP64: stores E = dS_l - Phi_sc alpha.
-            // Each pair costs about 40 FP64 instructions, which issue at one
-            // warp instruction per 64 cycles per SM sub-partition: the lists
-            // are cut into chunks of 8 controls or more, so that the blocks
-            // cover the SMs several times over
-            {
-                SweepArgs a = base_sweep_args(m, L.R, L.tau);
-                a.n = n;
-                const int want = (4 * kTargetCTAs + m->n_pb - 1) / m->n_pb;
-                const int nch = std::max(1, std::min({want, (n + 7) / 8, m->n_chunk_max}));
-                a.chunk_len = (n + nch - 1) / nch;
-                a.is_step = 0;
-                a.E_out = m->d_E;
-                launch_sweep(m->dim, m->opt.basis, 0, dim3(m->n_pb, nch), a, st);
-                RBFD_CUDA(cudaGetLastError());
-                m->stats.launches += 1;
+            if (!closed) {
+                enqueue_close(n, false);
                 read_state(m);
             }
             host_mark(2);

@@ -172,15 +172,21 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
                 }
                 __syncthreads();
                 if (MODE == 0) {
-                    if (valid)
-                        for (int q = 0; q < m; ++q) {
-                            double eta = __ddiv_rn(dist_f64<DIM>(px, py, pz, t64[0][q], t64[1][q], t64[2][q]), a.R);
+                    // a warp skips a control farther than R from all its points
+                    // (phi is exactly 0 there, the sums do not change)
+                    const double R2hi = __dmul_rn(__dmul_rn(a.R, a.R), 1.0 + 1e-12);
+                    for (int q = 0; q < m; ++q) {
+                        const double s2 = dist2_f64<DIM>(px, py, pz, t64[0][q], t64[1][q], t64[2][q]);
+                        if (!__any_sync(0xffffffffu, valid && s2 <= R2hi)) continue;
+                        if (valid) {
+                            double eta = __ddiv_rn(__dsqrt_rn(s2), a.R);
                             double f = phi_f64<BASIS>(eta);
                             useful += (eta < 1.0);
                             acc64[0] = __dadd_rn(acc64[0], __dmul_rn(t64[3][q], f));
                             acc64[1] = __dadd_rn(acc64[1], __dmul_rn(t64[4][q], f));
                             if (DIM == 3) acc64[2] = __dadd_rn(acc64[2], __dmul_rn(t64[5][q], f));
                         }
+                    }
                 } else {
                     // every lane of the warp takes part in the filter, then only
                     // the lanes with a point accumulate
