@@ -28,6 +28,7 @@ import subprocess
 import sys
 import threading
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -239,13 +240,19 @@ def run_ours(args):
     # each case gets its own stream so that the batch calls overlap them
     streams = [torch.cuda.Stream(dev) for _ in cases]
 
+    # the meshes are created side by side as well (the binding releases the
+    # interpreter lock during library calls)
+    create_pool = ThreadPoolExecutor(max_workers=len(cases), initializer=torch.cuda.set_device, initargs=(local,))
+
     def one_step(src, record):
-        """Both cases as one batch: create, greedy + deform (each case on its own
-        host thread and stream, side by side), destroy."""
-        ms = []
-        for c, d, s_ in zip(cases, src, streams):
-            ms.append(rbfd.Mesh(d["xyz_s"], d["dS"], c.R, c.eps, precision=precision, stream=s_.cuda_stream,
-                                profile=record, engine=args.engine, grid_ctas=args.ctas))
+        """Both cases as one batch: create (one host thread per case), greedy +
+        deform (each case on its own host thread and stream, side by side),
+        destroy."""
+        def make(q):
+            c, d, s_ = cases[q], src[q], streams[q]
+            return rbfd.Mesh(d["xyz_s"], d["dS"], c.R, c.eps, precision=precision, stream=s_.cuda_stream,
+                             profile=record, engine=args.engine, grid_ctas=args.ctas)
+        ms = list(create_pool.map(make, range(len(cases))))
         rbfd.greedy_deform_batch(ms, [d["xyz_v"] for d in src], [d["d_v"] for d in src], [c.D for c in cases],
                                  [c.k for c in cases], [d["out"] for d in src])
         stats = [m.stats() for m in ms]

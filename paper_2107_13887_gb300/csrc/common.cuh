@@ -461,6 +461,34 @@ __device__ __forceinline__ void grid_arrive_mono(GridBarrier *b) {
     }
 }
 
+// The same two halves for one thread of the block: arrive (after a block
+// barrier that ordered the block's writes before it), then poll until the
+// count reaches target or the bound runs out (sets the error word); returns
+// false on error.  The caller publishes the result to the block.
+__device__ __forceinline__ void grid_arrive_mono_one(GridBarrier *b) {
+    asm volatile("fence.acq_rel.gpu;\n\tred.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(&b->count) : "memory");
+}
+
+__device__ __forceinline__ bool grid_poll_mono_one(GridBarrier *b, unsigned target, unsigned long long limit) {
+    unsigned long long it = 0;
+    unsigned cnt, gen, err, pad;
+    for (;;) {
+        asm volatile("ld.relaxed.gpu.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(cnt), "=r"(gen), "=r"(err), "=r"(pad)
+                     : "l"(b)
+                     : "memory");
+        if (cnt >= target || err) break;
+        if (++it > limit) {
+            atomicExch(&b->err, 1);
+            err = 1;
+            break;
+        }
+        __nanosleep(8);
+    }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");  // acquire: pairs with the arrivals' release
+    return err == 0;
+}
+
 __device__ __forceinline__ bool grid_wait_mono(GridBarrier *b, unsigned target, unsigned long long limit) {
     __shared__ int s_ok;
     if (threadIdx.x == 0) {

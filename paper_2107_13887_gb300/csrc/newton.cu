@@ -44,6 +44,7 @@
 //   while the others load the winner's column.
 #include <algorithm>
 #include <cfloat>
+#include <climits>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
     // the step's scalars, computed by one warp: [2] 1 / l_j (mixed: its
     // double-float bits), [3] 1 / l_j and [4..6] w_j in FP64 for (b)
     __shared__ double s_dec[8];
-    __shared__ int s_flags, s_mc;
+    __shared__ int s_flags, s_mc, s_bar_ok;
     __shared__ unsigned s_nz[kNW], s_lm[kNW];
     __shared__ int s_win;
     __shared__ double4 s_wrec[3];
@@ -293,8 +294,10 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
     // would have evaluated there
     unsigned long long nz_cum = 0, pairs_useful = 0;
     uint32_t list_max = own_list ? own_cnt : 0;  // longest list this block keeps
-    // rows of the inverse factor: row k belongs to warp (k / P) % 8 of block k % P
-    const int k_first = (int)blockIdx.x + warp * (int)P;
+    // rows of the inverse factor: row k belongs to warp (k / P) % 7 of block
+    // k % P (the last warp arrives at and waits for the grid barrier meanwhile)
+    constexpr int kRowWarps = kNW - 1;
+    const int k_first = warp < kRowWarps ? (int)blockIdx.x + warp * (int)P : INT_MAX;
     const df invRd = {a.invR_hi, a.invR_lo};
     // profile mode, block 0: [0] marking c_j, [1] (a), [2] lists + record, [3] (b),
     // [4] barrier wait, [5] reading the records, [6] their argmax, [7] scalars
@@ -597,20 +600,25 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
         }
         RBFD_TMARK(2)
         if (a.test_skip_arrival && blockIdx.x == 0) return;  // the others' waits run out
-        grid_arrive_mono(a.bar);
-
-        // ---- (b) row j of the inverse factor on this block's rows, alpha (FP64)
-        {
+        __syncthreads();  // the block's record and candidate column are written
+        if (warp == kRowWarps) {
+            // the last warp arrives at the grid barrier and waits for it
+            if (lane == 0) {
+                grid_arrive_mono_one(a.bar);
+                s_bar_ok = grid_poll_mono_one(a.bar, (unsigned)(guard + 1) * P, a.spin_limit);
+            }
+        } else {
+            // ---- (b) row j of the inverse factor on this block's rows, alpha (FP64)
             if (MODE) {  // y to FP64 once per block, in place (each pair becomes its double)
-                for (int m = tid; m < j; m += kNT) {
+                for (int m = tid; m < j; m += kRowWarps * 32) {
                     const float2 v = s_y2[m];
                     s_y[m] = (double)v.x + (double)v.y;
                 }
-                __syncthreads();
+                asm volatile("bar.sync 1, %0;" ::"n"(kRowWarps * 32) : "memory");  // the row warps only
             }
             const double ilj64 = s_dec[3];
             const double4 wj64 = make_double4(s_dec[4], s_dec[5], s_dec[6], 0.0);
-            for (int k = k_first; k <= j; k += (int)P * kNW) {
+            for (int k = k_first; k <= j; k += (int)P * kRowWarps) {
                 if (k == j) {  // the diagonal and alpha_j
                     if (lane == 0) {
                         a.G[(size_t)j * a.cap + j] = ilj64;
@@ -668,7 +676,8 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
             }
         }
         RBFD_TMARK(3)
-        if (!grid_wait_mono(a.bar, (unsigned)(guard + 1) * P, a.spin_limit)) RBFD_NEXIT()
+        __syncthreads();  // the grid barrier has passed (or failed: s_bar_ok)
+        if (!s_bar_ok) RBFD_NEXIT()
         RBFD_TMARK(4)
 
         // ---- the step's decision: every block from the same records

@@ -263,8 +263,66 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *t
     if (s.launches) *s.launches += 3;
 }
 
+// Small arrays in one block: a bitonic sort in shared memory of the 64-bit
+// values (low key_bits of the key) << 32 | position, which orders by key and
+// keeps equal keys in input order (the same result as the stable radix sort),
+// then keys and values are gathered by position.  One launch instead of five
+// per 8-bit digit.
+constexpr int kSmallSort = 8192;
+constexpr int kSmallSortThreads = 1024;
+
+__global__ void __launch_bounds__(kSmallSortThreads) k_sort_small(uint32_t *keys, uint32_t *vals, int n, int n2,
+                                                                   uint32_t mask) {
+    extern __shared__ unsigned long long s_c[];  // [n2] composites, then [n] (key, value) pairs
+    uint2 *s_kv = reinterpret_cast<uint2 *>(s_c + n2);
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        if (i < n) {
+            const uint32_t k = keys[i];
+            s_kv[i] = make_uint2(k, vals[i]);
+            s_c[i] = ((unsigned long long)(k & mask) << 32) | (unsigned)i;
+        } else {
+            s_c[i] = ~0ull;  // padding sorts last
+        }
+    }
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const unsigned long long a = s_c[i], b = s_c[l];
+                    if ((a > b) == ((i & k) == 0)) {
+                        s_c[i] = b;
+                        s_c[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint2 kv = s_kv[(unsigned)s_c[i]];
+        keys[i] = kv.x;
+        vals[i] = kv.y;
+    }
+}
+
 void radix_sort_pairs(uint32_t *keys, uint32_t *vals, size_t n, int key_bits, SortScratch &s, cudaStream_t st) {
     if (n <= 1) return;
+    if (n <= (size_t)kSmallSort) {
+        int n2 = 2;
+        while (n2 < (int)n) n2 <<= 1;
+        const size_t smem = (size_t)n2 * 8 + n * 8;
+        // (one value for every launch and device: the attribute belongs to the kernel)
+        if (smem > 48 * 1024)
+            RBFD_CUDA(cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           kSmallSort * 16));
+        const uint32_t mask = key_bits >= 32 ? 0xffffffffu : ((1u << key_bits) - 1u);
+        k_sort_small<<<1, kSmallSortThreads, smem, st>>>(keys, vals, (int)n, n2, mask);
+        if (s.launches) *s.launches += 1;
+        RBFD_CUDA(cudaGetLastError());
+        return;
+    }
     s.reserve(n);
     int nblk = (int)((n + RS_TILE - 1) / RS_TILE);
     uint32_t *ka = keys, *va = vals, *kb = s.keys_alt, *vb = s.vals_alt;
