@@ -471,13 +471,15 @@ __device__ __forceinline__ void grid_arrive_mono_one(GridBarrier *b) {
 
 __device__ __forceinline__ bool grid_poll_mono_one(GridBarrier *b, unsigned target, unsigned long long limit) {
     unsigned long long it = 0;
-    unsigned cnt, gen, err, pad;
+    unsigned err = 0;
     for (;;) {
+        uint4 v;  // count, generation, error word, pad
         asm volatile("ld.relaxed.gpu.global.v4.u32 {%0, %1, %2, %3}, [%4];"
-                     : "=r"(cnt), "=r"(gen), "=r"(err), "=r"(pad)
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                      : "l"(b)
                      : "memory");
-        if (cnt >= target || err) break;
+        err = v.z;
+        if (v.x >= target || err) break;
         if (++it > limit) {
             atomicExch(&b->err, 1);
             err = 1;
@@ -494,13 +496,15 @@ __device__ __forceinline__ bool grid_wait_mono(GridBarrier *b, unsigned target, 
     if (threadIdx.x == 0) {
         // one 16-byte load per poll reads the count and the error word together
         unsigned long long it = 0;
-        unsigned cnt, gen, err, pad;
+        unsigned err = 0;
         for (;;) {
+            uint4 v;  // count, generation, error word, pad
             asm volatile("ld.relaxed.gpu.global.v4.u32 {%0, %1, %2, %3}, [%4];"
-                         : "=r"(cnt), "=r"(gen), "=r"(err), "=r"(pad)
+                         : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                          : "l"(b)
                          : "memory");
-            if (cnt >= target || err) break;
+            err = v.z;
+            if (v.x >= target || err) break;
             if (++it > limit) {
                 atomicExch(&b->err, 1);
                 err = 1;

@@ -90,45 +90,6 @@ __device__ __forceinline__ bool better_key(unsigned long long ka, int ia, unsign
     return (ka > kb) || (ka == kb && ia < ib && ia >= 0) || (ib < 0 && ia >= 0);
 }
 
-__device__ __forceinline__ void block_argmax_key(unsigned long long &k, int &i, unsigned long long *sk, int *si) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, k, o);
-        const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
-        if (better_key(k2, i2, k, i)) {
-            k = k2;
-            i = i2;
-        }
-    }
-    __syncthreads();
-    if (lane == 0) {
-        sk[w] = k;
-        si[w] = i;
-    }
-    __syncthreads();
-    if (w == 0) {
-        k = lane < nw ? sk[lane] : 0ull;
-        i = lane < nw ? si[lane] : -1;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, k, o);
-            const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
-            if (better_key(k2, i2, k, i)) {
-                k = k2;
-                i = i2;
-            }
-        }
-        if (lane == 0) {
-            sk[0] = k;
-            si[0] = i;
-        }
-    }
-    __syncthreads();
-    k = sk[0];
-    i = si[0];
-}
-
 // acc += y * v in double-float (TwoProduct by FMA, TwoSum on the high
 // parts, low parts summed plainly; renormalised once at the end).
 __device__ __forceinline__ void df_fma_acc(float &ah, float &al, float yh, float yl, float vh, float vl) {
@@ -175,6 +136,7 @@ struct NewtonArgs {
     uint32_t *cid;
     double *G, *Gt, *V;  // V: FP64, or hi/lo float pairs in mixed mode
     double4 *rec;  // [2][P][3] per block: integers (key, original index, longest list, position), coordinates + l^2, E
+    ulonglong2 *head;  // [2][P] per block: key, original index | longest list << 32 (what every block reads)
     double *ycol;  // [2][P][cn + 1] per block: V[.][candidate] (mixed mode: hi/lo float pairs)
     // (two copies, by the parity of the step: a block writes the next step's
     // record while a slower block may still read this step's)
@@ -215,13 +177,12 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
     // (FP64; mixed: hi [8][32] then lo [8][32] per group)
     __shared__ double s_part[kRound][kNW][32];
     __shared__ unsigned long long sk[32];
-    __shared__ int si[32];
+    __shared__ int si[32], sbw[32];
     // the step's scalars, computed by one warp: [2] 1 / l_j (mixed: its
     // double-float bits), [3] 1 / l_j and [4..6] w_j in FP64 for (b)
     __shared__ double s_dec[8];
     __shared__ int s_flags, s_mc, s_bar_ok;
     __shared__ unsigned s_nz[kNW], s_lm[kNW];
-    __shared__ int s_win;
     __shared__ double4 s_wrec[3];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -536,20 +497,43 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
             }
         }
         {
+            // the block's best candidate, its nonzero count and longest list:
+            // per warp by shuffles, then every thread reduces the warps'
+            // entries itself (one block barrier)
             unsigned long long kk = bkey;
-            int ii = bidx;
-            block_argmax_key(kk, ii, sk, si);  // (ends with __syncthreads)
-            if (ii >= 0 && bidx == ii) s_win = bslot;  // the one thread holding it
-            unsigned u = nz;
-            for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
-            unsigned lm = own_list ? own_cnt : 0u;
-            for (int o = 16; o > 0; o >>= 1) lm = max(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+            int ii = bidx, ws = bslot;
+            unsigned u = nz, lm = own_list ? own_cnt : 0u;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, kk, o);
+                const int i2 = __shfl_xor_sync(0xffffffffu, ii, o), w2 = __shfl_xor_sync(0xffffffffu, ws, o);
+                if (better_key(k2, i2, kk, ii)) {
+                    kk = k2;
+                    ii = i2;
+                    ws = w2;
+                }
+                u += __shfl_xor_sync(0xffffffffu, u, o);
+                lm = max(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+            }
             if (lane == 0) {
+                sk[warp] = kk;
+                si[warp] = ii;
+                sbw[warp] = ws;
                 s_nz[warp] = u;
                 s_lm[warp] = lm;
             }
             __syncthreads();
-            const int ws = ii >= 0 ? s_win : -1;
+            kk = sk[0];
+            ii = si[0];
+            ws = sbw[0];
+#pragma unroll
+            for (int w8 = 1; w8 < kNW; ++w8)
+                if (better_key(sk[w8], si[w8], kk, ii)) {
+                    kk = sk[w8];
+                    ii = si[w8];
+                    ws = sbw[w8];
+                }
+            if (ii < 0) ws = -1;
             if (tid == 0) {
                 unsigned bnz = 0;
                 for (int w8 = 0; w8 < kNW; ++w8) {
@@ -558,6 +542,9 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
                 }
                 nz_cum += bnz;
                 pairs_useful += nz_cum;  // the list sweep of this step would evaluate these pairs
+                a.head[(size_t)(j & 1) * P + blockIdx.x] =
+                    make_ulonglong2(ws >= 0 ? kk : 0ull, (unsigned long long)(unsigned)(ws >= 0 ? ii : -1) |
+                                                             ((unsigned long long)list_max << 32));
                 double4 *r = a.rec + 3 * ((size_t)(j & 1) * P + blockIdx.x);
                 ulonglong2 *ri = reinterpret_cast<ulonglong2 *>(r);
                 if (ws >= 0) {
@@ -681,48 +668,61 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
         RBFD_TMARK(4)
 
         // ---- the step's decision: every block from the same records
+        // every block reads the P heads (16 bytes each), takes the argmax per
+        // warp and then over the warps' entries (one block barrier); the
+        // winner's full record is read by one warp afterwards
         unsigned long long K = 0;
         int I = -1, Bw = -1;
         unsigned lmax = 0;
-        double4 r0 = make_double4(0, 0, 0, 0), r1 = r0, r2 = r0;
-        const double4 *rj = a.rec + 3 * (size_t)(j & 1) * P;
+        const ulonglong2 *hj = a.head + (size_t)(j & 1) * P;
         for (unsigned b = tid; b < P; b += kNT) {
-            const ulonglong2 *qi = reinterpret_cast<const ulonglong2 *>(&rj[3 * (size_t)b]);
-            const ulonglong2 i0 = __ldcg(qi), i1 = __ldcg(qi + 1);
-            const double4 q0 = make_double4(__longlong_as_double((long long)i0.x), __longlong_as_double((long long)i0.y),
-                                            __longlong_as_double((long long)i1.x), __longlong_as_double((long long)i1.y));
-            const double4 q1 = ldcg_d4(&rj[3 * (size_t)b + 1]);
-            const double4 q2 = ldcg_d4(&rj[3 * (size_t)b + 2]);
-            lmax = max(lmax, (unsigned)i1.x);
-            const int ib = (int)(long long)i0.y;
-            const unsigned long long kb = i0.x;
-            if (better_key(kb, ib, K, I)) {
-                K = kb;
+            const ulonglong2 h = __ldcg(&hj[b]);
+            lmax = max(lmax, (unsigned)(h.y >> 32));
+            const int ib = (int)(unsigned)h.y;
+            if (better_key(h.x, ib, K, I)) {
+                K = h.x;
                 I = ib;
                 Bw = (int)b;
-                r0 = q0;
-                r1 = q1;
-                r2 = q2;
             }
         }
-        for (int o = 16; o > 0; o >>= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-        if (lane == 0) s_lm[warp] = lmax;
         RBFD_TMARK(5)
-        {
-            const unsigned long long kk = K;
-            const int ii = I;
-            block_argmax_key(K, I, sk, si);  // (its barriers also publish s_lm)
-            if (I >= 0 && ii == I && kk == K) {
-                s_win = Bw;
-                s_wrec[0] = r0;
-                s_wrec[1] = r1;
-                s_wrec[2] = r2;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, K, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, I, o), b2 = __shfl_xor_sync(0xffffffffu, Bw, o);
+            if (better_key(k2, i2, K, I)) {
+                K = k2;
+                I = i2;
+                Bw = b2;
             }
-            __syncthreads();
+            lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
         }
+        if (lane == 0) {
+            sk[warp] = K;
+            si[warp] = I;
+            sbw[warp] = Bw;
+            s_lm[warp] = lmax;
+        }
+        __syncthreads();
+        K = sk[0];
+        I = si[0];
+        Bw = sbw[0];
+#pragma unroll
+        for (int w8 = 1; w8 < kNW; ++w8)
+            if (better_key(sk[w8], si[w8], K, I)) {
+                K = sk[w8];
+                I = si[w8];
+                Bw = sbw[w8];
+            }
         RBFD_TMARK(6)
         const int nn = n;  // index the next control takes
         if (warp == 0) {  // the step's scalars, on one warp
+            if (I >= 0) {  // the winner's record: 96 bytes, 16 per lane
+                if (lane < 6)
+                    reinterpret_cast<ulonglong2 *>(s_wrec)[lane] =
+                        __ldcg(reinterpret_cast<const ulonglong2 *>(a.rec + 3 * ((size_t)(j & 1) * P + Bw)) + lane);
+                __syncwarp();
+            }
             int mc = 1;
             for (int w8 = 0; w8 < kNW; ++w8) mc = max(mc, (int)s_lm[w8]);
             // e = sqrt(K) / S0 < tau, the same rounded test as the other
@@ -777,7 +777,7 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
             // meanwhile the other warps load the winner's column, y of the
             // next pass (written before this step's barrier, parity j & 1;
             // unused if the level stops here)
-            const double *yb = a.ycol + ((size_t)(j & 1) * P + s_win) * ycl;
+            const double *yb = a.ycol + ((size_t)(j & 1) * P + Bw) * ycl;
             if (MODE) {
                 const float2 *yf = reinterpret_cast<const float2 *>(yb);
                 for (int k = tid - 32; k < nn; k += kNT - 32) s_y2[k] = __ldcg(&yf[k]);
@@ -1070,11 +1070,13 @@ void newton_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
         m->d_nrec = nullptr;
         m->d_nycol = nullptr;
         m->newton_rec_rows = 0;
-        m->d_nrec = dalloc<double4>((size_t)2 * 3 * sh.ctas, "Newton block records");
+        // records [2][P][3], then the heads [2][P] (16 bytes each: P double4)
+        m->d_nrec = dalloc<double4>((size_t)2 * 3 * sh.ctas + sh.ctas, "Newton block records");
         m->d_nycol = dalloc<double>((size_t)2 * sh.ctas * ((size_t)m->newton_cols + 1), "Newton candidate columns");
         m->newton_rec_rows = sh.ctas;
     }
     a.rec = m->d_nrec;
+    a.head = reinterpret_cast<ulonglong2 *>(m->d_nrec + (size_t)2 * 3 * m->newton_rec_rows);
     a.ycol = m->d_nycol;
     a.bar = m->d_bar;
     a.spin_limit = 1ull << 24;
