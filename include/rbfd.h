@@ -321,10 +321,14 @@ int rbfd_deform_batch(rbfd_mesh **meshes, int n, const int64_t *n_v, const float
 /*
  * rbfd_greedy_deform_batch -- rbfd_greedy then rbfd_deform for each of n
  * meshes, mesh i's two calls one after the other on its own host thread and
- * stream, so that one mesh's volume update overlaps another's greedy.
- * Arguments as rbfd_deform_batch (d_v may be NULL, or any d_v[i], to compute
- * wall distances).  Returns RBFD_ENOTCONV, after deforming with the valid
- * levels, if a greedy hit its control cap; otherwise the worst status.
+ * stream, so that one mesh's volume update overlaps another's greedy.  With
+ * wall distances given, a mesh's volume (host copies, packing, Morton order)
+ * is prepared on a second stream while its own greedy runs; the results are
+ * those of rbfd_greedy + rbfd_deform bit for bit.  The volume arrays are read
+ * from the start of the call.  Arguments as rbfd_deform_batch (d_v may be
+ * NULL, or any d_v[i], to compute wall distances).  Returns RBFD_ENOTCONV,
+ * after deforming with the valid levels, if a greedy hit its control cap;
+ * otherwise the worst status.
  */
 int rbfd_greedy_deform_batch(rbfd_mesh **meshes, int n, const int64_t *n_v, const float *const *xyz_v,
                              const float *const *d_v, const double *D, const double *k, float *const *out);

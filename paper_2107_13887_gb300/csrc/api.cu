@@ -209,6 +209,7 @@ void mesh_free(rbfd_mesh *m) {
     cudaGetDevice(&prev);
     cudaSetDevice(m->device);
     if (m->stream) cudaStreamSynchronize(m->stream);
+    rbfd::volume_stage_release(m);
     for (auto &L : m->levels) rbfd::level_free(L);
     void *ptrs[] = {m->d_perm, m->d_inv, m->d_xs, m->d_dS, m->d_cur, m->d_E, m->d_pb_lo, m->d_pb_hi,
                     m->d_pb_org, m->d_xs_hi, m->d_xs_lo, m->d_sel, m->d_G, m->d_w, m->d_alpha, m->d_cx,
@@ -471,20 +472,26 @@ int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st) {
     });
 }
 
+// The argument checks of a volume update (everything but the greedy state).
+static void deform_check(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, double D, double k,
+                         const void *out) {
+    if (!m) rbfd::fail(RBFD_EINVAL, "rbfd_deform: NULL mesh");
+    if (n_v < 0 || n_v > ((int64_t)1 << 31) - 1) rbfd::fail(RBFD_EINVAL, "rbfd_deform: n_v out of range");
+    if (n_v > 0 && (!xyz_v || !out)) rbfd::fail(RBFD_EINVAL, "rbfd_deform: NULL array");
+    if (!(D >= 0.0) || !(k >= 0.0) || !std::isfinite(D) || !std::isfinite(k))
+        rbfd::fail(RBFD_EINVAL, "rbfd_deform: D and k must be finite and >= 0");
+    if (D == 0.0 && k == 0.0) rbfd::fail(RBFD_EINVAL, "rbfd_deform: D and k cannot both be 0");
+    RBFD_CUDA(cudaSetDevice(m->device));
+    if (m->opt.inputs_on_device && n_v > 0 &&
+        (!is_device_ptr(xyz_v) || (d_v && !is_device_ptr(d_v)) || !is_device_ptr(out)))
+        rbfd::fail(RBFD_EINVAL, "rbfd_deform: inputs_on_device set but arrays are not device memory");
+}
+
 static int deform_common(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, double D, double k,
                          void *out, bool f64) {
     return guarded([&] {
-        if (!m) rbfd::fail(RBFD_EINVAL, "rbfd_deform: NULL mesh");
-        if (n_v < 0 || n_v > ((int64_t)1 << 31) - 1) rbfd::fail(RBFD_EINVAL, "rbfd_deform: n_v out of range");
-        if (n_v > 0 && (!xyz_v || !out)) rbfd::fail(RBFD_EINVAL, "rbfd_deform: NULL array");
-        if (!(D >= 0.0) || !(k >= 0.0) || !std::isfinite(D) || !std::isfinite(k))
-            rbfd::fail(RBFD_EINVAL, "rbfd_deform: D and k must be finite and >= 0");
-        if (D == 0.0 && k == 0.0) rbfd::fail(RBFD_EINVAL, "rbfd_deform: D and k cannot both be 0");
+        deform_check(m, n_v, xyz_v, d_v, D, k, out);
         if (!m->greedy_done) rbfd::fail(RBFD_ESTATE, "rbfd_deform: run rbfd_greedy first");
-        RBFD_CUDA(cudaSetDevice(m->device));
-        if (m->opt.inputs_on_device && n_v > 0 &&
-            (!is_device_ptr(xyz_v) || (d_v && !is_device_ptr(d_v)) || !is_device_ptr(out)))
-            rbfd::fail(RBFD_EINVAL, "rbfd_deform: inputs_on_device set but arrays are not device memory");
         rbfd::deform_run(m, n_v, xyz_v, d_v, f64, D, k, out);
     });
 }
@@ -612,11 +619,19 @@ int rbfd_greedy_deform_batch(rbfd_mesh **meshes, int n, const int64_t *n_v, cons
     rc = run_batch(n, [&](int i) {
         rbfd_mesh *m = meshes[i];
         RBFD_CUDA(cudaSetDevice(m->device));
+        const void *dv = d_v ? d_v[i] : nullptr;
+        // the volume's copies, packing and Morton order run on a second
+        // stream while the greedy runs
+        deform_check(m, n_v[i], xyz_v[i], dv, D[i], k[i], out[i]);
+        rbfd::volume_stage(m, n_v[i], xyz_v[i], dv, false);
         bool notconv = false;
         try {
             rbfd::greedy_run(m);
         } catch (const Error &e) {
-            if (e.status != RBFD_ENOTCONV) throw;
+            if (e.status != RBFD_ENOTCONV) {
+                rbfd::volume_unstage(m);
+                throw;
+            }
             notconv = true;  // the levels are valid: deform with them, report it after
         }
         const int drc = deform_common(m, n_v[i], xyz_v[i], d_v ? d_v[i] : nullptr, D[i], k[i], out[i], false);

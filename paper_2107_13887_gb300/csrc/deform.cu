@@ -577,14 +577,14 @@ void reserve_volume(rbfd_mesh *m, size_t n) {
 
 // Morton order of n packed points vin: sorted copy into vsorted, caller
 // index of each sorted point into orig.  Uses the mesh's key buffer.
-void morton_order(rbfd_mesh *m, int64_t n, const double4 *vin, double4 *vsorted, uint32_t *orig) {
-    cudaStream_t st = m->stream;
+void morton_order(rbfd_mesh *m, int64_t n, const double4 *vin, double4 *vsorted, uint32_t *orig,
+                  cudaStream_t st, double *red, double *box, SortScratch &ss) {
     const int dim = m->dim;
     const int nbb = std::min<int>(cdiv(n, 256), 256);
-    k_bbox_partial_v<<<nbb, 256, 0, st>>>(vin, n, m->d_red);
-    k_bbox_reduce<<<1, 192, 0, st>>>(m->d_red, nbb, m->d_bbox);
-    morton_keys_f64_dev(vin, n, dim, m->d_bbox, m->d_vkeys, orig, st, vol_key_shift(dim));
-    radix_sort_pairs(m->d_vkeys, orig, (size_t)n, kVolKeyBits, m->sort, st);
+    k_bbox_partial_v<<<nbb, 256, 0, st>>>(vin, n, red);
+    k_bbox_reduce<<<1, 192, 0, st>>>(red, nbb, box);
+    morton_keys_f64_dev(vin, n, dim, box, m->d_vkeys, orig, st, vol_key_shift(dim));
+    radix_sort_pairs(m->d_vkeys, orig, (size_t)n, kVolKeyBits, ss, st);
     k_gather_vol<<<cdiv(n, 256), 256, 0, st>>>(vin, orig, n, vsorted);
     RBFD_CUDA(cudaGetLastError());
     m->stats.launches += 4;
@@ -661,6 +661,111 @@ void deform_levels(rbfd_mesh *m, int64_t nV, const double4 *vpos, const uint32_t
 
 }  // namespace
 
+namespace {
+// Staging streams, kept across meshes (creating one costs more than a launch).
+std::mutex g_side_mu;
+std::vector<std::pair<int, cudaStream_t>> g_side_free;
+
+cudaStream_t side_acquire(int dev) {
+    {
+        std::lock_guard<std::mutex> lk(g_side_mu);
+        for (size_t i = 0; i < g_side_free.size(); ++i)
+            if (g_side_free[i].first == dev) {
+                cudaStream_t s = g_side_free[i].second;
+                g_side_free.erase(g_side_free.begin() + (std::ptrdiff_t)i);
+                return s;
+            }
+    }
+    cudaStream_t s = nullptr;
+    RBFD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    return s;
+}
+
+// The device copy of the volume inputs: the inputs themselves when they are
+// device pointers, else the mesh's staging buffer filled on stream st.
+struct VolumeIO {
+    const void *x, *d;
+    void *out;
+};
+
+VolumeIO volume_io(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, void *out, bool f64,
+                   cudaStream_t st) {
+    VolumeIO io{xyz_v, d_v, out};
+    if (m->opt.inputs_on_device || n_v <= 0) return io;
+    const int dim = m->dim;
+    const size_t es = f64 ? sizeof(double) : sizeof(float);
+    const size_t need = (size_t)n_v * dim * es * 2 + (size_t)n_v * es + 256;
+    if (need > m->vio_bytes) {
+        dfree(m->d_vio);
+        m->d_vio = nullptr;
+        m->vio_bytes = 0;
+        m->d_vio = dmalloc(need, "volume staging");
+        m->vio_bytes = need;
+    }
+    char *base = static_cast<char *>(m->d_vio);
+    void *sx = base;
+    void *sd = base + (size_t)n_v * dim * es;
+    io.out = base + (size_t)n_v * dim * es + (((size_t)n_v * es + 255) / 256) * 256;
+    RBFD_CUDA(cudaMemcpyAsync(sx, xyz_v, (size_t)n_v * dim * es, cudaMemcpyHostToDevice, st));
+    if (d_v) RBFD_CUDA(cudaMemcpyAsync(sd, d_v, (size_t)n_v * es, cudaMemcpyHostToDevice, st));
+    io.x = sx;
+    io.d = d_v ? sd : nullptr;
+    return io;
+}
+}  // namespace
+
+void volume_stage(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64) {
+    volume_unstage(m);
+    if (n_v <= 0 || !d_v) return;  // (wall distances on the device are capped by the levels' D_l)
+    if (!m->vstream) m->vstream = side_acquire(m->device);
+    if (!m->ev_vfork) RBFD_CUDA(cudaEventCreateWithFlags(&m->ev_vfork, cudaEventDisableTiming));
+    if (!m->ev_vdone) RBFD_CUDA(cudaEventCreateWithFlags(&m->ev_vdone, cudaEventDisableTiming));
+    if (!m->d_vred) m->d_vred = dalloc<double>(6 * 256, "volume box partials");
+    if (!m->d_vbox) m->d_vbox = dalloc<double>(8, "volume box");
+    if (!m->vsort.launches) m->vsort.launches = &m->stats.launches;
+    reserve_volume(m, (size_t)n_v);
+    cudaStream_t vs = m->vstream;
+    RBFD_CUDA(cudaEventRecord(m->ev_vfork, m->stream));  // (the inputs are ready in the caller's order)
+    RBFD_CUDA(cudaStreamWaitEvent(vs, m->ev_vfork, 0));
+    const VolumeIO io = volume_io(m, n_v, xyz_v, d_v, nullptr, f64, vs);
+    double4 *vin = reinterpret_cast<double4 *>(m->d_vin);
+    double4 *vpos = reinterpret_cast<double4 *>(m->d_vpos);
+    k_vol_pack<<<cdiv(n_v, 256), 256, 0, vs>>>(io.x, io.d, n_v, m->dim, f64 ? 1 : 0, vin);
+    morton_order(m, n_v, vin, vpos, m->d_vorig, vs, m->d_vred, m->d_vbox, m->vsort);
+    RBFD_CUDA(cudaEventRecord(m->ev_vdone, vs));
+    RBFD_CUDA(cudaGetLastError());
+    m->stats.launches += 1;
+    m->vst_ok = true;
+    m->vst_n = n_v;
+    m->vst_x = xyz_v;
+    m->vst_d = d_v;
+    m->vst_f64 = f64;
+    m->vst_dout = io.out;  // (null for device outputs: the caller's array)
+}
+
+void volume_unstage(rbfd_mesh *m) {
+    if (!m->vst_ok) return;
+    m->vst_ok = false;
+    RBFD_CUDA(cudaStreamWaitEvent(m->stream, m->ev_vdone, 0));  // its buffers are reused after this
+}
+
+void volume_stage_release(rbfd_mesh *m) {
+    if (m->vstream) {
+        cudaStreamSynchronize(m->vstream);
+        std::lock_guard<std::mutex> lk(g_side_mu);
+        g_side_free.push_back({m->device, m->vstream});
+        m->vstream = nullptr;
+    }
+    if (m->ev_vfork) cudaEventDestroy(m->ev_vfork);
+    if (m->ev_vdone) cudaEventDestroy(m->ev_vdone);
+    m->ev_vfork = m->ev_vdone = nullptr;
+    m->vsort.release();
+    dfree(m->d_vred);
+    dfree(m->d_vbox);
+    m->d_vred = m->d_vbox = nullptr;
+    m->vst_ok = false;
+}
+
 void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64, double D, double k,
                 void *out) {
     cudaStream_t st = m->stream;
@@ -677,6 +782,26 @@ void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, b
         Dmax = std::max(Dmax, Dl[l]);
     }
     const bool host = !m->opt.inputs_on_device;
+    if (m->vst_ok && m->vst_n == n_v && m->vst_x == xyz_v && m->vst_d == d_v && m->vst_f64 == f64) {
+        // staged ahead: every point packed and Morton-sorted; the levels'
+        // reductions d < D_l run over all of them (points beyond every D_l
+        // stay 0)
+        m->vst_ok = false;
+        RBFD_CUDA(cudaStreamWaitEvent(st, m->ev_vdone, 0));
+        void *dout = host ? m->vst_dout : out;
+        if (Dmax > 0.0) deform_levels(m, n_v, reinterpret_cast<const double4 *>(m->d_vpos), m->d_vorig, Dl.data(), L,
+                                      dout, f64);
+        else RBFD_CUDA(cudaMemsetAsync(dout, 0, (size_t)n_v * dim * es, st));
+        if (host) RBFD_CUDA(cudaMemcpyAsync(out, dout, (size_t)n_v * dim * es, cudaMemcpyDeviceToHost, st));
+        RBFD_CUDA(cudaEventRecord(m->ev1, st));
+        RBFD_CUDA(cudaEventSynchronize(m->ev1));
+        float ms = 0;
+        RBFD_CUDA(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
+        m->stats.deform_ms = ms;
+        m->prof.flush();
+        return;
+    }
+    volume_unstage(m);
     void *dout = out;
     const void *dx = xyz_v, *dd = d_v;
     if (n_v > 0) {
@@ -703,13 +828,12 @@ void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, b
     }
     double4 *vin = reinterpret_cast<double4 *>(m->d_vin);
     double4 *vpos = reinterpret_cast<double4 *>(m->d_vpos);
-    int64_t nV = 0;
     if (n_v > 0 && Dmax > 0.0 && !dd) {
         // No wall distances given: Morton-sort every point, compute d(r) on
         // the device (needed only below max_l D_l, so capped there), then
         // keep d < max_l D_l in Morton order (steps (1) and (2) in one).
         k_vol_pack<<<cdiv(n_v, 256), 256, 0, st>>>(dx, nullptr, n_v, dim, f64 ? 1 : 0, vin);
-        morton_order(m, n_v, vin, vpos, m->d_vorig);
+        morton_order(m, n_v, vin, vpos, m->d_vorig, st, m->d_red, m->d_bbox, m->sort);
         wall_distance_sorted(m, n_v, vpos, Dmax, nullptr);
         k_flag_below<<<cdiv(n_v, 256), 256, 0, st>>>(vpos, nullptr, n_v, Dmax, m->d_vflag);
         exclusive_scan_u32(m->d_vflag, m->d_vscan, (size_t)n_v, &m->d_misc[4], m->sort, st);
@@ -726,31 +850,14 @@ void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, b
         }
         m->stats.launches += 6;  // pack, flags, compaction, gathers x2, scatter
     } else if (n_v > 0 && Dmax > 0.0) {
+        // every point packed and Morton-sorted (what a staged volume does
+        // ahead of the greedy), then the levels' reductions d < D_l over all
+        // of them: the same points in the same blocks either way, so both
+        // give the same results bit for bit
         k_vol_pack<<<cdiv(n_v, 256), 256, 0, st>>>(dx, dd, n_v, dim, f64 ? 1 : 0, vin);
-        // (1) volume point reduction: d < max_l D_l
-        k_flag_below<<<cdiv(n_v, 256), 256, 0, st>>>(vin, nullptr, n_v, Dmax, m->d_vflag);
-        exclusive_scan_u32(m->d_vflag, m->d_vscan, (size_t)n_v, &m->d_misc[4], m->sort, st);
-        k_compact<<<cdiv(n_v, 256), 256, 0, st>>>(m->d_vflag, m->d_vscan, n_v, m->d_vlist);
-        uint32_t cnt = 0;
-        RBFD_CUDA(cudaMemcpyAsync(&cnt, &m->d_misc[4], sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-        RBFD_CUDA(cudaStreamSynchronize(st));
-        nV = cnt;
-    }
-    if (nV > 0) {
-        // (2) Morton order of the kept points
-        const int nbb = std::min<int>(cdiv(nV, 256), 256);
-        k_bbox_idx<<<nbb, 256, 0, st>>>(vin, m->d_vlist, nV, m->d_red);
-        k_bbox_reduce<<<1, 192, 0, st>>>(m->d_red, nbb, m->d_bbox);
-        k_gather_vol<<<cdiv(nV, 256), 256, 0, st>>>(vin, m->d_vlist, nV, vpos);  // kept points, caller order
-        morton_keys_f64_dev(vpos, nV, dim, m->d_bbox, m->d_vkeys, m->d_vorig, st, vol_key_shift(dim));
-        radix_sort_pairs(m->d_vkeys, m->d_vorig, (size_t)nV, kVolKeyBits, m->sort, st);
-        k_gather_vol<<<cdiv(nV, 256), 256, 0, st>>>(vpos, m->d_vorig, nV, vin);  // vin := sorted points
-        // caller index of sorted point i = vlist[vorig[i]]
-        k_gather_u32<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vlist, m->d_vorig, nV, m->d_vflag);
-        RBFD_CUDA(cudaMemcpyAsync(m->d_vorig, m->d_vflag, sizeof(uint32_t) * nV, cudaMemcpyDeviceToDevice, st));
-        vpos = vin;
-        deform_levels(m, nV, vpos, m->d_vorig, Dl.data(), L, dout, f64);
-        m->stats.launches += 9;  // pack, flags, compaction, bbox x2, gathers x3, scatter
+        morton_order(m, n_v, vin, vpos, m->d_vorig, st, m->d_red, m->d_bbox, m->sort);
+        deform_levels(m, n_v, vpos, m->d_vorig, Dl.data(), L, dout, f64);
+        m->stats.launches += 1;
     }
     if (host && n_v > 0)
         RBFD_CUDA(cudaMemcpyAsync(out, dout, (size_t)n_v * dim * es, cudaMemcpyDeviceToHost, st));
@@ -790,7 +897,7 @@ void volume_register(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float 
     k_vol_pack<<<cdiv(n_v, 256), 256, 0, st>>>(dx, dd, n_v, dim, 0, vin);
     m->d_vreg = dalloc<double4>((size_t)n_v, "registered volume");
     m->d_vreg_orig = dalloc<uint32_t>((size_t)n_v, "registered volume order");
-    morton_order(m, n_v, vin, m->d_vreg, m->d_vreg_orig);
+    morton_order(m, n_v, vin, m->d_vreg, m->d_vreg_orig, st, m->d_red, m->d_bbox, m->sort);
     // no wall distances given: d(r) of every point, computed once (later
     // displacements may need any D_l)
     if (!dd) wall_distance_sorted(m, n_v, m->d_vreg, INFINITY, nullptr);
@@ -821,7 +928,7 @@ void wall_distance_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, bool f64, d
     double4 *vin = reinterpret_cast<double4 *>(m->d_vin);
     double4 *vpos = reinterpret_cast<double4 *>(m->d_vpos);
     k_vol_pack<<<cdiv(n_v, 256), 256, 0, st>>>(dx, nullptr, n_v, dim, f64 ? 1 : 0, vin);
-    morton_order(m, n_v, vin, vpos, m->d_vorig);
+    morton_order(m, n_v, vin, vpos, m->d_vorig, st, m->d_red, m->d_bbox, m->sort);
     double *dsorted = reinterpret_cast<double *>(m->d_vacc);
     wall_distance_sorted(m, n_v, vpos, INFINITY, dsorted);
     k_scatter_d<<<cdiv(n_v, 256), 256, 0, st>>>(dsorted, m->d_vorig, n_v, dout);

@@ -220,6 +220,19 @@ struct rbfd_mesh {
     uint32_t *d_vreg_orig = nullptr;
     uint32_t *d_misc = nullptr;    // small counters
     double *d_bbox = nullptr;      // 8 doubles
+    // volume staged ahead of the greedy (copies, packing, Morton order of every
+    // point on a second stream while the greedy runs): valid for one deform
+    // call with the same arguments
+    cudaStream_t vstream = nullptr;
+    cudaEvent_t ev_vfork = nullptr, ev_vdone = nullptr;
+    rbfd::SortScratch vsort;
+    double *d_vred = nullptr;      // box partials of the staging (6 x 256)
+    double *d_vbox = nullptr;      // box of the staged points (8 doubles)
+    bool vst_ok = false;
+    int64_t vst_n = 0;
+    const void *vst_x = nullptr, *vst_d = nullptr;
+    bool vst_f64 = false;
+    void *vst_dout = nullptr;      // device output (the staging buffer for host outputs)
 };
 
 namespace rbfd {
@@ -237,6 +250,15 @@ void level_free(Level &L);
 void level_fetch(rbfd_mesh *m, Level &L);
 void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64, double D, double k,
                 void *out);
+// Stage a volume for the next deform_run with the same arguments: copies,
+// packing and the Morton order of every point, on a second stream that
+// starts after the work queued so far on the mesh's stream (the greedy can
+// run meanwhile).  Only with wall distances given.
+void volume_stage(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64);
+// Drop a staged volume that will not be used (the mesh's stream waits for it).
+void volume_unstage(rbfd_mesh *m);
+// Return the staging stream and events (mesh destruction).
+void volume_stage_release(rbfd_mesh *m);
 void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS);
 void mesh_set_displacement(rbfd_mesh *m, const double *dS);
 void volume_register(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v);

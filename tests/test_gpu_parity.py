@@ -408,6 +408,40 @@ def test_barrier_wait_bound_returns_timeout(monkeypatch):
 # ---------------------------------------------------------------- batches
 
 
+def test_staged_volume_with_device_arrays_matches_plain_calls():
+    """greedy_deform_batch on device tensors prepares each volume on a second
+    stream while the greedy runs: the outputs equal rbfd_greedy + rbfd_deform
+    bit for bit, also when a batch call reuses the meshes' buffers, and the
+    volume arrays may be rewritten after the call."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    names = ["airfoil_horns_2lvl", "wing_ridge_2lvl", "airfoil_bump_333"]
+    cases = [CASES[n] for n in names]
+    want = []
+    for c in cases:
+        m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps)
+        m.greedy()
+        want.append(m.deform(c.xyz_v, c.d_v, c.D, c.k))
+        m.close()
+    for rep in range(2):
+        ms = [rbfd.Mesh(t(c.xyz_s), t(c.dS), c.R, c.eps) for c in cases]
+        xv = [t(c.xyz_v) for c in cases]
+        dv = [t(c.d_v) for c in cases]
+        outs = [torch.empty((c.n_v, c.dim), dtype=torch.float32, device=dev) for c in cases]
+        rbfd.greedy_deform_batch(ms, xv, dv, [c.D for c in cases], [c.k for c in cases], outs)
+        torch.cuda.synchronize()
+        for x in xv:
+            x.zero_()  # the call has finished with its inputs
+        for w, o in zip(want, outs):
+            assert np.array_equal(o.cpu().numpy(), w)
+        # the same meshes deformed again by a plain call: the staged buffers are not reused
+        for c, m, w in zip(cases, ms, want):
+            o2 = m.deform(t(c.xyz_v), t(c.d_v), c.D, c.k)
+            assert np.array_equal(o2.cpu().numpy(), w)
+            m.close()
+
+
 @pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
 def test_batch_matches_single_meshes(precision):
     names = ["airfoil_horns_2lvl", "wing_ridge_2lvl", "airfoil_pitch_2lvl", "airfoil_bump_333"]
