@@ -371,6 +371,9 @@ def run_ours(args):
                    "persist_ctas": int(stats[-1]["persist_ctas"]) if stats else 0},
         "time_to_eps_ms": {"pitch_heave": statistics.median(greedy_ms[0::2]),
                            "horns": statistics.median(greedy_ms[1::2])},
+        # device time of each case's volume update (after its greedy), median over the timed steps
+        "deform_ms": {"pitch_heave": statistics.median([s["deform_ms"] for s in stats[0::2]]),
+                      "horns": statistics.median([s["deform_ms"] for s in stats[1::2]])},
         "pairs_useful_per_step": pairs_all / args.steps / ws,
         "roofline": roofline,
         "e2e": e2e,

@@ -211,14 +211,10 @@ void mesh_free(rbfd_mesh *m) {
     if (m->stream) cudaStreamSynchronize(m->stream);
     rbfd::volume_stage_release(m);
     for (auto &L : m->levels) rbfd::level_free(L);
-    void *ptrs[] = {m->d_perm, m->d_inv, m->d_xs, m->d_dS, m->d_cur, m->d_E, m->d_pb_lo, m->d_pb_hi,
-                    m->d_pb_org, m->d_xs_hi, m->d_xs_lo, m->d_sel, m->d_G, m->d_w, m->d_alpha, m->d_cx,
-                    m->d_cdf, m->d_cid, m->d_phi, m->d_y, m->d_red, m->d_gpart, m->d_vec, m->d_vec2,
-                    m->d_nb_cnt, m->d_nb_list, m->d_part, m->d_pb_done, m->d_pb_key, m->d_pb_idx, m->d_pairs,
-                    m->d_st, m->d_vin, m->d_vpos, m->d_vorig, m->d_vflag, m->d_vscan, m->d_vlist, m->d_vkeys,
-                    m->d_vacc, m->d_vio, m->d_misc, m->d_bbox, m->d_bar, m->d_pred, m->d_Gt,
-                    m->d_nz_k, m->d_nz_v, m->d_phase_ns, m->d_vreg, m->d_vreg_orig, m->d_pb_fbox,
-                    m->d_V, m->d_nrec, m->d_nycol, m->d_nwdf, m->d_lvl, m->d_ckeys, m->d_vpos4};
+    // (the mesh's fixed buffers are carved out of d_arena)
+    void *ptrs[] = {m->d_arena, m->d_G, m->d_Gt, m->d_vin, m->d_vpos, m->d_vorig, m->d_vflag, m->d_vscan,
+                    m->d_vlist, m->d_vkeys, m->d_vacc, m->d_vio, m->d_vreg, m->d_vreg_orig, m->d_pb_fbox,
+                    m->d_V, m->d_nrec, m->d_nycol, m->d_nwdf, m->d_ckeys, m->d_vpos4};
     for (void *p : ptrs) dfree(p);
     m->sort.release();
     m->prof.release();

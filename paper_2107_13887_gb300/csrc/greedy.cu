@@ -218,7 +218,7 @@ struct SweepArgs {
     const uint32_t *perm;
     const uint32_t *nb_cnt, *nb_list;
     const double4 *cx, *alpha;
-    double R, S0, tau;
+    double R, S0, tau, invR;
     float invR_hi, invR_lo;
     double4 *part;
     double4 *E_out;  // non-null: store E (confirm sweep)
@@ -311,7 +311,12 @@ __global__ void __launch_bounds__(kThreads) k_sweep(SweepArgs a) {
                 const double s2 = dist2_f64<DIM>(px, py, pz, t64[0][q], t64[1][q], t64[2][q]);
                 if (!__any_sync(0xffffffffu, valid && s2 <= R2hi)) continue;
                 if (valid) {
-                    double eta = __ddiv_rn(__dsqrt_rn(s2), a.R);
+                    // a greedy step divides by R like the persistent engine's
+                    // sweep (the engines agree bit for bit); the confirm sweep
+                    // multiplies by 1/R (one rounding more in eta, a tenth of
+                    // the FP64 instructions of the division)
+                    const double d = __dsqrt_rn(s2);
+                    double eta = a.is_step ? __ddiv_rn(d, a.R) : __dmul_rn(d, a.invR);
                     double f = phi_f64<BASIS>(eta);
                     useful += (eta < 1.0);
                     acc64[0] = __dadd_rn(acc64[0], __dmul_rn(t64[3][q], f));
@@ -636,6 +641,7 @@ __global__ void __launch_bounds__(kThreads) k_resid(int n, const GreedyState *__
                                                     double *__restrict__ red, double tol, double *__restrict__ lvl,
                                                     unsigned *__restrict__ cnt) {
     if (lvl[2] != 0.0 || !close_rows(nfrom, n)) return;  // converged, or no close for this launch
+    const double invR = 1.0 / R;
     __shared__ double sm[kThreads / 32], sb[kThreads / 32];
     __shared__ bool sa[kThreads / 32];
     __shared__ bool s_last;
@@ -652,7 +658,7 @@ __global__ void __launch_bounds__(kThreads) k_resid(int n, const GreedyState *__
         for (int q = lane; q < cnt; q += 32) {
             const uint32_t j = list[q];
             const double4 c = cx[j], al = alpha[j];
-            const double f = phi_f64<BASIS>(__ddiv_rn(dist_f64<DIM>(xi.x, xi.y, xi.z, c.x, c.y, c.z), R));
+            const double f = phi_f64<BASIS>(__dmul_rn(dist_f64<DIM>(xi.x, xi.y, xi.z, c.x, c.y, c.z), invR));
             a0 = fma(al.x, f, a0);
             a1 = fma(al.y, f, a1);
             a2 = fma(al.z, f, a2);
@@ -882,6 +888,7 @@ SweepArgs base_sweep_args(rbfd_mesh *m, double R, double tau) {
     a.S0 = m->S0;
     a.tau = tau;
     double inv = 1.0 / R;
+    a.invR = inv;
     a.invR_hi = (float)inv;
     a.invR_lo = (float)(inv - (double)a.invR_hi);
     a.part = m->d_part;
@@ -982,112 +989,141 @@ void build_control_grid(rbfd_mesh *m, Level &L, const double *bb) {
 
 // ====================================================================== API
 
+namespace {
+// Buffers carved out of one device block: one pool call instead of one per
+// buffer (each 256-byte aligned).
+struct Carver {
+    struct Item {
+        void **dst;
+        size_t bytes;
+    };
+    std::vector<Item> items;
+    template <typename T>
+    void add(T *&p, size_t n) {
+        items.push_back({reinterpret_cast<void **>(&p), sizeof(T) * std::max<size_t>(n, 1)});
+    }
+    size_t total() const {
+        size_t t = 0;
+        for (const Item &i : items) t += (i.bytes + 255) / 256 * 256;
+        return t;
+    }
+    void assign(char *base) const {
+        size_t off = 0;
+        for (const Item &i : items) {
+            *i.dst = base + off;
+            off += (i.bytes + 255) / 256 * 256;
+        }
+    }
+};
+}  // namespace
+
 void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     const int64_t n = m->n_s;
     cudaStream_t st = m->stream;
+    m->n_pb = (int)cdiv(n, kPB);
+    int64_t cap = m->opt.nc_cap > 0 ? m->opt.nc_cap : 32768;
+    cap = std::min<int64_t>(cap, n);
+    m->cap = (int)cap;
+    const int n_red = (int)cdiv(cap + 1, kYWarps) + 8;
+    const int n_jt = (int)cdiv(cap + 1, kJT);
+    m->n_chunk_max = std::max(128, (kTargetCTAs + m->n_pb - 1) / m->n_pb);
+    // the mesh's fixed buffers in one block: first the words that start at
+    // zero (one memset), then the rest; the two factors G and G^T apart
+    Carver zero, rest;
+    zero.add(m->d_misc, 16);
+    zero.add(m->d_pairs, 8);
+    zero.add(m->d_st, 1);
+    zero.add(m->d_bar, 1);
+    zero.add(m->d_phase_ns, 8);
+    zero.add(m->d_lvl, 8);
+    zero.add(m->d_pb_done, m->n_pb);
+    rest.add(m->d_bbox, 8);
+    rest.add(m->d_perm, n);
+    rest.add(m->d_inv, n);
+    rest.add(m->d_xs, n);
+    rest.add(m->d_dS, n);
+    rest.add(m->d_cur, n);
+    rest.add(m->d_E, n);
+    rest.add(m->d_pb_lo, m->n_pb);
+    rest.add(m->d_pb_hi, m->n_pb);
+    rest.add(m->d_pb_org, m->n_pb);
+    rest.add(m->d_xs_hi, n);
+    rest.add(m->d_xs_lo, n);
+    rest.add(m->d_sel, n);
+    rest.add(m->d_w, cap + 1);
+    rest.add(m->d_alpha, cap + 1);
+    rest.add(m->d_cx, cap + 1);
+    rest.add(m->d_cdf, 2 * (cap + 1));
+    rest.add(m->d_cid, cap + 1);
+    rest.add(m->d_phi, cap + 1);
+    rest.add(m->d_y, cap + 1);
+    rest.add(m->d_red, (size_t)4 * n_red + 6 * 256);
+    rest.add(m->d_gpart, (size_t)n_jt * cap + cap);
+    rest.add(m->d_vec, cap + 1);
+    rest.add(m->d_vec2, cap + 1);
+    rest.add(m->d_nb_cnt, m->n_pb);
+    rest.add(m->d_nb_list, (size_t)m->n_pb * cap);
+    rest.add(m->d_part, (size_t)m->n_chunk_max * n);
+    rest.add(m->d_pb_key, std::max(m->n_pb, 1024));
+    rest.add(m->d_pb_idx, std::max(m->n_pb, 1024));
+    rest.add(m->d_pred, (size_t)4 * kMaxPersistCTAs);
+    rest.add(m->d_nz_k, cap + 1);
+    rest.add(m->d_nz_v, cap + 1);
+    const size_t zbytes = zero.total();
+    char *arena = static_cast<char *>(dmalloc(zbytes + rest.total(), "mesh state"));
+    m->d_arena = arena;
+    zero.assign(arena);
+    rest.assign(arena + zbytes);
+    RBFD_CUDA(cudaMemsetAsync(arena, 0, zbytes, st));
+    m->d_G = dalloc<double>((size_t)cap * cap, "inverse factor");
+    m->d_Gt = dalloc<double>((size_t)cap * cap, "inverse factor, transposed");
+    m->h_st = static_cast<GreedyState *>(pinned_alloc(sizeof(GreedyState)));
+    m->h_bar = static_cast<GridBarrier *>(pinned_alloc(sizeof(GridBarrier)));
+    m->h_lvl = static_cast<double *>(pinned_alloc(8 * sizeof(double)));
+
+    // temporaries (one block, back to the pool after the one synchronisation below)
+    Carver tmp;
+    double *dx = nullptr, *dd = nullptr, *part = nullptr;
+    double4 *x4 = nullptr, *d4 = nullptr;
+    uint32_t *keys = nullptr;
+    if (!m->opt.inputs_on_device) {
+        tmp.add(dx, (size_t)n * m->dim);
+        tmp.add(dd, (size_t)n * m->dim);
+    }
+    tmp.add(x4, n);
+    tmp.add(d4, n);
+    tmp.add(part, 6 * 256);
+    tmp.add(keys, n);
+    void *temps = dmalloc(tmp.total(), "set-up temporaries");
+    tmp.assign(static_cast<char *>(temps));
     // inputs to device (one copy each when they are host buffers)
     const size_t bytes = sizeof(double) * (size_t)n * m->dim;
-    double *dx = nullptr, *dd = nullptr;
     if (m->opt.inputs_on_device) {
         dx = const_cast<double *>(xyz_s);
         dd = const_cast<double *>(dS);
     } else {
-        dx = dalloc<double>((size_t)n * m->dim, "surface coordinates");
-        dd = dalloc<double>((size_t)n * m->dim, "surface displacements");
         RBFD_CUDA(cudaMemcpyAsync(dx, xyz_s, bytes, cudaMemcpyHostToDevice, st));
         RBFD_CUDA(cudaMemcpyAsync(dd, dS, bytes, cudaMemcpyHostToDevice, st));
     }
-    double4 *x4 = dalloc<double4>(n, "surface x4");
-    double4 *d4 = dalloc<double4>(n, "surface d4");
     k_unpack<<<cdiv(n, 256), 256, 0, st>>>(dx, dd, n, m->dim, x4, d4);
     RBFD_CUDA(cudaGetLastError());
-    // temporaries are returned to the pool after the one synchronisation below
-    std::vector<void *> temps = {x4, d4};
-    if (!m->opt.inputs_on_device) {
-        temps.push_back(dx);
-        temps.push_back(dd);
-    }
-    m->d_misc = dalloc<uint32_t>(16, "counters");
-    RBFD_CUDA(cudaMemsetAsync(m->d_misc, 0, 16 * sizeof(uint32_t), st));
-    m->d_bbox = dalloc<double>(8, "bbox");
-    // bounding box -> Morton keys -> stable radix sort -> permutation
+    // bounding box -> Morton keys -> stable sort -> permutation
     const int nbb = std::min<int>(cdiv(n, 256), 256);
-    double *part = dalloc<double>(6 * 256, "bbox partials");
     k_bbox_partial<<<nbb, 256, 0, st>>>(x4, n, part);
     k_bbox_final<<<1, 192, 0, st>>>(part, nbb, m->d_bbox);
-    temps.push_back(part);
-    uint32_t *keys = dalloc<uint32_t>(n, "morton keys");
-    temps.push_back(keys);
-    m->d_perm = dalloc<uint32_t>(n, "permutation");
-    m->d_inv = dalloc<uint32_t>(n, "inverse permutation");
     morton_keys_f64_dev(x4, n, m->dim, m->d_bbox, keys, m->d_perm, st);
     radix_sort_pairs(keys, m->d_perm, n, m->dim == 2 ? 32 : 30, m->sort, st);
-    m->d_xs = dalloc<double4>(n, "sorted surface");
-    m->d_dS = dalloc<double4>(n, "sorted displacement");
-    m->d_cur = dalloc<double4>(n, "level target");
-    m->d_E = dalloc<double4>(n, "surface error");
     k_gather_sorted<<<cdiv(n, 256), 256, 0, st>>>(m->d_perm, n, x4, d4, m->d_xs, m->d_dS, m->d_inv);
     RBFD_CUDA(cudaGetLastError());
     // point blocks
-    m->n_pb = (int)cdiv(n, kPB);
-    m->d_pb_lo = dalloc<double4>(m->n_pb, "block lo");
-    m->d_pb_hi = dalloc<double4>(m->n_pb, "block hi");
-    m->d_pb_org = dalloc<double4>(m->n_pb, "block origin");
-    m->d_xs_hi = dalloc<float4>(n, "surface hi");
-    m->d_xs_lo = dalloc<float4>(n, "surface lo");
     k_point_blocks<<<m->n_pb, kPB, 0, st>>>(m->d_xs, n, m->d_pb_lo, m->d_pb_hi, m->d_pb_org, m->d_xs_hi, m->d_xs_lo);
     RBFD_CUDA(cudaGetLastError());
-
-    // greedy workspace
-    int64_t cap = m->opt.nc_cap > 0 ? m->opt.nc_cap : 32768;
-    cap = std::min<int64_t>(cap, n);
-    m->cap = (int)cap;
-    m->d_sel = dalloc<unsigned char>(n, "selected flags");
-    m->d_G = dalloc<double>((size_t)cap * cap, "inverse factor");
-    m->d_w = dalloc<double4>(cap + 1, "w");
-    m->d_alpha = dalloc<double4>(cap + 1, "alpha");
-    m->d_cx = dalloc<double4>(cap + 1, "control coordinates");
-    m->d_cdf = dalloc<float4>(2 * (cap + 1), "control coordinates, double-float");
-    m->d_cid = dalloc<uint32_t>(cap + 1, "control ids");
-    m->d_phi = dalloc<double>(cap + 1, "phi column");
-    m->d_y = dalloc<double>(cap + 1, "y");
-    const int n_red = (int)cdiv(cap + 1, kYWarps) + 8;
-    m->d_red = dalloc<double>((size_t)4 * n_red + 6 * 256, "reductions");
-    const int n_jt = (int)cdiv(cap + 1, kJT);
-    m->d_gpart = dalloc<double>((size_t)n_jt * cap + cap, "column partials");
-    m->d_vec = dalloc<double4>(cap + 1, "refinement r");
-    m->d_vec2 = dalloc<double4>(cap + 1, "refinement z");
-    m->d_nb_cnt = dalloc<uint32_t>(m->n_pb, "block list counts");
-    m->d_nb_list = dalloc<uint32_t>((size_t)m->n_pb * cap, "block lists");
-    m->n_chunk_max = std::max(128, (kTargetCTAs + m->n_pb - 1) / m->n_pb);
-    m->d_part = dalloc<double4>((size_t)m->n_chunk_max * n, "sweep partials");
-    m->d_pb_done = dalloc<unsigned int>(m->n_pb, "block counters");
-    RBFD_CUDA(cudaMemsetAsync(m->d_pb_done, 0, sizeof(unsigned int) * m->n_pb, st));
-    m->d_pb_key = dalloc<double>(std::max(m->n_pb, 1024), "block keys");
-    m->d_pb_idx = dalloc<int>(std::max(m->n_pb, 1024), "block argmax");
-    m->d_pairs = dalloc<unsigned long long>(8, "pair counters");
-    RBFD_CUDA(cudaMemsetAsync(m->d_pairs, 0, 8 * sizeof(unsigned long long), st));
-    m->d_st = dalloc<GreedyState>(1, "greedy state");
-    RBFD_CUDA(cudaMemsetAsync(m->d_st, 0, sizeof(GreedyState), st));
-    m->d_bar = dalloc<GridBarrier>(1, "grid barrier");
-    RBFD_CUDA(cudaMemsetAsync(m->d_bar, 0, sizeof(GridBarrier), st));
-    m->d_pred = dalloc<double>((size_t)4 * kMaxPersistCTAs, "persistent reductions");
-    m->d_Gt = dalloc<double>((size_t)cap * cap, "inverse factor, transposed");
-    m->d_nz_k = dalloc<uint32_t>(cap + 1, "phi nonzero ids");
-    m->d_nz_v = dalloc<double>(cap + 1, "phi nonzero values");
-    m->d_phase_ns = dalloc<unsigned long long>(8, "phase timing");
-    RBFD_CUDA(cudaMemsetAsync(m->d_phase_ns, 0, 8 * sizeof(unsigned long long), st));
-    m->h_st = static_cast<GreedyState *>(pinned_alloc(sizeof(GreedyState)));
-    m->h_bar = static_cast<GridBarrier *>(pinned_alloc(sizeof(GridBarrier)));
-    m->h_lvl = static_cast<double *>(pinned_alloc(8 * sizeof(double)));
-    m->d_lvl = dalloc<double>(8, "level scalars");
-    RBFD_CUDA(cudaMemsetAsync(m->d_lvl, 0, 8 * sizeof(double), st));
 
     m->stats.launches += 6;  // unpack, bbox x2, morton, gather, point blocks
     // S0 = max_i |dS_i| and the surface box (the one synchronisation of the set-up)
     m->S0 = std::sqrt(maxnorm(m, m->d_dS, nullptr, m->h_sbox));
     m->stats.launches += 1;
-    for (void *p : temps) dfree(p);
+    dfree(temps);
 }
 
 namespace {

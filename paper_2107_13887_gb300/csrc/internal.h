@@ -218,6 +218,7 @@ struct rbfd_mesh {
     int64_t vreg_n = 0;
     double4 *d_vreg = nullptr;     // sorted points (x, y, z, d)
     uint32_t *d_vreg_orig = nullptr;
+    void *d_arena = nullptr;       // one block holding the fixed buffers of the set-up
     uint32_t *d_misc = nullptr;    // small counters
     double *d_bbox = nullptr;      // 8 doubles
     // volume staged ahead of the greedy (copies, packing, Morton order of every
