@@ -242,7 +242,8 @@ def run_ours(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
     # each case gets its own stream so that the batch calls overlap them
-    streams = [torch.cuda.Stream(dev) for _ in cases]
+    # (high priority: the library's staging streams, at the lowest, fill in behind the greedy)
+    streams = [torch.cuda.Stream(dev, priority=-1) for _ in cases]
 
     # the meshes are created side by side as well (the binding releases the
     # interpreter lock during library calls)

@@ -183,14 +183,21 @@ void Profiler::end(int kind, cudaEvent_t a, cudaStream_t st, int n_launches) {
 }
 
 void Profiler::flush() {
+    // pairs whose end has not been reached yet (work on another stream) stay pending
+    std::vector<Pending> keep;
     for (auto &p : pend) {
+        if (cudaEventQuery(p.b) == cudaErrorNotReady) {
+            cudaGetLastError();
+            keep.push_back(p);
+            continue;
+        }
         float ms_ = 0.f;
         if (cudaEventElapsedTime(&ms_, p.a, p.b) == cudaSuccess) ms[p.kind] += ms_;
         else cudaGetLastError();
         free_ev.push_back(p.a);
         free_ev.push_back(p.b);
     }
-    pend.clear();
+    pend.swap(keep);
 }
 
 void Profiler::release() {
@@ -372,7 +379,11 @@ int rbfd_create(rbfd_mesh **out, int dim, int64_t n_s, const double *xyz_s, cons
         if (o.stream) {
             m->stream = static_cast<cudaStream_t>(o.stream);
         } else {
-            RBFD_CUDA(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking));
+            // the highest priority: the greedy's launches go ahead of the
+            // volume work the library queues on its staging streams
+            int lo = 0, hi = 0;
+            RBFD_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            RBFD_CUDA(cudaStreamCreateWithPriority(&m->stream, cudaStreamNonBlocking, hi));
             m->own_stream = true;
         }
         RBFD_CUDA(cudaEventCreate(&m->ev0));
@@ -619,7 +630,7 @@ int rbfd_greedy_deform_batch(rbfd_mesh **meshes, int n, const int64_t *n_v, cons
         // the volume's copies, packing and Morton order run on a second
         // stream while the greedy runs
         deform_check(m, n_v[i], xyz_v[i], dv, D[i], k[i], out[i]);
-        rbfd::volume_stage(m, n_v[i], xyz_v[i], dv, false);
+        rbfd::volume_stage(m, n_v[i], xyz_v[i], dv, false, D[i], k[i]);
         bool notconv = false;
         try {
             rbfd::greedy_run(m);

@@ -593,70 +593,84 @@ void morton_order(rbfd_mesh *m, int64_t n, const double4 *vin, double4 *vsorted,
 // Steps (3) and (4) of the volume update for nV Morton-sorted points vpos
 // (caller indices vorig): per level, compaction to d < D_l and the fused
 // evaluation into the accumulator; then the scatter into dout (caller order).
-void deform_levels(rbfd_mesh *m, int64_t nV, const double4 *vpos, const uint32_t *vorig, const double *Dl, int L,
-                   void *dout, bool f64) {
-    cudaStream_t st = m->stream;
-    const int dim = m->dim;
+// The parts of steps (3) and (4) of the volume update for nV Morton-sorted
+// points vpos (caller indices vorig), each on stream st: clear the
+// accumulator (and make the float4 copy for the FP32-input sweep), then per
+// level the compaction to d < D_l and the fused evaluation into the
+// accumulator, then the scatter into dout (caller order).
+bool deform_fast(const rbfd_mesh *m, bool f64) { return m->opt.precision != RBFD_FP64 && !f64 && m->d_vpos4; }
+
+void deform_acc_init(rbfd_mesh *m, int64_t nV, const double4 *vpos, bool f64, cudaStream_t st) {
     RBFD_CUDA(cudaMemsetAsync(m->d_vacc, 0, sizeof(double4) * nV, st));
-    // mixed precision with FP32 inputs: the FP32-input sweep on a float4 copy
-    const bool fast = m->opt.precision != RBFD_FP64 && !f64 && m->d_vpos4;
-    if (fast) {
+    if (deform_fast(m, f64)) {
         k_to_f4<<<cdiv(nV, 256), 256, 0, st>>>(vpos, nV, m->d_vpos4);
         m->stats.launches += 1;
     }
+}
+
+void deform_one_level(rbfd_mesh *m, int l, int64_t nV, const double4 *vpos, double Dl, bool f64, cudaStream_t st,
+                      SortScratch &ss) {
+    const Level &Lv = m->levels[l];
+    if (Lv.nc == 0 || !(Dl > 0.0)) return;
+    const bool fast = deform_fast(m, f64);
     const int mode = m->opt.precision == RBFD_FP64 ? 0 : (fast ? 2 : 1);
-    // (3) per level: d < D_l, then the fused evaluation; the list length
-    // stays on the device (the sweep reads it), so no level waits for the host
-    for (int l = 0; l < L; ++l) {
-        const Level &Lv = m->levels[l];
-        if (Lv.nc == 0 || !(Dl[l] > 0.0)) continue;
-        k_flag_below<<<cdiv(nV, 256), 256, 0, st>>>(vpos, nullptr, nV, Dl[l], m->d_vflag);
-        exclusive_scan_u32(m->d_vflag, m->d_vscan, (size_t)nV, &m->d_misc[5], m->sort, st);
-        k_compact<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vflag, m->d_vscan, nV, m->d_vlist);
-        k_count_points<<<1, 32, 0, st>>>(&m->d_misc[5], m->d_pairs + 7);
-        VolArgs a{};
-        a.n_list = nV;  // upper bound; the exact count is read on the device
-        a.n_list_dev = &m->d_misc[5];
-        a.list = m->d_vlist;
-        a.vpos = vpos;
-        a.vacc = m->d_vacc;
-        a.cx = Lv.d_cx;
-        a.alpha = Lv.d_alpha;
-        a.cell_start = Lv.d_cell_start;
-        a.cell_ctrl = Lv.d_cell_ctrl;
-        a.g0 = Lv.g0;
-        a.h = Lv.h;
-        a.gd = Lv.gdim;
-        a.R = Lv.R;
-        a.Dl = Dl[l];
-        double inv = 1.0 / Lv.R;
-        a.invR_hi = (float)inv;
-        a.invR_lo = (float)(inv - (double)a.invR_hi);
-        a.pairs = m->d_pairs + 2;
-        if (fast) {
-            a.vp4 = m->d_vpos4;
-            a.cdf = Lv.d_cdf;
-            a.adf = Lv.d_adf;
-            a.g0f[0] = (float)Lv.g0.x;
-            a.g0f[1] = (float)Lv.g0.y;
-            a.g0f[2] = (float)Lv.g0.z;
-            a.hf = (float)Lv.h;
-            a.Rf = (float)Lv.R;
-            a.invDlf = (float)(1.0 / Dl[l]);
-        }
-        m->stats.launches += 4;  // flags, compaction, count (+ scan counted in the scan)
-        cudaEvent_t e0 = m->prof.begin(st);
-        launch_vol(dim, m->opt.basis, mode, cdiv(nV, kThreads), a, st);
-        RBFD_CUDA(cudaGetLastError());
-        m->prof.end(kProfVol, e0, st, 1);
-        m->stats.launches += 1;
+    // d < D_l, then the fused evaluation; the list length stays on the
+    // device (the sweep reads it), so no level waits for the host
+    k_flag_below<<<cdiv(nV, 256), 256, 0, st>>>(vpos, nullptr, nV, Dl, m->d_vflag);
+    exclusive_scan_u32(m->d_vflag, m->d_vscan, (size_t)nV, &m->d_misc[5], ss, st);
+    k_compact<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vflag, m->d_vscan, nV, m->d_vlist);
+    k_count_points<<<1, 32, 0, st>>>(&m->d_misc[5], m->d_pairs + 7);
+    VolArgs a{};
+    a.n_list = nV;  // upper bound; the exact count is read on the device
+    a.n_list_dev = &m->d_misc[5];
+    a.list = m->d_vlist;
+    a.vpos = vpos;
+    a.vacc = m->d_vacc;
+    a.cx = Lv.d_cx;
+    a.alpha = Lv.d_alpha;
+    a.cell_start = Lv.d_cell_start;
+    a.cell_ctrl = Lv.d_cell_ctrl;
+    a.g0 = Lv.g0;
+    a.h = Lv.h;
+    a.gd = Lv.gdim;
+    a.R = Lv.R;
+    a.Dl = Dl;
+    double inv = 1.0 / Lv.R;
+    a.invR_hi = (float)inv;
+    a.invR_lo = (float)(inv - (double)a.invR_hi);
+    a.pairs = m->d_pairs + 2;
+    if (fast) {
+        a.vp4 = m->d_vpos4;
+        a.cdf = Lv.d_cdf;
+        a.adf = Lv.d_adf;
+        a.g0f[0] = (float)Lv.g0.x;
+        a.g0f[1] = (float)Lv.g0.y;
+        a.g0f[2] = (float)Lv.g0.z;
+        a.hf = (float)Lv.h;
+        a.Rf = (float)Lv.R;
+        a.invDlf = (float)(1.0 / Dl);
     }
-    // (4) back to the caller's order
-    if (fast)
-        k_scatter_out_df<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vacc, vorig, nV, dim, static_cast<float *>(dout));
-    else
-        k_scatter_out<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vacc, vorig, nV, dim, f64 ? 1 : 0, dout);
+    m->stats.launches += 4;  // flags, compaction, count (+ scan counted in the scan)
+    cudaEvent_t e0 = m->prof.begin(st);
+    launch_vol(m->dim, m->opt.basis, mode, cdiv(nV, kThreads), a, st);
     RBFD_CUDA(cudaGetLastError());
+    m->prof.end(kProfVol, e0, st, 1);
+    m->stats.launches += 1;
+}
+
+void deform_scatter(rbfd_mesh *m, int64_t nV, const uint32_t *vorig, void *dout, bool f64, cudaStream_t st) {
+    if (deform_fast(m, f64))
+        k_scatter_out_df<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vacc, vorig, nV, m->dim, static_cast<float *>(dout));
+    else
+        k_scatter_out<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vacc, vorig, nV, m->dim, f64 ? 1 : 0, dout);
+    RBFD_CUDA(cudaGetLastError());
+}
+
+void deform_levels(rbfd_mesh *m, int64_t nV, const double4 *vpos, const uint32_t *vorig, const double *Dl, int L,
+                   void *dout, bool f64) {
+    deform_acc_init(m, nV, vpos, f64, m->stream);
+    for (int l = 0; l < L; ++l) deform_one_level(m, l, nV, vpos, Dl[l], f64, m->stream, m->sort);
+    deform_scatter(m, nV, vorig, dout, f64, m->stream);
 }
 
 }  // namespace
@@ -676,8 +690,11 @@ cudaStream_t side_acquire(int dev) {
                 return s;
             }
     }
+    // the lowest priority: the staged volume work fills the SMs the greedy leaves
     cudaStream_t s = nullptr;
-    RBFD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    int lo = 0, hi = 0;
+    RBFD_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    RBFD_CUDA(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, lo));
     return s;
 }
 
@@ -714,7 +731,7 @@ VolumeIO volume_io(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v
 }
 }  // namespace
 
-void volume_stage(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64) {
+void volume_stage(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64, double D, double k) {
     volume_unstage(m);
     if (n_v <= 0 || !d_v) return;  // (wall distances on the device are capped by the levels' D_l)
     if (!m->vstream) m->vstream = side_acquire(m->device);
@@ -732,15 +749,32 @@ void volume_stage(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v,
     double4 *vpos = reinterpret_cast<double4 *>(m->d_vpos);
     k_vol_pack<<<cdiv(n_v, 256), 256, 0, vs>>>(io.x, io.d, n_v, m->dim, f64 ? 1 : 0, vin);
     morton_order(m, n_v, vin, vpos, m->d_vorig, vs, m->d_vred, m->d_vbox, m->vsort);
+    deform_acc_init(m, n_v, vpos, f64, vs);
     RBFD_CUDA(cudaEventRecord(m->ev_vdone, vs));
     RBFD_CUDA(cudaGetLastError());
     m->stats.launches += 1;
+    // D_0 = k max|dS_0| (capped at D) is known now: max|dS_0| = S0
+    double d0 = (k > 0.0) ? k * m->S0 : D;
+    if (k > 0.0 && D > 0.0 && d0 > D) d0 = D;
+    m->vst_D0 = d0;
+    m->vst_l0 = false;
     m->vst_ok = true;
     m->vst_n = n_v;
     m->vst_x = xyz_v;
     m->vst_d = d_v;
     m->vst_f64 = f64;
     m->vst_dout = io.out;  // (null for device outputs: the caller's array)
+}
+
+void volume_level_early(rbfd_mesh *m, int l) {
+    if (!m->vst_ok || l != 0 || m->vst_l0 || m->levels.empty() || !(m->vst_D0 > 0.0)) return;
+    // the level's controls, weights and cell grid are queued on the mesh's stream
+    RBFD_CUDA(cudaEventRecord(m->ev_vfork, m->stream));
+    RBFD_CUDA(cudaStreamWaitEvent(m->vstream, m->ev_vfork, 0));
+    deform_one_level(m, 0, m->vst_n, reinterpret_cast<const double4 *>(m->d_vpos), m->vst_D0, m->vst_f64, m->vstream,
+                     m->vsort);
+    RBFD_CUDA(cudaEventRecord(m->ev_vdone, m->vstream));
+    m->vst_l0 = true;
 }
 
 void volume_unstage(rbfd_mesh *m) {
@@ -789,9 +823,21 @@ void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, b
         m->vst_ok = false;
         RBFD_CUDA(cudaStreamWaitEvent(st, m->ev_vdone, 0));
         void *dout = host ? m->vst_dout : out;
-        if (Dmax > 0.0) deform_levels(m, n_v, reinterpret_cast<const double4 *>(m->d_vpos), m->d_vorig, Dl.data(), L,
-                                      dout, f64);
-        else RBFD_CUDA(cudaMemsetAsync(dout, 0, (size_t)n_v * dim * es, st));
+        const double4 *vs_pos = reinterpret_cast<const double4 *>(m->d_vpos);
+        // level 0 may have run on the staging stream during the greedy (with
+        // D_0 from S0; the same value as from the level, checked here)
+        bool l0 = m->vst_l0;
+        if (l0 && !(L > 0 && Dl[0] == m->vst_D0)) {
+            deform_acc_init(m, n_v, vs_pos, f64, st);
+            l0 = false;
+        }
+        m->vst_l0 = false;
+        if (Dmax > 0.0) {
+            for (int l = l0 ? 1 : 0; l < L; ++l) deform_one_level(m, l, n_v, vs_pos, Dl[l], f64, st, m->sort);
+            deform_scatter(m, n_v, m->d_vorig, dout, f64, st);
+        } else {
+            RBFD_CUDA(cudaMemsetAsync(dout, 0, (size_t)n_v * dim * es, st));
+        }
         if (host) RBFD_CUDA(cudaMemcpyAsync(out, dout, (size_t)n_v * dim * es, cudaMemcpyDeviceToHost, st));
         RBFD_CUDA(cudaEventRecord(m->ev1, st));
         RBFD_CUDA(cudaEventSynchronize(m->ev1));

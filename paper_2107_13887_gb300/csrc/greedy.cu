@@ -1460,6 +1460,7 @@ void greedy_run(rbfd_mesh *m) {
         build_control_grid(m, L, m->h_sbox);
         if (L.status != RBFD_OK) final_status = RBFD_ENOTCONV;
         m->levels.push_back(std::move(L));
+        volume_level_early(m, l);  // (a staged volume's sweep of this level, if it can start now)
         // multi-level subspace: the next level interpolates this level's error
         RBFD_CUDA(cudaMemcpyAsync(m->d_cur, m->d_E, sizeof(double4) * m->n_s, cudaMemcpyDeviceToDevice, st));
     }

@@ -234,6 +234,8 @@ struct rbfd_mesh {
     const void *vst_x = nullptr, *vst_d = nullptr;
     bool vst_f64 = false;
     void *vst_dout = nullptr;      // device output (the staging buffer for host outputs)
+    double vst_D0 = 0.0;           // D_0 of the staged call
+    bool vst_l0 = false;           // level 0 already swept on the staging stream
 };
 
 namespace rbfd {
@@ -255,7 +257,11 @@ void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, b
 // packing and the Morton order of every point, on a second stream that
 // starts after the work queued so far on the mesh's stream (the greedy can
 // run meanwhile).  Only with wall distances given.
-void volume_stage(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64);
+void volume_stage(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64, double D, double k);
+// After level l is saved: with a staged volume, queue that level's volume
+// sweep on the staging stream (level 0 only: its D_0 follows from S0), so it
+// runs while the greedy continues.
+void volume_level_early(rbfd_mesh *m, int l);
 // Drop a staged volume that will not be used (the mesh's stream waits for it).
 void volume_unstage(rbfd_mesh *m);
 // Return the staging stream and events (mesh destruction).
