@@ -706,7 +706,7 @@ struct VolumeIO {
 };
 
 VolumeIO volume_io(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, void *out, bool f64,
-                   cudaStream_t st) {
+                   cudaStream_t st, bool copy = true) {
     VolumeIO io{xyz_v, d_v, out};
     if (m->opt.inputs_on_device || n_v <= 0) return io;
     const int dim = m->dim;
@@ -723,8 +723,10 @@ VolumeIO volume_io(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v
     void *sx = base;
     void *sd = base + (size_t)n_v * dim * es;
     io.out = base + (size_t)n_v * dim * es + (((size_t)n_v * es + 255) / 256) * 256;
-    RBFD_CUDA(cudaMemcpyAsync(sx, xyz_v, (size_t)n_v * dim * es, cudaMemcpyHostToDevice, st));
-    if (d_v) RBFD_CUDA(cudaMemcpyAsync(sd, d_v, (size_t)n_v * es, cudaMemcpyHostToDevice, st));
+    if (copy) {
+        RBFD_CUDA(cudaMemcpyAsync(sx, xyz_v, (size_t)n_v * dim * es, cudaMemcpyHostToDevice, st));
+        if (d_v) RBFD_CUDA(cudaMemcpyAsync(sd, d_v, (size_t)n_v * es, cudaMemcpyHostToDevice, st));
+    }
     io.x = sx;
     io.d = d_v ? sd : nullptr;
     return io;
@@ -741,18 +743,15 @@ void volume_stage(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v,
     if (!m->d_vbox) m->d_vbox = dalloc<double>(8, "volume box");
     if (!m->vsort.launches) m->vsort.launches = &m->stats.launches;
     reserve_volume(m, (size_t)n_v);
-    cudaStream_t vs = m->vstream;
-    RBFD_CUDA(cudaEventRecord(m->ev_vfork, m->stream));  // (the inputs are ready in the caller's order)
-    RBFD_CUDA(cudaStreamWaitEvent(vs, m->ev_vfork, 0));
-    const VolumeIO io = volume_io(m, n_v, xyz_v, d_v, nullptr, f64, vs);
-    double4 *vin = reinterpret_cast<double4 *>(m->d_vin);
-    double4 *vpos = reinterpret_cast<double4 *>(m->d_vpos);
-    k_vol_pack<<<cdiv(n_v, 256), 256, 0, vs>>>(io.x, io.d, n_v, m->dim, f64 ? 1 : 0, vin);
-    morton_order(m, n_v, vin, vpos, m->d_vorig, vs, m->d_vred, m->d_vbox, m->vsort);
-    deform_acc_init(m, n_v, vpos, f64, vs);
-    RBFD_CUDA(cudaEventRecord(m->ev_vdone, vs));
-    RBFD_CUDA(cudaGetLastError());
-    m->stats.launches += 1;
+    // the staging stream starts from here (the inputs are ready in the
+    // caller's order); its work is queued by volume_stage_enqueue, which the
+    // greedy calls once its first launch is on its way
+    RBFD_CUDA(cudaEventRecord(m->ev_vfork, m->stream));
+    RBFD_CUDA(cudaStreamWaitEvent(m->vstream, m->ev_vfork, 0));
+    const VolumeIO io = volume_io(m, n_v, xyz_v, d_v, nullptr, f64, m->vstream, false);
+    m->vst_io_x = io.x;
+    m->vst_io_d = io.d;
+    m->vst_queued = false;
     // D_0 = k max|dS_0| (capped at D) is known now: max|dS_0| = S0
     double d0 = (k > 0.0) ? k * m->S0 : D;
     if (k > 0.0 && D > 0.0 && d0 > D) d0 = D;
@@ -766,7 +765,31 @@ void volume_stage(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v,
     m->vst_dout = io.out;  // (null for device outputs: the caller's array)
 }
 
+void volume_stage_enqueue(rbfd_mesh *m) {
+    if (!m->vst_ok || m->vst_queued) return;
+    cudaStream_t vs = m->vstream;
+    const int64_t n_v = m->vst_n;
+    const bool f64 = m->vst_f64;
+    if (!m->opt.inputs_on_device) {  // host inputs: into the staging buffer
+        const size_t es = f64 ? sizeof(double) : sizeof(float);
+        RBFD_CUDA(cudaMemcpyAsync(const_cast<void *>(m->vst_io_x), m->vst_x, (size_t)n_v * m->dim * es,
+                                  cudaMemcpyHostToDevice, vs));
+        RBFD_CUDA(cudaMemcpyAsync(const_cast<void *>(m->vst_io_d), m->vst_d, (size_t)n_v * es, cudaMemcpyHostToDevice,
+                                  vs));
+    }
+    double4 *vin = reinterpret_cast<double4 *>(m->d_vin);
+    double4 *vpos = reinterpret_cast<double4 *>(m->d_vpos);
+    k_vol_pack<<<cdiv(n_v, 256), 256, 0, vs>>>(m->vst_io_x, m->vst_io_d, n_v, m->dim, f64 ? 1 : 0, vin);
+    morton_order(m, n_v, vin, vpos, m->d_vorig, vs, m->d_vred, m->d_vbox, m->vsort);
+    deform_acc_init(m, n_v, vpos, f64, vs);
+    RBFD_CUDA(cudaEventRecord(m->ev_vdone, vs));
+    RBFD_CUDA(cudaGetLastError());
+    m->stats.launches += 1;
+    m->vst_queued = true;
+}
+
 void volume_level_early(rbfd_mesh *m, int l) {
+    volume_stage_enqueue(m);
     if (!m->vst_ok || l != 0 || m->vst_l0 || m->levels.empty() || !(m->vst_D0 > 0.0)) return;
     // the level's controls, weights and cell grid are queued on the mesh's stream
     RBFD_CUDA(cudaEventRecord(m->ev_vfork, m->stream));
@@ -780,7 +803,8 @@ void volume_level_early(rbfd_mesh *m, int l) {
 void volume_unstage(rbfd_mesh *m) {
     if (!m->vst_ok) return;
     m->vst_ok = false;
-    RBFD_CUDA(cudaStreamWaitEvent(m->stream, m->ev_vdone, 0));  // its buffers are reused after this
+    // its buffers are reused after this (nothing was queued: the fork is all)
+    if (m->vst_queued) RBFD_CUDA(cudaStreamWaitEvent(m->stream, m->ev_vdone, 0));
 }
 
 void volume_stage_release(rbfd_mesh *m) {
@@ -817,6 +841,7 @@ void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, b
     }
     const bool host = !m->opt.inputs_on_device;
     if (m->vst_ok && m->vst_n == n_v && m->vst_x == xyz_v && m->vst_d == d_v && m->vst_f64 == f64) {
+        volume_stage_enqueue(m);
         // staged ahead: every point packed and Morton-sorted; the levels'
         // reductions d < D_l run over all of them (points beyond every D_l
         // stay 0)

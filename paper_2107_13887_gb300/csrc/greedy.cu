@@ -1339,6 +1339,7 @@ void greedy_run(rbfd_mesh *m) {
                     newton_run_level(m, L.R, L.tau, ctas);
                     m->prof.end(kProfNewton, e0, st, 1);
                     enqueue_close(std::min(m->newton_cols, m->cap), true);
+                    volume_stage_enqueue(m);  // (a staged volume: while this level runs)
                     read_state_bar(m);
                     m->prof.flush();
                     if (m->h_bar->err) fail(RBFD_ETIMEOUT, "Newton greedy: a grid barrier exceeded its wait bound");
@@ -1370,6 +1371,7 @@ void greedy_run(rbfd_mesh *m) {
                 cudaEvent_t e0 = m->prof.begin(st);
                 persist_run_level(m, L.R, L.tau, ctas);
                 m->prof.end(kProfPersist, e0, st, 1);
+                volume_stage_enqueue(m);  // (a staged volume: while this level runs)
                 m->stats.persist_ctas = ctas;
                 read_state_bar(m);
                 m->prof.flush();

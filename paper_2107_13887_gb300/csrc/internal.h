@@ -234,6 +234,8 @@ struct rbfd_mesh {
     const void *vst_x = nullptr, *vst_d = nullptr;
     bool vst_f64 = false;
     void *vst_dout = nullptr;      // device output (the staging buffer for host outputs)
+    const void *vst_io_x = nullptr, *vst_io_d = nullptr;  // device copies of the inputs
+    bool vst_queued = false;       // the staging work is on the staging stream
     double vst_D0 = 0.0;           // D_0 of the staged call
     bool vst_l0 = false;           // level 0 already swept on the staging stream
 };
@@ -262,6 +264,9 @@ void volume_stage(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v,
 // sweep on the staging stream (level 0 only: its D_0 follows from S0), so it
 // runs while the greedy continues.
 void volume_level_early(rbfd_mesh *m, int l);
+// Queue the staging work of a staged volume (copies, packing, Morton order)
+// on its stream, if not yet done: the greedy calls it after its first launch.
+void volume_stage_enqueue(rbfd_mesh *m);
 // Drop a staged volume that will not be used (the mesh's stream waits for it).
 void volume_unstage(rbfd_mesh *m);
 // Return the staging stream and events (mesh destruction).
