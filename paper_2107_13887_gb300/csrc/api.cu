@@ -2,7 +2,10 @@
 // point validates its arguments, converts internal errors into an
 // rbfd_status, and records a thread-local message for rbfd_last_error().
 #include <cmath>
+#include <condition_variable>
 #include <cstdlib>
+#include <deque>
+#include <functional>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -217,6 +220,8 @@ void mesh_free(rbfd_mesh *m) {
     cudaSetDevice(m->device);
     if (m->stream) cudaStreamSynchronize(m->stream);
     rbfd::volume_stage_release(m);
+    if (m->prep_temps) dfree(m->prep_temps);
+    if (m->h_prep) pinned_free(m->h_prep);
     for (auto &L : m->levels) rbfd::level_free(L);
     // (the mesh's fixed buffers are carved out of d_arena)
     void *ptrs[] = {m->d_arena, m->d_G, m->d_Gt, m->d_vin, m->d_vpos, m->d_vorig, m->d_vflag, m->d_vscan,
@@ -267,6 +272,61 @@ bool is_device_ptr(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Host threads for the batch calls, kept for the process (starting a thread
+// costs tens of microseconds, waking a waiting one a few).
+class WorkerPool {
+public:
+    static WorkerPool &get() {
+        static WorkerPool *p = new WorkerPool;  // (never destroyed: its threads wait for the process to end)
+        return *p;
+    }
+    // run task(i) for 1 <= i < n on the pool, task(0) on the calling thread, and wait
+    void run(int n, const std::function<void(int)> &task) {
+        if (n <= 0) return;
+        int left = n - 1;
+        std::mutex done_mu;
+        std::condition_variable done_cv;
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            while (idle_ < n - 1 + (int)queue_.size()) {
+                std::thread([this] { loop(); }).detach();
+                ++idle_;
+            }
+            for (int i = 1; i < n; ++i)
+                queue_.push_back([&, i] {
+                    task(i);
+                    std::lock_guard<std::mutex> dl(done_mu);
+                    if (--left == 0) done_cv.notify_one();
+                });
+        }
+        cv_.notify_all();
+        task(0);
+        std::unique_lock<std::mutex> dl(done_mu);
+        done_cv.wait(dl, [&] { return left == 0; });
+    }
+
+private:
+    void loop() {
+        for (;;) {
+            std::function<void()> job;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [this] { return !queue_.empty(); });
+                job = std::move(queue_.front());
+                queue_.pop_front();
+                --idle_;
+            }
+            job();
+            std::lock_guard<std::mutex> lk(mu_);
+            ++idle_;
+        }
+    }
+    std::mutex mu_;
+    std::condition_variable cv_;
+    std::deque<std::function<void()>> queue_;
+    int idle_ = 0;
+};
+
 // Run f(i) for i < n on n host threads (the calling thread takes i = 0);
 // returns the statuses, and the message of the first failure in *msg.
 template <typename F>
@@ -277,10 +337,7 @@ int run_batch(int n, F &&f, const char *name) {
         rc[i] = guarded([&] { f(i); });
         if (rc[i] != RBFD_OK) msg[i] = rbfd::g_last_error;
     };
-    std::vector<std::thread> th;
-    for (int i = 1; i < n; ++i) th.emplace_back(body, i);
-    if (n > 0) body(0);
-    for (auto &t : th) t.join();
+    WorkerPool::get().run(n, body);
     int worst = RBFD_OK;
     std::string wmsg;
     for (int i = 0; i < n; ++i) {

@@ -734,6 +734,7 @@ VolumeIO volume_io(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v
 }  // namespace
 
 void volume_stage(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64, double D, double k) {
+    mesh_ready(m);  // (S0 gives D_0)
     volume_unstage(m);
     if (n_v <= 0 || !d_v) return;  // (wall distances on the device are capped by the levels' D_l)
     if (!m->vstream) m->vstream = side_acquire(m->device);

@@ -1120,10 +1120,28 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     RBFD_CUDA(cudaGetLastError());
 
     m->stats.launches += 6;  // unpack, bbox x2, morton, gather, point blocks
-    // S0 = max_i |dS_i| and the surface box (the one synchronisation of the set-up)
-    m->S0 = std::sqrt(maxnorm(m, m->d_dS, nullptr, m->h_sbox));
+    // S0 = max_i |dS_i| and the surface box reach the host with the first
+    // call that needs them (mesh_ready): the set-up does not wait here
+    const int nbm = std::min<int>(cdiv(m->n_s, 256), 1024);
+    k_maxnorm<<<nbm, 256, 0, st>>>(m->d_dS, m->d_perm, m->n_s, m->dim, m->d_pb_key, m->d_pb_idx, &m->d_misc[0],
+                                   m->d_bbox + 6);
+    RBFD_CUDA(cudaGetLastError());
     m->stats.launches += 1;
-    dfree(temps);
+    m->h_prep = static_cast<double *>(pinned_alloc(8 * sizeof(double)));
+    RBFD_CUDA(cudaMemcpyAsync(m->h_prep, m->d_bbox, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RBFD_CUDA(cudaEventRecord(m->ev1, st));
+    m->prep_temps = temps;  // (back to the pool once the set-up has run)
+    m->prep_pending = true;
+}
+
+void mesh_ready(rbfd_mesh *m) {
+    if (!m->prep_pending) return;
+    RBFD_CUDA(cudaEventSynchronize(m->ev1));
+    m->S0 = std::sqrt(m->h_prep[6]);
+    std::memcpy(m->h_sbox, m->h_prep, 6 * sizeof(double));
+    dfree(m->prep_temps);
+    m->prep_temps = nullptr;
+    m->prep_pending = false;
 }
 
 namespace {
@@ -1140,6 +1158,7 @@ __global__ void k_gather_disp(const double *__restrict__ dS, const uint32_t *__r
 // and workspace are kept; the greedy results of the previous displacement are
 // dropped.
 void mesh_set_displacement(rbfd_mesh *m, const double *dS) {
+    mesh_ready(m);
     cudaStream_t st = m->stream;
     const int64_t n = m->n_s;
     const double *dd = dS;
@@ -1203,6 +1222,7 @@ void level_fetch(rbfd_mesh *m, Level &L) {
 }
 
 void greedy_run(rbfd_mesh *m) {
+    mesh_ready(m);
     cudaStream_t st = m->stream;
     for (auto &L : m->levels) level_free(L);
     m->levels.clear();

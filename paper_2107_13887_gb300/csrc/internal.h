@@ -219,6 +219,9 @@ struct rbfd_mesh {
     double4 *d_vreg = nullptr;     // sorted points (x, y, z, d)
     uint32_t *d_vreg_orig = nullptr;
     void *d_arena = nullptr;       // one block holding the fixed buffers of the set-up
+    bool prep_pending = false;     // the set-up's S0 and surface box not yet read (mesh_ready)
+    double *h_prep = nullptr;      // pinned: their copy
+    void *prep_temps = nullptr;    // the set-up's temporaries, freed by mesh_ready
     uint32_t *d_misc = nullptr;    // small counters
     double *d_bbox = nullptr;      // 8 doubles
     // volume staged ahead of the greedy (copies, packing, Morton order of every
@@ -272,6 +275,9 @@ void volume_unstage(rbfd_mesh *m);
 // Return the staging stream and events (mesh destruction).
 void volume_stage_release(rbfd_mesh *m);
 void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS);
+// Wait for the set-up queued by mesh_prepare and read S0 and the surface box
+// (first call only).
+void mesh_ready(rbfd_mesh *m);
 void mesh_set_displacement(rbfd_mesh *m, const double *dS);
 void volume_register(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v);
 void deform_registered(rbfd_mesh *m, double D, double k, float *out);
