@@ -32,7 +32,6 @@ import subprocess
 import sys
 import threading
 import time
-from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -245,22 +244,16 @@ def run_ours(args):
     # (high priority: the library's staging streams, at the lowest, fill in behind the greedy)
     streams = [torch.cuda.Stream(dev, priority=-1) for _ in cases]
 
-    # the meshes are created side by side as well (the binding releases the
-    # interpreter lock during library calls)
-    create_pool = ThreadPoolExecutor(max_workers=len(cases), initializer=torch.cuda.set_device, initargs=(local,))
-
     def one_step(src, record):
-        """Both cases as one batch: create (one host thread per case; the
-        spatial set-up of the surface), then greedy + deform (each case on its
-        own host thread and stream, side by side).  Returns the meshes; their
-        counters are read and they are destroyed after the timed region."""
-        def make(q):
-            c, d, s_ = cases[q], src[q], streams[q]
-            return rbfd.Mesh(d["xyz_s"], d["dS"], c.R, c.eps, precision=precision, stream=s_.cuda_stream,
-                             profile=record, engine=args.engine, grid_ctas=args.ctas)
-        ms = list(create_pool.map(make, range(len(cases))))
-        rbfd.greedy_deform_batch(ms, [d["xyz_v"] for d in src], [d["d_v"] for d in src], [c.D for c in cases],
-                                 [c.k for c in cases], [d["out"] for d in src])
+        """Both cases as one library call (rbfd_run_jobs): per case, create
+        (the spatial set-up of the surface), greedy and volume update, the
+        cases side by side on their own host threads and streams.  Returns the
+        meshes; their counters are read and they are destroyed after the timed
+        region."""
+        jobs = [dict(xyz_s=d["xyz_s"], dS=d["dS"], R=c.R, eps=c.eps, precision=precision, stream=s_.cuda_stream,
+                     profile=record, engine=args.engine, grid_ctas=args.ctas, xyz_v=d["xyz_v"], d_v=d["d_v"],
+                     D=c.D, k=c.k, out=d["out"]) for c, d, s_ in zip(cases, src, streams)]
+        ms, _ = rbfd.run_jobs(jobs)
         return ms
 
     def finish(ms):

@@ -333,6 +333,39 @@ int rbfd_deform_batch(rbfd_mesh **meshes, int n, const int64_t *n_v, const float
 int rbfd_greedy_deform_batch(rbfd_mesh **meshes, int n, const int64_t *n_v, const float *const *xyz_v,
                              const float *const *d_v, const double *D, const double *k, float *const *out);
 
+/*
+ * rbfd_job -- one whole deformation: the arguments of rbfd_create (surface,
+ * displacement, levels, eps, options) and of rbfd_deform (FP32 volume points,
+ * wall distances or NULL, D, k, output).  Pointer kinds follow
+ * opt->inputs_on_device; the caller owns every array.
+ */
+typedef struct rbfd_job {
+    int dim;                 /* 2 or 3 */
+    int n_levels;            /* entries of R */
+    int64_t n_s;             /* surface points */
+    const double *xyz_s;     /* [n_s][dim] surface coordinates */
+    const double *dS;        /* [n_s][dim] surface displacements */
+    const double *R;         /* [n_levels] support radius per level */
+    double eps;              /* final tolerance of the greedy */
+    const rbfd_options *opt; /* NULL: rbfd_options_default */
+    int64_t n_v;             /* volume points */
+    const float *xyz_v;      /* [n_v][dim] volume coordinates */
+    const float *d_v;        /* [n_v] wall distances, or NULL to compute them */
+    double D, k;             /* as rbfd_deform */
+    float *out;              /* [n_v][dim] volume displacements (written) */
+} rbfd_job;
+
+/*
+ * rbfd_run_jobs -- rbfd_create, rbfd_greedy and rbfd_deform for each of n
+ * jobs, the jobs side by side (one host thread and stream each, as
+ * rbfd_greedy_deform_batch), with no return to the caller in between.
+ * meshes[i] receives job i's mesh (NULL if its creation failed): the caller
+ * reads it (levels, statistics) and destroys it.  Returns RBFD_ENOTCONV, after
+ * deforming with the valid levels, if a greedy hit its control cap; otherwise
+ * the worst status (the message names the job).
+ */
+int rbfd_run_jobs(const rbfd_job *jobs, int n, rbfd_mesh **meshes);
+
 /* ------------------------------------------------------------- serving ---
  *
  * A request loop for deformation requests as icing time steps produce them:

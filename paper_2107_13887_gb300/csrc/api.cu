@@ -378,6 +378,7 @@ void unshare_grid(rbfd_mesh **meshes, int n) {
     }
 }
 
+
 }  // namespace
 
 extern "C" {
@@ -560,6 +561,29 @@ static int deform_common(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const voi
     });
 }
 
+// The greedy then the volume update of one mesh of a batch, on the calling
+// host thread: the volume's copies, packing and Morton order run on a second
+// stream while the greedy runs.
+static void greedy_deform_one(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *dv, double D, double k,
+                       float *out) {
+    RBFD_CUDA(cudaSetDevice(m->device));
+    deform_check(m, n_v, xyz_v, dv, D, k, out);
+    rbfd::volume_stage(m, n_v, xyz_v, dv, false, D, k);
+    bool notconv = false;
+    try {
+        rbfd::greedy_run(m);
+    } catch (const Error &e) {
+        if (e.status != RBFD_ENOTCONV) {
+            rbfd::volume_unstage(m);
+            throw;
+        }
+        notconv = true;  // the levels are valid: deform with them, report it after
+    }
+    const int drc = deform_common(m, n_v, xyz_v, dv, D, k, out, false);
+    if (drc != RBFD_OK) rbfd::fail(drc, rbfd::g_last_error);
+    if (notconv) rbfd::fail(RBFD_ENOTCONV, "greedy selection did not reach eps before the control cap");
+}
+
 int rbfd_set_displacement(rbfd_mesh *m, const double *dS) {
     return guarded([&] {
         if (!m || !dS) rbfd::fail(RBFD_EINVAL, "rbfd_set_displacement: NULL argument");
@@ -681,28 +705,32 @@ int rbfd_greedy_deform_batch(rbfd_mesh **meshes, int n, const int64_t *n_v, cons
     int rc = share_grid(meshes, n);
     if (rc != RBFD_OK) return rc;
     rc = run_batch(n, [&](int i) {
-        rbfd_mesh *m = meshes[i];
-        RBFD_CUDA(cudaSetDevice(m->device));
-        const void *dv = d_v ? d_v[i] : nullptr;
-        // the volume's copies, packing and Morton order run on a second
-        // stream while the greedy runs
-        deform_check(m, n_v[i], xyz_v[i], dv, D[i], k[i], out[i]);
-        rbfd::volume_stage(m, n_v[i], xyz_v[i], dv, false, D[i], k[i]);
-        bool notconv = false;
-        try {
-            rbfd::greedy_run(m);
-        } catch (const Error &e) {
-            if (e.status != RBFD_ENOTCONV) {
-                rbfd::volume_unstage(m);
-                throw;
-            }
-            notconv = true;  // the levels are valid: deform with them, report it after
-        }
-        const int drc = deform_common(m, n_v[i], xyz_v[i], d_v ? d_v[i] : nullptr, D[i], k[i], out[i], false);
-        if (drc != RBFD_OK) rbfd::fail(drc, rbfd::g_last_error);
-        if (notconv) rbfd::fail(RBFD_ENOTCONV, "greedy selection did not reach eps before the control cap");
+        greedy_deform_one(meshes[i], n_v[i], xyz_v[i], d_v ? d_v[i] : nullptr, D[i], k[i], out[i]);
     }, "rbfd_greedy_deform_batch");
     unshare_grid(meshes, n);
+    return rc;
+}
+
+int rbfd_run_jobs(const rbfd_job *jobs, int n, rbfd_mesh **meshes) {
+    if (n < 0 || (n > 0 && (!jobs || !meshes))) {
+        rbfd::g_last_error = "rbfd_run_jobs: bad arguments";
+        return RBFD_EINVAL;
+    }
+    for (int i = 0; i < n; ++i) meshes[i] = nullptr;
+    const int rc = run_batch(n, [&](int i) {
+        const rbfd_job &J = jobs[i];
+        rbfd_mesh *m = nullptr;
+        const int crc = rbfd_create(&m, J.dim, J.n_s, J.xyz_s, J.dS, J.n_levels, J.R, J.eps, J.opt);
+        if (crc != RBFD_OK) rbfd::fail(crc, rbfd::g_last_error);
+        meshes[i] = m;
+        if (n > 1) {  // the jobs run side by side: each mesh takes a share of the blocks
+            m->batch_ctas_cap = std::max(1, rbfd::persist_max_ctas(m) / n);
+            m->batch_share = n;
+        }
+        greedy_deform_one(m, J.n_v, J.xyz_v, J.d_v, J.D, J.k, J.out);
+    }, "rbfd_run_jobs");
+    for (int i = 0; i < n; ++i)
+        if (meshes[i]) unshare_grid(&meshes[i], 1);
     return rc;
 }
 

@@ -106,6 +106,25 @@ class rbfd_request(ctypes.Structure):
     _fields_ = [("dS", ctypes.c_void_p), ("out", ctypes.c_void_p)]
 
 
+class rbfd_job(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("n_levels", ctypes.c_int),
+        ("n_s", ctypes.c_int64),
+        ("xyz_s", ctypes.c_void_p),
+        ("dS", ctypes.c_void_p),
+        ("R", ctypes.c_void_p),
+        ("eps", ctypes.c_double),
+        ("opt", ctypes.POINTER(rbfd_options)),
+        ("n_v", ctypes.c_int64),
+        ("xyz_v", ctypes.c_void_p),
+        ("d_v", ctypes.c_void_p),
+        ("D", ctypes.c_double),
+        ("k", ctypes.c_double),
+        ("out", ctypes.c_void_p),
+    ]
+
+
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
 # (name, restype, argtypes) of every function include/rbfd.h declares
@@ -139,6 +158,7 @@ SIGNATURES = [
     ("rbfd_greedy_deform_batch", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_i64),
                                                 ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_d),
                                                 ctypes.POINTER(_d), ctypes.POINTER(_vp)]),
+    ("rbfd_run_jobs", ctypes.c_int, [ctypes.POINTER(rbfd_job), ctypes.c_int, ctypes.POINTER(_vp)]),
     ("rbfd_destroy", ctypes.c_int, [_vp]),
     ("rbfd_server_options_default", None, [ctypes.POINTER(rbfd_server_options)]),
     ("rbfd_server_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(rbfd_server_options)]),
@@ -210,6 +230,34 @@ def default_options() -> rbfd_options:
     return o
 
 
+def _create_args(xyz_s, dS, R, precision=MIXED, basis=2, first_point=0, nc_cap=0, stream=None,
+                 eps_absolute=False, refine_iters=3, profile=False, engine=0, grid_ctas=0):
+    """rbfd_create's arrays (FP64, contiguous) and options."""
+    on_dev = _is_torch_cuda(xyz_s)
+    if on_dev:
+        import torch
+
+        xyz_s = xyz_s.to(torch.float64).contiguous()
+        dS = dS.to(torch.float64).contiguous()
+    else:
+        xyz_s = np.ascontiguousarray(xyz_s, dtype=np.float64)
+        dS = np.ascontiguousarray(dS, dtype=np.float64)
+    Rv = np.ascontiguousarray(np.atleast_1d(R), dtype=np.float64)
+    o = default_options()
+    o.precision = int(precision)
+    o.basis = int(basis)
+    o.first_point = int(first_point)
+    o.inputs_on_device = 1 if on_dev else 0
+    o.nc_cap = int(nc_cap)
+    o.stream = stream
+    o.eps_absolute = 1 if eps_absolute else 0
+    o.refine_iters = int(refine_iters)
+    o.profile = 1 if profile else 0
+    o.engine = int(engine)
+    o.grid_ctas = int(grid_ctas)
+    return xyz_s, dS, Rv, o
+
+
 @dataclasses.dataclass
 class LevelResult:
     idx: np.ndarray
@@ -225,37 +273,19 @@ class Mesh:
     ``rbfd_destroy`` on ``close()`` / garbage collection."""
 
     def __init__(self, xyz_s, dS, R, eps, precision=MIXED, basis=2, first_point=0, nc_cap=0, stream=None,
-                 eps_absolute=False, refine_iters=3, profile=False, engine=0, grid_ctas=0):
+                 eps_absolute=False, refine_iters=3, profile=False, engine=0, grid_ctas=0, _handle=None):
         lib = load()
         self._lib = lib
-        on_dev = _is_torch_cuda(xyz_s)
-        if on_dev:
-            import torch
-
-            xyz_s = xyz_s.to(torch.float64).contiguous()
-            dS = dS.to(torch.float64).contiguous()
-            n_s, dim = xyz_s.shape
-        else:
-            xyz_s = np.ascontiguousarray(xyz_s, dtype=np.float64)
-            dS = np.ascontiguousarray(dS, dtype=np.float64)
-            n_s, dim = xyz_s.shape
+        xyz_s, dS, Rv, o = _create_args(xyz_s, dS, R, precision=precision, basis=basis, first_point=first_point,
+                                        nc_cap=nc_cap, stream=stream, eps_absolute=eps_absolute,
+                                        refine_iters=refine_iters, profile=profile, engine=engine,
+                                        grid_ctas=grid_ctas)
         self._keep = (xyz_s, dS)
-        self.dim = int(dim)
-        self.n_s = int(n_s)
-        Rv = np.ascontiguousarray(np.atleast_1d(R), dtype=np.float64)
-        o = default_options()
-        o.precision = int(precision)
-        o.basis = int(basis)
-        o.first_point = int(first_point)
-        o.inputs_on_device = 1 if on_dev else 0
-        o.nc_cap = int(nc_cap)
-        o.stream = stream
-        o.eps_absolute = 1 if eps_absolute else 0
-        o.refine_iters = int(refine_iters)
-        o.profile = 1 if profile else 0
-        o.engine = int(engine)
-        o.grid_ctas = int(grid_ctas)
-        self.on_device = on_dev
+        self.n_s, self.dim = (int(x) for x in xyz_s.shape)
+        self.on_device = bool(o.inputs_on_device)
+        if _handle is not None:  # created by rbfd_run_jobs
+            self.h = _handle
+            return
         h = ctypes.c_void_p()
         _check(lib.rbfd_create(ctypes.byref(h), self.dim, self.n_s, _ptr(xyz_s), _ptr(dS), len(Rv),
                                _ptr(Rv), float(eps), ctypes.byref(o)))
@@ -475,6 +505,50 @@ def greedy_deform_batch(meshes, xyz_v, d_v, D, k, out, allow_not_converged: bool
         return rc
     _check(rc)
     return rc
+
+
+def run_jobs(jobs, allow_not_converged: bool = True):
+    """``rbfd_run_jobs``: create, greedy and volume update for each job, the
+    jobs side by side, in one library call.  Each job is a dict with the
+    arguments of ``Mesh`` (xyz_s, dS, R, eps and options) and of
+    ``Mesh.deform`` (xyz_v, d_v (may be None), D, k, out: float32 arrays of
+    the same kind as xyz_s).  Returns (meshes, status): the ``Mesh`` objects
+    (None where creation failed) for reading levels and statistics."""
+    lib = load()
+    n = len(jobs)
+    arr = (rbfd_job * n)()
+    keep = []
+    for i, j in enumerate(jobs):
+        opts = {key: j[key] for key in ("precision", "basis", "first_point", "nc_cap", "stream", "eps_absolute",
+                                        "refine_iters", "profile", "engine", "grid_ctas") if key in j}
+        xyz_s, dS, Rv, o = _create_args(j["xyz_s"], j["dS"], j["R"], **opts)
+        keep.append((xyz_s, dS, Rv, o, j))
+        a = arr[i]
+        a.dim, a.n_levels, a.n_s = int(xyz_s.shape[1]), len(Rv), int(xyz_s.shape[0])
+        a.xyz_s, a.dS, a.R = _ptr(xyz_s).value, _ptr(dS).value, _ptr(Rv).value
+        a.eps = float(j["eps"])
+        a.opt = ctypes.pointer(o)
+        a.n_v = int(j["xyz_v"].shape[0])
+        a.xyz_v = _ptr(j["xyz_v"]).value
+        a.d_v = None if j.get("d_v") is None else _ptr(j["d_v"]).value
+        a.D, a.k = float(j["D"]), float(j["k"])
+        a.out = _ptr(j["out"]).value
+    handles = (_vp * n)()
+    rc = lib.rbfd_run_jobs(arr, n, handles)
+    meshes = []
+    for i, (xyz_s, dS, Rv, o, j) in enumerate(keep):
+        if handles[i]:
+            opts = {key: j[key] for key in ("precision", "stream") if key in j}
+            meshes.append(Mesh(xyz_s, dS, Rv, j["eps"], _handle=ctypes.c_void_p(handles[i]), **opts))
+        else:
+            meshes.append(None)
+    if not (rc == ENOTCONV and allow_not_converged):
+        if rc != 0:
+            for m in meshes:
+                if m is not None:
+                    m.close()
+        _check(rc)
+    return meshes, rc
 
 
 class Server:

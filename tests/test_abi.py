@@ -72,11 +72,12 @@ def test_struct_layout_matches_header(tmp_path):
         'printf("%zu %zu %zu %zu\\n", sizeof(rbfd_stats), offsetof(rbfd_stats, confirm_resumes),'
         " offsetof(rbfd_stats, persist_phase_ms), offsetof(rbfd_stats, wall_pairs_exact));\n"
         'printf("%zu %zu\\n", sizeof(rbfd_quality), offsetof(rbfd_quality, hist));\n'
+        'printf("%zu %zu %zu\\n", sizeof(rbfd_job), offsetof(rbfd_job, opt), offsetof(rbfd_job, out));\n'
         "return 0;}\n"
     )
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
-    a, b, c = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:3]
+    a, b, c, d = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:4]
     so, onc, ost, ori = map(int, a.split())
     ss, ocr, ovp, owp = map(int, b.split())
     assert so == ctypes.sizeof(rbfd.rbfd_options)
@@ -89,3 +90,6 @@ def test_struct_layout_matches_header(tmp_path):
     assert owp == rbfd.rbfd_stats.wall_pairs_exact.offset
     sq, oh = map(int, c.split())
     assert sq == ctypes.sizeof(rbfd.rbfd_quality) and oh == rbfd.rbfd_quality.hist.offset
+    sj, oo, ou = map(int, d.split())
+    assert sj == ctypes.sizeof(rbfd.rbfd_job)
+    assert oo == rbfd.rbfd_job.opt.offset and ou == rbfd.rbfd_job.out.offset

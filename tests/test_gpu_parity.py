@@ -442,6 +442,47 @@ def test_staged_volume_with_device_arrays_matches_plain_calls():
             m.close()
 
 
+def test_run_jobs_matches_separate_calls():
+    """rbfd_run_jobs (create, greedy and volume update per job, side by side,
+    in one call) gives the levels and volumes of the separate calls bit for
+    bit, on host arrays and on device tensors; a bad job fails alone."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    names = ["airfoil_horns_2lvl", "wing_ridge_2lvl", "airfoil_pitch_2lvl"]
+    cases = [CASES[n] for n in names]
+    want = []
+    for c in cases:
+        m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps)
+        m.greedy()
+        want.append((m.levels(), m.deform(c.xyz_v, c.d_v, c.D, c.k)))
+        m.close()
+    for on_dev in (False, True):
+        conv = t if on_dev else (lambda a: a)
+        jobs = [dict(xyz_s=conv(c.xyz_s), dS=conv(c.dS), R=c.R, eps=c.eps, xyz_v=conv(c.xyz_v), d_v=conv(c.d_v),
+                     D=c.D, k=c.k,
+                     out=(torch.empty((c.n_v, c.dim), dtype=torch.float32, device=dev) if on_dev
+                          else np.empty((c.n_v, c.dim), np.float32))) for c in cases]
+        ms, rc = rbfd.run_jobs(jobs)
+        assert rc == 0
+        for j, m, (lv, w) in zip(jobs, ms, want):
+            out = j["out"].cpu().numpy() if on_dev else j["out"]
+            assert np.array_equal(out, w)
+            for x, y in zip(m.levels(), lv):
+                assert np.array_equal(x.idx, y.idx) and np.array_equal(x.alpha, y.alpha)
+            assert m.stats()["greedy_steps"] > 0
+            m.close()
+    # a job with an invalid radius: its mesh is not created, the others run
+    c0, c1 = cases[0], cases[1]
+    jobs = [dict(xyz_s=c0.xyz_s, dS=c0.dS, R=c0.R, eps=c0.eps, xyz_v=c0.xyz_v, d_v=c0.d_v, D=c0.D, k=c0.k,
+                 out=np.empty((c0.n_v, c0.dim), np.float32)),
+            dict(xyz_s=c1.xyz_s, dS=c1.dS, R=(-1.0,), eps=c1.eps, xyz_v=c1.xyz_v, d_v=c1.d_v, D=c1.D, k=c1.k,
+                 out=np.empty((c1.n_v, c1.dim), np.float32))]
+    with pytest.raises(rbfd.RbfdError) as ei:
+        rbfd.run_jobs(jobs)
+    assert ei.value.status == rbfd.EINVAL and "mesh 1" in str(ei.value)
+
+
 @pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
 def test_batch_matches_single_meshes(precision):
     names = ["airfoil_horns_2lvl", "wing_ridge_2lvl", "airfoil_pitch_2lvl", "airfoil_bump_333"]
