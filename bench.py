@@ -79,6 +79,26 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate_over_ranks(ms, units, dev):
+    """The whole job's (time, units) from every rank's: the slowest rank's
+    time and the sum of the units (the ranks are independent replicas; this
+    is the only collective)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def reference_rank_works(rank):
+    """The reference arm (the oracle on the host cores) runs on rank 0 alone;
+    the other ranks exit without work."""
+    return rank == 0
+
+
 def make_cases():
     from paper_2107_13887_gb300 import synth
 
@@ -297,19 +317,9 @@ def run_ours(args):
         ms_e, pairs_e, _ = timed(hcases, args.steps, args.warmup, False)
     # aggregate over ranks: units summed, time = max
     if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        u = torch.tensor([float(pairs)], dtype=torch.float64, device=dev)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        ms_all, pairs_all = float(t.item()), float(u.item())
+        ms_all, pairs_all = aggregate_over_ranks(ms, pairs, dev)
         if not args.no_e2e:
-            t = torch.tensor([ms_e], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            u = torch.tensor([float(pairs_e)], dtype=torch.float64, device=dev)
-            dist.all_reduce(u, op=dist.ReduceOp.SUM)
-            ms_e, pairs_e = float(t.item()), float(u.item())
+            ms_e, pairs_e = aggregate_over_ranks(ms_e, pairs_e, dev)
     else:
         ms_all, pairs_all = ms, float(pairs)
     if not args.no_e2e:
@@ -471,7 +481,7 @@ def run_serving(n_requests=200, rate=50.0, slots=4, seed=0):
 
 def run_reference(args):
     ws, rank, _ = dist_env()
-    if rank != 0:
+    if not reference_rank_works(rank):
         return
     cases = make_cases()
     frac = 1.0  # the whole workload each step
