@@ -19,29 +19,33 @@
 // point.  It pays while the supports overlap most of the controls (large R
 // relative to the surface, early in a level); the host hands the level to the
 // list sweep (persist.cu) once the lists get much shorter than the control
-// count or V is full.  Everything runs in FP64.
+// count or V is full.  In mixed precision the per-point work (dot product,
+// phi, E, s2) runs in double-float on the FP32 pipe and the inverse-factor
+// rows in FP64; in FP64 mode everything is FP64.
 //
 // Each block owns fixed groups of 32 surface points and keeps their state in
 // shared memory across steps: the first cs columns of V, E, coordinates, the
 // running sum s2 = sum_k v_k(x)^2 and the selected flags.  Every candidate
 // point therefore knows l^2 = 1 - s2 and w = E / l of its own, and a block
-// publishes a complete record of its best candidate (key, position,
-// coordinates, l^2, E) plus its column y = V[.][candidate].  Per pass, for the
-// control c_j decided in the previous pass (y = the winner's published
-// column, loaded during that decision):
-//   (a) v_j at the block's points: V[j][i], E_i -= w_j v_j(x_i), s2_i += v_j^2,
-//       the block's argmax of |E_i|^2 over unselected points -> its record;
-//       c_j appended to the control lists of the point blocks within R;
-//   -- arrive at the grid barrier --
-//   (b) the growth of the inverse factor for c_j on the rows this block owns
-//       (row j of G, column j of G^T: g_k = -(sum_m G_mk y_m) / l_j,
-//       alpha_k += w_j g_k): no other block reads them during the launch, so
-//       this work overlaps the barrier wait;
-//   -- wait --
-//   every block reads the P records and takes the same decision: global
-//   argmax, stop test |E|max / S0 < tau_l in FP64, pivot test, the next
-//   control; block 0 records it.  One warp computes the step's scalars
-//   while the others load the winner's column.
+// publishes a 16-byte head (key, index, longest list), a record of its best
+// candidate (position, coordinates, l^2, E) and that candidate's column
+// y = V[.][candidate].  Per pass, for the control c_j decided in the previous
+// pass (y = the winner's published column, loaded during that decision):
+//   c_j appended to the control lists of the point blocks within R;
+//   (a) v_j at the block's points: warp 0 evaluates phi while seven warps
+//       compute the dot product in slices; then V[j][i], E_i -= w_j v_j(x_i),
+//       s2_i += v_j^2 and the block's argmax of |E_i|^2 over the unselected
+//       points -> its head, record and column;
+//   -- the last warp arrives at the grid barrier and polls it, while --
+//   (b) the other seven grow the inverse factor for c_j on the rows this
+//       block owns (row j of G, column j of G^T: g_k = -(sum_m G_mk y_m) / l_j,
+//       alpha_k += w_j g_k): no other block reads them during the launch;
+//   -- the barrier has passed --
+//   every block reads the P heads and takes the same decision: global
+//   argmax, stop test |E|max / S0 < tau_l in FP64 (on the keys outside a
+//   narrow bracket), pivot test, the next control; block 0 records it.  One
+//   warp fetches the winner's record and computes the step's scalars while
+//   the others load the winner's column.
 #include <algorithm>
 #include <cfloat>
 #include <climits>
