@@ -273,7 +273,7 @@ class Mesh:
     ``rbfd_destroy`` on ``close()`` / garbage collection."""
 
     def __init__(self, xyz_s, dS, R, eps, precision=MIXED, basis=2, first_point=0, nc_cap=0, stream=None,
-                 eps_absolute=False, refine_iters=3, profile=False, engine=0, grid_ctas=0, _handle=None):
+                 eps_absolute=False, refine_iters=3, profile=False, engine=0, grid_ctas=0):
         lib = load()
         self._lib = lib
         xyz_s, dS, Rv, o = _create_args(xyz_s, dS, R, precision=precision, basis=basis, first_point=first_point,
@@ -283,13 +283,21 @@ class Mesh:
         self._keep = (xyz_s, dS)
         self.n_s, self.dim = (int(x) for x in xyz_s.shape)
         self.on_device = bool(o.inputs_on_device)
-        if _handle is not None:  # created by rbfd_run_jobs
-            self.h = _handle
-            return
         h = ctypes.c_void_p()
         _check(lib.rbfd_create(ctypes.byref(h), self.dim, self.n_s, _ptr(xyz_s), _ptr(dS), len(Rv),
                                _ptr(Rv), float(eps), ctypes.byref(o)))
         self.h = h
+
+    @classmethod
+    def _wrap(cls, h, xyz_s, dS, on_device):
+        """A Mesh for a handle made by the library (rbfd_run_jobs)."""
+        m = cls.__new__(cls)
+        m._lib = load()
+        m._keep = (xyz_s, dS)
+        m.n_s, m.dim = (int(x) for x in xyz_s.shape)
+        m.on_device = bool(on_device)
+        m.h = h
+        return m
 
     def close(self):
         if getattr(self, "h", None):
@@ -535,13 +543,8 @@ def run_jobs(jobs, allow_not_converged: bool = True):
         a.out = _ptr(j["out"]).value
     handles = (_vp * n)()
     rc = lib.rbfd_run_jobs(arr, n, handles)
-    meshes = []
-    for i, (xyz_s, dS, Rv, o, j) in enumerate(keep):
-        if handles[i]:
-            opts = {key: j[key] for key in ("precision", "stream") if key in j}
-            meshes.append(Mesh(xyz_s, dS, Rv, j["eps"], _handle=ctypes.c_void_p(handles[i]), **opts))
-        else:
-            meshes.append(None)
+    meshes = [Mesh._wrap(ctypes.c_void_p(handles[i]), xyz_s, dS, o.inputs_on_device) if handles[i] else None
+              for i, (xyz_s, dS, Rv, o, j) in enumerate(keep)]
     if not (rc == ENOTCONV and allow_not_converged):
         if rc != 0:
             for m in meshes:

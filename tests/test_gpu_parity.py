@@ -472,8 +472,21 @@ def test_run_jobs_matches_separate_calls():
                 assert np.array_equal(x.idx, y.idx) and np.array_equal(x.alpha, y.alpha)
             assert m.stats()["greedy_steps"] > 0
             m.close()
-    # a job with an invalid radius: its mesh is not created, the others run
+    # one FP64 job with the wall distances computed on the device, beside a mixed one
     c0, c1 = cases[0], cases[1]
+    m0 = rbfd.Mesh(c0.xyz_s, c0.dS, c0.R, c0.eps, precision=rbfd.FP64)
+    m0.greedy()
+    w0 = m0.deform(c0.xyz_v, None, c0.D, c0.k)
+    m0.close()
+    jobs = [dict(xyz_s=c0.xyz_s, dS=c0.dS, R=c0.R, eps=c0.eps, precision=rbfd.FP64, xyz_v=c0.xyz_v, d_v=None,
+                 D=c0.D, k=c0.k, out=np.empty((c0.n_v, c0.dim), np.float32)),
+            dict(xyz_s=c1.xyz_s, dS=c1.dS, R=c1.R, eps=c1.eps, xyz_v=c1.xyz_v, d_v=c1.d_v, D=c1.D, k=c1.k,
+                 out=np.empty((c1.n_v, c1.dim), np.float32))]
+    ms, rc = rbfd.run_jobs(jobs)
+    assert rc == 0 and np.array_equal(jobs[0]["out"], w0) and np.array_equal(jobs[1]["out"], want[1][1])
+    for m in ms:
+        m.close()
+    # a job with an invalid radius: its mesh is not created, the others run
     jobs = [dict(xyz_s=c0.xyz_s, dS=c0.dS, R=c0.R, eps=c0.eps, xyz_v=c0.xyz_v, d_v=c0.d_v, D=c0.D, k=c0.k,
                  out=np.empty((c0.n_v, c0.dim), np.float32)),
             dict(xyz_s=c1.xyz_s, dS=c1.dS, R=(-1.0,), eps=c1.eps, xyz_v=c1.xyz_v, d_v=c1.d_v, D=c1.D, k=c1.k,
