@@ -388,6 +388,11 @@ def run_ours(args):
         "deform_ms": {"pitch_heave": statistics.median([s["deform_ms"] for s in stats[0::2]]),
                       "horns": statistics.median([s["deform_ms"] for s in stats[1::2]])},
         "pairs_useful_per_step": pairs_all / args.steps / ws,
+        # the second count: pairs the kernels evaluated (the useful ones plus
+        # those the cell and control lists let through beyond R; the Newton
+        # start counts its basis multiply-adds), per step and per second (rank 0)
+        "pairs_visited_per_step": sum(s["pairs_visited"] for s in stats) / args.steps,
+        "visited_per_s": sum(s["pairs_visited"] for s in stats) / (ms / 1e3),
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": int(sum(s["launches"] for s in stats)),

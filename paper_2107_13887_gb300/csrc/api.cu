@@ -235,6 +235,8 @@ void mesh_free(rbfd_mesh *m) {
     if (m->h_lvl) pinned_free(m->h_lvl);
     if (m->ev0) cudaEventDestroy(m->ev0);
     if (m->ev1) cudaEventDestroy(m->ev1);
+    if (m->ev_g0) cudaEventDestroy(m->ev_g0);
+    if (m->ev_g1) cudaEventDestroy(m->ev_g1);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     cudaSetDevice(prev);
 }
@@ -446,6 +448,8 @@ int rbfd_create(rbfd_mesh **out, int dim, int64_t n_s, const double *xyz_s, cons
         }
         RBFD_CUDA(cudaEventCreate(&m->ev0));
         RBFD_CUDA(cudaEventCreate(&m->ev1));
+        RBFD_CUDA(cudaEventCreate(&m->ev_g0));
+        RBFD_CUDA(cudaEventCreate(&m->ev_g1));
         m->prof.on = o.profile != 0;
         m->sort.launches = &m->stats.launches;
         rbfd::mesh_prepare(m, xyz_s, dS);
@@ -563,7 +567,9 @@ static int deform_common(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const voi
 
 // The greedy then the volume update of one mesh of a batch, on the calling
 // host thread: the volume's copies, packing and Morton order run on a second
-// stream while the greedy runs.
+// stream while the greedy runs, and the update is queued behind the greedy's
+// last launches without a host wait between the two (its D_l are computed
+// on the device from the levels' scalars).
 static void greedy_deform_one(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *dv, double D, double k,
                        float *out) {
     RBFD_CUDA(cudaSetDevice(m->device));
@@ -571,7 +577,7 @@ static void greedy_deform_one(rbfd_mesh *m, int64_t n_v, const float *xyz_v, con
     rbfd::volume_stage(m, n_v, xyz_v, dv, false, D, k);
     bool notconv = false;
     try {
-        rbfd::greedy_run(m);
+        rbfd::greedy_run(m, false);
     } catch (const Error &e) {
         if (e.status != RBFD_ENOTCONV) {
             rbfd::volume_unstage(m);
@@ -580,6 +586,7 @@ static void greedy_deform_one(rbfd_mesh *m, int64_t n_v, const float *xyz_v, con
         notconv = true;  // the levels are valid: deform with them, report it after
     }
     const int drc = deform_common(m, n_v, xyz_v, dv, D, k, out, false);
+    rbfd::greedy_finish(m);  // (done by the update unless it failed first)
     if (drc != RBFD_OK) rbfd::fail(drc, rbfd::g_last_error);
     if (notconv) rbfd::fail(RBFD_ENOTCONV, "greedy selection did not reach eps before the control cap");
 }

@@ -14,6 +14,7 @@
 // displacement back to the caller's order.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <string>
 
@@ -49,11 +50,27 @@ __global__ void k_vol_pack(const void *__restrict__ xyz, const void *__restrict_
 }
 
 __global__ void k_flag_below(const double4 *__restrict__ p, const uint32_t *__restrict__ idx, int64_t n, double D,
-                             uint32_t *__restrict__ flag) {
+                             uint32_t *__restrict__ flag, const double *__restrict__ D_dev = nullptr) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (D_dev) D = *D_dev;
     double d = p[idx ? idx[i] : i].w;
     flag[i] = (d < D) ? 1u : 0u;
+}
+
+// D_l of levels 0..L-1 on the device, exactly as the host forms it from the
+// level's max |dS_l| (k max|dS_l| capped at D when k > 0, else D), and its
+// FP32 inverse; flags *mismatch if D_0 differs from d0 (the D_0 a staged
+// volume's early level-0 sweep used).
+__global__ void k_level_D(const double *__restrict__ hist, int L, double k, double D, double *__restrict__ Dl,
+                          float *__restrict__ invDlf, double d0, unsigned *__restrict__ mismatch) {
+    const int l = threadIdx.x;
+    if (l >= L) return;
+    double v = (k > 0.0) ? k * __dsqrt_rn(hist[l]) : D;
+    if (k > 0.0 && D > 0.0 && v > D) v = D;
+    Dl[l] = v;
+    invDlf[l] = v > 0.0 ? (float)(1.0 / v) : 0.f;
+    if (l == 0 && mismatch && v != d0) *mismatch = 1u;
 }
 
 __global__ void k_compact(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pos, int64_t n,
@@ -220,6 +237,9 @@ struct VolArgs {
     const float4 *cdf;      // [2n]: coordinates hi, lo
     const float4 *adf;      // [2n]: (ax hi, ax lo, ay hi, ay lo), (az hi, az lo, -, -)
     float g0f[3], hf, Rf, invDlf;
+    // if set: D_l and its FP32 inverse in device memory (they replace Dl, invDlf)
+    const double *Dl_dev;
+    const float *invDlf_dev;
 };
 
 template <int DIM, int BASIS, int MODE>
@@ -353,7 +373,8 @@ __global__ void __launch_bounds__(kThreads) k_vol_sweep(VolArgs a) {
         acc64[2] = df_to_double(acc[2]);
     }
     if (valid) {
-        const double w = __dsub_rn(1.0, __ddiv_rn(P.w, a.Dl));  // psi(d / D_l), d < D_l here
+        const double Dl = a.Dl_dev ? *a.Dl_dev : a.Dl;
+        const double w = __dsub_rn(1.0, __ddiv_rn(P.w, Dl));  // psi(d / D_l), d < D_l here
         double4 v = a.vacc[s];
         v.x = __dadd_rn(v.x, __dmul_rn(w, acc64[0]));
         v.y = __dadd_rn(v.y, __dmul_rn(w, acc64[1]));
@@ -477,7 +498,7 @@ __global__ void __launch_bounds__(kThreads) k_vol_sweep_f32(VolArgs a) {
         }
     }
     if (valid) {
-        const float w = 1.0f - P.w * a.invDlf;  // psi(d / D_l), d < D_l here
+        const float w = 1.0f - P.w * (a.invDlf_dev ? *a.invDlf_dev : a.invDlf);  // psi(d / D_l), d < D_l here
         float4 *va = reinterpret_cast<float4 *>(a.vacc + s);
         const float4 v0 = va[0], v1 = va[1];
         const df sx = df_add({v0.x, v0.y}, df_mul(acc[0], {w, 0.f}));
@@ -609,14 +630,14 @@ void deform_acc_init(rbfd_mesh *m, int64_t nV, const double4 *vpos, bool f64, cu
 }
 
 void deform_one_level(rbfd_mesh *m, int l, int64_t nV, const double4 *vpos, double Dl, bool f64, cudaStream_t st,
-                      SortScratch &ss) {
+                      SortScratch &ss, const double *Dl_dev = nullptr, const float *invDlf_dev = nullptr) {
     const Level &Lv = m->levels[l];
-    if (Lv.nc == 0 || !(Dl > 0.0)) return;
+    if (Lv.nc == 0 || (!Dl_dev && !(Dl > 0.0))) return;
     const bool fast = deform_fast(m, f64);
     const int mode = m->opt.precision == RBFD_FP64 ? 0 : (fast ? 2 : 1);
     // d < D_l, then the fused evaluation; the list length stays on the
     // device (the sweep reads it), so no level waits for the host
-    k_flag_below<<<cdiv(nV, 256), 256, 0, st>>>(vpos, nullptr, nV, Dl, m->d_vflag);
+    k_flag_below<<<cdiv(nV, 256), 256, 0, st>>>(vpos, nullptr, nV, Dl, m->d_vflag, Dl_dev);
     exclusive_scan_u32(m->d_vflag, m->d_vscan, (size_t)nV, &m->d_misc[5], ss, st);
     k_compact<<<cdiv(nV, 256), 256, 0, st>>>(m->d_vflag, m->d_vscan, nV, m->d_vlist);
     k_count_points<<<1, 32, 0, st>>>(&m->d_misc[5], m->d_pairs + 7);
@@ -639,6 +660,8 @@ void deform_one_level(rbfd_mesh *m, int l, int64_t nV, const double4 *vpos, doub
     a.invR_hi = (float)inv;
     a.invR_lo = (float)(inv - (double)a.invR_hi);
     a.pairs = m->d_pairs + 2;
+    a.Dl_dev = Dl_dev;
+    a.invDlf_dev = invDlf_dev;
     if (fast) {
         a.vp4 = m->d_vpos4;
         a.cdf = Lv.d_cdf;
@@ -648,7 +671,7 @@ void deform_one_level(rbfd_mesh *m, int l, int64_t nV, const double4 *vpos, doub
         a.g0f[2] = (float)Lv.g0.z;
         a.hf = (float)Lv.h;
         a.Rf = (float)Lv.R;
-        a.invDlf = (float)(1.0 / Dl);
+        a.invDlf = Dl > 0.0 ? (float)(1.0 / Dl) : 0.f;
     }
     m->stats.launches += 4;  // flags, compaction, count (+ scan counted in the scan)
     cudaEvent_t e0 = m->prof.begin(st);
@@ -832,14 +855,8 @@ void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, b
     const size_t es = f64 ? sizeof(double) : sizeof(float);
     RBFD_CUDA(cudaEventRecord(m->ev0, st));
     const int L = (int)m->levels.size();
-    std::vector<double> Dl(L, 0.0);
+    std::vector<double> Dl(L, 0.0);  // (filled once the levels' scalars are on the host)
     double Dmax = 0.0;
-    for (int l = 0; l < L; ++l) {
-        double v = (k > 0.0) ? k * m->levels[l].smax : D;
-        if (k > 0.0 && D > 0.0 && v > D) v = D;
-        Dl[l] = (m->levels[l].nc > 0) ? v : 0.0;
-        Dmax = std::max(Dmax, Dl[l]);
-    }
     const bool host = !m->opt.inputs_on_device;
     if (m->vst_ok && m->vst_n == n_v && m->vst_x == xyz_v && m->vst_d == d_v && m->vst_f64 == f64) {
         volume_stage_enqueue(m);
@@ -853,11 +870,55 @@ void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, b
         // level 0 may have run on the staging stream during the greedy (with
         // D_0 from S0; the same value as from the level, checked here)
         bool l0 = m->vst_l0;
+        m->vst_l0 = false;
+        if (m->greedy_pending && L > 0) {
+            // the greedy's last wait has not happened (its work is queued
+            // ahead on this stream): D_l from the levels' scalars on the
+            // device, and no host wait between the greedy and this update
+            RBFD_CUDA(cudaMemsetAsync(&m->d_misc[9], 0, sizeof(uint32_t), st));
+            k_level_D<<<1, (unsigned)cdiv(L, 32) * 32, 0, st>>>(m->d_lvl_hist, L, k, D, m->d_Dl, m->d_invDlf,
+                                                               m->vst_D0, l0 ? &m->d_misc[9] : nullptr);
+            for (int l = l0 ? 1 : 0; l < L; ++l)
+                deform_one_level(m, l, n_v, vs_pos, 0.0, f64, st, m->sort, m->d_Dl + l, m->d_invDlf + l);
+            deform_scatter(m, n_v, m->d_vorig, dout, f64, st);
+            RBFD_CUDA(cudaMemcpyAsync(m->h_prep, &m->d_misc[9], sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            m->stats.launches += 1;
+            if (host) RBFD_CUDA(cudaMemcpyAsync(out, dout, (size_t)n_v * dim * es, cudaMemcpyDeviceToHost, st));
+            RBFD_CUDA(cudaEventRecord(m->ev1, st));
+            RBFD_CUDA(cudaEventSynchronize(m->ev1));
+            greedy_finish(m);
+            unsigned mismatch = 0;
+            std::memcpy(&mismatch, m->h_prep, sizeof(mismatch));
+            if (mismatch) {  // (not expected: D_0 from S0 and from level 0 agree) the update again, host D_l
+                for (int l = 0; l < L; ++l) {
+                    double v = (k > 0.0) ? k * m->levels[l].smax : D;
+                    if (k > 0.0 && D > 0.0 && v > D) v = D;
+                    Dl[l] = (m->levels[l].nc > 0) ? v : 0.0;
+                }
+                deform_acc_init(m, n_v, vs_pos, f64, st);
+                for (int l = 0; l < L; ++l) deform_one_level(m, l, n_v, vs_pos, Dl[l], f64, st, m->sort);
+                deform_scatter(m, n_v, m->d_vorig, dout, f64, st);
+                if (host) RBFD_CUDA(cudaMemcpyAsync(out, dout, (size_t)n_v * dim * es, cudaMemcpyDeviceToHost, st));
+                RBFD_CUDA(cudaEventRecord(m->ev1, st));
+                RBFD_CUDA(cudaEventSynchronize(m->ev1));
+            }
+            float ms = 0;
+            RBFD_CUDA(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
+            m->stats.deform_ms = ms;
+            m->prof.flush();
+            return;
+        }
+        greedy_finish(m);
+        for (int l = 0; l < L; ++l) {  // (the levels' D_l, now that their scalars are on the host)
+            double v = (k > 0.0) ? k * m->levels[l].smax : D;
+            if (k > 0.0 && D > 0.0 && v > D) v = D;
+            Dl[l] = (m->levels[l].nc > 0) ? v : 0.0;
+            Dmax = std::max(Dmax, Dl[l]);
+        }
         if (l0 && !(L > 0 && Dl[0] == m->vst_D0)) {
             deform_acc_init(m, n_v, vs_pos, f64, st);
             l0 = false;
         }
-        m->vst_l0 = false;
         if (Dmax > 0.0) {
             for (int l = l0 ? 1 : 0; l < L; ++l) deform_one_level(m, l, n_v, vs_pos, Dl[l], f64, st, m->sort);
             deform_scatter(m, n_v, m->d_vorig, dout, f64, st);
@@ -874,6 +935,13 @@ void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, b
         return;
     }
     volume_unstage(m);
+    greedy_finish(m);
+    for (int l = 0; l < L; ++l) {  // (the levels' D_l, now that their scalars are on the host)
+        double v = (k > 0.0) ? k * m->levels[l].smax : D;
+        if (k > 0.0 && D > 0.0 && v > D) v = D;
+        Dl[l] = (m->levels[l].nc > 0) ? v : 0.0;
+        Dmax = std::max(Dmax, Dl[l]);
+    }
     void *dout = out;
     const void *dx = xyz_v, *dd = d_v;
     if (n_v > 0) {

@@ -1069,6 +1069,9 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     rest.add(m->d_pred, (size_t)4 * kMaxPersistCTAs);
     rest.add(m->d_nz_k, cap + 1);
     rest.add(m->d_nz_v, cap + 1);
+    rest.add(m->d_lvl_hist, m->n_levels_req);
+    rest.add(m->d_Dl, m->n_levels_req);
+    rest.add(m->d_invDlf, m->n_levels_req);
     const size_t zbytes = zero.total();
     char *arena = static_cast<char *>(dmalloc(zbytes + rest.total(), "mesh state"));
     m->d_arena = arena;
@@ -1159,6 +1162,7 @@ __global__ void k_gather_disp(const double *__restrict__ dS, const uint32_t *__r
 // dropped.
 void mesh_set_displacement(rbfd_mesh *m, const double *dS) {
     mesh_ready(m);
+    greedy_finish(m);
     cudaStream_t st = m->stream;
     const int64_t n = m->n_s;
     const double *dd = dS;
@@ -1221,8 +1225,23 @@ void level_fetch(rbfd_mesh *m, Level &L) {
     L.fetched = true;
 }
 
-void greedy_run(rbfd_mesh *m) {
+void greedy_finish(rbfd_mesh *m) {
+    if (!m->greedy_pending) return;
+    m->greedy_pending = false;
+    RBFD_CUDA(cudaEventSynchronize(m->ev_g1));
+    for (auto &L : m->levels) {
+        L.smax = std::sqrt(L.h_scal[0]);
+        m->stats.refine_sweeps += (int64_t)L.h_scal[3];
+    }
+    float ms = 0;
+    RBFD_CUDA(cudaEventElapsedTime(&ms, m->ev_g0, m->ev_g1));
+    m->stats.greedy_ms = ms;
+    m->prof.flush();
+}
+
+void greedy_run(rbfd_mesh *m, bool wait) {
     mesh_ready(m);
+    greedy_finish(m);  // (a previous run's)
     cudaStream_t st = m->stream;
     for (auto &L : m->levels) level_free(L);
     m->levels.clear();
@@ -1239,10 +1258,10 @@ void greedy_run(rbfd_mesh *m) {
     m->stats.newton_steps = 0;
     m->stats.refine_sweeps = 0;
     m->stats.confirm_resumes = 0;
-    RBFD_CUDA(cudaEventRecord(m->ev0, st));
+    RBFD_CUDA(cudaEventRecord(m->ev_g0, st));
     if (m->S0 == 0.0) {  // nothing moves: zero levels
-        RBFD_CUDA(cudaEventRecord(m->ev1, st));
-        RBFD_CUDA(cudaEventSynchronize(m->ev1));
+        RBFD_CUDA(cudaEventRecord(m->ev_g1, st));
+        RBFD_CUDA(cudaEventSynchronize(m->ev_g1));
         m->stats.greedy_ms = 0;
         m->greedy_done = true;
         return;
@@ -1479,6 +1498,7 @@ void greedy_run(rbfd_mesh *m) {
         // greedy; indices and weights are copied only when asked for
         L.h_scal = static_cast<double *>(pinned_alloc(4 * sizeof(double)));
         RBFD_CUDA(cudaMemcpyAsync(L.h_scal, m->d_lvl, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        RBFD_CUDA(cudaMemcpyAsync(m->d_lvl_hist + l, m->d_lvl, sizeof(double), cudaMemcpyDeviceToDevice, st));
         build_control_grid(m, L, m->h_sbox);
         if (L.status != RBFD_OK) final_status = RBFD_ENOTCONV;
         m->levels.push_back(std::move(L));
@@ -1486,18 +1506,11 @@ void greedy_run(rbfd_mesh *m) {
         // multi-level subspace: the next level interpolates this level's error
         RBFD_CUDA(cudaMemcpyAsync(m->d_cur, m->d_E, sizeof(double4) * m->n_s, cudaMemcpyDeviceToDevice, st));
     }
-    RBFD_CUDA(cudaEventRecord(m->ev1, st));
-    RBFD_CUDA(cudaEventSynchronize(m->ev1));
-    for (auto &L : m->levels) {
-        L.smax = std::sqrt(L.h_scal[0]);
-        m->stats.refine_sweeps += (int64_t)L.h_scal[3];
-    }
-    host_mark(3);
-    float ms = 0;
-    RBFD_CUDA(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
-    m->stats.greedy_ms = ms;
-    m->prof.flush();
+    RBFD_CUDA(cudaEventRecord(m->ev_g1, st));
+    m->greedy_pending = true;
     m->greedy_done = true;
+    if (wait) greedy_finish(m);
+    host_mark(3);
     if (!m->levels.empty() && !(m->levels.back().emax < eps_rel)) final_status = RBFD_ENOTCONV;
     if (final_status != RBFD_OK) fail(final_status, "greedy selection did not reach eps before the control cap");
 }

@@ -201,6 +201,11 @@ struct rbfd_mesh {
     bool greedy_done = false;
     rbfd_stats stats{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev_g0 = nullptr, ev_g1 = nullptr;  // the greedy's start and end
+    bool greedy_pending = false;   // the greedy's last wait and epilogue not yet done (greedy_finish)
+    double *d_lvl_hist = nullptr;  // [levels] max |dS_l|^2 of each level
+    double *d_Dl = nullptr;        // [levels] D_l on the device (volume update after a pending greedy)
+    float *d_invDlf = nullptr;     // [levels] 1 / D_l in FP32
     rbfd::SortScratch sort;
     rbfd::Profiler prof;
 
@@ -251,7 +256,10 @@ void newton_reserve(rbfd_mesh *m);
 void newton_run_level(rbfd_mesh *m, double R, double tau, int ctas);
 int persist_max_ctas(rbfd_mesh *m);
 void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas);
-void greedy_run(rbfd_mesh *m);
+// wait = false: the greedy returns once its work is queued; its last wait and
+// epilogue (level scalars, timing) happen in greedy_finish
+void greedy_run(rbfd_mesh *m, bool wait = true);
+void greedy_finish(rbfd_mesh *m);
 // a level's device and pinned buffers back to the pools (its stream synchronised)
 void level_free(Level &L);
 // the host copies of a level's indices and weights (one synchronised copy, first call only)
