@@ -168,6 +168,13 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+# DRAM bytes per launch (read + written) from an ncu capture of the same
+# workload, for the kernels whose code has not changed since
+# (profiles/k_greedy_newton_naca0012_4000s.md: the mean of the four launches
+# of one step)
+DRAM_BYTES_PER_LAUNCH = {"newton": 434624}
+
+
 # ------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -195,6 +202,9 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def count(self):
+        return len(self.lines)
 
     def stop(self):
         if not self.proc:
@@ -311,7 +321,16 @@ def run_ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     ms, pairs, stats = timed(dcases, args.steps, args.warmup, True)
+    # nvidia-smi samples every 200 ms, longer than a short timed region: the
+    # same step keeps running (untimed) until three samples have been taken
+    # under this load, at most 3 s
+    t_stop = time.monotonic() + 3.0
+    while sampler.count() < 3 and time.monotonic() < t_stop:
+        finish(one_step(dcases, False))
+    torch.cuda.synchronize()
     clocks = sampler.stop()
+    if clocks is not None:
+        clocks["sampled_over"] = "warm-up, timed steps and untimed repeats of the same step"
     e2e = None
     if not args.no_e2e:
         ms_e, pairs_e, _ = timed(hcases, args.steps, args.warmup, False)
@@ -362,7 +381,8 @@ def run_ours(args):
     roofline = {
         "bound": "alu", "kernel": names[dom],
         "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "TFLOP/s",
-        "frac": achieved / peak_ops, "traffic": None,
+        "frac": achieved / peak_ops, "traffic": DRAM_BYTES_PER_LAUNCH.get(dom),
+        "traffic_unit": "bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, ncu)",
         "avg_launch_ms": d_ms / max(1, d_launch), "launches": int(d_launch),
         "kernel_ms": {k: round(v[0], 3) for k, v in kinds.items()},
         "kernel_frac": {k: round(v[2] / (v[0] / 1e3) / peak_ops, 5) for k, v in kinds.items() if v[0] > 0 and v[2]},
