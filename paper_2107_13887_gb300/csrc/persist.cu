@@ -41,6 +41,7 @@ namespace rbfd {
 namespace {
 
 constexpr int kT = 128;        // threads per block (4 warps)
+constexpr int kPfxMax = 2048;  // point blocks up to which the sweep's items are balanced (prefix in shared memory)
 
 
 struct PersistArgs {
@@ -69,6 +70,7 @@ struct PersistArgs {
     unsigned long long *pairs;
     int test_skip_arrival;  // tests only: block 0 leaves before its first barrier arrival
     unsigned long long *phase_ns;  // non-null: block 0 accumulates [work, wait] ns per phase (8 words)
+    unsigned long long *item_ctr;  // the sweep's item counter (zero at launch)
 };
 
 __device__ __forceinline__ uint32_t ldcg_u32(const uint32_t *p) { return __ldcg(p); }
@@ -86,6 +88,8 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
     __shared__ bool s_last, s_lead;
     __shared__ unsigned s_scan[32];
     __shared__ unsigned char s_hits[4][kTile];
+    __shared__ unsigned s_pfx[kPfxMax + 1];
+    __shared__ int s_item;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned P = gridDim.x;
@@ -119,6 +123,10 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
         return;                                                                  \
     }
 
+    // the sweep's items are handed out by one counter over the launch: a step
+    // with N items takes N + P fetches (every block's last fetch finds none),
+    // so every block knows the step's base
+    unsigned long long item_base = 0;
     for (int guard = 0; guard <= a.cap; ++guard) {
         // ------------------------------------------------ phase 1: sweep (+ the step's decision)
         // every block list is cut into chunks of at most cl controls, cl set by
@@ -127,11 +135,65 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
         int nch = max((int)((P + a.n_pb - 1) / a.n_pb), (max_cnt + 127) / 128);
         nch = max(1, min(nch, min(a.n_chunk_max, (max_cnt + 15) / 16)));
         const int cl = (max_cnt + nch - 1) / nch;
-        for (int item = blockIdx.x; item < a.n_pb * nch; item += P) {
-            const int pb = item / nch, ch = item % nch;
-            const int cnt = (int)ldcg_u32(&a.nb_cnt[pb]);
-            const int used = min(nch, max(1, (cnt + cl - 1) / cl));  // chunks this block's list occupies
-            if (ch >= used) continue;                                // same decision in every thread
+        // the items are the chunks the lists occupy (at least one per point
+        // block, whose last chunk forms E): every block builds the same
+        // prefix over the point blocks, to map an item to its (point block,
+        // chunk).  (Beyond kPfxMax point blocks: every (point block, chunk)
+        // pair is an item, the unoccupied ones skipped.)
+        const bool balanced = a.n_pb <= kPfxMax;
+        int n_items = a.n_pb * nch;
+        if (balanced) {
+            const int per = (a.n_pb + kT - 1) / kT;
+            const int b0 = min(a.n_pb, tid * per), b1 = min(a.n_pb, b0 + per);
+            unsigned mine = 0;
+            for (int b = b0; b < b1; ++b) {
+                const int cb = (int)ldcg_u32(&a.nb_cnt[b]);
+                const unsigned ub = (unsigned)min(nch, max(1, (cb + cl - 1) / cl));
+                s_pfx[b] = ub;
+                mine += ub;
+            }
+            unsigned tot;
+            unsigned run = block_excl_scan_u32(mine, s_scan, &tot);
+            for (int b = b0; b < b1; ++b) {
+                const unsigned ub = s_pfx[b];
+                s_pfx[b] = run;
+                run += ub;
+            }
+            if (tid == 0) {
+                s_pfx[a.n_pb] = tot;
+                s_item = (int)(atomicAdd(a.item_ctr, 1ull) - item_base);
+            }
+            __syncthreads();
+            n_items = (int)tot;
+        }
+        // balanced: items taken from the counter as blocks come free (their
+        // costs differ with the density of controls); the next index is
+        // fetched while the current item runs.  Otherwise every P-th item.
+        int item = balanced ? s_item : (int)blockIdx.x;
+        unsigned long long nxt = 0;
+        for (; item < n_items; item = balanced ? s_item : item + (int)P) {
+            if (balanced) {
+                __syncthreads();  // every thread has read s_item
+                if (tid == 0) nxt = atomicAdd(a.item_ctr, 1ull);
+            }
+            int pb, ch, cnt, used;
+            if (balanced) {
+                int bl = 0, bh = a.n_pb;  // s_pfx[bl] <= item < s_pfx[bh]
+                while (bh - bl > 1) {
+                    const int mid = (bl + bh) >> 1;
+                    if (s_pfx[mid] <= (unsigned)item) bl = mid; else bh = mid;
+                }
+                pb = bl;
+                ch = item - (int)s_pfx[pb];
+                used = (int)(s_pfx[pb + 1] - s_pfx[pb]);
+                cnt = (int)ldcg_u32(&a.nb_cnt[pb]);
+            } else {
+                pb = item / nch;
+                ch = item % nch;
+                cnt = (int)ldcg_u32(&a.nb_cnt[pb]);
+                used = min(nch, max(1, (cnt + cl - 1) / cl));  // chunks this block's list occupies
+                if (ch >= used) continue;                     // same decision in every thread
+            }
             const int64_t p = (int64_t)pb * kPB + tid;
             const bool valid = p < a.n_s;
             const int lo = ch * cl, hi = (ch == used - 1) ? cnt : min(cnt, lo + cl);  // the last takes the rest
@@ -211,6 +273,8 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
                     atomicAdd(&a.pairs[1], nv * (unsigned long long)(hi - lo));
                 }
             }
+            // (the next item, read after the barriers below)
+            if (balanced && tid == 0) s_item = (int)(nxt - item_base);
             // last chunk of this point block: E, key, block argmax; the last
             // point block to finish then takes the step's decision
             __threadfence();
@@ -292,30 +356,58 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
                         const int per = (cntc + kT - 1) / kT;
                         const int q0 = min(cntc, tid * per), q1 = min(cntc, q0 + per);
                         unsigned mine = 0;
-                        for (int q = q0; q < q1; ++q) {
-                            const uint32_t k = ldcg_u32(lst + q);
-                            double f;
-                            if (MODE == 0) {
+                        if constexpr (MODE == 0) {
+                            for (int q = q0; q < q1; ++q) {
+                                const uint32_t k = ldcg_u32(lst + q);
                                 const double4 ck = ldcg_d4(&a.cx[k]);
-                                f = phi_f64<BASIS>(__ddiv_rn(dist_f64<DIM>(xc.x, xc.y, xc.z, ck.x, ck.y, ck.z), a.R));
-                            } else {  // double-float on the FP32 pipe from the split coordinates
-                                const float4 h = ldcg_f4(&a.cdf[k]), l = ldcg_f4(&a.cdf[a.cap + 1 + k]);
-                                const df dx = df_add({h.x, l.x}, df_neg(xcx)), dy = df_add({h.y, l.y}, df_neg(xcy));
-                                df r2 = df_add(df_sqr(dx), df_sqr(dy));
-                                if (DIM == 3) r2 = df_add(r2, df_sqr(df_add({h.z, l.z}, df_neg(xcz))));
-                                f = df_to_double(phi_df<BASIS>(df_mul(df_sqrt(r2), invR)));
+                                const double f = phi_f64<BASIS>(
+                                    __ddiv_rn(dist_f64<DIM>(xc.x, xc.y, xc.z, ck.x, ck.y, ck.z), a.R));
+                                a.phi[q] = f;
+                                mine += (f != 0.0);
                             }
-                            a.phi[q] = f;
-                            mine += (f != 0.0);
+                        } else {
+                            // double-float on the FP32 pipe from the split coordinates,
+                            // four entries at a time (their loads issued together)
+                            for (int q = q0; q < q1; q += 4) {
+                                uint32_t kk[4];
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) kk[u] = q + u < q1 ? ldcg_u32(lst + q + u) : 0u;
+                                float4 h[4], l[4];
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) {
+                                    h[u] = q + u < q1 ? ldcg_f4(&a.cdf[kk[u]]) : make_float4(0, 0, 0, 0);
+                                    l[u] = q + u < q1 ? ldcg_f4(&a.cdf[a.cap + 1 + kk[u]]) : make_float4(0, 0, 0, 0);
+                                }
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) {
+                                    if (q + u >= q1) break;
+                                    const df dx = df_add({h[u].x, l[u].x}, df_neg(xcx)),
+                                             dy = df_add({h[u].y, l[u].y}, df_neg(xcy));
+                                    df r2 = df_add(df_sqr(dx), df_sqr(dy));
+                                    if (DIM == 3) r2 = df_add(r2, df_sqr(df_add({h[u].z, l[u].z}, df_neg(xcz))));
+                                    const double f = df_to_double(phi_df<BASIS>(df_mul(df_sqrt(r2), invR)));
+                                    a.phi[q + u] = f;
+                                    mine += (f != 0.0);
+                                }
+                            }
                         }
                         unsigned nnz;
                         unsigned pos = block_excl_scan_u32(mine, s_scan, &nnz);
-                        for (int q = q0; q < q1; ++q) {
-                            const double f = a.phi[q];  // written by this thread above
-                            if (f != 0.0) {
-                                a.nz_k[pos] = ldcg_u32(lst + q);
-                                a.nz_v[pos] = f;
-                                ++pos;
+                        for (int q = q0; q < q1; q += 4) {  // (loads of four entries issued together)
+                            double ff[4];
+                            uint32_t kk[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                ff[u] = q + u < q1 ? a.phi[q + u] : 0.0;  // written by this thread above
+                                kk[u] = q + u < q1 ? ldcg_u32(lst + q + u) : 0u;
+                            }
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                if (ff[u] != 0.0) {
+                                    a.nz_k[pos] = kk[u];
+                                    a.nz_v[pos] = ff[u];
+                                    ++pos;
+                                }
                             }
                         }
                         // (the block lists get c_n after the barrier: other blocks may
@@ -344,6 +436,7 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
                 }
             }
         }
+        if (balanced) item_base += (unsigned long long)n_items + P;
         if (a.test_skip_arrival && blockIdx.x == 0) return;  // the others' waits run out
         RBFD_SYNC(0)
 
@@ -563,6 +656,8 @@ void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
     if (const char *v = std::getenv("RBFD_TEST_BARRIER_POLLS")) a.spin_limit = std::strtoull(v, nullptr, 10);
     if (const char *v = std::getenv("RBFD_TEST_SKIP_ARRIVAL")) a.test_skip_arrival = std::atoi(v) != 0;
     a.phase_ns = m->prof.on ? m->d_phase_ns : nullptr;
+    a.item_ctr = reinterpret_cast<unsigned long long *>(&m->d_misc[10]);  // (8-byte aligned)
+    RBFD_CUDA(cudaMemsetAsync(a.item_ctr, 0, sizeof(unsigned long long), m->stream));
     a.st = m->d_st;
     a.pairs = m->d_pairs;
     const void *k = select_kernel(m->dim, m->opt.basis, m->opt.precision == RBFD_FP64 ? 0 : 1);
