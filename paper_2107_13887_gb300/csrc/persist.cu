@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
         // every block list is cut into chunks of at most cl controls, cl set by
         // the longest list, so that no point block holds the step back
         const int max_cnt = max(1, (int)__ldcg(&a.st->max_cnt));
-        int nch = max((int)((P + a.n_pb - 1) / a.n_pb), (max_cnt + 127) / 128);
+        int nch = max((int)((P + a.n_pb - 1) / a.n_pb), (max_cnt + 63) / 64);
         nch = max(1, min(nch, min(a.n_chunk_max, (max_cnt + 15) / 16)));
         const int cl = (max_cnt + nch - 1) / nch;
         // the items are the chunks the lists occupy (at least one per point
