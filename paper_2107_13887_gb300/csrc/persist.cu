@@ -71,6 +71,7 @@ struct PersistArgs {
     int test_skip_arrival;  // tests only: block 0 leaves before its first barrier arrival
     unsigned long long *phase_ns;  // non-null: block 0 accumulates [work, wait] ns per phase (8 words)
     unsigned long long *item_ctr;  // the sweep's item counter (zero at launch)
+    int pfx_max;                   // balanced sweep items up to this many point blocks (<= kPfxMax)
 };
 
 __device__ __forceinline__ uint32_t ldcg_u32(const uint32_t *p) { return __ldcg(p); }
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
         // prefix over the point blocks, to map an item to its (point block,
         // chunk).  (Beyond kPfxMax point blocks: every (point block, chunk)
         // pair is an item, the unoccupied ones skipped.)
-        const bool balanced = a.n_pb <= kPfxMax;
+        const bool balanced = a.n_pb <= a.pfx_max;
         int n_items = a.n_pb * nch;
         if (balanced) {
             const int per = (a.n_pb + kT - 1) / kT;
@@ -655,6 +656,9 @@ void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
     // skipping its first barrier arrival so that the others' waits run out
     if (const char *v = std::getenv("RBFD_TEST_BARRIER_POLLS")) a.spin_limit = std::strtoull(v, nullptr, 10);
     if (const char *v = std::getenv("RBFD_TEST_SKIP_ARRIVAL")) a.test_skip_arrival = std::atoi(v) != 0;
+    // (and the round-robin sweep items at any size, to check both assignments)
+    a.pfx_max = kPfxMax;
+    if (const char *v = std::getenv("RBFD_TEST_SWEEP_ROUND_ROBIN")) a.pfx_max = std::atoi(v) != 0 ? 0 : kPfxMax;
     a.phase_ns = m->prof.on ? m->d_phase_ns : nullptr;
     a.item_ctr = reinterpret_cast<unsigned long long *>(&m->d_misc[10]);  // (8-byte aligned)
     RBFD_CUDA(cudaMemsetAsync(a.item_ctr, 0, sizeof(unsigned long long), m->stream));

@@ -354,6 +354,29 @@ def test_persistent_engine_matches_step_engine(name, precision):
         check_valid(c, m0.levels(), S0)
 
 
+@pytest.mark.parametrize("name", ["airfoil_horns_2lvl", "wing_ridge_2lvl"])
+@pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
+def test_sweep_item_assignment_does_not_change_results(name, precision, monkeypatch):
+    """The persistent sweep hands its items (chunks of the point blocks'
+    control lists) out from a counter as blocks come free; on meshes with more
+    point blocks than its shared-memory prefix holds it takes them round-robin
+    instead (test hook: round-robin at any size).  A chunk's partial sums do
+    not depend on the block that computes them and are reduced in chunk
+    order, so both give the same controls and weights bit for bit."""
+    c = CASES[name]
+    runs = []
+    for rr in ("0", "1"):
+        monkeypatch.setenv("RBFD_TEST_SWEEP_ROUND_ROBIN", rr)
+        m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, engine=2, grid_ctas=7)
+        m.greedy()
+        runs.append(m.levels())
+    monkeypatch.delenv("RBFD_TEST_SWEEP_ROUND_ROBIN")
+    assert len(runs[0]) == len(runs[1])
+    for x, y in zip(*runs):
+        assert np.array_equal(x.idx, y.idx)
+        assert np.array_equal(x.alpha, y.alpha)
+
+
 @pytest.mark.parametrize("name", ["airfoil_horns_2lvl", "wing_ridge_2lvl", "airfoil_bump_333"])
 @pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
 def test_newton_start_matches_list_sweep(name, precision, monkeypatch):
