@@ -274,6 +274,24 @@ int rbfd_orthogonality(int dim, int64_t n_i, int64_t n_k, int64_t n_layers, int 
                        rbfd_quality *q, int on_device, void *stream);
 
 /*
+ * rbfd_sort_pairs -- the stable sort of (key, value) pairs that orders the
+ * surface, volume and control points by Morton key (spatial preparation: the
+ * neighbour lists of the compact-support sums of Section 3 and Eq. 23 are
+ * read in this order).  Exposed so that callers can order their own points
+ * the same way.
+ *
+ * keys, vals: n uint32 each, DEVICE memory, sorted in place by the low
+ * key_bits bits of the key (1..32), equal keys kept in input order; values
+ * follow their keys.  Up to 8,192 pairs one block sorts them in registers and
+ * shared memory; beyond, an LSD radix sort of 8-bit digits.  stream: a
+ * cudaStream_t (NULL: the per-thread default stream); the call returns after
+ * the sort has finished.  Scratch memory is allocated and freed by the call.
+ * Errors: RBFD_EINVAL (n < 0 or above 2^31 - 1, key_bits outside 1..32, NULL
+ * or non-device arrays with n > 0), RBFD_ENOMEM, RBFD_ECUDA.
+ */
+int rbfd_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, int key_bits, void *stream);
+
+/*
  * rbfd_deform_noalloc -- the volume update of rbfd_deform for callers that
  * cannot allocate device memory while they run: a solver loop whose device
  * memory was reserved up front (a pool or a fixed budget), or a host that keeps

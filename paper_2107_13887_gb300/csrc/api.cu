@@ -669,6 +669,30 @@ int rbfd_orthogonality(int dim, int64_t n_i, int64_t n_k, int64_t n_layers, int 
     });
 }
 
+int rbfd_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, int key_bits, void *stream) {
+    return guarded([&] {
+        if (n < 0 || n > ((int64_t)1 << 31) - 1) rbfd::fail(RBFD_EINVAL, "rbfd_sort_pairs: n out of range");
+        if (key_bits < 1 || key_bits > 32) rbfd::fail(RBFD_EINVAL, "rbfd_sort_pairs: key_bits must be 1..32");
+        if (n == 0) return;
+        if (!keys || !vals || !is_device_ptr(keys) || !is_device_ptr(vals))
+            rbfd::fail(RBFD_EINVAL, "rbfd_sort_pairs: keys and vals must be device memory");
+        cudaPointerAttributes at{};
+        RBFD_CUDA(cudaPointerGetAttributes(&at, keys));
+        RBFD_CUDA(cudaSetDevice(at.device));
+        cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : cudaStreamPerThread;
+        rbfd::SortScratch ss;
+        try {
+            rbfd::radix_sort_pairs(keys, vals, (size_t)n, key_bits, ss, st);
+            RBFD_CUDA(cudaStreamSynchronize(st));
+        } catch (...) {
+            cudaStreamSynchronize(st);
+            ss.release();
+            throw;
+        }
+        ss.release();
+    });
+}
+
 int rbfd_deform(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v, double D, double k, float *out) {
     return deform_common(m, n_v, xyz_v, d_v, D, k, out, false);
 }

@@ -19,8 +19,8 @@ constexpr int SC_THREADS = 256;
 constexpr int SC_ITEMS = 8;
 constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
 
-__global__ void k_rs_hist(const uint32_t *__restrict__ keys, size_t n, int shift, uint32_t *__restrict__ hist,
-                          int nblk) {
+__global__ void k_rs_hist(const uint32_t *__restrict__ keys, size_t n, int shift, uint32_t dmask,
+                          uint32_t *__restrict__ hist, int nblk) {
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -28,7 +28,7 @@ __global__ void k_rs_hist(const uint32_t *__restrict__ keys, size_t n, int shift
 #pragma unroll
     for (int r = 0; r < RS_ITEMS; ++r) {
         size_t i = base + (size_t)r * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & dmask], 1u);
     }
     __syncthreads();
     hist[(size_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
@@ -38,7 +38,7 @@ __global__ void k_rs_hist(const uint32_t *__restrict__ keys, size_t n, int shift
 // round ranks 256 consecutive items with warp match + per-warp digit counts.
 __global__ void k_rs_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                              uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, size_t n, int shift,
-                             const uint32_t *__restrict__ offs, int nblk) {
+                             uint32_t dmask, const uint32_t *__restrict__ offs, int nblk) {
     __shared__ uint32_t base[256];
     __shared__ uint32_t wcnt[RS_THREADS / 32][256];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -51,7 +51,7 @@ __global__ void k_rs_scatter(const uint32_t *__restrict__ kin, const uint32_t *_
         bool valid = i < n;
         uint32_t k = valid ? kin[i] : 0u;
         uint32_t v = valid ? vin[i] : 0u;
-        uint32_t d = valid ? ((k >> shift) & 255u) : 256u;
+        uint32_t d = valid ? ((k >> shift) & dmask) : 256u;
         __syncthreads();
         unsigned peers = __match_any_sync(0xffffffffu, d);
         int lrank = __popc(peers & lt);
@@ -185,14 +185,22 @@ __device__ __forceinline__ uint32_t morton(double x, double y, double z, int dim
 }
 
 // Morton keys with the box read from device memory (lo xyz, hi xyz), so that
-// no host round trip separates the box reduction from the keys.
+// no host round trip separates the box reduction from the keys.  The three
+// reciprocal extents are computed once per block (an FP64 division costs
+// several times the rest of a key).
 __global__ void k_morton_f64_dev(const double4 *__restrict__ p, size_t n, int dim, const double *__restrict__ bb,
                                  int shift, uint32_t *keys, uint32_t *vals) {
+    __shared__ double s_lo[3], s_inv[3];
+    if (threadIdx.x < 3) {
+        const int a = threadIdx.x;
+        s_lo[a] = bb[a];
+        s_inv[a] = (bb[a + 3] > bb[a]) ? 1.0 / (bb[a + 3] - bb[a]) : 0.0;
+    }
+    __syncthreads();
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    auto f = [](double a, double b) { return (b > a) ? 1.0 / (b - a) : 0.0; };
-    const double3 lo = make_double3(bb[0], bb[1], bb[2]);
-    const double3 inv = make_double3(f(bb[0], bb[3]), f(bb[1], bb[4]), f(bb[2], bb[5]));
+    const double3 lo = make_double3(s_lo[0], s_lo[1], s_lo[2]);
+    const double3 inv = make_double3(s_inv[0], s_inv[1], s_inv[2]);
     double4 q = p[i];
     keys[i] = morton(q.x, q.y, q.z, dim, lo, inv) >> shift;
     vals[i] = (uint32_t)i;
@@ -263,62 +271,117 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *t
     if (s.launches) *s.launches += 3;
 }
 
-// Small arrays in one block: a bitonic sort in shared memory of the 64-bit
-// values (low key_bits of the key) << 32 | position, which orders by key and
-// keeps equal keys in input order (the same result as the stable radix sort),
-// then keys and values are gathered by position.  One launch instead of five
-// per 8-bit digit.
+// Small arrays in one block: a bitonic sort of the 64-bit values (low
+// key_bits of the key) << 32 | position, which orders by key and keeps equal
+// keys in input order (the same result as the stable radix sort), then keys
+// and values are gathered by position.  One launch instead of five per 8-bit
+// digit.  Thread t holds the E consecutive values E t .. E t + E - 1 in
+// registers: compare-exchange partners closer than E are in the same thread,
+// closer than 32 E in the same warp (shuffles), and only the farther ones go
+// through shared memory (two block barriers per such stage; 15 of the 78
+// stages of 4,096 values).
 constexpr int kSmallSort = 8192;
 constexpr int kSmallSortThreads = 1024;
 
-__global__ void __launch_bounds__(kSmallSortThreads) k_sort_small(uint32_t *keys, uint32_t *vals, int n, int n2,
-                                                                   uint32_t mask) {
-    extern __shared__ unsigned long long s_c[];  // [n2] composites, then [n] (key, value) pairs
-    uint2 *s_kv = reinterpret_cast<uint2 *>(s_c + n2);
-    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-        if (i < n) {
-            const uint32_t k = keys[i];
-            s_kv[i] = make_uint2(k, vals[i]);
-            s_c[i] = ((unsigned long long)(k & mask) << 32) | (unsigned)i;
-        } else {
-            s_c[i] = ~0ull;  // padding sorts last
-        }
-    }
-    __syncthreads();
-    for (int k = 2; k <= n2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const unsigned long long a = s_c[i], b = s_c[l];
-                    if ((a > b) == ((i & k) == 0)) {
-                        s_c[i] = b;
-                        s_c[l] = a;
-                    }
-                }
+// the kept value of a compare-exchange: the smaller one where the element
+// sorts ascending and is the lower of the pair, or descending and the upper
+__device__ __forceinline__ unsigned long long cx_keep(unsigned long long mine, unsigned long long other, bool asc,
+                                                      bool lower) {
+    const bool take_min = asc == lower;
+    const unsigned long long lo = mine < other ? mine : other, hi = mine < other ? other : mine;
+    return take_min ? lo : hi;
+}
+
+// partners J apart inside the thread (J < E)
+template <int E, int J>
+__device__ __forceinline__ void cx_in_thread(unsigned long long (&c)[E], int base, int k) {
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        if ((r & J) == 0) {
+            const bool asc = ((base + r) & k) == 0;
+            const unsigned long long a = c[r], b = c[r | J];
+            if ((a > b) == asc) {
+                c[r] = b;
+                c[r | J] = a;
             }
-            __syncthreads();
         }
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const uint2 kv = s_kv[(unsigned)s_c[i]];
-        keys[i] = kv.x;
-        vals[i] = kv.y;
+}
+
+template <int E>
+__global__ void __launch_bounds__(kSmallSortThreads) k_sort_small(uint32_t *keys, uint32_t *vals, int n, int N,
+                                                                   uint32_t mask) {
+    extern __shared__ unsigned long long s_c[];  // [N] values (far stages), then [n] (key, value) pairs
+    uint2 *s_kv = reinterpret_cast<uint2 *>(s_c + N);
+    const int tid = threadIdx.x, base = E * tid;
+    unsigned long long c[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int i = base + r;
+        if (i < n) {
+            const uint32_t kk = keys[i];
+            s_kv[i] = make_uint2(kk, vals[i]);
+            c[r] = ((unsigned long long)(kk & mask) << 32) | (unsigned)i;
+        } else {
+            c[r] = ~0ull;  // padding sorts last
+        }
+    }
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32 * E) {  // partner in another warp
+#pragma unroll
+                for (int r = 0; r < E; ++r) s_c[base + r] = c[r];
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const int i = base + r;
+                    c[r] = cx_keep(c[r], s_c[i ^ j], (i & k) == 0, (i & j) == 0);
+                }
+                __syncthreads();
+            } else if (j >= E) {  // partner in another lane of this warp, same register
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const int i = base + r;
+                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, c[r], j / E);
+                    c[r] = cx_keep(c[r], o, (i & k) == 0, (i & j) == 0);
+                }
+            } else {  // same thread
+                if constexpr (E > 4) { if (j == 4) cx_in_thread<E, 4>(c, base, k); }
+                if constexpr (E > 2) { if (j == 2) cx_in_thread<E, 2>(c, base, k); }
+                if constexpr (E > 1) { if (j == 1) cx_in_thread<E, 1>(c, base, k); }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int i = base + r;
+        if (i < n) {
+            const uint2 kv = s_kv[(unsigned)c[r]];
+            keys[i] = kv.x;
+            vals[i] = kv.y;
+        }
     }
 }
 
 void radix_sort_pairs(uint32_t *keys, uint32_t *vals, size_t n, int key_bits, SortScratch &s, cudaStream_t st) {
     if (n <= 1) return;
     if (n <= (size_t)kSmallSort) {
-        int n2 = 2;
-        while (n2 < (int)n) n2 <<= 1;
-        const size_t smem = (size_t)n2 * 8 + n * 8;
-        // (one value for every launch and device: the attribute belongs to the kernel)
-        if (smem > 48 * 1024)
-            RBFD_CUDA(cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           kSmallSort * 16));
+        // N = n rounded up to a power of two, at least a warp; T threads of E values each
+        int N = 32;
+        while (N < (int)n) N <<= 1;
+        const int T = std::min(N, kSmallSortThreads), E = N / T;
+        const size_t smem = (size_t)N * 8 + n * 8;
         const uint32_t mask = key_bits >= 32 ? 0xffffffffu : ((1u << key_bits) - 1u);
-        k_sort_small<<<1, kSmallSortThreads, smem, st>>>(keys, vals, (int)n, n2, mask);
+        auto launch = [&](auto kern) {
+            // (one value for every launch and device: the attribute belongs to the kernel)
+            if (smem > 48 * 1024)
+                RBFD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallSort * 16));
+            kern<<<1, T, smem, st>>>(keys, vals, (int)n, N, mask);
+        };
+        if (E == 1) launch(k_sort_small<1>);
+        else if (E == 2) launch(k_sort_small<2>);
+        else if (E == 4) launch(k_sort_small<4>);
+        else launch(k_sort_small<8>);
         if (s.launches) *s.launches += 1;
         RBFD_CUDA(cudaGetLastError());
         return;
@@ -329,9 +392,11 @@ void radix_sort_pairs(uint32_t *keys, uint32_t *vals, size_t n, int key_bits, So
     int passes = (key_bits + 7) / 8;
     for (int p = 0; p < passes; ++p) {
         int shift = 8 * p;
-        k_rs_hist<<<nblk, RS_THREADS, 0, st>>>(ka, n, shift, s.hist, nblk);
+        // (the last digit holds only the key bits that are left)
+        const uint32_t dmask = (p == passes - 1 && key_bits % 8) ? (1u << (key_bits % 8)) - 1u : 255u;
+        k_rs_hist<<<nblk, RS_THREADS, 0, st>>>(ka, n, shift, dmask, s.hist, nblk);
         exclusive_scan_u32(s.hist, s.hist, (size_t)256 * nblk, nullptr, s, st);
-        k_rs_scatter<<<nblk, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, s.hist, nblk);
+        k_rs_scatter<<<nblk, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, dmask, s.hist, nblk);
         if (s.launches) *s.launches += 2;
         std::swap(ka, kb);
         std::swap(va, vb);

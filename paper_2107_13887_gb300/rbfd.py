@@ -148,6 +148,7 @@ SIGNATURES = [
     ("rbfd_orthogonality", ctypes.c_int, [ctypes.c_int, _i64, _i64, _i64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp,
                                           ctypes.POINTER(rbfd_quality), ctypes.c_int, _vp]),
     ("rbfd_wall_distance_f64", ctypes.c_int, [_vp, _i64, _vp, _vp]),
+    ("rbfd_sort_pairs", ctypes.c_int, [_vp, _vp, _i64, ctypes.c_int, _vp]),
     ("rbfd_set_displacement", ctypes.c_int, [_vp, _vp]),
     ("rbfd_set_volume", ctypes.c_int, [_vp, _i64, _vp, _vp]),
     ("rbfd_deform_volume", ctypes.c_int, [_vp, _d, _d, _vp]),
@@ -466,6 +467,19 @@ def orthogonality(wall, vol, n_layers, periodic_i=True, wall_disp=None, vol_disp
     summ = {f: getattr(q, f) for f, _ in rbfd_quality._fields_}
     summ["hist"] = list(q.hist)
     return th, summ
+
+
+def sort_pairs(keys, vals, key_bits=32, stream=None):
+    """``rbfd_sort_pairs``: stable in-place sort of (key, value) pairs, int32 or
+    uint32 torch CUDA tensors of one length, by the low ``key_bits`` bits of
+    the key."""
+    lib = load()
+    if not (_is_torch_cuda(keys) and _is_torch_cuda(vals)) or keys.numel() != vals.numel():
+        raise ValueError("sort_pairs: keys and vals must be CUDA tensors of one length")
+    if keys.element_size() != 4 or vals.element_size() != 4 or not keys.is_contiguous() or not vals.is_contiguous():
+        raise ValueError("sort_pairs: contiguous 32-bit tensors expected")
+    _check(lib.rbfd_sort_pairs(_ptr(keys), _ptr(vals), int(keys.numel()), int(key_bits), stream))
+    return keys, vals
 
 
 def greedy_batch(meshes, allow_not_converged: bool = True) -> int:
