@@ -387,6 +387,10 @@ def run_ours(args):
         "kernel_ms": {k: round(v[0], 3) for k, v in kinds.items()},
         "kernel_frac": {k: round(v[2] / (v[0] / 1e3) / peak_ops, 5) for k, v in kinds.items() if v[0] > 0 and v[2]},
         "persist_phase_ms": [round(sum(s["persist_phase_ms"][q] for s in stats), 3) for q in range(8)],
+        # the Newton launches' device time per greedy step (the two cases run
+        # side by side, so this is the latency of one case's step)
+        "newton_us_per_step": round(1e3 * sum(s["newton_ms"] for s in stats)
+                                    / max(1, sum(s["newton_steps"] for s in stats)), 3),
         "note": ("FP32-pipe operations: 210 (2D) / 284 (3D) per double-float pair evaluation, 12 per "
                  "double-float basis multiply-add; peak = 152 SMs x 128 FP32 lanes x 2.07 GHz. The greedy "
                  "launches are latency-bound chains of dependent steps (one grid barrier per step)"),

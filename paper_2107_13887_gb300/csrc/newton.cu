@@ -977,7 +977,7 @@ NewtonShape newton_shape(rbfd_mesh *m, int want_ctas) {
     const void *k = select_newton(m->dim, m->opt.basis, mode);
     static const size_t kSmemMax = 220 * 1024;   // dynamic shared memory per block (of 227 KB)
     static const size_t kSmemPerSM = 228 * 1024;  // shared memory of one SM
-    static const size_t kPerBlockReserve = 6 * 1024;  // static shared memory and the system's share
+    static const size_t kPerBlockReserve = 7 * 1024;  // static shared memory (5.2 KB) and the system's 1 KB
     NewtonShape s;
     int sms = 0;
     RBFD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
