@@ -519,6 +519,38 @@ def test_run_jobs_matches_separate_calls():
     assert ei.value.status == rbfd.EINVAL and "mesh 1" in str(ei.value)
 
 
+def test_run_jobs_device_radii_and_capped_job():
+    """In rbfd_run_jobs the volume update is queued behind the greedy without a
+    host wait: D_l = min(k max|dS_l|, D) (or D when k = 0) is formed on the
+    device from the levels' scalars.  Every rule gives the volumes of the
+    separate calls bit for bit: k > 0 with D capping some levels, k > 0 with
+    no cap (D = 0), k = 0 (D at every level), and a job whose greedy stops at
+    its control cap (ENOTCONV reported, its levels still used)."""
+    c = CASES["airfoil_horns_2lvl"]
+    c2 = CASES["airfoil_pitch_2lvl"]
+    S0 = float(np.sqrt((c.dS**2).sum(1)).max())
+    variants = [dict(case=c, D=c.D, k=c.k), dict(case=c, D=0.0, k=3.0),
+                dict(case=c2, D=0.25, k=0.0), dict(case=c, D=3.0 * S0, k=1.5, nc_cap=7)]
+    want = []
+    for v in variants:
+        cc = v["case"]
+        m = rbfd.Mesh(cc.xyz_s, cc.dS, cc.R, cc.eps, nc_cap=v.get("nc_cap", 0))
+        rc = m.greedy()
+        want.append((rc, m.levels(), m.deform(cc.xyz_v, cc.d_v, v["D"], v["k"])))
+        m.close()
+    assert want[3][0] == rbfd.ENOTCONV
+    jobs = [dict(xyz_s=v["case"].xyz_s, dS=v["case"].dS, R=v["case"].R, eps=v["case"].eps,
+                 nc_cap=v.get("nc_cap", 0), xyz_v=v["case"].xyz_v, d_v=v["case"].d_v, D=v["D"], k=v["k"],
+                 out=np.empty((v["case"].n_v, v["case"].dim), np.float32)) for v in variants]
+    ms, rc = rbfd.run_jobs(jobs)
+    assert rc == rbfd.ENOTCONV
+    for j, m, (rc1, lv, w) in zip(jobs, ms, want):
+        assert np.array_equal(j["out"], w)
+        for x, y in zip(m.levels(), lv):
+            assert np.array_equal(x.idx, y.idx) and np.array_equal(x.alpha, y.alpha)
+        m.close()
+
+
 @pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
 def test_batch_matches_single_meshes(precision):
     names = ["airfoil_horns_2lvl", "wing_ridge_2lvl", "airfoil_pitch_2lvl", "airfoil_bump_333"]
