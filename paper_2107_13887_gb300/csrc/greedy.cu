@@ -1110,7 +1110,10 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     }
     // bounding box -> Morton keys -> stable sort -> permutation (one block
     // and one launch for small surfaces: the same results)
-    if (surface_order_small(dx, dd, n, m->dim, m->d_bbox, m->d_perm, m->d_xs, m->d_dS, m->d_inv, st)) {
+    // (test hook, read per call: the multi-launch path at any size)
+    const char *multi = std::getenv("RBFD_TEST_SURFACE_ORDER_MULTI");
+    if (!(multi && std::atoi(multi) != 0) &&
+        surface_order_small(dx, dd, n, m->dim, m->d_bbox, m->d_perm, m->d_xs, m->d_dS, m->d_inv, st)) {
         m->stats.launches += 1;
     } else {
         k_unpack<<<cdiv(n, 256), 256, 0, st>>>(dx, dd, n, m->dim, x4, d4);
