@@ -93,3 +93,18 @@ def test_struct_layout_matches_header(tmp_path):
     sj, oo, ou = map(int, d.split())
     assert sj == ctypes.sizeof(rbfd.rbfd_job)
     assert oo == rbfd.rbfd_job.opt.offset and ou == rbfd.rbfd_job.out.offset
+
+
+def test_argument_checks_before_any_device_work(lib):
+    """Calls with invalid arguments fail with RBFD_EINVAL and a message before
+    they touch a device (no GPU here): bad sizes, bit counts and NULL arrays."""
+    L = rbfd.load()
+    i64 = ctypes.c_int64
+    assert L.rbfd_sort_pairs(None, None, i64(-1), 32, None) == rbfd.EINVAL
+    assert b"n out of range" in L.rbfd_last_error()
+    assert L.rbfd_sort_pairs(None, None, i64(4), 0, None) == rbfd.EINVAL
+    assert L.rbfd_sort_pairs(None, None, i64(4), 33, None) == rbfd.EINVAL
+    assert b"key_bits" in L.rbfd_last_error()
+    assert L.rbfd_sort_pairs(None, None, i64(0), 32, None) == rbfd.OK  # nothing to sort
+    assert L.rbfd_sort_pairs(None, None, i64(4), 32, None) == rbfd.EINVAL  # NULL arrays
+    assert b"device memory" in L.rbfd_last_error()
