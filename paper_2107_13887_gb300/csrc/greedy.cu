@@ -1108,30 +1108,21 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
         RBFD_CUDA(cudaMemcpyAsync(dx, xyz_s, bytes, cudaMemcpyHostToDevice, st));
         RBFD_CUDA(cudaMemcpyAsync(dd, dS, bytes, cudaMemcpyHostToDevice, st));
     }
-    // bounding box -> Morton keys -> stable sort -> permutation (one block
-    // and one launch for small surfaces: the same results)
-    // (test hook, read per call: the multi-launch path at any size)
-    const char *multi = std::getenv("RBFD_TEST_SURFACE_ORDER_MULTI");
-    if (!(multi && std::atoi(multi) != 0) &&
-        surface_order_small(dx, dd, n, m->dim, m->d_bbox, m->d_perm, m->d_xs, m->d_dS, m->d_inv, st)) {
-        m->stats.launches += 1;
-    } else {
-        k_unpack<<<cdiv(n, 256), 256, 0, st>>>(dx, dd, n, m->dim, x4, d4);
-        RBFD_CUDA(cudaGetLastError());
-        const int nbb = std::min<int>(cdiv(n, 256), 256);
-        k_bbox_partial<<<nbb, 256, 0, st>>>(x4, n, part);
-        k_bbox_final<<<1, 192, 0, st>>>(part, nbb, m->d_bbox);
-        morton_keys_f64_dev(x4, n, m->dim, m->d_bbox, keys, m->d_perm, st);
-        radix_sort_pairs(keys, m->d_perm, n, m->dim == 2 ? 32 : 30, m->sort, st);
-        k_gather_sorted<<<cdiv(n, 256), 256, 0, st>>>(m->d_perm, n, x4, d4, m->d_xs, m->d_dS, m->d_inv);
-        RBFD_CUDA(cudaGetLastError());
-        m->stats.launches += 5;  // unpack, bbox x2, morton, gather (+ the sort's own)
-    }
+    k_unpack<<<cdiv(n, 256), 256, 0, st>>>(dx, dd, n, m->dim, x4, d4);
+    RBFD_CUDA(cudaGetLastError());
+    // bounding box -> Morton keys -> stable sort -> permutation
+    const int nbb = std::min<int>(cdiv(n, 256), 256);
+    k_bbox_partial<<<nbb, 256, 0, st>>>(x4, n, part);
+    k_bbox_final<<<1, 192, 0, st>>>(part, nbb, m->d_bbox);
+    morton_keys_f64_dev(x4, n, m->dim, m->d_bbox, keys, m->d_perm, st);
+    radix_sort_pairs(keys, m->d_perm, n, m->dim == 2 ? 32 : 30, m->sort, st);
+    k_gather_sorted<<<cdiv(n, 256), 256, 0, st>>>(m->d_perm, n, x4, d4, m->d_xs, m->d_dS, m->d_inv);
+    RBFD_CUDA(cudaGetLastError());
     // point blocks
     k_point_blocks<<<m->n_pb, kPB, 0, st>>>(m->d_xs, n, m->d_pb_lo, m->d_pb_hi, m->d_pb_org, m->d_xs_hi, m->d_xs_lo);
     RBFD_CUDA(cudaGetLastError());
 
-    m->stats.launches += 1;  // point blocks
+    m->stats.launches += 6;  // unpack, bbox x2, morton, gather, point blocks
     // S0 = max_i |dS_i| and the surface box reach the host with the first
     // call that needs them (mesh_ready): the set-up does not wait here
     const int nbm = std::min<int>(cdiv(m->n_s, 256), 1024);

@@ -73,11 +73,6 @@ constexpr int kVolKeyBits = 24;
 inline int vol_key_shift(int dim) { return dim == 2 ? 32 - kVolKeyBits : 30 - kVolKeyBits; }
 void morton_keys_f32(const float4 *xyzd, const uint32_t *idx, size_t n, int dim, double3 lo, double3 hi,
                      uint32_t *keys, uint32_t *vals, cudaStream_t st);
-// The surface's Morton order in one launch when it has at most 8,192 points
-// (box -> bbox[0..5], keys, stable sort, gather into xs/ds, perm and its
-// inverse); false (nothing queued) for larger surfaces.
-bool surface_order_small(const double *xyz, const double *dS, int64_t n, int dim, double *bbox, uint32_t *perm,
-                         double4 *xs, double4 *ds, uint32_t *inv, cudaStream_t st);
 
 // ------------------------------------------------------------ mesh state
 

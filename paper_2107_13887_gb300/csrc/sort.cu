@@ -371,81 +371,6 @@ __global__ void __launch_bounds__(kSmallSortThreads) k_sort_small(uint32_t *keys
     }
 }
 
-// The surface's order for up to kSmallSort points in one block: bounding box,
-// Morton keys (the same keys as k_morton_f64_dev), the stable sort by key and
-// the gather of coordinates and displacements into that order, with the
-// permutation and its inverse.  The same results as the multi-launch path.
-template <int E>
-__global__ void __launch_bounds__(kSmallSortThreads) k_surface_order_small(
-    const double *__restrict__ xyz, const double *__restrict__ dS, int n, int N, int dim, uint32_t mask,
-    double *__restrict__ bbox, uint32_t *__restrict__ perm, double4 *__restrict__ xs, double4 *__restrict__ ds,
-    uint32_t *__restrict__ inv) {
-    extern __shared__ unsigned long long s_c[];  // [N]
-    __shared__ double s_red[6][32];
-    __shared__ double s_lo[3], s_inv[3];
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, T = blockDim.x, base = E * tid;
-    // box (min and max are exact: any order gives the same values)
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int i = tid; i < n; i += T) {
-        const double *p = xyz + (size_t)i * dim;
-        const double q[3] = {p[0], p[1], dim == 3 ? p[2] : 0.0};
-        for (int a = 0; a < 3; ++a) {
-            lo[a] = fmin(lo[a], q[a]);
-            hi[a] = fmax(hi[a], q[a]);
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1)
-        for (int a = 0; a < 3; ++a) {
-            lo[a] = fmin(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
-            hi[a] = fmax(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
-        }
-    if (lane == 0)
-        for (int a = 0; a < 3; ++a) {
-            s_red[a][w] = lo[a];
-            s_red[3 + a][w] = hi[a];
-        }
-    __syncthreads();
-    if (tid < 6) {
-        double v = s_red[tid][0];
-        for (int q = 1; q < T / 32; ++q) v = tid < 3 ? fmin(v, s_red[tid][q]) : fmax(v, s_red[tid][q]);
-        s_red[tid][0] = v;
-        bbox[tid] = v;
-    }
-    __syncthreads();
-    if (tid < 3) {
-        s_lo[tid] = s_red[tid][0];
-        s_inv[tid] = (s_red[3 + tid][0] > s_red[tid][0]) ? 1.0 / (s_red[3 + tid][0] - s_red[tid][0]) : 0.0;
-    }
-    __syncthreads();
-    const double3 blo = make_double3(s_lo[0], s_lo[1], s_lo[2]);
-    const double3 binv = make_double3(s_inv[0], s_inv[1], s_inv[2]);
-    unsigned long long c[E];
-#pragma unroll
-    for (int r = 0; r < E; ++r) {
-        const int i = base + r;
-        if (i < n) {
-            const double *p = xyz + (size_t)i * dim;
-            const uint32_t key = morton(p[0], p[1], dim == 3 ? p[2] : 0.0, dim, blo, binv);
-            c[r] = ((unsigned long long)(key & mask) << 32) | (unsigned)i;
-        } else {
-            c[r] = ~0ull;
-        }
-    }
-    bitonic_regs<E>(c, N, s_c);
-#pragma unroll
-    for (int r = 0; r < E; ++r) {
-        const int i = base + r;
-        if (i < n) {
-            const uint32_t o = (uint32_t)c[r];
-            const double *p = xyz + (size_t)o * dim, *q = dS + (size_t)o * dim;
-            perm[i] = o;
-            xs[i] = make_double4(p[0], p[1], dim == 3 ? p[2] : 0.0, 0.0);
-            ds[i] = make_double4(q[0], q[1], dim == 3 ? q[2] : 0.0, 0.0);
-            inv[o] = (uint32_t)i;
-        }
-    }
-}
-
 void radix_sort_pairs(uint32_t *keys, uint32_t *vals, size_t n, int key_bits, SortScratch &s, cudaStream_t st) {
     if (n <= 1) return;
     if (n <= (size_t)kSmallSort) {
@@ -503,28 +428,6 @@ void morton_keys_f32(const float4 *xyzd, const uint32_t *idx, size_t n, int dim,
     if (!n) return;
     k_morton_f32<<<grid1(n, 256), 256, 0, st>>>(xyzd, idx, n, dim, lo, inv_extent(lo, hi), keys, vals);
     RBFD_CUDA(cudaGetLastError());
-}
-
-bool surface_order_small(const double *xyz, const double *dS, int64_t n, int dim, double *bbox, uint32_t *perm,
-                         double4 *xs, double4 *ds, uint32_t *inv, cudaStream_t st) {
-    if (n < 1 || n > kSmallSort) return false;
-    int N = 32;
-    while (N < (int)n) N <<= 1;
-    const int T = std::min(N, kSmallSortThreads), E = N / T;
-    const size_t smem = (size_t)N * 8;
-    const uint32_t mask = dim == 2 ? 0xffffffffu : ((1u << 30) - 1u);
-    auto launch = [&](auto kern) {
-        // (one value for every launch and device: the attribute belongs to the kernel)
-        if (smem > 40 * 1024)
-            RBFD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallSort * 8));
-        kern<<<1, T, smem, st>>>(xyz, dS, (int)n, N, dim, mask, bbox, perm, xs, ds, inv);
-    };
-    if (E == 1) launch(k_surface_order_small<1>);
-    else if (E == 2) launch(k_surface_order_small<2>);
-    else if (E == 4) launch(k_surface_order_small<4>);
-    else launch(k_surface_order_small<8>);
-    RBFD_CUDA(cudaGetLastError());
-    return true;
 }
 
 }  // namespace rbfd

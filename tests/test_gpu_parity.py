@@ -519,28 +519,6 @@ def test_run_jobs_matches_separate_calls():
     assert ei.value.status == rbfd.EINVAL and "mesh 1" in str(ei.value)
 
 
-@pytest.mark.parametrize("name", ["airfoil_horns_2lvl", "wing_ridge_2lvl"])
-def test_surface_order_one_launch_matches_multi_launch(name, monkeypatch):
-    """Surfaces of up to 8,192 points are ordered in one launch (box, Morton
-    keys, stable sort, gather); larger ones by separate box, key, radix-sort
-    and gather launches (test hook: those at any size).  The order, and so the
-    levels and the volume, are the same bit for bit."""
-    c = CASES[name]
-    res = []
-    for multi in ("0", "1"):
-        monkeypatch.setenv("RBFD_TEST_SURFACE_ORDER_MULTI", multi)
-        m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps)
-        m.greedy()
-        res.append((m.levels(), m.deform(c.xyz_v, c.d_v, c.D, c.k)))
-        m.close()
-    monkeypatch.delenv("RBFD_TEST_SURFACE_ORDER_MULTI")
-    (la, va), (lb, vb) = res
-    assert len(la) == len(lb)
-    for x, y in zip(la, lb):
-        assert np.array_equal(x.idx, y.idx) and np.array_equal(x.alpha, y.alpha)
-    assert np.array_equal(va, vb)
-
-
 def test_run_jobs_device_radii_and_capped_job():
     """In rbfd_run_jobs the volume update is queued behind the greedy without a
     host wait: D_l = min(k max|dS_l|, D) (or D when k = 0) is formed on the
