@@ -15,10 +15,14 @@ value   = useful point/control pair evaluations (|r - r_c| < R) of all timed
 e2e     = the same through host (pinned) buffers: host->device copies of the
           inputs and device->host copies of the results inside the timed region.
 roofline = the dominant kernel class by device time, its counted FP32-pipe
-          operations over that time against the FP32 issue rate;
+          operations over that time against the FP32 issue rate, its DRAM bytes
+          per launch from an ncu capture of the same workload, and the Newton
+          step's latency;
 cpu_baseline = the FP64 oracle on the host cores over a bounded sample;
-clocks = SM clocks sampled during the timed region; gpu_launches = the
-          library's kernel launches in the timed region.
+clocks = SM clocks and throttle reasons sampled (nvidia-smi, every 200 ms) from
+          the warm-up on, the same step kept running untimed until three
+          samples are in; gpu_launches = the library's kernel launches in the
+          timed region.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
