@@ -32,3 +32,25 @@ def test_reference_arm_json_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == bench.UNIT
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_clock_sampler_parses_nvidia_smi_lines():
+    """The clocks object of the bench line: median SM clock under load, the
+    highest max clock seen and every throttle reason reported Active."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    s = bench.ClockSampler(0)
+    s.proc = type("P", (), {"terminate": lambda self: None, "wait": lambda self, timeout=None: 0})()
+    s.lines = [
+        "1980, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "2070, 2070, 1100.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "2055, 2070, 1050.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ]
+    c = s.stop()
+    assert c == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    s.lines = ["1500, 2070, 1200.0, 0x20, Not Active, Active, Not Active, Not Active"]
+    assert s.stop()["reasons"] == ["hw_thermal_slowdown"]
+    s.lines = []
+    assert s.stop() is None
