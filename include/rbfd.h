@@ -299,15 +299,25 @@ int rbfd_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, int key_bits, voi
  * device and can fail in the middle of a run.  The paper has no counterpart;
  * this is a deployment variant of the same computation.
  *
- * Same arguments and result as rbfd_deform, with three differences:
- *   - xyz_v, d_v and out must be device memory (of the mesh's device);
+ * Same arguments as rbfd_deform, with these differences:
+ *   - xyz_v, d_v and out must be device memory of the mesh's GPU (float32,
+ *     n_v x dim, n_v and n_v x dim values); anything else returns RBFD_EINVAL;
+ *   - d_v is required (rbfd_deform computes missing wall distances; this call
+ *     cannot, since that needs scratch of its own): NULL returns RBFD_EINVAL;
  *   - n_v must not exceed 131072: every per-call buffer lives in one fixed
  *     device array of about 16 MB that each GPU loading the library holds
  *     until the process exits; larger n_v returns RBFD_EINVAL;
  *   - the call allocates nothing (no cudaMalloc/cudaFree, no allocating
  *     library routine).  On each device the first call looks up the array's
  *     device address once (cudaGetSymbolAddress); make that first call before
- *     any stream capture.
+ *     any stream capture;
+ *   - it returns once its work on the mesh's stream has finished (it reads
+ *     one count back to size its sort, and waits for its end event);
+ *   - results: in FP64 mode the same per-point FP64 sums as rbfd_deform (only
+ *     the grouping of points into blocks differs: agreement to rounding, far
+ *     inside 1e-10 max|dS|); in mixed mode it runs the double-float sweep on
+ *     FP64-packed points rather than rbfd_deform's FP32-input sweep, so the two
+ *     agree within the mixed-mode bound of 1e-5 max|dS|, not bit for bit.
  * All calls share the array and it keeps the previous call's contents (the
  * call clears what must start at zero).  Calls whose work overlaps on the
  * GPU (two host threads, or two meshes on different streams) race on it: run

@@ -15,7 +15,9 @@ from __future__ import annotations
 
 import ctypes
 import dataclasses
+import hashlib
 import os
+import platform
 import subprocess
 import threading
 
@@ -35,8 +37,15 @@ def build(force: bool = False, src: str = _SRC, out: str = _LIB) -> str:
     """Compile the oracle C source (gcc, -O2, -ffp-contract=off, OpenMP when
     the compiler supports it) into a shared library; returns its path."""
     os.makedirs(os.path.dirname(out), exist_ok=True)
-    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
-        return out
+    # the source's hash and the machine: a library built elsewhere or from
+    # another source is never taken for current
+    with open(src, "rb") as fh:
+        stamp = hashlib.sha256(platform.machine().encode() + fh.read()).hexdigest()
+    stamp_path = out + ".stamp"
+    if not force and os.path.exists(out) and os.path.exists(stamp_path):
+        with open(stamp_path) as fh:
+            if fh.read().strip() == stamp:
+                return out
     base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11"]
     tmp = out + f".tmp{os.getpid()}"
     try:
@@ -44,6 +53,8 @@ def build(force: bool = False, src: str = _SRC, out: str = _LIB) -> str:
     except subprocess.CalledProcessError:
         subprocess.run(base + [src, "-o", tmp, "-lm"], check=True, capture_output=True)
     os.replace(tmp, out)
+    with open(stamp_path, "w") as fh:
+        fh.write(stamp + "\n")
     return out
 
 

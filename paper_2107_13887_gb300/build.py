@@ -10,7 +10,9 @@ extension machinery: the library has no torch dependency.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import hashlib
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -38,11 +40,28 @@ def _deps():
     return files
 
 
+STAMP = os.path.join(OUT_DIR, "librbfd.stamp")
+
+
+def _fingerprint() -> str:
+    """Hash of every source the library is built from, the build flags and
+    the machine it is built on: a library copied from another machine or built
+    from other sources never passes for current."""
+    h = hashlib.sha256()
+    h.update(platform.machine().encode())
+    h.update(" ".join(ARCH).encode())
+    for f in sorted(_deps()):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(STAMP)):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(f) <= t for f in _deps())
+    with open(STAMP) as fh:
+        return fh.read().strip() == _fingerprint()
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -74,6 +93,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(_fingerprint() + "\n")
     return LIB
 
 

@@ -1137,9 +1137,12 @@ constexpr int64_t kNoAllocMaxPoints = 1 << 17;  // 131,072 volume points per cal
 constexpr size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 constexpr size_t kNaD4 = al256(sizeof(double4) * (size_t)kNoAllocMaxPoints);
 constexpr size_t kNaU32 = al256(sizeof(uint32_t) * (size_t)kNoAllocMaxPoints);
-constexpr size_t kNaSortBlocks = (size_t)kNoAllocMaxPoints / 2048 + 1;      // radix tiles of 2048 (+1)
-constexpr size_t kNaHistN = 256 * kNaSortBlocks;
-constexpr size_t kNaSumsN = (kNaHistN + 2047) / 2048 + (size_t)kNoAllocMaxPoints / 2048 + 4;
+// the sort and scan scratch at their largest (SortScratch::reserve's own
+// formulas): reserve() then never allocates for a call of up to
+// kNoAllocMaxPoints points
+constexpr size_t kNaHistN = sort_hist_need((size_t)kNoAllocMaxPoints);
+constexpr size_t kNaSumsN = sort_sums_need((size_t)kNoAllocMaxPoints);
+static_assert(kNaHistN >= sort_hist_need(1) && kNaSumsN >= sort_sums_need(1), "scratch sizes grow with n");
 constexpr size_t kNaBytes = 3 * kNaD4 + 7 * kNaU32 + al256(sizeof(uint32_t) * kNaHistN) +
                             al256(sizeof(uint32_t) * kNaSumsN);
 
@@ -1233,12 +1236,11 @@ void deform_noalloc_run(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const flo
             k_flag_below<<<cdiv(nV, 256), 256, 0, st>>>(vin, nullptr, nV, Dl[l], vflag);
             exclusive_scan_u32(vflag, vscan, (size_t)nV, &m->d_misc[7], ss, st);
             k_compact<<<cdiv(nV, 256), 256, 0, st>>>(vflag, vscan, nV, vlist);
-            uint32_t nl = 0;
-            RBFD_CUDA(cudaMemcpyAsync(&nl, &m->d_misc[7], sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-            RBFD_CUDA(cudaStreamSynchronize(st));
-            if (nl == 0) continue;
+            // the level's list length stays on the device (the sweep reads
+            // it, nV is its upper bound): no host wait per level
             VolArgs a{};
-            a.n_list = nl;
+            a.n_list = nV;
+            a.n_list_dev = &m->d_misc[7];
             a.list = vlist;
             a.vpos = vin;
             a.vacc = vacc;
@@ -1255,7 +1257,7 @@ void deform_noalloc_run(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const flo
             a.invR_hi = (float)inv;
             a.invR_lo = (float)(inv - (double)a.invR_hi);
             a.pairs = m->d_pairs + 2;
-            launch_vol(dim, m->opt.basis, mode, cdiv(nl, kThreads), a, st);
+            launch_vol(dim, m->opt.basis, mode, cdiv(nV, kThreads), a, st);
             RBFD_CUDA(cudaGetLastError());
             m->stats.launches += 4;
         }
@@ -1270,13 +1272,14 @@ void deform_noalloc_run(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const flo
     m->stats.deform_ms = ms;
 }
 
-bool na_is_device_ptr(const void *p) {
+// p is device (or managed) memory of GPU `device`
+bool na_is_device_ptr(const void *p, int device) {
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == device;
 }
 
 }  // namespace
@@ -1296,9 +1299,9 @@ extern "C" int rbfd_deform_noalloc(rbfd_mesh *m, int64_t n_v, const float *xyz_v
         if (!m->greedy_done) rbfd::fail(RBFD_ESTATE, "rbfd_deform_noalloc: run rbfd_greedy first");
         if ((int)m->levels.size() > 64) rbfd::fail(RBFD_EINVAL, "rbfd_deform_noalloc: more than 64 levels");
         RBFD_CUDA(cudaSetDevice(m->device));
-        if (n_v > 0 && (!rbfd::na_is_device_ptr(xyz_v) || !rbfd::na_is_device_ptr(d_v) ||
-                        !rbfd::na_is_device_ptr(out)))
-            rbfd::fail(RBFD_EINVAL, "rbfd_deform_noalloc: xyz_v, d_v and out must be device memory");
+        if (n_v > 0 && (!rbfd::na_is_device_ptr(xyz_v, m->device) || !rbfd::na_is_device_ptr(d_v, m->device) ||
+                        !rbfd::na_is_device_ptr(out, m->device)))
+            rbfd::fail(RBFD_EINVAL, "rbfd_deform_noalloc: xyz_v, d_v and out must be device memory of the mesh's GPU");
         rbfd::deform_noalloc_run(m, n_v, xyz_v, d_v, D, k, out);
         rbfd::set_last_error("");
         return RBFD_OK;

@@ -41,6 +41,18 @@ T *dalloc(size_t n, const char *what) {
 
 // ------------------------------------------------------------ spatial prep
 
+// Tile sizes of the radix sort and of the scan (keys per block), and the
+// scratch capacities they need for n keys: SortScratch::reserve grows to
+// these, and fixed scratch arrays are sized by them.
+constexpr int kSortTile = 2048;
+constexpr int kScanTile = 2048;
+constexpr size_t sort_hist_need(size_t n) { return 256 * ((n + kSortTile - 1) / kSortTile + 1); }
+constexpr size_t sort_sums_need(size_t n) {
+    return ((sort_hist_need(n) + kScanTile - 1) / kScanTile > (n + kScanTile - 1) / kScanTile
+                ? (sort_hist_need(n) + kScanTile - 1) / kScanTile
+                : (n + kScanTile - 1) / kScanTile) + 2;
+}
+
 // Scratch for the radix sort / scan / compaction primitives (grown on demand).
 struct SortScratch {
     int64_t *launches = nullptr;  // kernel launch counter of the owning mesh

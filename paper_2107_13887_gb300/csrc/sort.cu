@@ -18,6 +18,7 @@ constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int SC_THREADS = 256;
 constexpr int SC_ITEMS = 8;
 constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
+static_assert(RS_TILE == kSortTile && SC_TILE == kScanTile, "tile sizes of internal.h");
 
 __global__ void k_rs_hist(const uint32_t *__restrict__ keys, size_t n, int shift, uint32_t dmask,
                           uint32_t *__restrict__ hist, int nblk) {
@@ -226,7 +227,6 @@ inline unsigned grid1(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 }  // namespace
 
 void SortScratch::reserve(size_t n) {
-    size_t nb = (n + RS_TILE - 1) / RS_TILE + 1;
     if (n > cap_items) {
         dfree(keys_alt);
         dfree(vals_alt);
@@ -234,12 +234,13 @@ void SortScratch::reserve(size_t n) {
         vals_alt = dalloc<uint32_t>(n, "sort values");
         cap_items = n;
     }
-    if (256 * nb > cap_hist) {
+    const size_t nh = sort_hist_need(n);
+    if (nh > cap_hist) {
         dfree(hist);
-        hist = dalloc<uint32_t>(256 * nb, "sort histogram");
-        cap_hist = 256 * nb;
+        hist = dalloc<uint32_t>(nh, "sort histogram");
+        cap_hist = nh;
     }
-    size_t ns = std::max((256 * nb + SC_TILE - 1) / SC_TILE, (n + SC_TILE - 1) / SC_TILE) + 2;
+    const size_t ns = sort_sums_need(n);
     if (ns > cap_sums) {
         dfree(block_sums);
         block_sums = dalloc<uint32_t>(ns, "scan block sums");

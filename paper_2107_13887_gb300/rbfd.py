@@ -424,9 +424,20 @@ class Mesh:
 
     def deform_noalloc(self, xyz_v, d_v, D: float, k: float, out):
         """``rbfd_deform_noalloc``: float32 torch CUDA tensors in, result written
-        into ``out`` (a preallocated float32 CUDA tensor); at most 131,072 points."""
-        _check(self._lib.rbfd_deform_noalloc(self.h, int(xyz_v.shape[0]), _ptr(xyz_v), _ptr(d_v), float(D), float(k),
-                                             _ptr(out)))
+        into ``out`` (a preallocated float32 CUDA tensor); at most 131,072 points.
+        The shapes, dtypes and layout are checked here, since the library sees
+        only pointers: xyz_v and out [n_v, dim], d_v [n_v], all contiguous."""
+        import torch
+
+        n_v = int(xyz_v.shape[0]) if xyz_v.dim() == 2 else -1
+        for name, t, shape in (("xyz_v", xyz_v, (n_v, self.dim)), ("d_v", d_v, (n_v,)),
+                               ("out", out, (n_v, self.dim))):
+            if t is None or not isinstance(t, torch.Tensor):
+                raise RbfdError(EINVAL, f"rbfd_deform_noalloc: {name} must be a tensor")
+            if t.dtype != torch.float32 or not t.is_contiguous() or tuple(t.shape) != shape:
+                raise RbfdError(EINVAL, f"rbfd_deform_noalloc: {name} must be a contiguous float32 tensor of "
+                                        f"shape {shape}, got {t.dtype} {tuple(t.shape)}")
+        _check(self._lib.rbfd_deform_noalloc(self.h, n_v, _ptr(xyz_v), _ptr(d_v), float(D), float(k), _ptr(out)))
         return out
 
 
