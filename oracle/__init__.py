@@ -77,6 +77,9 @@ def _bind(path: str):
     lib.orc_greedy.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp, ctypes.c_int, dp, ctypes.c_double,
                                ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                i64p, i64p, dp, dp, dp, dp, dp, dp]
+    lib.orc_replay.restype = ctypes.c_int
+    lib.orc_replay.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp, ctypes.c_int, dp, ctypes.c_int,
+                               ctypes.c_int64, i64p, i64p, ctypes.c_int, dp, dp, dp, dp, dp, dp]
     lib.orc_support_distances.restype = None
     lib.orc_support_distances.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp]
     lib.orc_deform.restype = ctypes.c_int
@@ -224,6 +227,49 @@ def greedy(xyz_s, dS, R, eps, basis="C2", nc_cap=None, first_rule=0, solve_mode=
     return GreedyResult(rc, [idx[l, : nc[l]].copy() for l in range(L)],
                         [alpha[l, : nc[l]].copy() for l in range(L)], smax, emax, gap, E, S0,
                         [sg[l, : nc[l]].copy() for l in range(L)])
+
+
+@dataclasses.dataclass
+class ReplayResult:
+    """Per level l, per slot k = 1 .. n_l (before given control k is added;
+    slot n_l after the last one): the largest key among unselected points,
+    the key of the given control (of that best point at slot n_l), and the
+    rounding scales |dS_l,i| + sum_j |alpha_j| phi_ij of E at both points."""
+    best_key: list
+    pick_key: list
+    best_scale: list
+    pick_scale: list
+    alpha: list
+    smax: np.ndarray
+
+
+def replay(xyz_s, dS, R, given, basis="C2", n_threads=1, lib=None):
+    """Replay the control sequences ``given`` (one index array per level)
+    through the greedy of Section 3 (see orc_replay in rbfd_oracle.c)."""
+    lib = lib or _load()
+    xyz_s = _f64(xyz_s)
+    dS = _f64(dS)
+    n_s, dim = xyz_s.shape
+    R = _f64(np.atleast_1d(R))
+    L = R.shape[0]
+    if len(given) != L:
+        raise ValueError("one given sequence per level")
+    cap = max(1, max(len(g) for g in given))
+    gnc = np.array([len(g) for g in given], dtype=np.int64)
+    gidx = np.zeros((L, cap), dtype=np.int64)
+    for l, g in enumerate(given):
+        gidx[l, : len(g)] = np.asarray(g, dtype=np.int64)
+    alpha = np.zeros(L * cap * dim)
+    smax = np.zeros(L)
+    bk, pk, bs, ps = (np.zeros(L * (cap + 1)) for _ in range(4))
+    rc = lib.orc_replay(dim, n_s, _dp(xyz_s), _dp(dS), L, _dp(R), BASIS[basis], cap, _ip(gnc),
+                        _ip(gidx.reshape(-1)), int(n_threads), _dp(alpha), _dp(smax), _dp(bk), _dp(pk), _dp(bs),
+                        _dp(ps))
+    if rc != OK:
+        raise RuntimeError(f"oracle replay failed with status {rc}")
+    alpha = alpha.reshape(L, cap, dim)
+    cut = lambda a: [a.reshape(L, cap + 1)[l, 1 : gnc[l] + 1].copy() for l in range(L)]
+    return ReplayResult(cut(bk), cut(pk), cut(bs), cut(ps), [alpha[l, : gnc[l]].copy() for l in range(L)], smax)
 
 
 def support_distances(smax, k: float, D: float, lib=None):

@@ -362,6 +362,135 @@ done:
     return status;
 }
 
+/*
+ * Replay of a given control sequence through the greedy of Section 3, as a
+ * check of another implementation's choices (test infrastructure).
+ *
+ * Level by level, the controls are given[l*nc_cap + j] for j < given_nc[l]
+ * (the first one included) instead of being chosen here; everything else is
+ * orc_greedy's arithmetic: Eq. 9 solved on the controls so far, Eq. 12 by
+ * brute force, keys |E_i|^2, and the next level's target is the replayed
+ * level's error.  Before appending given control k (k >= 1), and once more
+ * after the last one (slot k = given_nc[l]), the step is recorded at
+ * [l*(nc_cap+1) + k]:
+ *   best_key   the largest key over the points not yet selected (the point
+ *              this oracle would pick);
+ *   pick_key   the key of the given control k (of the best point at the last
+ *              slot, where nothing is picked);
+ *   best_scale, pick_scale   the rounding scale of E at those two points,
+ *              |dS_l,i|_2 + sum_j |alpha_j|_2 phi_ij: two evaluations of
+ *              Eq. 12 that sum in different orders differ by a few n u times it.
+ * alpha_out[(l*nc_cap + j)*dim + k] receives the weights of the replayed
+ * levels, smax_out[l] the max |dS_l|.  Returns ORC_OK, ORC_EINVAL (a given
+ * index out of range or repeated in a level), ORC_ESINGULAR or ORC_ENOMEM.
+ */
+int orc_replay(int dim, int64_t n_s, const double *xyz_s, const double *dS, int n_levels,
+               const double *R, int basis, int64_t nc_cap, const int64_t *given_nc, const int64_t *given,
+               int n_threads, double *alpha_out, double *smax_out, double *best_key, double *pick_key,
+               double *best_scale, double *pick_scale)
+{
+    if ((dim != 2 && dim != 3) || n_s < 1 || n_levels < 1 || nc_cap < 1 || !xyz_s || !dS || !R || !given_nc ||
+        !given || !alpha_out || !smax_out || !best_key || !pick_key || !best_scale || !pick_scale)
+        return ORC_EINVAL;
+    for (int l = 0; l < n_levels; ++l) {
+        if (!(R[l] > 0.0) || given_nc[l] < 1 || given_nc[l] > nc_cap) return ORC_EINVAL;
+        for (int64_t j = 0; j < given_nc[l]; ++j)
+            if (given[l * nc_cap + j] < 0 || given[l * nc_cap + j] >= n_s) return ORC_EINVAL;
+    }
+    int status = ORC_OK;
+    double *cur = (double *)malloc(sizeof(double) * (size_t)(n_s * dim));
+    double *E = (double *)malloc(sizeof(double) * (size_t)(n_s * dim));
+    unsigned char *sel = (unsigned char *)malloc((size_t)n_s);
+    double *L = (double *)malloc(sizeof(double) * (size_t)(nc_cap * nc_cap));
+    double *arow = (double *)malloc(sizeof(double) * (size_t)(nc_cap + 1));
+    double *b = (double *)malloc(sizeof(double) * (size_t)(nc_cap * dim));
+    double *xc = (double *)malloc(sizeof(double) * (size_t)(nc_cap * dim));
+    if (!cur || !E || !sel || !L || !arow || !b || !xc) {
+        status = ORC_ENOMEM;
+        goto done;
+    }
+    memcpy(cur, dS, sizeof(double) * (size_t)(n_s * dim));
+    for (int l = 0; l < n_levels; ++l) {
+        const double Rl = R[l];
+        const int64_t nl = given_nc[l];
+        const int64_t *gl = given + l * nc_cap;
+        double *alpha = alpha_out + l * nc_cap * dim;
+        double smax = 0.0;
+        for (int64_t i = 0; i < n_s; ++i) {
+            double v = norm2sq(cur + i * dim, dim);
+            if (v > smax) smax = v;
+        }
+        smax_out[l] = sqrt(smax);
+        memset(sel, 0, (size_t)n_s);
+        int64_t n = 1;
+        sel[gl[0]] = 1;
+        memcpy(xc, xyz_s + gl[0] * dim, sizeof(double) * (size_t)dim);
+        arow[0] = orc_phi(basis, 0.0);
+        if (chol_row(L, nc_cap, 0, arow, L) != 0) {
+            status = ORC_ESINGULAR;
+            goto done;
+        }
+        for (;;) {
+            for (int64_t j = 0; j < n; ++j)
+                for (int k = 0; k < dim; ++k) b[j * dim + k] = cur[gl[j] * dim + k];
+            orc_chol_solve(n, L, nc_cap, dim, b, alpha);
+            orc_eval(dim, basis, Rl, n, xc, alpha, n_s, xyz_s, E, n_threads);
+            for (int64_t i = 0; i < n_s * dim; ++i) E[i] = cur[i] - E[i];
+            int64_t best = -1;
+            double bestv = -1.0;
+            for (int64_t i = 0; i < n_s; ++i) {
+                if (sel[i]) continue;
+                double v = norm2sq(E + i * dim, dim);
+                if (v > bestv) {
+                    bestv = v;
+                    best = i;
+                }
+            }
+            const int64_t pick = n < nl ? gl[n] : best;
+            const int64_t slot = l * (nc_cap + 1) + n;
+            best_key[slot] = bestv;
+            pick_key[slot] = pick >= 0 ? norm2sq(E + pick * dim, dim) : -1.0;
+            for (int which = 0; which < 2; ++which) {
+                const int64_t i = which == 0 ? best : pick;
+                double sc = 0.0;
+                if (i >= 0) {
+                    sc = sqrt(norm2sq(cur + i * dim, dim));
+                    for (int64_t j = 0; j < n; ++j)
+                        sc = sc + sqrt(norm2sq(alpha + j * dim, dim)) *
+                                      orc_phi(basis, dist(xyz_s + i * dim, xc + j * dim, dim) / Rl);
+                }
+                if (which == 0) best_scale[slot] = sc;
+                else pick_scale[slot] = sc;
+            }
+            if (n == nl) break;
+            if (sel[pick]) {
+                status = ORC_EINVAL; /* a control given twice in one level */
+                goto done;
+            }
+            const double *xb = xyz_s + pick * dim;
+            for (int64_t j = 0; j < n; ++j) arow[j] = orc_phi(basis, dist(xb, xc + j * dim, dim) / Rl);
+            arow[n] = orc_phi(basis, 0.0);
+            sel[pick] = 1;
+            memcpy(xc + n * dim, xb, sizeof(double) * (size_t)dim);
+            if (chol_row(L, nc_cap, n, arow, L + n * nc_cap) != 0) {
+                status = ORC_ESINGULAR;
+                goto done;
+            }
+            ++n;
+        }
+        memcpy(cur, E, sizeof(double) * (size_t)(n_s * dim));
+    }
+done:
+    free(cur);
+    free(E);
+    free(sel);
+    free(L);
+    free(arow);
+    free(b);
+    free(xc);
+    return status;
+}
+
 /* ----------------------------------------------------------- volume update */
 
 /* Support distance per level (Section 4): D_l = k * max_i |dS_l,i| (capped at

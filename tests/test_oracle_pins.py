@@ -231,6 +231,60 @@ def pin_greedy(o, case, first_rule=0):
     return bad
 
 
+def pin_replay(o, case, seed=0):
+    """Replay of a given (non-greedy, random) control sequence: at every slot
+    the weights solve Eq. 9 on the controls so far (numpy.linalg.solve), the
+    best key is the largest |E_i|^2 of Eq. 12 over unselected points (dense
+    numpy product), the pick key is that of the given control, and the scale
+    is |dS_l,i| + sum_j |alpha_j| phi_ij at both points; the next level's target
+    is the replayed level's error.  Replaying the greedy's own sequence picks
+    the best point at every step."""
+    bad = []
+    rng = np.random.default_rng(seed)
+    given = [rng.permutation(case.n_s)[: min(case.n_s, 12 + 5 * l)] for l in range(len(case.R))]
+    rp = o.replay(case.xyz_s, case.dS, case.R, given)
+    cur = case.dS.copy()
+    S0 = float(np.sqrt((case.dS**2).sum(1)).max())
+    for l, R in enumerate(case.R):
+        g = list(given[l])
+        if abs(rp.smax[l] - np.sqrt((cur**2).sum(1)).max()) > 1e-14 * S0:
+            bad.append(f"replay level {l}: smax")
+        for k in range(1, len(g) + 1):
+            C = g[:k]
+            A = phi_expanded(cdist(case.xyz_s[C], case.xyz_s[C]) / R)
+            a = np.linalg.solve(A, cur[C])
+            P = phi_expanded(cdist(case.xyz_s, case.xyz_s[C]) / R)
+            E = cur - P @ a
+            key = (E**2).sum(1)
+            key[C] = -1.0
+            best = int(np.argmax(key))
+            pick = g[k] if k < len(g) else best
+            sc = np.sqrt((cur**2).sum(1)) + P @ np.sqrt((a**2).sum(1))
+            tol = 1e-9 * key[best] + 1e-24
+            if abs(rp.best_key[l][k - 1] - key[best]) > tol:
+                bad.append(f"replay level {l} slot {k}: best key {rp.best_key[l][k - 1]:g} != {key[best]:g}")
+                break
+            if abs(rp.pick_key[l][k - 1] - key[pick]) > 1e-9 * max(key[pick], key[best]) + 1e-24:
+                bad.append(f"replay level {l} slot {k}: pick key")
+                break
+            if abs(rp.pick_scale[l][k - 1] - sc[pick]) > 1e-9 * sc[pick]:
+                bad.append(f"replay level {l} slot {k}: pick scale")
+                break
+            if abs(rp.best_scale[l][k - 1] - sc[best]) > 1e-9 * sc[best]:
+                bad.append(f"replay level {l} slot {k}: best scale")
+                break
+            if k == len(g):
+                if np.abs(rp.alpha[l] - a).max() > 1e-7 * (np.abs(a).max() + S0):
+                    bad.append(f"replay level {l}: weights differ from numpy.linalg.solve")
+                cur = cur - P @ a
+    res = o.greedy(case.xyz_s, case.dS, case.R, case.eps)
+    own = o.replay(case.xyz_s, case.dS, case.R, res.idx)
+    for l in range(len(case.R)):
+        if not np.array_equal(own.best_key[l][:-1], own.pick_key[l][:-1]):
+            bad.append(f"replay of the greedy's own sequence: level {l} picks below the best key")
+    return bad
+
+
 def pin_dense_limit(o):
     """With eps -> 0 every surface point becomes a control and the result is
     the full RBF system of Eq. 9 / Eq. 10 solved densely."""
@@ -397,6 +451,8 @@ def all_pins(o):
     bad += pin_greedy(o, tiny_airfoil(n=60, displacement="horns", R=(1.0, 0.2), eps=1e-6))
     bad += pin_greedy(o, tiny_wing())
     bad += pin_dense_limit(o)
+    bad += pin_replay(o, tiny_airfoil(n=60, displacement="horns", R=(1.0, 0.2), eps=1e-6))
+    bad += pin_replay(o, tiny_wing(), seed=1)
     bad += pin_deform(o, tiny_airfoil_k5())
     bad += pin_deform(o, tiny_wing())
     bad += pin_wall_distance(o)
@@ -450,6 +506,11 @@ def test_greedy_first_rule_argmax():
 
 def test_greedy_wing_3d():
     assert pin_greedy(oracle, tiny_wing()) == []
+
+
+def test_replay_of_given_sequences():
+    assert pin_replay(oracle, tiny_airfoil(n=60, displacement="horns", R=(1.0, 0.2), eps=1e-6)) == []
+    assert pin_replay(oracle, tiny_wing(), seed=1) == []
 
 
 def test_dense_limit():
@@ -549,6 +610,10 @@ MUTATIONS = {
     "distance drops z": ("for (int k = 0; k < dim; ++k) {\n        double d = a[k] - b[k];",
                          "for (int k = 0; k < 2; ++k) {\n        double d = a[k] - b[k];"),
     "first control not point 0": ("int64_t first = 0;", "int64_t first = 1;"),
+    "replay records the key before the pick's": ("pick_key[slot] = pick >= 0 ? norm2sq(E + pick * dim, dim) : -1.0;",
+                                                 "pick_key[slot] = pick >= 0 ? norm2sq(E + best * dim, dim) : -1.0;"),
+    "replay scale drops the weights": ("sc = sc + sqrt(norm2sq(alpha + j * dim, dim)) *",
+                                       "sc = sc + 0.0 * sqrt(norm2sq(alpha + j * dim, dim)) *"),
     "wall distance skips the last point": ("for (int64_t i = 0; i < n_s; ++i) {\n            double r = dist(",
                                            "for (int64_t i = 0; i < n_s - 1; ++i) {\n            double r = dist("),
     "orthogonality drops the ring-closing cell": ("int64_t n_ci = periodic_i ? n_i : n_i - 1;",
