@@ -1,34 +1,50 @@
-"""Benchmark: RBF pair-evaluations/s of the multi-level greedy RBF mesh
-deformation hot path on one GB300 (or N replicas under torchrun).
+"""Benchmark: the multi-level greedy RBF mesh deformation hot path on one
+GB300 (or N replicas under torchrun).
 
-One step = the whole path for the 2D airfoil workload of 4,000 surface and
-1,000,000 volume points, two greedy levels (R = 1c then 0.2c), eps = 1e-5,
-for both displacement cases: a global rigid pitch (5 deg) + heave (0.05c), and
-a three-horn ice shape.  For each case: rbfd_create (Morton prep), rbfd_greedy
-(both levels, to eps), rbfd_deform (volume point reduction + update of every
-volume point), the cases side by side; the counters are read and the meshes
+One step = the whole path for the 3D swept-wing workload: 60,000 surface
+points (400 chordwise x 150 spanwise), 6,000,000 volume points, three greedy
+levels (R = 1.5c, 0.4c, 0.1c), eps = 1e-5, volume reduction factor k = 4 with
+D = 1c, a leading-edge ice ridge.  rbfd_create (Morton preparation of the
+surface), rbfd_greedy (every level to its tolerance, about 31,000 controls)
+and rbfd_deform (volume point reduction and the psi-blended update of every
+volume point), as one rbfd_run_jobs call; the counters are read and the mesh
 destroyed after the timed region.
 
-value   = useful point/control pair evaluations (|r - r_c| < R) of all timed
-          steps on all ranks / max over ranks of the device time (CUDA events on
-          the library's stream), inputs resident in HBM, L2 flushed between steps.
-e2e     = the same through host (pinned) buffers: host->device copies of the
-          inputs and device->host copies of the results inside the timed region.
-roofline = the dominant kernel class by device time, its counted FP32-pipe
-          operations over that time against the FP32 issue rate, its DRAM bytes
-          per launch from an ncu capture of the same workload, and the Newton
-          step's latency;
-cpu_baseline = the FP64 oracle on the host cores over a bounded sample;
-clocks = SM clocks and throttle reasons sampled (nvidia-smi, every 200 ms) from
-          the warm-up on, the same step kept running untimed until three
-          samples are in; gpu_launches = the library's kernel launches in the
-          timed region.
+value    = RBF pair evaluations with |r - r_c| < R that the kernels performed
+           (list sweeps of Eq. 12, the Newton-basis update's phi values, the
+           volume update of Eq. 23) over the timed steps on all ranks / max
+           over ranks of the device time (CUDA events on the launching stream),
+           inputs resident in HBM; L2 is flushed between steps and the volume
+           (96 MB in, 72 MB out, plus the packed copies) exceeds it anyway.
+           Eq. 12's own pair count for every greedy step (what a list sweep of
+           each step evaluates) is reported beside it as eq12_pairs_per_step.
+time_to_eps_ms = device time of rbfd_greedy (all levels to eps).
+e2e      = the same through host (pinned) buffers: host->device copies of the
+           inputs and device->host copy of the volume displacement inside the
+           timed region.
+roofline = the dominant kernel by device time (library profiler, CUDA events
+           on the mesh's stream): its useful pair evaluations x the FP32-pipe
+           operations of one plain FP32 pair (13 in 2D, 16 in 3D) over its
+           launch time, against the FP32 issue rate (SMs x 128 lanes x max SM
+           clock); the same with the double-float evaluation's own operation
+           count beside it; per-phase times of the persistent launch; the
+           volume sweep's own figures.  traffic: DRAM bytes per launch from an
+           ncu capture, only while the kernel source is the one captured.
+cpu_baseline = the FP64 oracle on the host cores over a bounded sample: the
+           first K greedy steps of every level and a volume subset (the full
+           greedy of 31,000 controls would take the oracle hours); the full
+           step's oracle time is extrapolated from it and labelled so.
+clocks   = SM clocks and throttle reasons sampled by nvidia-smi every 200 ms
+           over the warm-up and timed steps; gpu_launches = the library's
+           kernel launches in the timed region.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision mixed|fp64] [--workload NAME]
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -43,37 +59,47 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "naca0012_4000s_1mv"
-CASES = ("naca0012_4000s_1mv_pitch_heave", "naca0012_4000s_1mv_horns")
+WORKLOAD = "wing_60ks_6mv_ridge"
+CASES = (WORKLOAD,)
 METRIC = "rbf_pair_evals_per_s"
 UNIT = "pair-evals/s"
 
-# FP32-pipe operations per useful pair of the double-float evaluation, counted
-# from csrc/common.cuh (df_add 20, df_mul 7, df_sqr 7, df_sqrt 12 incl. MUFU).
-# 2D: differences 2 x 20, r^2 2 x 7 + 20,
-# sqrt 12, eta 7, phi 63, accumulate 2 x 27 -> 210; 3D -> 284.
+# FP32-pipe operations of one useful pair evaluated in plain FP32 (the
+# evaluation's algorithmic unit: differences, r^2, rsqrt-based eta, phi, three
+# accumulating FMAs; 2D has two coordinates and two components)
+OPS_PER_PAIR_FP32 = {2: 13, 3: 16}
+# FP32-pipe operations of one pair in the double-float evaluation the mixed
+# mode runs, counted from csrc/common.cuh (df_add 20, df_mul 7, df_sqr 7,
+# df_sqrt 12 incl. MUFU): 2D differences 2 x 20, r^2 2 x 7 + 20, sqrt 12,
+# eta 7, phi 63, accumulate 2 x 27 -> 210; 3D -> 284
 OPS_PER_PAIR_DF = {2: 210, 3: 284}
-CPU_BASELINE_S = 10.0  # seconds of oracle time behind the cpu_baseline figure
-OPS_PER_NEWTON_TERM = 12  # df multiply-add of a basis value: TwoProduct by FMA (4), TwoSum (6), two adds
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+CPU_BASELINE_S = 15.0  # about this much oracle time behind the cpu_baseline figure
+
+# DRAM bytes (read + written) per launch from an ncu capture, each with the
+# SHA-256 prefix of the kernel's source file when it was captured: a figure
+# whose source has changed since is reported as null
+DRAM_BYTES_PER_LAUNCH = {}
 
 
-def parse_args():
+def parse_args(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=2)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--engine", type=int, default=0,
                    help="0: Newton-basis start + persistent list sweep, 2: persistent list sweep, 1: launches per step")
     p.add_argument("--ctas", type=int, default=0, help="blocks of the persistent launch (0: automatic)")
     p.add_argument("--no-serve", action="store_true", help="skip the serving leg (p50/p99 latency)")
-    p.add_argument("--serve-requests", type=int, default=200)
-    return p.parse_args()
+    p.add_argument("--serve-requests", type=int, default=1000)
+    p.add_argument("--oracle-steps", type=int, default=0,
+                   help="greedy steps per level of the oracle sample (0: sized to about 15 s)")
+    return p.parse_args(argv)
 
 
 def dist_env():
@@ -103,66 +129,90 @@ def reference_rank_works(rank):
     return rank == 0
 
 
-def make_cases():
+def make_case(name):
     from paper_2107_13887_gb300 import synth
 
-    return [synth.make_config(n, seed=0) for n in CASES]
+    return synth.make_config(name, seed=0)
 
 
-# ------------------------------------------------------------ useful pairs
+def workload_config(c):
+    return {"workload": c.name, "cases": [c.name], "n_surface": int(c.n_s), "n_volume": int(c.n_v),
+            "dim": int(c.dim), "levels": len(c.R), "R": list(c.R), "eps": c.eps, "k": c.k, "D": c.D}
 
-def useful_pairs_oracle_run(case, res, Dl, sample_idx=None):
-    """Useful pair evaluations (|r - r_c| < R) of the oracle's own run:
-    every greedy sweep (one per added control, plus the stopping sweep) and
-    the volume update of the sampled volume points."""
+
+def source_sha16(rel):
+    with open(os.path.join(ROOT, "paper_2107_13887_gb300", "csrc", rel), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+# ------------------------------------------------------------ oracle sample
+
+def oracle_sample(c, k_steps, n_vol, n_threads=None, seed=0):
+    """The FP64 oracle on a bounded sample of the workload: the first
+    k_steps greedy steps of every level (nc_cap = k_steps; each later level
+    takes the capped level's error) and the volume update of n_vol sampled
+    volume points with those levels.  Returns a dict with the useful pair
+    evaluations (|r - r_c| < R, counted with a k-d tree), the brute-force pair
+    evaluations (every point against every control, as the oracle forms
+    them) and the seconds of oracle time."""
+    import oracle
     from scipy.spatial import cKDTree
 
-    total = 0
-    tree_s = cKDTree(case.xyz_s)
-    for l, R in enumerate(case.R):
+    nt = n_threads or (os.cpu_count() or 1)
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(c.n_v, size=min(n_vol, c.n_v), replace=False))
+    xv = np.ascontiguousarray(c.xyz_v[idx])
+    dv = np.ascontiguousarray(c.d_v[idx])
+    t0 = time.perf_counter()
+    res = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, nc_cap=k_steps, n_threads=nt)
+    t1 = time.perf_counter()
+    oracle.deform(res, c.xyz_s, c.R, xv, dv, c.k, c.D, n_threads=nt)
+    t2 = time.perf_counter()
+    tree_s = cKDTree(c.xyz_s)
+    useful, brute_greedy = 0, 0
+    for l, R in enumerate(c.R):
         C = res.idx[l]
         n = len(C)
-        cnt = np.array([len(v) for v in tree_s.query_ball_point(case.xyz_s[C], r=R * (1 - 1e-12))])
-        # control j is present in the sweeps of steps j+1 .. n (n - j sweeps)
-        total += int((cnt * (n - np.arange(n))).sum())
-    xv = case.xyz_v if sample_idx is None else case.xyz_v[sample_idx]
-    dv = case.d_v if sample_idx is None else case.d_v[sample_idx]
-    for l, R in enumerate(case.R):
+        cnt = np.array([len(v) for v in tree_s.query_ball_point(c.xyz_s[C], r=R * (1 - 1e-12))])
+        # control j is in the sweeps of steps j + 1 .. n (n - j sweeps, the stopping sweep included)
+        useful += int((cnt * (n - np.arange(n))).sum())
+        brute_greedy += c.n_s * n * (n + 1) // 2
+    Dl = oracle.support_distances(res.smax, c.k, c.D)
+    brute_vol = 0
+    for l, R in enumerate(c.R):
         if not Dl[l] > 0 or len(res.idx[l]) == 0:
             continue
         keep = dv.astype(np.float64) < Dl[l]
-        if not keep.any():
-            continue
-        tree_c = cKDTree(case.xyz_s[res.idx[l]])
-        total += int(sum(len(v) for v in tree_c.query_ball_point(xv[keep].astype(np.float64), r=R * (1 - 1e-12))))
-    return total
+        brute_vol += int(keep.sum()) * len(res.idx[l])
+        if keep.any():
+            tree_c = cKDTree(c.xyz_s[res.idx[l]])
+            useful += int(sum(len(v) for v in tree_c.query_ball_point(xv[keep].astype(np.float64),
+                                                                      r=R * (1 - 1e-12))))
+    return {"pairs_useful": useful, "brute_greedy": brute_greedy, "brute_vol": brute_vol,
+            "greedy_s": t1 - t0, "vol_s": t2 - t1, "seconds": t2 - t0, "k_steps": k_steps,
+            "n_vol": int(len(idx)), "cores": nt}
 
 
-def oracle_step(cases, frac, rng_seed=0, n_threads=None, count=True):
-    """One CPU step with the FP64 oracle: full greedy of every case, volume
-    update of a random `frac` of the volume points (all of them at frac = 1).
-    Returns (useful_pairs, seconds)."""
-    import oracle
+def oracle_extrapolate(c, sample, nc_levels):
+    """Oracle time of the full step, extrapolated from the sample's brute-force
+    pair rates: the greedy of Section 3 forms n_s x n pairs at a step with n
+    controls (its Eq. 9 solves are not counted, so this is a lower bound), the
+    volume update forms (points below D_l) x n_l pairs per level, taken here
+    as every volume point."""
+    rate_g = sample["brute_greedy"] / max(sample["greedy_s"], 1e-9)
+    rate_v = sample["brute_vol"] / max(sample["vol_s"], 1e-9) if sample["brute_vol"] else rate_g
+    pairs_g = sum(c.n_s * n * (n + 1) // 2 for n in nc_levels)
+    pairs_v = sum(c.n_v * n for n in nc_levels)
+    return pairs_g / rate_g + pairs_v / rate_v
 
-    nt = n_threads or (os.cpu_count() or 1)
-    rng = np.random.default_rng(rng_seed)
-    pairs = 0
-    secs = 0.0
-    for c in cases:
-        if frac >= 1.0:
-            idx = np.arange(c.n_v)
-        else:
-            idx = np.sort(rng.choice(c.n_v, size=max(1, int(frac * c.n_v)), replace=False))
-        xv = np.ascontiguousarray(c.xyz_v[idx])
-        dv = np.ascontiguousarray(c.d_v[idx])
-        t0 = time.perf_counter()
-        res = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, n_threads=nt)
-        oracle.deform(res, c.xyz_s, c.R, xv, dv, c.k, c.D, n_threads=nt)
-        secs += time.perf_counter() - t0
-        if count:
-            Dl = oracle.support_distances(res.smax, c.k, c.D)
-            pairs += useful_pairs_oracle_run(c, res, Dl, idx)
-    return pairs, secs
+
+def oracle_steps_for(c, budget_s=CPU_BASELINE_S, cores=None):
+    """Greedy steps per level that keep the oracle sample near budget_s on
+    the host cores (about 2e8 brute-force pairs per second per core)."""
+    cores = cores or (os.cpu_count() or 1)
+    rate = 2.0e8 * cores
+    k = int(np.sqrt(2.0 * budget_s * rate / (len(c.R) * c.n_s)))
+    return int(max(20, min(k, 2000)))
 
 
 def cpu_cores():
@@ -170,13 +220,6 @@ def cpu_cores():
         return len(os.sched_getaffinity(0))
     except Exception:
         return os.cpu_count() or 1
-
-
-# DRAM bytes per launch (read + written) from an ncu capture of the same
-# workload, for the kernels whose code has not changed since
-# (profiles/k_greedy_newton_naca0012_4000s.md: the mean of the four launches
-# of one step)
-DRAM_BYTES_PER_LAUNCH = {"newton": 434624}
 
 
 # ------------------------------------------------------------ clocks
@@ -238,6 +281,67 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------ roofline
+
+def roofline_of(stats, dim, sms, sm_clock_hz, precision_mixed):
+    """Roofline of the dominant kernel by device time (the library's event
+    timing on the mesh's stream).  The evaluation kernels are bound by the
+    FP32 pipe (neither HBM nor tensor cores): peak = SMs x 128 lanes x clock.
+    Their work is the useful pairs they evaluated x the operations of one
+    plain FP32 pair; the double-float operation count is given beside it."""
+    peak = sms * FP32_LANES_PER_SM * sm_clock_hz
+    tot = lambda key: sum(s[key] for s in stats)
+    kinds = {
+        # (device ms, launches, useful pairs evaluated)
+        "persist": (tot("persist_ms"), tot("persist_launches"), tot("sweep_pairs_useful")),
+        "newton": (tot("newton_ms"), tot("newton_launches"), tot("newton_pairs_useful")),
+        "vol": (tot("vol_ms"), tot("vol_launches"), tot("vol_pairs_useful")),
+        "sweep": (tot("sweep_ms"), tot("sweep_launches"), 0),
+    }
+    names = {"persist": f"k_greedy_persist<{dim},2,{1 if precision_mixed else 0}>",
+             "newton": f"k_greedy_newton<{dim},2,{1 if precision_mixed else 0}>",
+             "vol": f"k_vol_sweep<{dim},2,{2 if precision_mixed else 0}>",
+             "sweep": f"k_sweep<{dim},2,{1 if precision_mixed else 0}>"}
+    srcs = {"persist": "persist.cu", "newton": "newton.cu", "vol": "deform.cu", "sweep": "greedy.cu"}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    ms, launches, pairs = kinds[dom]
+
+    def fr(p, ms_, ops):
+        return (p * ops / (ms_ / 1e3)) / peak if ms_ > 0 else 0.0
+
+    achieved = pairs * OPS_PER_PAIR_FP32[dim] / (ms / 1e3) if ms > 0 else 0.0
+    traffic = None
+    cap = DRAM_BYTES_PER_LAUNCH.get(dom)
+    if cap and cap[1] == source_sha16(srcs[dom]):
+        traffic = cap[0]
+    phases = [round(sum(s["persist_phase_ms"][q] for s in stats), 3) for q in range(8)]
+    vol_ms, vol_pairs = kinds["vol"][0], kinds["vol"][2]
+    return {
+        "bound": "alu", "kernel": names[dom],
+        "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+        "frac": achieved / peak if peak else 0.0,
+        "frac_df_ops": fr(pairs, ms, OPS_PER_PAIR_DF[dim]) if precision_mixed else None,
+        "traffic": traffic,
+        "traffic_unit": "bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, ncu)",
+        "avg_launch_ms": ms / max(1, launches), "launches": int(launches),
+        "pairs_per_launch": pairs / max(1, launches),
+        "kernel_ms": {k: round(v[0], 3) for k, v in kinds.items()},
+        "kernel_frac": {k: round(fr(v[2], v[0], OPS_PER_PAIR_FP32[dim]), 5) for k, v in kinds.items()
+                        if v[0] > 0 and v[2]},
+        # block 0 of the persistent launch, summed over levels and steps:
+        # [2p] work of phase p (sweep, argmax + phi column, G phi, G row), [2p+1] wait at its barrier
+        "persist_phase_ms": phases,
+        "vol_sweep": {"ms": round(vol_ms, 3), "pairs_useful": int(vol_pairs),
+                      "frac": round(fr(vol_pairs, vol_ms, OPS_PER_PAIR_FP32[dim]), 5),
+                      "frac_df_ops": round(fr(vol_pairs, vol_ms, OPS_PER_PAIR_DF[dim]), 5) if precision_mixed
+                      else None},
+        "peak_basis": (f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_clock_hz / 1e9:.2f} GHz (derived from "
+                       "unit counts and clocks: MEASURED_PEAKS.json has no FP32 figure); work = useful pairs x "
+                       f"{OPS_PER_PAIR_FP32[dim]} FP32-pipe operations of a plain FP32 pair (frac_df_ops: x "
+                       f"{OPS_PER_PAIR_DF[dim]}, the double-float pair the mixed mode evaluates)"),
+    }
+
+
 # ------------------------------------------------------------ GPU arm
 
 def run_ours(args):
@@ -253,54 +357,44 @@ def run_ours(args):
     from paper_2107_13887_gb300 import rbfd
 
     rbfd.load()
+    props = torch.cuda.get_device_properties(dev)
+    sms = int(props.multi_processor_count)
     precision = rbfd.MIXED if args.precision == "mixed" else rbfd.FP64
-    cases = make_cases()
-    stream = torch.cuda.current_stream(dev)
+    c = make_case(args.workload)
+    stream = torch.cuda.Stream(dev, priority=-1)
 
-    # device-resident inputs
-    dcases = []
-    for c in cases:
-        dcases.append(dict(
-            xyz_s=torch.from_numpy(c.xyz_s).to(dev), dS=torch.from_numpy(c.dS).to(dev),
-            xyz_v=torch.from_numpy(c.xyz_v).to(dev), d_v=torch.from_numpy(c.d_v).to(dev),
-            out=torch.empty((c.n_v, c.dim), dtype=torch.float32, device=dev)))
-    # pinned host inputs for the end-to-end leg
-    hcases = []
-    for c in cases:
-        def pin(a):
-            t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-            return t.numpy()
-        hcases.append(dict(xyz_s=pin(c.xyz_s), dS=pin(c.dS), xyz_v=pin(c.xyz_v), d_v=pin(c.d_v),
-                           out=pin(np.zeros((c.n_v, c.dim), np.float32))))
+    d = dict(xyz_s=torch.from_numpy(c.xyz_s).to(dev), dS=torch.from_numpy(c.dS).to(dev),
+             xyz_v=torch.from_numpy(c.xyz_v).to(dev), d_v=torch.from_numpy(c.d_v).to(dev),
+             out=torch.empty((c.n_v, c.dim), dtype=torch.float32, device=dev))
+
+    def pin(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+    h = dict(xyz_s=pin(c.xyz_s), dS=pin(c.dS), xyz_v=pin(c.xyz_v), d_v=pin(c.d_v),
+             out=pin(np.zeros((c.n_v, c.dim), np.float32)))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
-    # each case gets its own stream so that the batch calls overlap them
-    # (high priority: the library's staging streams, at the lowest, fill in behind the greedy)
-    streams = [torch.cuda.Stream(dev, priority=-1) for _ in cases]
-
     def one_step(src, record):
-        """Both cases as one library call (rbfd_run_jobs): per case, create
-        (the spatial set-up of the surface), greedy and volume update, the
-        cases side by side on their own host threads and streams.  Returns the
-        meshes; their counters are read and they are destroyed after the timed
-        region."""
-        jobs = [dict(xyz_s=d["xyz_s"], dS=d["dS"], R=c.R, eps=c.eps, precision=precision, stream=s_.cuda_stream,
-                     profile=record, engine=args.engine, grid_ctas=args.ctas, xyz_v=d["xyz_v"], d_v=d["d_v"],
-                     D=c.D, k=c.k, out=d["out"]) for c, d, s_ in zip(cases, src, streams)]
-        ms, _ = rbfd.run_jobs(jobs)
-        return ms
+        """rbfd_run_jobs with one job: create (the surface's spatial set-up),
+        greedy, volume update.  Returns the mesh; its counters are read and it
+        is destroyed after the timed region."""
+        job = dict(xyz_s=src["xyz_s"], dS=src["dS"], R=c.R, eps=c.eps, precision=precision,
+                   stream=stream.cuda_stream, profile=record, engine=args.engine, grid_ctas=args.ctas,
+                   xyz_v=src["xyz_v"], d_v=src["d_v"], D=c.D, k=c.k, out=src["out"])
+        ms, _ = rbfd.run_jobs([job])
+        return ms[0]
 
-    def finish(ms):
-        stats = [m.stats() for m in ms]
-        for m in ms:
-            m.close()
-        return sum(st["pairs_useful"] for st in stats), stats
+    def finish(m):
+        st = m.stats()
+        lv = [len(L.idx) for L in m.levels()]
+        m.close()
+        return st, lv
 
     def timed(src, K, W, record):
         for _ in range(W):
             finish(one_step(src, False))
         torch.cuda.synchronize()
-        tot_ms, tot_pairs, all_stats = 0.0, 0, []
+        tot_ms, stats, nc = 0.0, [], None
         for _ in range(K):
             flush.zero_()
             torch.cuda.synchronize()
@@ -309,36 +403,25 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for s_ in streams:  # the case streams start after e0
-                s_.wait_event(e0)
-            meshes = one_step(src, record)
-            for s_ in streams:  # e1 follows the work of every case stream
-                stream.wait_stream(s_)
+            m = one_step(src, record)
             e1.record(stream)
             torch.cuda.synchronize()
             tot_ms += e0.elapsed_time(e1)
-            p, st = finish(meshes)
-            tot_pairs += p
-            all_stats.extend(st)
-        return tot_ms, tot_pairs, all_stats
+            st, nc = finish(m)
+            stats.append(st)
+        return tot_ms, stats, nc
 
     sampler = ClockSampler(local)
     sampler.start()
-    ms, pairs, stats = timed(dcases, args.steps, args.warmup, True)
-    # nvidia-smi samples every 200 ms, longer than a short timed region: the
-    # same step keeps running (untimed) until three samples have been taken
-    # under this load, at most 3 s
-    t_stop = time.monotonic() + 3.0
-    while sampler.count() < 3 and time.monotonic() < t_stop:
-        finish(one_step(dcases, False))
-    torch.cuda.synchronize()
+    ms, stats, nc_levels = timed(d, args.steps, args.warmup, True)
     clocks = sampler.stop()
     if clocks is not None:
-        clocks["sampled_over"] = "warm-up, timed steps and untimed repeats of the same step"
+        clocks["sampled_over"] = "warm-up and timed steps"
+    pairs = sum(s["pairs_useful"] for s in stats)
     e2e = None
     if not args.no_e2e:
-        ms_e, pairs_e, _ = timed(hcases, args.steps, args.warmup, False)
-    # aggregate over ranks: units summed, time = max
+        ms_e, stats_e, _ = timed(h, args.steps, 0, False)
+        pairs_e = sum(s["pairs_useful"] for s in stats_e)
     if ws > 1:
         ms_all, pairs_all = aggregate_over_ranks(ms, pairs, dev)
         if not args.no_e2e:
@@ -346,8 +429,8 @@ def run_ours(args):
     else:
         ms_all, pairs_all = ms, float(pairs)
     if not args.no_e2e:
-        h2d = sum(c.xyz_s.nbytes + c.dS.nbytes + c.xyz_v.nbytes + c.d_v.nbytes for c in cases)
-        d2h = sum(c.n_v * c.dim * 4 for c in cases)
+        h2d = c.xyz_s.nbytes + c.dS.nbytes + c.xyz_v.nbytes + c.d_v.nbytes
+        d2h = c.n_v * c.dim * 4
         e2e = {"value": pairs_e / (ms_e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e / args.steps}
     if rank != 0:
@@ -355,92 +438,45 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return
 
-    # roofline of the dominant kernel class (device time inside the timed region)
-    sweep_pairs = sum(s["sweep_pairs_useful"] for s in stats)
-    dim = cases[0].dim
-    peak_ops = SM_COUNT * FP32_LANES_PER_SM * 2.07e9  # FP32 issue slots per second at max SM clock
-    # (device ms, launches, FP32-pipe operations of the work the class did)
-    kinds = {
-        "sweep": (sum(s["sweep_ms"] for s in stats), sum(s["sweep_launches"] for s in stats),
-                  sweep_pairs * OPS_PER_PAIR_DF[dim]),
-        "grow": (sum(s["grow_ms"] for s in stats), sum(s["grow_launches"] for s in stats), 0),
-        "vol": (sum(s["vol_ms"] for s in stats), sum(s["vol_launches"] for s in stats),
-                sum(s["vol_pairs_useful"] for s in stats) * OPS_PER_PAIR_DF[dim]),
-        # the persistent list sweep runs the sweeps AND the FP64 growth; only
-        # its sweep pairs are counted as work here, so its fraction is a lower bound
-        "persist": (sum(s["persist_ms"] for s in stats), sum(s["persist_launches"] for s in stats),
-                    0),
-        # the Newton-basis launch: one double-float multiply-add (12 FP32
-        # operations) per basis value read; its per-point tail and growth are
-        # not counted, so the fraction is a lower bound
-        "newton": (sum(s["newton_ms"] for s in stats), sum(s["newton_launches"] for s in stats),
-                   sum(s["newton_terms"] for s in stats) * OPS_PER_NEWTON_TERM),
-    }
-    names = {"sweep": f"k_sweep<{dim},2,1>", "vol": f"k_vol_sweep<{dim},2,1>",
-             "persist": f"k_greedy_persist<{dim},2,1>", "newton": f"k_greedy_newton<{dim},2,1>"}
-    ev_kinds = {k: v for k, v in kinds.items() if k != "grow"}
-    dom = max(ev_kinds, key=lambda k: ev_kinds[k][0])
-    d_ms, d_launch, d_ops = ev_kinds[dom]
-    achieved = d_ops / (d_ms / 1e3) if d_ms > 0 else 0.0
-    roofline = {
-        "bound": "alu", "kernel": names[dom],
-        "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "TFLOP/s",
-        "frac": achieved / peak_ops, "traffic": DRAM_BYTES_PER_LAUNCH.get(dom),
-        "traffic_unit": "bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, ncu)",
-        "avg_launch_ms": d_ms / max(1, d_launch), "launches": int(d_launch),
-        "kernel_ms": {k: round(v[0], 3) for k, v in kinds.items()},
-        "kernel_frac": {k: round(v[2] / (v[0] / 1e3) / peak_ops, 5) for k, v in kinds.items() if v[0] > 0 and v[2]},
-        "persist_phase_ms": [round(sum(s["persist_phase_ms"][q] for s in stats), 3) for q in range(8)],
-        # the Newton launches' device time per greedy step (the two cases run
-        # side by side, so this is the latency of one case's step)
-        "newton_us_per_step": round(1e3 * sum(s["newton_ms"] for s in stats)
-                                    / max(1, sum(s["newton_steps"] for s in stats)), 3),
-        "note": ("FP32-pipe operations: 210 (2D) / 284 (3D) per double-float pair evaluation, 12 per "
-                 "double-float basis multiply-add; peak = 152 SMs x 128 FP32 lanes x 2.07 GHz. The greedy "
-                 "launches are latency-bound chains of dependent steps (one grid barrier per step)"),
-    }
-    greedy_ms = [s["greedy_ms"] for s in stats]
+    clock_hz = 1e6 * (clocks["sm_max_mhz"] if clocks else 2070.0)
+    mixed = precision == rbfd.MIXED
+    med = lambda key: statistics.median([s[key] for s in stats])
     line = {
         "metric": METRIC, "value": pairs_all / (ms_all / 1e3), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32x2+f64" if precision == rbfd.MIXED else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cases": list(CASES), "n_surface": 4000, "n_volume": 1000000,
-                   "levels": 2, "R": [1.0, 0.2], "eps": 1e-5, "k": 5.0, "D": 2.0, "precision": args.precision,
-                   "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas{ws}",
-                   "engine": {0: "newton+persistent", 1: "per-step launches", 2: "persistent"}[args.engine],
-                   "persist_ctas": int(stats[-1]["persist_ctas"]) if stats else 0},
-        "time_to_eps_ms": {"pitch_heave": statistics.median(greedy_ms[0::2]),
-                           "horns": statistics.median(greedy_ms[1::2])},
-        # device time of each case's volume update (after its greedy), median over the timed steps
-        "deform_ms": {"pitch_heave": statistics.median([s["deform_ms"] for s in stats[0::2]]),
-                      "horns": statistics.median([s["deform_ms"] for s in stats[1::2]])},
+        "dtype": "f32x2+f64" if mixed else "f64", "data": "synthetic",
+        "config": dict(workload_config(c), precision=args.precision,
+                       l2="flushed (256 MB write) between timed steps; the 6M-point volume exceeds L2",
+                       parallelism=f"replicas{ws}",
+                       engine={0: "newton+persistent", 1: "per-step launches", 2: "persistent"}[args.engine],
+                       persist_ctas=int(stats[-1]["persist_ctas"]) if stats else 0),
+        "time_to_eps_ms": med("greedy_ms"),
+        "deform_ms": med("deform_ms"),
+        "controls_per_level": nc_levels,
         "pairs_useful_per_step": pairs_all / args.steps / ws,
-        # the second count: pairs the kernels evaluated (the useful ones plus
-        # those the cell and control lists let through beyond R; the Newton
-        # start counts its basis multiply-adds), per step and per second (rank 0)
+        # Eq. 12's nonzeros for every greedy step (what a list sweep of each
+        # step evaluates; the Newton-basis steps evaluate one phi per point
+        # instead) plus the volume update's pairs: the method's own count
+        "eq12_pairs_per_step": sum(s["eq12_pairs"] + s["vol_pairs_useful"] for s in stats) / args.steps,
         "pairs_visited_per_step": sum(s["pairs_visited"] for s in stats) / args.steps,
-        "visited_per_s": sum(s["pairs_visited"] for s in stats) / (ms / 1e3),
-        "roofline": roofline,
+        "roofline": roofline_of(stats, c.dim, sms, clock_hz, mixed),
         "e2e": e2e,
         "gpu_launches": int(sum(s["launches"] for s in stats)),
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
-        # the whole step (both cases, every volume point), repeated until at
-        # least CPU_BASELINE_S seconds of oracle time have run
-        # (the full step is the same every time: its pairs are counted once)
-        p_cpu, s_cpu, reps, p_one = 0, 0.0, 0, 0
-        while s_cpu < CPU_BASELINE_S and reps < 200:
-            p, s_ = oracle_step(cases, 1.0, count=(reps == 0))
-            p_one = p_one or p
-            p_cpu += p_one
-            s_cpu += s_
-            reps += 1
-        line["cpu_baseline"] = {"value": p_cpu / s_cpu, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                                "sample": f"the full step (greedy of both cases + volume update of all their "
-                                          f"volume points) repeated {reps} times (FP64 oracle, OpenMP)",
-                                "seconds": s_cpu}
+        k = args.oracle_steps or oracle_steps_for(c)
+        smp = oracle_sample(c, k, n_vol=20000)
+        line["cpu_baseline"] = {
+            "value": smp["pairs_useful"] / smp["seconds"], "unit": UNIT, "cores": smp["cores"], "kind": "oracle",
+            "sample": (f"first {k} greedy steps of each of the {len(c.R)} levels (nc_cap = {k}) + the volume "
+                       f"update of {smp['n_vol']} sampled volume points (FP64 oracle, OpenMP)"),
+            "seconds": smp["seconds"],
+            "extrapolated_full_step_s": oracle_extrapolate(c, smp, nc_levels),
+            "extrapolation": "lower bound: brute-force pair rates of the sample applied to the full step's "
+                             "control counts, Eq. 9 solves not counted",
+        }
     if not args.no_serve:
         line["serving"] = run_serving(n_requests=args.serve_requests)
     print(json.dumps(line), flush=True)
@@ -467,7 +503,7 @@ def serving_meshes():
     ]
 
 
-def run_serving(n_requests=200, rate=50.0, slots=4, seed=0):
+def run_serving(n_requests=1000, rate=50.0, slots=4, seed=0):
     """Requests with Poisson arrivals at `rate`/s, each one time step of an
     ice-growth sequence (displacement scaled up linearly with the step) on one
     of the meshes; submitted in real time to the request loop.  Returns the
@@ -516,27 +552,25 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if not reference_rank_works(rank):
         return
-    cases = make_cases()
-    frac = 1.0  # the whole workload each step
+    c = make_case(args.workload)
+    k = args.oracle_steps or oracle_steps_for(c, budget_s=CPU_BASELINE_S / 2)
     cores = cpu_cores()
     for _ in range(args.warmup):
-        oracle_step(cases, frac, rng_seed=1, count=False)
-    tot_p, tot_s, p_one = 0, 0.0, 0
-    for k in range(args.steps):
-        p, s = oracle_step(cases, frac, rng_seed=100 + k, count=(k == 0))  # the same full step each time
-        p_one = p_one or p
-        tot_p += p_one
-        tot_s += s
+        oracle_sample(c, max(10, k // 4), n_vol=2000, seed=1)
+    tot_p, tot_s, smp = 0, 0.0, None
+    for step in range(args.steps):
+        smp = oracle_sample(c, k, n_vol=20000, seed=100 + step)
+        tot_p += smp["pairs_useful"]
+        tot_s += smp["seconds"]
     v = tot_p / tot_s
+    sample = (f"each step: the first {k} greedy steps of each of the {len(c.R)} levels (nc_cap = {k}) + the volume "
+              f"update of {smp['n_vol']} sampled volume points (FP64 oracle, OpenMP on {smp['cores']} threads)")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_s * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cases": list(CASES), "n_surface": 4000, "n_volume": 1000000,
-                   "levels": 2, "R": [1.0, 0.2], "eps": 1e-5, "k": 5.0, "D": 2.0},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "each step: the full workload (greedy of both cases + volume update of "
-                                   "all their volume points)"},
+        "config": dict(workload_config(c), precision="fp64"),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": smp["cores"], "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

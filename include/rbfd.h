@@ -35,7 +35,8 @@ typedef enum rbfd_status {
     RBFD_ETIMEOUT = 5,   /* a bounded device-side or host-side wait hit its limit */
     RBFD_EBUSY = 6,      /* serving admission refused for now (device memory); retry later */
     RBFD_ECUDA = 7,      /* a CUDA runtime call failed (message in rbfd_last_error) */
-    RBFD_ESTATE = 8      /* call out of order (e.g. deform before greedy) */
+    RBFD_ESTATE = 8,     /* call out of order (e.g. deform before greedy) */
+    RBFD_ECOMM = 9       /* the caller's reduction callback failed (rbfd_greedy_split) */
 } rbfd_status;
 
 typedef enum rbfd_precision {
@@ -132,7 +133,7 @@ typedef struct rbfd_stats {
     double greedy_ms;        /* device time of the last rbfd_greedy (CUDA events) */
     double deform_ms;        /* device time of the last rbfd_deform */
     int64_t greedy_steps;    /* control additions over all levels */
-    int64_t pairs_useful;    /* greedy + deform point/control pairs with |r - r_c| < R */
+    int64_t pairs_useful;    /* greedy + deform point/control pairs evaluated with |r - r_c| < R */
     int64_t pairs_visited;   /* pairs the kernels evaluated (a superset of the useful ones) */
     int64_t deform_points;   /* volume points updated at least at one level (sum over levels) */
     int64_t refine_sweeps;   /* iterative-refinement sweeps run at level close */
@@ -163,6 +164,17 @@ typedef struct rbfd_stats {
        [2] level close (refinement, confirm sweep), [3] level save (results to
        the host, control grid) */
     double greedy_host_ms[4];
+    /* pair evaluations the kernels performed with |r - r_c| < R, by kind: the
+       Newton-basis update evaluates phi of each step's control at every
+       surface point (newton_pairs_useful within R, newton_pairs_formed in all),
+       where a list sweep of the same step evaluates the nonzeros of Eq. 12:
+       eq12_pairs counts those for every greedy step and the confirm sweeps,
+       whichever engine ran (the method's own pair count, as Section 3 states
+       it); pairs_useful = sweep_pairs_useful + vol_pairs_useful +
+       newton_pairs_useful is what was evaluated */
+    int64_t newton_pairs_useful;
+    int64_t newton_pairs_formed;
+    int64_t eq12_pairs;
 } rbfd_stats;
 
 int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st);
@@ -326,6 +338,41 @@ int rbfd_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, int key_bits, voi
  */
 int rbfd_deform_noalloc(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v, double D, double k,
                         float *out);
+
+/*
+ * rbfd_greedy_split -- rbfd_greedy with the surface points split over `world`
+ * ranks (one GPU each), for the argmax of Section 3: at every greedy step
+ * E = dS_l - Phi_sc alpha (Eq. 12) is swept over this rank's share of the
+ * surface only -- a contiguous range of the Morton-ordered point blocks,
+ * [rank n_pb / world, (rank + 1) n_pb / world) -- and the ranks combine their
+ * best candidates with one all-reduce-maxloc of 16 bytes per step, which the
+ * caller performs in `maxloc` (over NCCL, gloo, MPI, ...).
+ *
+ * Every rank creates the same mesh (rbfd_create with the full surface: the
+ * coordinates and displacements are replicated, a few MB) and calls this
+ * function with its own rank; the control system (the inverse factor G, the
+ * weights alpha, the per-block control lists) is then updated identically and
+ * deterministically on every rank, and the once-per-level confirm sweep runs
+ * over the whole surface on every rank, so every rank ends with the same
+ * levels: the controls and weights of rbfd_greedy with options.engine = 1,
+ * bit for bit.  rbfd_deform can then be split by volume points (Morton ranges)
+ * with no collective at all.
+ *
+ * maxloc(user, key, idx): on entry *key is the rank's largest |E_i|^2 over its
+ * unselected points (-1 if it has none) and *idx that point's original
+ * surface index (-1 if none); it must store the largest key over all ranks
+ * and its index, the lowest index among equal keys, identically on every
+ * rank, and return 0 (nonzero: the call fails with RBFD_ECOMM).  It is called
+ * once per greedy step, from the calling thread.
+ *
+ * The steps run as separate launches with one host round trip each (the
+ * exchange), so this form pays off when a rank's surface sweep is long
+ * against that round trip; world = 1 is rbfd_greedy with engine 1.
+ * Errors: as rbfd_greedy, plus RBFD_EINVAL (rank outside [0, world), world < 1,
+ * NULL callback) and RBFD_ECOMM.
+ */
+typedef int (*rbfd_maxloc_fn)(void *user, double *key, int64_t *idx);
+int rbfd_greedy_split(rbfd_mesh *m, int rank, int world, rbfd_maxloc_fn maxloc, void *user);
 
 /*
  * rbfd_greedy_batch -- rbfd_greedy on n meshes at once.  Each greedy is a

@@ -470,6 +470,36 @@ int rbfd_greedy(rbfd_mesh *m) {
     });
 }
 
+int rbfd_greedy_split(rbfd_mesh *m, int rank, int world, rbfd_maxloc_fn maxloc, void *user) {
+    return guarded([&] {
+        if (!m) rbfd::fail(RBFD_EINVAL, "rbfd_greedy_split: NULL mesh");
+        if (world < 1 || rank < 0 || rank >= world)
+            rbfd::fail(RBFD_EINVAL, "rbfd_greedy_split: rank " + std::to_string(rank) + " outside [0, world = " +
+                                        std::to_string(world) + ")");
+        if (!maxloc) rbfd::fail(RBFD_EINVAL, "rbfd_greedy_split: NULL maxloc callback");
+        RBFD_CUDA(cudaSetDevice(m->device));
+        // the split runs the step engine (one launch per sweep), whatever the options say
+        const int engine = m->opt.engine;
+        m->opt.engine = 1;
+        m->split_world = world;
+        m->split_rank = rank;
+        m->split_maxloc = maxloc;
+        m->split_user = user;
+        struct Restore {
+            rbfd_mesh *m;
+            int engine;
+            ~Restore() {
+                m->opt.engine = engine;
+                m->split_world = 1;
+                m->split_rank = 0;
+                m->split_maxloc = nullptr;
+                m->split_user = nullptr;
+            }
+        } restore{m, engine};
+        rbfd::greedy_run(m);
+    });
+}
+
 int rbfd_num_levels(rbfd_mesh *m, int *n_levels) {
     return guarded([&] {
         if (!m || !n_levels) rbfd::fail(RBFD_EINVAL, "rbfd_num_levels: NULL argument");
@@ -508,7 +538,7 @@ int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st) {
     return guarded([&] {
         if (!m || !st) rbfd::fail(RBFD_EINVAL, "rbfd_get_stats: NULL argument");
         RBFD_CUDA(cudaSetDevice(m->device));
-        unsigned long long pr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        unsigned long long pr[16] = {};
         RBFD_CUDA(cudaStreamSynchronize(m->stream));
         RBFD_CUDA(cudaMemcpy(pr, m->d_pairs, sizeof(pr), cudaMemcpyDeviceToHost));
         m->prof.flush();
@@ -518,8 +548,11 @@ int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st) {
         st->sweep_pairs_visited = (int64_t)pr[1];
         st->vol_pairs_useful = (int64_t)pr[2];
         st->vol_pairs_visited = (int64_t)pr[3];
-        st->pairs_useful = (int64_t)(pr[0] + pr[2]);
-        st->pairs_visited = (int64_t)(pr[1] + pr[3]);
+        st->newton_pairs_useful = (int64_t)pr[8];
+        st->newton_pairs_formed = (int64_t)pr[9];
+        st->eq12_pairs = (int64_t)(pr[0] + pr[10]);
+        st->pairs_useful = (int64_t)(pr[0] + pr[2] + pr[8]);
+        st->pairs_visited = (int64_t)(pr[1] + pr[3] + pr[9]);
         st->sweep_ms = m->prof.ms[rbfd::kProfSweep];
         st->grow_ms = m->prof.ms[rbfd::kProfGrow];
         st->vol_ms = m->prof.ms[rbfd::kProfVol];

@@ -234,6 +234,10 @@ struct SweepArgs {
     // chunks of equal length, the launch's other chunk blocks are idle
     const GreedyState *n_from;
     int chunk_cap;
+    // point blocks pb_lo .. pb_lo + pb_n - 1 only (grid.x = pb_n): a rank's
+    // Morton range in the surface split; local_only: the tail records the
+    // range's argmax and leaves the stop decision to the caller
+    int pb_lo, pb_n, local_only;
 };
 
 template <int DIM, int BASIS, int MODE>
@@ -257,7 +261,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(SweepArgs a) {
         chunk_len = (n_c + nch - 1) / nch;
     }
 
-    const int pb = blockIdx.x, ch = blockIdx.y, tid = threadIdx.x;
+    const int pb = a.pb_lo + (int)blockIdx.x, ch = blockIdx.y, tid = threadIdx.x;
     const int64_t p = (int64_t)pb * kPB + tid;
     const bool valid = p < a.n_s;
     const uint32_t cnt = a.nb_cnt[pb];
@@ -381,14 +385,14 @@ __global__ void __launch_bounds__(kThreads) k_sweep(SweepArgs a) {
         a.pb_idx[pb] = orig;
         a.pb_done[pb] = 0;
         __threadfence();
-        s_last = atomicAdd(&a.st->pb_done, 1u) == (unsigned)(a.n_pb - 1);
+        s_last = atomicAdd(&a.st->pb_done, 1u) == (unsigned)(a.pb_n - 1);
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     key = -1.0;
     orig = -1;
-    for (int b = tid; b < a.n_pb; b += kThreads) {
+    for (int b = a.pb_lo + tid; b < a.pb_lo + a.pb_n; b += kThreads) {
         double kb = __ldcg(&a.pb_key[b]);
         int ib = __ldcg(&a.pb_idx[b]);
         if (better(kb, ib, key, orig)) {
@@ -404,7 +408,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(SweepArgs a) {
         st->best_key = key;
         double e = orig >= 0 ? __ddiv_rn(__dsqrt_rn(key), a.S0) : 0.0;
         st->emax = e;
-        if (a.is_step) {
+        if (a.is_step && !a.local_only) {
             if (orig < 0 || e < a.tau) {
                 st->stop = 1;
             } else if (a.n >= a.cap) {
@@ -412,6 +416,21 @@ __global__ void __launch_bounds__(kThreads) k_sweep(SweepArgs a) {
                 st->status = RBFD_ENOTCONV;
             }
         }
+    }
+}
+
+// The step decision of the surface split, from the argmax over every rank's
+// range (the caller's all-reduce-maxloc): the same stop test as k_sweep's tail.
+__global__ void k_split_decide(GreedyState *st, double key, int orig, double S0, double tau, int n, int cap) {
+    st->best_orig = orig;
+    st->best_key = key;
+    const double e = orig >= 0 ? __ddiv_rn(__dsqrt_rn(key), S0) : 0.0;
+    st->emax = e;
+    if (orig < 0 || e < tau) {
+        st->stop = 1;
+    } else if (n >= cap) {
+        st->stop = 1;
+        st->status = RBFD_ENOTCONV;
     }
 }
 
@@ -898,6 +917,9 @@ SweepArgs base_sweep_args(rbfd_mesh *m, double R, double tau) {
     a.st = m->d_st;
     a.pairs = m->d_pairs;
     a.dim = m->dim;
+    a.pb_lo = 0;
+    a.pb_n = m->n_pb;
+    a.local_only = 0;
     return a;
 }
 
@@ -1031,7 +1053,7 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     // zero (one memset), then the rest; the two factors G and G^T apart
     Carver zero, rest;
     zero.add(m->d_misc, 16);
-    zero.add(m->d_pairs, 8);
+    zero.add(m->d_pairs, 16);
     zero.add(m->d_st, 1);
     zero.add(m->d_bar, 1);
     zero.add(m->d_phase_ns, 8);
@@ -1364,7 +1386,8 @@ void greedy_run(rbfd_mesh *m, bool wait) {
             bool stopped = false;
             // a level starts in the Newton basis (engine 0) while that pays; the
             // list sweep below takes over where it hands the level on
-            if (m->opt.engine == 0 && resumes == 0 && newton_enabled()) {
+            const bool split = m->split_world > 1;
+            if (m->opt.engine == 0 && resumes == 0 && newton_enabled() && !split) {
                 newton_reserve(m);
                 if (m->newton_cols >= 2) {
                     // one block per 32 surface points, as far as they fit (newton_shape)
@@ -1397,7 +1420,7 @@ void greedy_run(rbfd_mesh *m, bool wait) {
                     }
                 }
             }
-            if (!stopped && (m->opt.engine == 0 || m->opt.engine == 2)) {
+            if (!stopped && !split && (m->opt.engine == 0 || m->opt.engine == 2)) {
                 const int maxc = std::min(persist_max_ctas(m), kMaxPersistCTAs);
                 if (maxc < 1) fail(RBFD_ECUDA, "persistent greedy kernel cannot be resident on this device");
                 // small meshes: few blocks keep the barriers cheap; large ones fill the GPU
@@ -1422,8 +1445,14 @@ void greedy_run(rbfd_mesh *m, bool wait) {
                 n = m->h_st->n;
                 stopped = true;
             }
-            // ... or separate launches per step, in batches (engine 1)
-            const int kBatch = 16;
+            // ... or separate launches per step, in batches (engine 1).  In
+            // the surface split every step sweeps this rank's range of point
+            // blocks, waits for the range's argmax, combines it with the other
+            // ranks' through the caller's all-reduce-maxloc and takes the
+            // step's decision from the combined argmax: one step per batch
+            const int kBatch = split ? 1 : 16;
+            const int pb_lo = split ? (int)((int64_t)m->n_pb * m->split_rank / m->split_world) : 0;
+            const int pb_hi = split ? (int)((int64_t)m->n_pb * (m->split_rank + 1) / m->split_world) : m->n_pb;
             while (!stopped) {
                 for (int s = 0; s < kBatch; ++s) {
                     SweepArgs a = base_sweep_args(m, L.R, L.tau);
@@ -1433,9 +1462,31 @@ void greedy_run(rbfd_mesh *m, bool wait) {
                     a.is_step = 1;
                     a.E_out = nullptr;
                     cudaEvent_t e0 = m->prof.begin(st);
-                    launch_sweep(m->dim, m->opt.basis, mode, dim3(m->n_pb, nch), a, st);
+                    if (split) {
+                        a.pb_lo = pb_lo;
+                        a.pb_n = pb_hi - pb_lo;
+                        a.local_only = 1;
+                        double key = -1.0;
+                        int64_t orig = -1;
+                        if (a.pb_n > 0) {  // (a rank may own no block of a tiny surface)
+                            launch_sweep(m->dim, m->opt.basis, mode, dim3(a.pb_n, nch), a, st);
+                            m->stats.launches += 1;
+                            read_state(m);
+                            key = m->h_st->best_key;
+                            orig = m->h_st->best_orig;
+                        }
+                        if (m->split_maxloc(m->split_user, &key, &orig) != 0)
+                            fail(RBFD_ECOMM, "rbfd_greedy_split: the all-reduce-maxloc callback failed");
+                        if (orig < -1 || orig >= m->n_s)
+                            fail(RBFD_ECOMM, "rbfd_greedy_split: the all-reduce-maxloc returned index " +
+                                                 std::to_string(orig));
+                        k_split_decide<<<1, 1, 0, st>>>(m->d_st, key, (int)orig, m->S0, L.tau, n, m->cap);
+                        m->stats.launches += 1;
+                    } else {
+                        launch_sweep(m->dim, m->opt.basis, mode, dim3(m->n_pb, nch), a, st);
+                        m->stats.launches += 1;
+                    }
                     m->prof.end(kProfSweep, e0, st, 1);
-                    m->stats.launches += 1;
                     if (n >= m->cap) break;  // the sweep above stops the level
                     cudaEvent_t e1 = m->prof.begin(st);
                     g.n = n;

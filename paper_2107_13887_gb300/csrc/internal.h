@@ -184,8 +184,10 @@ struct rbfd_mesh {
     unsigned int *d_pb_done = nullptr;
     double *d_pb_key = nullptr;
     int *d_pb_idx = nullptr;
-    unsigned long long *d_pairs = nullptr;  // [8]: surface sweep useful, visited; volume useful, visited;
-                                            //     wall distance search, exact pass; Newton basis terms
+    unsigned long long *d_pairs = nullptr;  // [16]: surface sweep useful, visited; volume useful, visited;
+                                            //     wall distance search, exact pass; Newton basis terms;
+                                            //     deform points; Newton phi values within R, all formed;
+                                            //     Eq. 12 nonzeros of the Newton steps
     rbfd::GreedyState *d_st = nullptr;
     rbfd::GreedyState *h_st = nullptr;  // pinned
     rbfd::GridBarrier *h_bar = nullptr; // pinned
@@ -208,6 +210,13 @@ struct rbfd_mesh {
     double4 *d_nrec = nullptr;      // [blocks][3] per-block candidate records
     double *d_nycol = nullptr;      // [blocks][newton_cols + 1] their columns of V
     unsigned long long *d_phase_ns = nullptr;  // [8] persistent phase timing (profile mode)
+
+    // surface split of the greedy over ranks (rbfd_greedy_split): this rank's
+    // share of the Morton point blocks and the caller's all-reduce-maxloc of
+    // each step's candidate; split_world = 1 outside that call
+    int split_world = 1, split_rank = 0;
+    rbfd_maxloc_fn split_maxloc = nullptr;
+    void *split_user = nullptr;
 
     std::vector<rbfd::Level> levels;
     bool greedy_done = false;

@@ -816,7 +816,13 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
         const int flags = s_flags;
         const bool writer = blockIdx.x == 0 && tid == 0;
         if (flags) {
-            if (tid == 0) atomicAdd(&a.pairs[0], pairs_useful);
+            if (tid == 0) {
+                // pairs evaluated here (phi of each step's control at this
+                // block's points within R), and the Eq. 12 nonzeros a list
+                // sweep of every step would have evaluated instead
+                atomicAdd(&a.pairs[8], nz_cum);
+                atomicAdd(&a.pairs[10], pairs_useful);
+            }
             if (blockIdx.x == 0) {
                 if (MODE)  // the controls' records in FP64 for what follows the launch
                     for (int k = 1 + tid; k < nn; k += kNT) {
@@ -838,8 +844,9 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
                     // per step, the basis update touches n_s x (controls so far) values of V
                     const unsigned long long terms =
                         (unsigned long long)a.n_s * (unsigned long long)(nn) * (unsigned long long)(nn + 1) / 2;
-                    a.pairs[1] += terms;
                     a.pairs[6] += terms;
+                    // phi values formed by the basis update: every point, every step
+                    a.pairs[9] += (unsigned long long)a.n_s * (unsigned long long)nn;
                     a.st->best_orig = I;
                     a.st->best_key = I >= 0 ? key_value<MODE>(K) : -1.0;
                     a.st->emax = e;

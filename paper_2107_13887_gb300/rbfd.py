@@ -17,10 +17,10 @@ import numpy as np
 
 from . import build as _build
 
-OK, EINVAL, ENOMEM, ESINGULAR, ENOTCONV, ETIMEOUT, EBUSY, ECUDA, ESTATE = range(9)
+OK, EINVAL, ENOMEM, ESINGULAR, ENOTCONV, ETIMEOUT, EBUSY, ECUDA, ESTATE, ECOMM = range(10)
 FP64, MIXED = 0, 1
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ESINGULAR", 4: "ENOTCONV", 5: "ETIMEOUT", 6: "EBUSY",
-                7: "ECUDA", 8: "ESTATE"}
+                7: "ECUDA", 8: "ESTATE", 9: "ECOMM"}
 
 
 class RbfdError(RuntimeError):
@@ -79,6 +79,9 @@ class rbfd_stats(ctypes.Structure):
         ("newton_launches", ctypes.c_int64),
         ("newton_terms", ctypes.c_int64),
         ("greedy_host_ms", ctypes.c_double * 4),
+        ("newton_pairs_useful", ctypes.c_int64),
+        ("newton_pairs_formed", ctypes.c_int64),
+        ("eq12_pairs", ctypes.c_int64),
     ]
 
 
@@ -127,6 +130,10 @@ class rbfd_job(ctypes.Structure):
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
+# int maxloc(void *user, double *key, int64_t *idx) (rbfd_greedy_split)
+MAXLOC_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_int64))
+
 # (name, restype, argtypes) of every function include/rbfd.h declares
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -136,6 +143,7 @@ SIGNATURES = [
     ("rbfd_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i64, _vp, _vp, ctypes.c_int, _vp, _d,
                                    ctypes.POINTER(rbfd_options)]),
     ("rbfd_greedy", ctypes.c_int, [_vp]),
+    ("rbfd_greedy_split", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, MAXLOC_FN, _vp]),
     ("rbfd_get_level", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_i64), _vp, _vp, ctypes.POINTER(_d)]),
     ("rbfd_num_levels", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     ("rbfd_level_info", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_d), ctypes.POINTER(_d),
@@ -313,6 +321,32 @@ class Mesh:
 
     def greedy(self, allow_not_converged: bool = True) -> int:
         rc = self._lib.rbfd_greedy(self.h)
+        if rc == ENOTCONV and allow_not_converged:
+            return rc
+        _check(rc)
+        return rc
+
+    def greedy_split(self, rank: int, world: int, maxloc, allow_not_converged: bool = True) -> int:
+        """``rbfd_greedy_split``: the greedy with the surface sweep split over
+        ``world`` ranks; ``maxloc(key, idx) -> (key, idx)`` combines this rank's
+        best candidate with the other ranks' (largest key, lowest index on
+        ties), once per greedy step."""
+        err = []
+
+        def cb(_user, key_p, idx_p):
+            try:
+                k, i = maxloc(float(key_p[0]), int(idx_p[0]))
+                key_p[0] = float(k)
+                idx_p[0] = int(i)
+                return 0
+            except Exception as exc:  # reported as RBFD_ECOMM
+                err.append(exc)
+                return 1
+
+        fn = MAXLOC_FN(cb)
+        rc = self._lib.rbfd_greedy_split(self.h, int(rank), int(world), fn, None)
+        if err and rc == ECOMM:
+            raise RbfdError(ECOMM, f"maxloc callback raised {err[0]!r}") from err[0]
         if rc == ENOTCONV and allow_not_converged:
             return rc
         _check(rc)

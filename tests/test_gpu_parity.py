@@ -1,13 +1,21 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Greedy: the selected control sequence must equal the oracle's exactly up to
-the first step where the oracle's two largest error keys are within rounding
-of each other (relative gap below TIE); past such a near-tie both answers are
-correct, so the rest is checked for validity instead (every level below its
-tolerance, weights solving Eq. 9 on the GPU's own controls).
+Greedy, three checks:
+* the selected control sequence equals the oracle's exactly up to the first
+  step where the oracle's two largest error keys are within rounding of each
+  other (relative gap below TIE); past such a near-tie both answers are
+  correct and the runs interpolate different targets;
+* replay (every case, split or not): the oracle follows the GPU's own
+  sequence and at every step the GPU's pick must be the oracle's argmax of
+  Eq. 12 up to the rounding of Eq. 12 itself, and every stop decision must
+  agree with the oracle's error against tau_l up to the same rounding;
+* validity: each level's weights solve Eq. 9 on the GPU's own controls, each
+  level's error is below tau_l, the levels telescope.
 
-Volume: FP64 mode within 1e-10 max|dS| of the oracle, mixed mode within
-1e-5 max|dS| (both when the control sequences agree in full).
+Volume: the GPU's update against the oracle's psi-blended update with the
+GPU's own controls and weights (always): 1e-10 max|dS| in FP64 mode, 1e-5
+max|dS| in mixed mode; and, where the sequences agree in full, against the
+oracle's own run (FP64: fp64_volume_tol, mixed: 1e-5 max|dS|).
 """
 import os
 
@@ -22,6 +30,14 @@ pytestmark = pytest.mark.gpu
 
 NT = os.cpu_count() or 1
 TIE = 1e-7
+U = 2.0**-53
+# rounding of Eq. 12: two FP64 (or double-float, |error| below 2^-44 per
+# operation) evaluations of E_i = dS_l,i - sum_j alpha_j phi_ij with n terms,
+# summed in different orders and with weights from different (backward
+# stable) solves, differ by a small multiple of n u (|dS_l,i| + sum_j
+# |alpha_j| phi_ij); REPLAY_SLACK is that multiple (measured at most 0.15 on
+# the benchmark inputs and the 3D wing's first 400 steps per level)
+REPLAY_SLACK = 8.0
 C2 = [4.0, -15.0, 20.0, -10.0, 0.0, 1.0]
 
 
@@ -58,6 +74,84 @@ def check_sequences(ref, levels, strict_full=False):
     return True
 
 
+def check_replay(c, levels, basis="C2"):
+    """The oracle replays the GPU's own sequence (oracle.replay): every pick
+    must be the oracle's argmax of Eq. 12 up to the rounding of Eq. 12 (a
+    key deficit of at most 2 |E| dE + dE^2, dE = REPLAY_SLACK n u (scale of
+    E at the best point + at the pick)), the greedy must have continued only
+    while the oracle's largest error was above tau_l S0 and stopped a
+    converged level with it below, both up to dE.  Returns the largest
+    deficit relative to its allowance."""
+    S0 = float(np.sqrt((c.dS**2).sum(1)).max())
+    rp = oracle.replay(c.xyz_s, c.dS, c.R, [L.idx for L in levels], basis=basis, n_threads=NT)
+    worst = 0.0
+    for l, L in enumerate(levels):
+        n = np.arange(1, len(L.idx) + 1, dtype=np.float64)
+        bk, pk = rp.best_key[l], rp.pick_key[l]
+        dE = REPLAY_SLACK * n * U * (rp.best_scale[l] + rp.pick_scale[l])
+        allow = 2.0 * np.sqrt(bk) * dE + dE * dE
+        d = (bk - pk)[:-1]
+        if d.size:
+            k = int(np.argmax(d - allow[:-1]))
+            assert d[k] <= allow[k], (f"level {l}: control {k + 1} ({L.idx[k + 1]}) has key {pk[k]:.17g}, the "
+                                      f"oracle's best is {bk[k]:.17g} (allowed deficit {allow[k]:g})")
+            worst = max(worst, float((d / np.maximum(allow[:-1], 1e-300)).max()))
+        tauS = L.tau * S0
+        e = np.sqrt(bk)
+        assert (e[:-1] + dE[:-1] >= tauS).all(), f"level {l}: the greedy went on below tau"
+        if L.e_max < L.tau:
+            assert e[-1] - dE[-1] < tauS, f"level {l}: stopped with the oracle's error {e[-1] / S0:g} above tau"
+    return worst
+
+
+def gpu_result(levels, S0):
+    """The GPU's levels (controls, weights, max |dS_l|) as an oracle result,
+    for the oracle's volume update on the GPU's own controls and weights."""
+    L = len(levels)
+    return oracle.GreedyResult(oracle.OK, [x.idx for x in levels], [x.alpha for x in levels],
+                               np.array([x.smax for x in levels]), np.zeros(L), np.zeros(L), None, S0)
+
+
+def volume_rounding_scale(c, levels, basis="C2"):
+    """max over the volume points of sum_l psi(d / D_l) sum_j |alpha_j^(l)| phi_vj:
+    two evaluations of Eq. 19 / Eq. 23 that sum in different orders differ by
+    a few n u times this (dense products: small cases only)."""
+    poly = POLY.get(basis, C2)
+    ph = lambda e: np.where(e < 1.0, np.polyval(poly, np.minimum(e, 1.0)), 0.0)
+    Dl = oracle.support_distances(np.array([L.smax for L in levels]), c.k, c.D)
+    xv = c.xyz_v.astype(np.float64)
+    dv = c.d_v.astype(np.float64)
+    tot = np.zeros(len(xv))
+    for l, L in enumerate(levels):
+        if not Dl[l] > 0:
+            continue
+        w = psi_np(dv / Dl[l])
+        tot += w * (ph(cdist(xv, c.xyz_s[L.idx]) / c.R[l]) @ np.abs(L.alpha).sum(1))
+    return float(tot.max()) if len(tot) else 0.0
+
+
+def check_volume_own(c, m, levels, precision, basis="C2"):
+    """The GPU's volume update against the oracle's (Eq. 19, Eq. 23) on the
+    GPU's own controls and weights: only the evaluation's rounding differs.
+    FP64: 1e-10 max|dS|, or the rounding of the sums where the weights are so
+    large (ill-conditioned control systems) that it exceeds that: 8 n u times
+    the volume_rounding_scale, n the most controls of a level."""
+    S0 = float(np.sqrt((c.dS**2).sum(1)).max())
+    want = oracle.deform(gpu_result(levels, S0), c.xyz_s, c.R, c.xyz_v, c.d_v, c.k, c.D, basis=basis,
+                         n_threads=NT)
+    if precision == rbfd.FP64:
+        nmax = max(len(L.idx) for L in levels)
+        tol = max(1e-10 * S0, 8.0 * nmax * U * volume_rounding_scale(c, levels, basis))
+    else:
+        tol = 1e-5 * S0
+    got = m.deform(c.xyz_v, c.d_v, c.D, c.k).astype(np.float64)
+    assert np.abs(got - want).max() <= tol + np.abs(want).max() * 2.0**-24
+    got64 = m.deform(c.xyz_v.astype(np.float64), c.d_v.astype(np.float64), c.D, c.k)
+    err64 = np.abs(got64 - want).max()
+    assert err64 <= tol, f"volume error {err64 / S0:g} S0 on the GPU's own controls"
+    return err64 / S0
+
+
 def check_valid(c, levels, S0):
     """Validity of any correct answer: each level's weights solve Eq. 9 on its
     own controls, the level error is below tau_l, levels telescope."""
@@ -81,11 +175,19 @@ def psi_np(xi):
     return np.where(xi < 1.0, 1.0 - xi, 0.0)
 
 
-def fp64_volume_tol(c, ref, basis_poly=None):
-    """FP64 volume bound: the larger of 1e-10 max|dS| and ten times the
-    disagreement, at the volume points, between two backward-stable FP64 solves
-    of Eq. 9 on the oracle's controls (its row Cholesky and LAPACK's LU).
-    Both are correct to about cond(Phi_cc) u; no solver can do better."""
+# cases whose FP64 volume bound against the oracle's own run exceeds
+# 1e-10 max|dS| (ill-conditioned control systems; their volumes are held to
+# 1e-10 max|dS| on the GPU's own weights instead)
+FP64_BOUND_ABOVE_1E10 = {"wing_ridge_2lvl", "C4", "C6"}
+
+
+def fp64_volume_tol(c, ref, basis_poly=None, name=None):
+    """FP64 volume bound against the oracle's own run: the larger of 1e-10
+    max|dS| and ten times the disagreement, at the volume points, between two
+    backward-stable FP64 solves of Eq. 9 on the oracle's controls (its row
+    Cholesky and LAPACK's LU).  Both are correct to about cond(Phi_cc) u; no
+    solver can do better.  The bound is printed, and the cases where it
+    exceeds 1e-10 max|dS| must be the ones listed in FP64_BOUND_ABOVE_1E10."""
     poly = basis_poly or C2
     ph = lambda e: np.where(e < 1.0, np.polyval(poly, np.minimum(e, 1.0)), 0.0)
     Dl = oracle.support_distances(ref.smax, c.k, c.D)
@@ -103,7 +205,11 @@ def fp64_volume_tol(c, ref, basis_poly=None):
         va += w * (P @ ref.alpha[l])
         vb += w * (P @ a_lu)
         cur = cur - ph(cdist(c.xyz_s, c.xyz_s[C]) / R) @ ref.alpha[l]
-    return max(1e-10 * ref.S0, 10.0 * np.abs(va - vb).max())
+    tol = max(1e-10 * ref.S0, 10.0 * np.abs(va - vb).max())
+    print(f"fp64_volume_tol[{name}] = {tol / ref.S0:.3g} max|dS|")
+    if name is not None:
+        assert (tol > 1e-10 * ref.S0) == (name in FP64_BOUND_ABOVE_1E10), f"{name}: bound {tol / ref.S0:g} S0"
+    return tol
 
 
 def small_cases():
@@ -131,7 +237,9 @@ def test_greedy_and_deform_parity(name, precision):
     m, rc = run_gpu(c, precision)
     levels = m.levels()
     full = check_sequences(ref, levels)
+    check_replay(c, levels)
     check_valid(c, levels, ref.S0)
+    check_volume_own(c, m, levels, precision)
     for l, lv in enumerate(levels):
         # level 0 targets are the inputs; later levels' targets carry the
         # rounding of Eq. 12 (about n u sum|alpha phi|, below 1e-9 S0 here).
@@ -148,7 +256,7 @@ def test_greedy_and_deform_parity(name, precision):
         return
     dv_ref = oracle.deform(ref, c.xyz_s, c.R, c.xyz_v, c.d_v, c.k, c.D, n_threads=NT)
     dv = m.deform(c.xyz_v, c.d_v, c.D, c.k)
-    tol = fp64_volume_tol(c, ref) if precision == rbfd.FP64 else 1e-5 * ref.S0
+    tol = fp64_volume_tol(c, ref, name=name) if precision == rbfd.FP64 else 1e-5 * ref.S0
     err = np.abs(dv.astype(np.float64) - dv_ref).max()
     # float32 output: add half an ulp of the largest displacement
     assert err <= tol + np.abs(dv_ref).max() * 2.0**-24, f"volume error {err / ref.S0:g} S0"
@@ -168,16 +276,25 @@ POLY = {
 
 
 @pytest.mark.parametrize("basis", ["C0", "C4", "C6"])
-def test_other_wendland_bases_fp64(basis):
+@pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
+def test_other_wendland_bases(basis, precision):
+    """Wendland C0, C4, C6 (Table 1) on an airfoil with a 2D ice horn, in both
+    precisions: sequence (up to near-ties), replay, validity, volume on the
+    GPU's own weights, and against the oracle's own run where the sequences
+    agree in full."""
     c = synth.airfoil_case(256, 6, displacement="bump", seed=0, R=(0.6,), eps=1e-3, D=2.0, k=0.0)
     ref = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, basis=basis, n_threads=NT)
-    m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=rbfd.FP64, basis=oracle.BASIS[basis])
+    m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, basis=oracle.BASIS[basis])
     m.greedy()
-    full = check_sequences(ref, m.levels())
+    levels = m.levels()
+    full = check_sequences(ref, levels)
+    check_replay(c, levels, basis=basis)
+    check_volume_own(c, m, levels, precision, basis=basis)
     if full:
         dv_ref = oracle.deform(ref, c.xyz_s, c.R, c.xyz_v, c.d_v, c.k, c.D, basis=basis, n_threads=NT)
         dv = m.deform(c.xyz_v.astype(np.float64), c.d_v.astype(np.float64), c.D, c.k)
-        assert np.abs(dv - dv_ref).max() <= fp64_volume_tol(c, ref, POLY[basis])
+        tol = fp64_volume_tol(c, ref, POLY[basis], name=basis) if precision == rbfd.FP64 else 1e-5 * ref.S0
+        assert np.abs(dv - dv_ref).max() <= tol
 
 
 @pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
@@ -196,23 +313,61 @@ def test_naca0012_400_full_fp64_and_mixed():
     for precision in (rbfd.FP64, rbfd.MIXED):
         m, _ = run_gpu(c, precision)
         assert check_sequences(ref, m.levels(), strict_full=True)
+        check_replay(c, m.levels())
         dv = m.deform(c.xyz_v, c.d_v, c.D, c.k).astype(np.float64)
-        tol = fp64_volume_tol(c, ref) if precision == rbfd.FP64 else 1e-5 * ref.S0
+        tol = fp64_volume_tol(c, ref, name=c.name) if precision == rbfd.FP64 else 1e-5 * ref.S0
         assert np.abs(dv - dv_ref).max() <= tol + np.abs(dv_ref).max() * 2.0**-24
 
 
 @pytest.mark.parametrize("disp", ["horns", "pitch_heave"])
-def test_naca0012_4000_1m_full_mixed(disp):
+@pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
+def test_naca0012_4000_1m_full(disp, precision):
+    """The 4,000-point / 1M-point airfoil configurations, both cases, both
+    precisions: the control sequence must equal the oracle's in full (the
+    oracle's smallest top-2 gap on these inputs, 1.8e-8, is far above the
+    rounding of Eq. 12 in either precision), the replay must pass, and the
+    volume must meet the FP64 (1e-10 max|dS|) or mixed (1e-5 max|dS|) bar
+    against the oracle's own run."""
     c = synth.make_config(f"naca0012_4000s_1mv_{disp}")
     ref = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, n_threads=NT)
-    m, _ = run_gpu(c, rbfd.MIXED)
+    m, _ = run_gpu(c, precision)
     levels = m.levels()
-    # the oracle's smallest top-2 gap on these inputs is well above rounding
     assert check_sequences(ref, levels, strict_full=True)
+    check_replay(c, levels)
     check_valid(c, levels, ref.S0)
-    dv = m.deform(c.xyz_v, c.d_v, c.D, c.k).astype(np.float64)
     dv_ref = oracle.deform(ref, c.xyz_s, c.R, c.xyz_v, c.d_v, c.k, c.D, n_threads=NT)
-    assert np.abs(dv - dv_ref).max() <= 1e-5 * ref.S0 + np.abs(dv_ref).max() * 2.0**-24
+    if precision == rbfd.FP64:
+        tol = fp64_volume_tol(c, ref, name=c.name)
+        assert tol == 1e-10 * ref.S0
+        dv = m.deform(c.xyz_v.astype(np.float64), c.d_v.astype(np.float64), c.D, c.k)
+        assert np.abs(dv - dv_ref).max() <= tol
+    else:
+        dv = m.deform(c.xyz_v, c.d_v, c.D, c.k).astype(np.float64)
+        assert np.abs(dv - dv_ref).max() <= 1e-5 * ref.S0 + np.abs(dv_ref).max() * 2.0**-24
+
+
+def test_mixed_batched_matches_fp64_single():
+    """The mixed-precision batched form (rbfd_run_jobs: both 4,000-point cases
+    and the 400-point case in one call) against the plain FP64 single-request
+    form (rbfd_create + rbfd_greedy + rbfd_deform_f64) on the same GPU: the
+    volume displacements agree within 1e-5 max|dS|."""
+    names = ["naca0012_4000s_1mv_horns", "naca0012_4000s_1mv_pitch_heave", "naca0012_400s_40kv_bump"]
+    cases = [synth.make_config(n) for n in names]
+    want = []
+    for c in cases:
+        m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=rbfd.FP64)
+        m.greedy()
+        want.append(m.deform(c.xyz_v.astype(np.float64), c.d_v.astype(np.float64), c.D, c.k))
+        m.close()
+    jobs = [dict(xyz_s=c.xyz_s, dS=c.dS, R=c.R, eps=c.eps, precision=rbfd.MIXED, xyz_v=c.xyz_v, d_v=c.d_v,
+                 D=c.D, k=c.k, out=np.empty((c.n_v, c.dim), np.float32)) for c in cases]
+    ms, rc = rbfd.run_jobs(jobs)
+    assert rc == rbfd.OK
+    for c, j, w, m in zip(cases, jobs, want, ms):
+        S0 = float(np.sqrt((c.dS**2).sum(1)).max())
+        err = np.abs(j["out"].astype(np.float64) - w).max()
+        assert err <= 1e-5 * S0 + np.abs(w).max() * 2.0**-24, f"{c.name}: {err / S0:g} max|dS|"
+        m.close()
 
 
 # ---------------------------------------------------------------- edge cases

@@ -20,6 +20,7 @@ import os
 
 import numpy as np
 import pytest
+from scipy.spatial.distance import cdist
 
 import oracle
 from paper_2107_13887_gb300 import rbfd, synth
@@ -27,6 +28,40 @@ from paper_2107_13887_gb300 import rbfd, synth
 pytestmark = pytest.mark.gpu
 
 NT = os.cpu_count() or 1
+
+
+@pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
+def test_wing_60k_first_steps_replayed(precision):
+    """The first K = 400 greedy steps of each of the three levels of the 60k
+    wing (nc_cap = K: each capped level hands its error to the next), in the
+    default engine (Newton-basis start, then the list sweep).  The oracle
+    replays the GPU's sequence: every pick is the oracle's argmax of Eq. 12 up
+    to the rounding of Eq. 12 (the ridge is symmetric about the chord plane,
+    so exact ties occur: there either point is the argmax), the weights solve
+    Eq. 9 as the oracle's do, and the sequence equals the oracle's own up to
+    its first near-tie."""
+    from test_gpu_parity import check_replay, check_sequences, phi_np
+
+    K = 400
+    c = synth.make_config("wing_60ks_6mv_ridge", n_layers=0)
+    m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=precision, nc_cap=K)
+    assert m.greedy() == rbfd.ENOTCONV
+    lv = m.levels()
+    assert [len(L.idx) for L in lv] == [K, K, K]
+    worst = check_replay(c, lv)
+    print(f"largest pick deficit / allowance: {worst:g}")
+    ref = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, nc_cap=K, n_threads=NT)
+    check_sequences(ref, lv)
+    S0 = float(np.sqrt((c.dS**2).sum(1)).max())
+    cur = c.dS.copy()
+    for l, L in enumerate(lv):
+        # Eq. 9 on the GPU's own controls, and the level targets (max |dS_l|)
+        assert abs(L.smax - np.sqrt((cur**2).sum(1)).max()) <= 1e-9 * S0
+        A = phi_np(cdist(c.xyz_s[L.idx], c.xyz_s[L.idx]) / c.R[l])
+        res = A @ L.alpha - cur[L.idx]
+        assert np.abs(res).max() <= 1e-9 * S0 + 1e-12 * np.abs(L.alpha).max(), f"level {l}: Eq. 9 residual"
+        cur = cur - phi_np(cdist(c.xyz_s, c.xyz_s[L.idx]) / c.R[l]) @ L.alpha
+    m.close()
 
 
 def test_wing_60k_6m_full_size_sampled():
