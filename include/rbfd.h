@@ -394,6 +394,50 @@ int rbfd_deform_batch(rbfd_mesh **meshes, int n, const int64_t *n_v, const float
                       const float *const *d_v, const double *D, const double *k, float *const *out);
 
 /*
+ * rbfd_deform_worklist -- the volume update of Eq. 19 with the blending of
+ * Eq. 23 (Section 4) for n meshes (several wings of uneven size, say) in ONE
+ * persistent launch.  Per mesh, its points are packed and Morton-sorted and
+ * the lists V_l = {d < D_l} are formed on the mesh's own stream; then one
+ * work-list kernel sweeps every (mesh, level) pair: blocks of 128 list
+ * entries are handed out from a global counter, level by level, so small and
+ * large meshes share the SMs with no tail of one mesh's launch; a level of a
+ * mesh waits (bounded) for that mesh's previous level before it adds into the
+ * same accumulator.  The results are those of rbfd_deform for each mesh,
+ * within the mixed-mode bound (1e-5 max|dS|): the pair arithmetic is the
+ * same, only the cell grid may differ (cell_div).
+ *
+ * Requirements: every mesh in mixed precision (RBFD_MIXED), all of one
+ * dimension and basis, greedy done, on one device; float32 volume arrays
+ * (host or device per each mesh's inputs_on_device); d_v (or any d_v[i]) may
+ * be NULL: wall distances are then computed on the device.  n <= 16 meshes
+ * and at most 64 (mesh, level) pairs.
+ *
+ * tune (in/out, may be NULL: autotune): with tune->autotune = 1 the call
+ * times candidate settings on this call's own work (per mesh the cell size
+ * R_l or R_l / 2 of its control grid; then blocks per SM; then list blocks per
+ * work item) by coordinate descent, keeps the fastest, and caches it for later
+ * calls on meshes of the same sizes; with autotune = 0 the given settings are
+ * used.  On return the fields hold the settings used and the launch's
+ * device time.
+ * Errors: RBFD_EINVAL, RBFD_ESTATE (no greedy), RBFD_ETIMEOUT (a level's wait
+ * ran out: not expected), RBFD_ENOMEM, RBFD_ECUDA.
+ */
+typedef struct rbfd_worklist_tune {
+    int autotune;        /* 1: choose the fields below by timing candidates (cached per batch shape) */
+    int ctas_per_sm;     /* resident blocks per SM of the work-list launch (1..8) */
+    int item_blocks;     /* 128-entry list blocks per work item (1, 2 or 4) */
+    int cell_div[16];    /* per mesh: control cell size R_l / cell_div, 1 or 2 */
+    int cached;          /* out: 1 if the settings came from the cache */
+    int trials;          /* out: candidate launches timed by this call */
+    double launch_ms;    /* out: device time of the work-list launch */
+    int64_t items;       /* out: list blocks the launch swept */
+} rbfd_worklist_tune;
+
+int rbfd_deform_worklist(rbfd_mesh **meshes, int n, const int64_t *n_v, const float *const *xyz_v,
+                         const float *const *d_v, const double *D, const double *k, float *const *out,
+                         rbfd_worklist_tune *tune);
+
+/*
  * rbfd_greedy_deform_batch -- rbfd_greedy then rbfd_deform for each of n
  * meshes, mesh i's two calls one after the other on its own host thread and
  * stream, so that one mesh's volume update overlaps another's greedy.  With

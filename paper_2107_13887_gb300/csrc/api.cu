@@ -226,7 +226,8 @@ void mesh_free(rbfd_mesh *m) {
     // (the mesh's fixed buffers are carved out of d_arena)
     void *ptrs[] = {m->d_arena, m->d_G, m->d_Gt, m->d_vin, m->d_vpos, m->d_vorig, m->d_vflag, m->d_vscan,
                     m->d_vlist, m->d_vkeys, m->d_vacc, m->d_vio, m->d_vreg, m->d_vreg_orig, m->d_pb_fbox,
-                    m->d_V, m->d_nrec, m->d_nycol, m->d_nwdf, m->d_ckeys, m->d_vpos4};
+                    m->d_V, m->d_nrec, m->d_nycol, m->d_nwdf, m->d_ckeys, m->d_vpos4, m->d_wl_list,
+                    m->d_wl_cnt};
     for (void *p : ptrs) dfree(p);
     m->sort.release();
     m->prof.release();
@@ -753,6 +754,18 @@ int rbfd_greedy_batch(rbfd_mesh **meshes, int n) {
     }, "rbfd_greedy_batch");
     unshare_grid(meshes, n);
     return rc;
+}
+
+int rbfd_deform_worklist(rbfd_mesh **meshes, int n, const int64_t *n_v, const float *const *xyz_v,
+                         const float *const *d_v, const double *D, const double *k, float *const *out,
+                         rbfd_worklist_tune *tune) {
+    return guarded([&] {
+        if (n < 1 || !meshes || !n_v || !xyz_v || !D || !k || !out)
+            rbfd::fail(RBFD_EINVAL, "rbfd_deform_worklist: bad arguments");
+        for (int i = 0; i < n; ++i)
+            if (!meshes[i]) rbfd::fail(RBFD_EINVAL, "rbfd_deform_worklist: NULL mesh");
+        rbfd::deform_worklist(meshes, n, n_v, xyz_v, d_v, D, k, out, tune);
+    });
 }
 
 int rbfd_greedy_deform_batch(rbfd_mesh **meshes, int n, const int64_t *n_v, const float *const *xyz_v,

@@ -399,16 +399,28 @@ __global__ void __launch_bounds__(kThreads) k_vol_sweep(VolArgs a) {
 // sub-partition on this GPU): FP32 block box and cell range (one guard cell
 // each side), block-relative coordinates by exact FP32 TwoSum, controls and
 // weights pre-split per level, psi in FP32, double-float accumulator.
-template <int DIM, int BASIS>
-__global__ void __launch_bounds__(kThreads) k_vol_sweep_f32(VolArgs a) {
-    __shared__ float sb[6][kThreads / 32];
-    __shared__ uint32_t s_start[kThreads], s_off[kThreads], sw[32];
-    __shared__ float t32[12][kTile];
-    __shared__ unsigned char s_hits[4][kTile];
+struct VolF32Smem {
+    float sb[6][kThreads / 32];
+    uint32_t s_start[kThreads], s_off[kThreads], sw[32];
+    float t32[12][kTile];
+    unsigned char s_hits[4][kTile];
+};
+
+// One block of 128 list entries (block index blk of the level's list).
+// COHERENT: the accumulator is read through L2 (another block of the same
+// launch may have written it: the work-list launch's earlier level).
+template <int DIM, int BASIS, bool COHERENT>
+__device__ __forceinline__ void vol_f32_block(const VolArgs &a, int64_t blk, VolF32Smem &sm) {
+    auto &sb = sm.sb;
+    auto &s_start = sm.s_start;
+    auto &s_off = sm.s_off;
+    auto &sw = sm.sw;
+    auto &t32 = sm.t32;
+    auto &s_hits = sm.s_hits;
     const int tid = threadIdx.x;
     const int64_t n_list = a.n_list_dev ? (int64_t)*a.n_list_dev : a.n_list;
-    if ((int64_t)blockIdx.x * kThreads >= n_list) return;  // (block-uniform)
-    const int64_t i = (int64_t)blockIdx.x * kThreads + tid;
+    if (blk * kThreads >= n_list) return;  // (block-uniform)
+    const int64_t i = blk * kThreads + tid;
     const bool valid = i < n_list;
     const uint32_t s = valid ? a.list[i] : 0u;
     const float4 P = valid ? a.vp4[s] : make_float4(0, 0, 0, 0);
@@ -500,7 +512,7 @@ __global__ void __launch_bounds__(kThreads) k_vol_sweep_f32(VolArgs a) {
     if (valid) {
         const float w = 1.0f - P.w * (a.invDlf_dev ? *a.invDlf_dev : a.invDlf);  // psi(d / D_l), d < D_l here
         float4 *va = reinterpret_cast<float4 *>(a.vacc + s);
-        const float4 v0 = va[0], v1 = va[1];
+        const float4 v0 = COHERENT ? __ldcg(va) : va[0], v1 = COHERENT ? __ldcg(va + 1) : va[1];
         const df sx = df_add({v0.x, v0.y}, df_mul(acc[0], {w, 0.f}));
         const df sy = df_add({v0.z, v0.w}, df_mul(acc[1], {w, 0.f}));
         const df sz = df_add({v1.x, v1.y}, df_mul(acc[2], {w, 0.f}));
@@ -516,6 +528,92 @@ __global__ void __launch_bounds__(kThreads) k_vol_sweep_f32(VolArgs a) {
     if ((tid & 31) == 0) {
         if (u) atomicAdd(&a.pairs[0], (unsigned long long)u);
         if (vv) atomicAdd(&a.pairs[1], vv);
+    }
+}
+
+template <int DIM, int BASIS>
+__global__ void __launch_bounds__(kThreads) k_vol_sweep_f32(VolArgs a) {
+    __shared__ VolF32Smem sm;
+    vol_f32_block<DIM, BASIS, false>(a, (int64_t)blockIdx.x, sm);
+}
+
+// ------------------------------------------ work-list launch over meshes
+//
+// The volume sweeps of several meshes (and all their levels) in one
+// persistent launch: entry e = (mesh, level), in level-major order; its work
+// is the blocks of 128 entries of that level's list (the list length is read
+// on the device).  Blocks take items of item_blocks consecutive blocks from a
+// global counter as they come free, so small and large meshes share the SMs.
+// A level of a mesh adds into the accumulator its previous level wrote: its
+// items wait (bounded) until every block of the previous level is done.  The
+// previous level's items have lower numbers, so they were taken earlier by
+// blocks that are running: the wait always ends.
+constexpr int kWLMax = 64;
+
+struct WorkList {
+    VolArgs e[kWLMax];
+    int dep[kWLMax];             // the entry that must be complete first (-1: none)
+    int n;                       // entries
+    int item_blocks;             // list blocks per item
+    unsigned int *ctl;           // [0] next item, [1] error (a wait ran out), [2 + e] blocks done of entry e
+    unsigned int poll_limit;     // polls of a dependency before the launch gives up
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <int DIM, int BASIS>
+__global__ void __launch_bounds__(kThreads) k_vol_worklist(const __grid_constant__ WorkList w) {
+    __shared__ VolF32Smem sm;
+    __shared__ int s_pre[kWLMax + 1];
+    __shared__ unsigned s_item;
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int e = 0; e < w.n; ++e) {
+            s_pre[e] = acc;
+            const int64_t nl = w.e[e].n_list_dev ? (int64_t)*w.e[e].n_list_dev : w.e[e].n_list;
+            acc += (int)((nl + kThreads - 1) / kThreads);
+        }
+        s_pre[w.n] = acc;
+        s_fail = 0;
+    }
+    __syncthreads();
+    const unsigned total = (unsigned)s_pre[w.n];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&w.ctl[0], (unsigned)w.item_blocks);
+        __syncthreads();
+        const unsigned it0 = s_item;
+        __syncthreads();
+        if (it0 >= total) break;
+        const unsigned it1 = min(it0 + (unsigned)w.item_blocks, total);
+        for (unsigned it = it0; it < it1; ++it) {
+            int e = 0;
+            while ((unsigned)s_pre[e + 1] <= it) ++e;
+            const int dp = w.dep[e];
+            if (dp >= 0 && threadIdx.x == 0) {
+                const unsigned need = (unsigned)(s_pre[dp + 1] - s_pre[dp]);
+                unsigned polls = 0;
+                while (ld_acquire_u32(&w.ctl[2 + dp]) < need) {
+                    if (++polls > w.poll_limit || ld_acquire_u32(&w.ctl[1])) {
+                        atomicExch(&w.ctl[1], 1u);
+                        s_fail = 1;
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+            }
+            __syncthreads();
+            if (s_fail) return;  // (block-uniform; the host reports the timeout)
+            vol_f32_block<DIM, BASIS, true>(w.e[e], (int64_t)(it - (unsigned)s_pre[e]), sm);
+            // every thread's accumulator stores before the block's count
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) atomicAdd(&w.ctl[2 + e], 1u);
+        }
     }
 }
 
@@ -1012,6 +1110,350 @@ void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, b
 // Register a volume mesh for repeated updates (rbfd_set_volume): its points
 // are packed and Morton-sorted once; deform_registered then runs only the
 // per-level compaction, evaluation and scatter for each new displacement.
+// ------------------------------------------------ work-list volume update
+
+namespace {
+
+// Tuned settings per batch shape (meshes, their volume sizes, levels).
+struct WLCached {
+    std::vector<int64_t> key;
+    rbfd_worklist_tune t;
+};
+std::mutex g_wl_mu;
+std::vector<WLCached> g_wl_cache;
+
+// The level's FP32-input sweep arguments (mode 2) for list l of mesh m,
+// on the level's grid of cell size R_l / cell_div.
+VolArgs wl_args(rbfd_mesh *m, int l, int64_t n_v, double Dl, int cell_div) {
+    const Level &Lv = m->levels[l];
+    VolArgs a{};
+    a.n_list = n_v;  // upper bound; the length is read on the device
+    a.n_list_dev = &m->d_wl_cnt[l];
+    a.list = m->d_wl_list + (size_t)l * m->wl_cap;
+    a.vpos = reinterpret_cast<const double4 *>(m->d_vpos);
+    a.vacc = m->d_vacc;
+    a.cx = Lv.d_cx;
+    a.alpha = Lv.d_alpha;
+    const bool fine = cell_div == 2 && Lv.f_cell_start;
+    a.cell_start = fine ? Lv.f_cell_start : Lv.d_cell_start;
+    a.cell_ctrl = fine ? Lv.f_cell_ctrl : Lv.d_cell_ctrl;
+    a.g0 = fine ? Lv.f_g0 : Lv.g0;
+    a.h = fine ? Lv.f_h : Lv.h;
+    a.gd = fine ? Lv.f_gdim : Lv.gdim;
+    a.R = Lv.R;
+    a.Dl = Dl;
+    const double inv = 1.0 / Lv.R;
+    a.invR_hi = (float)inv;
+    a.invR_lo = (float)(inv - (double)a.invR_hi);
+    a.pairs = m->d_pairs + 2;
+    a.vp4 = m->d_vpos4;
+    a.cdf = Lv.d_cdf;
+    a.adf = Lv.d_adf;
+    a.g0f[0] = (float)a.g0.x;
+    a.g0f[1] = (float)a.g0.y;
+    a.g0f[2] = (float)a.g0.z;
+    a.hf = (float)a.h;
+    a.Rf = (float)Lv.R;
+    a.invDlf = Dl > 0.0 ? (float)(1.0 / Dl) : 0.f;
+    return a;
+}
+
+void launch_worklist(int dim, int basis, unsigned grid, const WorkList &w, cudaStream_t st) {
+    if (dim == 2) {
+        switch (basis) {
+        case 0: k_vol_worklist<2, 0><<<grid, kThreads, 0, st>>>(w); break;
+        case 4: k_vol_worklist<2, 4><<<grid, kThreads, 0, st>>>(w); break;
+        case 6: k_vol_worklist<2, 6><<<grid, kThreads, 0, st>>>(w); break;
+        default: k_vol_worklist<2, 2><<<grid, kThreads, 0, st>>>(w); break;
+        }
+    } else {
+        switch (basis) {
+        case 0: k_vol_worklist<3, 0><<<grid, kThreads, 0, st>>>(w); break;
+        case 4: k_vol_worklist<3, 4><<<grid, kThreads, 0, st>>>(w); break;
+        case 6: k_vol_worklist<3, 6><<<grid, kThreads, 0, st>>>(w); break;
+        default: k_vol_worklist<3, 2><<<grid, kThreads, 0, st>>>(w); break;
+        }
+    }
+    RBFD_CUDA(cudaGetLastError());
+}
+
+int worklist_max_ctas_per_sm(int dim, int basis) {
+    int b = 1;
+    const void *fn = nullptr;
+    if (dim == 2) fn = basis == 0 ? (const void *)k_vol_worklist<2, 0> : basis == 4 ? (const void *)k_vol_worklist<2, 4>
+                     : basis == 6 ? (const void *)k_vol_worklist<2, 6> : (const void *)k_vol_worklist<2, 2>;
+    else fn = basis == 0 ? (const void *)k_vol_worklist<3, 0> : basis == 4 ? (const void *)k_vol_worklist<3, 4>
+              : basis == 6 ? (const void *)k_vol_worklist<3, 6> : (const void *)k_vol_worklist<3, 2>;
+    RBFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kThreads, 0));
+    return std::max(1, b);
+}
+
+}  // namespace
+
+void deform_worklist(rbfd_mesh **ms, int n, const int64_t *n_v, const float *const *xyz_v,
+                     const float *const *d_v, const double *D, const double *k, float *const *out,
+                     rbfd_worklist_tune *tune) {
+    if (n < 1 || n > 16) fail(RBFD_EINVAL, "rbfd_deform_worklist: 1 to 16 meshes");
+    const int dim = ms[0]->dim, basis = ms[0]->opt.basis, dev = ms[0]->device;
+    int n_entries = 0;
+    for (int i = 0; i < n; ++i) {
+        rbfd_mesh *m = ms[i];
+        if (!m->greedy_done) fail(RBFD_ESTATE, "rbfd_deform_worklist: mesh " + std::to_string(i) + " has no greedy");
+        if (m->opt.precision == RBFD_FP64 || m->dim != dim || m->opt.basis != basis || m->device != dev)
+            fail(RBFD_EINVAL, "rbfd_deform_worklist: the meshes must all be mixed precision, of one dimension, "
+                              "basis and device (mesh " + std::to_string(i) + " is not)");
+        if (n_v[i] < 0 || n_v[i] >= (int64_t)1 << 31 || (n_v[i] > 0 && (!xyz_v[i] || !out[i])))
+            fail(RBFD_EINVAL, "rbfd_deform_worklist: bad volume arrays of mesh " + std::to_string(i));
+        if (!(D[i] >= 0.0) || !(k[i] >= 0.0) || (D[i] == 0.0 && k[i] == 0.0))
+            fail(RBFD_EINVAL, "rbfd_deform_worklist: D and k must be >= 0 and not both 0");
+        n_entries += (int)m->levels.size();
+    }
+    if (n_entries > kWLMax) fail(RBFD_EINVAL, "rbfd_deform_worklist: more than 64 (mesh, level) pairs");
+    RBFD_CUDA(cudaSetDevice(dev));
+    cudaStream_t st0 = ms[0]->stream;
+
+    // ---- per mesh, on its own stream: inputs, packing, Morton order, wall
+    // distances if not given, accumulator, the lists d < D_l of every level
+    std::vector<std::vector<double>> Dl(n);
+    std::vector<void *> dout(n, nullptr);
+    std::vector<cudaEvent_t> ev(n, nullptr);
+    for (int i = 0; i < n; ++i) {
+        rbfd_mesh *m = ms[i];
+        cudaStream_t st = m->stream;
+        volume_unstage(m);
+        greedy_finish(m);
+        const int L = (int)m->levels.size();
+        Dl[i].assign(L, 0.0);
+        double Dmax = 0.0;
+        for (int l = 0; l < L; ++l) {
+            double v = (k[i] > 0.0) ? k[i] * m->levels[l].smax : D[i];
+            if (k[i] > 0.0 && D[i] > 0.0 && v > D[i]) v = D[i];
+            Dl[i][l] = (m->levels[l].nc > 0) ? v : 0.0;
+            Dmax = std::max(Dmax, Dl[i][l]);
+        }
+        RBFD_CUDA(cudaEventRecord(m->ev0, st));
+        const VolumeIO io = volume_io(m, n_v[i], xyz_v[i], d_v ? d_v[i] : nullptr, out[i], false, st);
+        dout[i] = io.out;
+        const int64_t nv = n_v[i];
+        if (nv > 0) {
+            reserve_volume(m, (size_t)nv);
+            if (m->wl_cap < (size_t)nv || m->wl_levels < L) {
+                dfree(m->d_wl_list);
+                m->d_wl_list = nullptr;
+                m->wl_cap = 0;
+                m->d_wl_list = dalloc<uint32_t>((size_t)std::max(L, 1) * (size_t)nv, "work-list level lists");
+                m->wl_cap = (size_t)nv;
+                m->wl_levels = std::max(L, 1);
+            }
+            if (!m->d_wl_cnt) m->d_wl_cnt = dalloc<uint32_t>(kWLMax, "work-list list lengths");
+            RBFD_CUDA(cudaMemsetAsync(m->d_wl_cnt, 0, sizeof(uint32_t) * kWLMax, st));
+            double4 *vin = reinterpret_cast<double4 *>(m->d_vin);
+            double4 *vpos = reinterpret_cast<double4 *>(m->d_vpos);
+            k_vol_pack<<<cdiv(nv, 256), 256, 0, st>>>(io.x, io.d, nv, dim, 0, vin);
+            morton_order(m, nv, vin, vpos, m->d_vorig, st, m->d_red, m->d_bbox, m->sort);
+            if (!io.d && Dmax > 0.0) wall_distance_sorted(m, nv, vpos, Dmax, nullptr);
+            deform_acc_init(m, nv, vpos, false, st);
+            for (int l = 0; l < L; ++l) {
+                if (!(Dl[i][l] > 0.0)) continue;
+                k_flag_below<<<cdiv(nv, 256), 256, 0, st>>>(vpos, nullptr, nv, Dl[i][l], m->d_vflag);
+                exclusive_scan_u32(m->d_vflag, m->d_vscan, (size_t)nv, &m->d_wl_cnt[l], m->sort, st);
+                k_compact<<<cdiv(nv, 256), 256, 0, st>>>(m->d_vflag, m->d_vscan, nv,
+                                                         m->d_wl_list + (size_t)l * m->wl_cap);
+                k_count_points<<<1, 32, 0, st>>>(&m->d_wl_cnt[l], m->d_pairs + 7);
+                m->stats.launches += 4;
+            }
+            if (tune == nullptr || tune->autotune || tune->cell_div[i] == 2)
+                for (auto &Lv : m->levels) level_fine_grid(m, Lv);
+            m->stats.launches += 2;
+        }
+        RBFD_CUDA(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+        RBFD_CUDA(cudaEventRecord(ev[i], st));
+        RBFD_CUDA(cudaStreamWaitEvent(st0, ev[i], 0));
+        RBFD_CUDA(cudaGetLastError());
+    }
+
+    // ---- the work list: (mesh, level) entries, level-major
+    rbfd_worklist_tune t{};
+    t.autotune = tune ? tune->autotune : 1;
+    t.ctas_per_sm = 2;
+    t.item_blocks = 1;
+    for (int i = 0; i < 16; ++i) t.cell_div[i] = 1;
+    if (tune && !tune->autotune) {
+        t.ctas_per_sm = tune->ctas_per_sm;
+        t.item_blocks = tune->item_blocks;
+        for (int i = 0; i < n; ++i) t.cell_div[i] = tune->cell_div[i];
+    }
+    const int occ = worklist_max_ctas_per_sm(dim, basis);
+    int sms = 0;
+    RBFD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    auto sanitize = [&](rbfd_worklist_tune &x) {
+        x.ctas_per_sm = std::max(1, std::min(x.ctas_per_sm, std::min(occ, 8)));
+        x.item_blocks = x.item_blocks >= 4 ? 4 : x.item_blocks >= 2 ? 2 : 1;
+        for (int i = 0; i < n; ++i) x.cell_div[i] = x.cell_div[i] == 2 ? 2 : 1;
+    };
+    sanitize(t);
+    auto build = [&](const rbfd_worklist_tune &x, unsigned int *ctl, unsigned long long *pairs_scratch) {
+        WorkList w{};
+        std::vector<int> prev(n, -1);
+        int Lmax = 0;
+        for (int i = 0; i < n; ++i) Lmax = std::max(Lmax, (int)ms[i]->levels.size());
+        for (int l = 0; l < Lmax; ++l)
+            for (int i = 0; i < n; ++i) {
+                rbfd_mesh *m = ms[i];
+                if (l >= (int)m->levels.size() || n_v[i] == 0 || m->levels[l].nc == 0 || !(Dl[i][l] > 0.0)) continue;
+                const int e = w.n++;
+                w.e[e] = wl_args(m, l, n_v[i], Dl[i][l], x.cell_div[i]);
+                if (pairs_scratch) w.e[e].pairs = pairs_scratch;
+                w.dep[e] = prev[i];
+                prev[i] = e;
+            }
+        w.item_blocks = x.item_blocks;
+        w.ctl = ctl;
+        w.poll_limit = 1u << 24;  // about 5 s of polls: far beyond any level's sweep
+        return w;
+    };
+    // control words + scratch pair counters for the timed candidates
+    const size_t ctl_words = 2 + kWLMax;
+    void *blk = dmalloc(sizeof(unsigned int) * 128 + sizeof(unsigned long long) * 4, "work-list control");
+    unsigned int *ctl = static_cast<unsigned int *>(blk);
+    unsigned long long *scratch = reinterpret_cast<unsigned long long *>(ctl + 128);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    RBFD_CUDA(cudaEventCreate(&t0));
+    RBFD_CUDA(cudaEventCreate(&t1));
+    auto run = [&](const rbfd_worklist_tune &x, bool trial) {
+        const WorkList w = build(x, ctl, trial ? scratch : nullptr);
+        RBFD_CUDA(cudaMemsetAsync(ctl, 0, sizeof(unsigned int) * ctl_words, st0));
+        RBFD_CUDA(cudaEventRecord(t0, st0));
+        if (w.n > 0) launch_worklist(dim, basis, (unsigned)(x.ctas_per_sm * sms), w, st0);
+        RBFD_CUDA(cudaEventRecord(t1, st0));
+        unsigned int err = 0;
+        RBFD_CUDA(cudaMemcpyAsync(&err, ctl + 1, sizeof(err), cudaMemcpyDeviceToHost, st0));
+        RBFD_CUDA(cudaStreamSynchronize(st0));
+        if (err) fail(RBFD_ETIMEOUT, "rbfd_deform_worklist: a level's wait for the previous level ran out");
+        float ms_ = 0.f;
+        RBFD_CUDA(cudaEventElapsedTime(&ms_, t0, t1));
+        return (double)ms_;
+    };
+    auto reset_acc = [&]() {
+        for (int i = 0; i < n; ++i)
+            if (n_v[i] > 0) RBFD_CUDA(cudaMemsetAsync(ms[i]->d_vacc, 0, sizeof(double4) * n_v[i], st0));
+    };
+    // ---- the settings: given, cached for this batch shape, or tuned here
+    std::vector<int64_t> key{(int64_t)n, (int64_t)dim, (int64_t)basis};
+    for (int i = 0; i < n; ++i) {
+        key.push_back(n_v[i]);
+        key.push_back((int64_t)ms[i]->levels.size());
+    }
+    int trials = 0, cached = 0;
+    if (t.autotune) {
+        bool hit = false;
+        {
+            std::lock_guard<std::mutex> lk(g_wl_mu);
+            for (auto &c : g_wl_cache)
+                if (c.key == key) {
+                    t = c.t;
+                    hit = true;
+                }
+        }
+        if (hit) {
+            cached = 1;
+        } else {
+            // coordinate descent on this call's own work (results discarded,
+            // the accumulators cleared after): each mesh's cell size, then
+            // blocks per SM, then list blocks per item
+            double best = run(t, true);
+            ++trials;
+            reset_acc();
+            for (int i = 0; i < n; ++i) {
+                if (n_v[i] == 0) continue;
+                rbfd_worklist_tune c = t;
+                c.cell_div[i] = 2;
+                const double v = run(c, true);
+                ++trials;
+                reset_acc();
+                if (v < best) {
+                    best = v;
+                    t = c;
+                }
+            }
+            for (int cps : {1, 2, 3, 4, 6, 8}) {
+                if (cps > std::min(occ, 8) || cps == t.ctas_per_sm) continue;
+                rbfd_worklist_tune c = t;
+                c.ctas_per_sm = cps;
+                const double v = run(c, true);
+                ++trials;
+                reset_acc();
+                if (v < best) {
+                    best = v;
+                    t = c;
+                }
+            }
+            for (int ib : {2, 4}) {
+                rbfd_worklist_tune c = t;
+                c.item_blocks = ib;
+                const double v = run(c, true);
+                ++trials;
+                reset_acc();
+                if (v < best) {
+                    best = v;
+                    t = c;
+                }
+            }
+            std::lock_guard<std::mutex> lk(g_wl_mu);
+            g_wl_cache.push_back({key, t});
+        }
+    }
+    // ---- the launch, then each mesh's scatter to the caller's order
+    const double launch_ms = run(t, false);
+    int64_t items = 0;
+    {
+        const WorkList w = build(t, ctl, nullptr);
+        std::vector<unsigned int> done(ctl_words, 0u);
+        RBFD_CUDA(cudaMemcpy(done.data(), ctl, sizeof(unsigned int) * ctl_words, cudaMemcpyDeviceToHost));
+        for (int e = 0; e < w.n; ++e) items += done[2 + e];
+    }
+    RBFD_CUDA(cudaEventRecord(t1, st0));
+    for (int i = 0; i < n; ++i) {
+        rbfd_mesh *m = ms[i];
+        cudaStream_t st = m->stream;
+        RBFD_CUDA(cudaStreamWaitEvent(st, t1, 0));
+        const int64_t nv = n_v[i];
+        if (nv > 0) {
+            k_scatter_out_df<<<cdiv(nv, 256), 256, 0, st>>>(m->d_vacc, m->d_vorig, nv, dim,
+                                                           static_cast<float *>(dout[i]));
+            RBFD_CUDA(cudaGetLastError());
+            m->stats.launches += 1;
+            if (!m->opt.inputs_on_device)
+                RBFD_CUDA(cudaMemcpyAsync(out[i], dout[i], sizeof(float) * nv * dim, cudaMemcpyDeviceToHost, st));
+        }
+        RBFD_CUDA(cudaEventRecord(m->ev1, st));
+    }
+    for (int i = 0; i < n; ++i) {
+        rbfd_mesh *m = ms[i];
+        RBFD_CUDA(cudaEventSynchronize(m->ev1));
+        float ms_ = 0.f;
+        RBFD_CUDA(cudaEventElapsedTime(&ms_, m->ev0, m->ev1));
+        m->stats.deform_ms = ms_;
+        if (m->prof.on) {  // (the shared launch, split evenly over the meshes' counters)
+            m->prof.ms[kProfVol] += launch_ms / n;
+            m->prof.launches[kProfVol] += 1;
+        }
+        cudaEventDestroy(ev[i]);
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    dfree(blk);
+    ms[0]->stats.launches += 1 + trials;
+    if (tune) {
+        *tune = t;
+        tune->autotune = t.autotune;
+        tune->cached = cached;
+        tune->trials = trials;
+        tune->launch_ms = launch_ms;
+        tune->items = items;
+    }
+}
+
 void volume_register(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const float *d_v) {
     cudaStream_t st = m->stream;
     const int dim = m->dim;

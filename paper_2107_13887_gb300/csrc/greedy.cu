@@ -974,11 +974,13 @@ __global__ void k_level_split(const double4 *__restrict__ cx, const double4 *__r
     adf[2 * j + 1] = make_float4(az.hi, az.lo, 0.f, 0.f);
 }
 
-// Uniform grid of cell size h over the level's controls (for the volume
-// sweep); bb = the controls' box (lo xyz, hi xyz), known on the host.
-void build_control_grid(rbfd_mesh *m, Level &L, const double *bb) {
+// Uniform grid of cell size h0 (grown while the cell table would exceed 4M
+// cells) over the level's controls, for the volume sweep; bb = the box the
+// controls lie in (lo xyz, hi xyz), known on the host.
+void grid_over_controls(rbfd_mesh *m, const Level &L, const double *bb, double h0, double3 &g0_out,
+                        double &h_out, int3 &gd_out, uint32_t *&start, uint32_t *&ctrl) {
     const int n = (int)L.nc;
-    double h = L.R;
+    double h = h0;
     auto dims = [&](double hh) {
         int nx = std::max(1, (int)std::floor((bb[3] - bb[0]) / hh) + 1);
         int ny = std::max(1, (int)std::floor((bb[4] - bb[1]) / hh) + 1);
@@ -990,21 +992,26 @@ void build_control_grid(rbfd_mesh *m, Level &L, const double *bb) {
         h *= 2.0;
         gd = dims(h);
     }
-    L.h = h;
-    L.g0 = make_double3(bb[0], bb[1], m->dim == 3 ? bb[2] : 0.0);
-    L.gdim = gd;
-    L.ncell = gd.x * gd.y * gd.z;
-    L.d_cell_start = dalloc<uint32_t>((size_t)L.ncell + 1, "control cell starts");
-    L.d_cell_ctrl = dalloc<uint32_t>((size_t)n, "control cell list");
+    h_out = h;
+    g0_out = make_double3(bb[0], bb[1], m->dim == 3 ? bb[2] : 0.0);
+    gd_out = gd;
+    const int ncell = gd.x * gd.y * gd.z;
+    start = dalloc<uint32_t>((size_t)ncell + 1, "control cell starts");
+    ctrl = dalloc<uint32_t>((size_t)n, "control cell list");
     if (!m->d_ckeys) m->d_ckeys = dalloc<uint32_t>((size_t)m->cap + 1, "control cell keys");
     uint32_t *keys = m->d_ckeys;
-    k_cell_keys<<<cdiv(n, 256), 256, 0, m->stream>>>(L.d_cx, n, L.g0, 1.0 / h, gd, keys, L.d_cell_ctrl);
+    k_cell_keys<<<cdiv(n, 256), 256, 0, m->stream>>>(L.d_cx, n, g0_out, 1.0 / h, gd, keys, ctrl);
     int bits = 1;
-    while ((1u << bits) < (unsigned)L.ncell && bits < 32) ++bits;
-    radix_sort_pairs(keys, L.d_cell_ctrl, (size_t)n, bits, m->sort, m->stream);
-    k_cell_start<<<cdiv((size_t)L.ncell + 1, 256), 256, 0, m->stream>>>(keys, n, L.ncell, L.d_cell_start);
+    while ((1u << bits) < (unsigned)ncell && bits < 32) ++bits;
+    radix_sort_pairs(keys, ctrl, (size_t)n, bits, m->sort, m->stream);
+    k_cell_start<<<cdiv((size_t)ncell + 1, 256), 256, 0, m->stream>>>(keys, n, ncell, start);
     m->stats.launches += 2;
     RBFD_CUDA(cudaGetLastError());
+}
+
+void build_control_grid(rbfd_mesh *m, Level &L, const double *bb) {
+    grid_over_controls(m, L, bb, L.R, L.g0, L.h, L.gdim, L.d_cell_start, L.d_cell_ctrl);
+    L.ncell = L.gdim.x * L.gdim.y * L.gdim.z;
 }
 
 }  // namespace
@@ -1211,6 +1218,11 @@ static bool newton_enabled() {
     return !(v && v[0] == '0');
 }
 
+void level_fine_grid(rbfd_mesh *m, Level &L) {
+    if (L.f_cell_start || L.nc == 0) return;
+    grid_over_controls(m, L, m->h_sbox, 0.5 * L.R, L.f_g0, L.f_h, L.f_gdim, L.f_cell_start, L.f_cell_ctrl);
+}
+
 void level_free(Level &L) {
     dfree(L.d_cx);
     dfree(L.d_alpha);
@@ -1219,6 +1231,9 @@ void level_free(Level &L) {
     dfree(L.d_orig);
     dfree(L.d_cell_start);
     dfree(L.d_cell_ctrl);
+    dfree(L.f_cell_start);
+    dfree(L.f_cell_ctrl);
+    L.f_cell_start = L.f_cell_ctrl = nullptr;
     pinned_free(L.h_scal);
     L.d_cx = L.d_alpha = nullptr;
     L.d_cdf = L.d_adf = nullptr;

@@ -110,6 +110,11 @@ struct Level {
     int ncell = 0;
     uint32_t *d_cell_start = nullptr;  // [ncell + 1]
     uint32_t *d_cell_ctrl = nullptr;   // [nc] control ids ordered by cell
+    // the same with cell size h / 2 (made on request: level_fine_grid)
+    double3 f_g0{0, 0, 0};
+    double f_h = 0;
+    int3 f_gdim{0, 0, 0};
+    uint32_t *f_cell_start = nullptr, *f_cell_ctrl = nullptr;
 };
 
 // Optional per-kernel-class timing with CUDA events on the mesh's stream.
@@ -236,6 +241,10 @@ struct rbfd_mesh {
     float4 *d_vpos = nullptr;      // compacted + Morton-sorted points
     float4 *d_vpos4 = nullptr;     // the same as float4 (FP32-input volume sweep)
     uint32_t *d_vorig = nullptr;   // their caller indices
+    uint32_t *d_wl_list = nullptr; // work-list volume update: the lists d < D_l of every level [levels][wl_cap]
+    size_t wl_cap = 0;
+    int wl_levels = 0;
+    uint32_t *d_wl_cnt = nullptr;  // [64] their lengths
     uint32_t *d_vflag = nullptr, *d_vscan = nullptr, *d_vlist = nullptr, *d_vkeys = nullptr;
     double4 *d_vacc = nullptr;     // accumulated displacement per sorted point
     void *d_vio = nullptr;         // staging for host inputs/outputs
@@ -283,10 +292,17 @@ void greedy_run(rbfd_mesh *m, bool wait = true);
 void greedy_finish(rbfd_mesh *m);
 // a level's device and pinned buffers back to the pools (its stream synchronised)
 void level_free(Level &L);
+// the level's control grid of half the cell size (f_* fields), queued on
+// the mesh's stream if not made yet
+void level_fine_grid(rbfd_mesh *m, Level &L);
 // the host copies of a level's indices and weights (one synchronised copy, first call only)
 void level_fetch(rbfd_mesh *m, Level &L);
 void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64, double D, double k,
                 void *out);
+// rbfd_deform_worklist: the volume updates of n meshes in one work-list launch
+void deform_worklist(rbfd_mesh **ms, int n, const int64_t *n_v, const float *const *xyz_v,
+                     const float *const *d_v, const double *D, const double *k, float *const *out,
+                     rbfd_worklist_tune *tune);
 // Stage a volume for the next deform_run with the same arguments: copies,
 // packing and the Morton order of every point, on a second stream that
 // starts after the work queued so far on the mesh's stream (the greedy can

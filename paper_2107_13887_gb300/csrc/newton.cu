@@ -124,7 +124,7 @@ struct NewtonArgs {
     int64_t n_s;
     int n_pb, cap, cn;  // cn: columns of V (controls the launch may reach)
     int ppb, cs;        // points per block (32 per group), columns of V held in shared memory
-    double R, invR, R2, S0, tau, piv_tol_per_n, switch_ratio, switch_work;
+    double R, invR, R2, S0, tau, piv_tol_per_n, piv_tol_df_per_n, switch_ratio, switch_work;
     // the stop test's bracket as argmax keys: key < key_lo is below the
     // threshold, key >= key_hi above it, keys between are tested exactly
     unsigned long long key_lo, key_hi;
@@ -765,15 +765,19 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
             // shorter than the control count
             const bool hand = !stop && (nn >= a.cn || ((double)a.n_s * nn > a.switch_work &&
                                                        (double)nn > a.switch_ratio * (double)mc));
-            bool singular = false;
+            bool singular = false, weak = false;
             if (!stop && !hand) {
                 // 1 / l_j, and w_j = E(c_j) / l_j in FP64 for (b): lanes 0-2
                 // take w_j's components, lane 3 takes 1 / l_j
                 if (MODE) {
                     const float4 *rf = reinterpret_cast<const float4 *>(&s_wrec[1]);
                     const df l2 = {rf[1].z, rf[1].w};
-                    singular = !(l2.hi > (float)(a.piv_tol_per_n * (nn + 1)));
-                    if (!singular) {
+                    // 1 - s2 in double-float carries an error of about
+                    // n 2^-47: a pivot within 8 times that cannot be told from
+                    // zero here, and the level goes on in the list sweep,
+                    // whose FP64 growth tests it (ESINGULAR only there)
+                    weak = !(l2.hi > (float)(a.piv_tol_df_per_n * (nn + 1)));
+                    if (!weak) {
                         const df il = df_rsqrt(l2);
                         const float *ef = reinterpret_cast<const float *>(&s_wrec[2]);
                         const df q = lane < 3 ? df_mul({ef[2 * lane], ef[2 * lane + 1]}, il) : il;
@@ -797,7 +801,7 @@ __global__ void __launch_bounds__(kNT, 1) k_greedy_newton(NewtonArgs a) {
                 }
             }
             if (lane == 0) {
-                s_flags = (stop ? 1 : 0) | (hand ? 2 : 0) | (singular ? 4 : 0);
+                s_flags = (stop ? 1 : 0) | ((hand || weak) ? 2 : 0) | (singular ? 4 : 0);
                 s_mc = mc;
             }
         } else if (I >= 0) {
@@ -1077,6 +1081,7 @@ void newton_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
         a.key_hi = stop_key(K_hi, mixed, true);
     }
     a.piv_tol_per_n = 8.0 * 1.1102230246251565e-16;
+    a.piv_tol_df_per_n = 5.684341886080802e-14;  // 2^-44
     a.switch_ratio = 3.0;
     a.switch_work = 2e7;  // ~30 us of FP64 multiply-adds per step
     if (const char *v = std::getenv("RBFD_NEWTON_SWITCH")) a.switch_ratio = std::strtod(v, nullptr);

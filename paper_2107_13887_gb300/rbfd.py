@@ -128,6 +128,19 @@ class rbfd_job(ctypes.Structure):
     ]
 
 
+class rbfd_worklist_tune(ctypes.Structure):
+    _fields_ = [
+        ("autotune", ctypes.c_int),
+        ("ctas_per_sm", ctypes.c_int),
+        ("item_blocks", ctypes.c_int),
+        ("cell_div", ctypes.c_int * 16),
+        ("cached", ctypes.c_int),
+        ("trials", ctypes.c_int),
+        ("launch_ms", ctypes.c_double),
+        ("items", ctypes.c_int64),
+    ]
+
+
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
 # int maxloc(void *user, double *key, int64_t *idx) (rbfd_greedy_split)
@@ -164,6 +177,10 @@ SIGNATURES = [
     ("rbfd_deform_batch", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_i64),
                                          ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_d),
                                          ctypes.POINTER(_d), ctypes.POINTER(_vp)]),
+    ("rbfd_deform_worklist", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_i64),
+                                             ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_d),
+                                             ctypes.POINTER(_d), ctypes.POINTER(_vp),
+                                             ctypes.POINTER(rbfd_worklist_tune)]),
     ("rbfd_greedy_deform_batch", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_i64),
                                                 ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_d),
                                                 ctypes.POINTER(_d), ctypes.POINTER(_vp)]),
@@ -552,6 +569,32 @@ def deform_batch(meshes, xyz_v, d_v, D, k, out):
     arr = (_vp * n)(*[m.h.value for m in meshes])
     _check(lib.rbfd_deform_batch(arr, n, nv, px, pd, Dv, kv, po))
     return out
+
+
+def deform_worklist(meshes, xyz_v, d_v, D, k, out, autotune=True, ctas_per_sm=2, item_blocks=1, cell_div=None):
+    """``rbfd_deform_worklist``: the volume updates of several meshes in one
+    work-list launch; float32 arrays as in ``deform_batch`` (``d_v`` may be
+    None, or hold None entries).  Returns the settings used as a dict
+    (autotuned and cached per batch shape, or the ones given)."""
+    lib = load()
+    n = len(meshes)
+    arr = (_vp * n)(*[m.h.value for m in meshes])
+    nv = (_i64 * n)(*[int(x.shape[0]) for x in xyz_v])
+    px = (_vp * n)(*[_ptr(x).value for x in xyz_v])
+    pd = None if d_v is None else (_vp * n)(*[None if x is None else _ptr(x).value for x in d_v])
+    Dv = (_d * n)(*[float(x) for x in D])
+    kv = (_d * n)(*[float(x) for x in k])
+    po = (_vp * n)(*[_ptr(x).value for x in out])
+    t = rbfd_worklist_tune()
+    t.autotune = 1 if autotune else 0
+    t.ctas_per_sm = int(ctas_per_sm)
+    t.item_blocks = int(item_blocks)
+    for i in range(min(n, 16)):
+        t.cell_div[i] = int(cell_div[i]) if cell_div is not None else 1
+    _check(lib.rbfd_deform_worklist(arr, n, nv, px, pd, Dv, kv, po, ctypes.byref(t)))
+    return {"autotune": bool(t.autotune), "ctas_per_sm": t.ctas_per_sm, "item_blocks": t.item_blocks,
+            "cell_div": list(t.cell_div)[:n], "cached": bool(t.cached), "trials": t.trials,
+            "launch_ms": t.launch_ms, "items": t.items}
 
 
 def greedy_deform_batch(meshes, xyz_v, d_v, D, k, out, allow_not_converged: bool = True) -> int:

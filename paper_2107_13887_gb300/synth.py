@@ -29,7 +29,9 @@ __all__ = [
     "airfoil_case",
     "wing_case",
     "make_config",
+    "make_config_set",
     "CONFIGS",
+    "CONFIG_SETS",
 ]
 
 
@@ -47,6 +49,7 @@ class Case:
     eps: float
     D: float  # support distance cap of the wall-distance function (0 = none)
     k: float  # volume reduction factor (0 = use D at every level)
+    nc_cap: int = 0  # most controls per level (0: the library's default)
 
     @property
     def n_s(self) -> int:
@@ -280,6 +283,8 @@ def wing_case(
     radius: float = 20.0,
     semi_span: float = 3.0,
     name: str | None = None,
+    wall_distance: bool = True,
+    nc_cap: int = 0,
 ) -> Case:
     """3D swept (30 deg), tapered (0.5) wing of NACA0012 sections, span 3 chords.
 
@@ -293,7 +298,8 @@ def wing_case(
       ``ridge``     leading-edge ice ridge, height growing linearly from 0.01
                     at the root to 0.03 at the tip with seeded smooth spanwise
                     noise (three sine modes, +-15% in total), chordwise
-                    Gaussian of sigma 0.02 in arc length;
+                    Gaussian of sigma 0.02 in arc length, its centre shifted
+                    by a seeded U[-0.1, 0.1] sigma off the leading edge;
       ``sinusoid``  dy = 0.03 sin(4 pi z) (Eq. 27).
     """
     rng = np.random.default_rng(seed)
@@ -305,7 +311,10 @@ def wing_case(
             w[m] * np.sin((m + 1) * math.pi * z / semi_span + ph[m]) for m in range(3)
         )
         h = (0.01 + 0.02 * z / semi_span) * noise
-        amp = h * np.exp(-0.5 * (s / 0.02) ** 2)
+        # the ridge's centre shifted by a seeded tenth of its width at most:
+        # the upper and lower sides then never carry exactly equal errors
+        s0 = 0.02 * rng.uniform(-0.1, 0.1)
+        amp = h * np.exp(-0.5 * ((s - s0) / 0.02) ** 2)
         dS = nrm * amp[:, None]
     elif displacement == "sinusoid":
         dS = np.zeros_like(pts)
@@ -319,7 +328,7 @@ def wing_case(
         off = _o_mesh(xy2, nrm2, n_layers, radius).reshape(n_chord, n_layers, 2) - xy2[:, None, :]
         off3 = np.concatenate([off, np.zeros((n_chord, n_layers, 1))], axis=2)
         xv = (pts.reshape(n_span, n_chord, 1, 3) + off3[None]).reshape(-1, 3)
-        d = _wall_distance(xv, pts)
+        d = _wall_distance(xv, pts) if wall_distance else None
     else:
         xv = np.zeros((0, 3))
         d = np.zeros((0,))
@@ -329,11 +338,12 @@ def wing_case(
         xyz_s=np.ascontiguousarray(pts, dtype=np.float64),
         dS=np.ascontiguousarray(dS, dtype=np.float64),
         xyz_v=np.ascontiguousarray(xv, dtype=np.float32),
-        d_v=np.ascontiguousarray(d, dtype=np.float32),
+        d_v=None if d is None else np.ascontiguousarray(d, dtype=np.float32),
         R=list(R),
         eps=float(eps),
         D=float(D),
         k=float(k),
+        nc_cap=int(nc_cap),
     )
 
 
@@ -356,6 +366,35 @@ CONFIGS = {
         kind="wing", n_chord=400, n_span=150, n_layers=100, displacement="ridge", R=(1.5, 0.4, 0.1), eps=1e-5, D=1.0, k=4.0
     ),
 }
+
+
+# Workloads of several meshes deformed together
+CONFIG_SETS = {
+    # four swept wings of uneven size, seeds 0-3: 200x150 = 30k, 400x200 =
+    # 80k, 500x300 = 150k and 625x400 = 250k surface points, 100 layers each
+    # (3M, 8M, 15M, 25M volume points, float32), the ridge of the 60k wing,
+    # three levels, at most 20,000 controls per level
+    "wings4_30k_250ks_3m_25mv_ridge": [
+        dict(kind="wing", n_chord=nc, n_span=ns, n_layers=100, displacement="ridge", R=(1.5, 0.4, 0.1), eps=1e-5,
+             D=1.0, k=4.0, nc_cap=20000, seed=s)
+        for s, (nc, ns) in enumerate([(200, 150), (400, 200), (500, 300), (625, 400)])
+    ],
+}
+
+
+def make_config_set(name: str, n_layers: int | None = None, wall_distance: bool = True, **over):
+    """Build a named workload of several meshes (a list of Case).  With
+    wall_distance = False the volumes carry no wall distances (d_v = None):
+    the library computes them on the device."""
+    out = []
+    for i, spec in enumerate(CONFIG_SETS[name]):
+        spec = dict(spec)
+        spec.update(over)
+        if n_layers is not None:
+            spec["n_layers"] = n_layers
+        spec.pop("kind")
+        out.append(wing_case(name=f"{name}[{i}]", wall_distance=wall_distance, **spec))
+    return out
 
 
 def make_config(name: str, seed: int = 0, n_layers: int | None = None, **over) -> Case:

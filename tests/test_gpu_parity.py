@@ -293,7 +293,11 @@ def test_other_wendland_bases(basis, precision):
     if full:
         dv_ref = oracle.deform(ref, c.xyz_s, c.R, c.xyz_v, c.d_v, c.k, c.D, basis=basis, n_threads=NT)
         dv = m.deform(c.xyz_v.astype(np.float64), c.d_v.astype(np.float64), c.D, c.k)
-        tol = fp64_volume_tol(c, ref, POLY[basis], name=basis) if precision == rbfd.FP64 else 1e-5 * ref.S0
+        # against the oracle's own weights no result can be closer than two
+        # backward-stable FP64 solves are to each other (fp64_volume_tol)
+        tol = fp64_volume_tol(c, ref, POLY[basis], name=basis)
+        if precision == rbfd.MIXED:
+            tol = max(tol, 1e-5 * ref.S0)
         assert np.abs(dv - dv_ref).max() <= tol
 
 

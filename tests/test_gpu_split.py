@@ -7,7 +7,9 @@ waits for another rank's kernels.
 * rbfd_greedy_split: every rank ends with the levels of the single-rank step
   engine (options.engine = 1), controls and weights bit for bit;
 * the volume update split by Morton ranges of the volume points: the ranks'
-  results together are the single-call update of every point, bit for bit.
+  results together are the single-call update of every point, bit for bit
+  in FP64 mode (each point's sum runs over the same controls in the same
+  order), within 1e-5 max|dS| in mixed mode.
 """
 import threading
 
@@ -89,7 +91,14 @@ def test_greedy_split_equals_single_rank(name, world, precision):
         got[idx] = part
         seen[idx] += 1
     assert (seen == 1).all()
-    assert np.array_equal(got, full)
+    if precision == rbfd.FP64:
+        assert np.array_equal(got, full)
+    else:
+        # the FP32-input sweep forms coordinates relative to each point
+        # block's corner, and the blocks of a range differ from those of the
+        # whole volume: agreement within the mixed-mode bar
+        S0 = float(np.sqrt((c.dS**2).sum(1)).max())
+        assert np.abs(got.astype(np.float64) - full).max() <= 1e-5 * S0 + np.abs(full).max() * 2.0**-24
     for m in meshes + [one]:
         m.close()
 
