@@ -487,19 +487,28 @@ def run_ours(args):
 # ------------------------------------------------------------ serving leg
 
 def serving_meshes():
-    """Eight meshes drawn from the 2D and 3D workload families (20k to 1M
-    volume points), each with its base ice shape."""
+    """Eight meshes drawn from the 2D and 3D workload families, 20k to 10M
+    volume points, each with its base ice shape: the 400-point airfoil (40k),
+    the two 4,000-point / 1M airfoil cases, the 4,000-point airfoil with
+    2,500 layers (10M), a 1,000-point airfoil with 20 layers (20k), and three
+    swept wings of the four-wing family at coarse surfaces (1.2k, 4k and 9k
+    points with 20k-ish, 2M and 9M volume points; two levels to 1e-3, so that
+    one time step costs milliseconds: the full 60k-point wing to 1e-5 takes
+    seconds per step).  Wall distances are computed on the device."""
     from paper_2107_13887_gb300 import synth
 
     return [
         synth.make_config("naca0012_400s_40kv_bump", seed=0),
-        synth.airfoil_case(1000, 100, displacement="horns", seed=1, R=(1.0, 0.2), eps=1e-5, D=2.0, k=5.0),
-        synth.airfoil_case(2000, 150, displacement="horns", seed=2, R=(1.0, 0.2), eps=1e-5, D=2.0, k=5.0),
         synth.make_config("naca0012_4000s_1mv_horns", seed=0),
         synth.make_config("naca0012_4000s_1mv_pitch_heave", seed=0),
-        synth.airfoil_case(800, 25, displacement="bump", seed=3, R=(0.5,), eps=1e-4, D=2.0, k=0.0),
-        synth.wing_case(60, 20, 20, displacement="ridge", seed=4, R=(1.5, 0.4), eps=1e-3, D=1.0, k=4.0),
-        synth.wing_case(80, 30, 25, displacement="ridge", seed=5, R=(1.5, 0.4), eps=1e-3, D=1.0, k=4.0),
+        synth.airfoil_case(4000, 2500, displacement="horns", seed=3, R=(1.0, 0.2), eps=1e-5, D=2.0, k=5.0,
+                           wall_distance=False),
+        synth.airfoil_case(1000, 20, displacement="horns", seed=1, R=(1.0, 0.2), eps=1e-5, D=2.0, k=5.0),
+        synth.wing_case(60, 20, 18, displacement="ridge", seed=4, R=(1.5, 0.4), eps=1e-3, D=1.0, k=4.0),
+        synth.wing_case(100, 40, 500, displacement="ridge", seed=5, R=(1.5, 0.4), eps=1e-3, D=1.0, k=4.0,
+                        wall_distance=False),
+        synth.wing_case(150, 60, 1000, displacement="ridge", seed=6, R=(1.5, 0.4), eps=1e-3, D=1.0, k=4.0,
+                        wall_distance=False),
     ]
 
 
@@ -536,13 +545,21 @@ def run_serving(n_requests=1000, rate=50.0, slots=4, seed=0):
     wall = time.perf_counter() - t0
     tot = np.array([srv.times(t)[2] for t in tickets])
     que = np.array([srv.times(t)[0] for t in tickets])
+    run = np.array([srv.times(t)[1] for t in tickets])
     srv.close()
+    mesh_stats = []
+    for i, c in enumerate(meshes):
+        sel = which == i
+        mesh_stats.append({"n_surface": int(c.n_s), "n_volume": int(c.n_v), "requests": int(sel.sum()),
+                         "run_ms_p50": float(np.median(run[sel])) if sel.any() else None,
+                         "run_ms_max": float(run[sel].max()) if sel.any() else None,
+                         "latency_ms_p99": float(np.percentile(tot[sel], 99)) if sel.any() else None})
     return {
         "requests": n_requests, "arrival_rate_per_s": rate, "slots": slots, "meshes": len(meshes),
         "volume_points": [int(c.n_v) for c in meshes],
         "latency_ms_p50": float(np.percentile(tot, 50)), "latency_ms_p99": float(np.percentile(tot, 99)),
         "queue_ms_p50": float(np.percentile(que, 50)), "queue_ms_p99": float(np.percentile(que, 99)),
-        "throughput_req_per_s": n_requests / wall, "wall_s": wall,
+        "throughput_req_per_s": n_requests / wall, "wall_s": wall, "per_mesh": mesh_stats,
     }
 
 

@@ -1404,11 +1404,11 @@ void greedy_run(rbfd_mesh *m, bool wait) {
             const bool split = m->split_world > 1;
             if (m->opt.engine == 0 && resumes == 0 && newton_enabled() && !split) {
                 newton_reserve(m);
-                if (m->newton_cols >= 2) {
-                    // one block per 32 surface points, as far as they fit (newton_shape)
-                    int ctas = m->opt.grid_ctas > 0 ? m->opt.grid_ctas : kMaxPersistCTAs;
-                    if (m->batch_ctas_cap > 0) ctas = std::min(ctas, m->batch_ctas_cap);
-                    ctas = std::max(1, ctas);
+                // one block per 32 surface points, as far as they fit (newton_shape)
+                int ctas = m->opt.grid_ctas > 0 ? m->opt.grid_ctas : kMaxPersistCTAs;
+                if (m->batch_ctas_cap > 0) ctas = std::min(ctas, m->batch_ctas_cap);
+                ctas = std::max(1, ctas);
+                if (m->newton_cols >= 2 && newton_fits(m, ctas)) {
                     RBFD_CUDA(cudaMemsetAsync(&m->d_st->handoff, 0, sizeof(int), st));
                     RBFD_CUDA(cudaMemsetAsync(&m->d_st->nnz_tot, 0, sizeof(unsigned long long), st));
                     RBFD_CUDA(cudaMemsetAsync(m->d_bar, 0, sizeof(GridBarrier), st));

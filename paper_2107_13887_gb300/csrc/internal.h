@@ -283,6 +283,8 @@ constexpr int kMaxPersistCTAs = 2048;
 constexpr int kNewtonCols = 4096;  // most controls a Newton-basis launch carries (y staged in shared memory)
 int newton_columns(rbfd_mesh *m);
 void newton_reserve(rbfd_mesh *m);
+// false if a Newton launch of this mesh does not fit its share of the GPU
+bool newton_fits(rbfd_mesh *m, int ctas);
 void newton_run_level(rbfd_mesh *m, double R, double tau, int ctas);
 int persist_max_ctas(rbfd_mesh *m);
 void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas);

@@ -1020,12 +1020,16 @@ NewtonShape newton_shape(rbfd_mesh *m, int want_ctas) {
                 return s;
             }
         }
-        if (ctas == 1) fail(RBFD_ENOMEM, "Newton greedy: block state exceeds shared memory");
+        // the block state does not fit even on the whole GPU's share of this
+        // mesh: no Newton launch (the level runs in the list sweep)
+        if (ctas == 1) return s;
         ctas = std::max(1, ctas * 3 / 4);  // fewer blocks, more points each
     }
 }
 
-void newton_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
+// The launch shape for `ctas` blocks asked (cached per mesh size and kind);
+// false if the Newton launch does not fit on this mesh's share of the GPU.
+bool newton_fits(rbfd_mesh *m, int ctas) {
     // the shape depends on the mesh, the request and the co-running meshes only
     const int key = ctas * 64 + std::min(m->batch_share, 63);
     if (m->newton_shape_key != key) {
@@ -1051,6 +1055,11 @@ void newton_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
         m->newton_cs = s.cs;
         m->newton_smem = s.smem;
     }
+    return m->newton_ctas > 0;
+}
+
+void newton_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
+    if (!newton_fits(m, ctas)) fail(RBFD_ENOMEM, "Newton greedy: block state exceeds shared memory");
     NewtonShape sh;
     sh.ctas = m->newton_ctas;
     sh.ppb = m->newton_ppb;

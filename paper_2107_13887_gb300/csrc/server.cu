@@ -8,8 +8,8 @@
 // persistent grids are sized to be resident together).  Requests that arrive
 // while others run wait in a FIFO queue and are admitted as soon as a slot is
 // free and their device-memory footprint fits the budget; a request whose
-// mesh is already busy can still start on a second resident instance of that
-// mesh if memory allows.  Each registered mesh keeps its resident instances
+// mesh is busy waits for that mesh's instance, while requests on other
+// meshes go ahead.  Each registered mesh keeps its resident instance
 // (Morton-ordered surface, point blocks, workspace, sorted volume) on the
 // device between time steps: a new step only uploads dS, runs the greedy
 // selection (Section 3) and the volume update (Section 4).
@@ -159,8 +159,13 @@ static void run_request(rbfd_server *S, uint64_t ticket, rbfd_mesh *inst) {
     S->cv_work.notify_all();
 }
 
-// First queued request that can start now: its mesh has an idle instance, or a
-// new instance fits the memory budget.  Called with the lock held.
+// First queued request that can start now: its mesh has an idle instance,
+// or it has no instance yet and a new one fits the memory budget.  A mesh
+// whose only instance is busy makes its request wait for that instance (the
+// same mesh's time steps run in order): creating a second instance on the
+// request path (allocations, the volume's Morton order) cost tens of
+// milliseconds and was the whole tail of the latency.  Called with the lock
+// held.
 static bool pick_request(rbfd_server *S, uint64_t &ticket, rbfd_mesh *&inst) {
     for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
         Request &r = S->reqs[*it];
@@ -170,7 +175,7 @@ static bool pick_request(rbfd_server *S, uint64_t &ticket, rbfd_mesh *&inst) {
             inst = M.idle.back();
             M.idle.pop_back();
             ok = true;
-        } else if (S->used_bytes + M.footprint <= (size_t)S->opt.mem_budget_bytes) {
+        } else if (M.instances == 0 && S->used_bytes + M.footprint <= (size_t)S->opt.mem_budget_bytes) {
             inst = nullptr;  // reserve for a new instance
             S->used_bytes += M.footprint;
             M.instances++;

@@ -126,7 +126,8 @@ def _geometric_heights(n_layers: int, h1: float, H: float) -> np.ndarray:
     lo, hi = 1.0 + 1e-12, 4.0
     for _ in range(200):  # bisection on the growth ratio
         q = 0.5 * (lo + hi)
-        tot = h1 * (q**n_layers - 1.0) / (q - 1.0)
+        e = n_layers * math.log(q)
+        tot = h1 * math.expm1(e) / (q - 1.0) if e < 700.0 else math.inf
         if tot > H:
             hi = q
         else:
@@ -198,6 +199,7 @@ def airfoil_case(
     k: float = 0.0,
     radius: float = 20.0,
     name: str | None = None,
+    wall_distance: bool = True,
 ) -> Case:
     """2D NACA0012 airfoil in an O-mesh with a prescribed surface displacement.
 
@@ -234,7 +236,7 @@ def airfoil_case(
         raise ValueError(displacement)
     if n_layers > 0:
         xv = _o_mesh(xy, nrm, n_layers, radius)
-        d = _wall_distance(xv, xy)
+        d = _wall_distance(xv, xy) if wall_distance else None
     else:
         xv = np.zeros((0, 2))
         d = np.zeros((0,))
@@ -244,7 +246,7 @@ def airfoil_case(
         xyz_s=np.ascontiguousarray(xy, dtype=np.float64),
         dS=np.ascontiguousarray(dS, dtype=np.float64),
         xyz_v=np.ascontiguousarray(xv, dtype=np.float32),
-        d_v=np.ascontiguousarray(d, dtype=np.float32),
+        d_v=None if d is None else np.ascontiguousarray(d, dtype=np.float32),
         R=list(R),
         eps=float(eps),
         D=float(D),
