@@ -97,6 +97,8 @@ def parse_args(argv=None):
     p.add_argument("--ctas", type=int, default=0, help="blocks of the persistent launch (0: automatic)")
     p.add_argument("--no-serve", action="store_true", help="skip the serving leg (p50/p99 latency)")
     p.add_argument("--serve-requests", type=int, default=1000)
+    p.add_argument("--no-local-global", action="store_true",
+                   help="skip Section 5's local (ice) vs global (sinusoid) comparison over the Wendland bases")
     p.add_argument("--oracle-steps", type=int, default=0,
                    help="greedy steps per level of the oracle sample (0: sized to about 15 s)")
     return p.parse_args(argv)
@@ -477,11 +479,53 @@ def run_ours(args):
             "extrapolation": "lower bound: brute-force pair rates of the sample applied to the full step's "
                              "control counts, Eq. 9 solves not counted",
         }
+    if not args.no_local_global:
+        line["local_vs_global"] = local_global_comparison()
     if not args.no_serve:
         line["serving"] = run_serving(n_requests=args.serve_requests)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------ local vs global
+
+def local_global_comparison(precision_names=("fp64", "mixed")):
+    """Section 5's comparison of a local (ice) and a global (sinusoid)
+    deformation, with the Wendland bases of Table 1: per case and basis the
+    controls per level, the final error and the greedy's device time to eps.
+    2D: the 4,000-point airfoil with its three ice horns against the
+    sinusoid dy = 0.01 sin(15 pi x) of Section 5.1; 3D: a 4,000-point wing
+    (100 x 40) with the leading-edge ridge against the sinusoid of Eq. 27,
+    dy = 0.03 sin(4 pi z).  Levels R = 1c then 0.2c (2D) and 1.5c then 0.4c
+    (3D), eps = 1e-5 (2D) and 1e-4 (3D).  A basis whose control system the
+    precision cannot resolve reports its status instead."""
+    from paper_2107_13887_gb300 import rbfd, synth
+
+    cases = {
+        "2d_ice": synth.airfoil_case(4000, 0, displacement="horns", seed=0, R=(1.0, 0.2), eps=1e-5),
+        "2d_sinusoid": synth.airfoil_case(4000, 0, displacement="sinusoid", seed=0, R=(1.0, 0.2), eps=1e-5),
+        "3d_ice": synth.wing_case(100, 40, 0, displacement="ridge", seed=0, R=(1.5, 0.4), eps=1e-4),
+        "3d_sinusoid": synth.wing_case(100, 40, 0, displacement="sinusoid", seed=0, R=(1.5, 0.4), eps=1e-4),
+    }
+    out = {}
+    for pname in precision_names:
+        prec = rbfd.FP64 if pname == "fp64" else rbfd.MIXED
+        for cname, c in cases.items():
+            for bname, bid in (("C0", 0), ("C2", 2), ("C4", 4), ("C6", 6)):
+                key = f"{cname}/{bname}/{pname}"
+                try:
+                    m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, precision=prec, basis=bid, nc_cap=c.n_s)
+                    rc = m.greedy()
+                    lv = m.levels()
+                    st = m.stats()
+                    out[key] = {"controls_per_level": [len(L.idx) for L in lv],
+                                "e_max": lv[-1].e_max if lv else 0.0, "time_to_eps_ms": st["greedy_ms"],
+                                "status": rbfd.STATUS_NAMES.get(rc, rc)}
+                    m.close()
+                except rbfd.RbfdError as exc:
+                    out[key] = {"status": rbfd.STATUS_NAMES.get(exc.status, exc.status), "error": str(exc)[:160]}
+    return out
 
 
 # ------------------------------------------------------------ serving leg

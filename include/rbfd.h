@@ -340,6 +340,27 @@ int rbfd_deform_noalloc(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const flo
                         float *out);
 
 /*
+ * rbfd_greedy_warm -- rbfd_greedy for the mesh's current displacement
+ * (rbfd_set_displacement), started from the previous run on this mesh: every
+ * level begins with the previous run's controls of that level and their
+ * inverse Cholesky factor, solves Eq. 9 for the new targets on it, and runs
+ * the level close (FP64 refinement and the confirm sweep of Eq. 12).  If the
+ * level's error is below tau_l the level keeps those controls; otherwise the
+ * greedy of Section 3 continues from them.  A time step of an ice-growth
+ * sequence, whose displacement changes little, then costs a few triangular
+ * products and one sweep per level instead of the whole selection.  The
+ * controls of a warm run are valid (every level below tau_l, Eq. 9 solved)
+ * but they are the previous run's, not the greedy's own choice for the new
+ * displacement.
+ *
+ * The first call on a mesh, or one after the levels changed, runs the plain
+ * greedy.  From the first call on, every greedy on the mesh keeps each
+ * level's factor on the device for the next call: 16 n_l^2 bytes per level
+ * (about 80 MB for 2,300 controls).  Errors: as rbfd_greedy.
+ */
+int rbfd_greedy_warm(rbfd_mesh *m);
+
+/*
  * rbfd_greedy_split -- rbfd_greedy with the surface points split over `world`
  * ranks (one GPU each), for the argmax of Section 3: at every greedy step
  * E = dS_l - Phi_sc alpha (Eq. 12) is swept over this rank's share of the

@@ -471,6 +471,15 @@ int rbfd_greedy(rbfd_mesh *m) {
     });
 }
 
+int rbfd_greedy_warm(rbfd_mesh *m) {
+    return guarded([&] {
+        if (!m) rbfd::fail(RBFD_EINVAL, "rbfd_greedy_warm: NULL mesh");
+        RBFD_CUDA(cudaSetDevice(m->device));
+        m->keep_factors = true;
+        rbfd::greedy_run(m, true, true);
+    });
+}
+
 int rbfd_greedy_split(rbfd_mesh *m, int rank, int world, rbfd_maxloc_fn maxloc, void *user) {
     return guarded([&] {
         if (!m) rbfd::fail(RBFD_EINVAL, "rbfd_greedy_split: NULL mesh");

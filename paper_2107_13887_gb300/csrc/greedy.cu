@@ -881,6 +881,71 @@ void launch_resid_d(int basis, unsigned g, int n, const GreedyState *nfrom, doub
 #undef RBFD_RESID
 }
 
+// ------------------------------------------------------------ warm start
+
+// A level restarted from a previous run's n controls (sorted positions cid):
+// coordinates (FP64 and double-float split), selected flags, the greedy
+// state as after n - 1 steps; alpha cleared (re-solved by the caller).
+__global__ void k_warm_restore(int n, int cap, const uint32_t *__restrict__ cid_in, const double4 *__restrict__ xs,
+                               unsigned char *__restrict__ sel, double4 *__restrict__ cx, float4 *__restrict__ cdf,
+                               uint32_t *__restrict__ cid, double4 *__restrict__ alpha, GreedyState *st) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) {
+        const uint32_t c = cid_in[k];
+        const double4 x = xs[c];
+        sel[c] = 1;
+        cx[k] = x;
+        cid[k] = c;
+        const float hx = __double2float_rn(x.x), hy = __double2float_rn(x.y), hz = __double2float_rn(x.z);
+        cdf[k] = make_float4(hx, hy, hz, 0.f);
+        cdf[cap + 1 + k] = make_float4(__double2float_rn(x.x - (double)hx), __double2float_rn(x.y - (double)hy),
+                                       __double2float_rn(x.z - (double)hz), 0.f);
+        alpha[k] = make_double4(0.0, 0.0, 0.0, 0.0);
+    }
+    if (k == 0) {
+        st->n = n;
+        st->stop = 0;
+        st->status = RBFD_OK;
+        st->best = -1;
+        st->best_orig = -1;
+        st->best_key = 0;
+        st->second_key = 0;
+        st->min_gap = 1.0;
+        st->emax = 0;
+        st->pb_done = 0;
+        st->red_done = 0;
+        st->max_cnt = 1;
+        st->nnz = 0;
+        st->handoff = 0;
+    }
+}
+
+// The per-block control lists of the restored controls, in control order:
+// the same test as a greedy step's listing (box distance below R).
+__global__ void k_warm_lists(int n, int n_pb, int cap, int dim, double R2, const double4 *__restrict__ cx,
+                             const double4 *__restrict__ pb_lo, const double4 *__restrict__ pb_hi,
+                             uint32_t *__restrict__ nb_cnt, uint32_t *__restrict__ nb_list) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_pb) return;
+    const double4 l = pb_lo[t], h = pb_hi[t];
+    uint32_t cnt = 0;
+    for (int k = 0; k < n; ++k) {
+        const double4 x = cx[k];
+        const double dx = fmax(fmax(l.x - x.x, x.x - h.x), 0.0);
+        const double dy = fmax(fmax(l.y - x.y, x.y - h.y), 0.0);
+        const double dz = dim == 3 ? fmax(fmax(l.z - x.z, x.z - h.z), 0.0) : 0.0;
+        if (dx * dx + dy * dy + dz * dz < R2 * (1.0 + 1e-9)) nb_list[(size_t)t * cap + cnt++] = (uint32_t)k;
+    }
+    nb_cnt[t] = cnt;
+}
+
+// v_k = dS_l at control k (the right-hand sides of Eq. 9).
+__global__ void k_gather_ctrl(int n, const uint32_t *__restrict__ cid, const double4 *__restrict__ cur,
+                              double4 *__restrict__ v) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) v[k] = cur[cid[k]];
+}
+
 int n_chunks_for(const rbfd_mesh *m, int n) {
     int want = (kTargetCTAs + m->n_pb - 1) / m->n_pb;
     int by_len = (n + 31) / 32;
@@ -1234,6 +1299,11 @@ void level_free(Level &L) {
     dfree(L.f_cell_start);
     dfree(L.f_cell_ctrl);
     L.f_cell_start = L.f_cell_ctrl = nullptr;
+    dfree(L.d_Gs);
+    dfree(L.d_Gts);
+    dfree(L.d_cids);
+    L.d_Gs = L.d_Gts = nullptr;
+    L.d_cids = nullptr;
     pinned_free(L.h_scal);
     L.d_cx = L.d_alpha = nullptr;
     L.d_cdf = L.d_adf = nullptr;
@@ -1276,12 +1346,25 @@ void greedy_finish(rbfd_mesh *m) {
     m->prof.flush();
 }
 
-void greedy_run(rbfd_mesh *m, bool wait) {
+void greedy_run(rbfd_mesh *m, bool wait, bool warm) {
     mesh_ready(m);
     greedy_finish(m);  // (a previous run's)
     cudaStream_t st = m->stream;
-    for (auto &L : m->levels) level_free(L);
-    m->levels.clear();
+    // the previous run's levels: their factors start a warm run's levels;
+    // they are returned to the pools once this run's work is queued
+    std::vector<Level> prev;
+    prev.swap(m->levels);
+    struct FreePrev {
+        std::vector<Level> &p;
+        cudaStream_t s;
+        ~FreePrev() {
+            if (!p.empty()) cudaStreamSynchronize(s);
+            for (auto &L : p) level_free(L);
+        }
+    } free_prev{prev, st};
+    warm = warm && m->split_world == 1 && (int)prev.size() == m->n_levels_req;
+    for (size_t l = 0; warm && l < prev.size(); ++l)
+        warm = prev[l].d_Gs != nullptr && prev[l].R == m->R[l] && prev[l].nc >= 1;
     m->greedy_done = false;
     m->stats.greedy_steps = 0;
     // host wall time by part of the level (rbfd_stats.greedy_host_ms)
@@ -1318,12 +1401,37 @@ void greedy_run(rbfd_mesh *m, bool wait) {
         maxnorm_async(m, m->d_cur, m->d_lvl);
         const double R2 = L.R * L.R;
         RBFD_CUDA(cudaMemsetAsync(m->d_sel, 0, m->n_s, st));
-        k_level_init<<<cdiv(std::max(m->n_pb, 1), kThreads), kThreads, 0, st>>>(
-            m->opt.first_point == 1 ? 1 : 0, 0, m->d_inv, m->d_xs, m->d_cur, m->n_pb, m->cap, m->dim, R2,
-            m->d_pb_lo, m->d_pb_hi, m->d_sel, m->d_cx, m->d_cdf, m->d_cid, m->d_G, m->d_Gt, m->d_w, m->d_alpha, m->d_nb_cnt,
-            m->d_nb_list, m->d_lvl, m->d_st);
-        RBFD_CUDA(cudaGetLastError());
-        m->stats.launches += 2;  // maxnorm + level init
+        // a warm level restarts from the previous run's controls of this level
+        const int n_warm = warm ? (int)std::min<int64_t>(prev[l].nc, m->cap) : 0;
+        if (n_warm > 0) {
+            const Level &P = prev[l];
+            const size_t pitch = sizeof(double) * (size_t)m->cap, row = sizeof(double) * (size_t)n_warm;
+            RBFD_CUDA(cudaMemcpy2DAsync(m->d_G, pitch, P.d_Gs, sizeof(double) * (size_t)P.nc, row, n_warm,
+                                        cudaMemcpyDeviceToDevice, st));
+            RBFD_CUDA(cudaMemcpy2DAsync(m->d_Gt, pitch, P.d_Gts, sizeof(double) * (size_t)P.nc, row, n_warm,
+                                        cudaMemcpyDeviceToDevice, st));
+            k_warm_restore<<<cdiv(n_warm, 256), 256, 0, st>>>(n_warm, m->cap, P.d_cids, m->d_xs, m->d_sel, m->d_cx,
+                                                            m->d_cdf, m->d_cid, m->d_alpha, m->d_st);
+            k_warm_lists<<<cdiv(std::max(m->n_pb, 1), kThreads), kThreads, 0, st>>>(
+                n_warm, m->n_pb, m->cap, m->dim, R2, m->d_cx, m->d_pb_lo, m->d_pb_hi, m->d_nb_cnt, m->d_nb_list);
+            // Eq. 9 for the current target on the kept factor: w = G dS_l(C),
+            // alpha = G^T w (the level close refines it)
+            const unsigned nb8 = (unsigned)std::min<int64_t>(cdiv(n_warm, 8), 4 * 152);
+            RBFD_CUDA(cudaMemsetAsync(m->d_lvl + 2, 0, sizeof(double), st));
+            k_gather_ctrl<<<cdiv(n_warm, 256), 256, 0, st>>>(n_warm, m->d_cid, m->d_cur, m->d_vec);
+            k_lower_mv3<<<nb8, 256, 0, st>>>(n_warm, nullptr, m->cap, m->d_G, m->d_vec, m->d_w, m->d_lvl + 2);
+            k_upper_mv3_add<<<nb8, 256, 0, st>>>(n_warm, nullptr, m->cap, m->d_Gt, m->d_w, m->d_alpha,
+                                                 m->d_lvl + 2);
+            RBFD_CUDA(cudaGetLastError());
+            m->stats.launches += 7;
+        } else {
+            k_level_init<<<cdiv(std::max(m->n_pb, 1), kThreads), kThreads, 0, st>>>(
+                m->opt.first_point == 1 ? 1 : 0, 0, m->d_inv, m->d_xs, m->d_cur, m->n_pb, m->cap, m->dim, R2,
+                m->d_pb_lo, m->d_pb_hi, m->d_sel, m->d_cx, m->d_cdf, m->d_cid, m->d_G, m->d_Gt, m->d_w, m->d_alpha,
+                m->d_nb_cnt, m->d_nb_list, m->d_lvl, m->d_st);
+            RBFD_CUDA(cudaGetLastError());
+            m->stats.launches += 2;  // maxnorm + level init
+        }
 
         GrowArgs g{};
         g.cap = m->cap;
@@ -1352,8 +1460,12 @@ void greedy_run(rbfd_mesh *m, bool wait) {
         g.cur = m->d_cur;
         g.st = m->d_st;
 
-        int n = 1;
+        int n = n_warm > 0 ? n_warm : 1;
         int resumes = 0;
+        // a warm level's first pass only closes the restored control set
+        // (refinement and confirm sweep); if that misses tau the greedy
+        // continues from it like a resumed level
+        bool warm_close = n_warm > 0;
         // ---- level close: FP64 iterative refinement of alpha, alpha +=
         // G^T G (dS_l - Phi_cc alpha) at the controls, then the FP64 confirm
         // sweep E = dS_l - Phi_sc alpha.  The convergence test of the
@@ -1398,11 +1510,11 @@ void greedy_run(rbfd_mesh *m, bool wait) {
         for (;;) {
             bool closed = false;
             // ---- greedy steps: one persistent cooperative launch (engine 0) ...
-            bool stopped = false;
+            bool stopped = warm_close;
             // a level starts in the Newton basis (engine 0) while that pays; the
             // list sweep below takes over where it hands the level on
             const bool split = m->split_world > 1;
-            if (m->opt.engine == 0 && resumes == 0 && newton_enabled() && !split) {
+            if (m->opt.engine == 0 && resumes == 0 && newton_enabled() && !split && !stopped) {
                 newton_reserve(m);
                 // one block per 32 surface points, as far as they fit (newton_shape)
                 int ctas = m->opt.grid_ctas > 0 ? m->opt.grid_ctas : kMaxPersistCTAs;
@@ -1527,8 +1639,7 @@ void greedy_run(rbfd_mesh *m, bool wait) {
                     fail(RBFD_ESINGULAR, "Phi_cc is not positive definite at level " + std::to_string(l) +
                                              " (coincident or near-coincident controls)");
             }
-            n = m->h_st->n;
-            m->stats.greedy_steps += 0;
+            if (!warm_close) n = m->h_st->n;
             host_mark(1);
             if (!closed) {
                 enqueue_close(n, false);
@@ -1542,13 +1653,17 @@ void greedy_run(rbfd_mesh *m, bool wait) {
                 L.status = (emax < L.tau) ? RBFD_OK : RBFD_ENOTCONV;
                 break;
             }
-            // the mixed-precision selection stopped a little early: resume
-            ++resumes;
-            m->stats.confirm_resumes++;
+            // the mixed-precision selection stopped a little early, or a warm
+            // level's restored controls do not reach tau for this target: resume
+            if (!warm_close) {
+                ++resumes;
+                m->stats.confirm_resumes++;
+            }
+            warm_close = false;
             RBFD_CUDA(cudaMemsetAsync(&m->d_st->stop, 0, sizeof(int), st));
         }
         L.nc = n;
-        m->stats.greedy_steps += n - 1;
+        m->stats.greedy_steps += n - std::max(1, n_warm);
         // save the level
         L.d_cx = dalloc<double4>(n, "level controls");
         L.d_alpha = dalloc<double4>(n, "level weights");
@@ -1560,6 +1675,15 @@ void greedy_run(rbfd_mesh *m, bool wait) {
         L.d_orig = dalloc<uint32_t>(n, "level control indices");
         k_orig_of_controls<<<cdiv(n, 256), 256, 0, st>>>(m->d_perm, m->d_cid, n, L.d_orig);
         m->stats.launches += 2;
+        if (m->keep_factors) {  // the factor for a warm start of the next time step
+            const size_t pitch = sizeof(double) * (size_t)m->cap, row = sizeof(double) * (size_t)n;
+            L.d_Gs = dalloc<double>((size_t)n * n, "kept inverse factor");
+            L.d_Gts = dalloc<double>((size_t)n * n, "kept inverse factor (transposed)");
+            L.d_cids = dalloc<uint32_t>(n, "kept control positions");
+            RBFD_CUDA(cudaMemcpy2DAsync(L.d_Gs, row, m->d_G, pitch, row, n, cudaMemcpyDeviceToDevice, st));
+            RBFD_CUDA(cudaMemcpy2DAsync(L.d_Gts, row, m->d_Gt, pitch, row, n, cudaMemcpyDeviceToDevice, st));
+            RBFD_CUDA(cudaMemcpyAsync(L.d_cids, m->d_cid, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
+        }
         // the level's scalars reach the host with the final wait of the
         // greedy; indices and weights are copied only when asked for
         L.h_scal = static_cast<double *>(pinned_alloc(4 * sizeof(double)));

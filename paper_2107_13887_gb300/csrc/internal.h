@@ -110,6 +110,11 @@ struct Level {
     int ncell = 0;
     uint32_t *d_cell_start = nullptr;  // [ncell + 1]
     uint32_t *d_cell_ctrl = nullptr;   // [nc] control ids ordered by cell
+    // kept for a warm start of the next time step (rbfd_greedy_warm): the
+    // level's inverse factor G = L^{-1} and its transpose, packed n x n rows,
+    // and the controls' sorted positions
+    double *d_Gs = nullptr, *d_Gts = nullptr;
+    uint32_t *d_cids = nullptr;
     // the same with cell size h / 2 (made on request: level_fine_grid)
     double3 f_g0{0, 0, 0};
     double f_h = 0;
@@ -220,6 +225,8 @@ struct rbfd_mesh {
     // share of the Morton point blocks and the caller's all-reduce-maxloc of
     // each step's candidate; split_world = 1 outside that call
     int split_world = 1, split_rank = 0;
+    // keep every level's inverse factor after the greedy (rbfd_greedy_warm)
+    bool keep_factors = false;
     rbfd_maxloc_fn split_maxloc = nullptr;
     void *split_user = nullptr;
 
@@ -290,7 +297,11 @@ int persist_max_ctas(rbfd_mesh *m);
 void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas);
 // wait = false: the greedy returns once its work is queued; its last wait and
 // epilogue (level scalars, timing) happen in greedy_finish
-void greedy_run(rbfd_mesh *m, bool wait = true);
+// warm = true: start every level from the previous run's controls and
+// factor (kept with keep_factors), re-solve the weights for the current
+// displacement, and continue the greedy only where the level's confirm
+// sweep is not below tau_l (rbfd_greedy_warm)
+void greedy_run(rbfd_mesh *m, bool wait = true, bool warm = false);
 void greedy_finish(rbfd_mesh *m);
 // a level's device and pinned buffers back to the pools (its stream synchronised)
 void level_free(Level &L);

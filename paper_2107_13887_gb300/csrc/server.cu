@@ -12,7 +12,9 @@
 // meshes go ahead.  Each registered mesh keeps its resident instance
 // (Morton-ordered surface, point blocks, workspace, sorted volume) on the
 // device between time steps: a new step only uploads dS, runs the greedy
-// selection (Section 3) and the volume update (Section 4).
+// selection (Section 3) warm -- every level starts from the previous step's
+// controls and inverse factor and continues the greedy only if they miss
+// tau_l -- and the volume update (Section 4).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -116,6 +118,7 @@ static void run_request(rbfd_server *S, uint64_t ticket, rbfd_mesh *inst) {
                                  &o);
             if (rc != RBFD_OK) fail(rc, std::string("server: creating a mesh instance: ") + rbfd_last_error());
             volume_register(inst, M.n_v, M.xyz_v.data(), M.d_v.empty() ? nullptr : M.d_v.data());
+            inst->keep_factors = true;  // the next time step starts warm
         } else {
             mesh_set_displacement(inst, dS.data());
         }
@@ -123,7 +126,9 @@ static void run_request(rbfd_server *S, uint64_t ticket, rbfd_mesh *inst) {
         inst->batch_ctas_cap = std::max(1, persist_max_ctas(inst) / std::max(1, S->opt.slots));
         inst->batch_share = S->opt.slots;
         try {
-            greedy_run(inst);
+            // a resident instance starts every level from its previous time
+            // step's controls and factor (rbfd_greedy_warm)
+            greedy_run(inst, true, !fresh);
         } catch (const Error &e) {
             if (e.status != RBFD_ENOTCONV) throw;
             status = RBFD_ENOTCONV;  // results valid

@@ -156,6 +156,7 @@ SIGNATURES = [
     ("rbfd_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i64, _vp, _vp, ctypes.c_int, _vp, _d,
                                    ctypes.POINTER(rbfd_options)]),
     ("rbfd_greedy", ctypes.c_int, [_vp]),
+    ("rbfd_greedy_warm", ctypes.c_int, [_vp]),
     ("rbfd_greedy_split", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, MAXLOC_FN, _vp]),
     ("rbfd_get_level", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_i64), _vp, _vp, ctypes.POINTER(_d)]),
     ("rbfd_num_levels", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
@@ -338,6 +339,15 @@ class Mesh:
 
     def greedy(self, allow_not_converged: bool = True) -> int:
         rc = self._lib.rbfd_greedy(self.h)
+        if rc == ENOTCONV and allow_not_converged:
+            return rc
+        _check(rc)
+        return rc
+
+    def greedy_warm(self, allow_not_converged: bool = True) -> int:
+        """``rbfd_greedy_warm``: the greedy for the current displacement,
+        every level started from the previous run's controls and factor."""
+        rc = self._lib.rbfd_greedy_warm(self.h)
         if rc == ENOTCONV and allow_not_converged:
             return rc
         _check(rc)
