@@ -48,7 +48,10 @@ typedef enum rbfd_precision {
 
 typedef struct rbfd_options {
     int precision;         /* rbfd_precision; default RBFD_MIXED */
-    int basis;             /* Wendland basis of Table 1: 0 = C0, 2 = C2 (Eq. 2, default), 4 = C4, 6 = C6 */
+    int basis;             /* Wendland basis of Table 1: 0 = C0, 2 = C2 (Eq. 2, default), 4 = C4, 6 = C6.
+                              C4 and C6 always run in FP64 (RBFD_MIXED applies to C0 and C2): their
+                              control systems carry weights up to about 1e9 max|dS| on ice shapes,
+                              beyond what the double-float sweeps resolve */
     int first_point;       /* 0: surface point 0 starts every level (Section 3, default);
                               1: the point of largest |dS_l| starts level l */
     int inputs_on_device;  /* 0: host pointers (default); 1: device pointers */

@@ -223,6 +223,7 @@ void mesh_free(rbfd_mesh *m) {
     if (m->prep_temps) dfree(m->prep_temps);
     if (m->h_prep) pinned_free(m->h_prep);
     for (auto &L : m->levels) rbfd::level_free(L);
+    for (auto &L : m->warm_prev) rbfd::level_free(L);
     // (the mesh's fixed buffers are carved out of d_arena)
     void *ptrs[] = {m->d_arena, m->d_G, m->d_Gt, m->d_vin, m->d_vpos, m->d_vorig, m->d_vflag, m->d_vscan,
                     m->d_vlist, m->d_vkeys, m->d_vacc, m->d_vio, m->d_vreg, m->d_vreg_orig, m->d_pb_fbox,
@@ -419,6 +420,10 @@ int rbfd_create(rbfd_mesh **out, int dim, int64_t n_s, const double *xyz_s, cons
             rbfd::fail(RBFD_EINVAL, "rbfd_create: basis must be 0, 2, 4 or 6");
         if (o.precision != RBFD_FP64 && o.precision != RBFD_MIXED)
             rbfd::fail(RBFD_EINVAL, "rbfd_create: unknown precision");
+        // C4 and C6 run in FP64 whatever the precision asked: their weights
+        // reach about 1e9 max|dS| on the 2D ice cases, beyond what the
+        // double-float sweeps (about 2^-44 relative) resolve
+        if (o.basis >= 4) o.precision = RBFD_FP64;
         if (o.nc_cap < 0) rbfd::fail(RBFD_EINVAL, "rbfd_create: nc_cap must be >= 0");
         if (o.engine < 0 || o.engine > 2) rbfd::fail(RBFD_EINVAL, "rbfd_create: engine must be 0, 1 or 2");
         if (o.grid_ctas < 0 || o.grid_ctas > rbfd::kMaxPersistCTAs)

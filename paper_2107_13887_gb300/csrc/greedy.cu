@@ -1272,8 +1272,14 @@ void mesh_set_displacement(rbfd_mesh *m, const double *dS) {
     m->S0 = std::sqrt(maxnorm(m, m->d_dS, nullptr));  // synchronises the stream
     m->stats.launches += 1;
     dfree(tmp);
-    for (auto &L : m->levels) level_free(L);
-    m->levels.clear();
+    for (auto &L : m->warm_prev) level_free(L);
+    m->warm_prev.clear();
+    if (m->keep_factors) {
+        m->warm_prev.swap(m->levels);  // (a warm greedy starts from them)
+    } else {
+        for (auto &L : m->levels) level_free(L);
+        m->levels.clear();
+    }
     m->greedy_done = false;
 }
 
@@ -1354,6 +1360,9 @@ void greedy_run(rbfd_mesh *m, bool wait, bool warm) {
     // they are returned to the pools once this run's work is queued
     std::vector<Level> prev;
     prev.swap(m->levels);
+    if (prev.empty()) prev.swap(m->warm_prev);
+    for (auto &L : m->warm_prev) level_free(L);
+    m->warm_prev.clear();
     struct FreePrev {
         std::vector<Level> &p;
         cudaStream_t s;

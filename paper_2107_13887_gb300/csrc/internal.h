@@ -231,6 +231,9 @@ struct rbfd_mesh {
     void *split_user = nullptr;
 
     std::vector<rbfd::Level> levels;
+    // levels of the run before a new displacement, kept (with their factors)
+    // for the warm start of the next greedy
+    std::vector<rbfd::Level> warm_prev;
     bool greedy_done = false;
     rbfd_stats stats{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -357,11 +357,7 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
                         const int per = (cntc + kT - 1) / kT;
                         const int q0 = min(cntc, tid * per), q1 = min(cntc, q0 + per);
                         unsigned mine = 0;
-                        // FP64 in FP64 mode, and in mixed mode for C4 and C6,
-                        // whose control systems are conditioned far beyond
-                        // what a 44-bit phi column resolves (pivots of
-                        // 1 - y.y near 1e-12 on the 2D ice cases)
-                        if constexpr (MODE == 0 || BASIS >= 4) {
+                        if constexpr (MODE == 0) {
                             for (int q = q0; q < q1; ++q) {
                                 const uint32_t k = ldcg_u32(lst + q);
                                 const double4 ck = ldcg_d4(&a.cx[k]);

@@ -279,7 +279,9 @@ POLY = {
 @pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
 def test_other_wendland_bases(basis, precision):
     """Wendland C0, C4, C6 (Table 1) on an airfoil with a 2D ice horn, in both
-    precisions: sequence (up to near-ties), replay, validity, volume on the
+    precisions (a mesh with C4 or C6 runs in FP64 when mixed is asked: its
+    weights reach about 1e9 max|dS| here, beyond what the double-float sweeps
+    resolve): sequence (up to near-ties), replay, validity, volume on the
     GPU's own weights, and against the oracle's own run where the sequences
     agree in full."""
     c = synth.airfoil_case(256, 6, displacement="bump", seed=0, R=(0.6,), eps=1e-3, D=2.0, k=0.0)
