@@ -36,7 +36,8 @@ typedef enum rbfd_status {
     RBFD_EBUSY = 6,      /* serving admission refused for now (device memory); retry later */
     RBFD_ECUDA = 7,      /* a CUDA runtime call failed (message in rbfd_last_error) */
     RBFD_ESTATE = 8,     /* call out of order (e.g. deform before greedy) */
-    RBFD_ECOMM = 9       /* the caller's reduction callback failed (rbfd_greedy_split) */
+    RBFD_ECOMM = 9,      /* the caller's reduction callback failed (rbfd_greedy_split) */
+    RBFD_ECANCELED = 10  /* the serving request was cancelled before it started (rbfd_cancel) */
 } rbfd_status;
 
 typedef enum rbfd_precision {
@@ -540,7 +541,8 @@ typedef enum rbfd_request_state {
     RBFD_REQ_QUEUED = 0,
     RBFD_REQ_RUNNING = 1,
     RBFD_REQ_DONE = 2,   /* out holds the result (status RBFD_OK or RBFD_ENOTCONV) */
-    RBFD_REQ_FAILED = 3  /* rbfd_poll returns the error status */
+    RBFD_REQ_FAILED = 3,    /* rbfd_poll returns the error status */
+    RBFD_REQ_CANCELLED = 4  /* removed from the queue by rbfd_cancel; out untouched (RBFD_ECANCELED) */
 } rbfd_request_state;
 
 void rbfd_server_options_default(rbfd_server_options *opt);
@@ -567,6 +569,15 @@ int rbfd_poll(rbfd_server *s, uint64_t ticket, int *state);
 
 /* Block until the request is done or timeout_s passes (<= 0: no limit; RBFD_ETIMEOUT). */
 int rbfd_wait(rbfd_server *s, uint64_t ticket, double timeout_s, int *state);
+
+/*
+ * Cancel a queued request: it leaves the queue, its out buffer is never
+ * written, and rbfd_poll / rbfd_wait report RBFD_REQ_CANCELLED with status
+ * RBFD_ECANCELED.  A request that already runs is not interrupted (its
+ * kernels finish): RBFD_EBUSY; one that finished: RBFD_ESTATE; an unknown
+ * ticket: RBFD_EINVAL.
+ */
+int rbfd_cancel(rbfd_server *s, uint64_t ticket);
 
 /* Host-clock times of a finished request: queued, running, and submit-to-done. */
 int rbfd_request_times(rbfd_server *s, uint64_t ticket, double *queue_ms, double *run_ms, double *total_ms);

@@ -78,7 +78,28 @@ void trim_locked(DevicePool &P, int dev, size_t keep) {
 
 }  // namespace
 
+// Host-side fault injection for tests: with RBFD_TEST_ENOMEM_AT=N in the
+// environment, the N-th device allocation after the variable last changed
+// fails as if the device were out of memory (no GPU fault, no real
+// exhaustion: the failure path of every caller is exercised on the host).
+static bool injected_enomem() {
+    static std::mutex mu;
+    static std::string seen;
+    static long count = 0;
+    const char *v = std::getenv("RBFD_TEST_ENOMEM_AT");
+    std::lock_guard<std::mutex> lk(mu);
+    const std::string cur = v ? v : "";
+    if (cur != seen) {
+        seen = cur;
+        count = 0;
+    }
+    if (cur.empty()) return false;
+    return ++count == std::strtol(cur.c_str(), nullptr, 10);
+}
+
 void *dmalloc(size_t bytes, const char *what) {
+    if (injected_enomem())
+        fail(RBFD_ENOMEM, std::string("allocating ") + what + ": out of device memory (injected by RBFD_TEST_ENOMEM_AT)");
     const size_t sz = ((bytes ? bytes : 1) + 511) / 512 * 512;
     int dev = 0;
     check_cuda(cudaGetDevice(&dev), "cudaGetDevice");

@@ -948,6 +948,7 @@ void volume_stage_release(rbfd_mesh *m) {
 
 void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64, double D, double k,
                 void *out) {
+    NvtxRange nvtx("rbfd volume update");
     cudaStream_t st = m->stream;
     const int dim = m->dim;
     const size_t es = f64 ? sizeof(double) : sizeof(float);
@@ -1193,6 +1194,7 @@ int worklist_max_ctas_per_sm(int dim, int basis) {
 void deform_worklist(rbfd_mesh **ms, int n, const int64_t *n_v, const float *const *xyz_v,
                      const float *const *d_v, const double *D, const double *k, float *const *out,
                      rbfd_worklist_tune *tune) {
+    NvtxRange nvtx("rbfd work-list volume update");
     if (n < 1 || n > 16) fail(RBFD_EINVAL, "rbfd_deform_worklist: 1 to 16 meshes");
     const int dim = ms[0]->dim, basis = ms[0]->opt.basis, dev = ms[0]->device;
     int n_entries = 0;

@@ -1402,6 +1402,9 @@ void greedy_run(rbfd_mesh *m, bool wait, bool warm) {
     int final_status = RBFD_OK;
     for (int l = 0; l < Lreq; ++l) {
         host_mark(3);  // (the set-up before the first level counts with the saves)
+        char level_name[48];
+        std::snprintf(level_name, sizeof(level_name), "rbfd greedy level %d%s", l, warm ? " (warm)" : "");
+        NvtxRange nvtx_level(level_name);
         Level L;
         L.R = m->R[l];
         L.tau = std::pow(eps_rel, (double)(l + 1) / (double)Lreq);
@@ -1484,6 +1487,7 @@ void greedy_run(rbfd_mesh *m, bool wait, bool warm) {
         // greedy launch before the host has read it, n_max bounding it) and
         // do nothing if that launch handed the level on.
         auto enqueue_close = [&](int n_max, bool from_state) {
+            NvtxRange nvtx_close("rbfd level close");
             const GreedyState *nfrom = from_state ? m->d_st : nullptr;
             RBFD_CUDA(cudaMemsetAsync(m->d_lvl + 2, 0, sizeof(double), st));
             RBFD_CUDA(cudaMemsetAsync(&m->d_misc[8], 0, sizeof(uint32_t), st));  // k_resid's block counter
@@ -1533,6 +1537,7 @@ void greedy_run(rbfd_mesh *m, bool wait, bool warm) {
                     RBFD_CUDA(cudaMemsetAsync(&m->d_st->handoff, 0, sizeof(int), st));
                     RBFD_CUDA(cudaMemsetAsync(&m->d_st->nnz_tot, 0, sizeof(unsigned long long), st));
                     RBFD_CUDA(cudaMemsetAsync(m->d_bar, 0, sizeof(GridBarrier), st));
+                    NvtxRange nvtx_newton("rbfd Newton-basis launch");
                     cudaEvent_t e0 = m->prof.begin(st);
                     newton_run_level(m, L.R, L.tau, ctas);
                     m->prof.end(kProfNewton, e0, st, 1);
@@ -1566,6 +1571,7 @@ void greedy_run(rbfd_mesh *m, bool wait, bool warm) {
                 if (m->batch_ctas_cap > 0) ctas = std::min(ctas, m->batch_ctas_cap);
                 ctas = std::max(1, std::min(ctas, maxc));
                 RBFD_CUDA(cudaMemsetAsync(m->d_bar, 0, sizeof(GridBarrier), st));
+                NvtxRange nvtx_persist("rbfd persistent list sweep");
                 cudaEvent_t e0 = m->prof.begin(st);
                 persist_run_level(m, L.R, L.tau, ctas);
                 m->prof.end(kProfPersist, e0, st, 1);
@@ -1591,6 +1597,7 @@ void greedy_run(rbfd_mesh *m, bool wait, bool warm) {
             const int pb_hi = split ? (int)((int64_t)m->n_pb * (m->split_rank + 1) / m->split_world) : m->n_pb;
             while (!stopped) {
                 for (int s = 0; s < kBatch; ++s) {
+                    NvtxRange nvtx_step("rbfd greedy step");
                     SweepArgs a = base_sweep_args(m, L.R, L.tau);
                     a.n = n;
                     int nch = n_chunks_for(m, n);

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/rbfd.h"
 #include "common.cuh"
@@ -24,6 +25,15 @@ void set_last_error(const std::string &msg);
 [[noreturn]] void fail(int status, const std::string &msg);
 void check_cuda(cudaError_t e, const char *what);
 #define RBFD_CUDA(call) ::rbfd::check_cuda((call), #call)
+
+// An NVTX range for the scope (greedy levels and steps, volume updates,
+// serving requests): named spans on a profiler's timeline, nothing without one.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 // Device allocation from the library's per-device caching pool; reports
 // RBFD_ENOMEM through Error.  dfree returns the block to the pool: call it

@@ -94,6 +94,7 @@ size_t mesh_footprint(int dim, int64_t n_s, int64_t n_v, int64_t cap) {
 // Run one admitted request.  inst is an idle resident instance of its mesh,
 // or nullptr when a new instance (already counted in used_bytes) is to be made.
 static void run_request(rbfd_server *S, uint64_t ticket, rbfd_mesh *inst) {
+    NvtxRange nvtx("rbfd serving request");
     int mesh_id;
     std::vector<double> dS;
     float *out;
@@ -330,7 +331,7 @@ int rbfd_poll(rbfd_server *S, uint64_t ticket, int *state) {
         return RBFD_EINVAL;
     }
     *state = it->second.state;
-    if (it->second.state == RBFD_REQ_FAILED) rbfd::set_last_error(it->second.msg);
+    if (it->second.state >= RBFD_REQ_FAILED) rbfd::set_last_error(it->second.msg);
     return it->second.state >= RBFD_REQ_DONE ? it->second.status : RBFD_OK;
 }
 
@@ -349,8 +350,31 @@ int rbfd_wait(rbfd_server *S, uint64_t ticket, double timeout_s, int *state) {
         rbfd::set_last_error("rbfd_wait: timed out");
         return RBFD_ETIMEOUT;
     }
-    if (it->second.state == RBFD_REQ_FAILED) rbfd::set_last_error(it->second.msg);
+    if (it->second.state >= RBFD_REQ_FAILED) rbfd::set_last_error(it->second.msg);
     return it->second.status;
+}
+
+int rbfd_cancel(rbfd_server *S, uint64_t ticket) {
+    return guarded_srv([&] {
+        if (!S) rbfd::fail(RBFD_EINVAL, "rbfd_cancel: NULL server");
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->reqs.find(ticket);
+        if (it == S->reqs.end()) rbfd::fail(RBFD_EINVAL, "rbfd_cancel: unknown ticket");
+        Request &r = it->second;
+        if (r.state == RBFD_REQ_RUNNING) rbfd::fail(RBFD_EBUSY, "rbfd_cancel: the request is running");
+        if (r.state != RBFD_REQ_QUEUED) rbfd::fail(RBFD_ESTATE, "rbfd_cancel: the request has finished");
+        for (auto q = S->queue.begin(); q != S->queue.end(); ++q)
+            if (*q == ticket) {
+                S->queue.erase(q);
+                break;
+            }
+        r.state = RBFD_REQ_CANCELLED;
+        r.status = RBFD_ECANCELED;
+        r.msg = "rbfd_cancel: cancelled before it started";
+        r.t_start = r.t_done = clk::now();
+        r.dS.clear();
+        S->cv_done.notify_all();
+    });
 }
 
 int rbfd_request_times(rbfd_server *S, uint64_t ticket, double *queue_ms, double *run_ms, double *total_ms) {

@@ -17,10 +17,10 @@ import numpy as np
 
 from . import build as _build
 
-OK, EINVAL, ENOMEM, ESINGULAR, ENOTCONV, ETIMEOUT, EBUSY, ECUDA, ESTATE, ECOMM = range(10)
+OK, EINVAL, ENOMEM, ESINGULAR, ENOTCONV, ETIMEOUT, EBUSY, ECUDA, ESTATE, ECOMM, ECANCELED = range(11)
 FP64, MIXED = 0, 1
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ESINGULAR", 4: "ENOTCONV", 5: "ETIMEOUT", 6: "EBUSY",
-                7: "ECUDA", 8: "ESTATE", 9: "ECOMM"}
+                7: "ECUDA", 8: "ESTATE", 9: "ECOMM", 10: "ECANCELED"}
 
 
 class RbfdError(RuntimeError):
@@ -141,7 +141,7 @@ class rbfd_worklist_tune(ctypes.Structure):
     ]
 
 
-REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 
 # int maxloc(void *user, double *key, int64_t *idx) (rbfd_greedy_split)
 MAXLOC_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
@@ -194,6 +194,7 @@ SIGNATURES = [
     ("rbfd_submit", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(rbfd_request), ctypes.POINTER(ctypes.c_uint64)]),
     ("rbfd_poll", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
     ("rbfd_wait", ctypes.c_int, [_vp, ctypes.c_uint64, _d, ctypes.POINTER(ctypes.c_int)]),
+    ("rbfd_cancel", ctypes.c_int, [_vp, ctypes.c_uint64]),
     ("rbfd_request_times", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(_d), ctypes.POINTER(_d),
                                           ctypes.POINTER(_d)]),
     ("rbfd_server_destroy", ctypes.c_int, [_vp]),
@@ -723,6 +724,11 @@ class Server:
         if rc not in (OK, ENOTCONV):
             raise RbfdError(rc, rbfd_last_error())
         return rc, self._live.pop(ticket)
+
+    def cancel(self, ticket: int):
+        """``rbfd_cancel``: drop a queued request (its result array is never written)."""
+        _check(self._lib.rbfd_cancel(self.h, ticket))
+        self._live.pop(ticket, None)
 
     def times(self, ticket: int):
         q, r, t = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
