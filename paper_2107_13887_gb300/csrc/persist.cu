@@ -72,6 +72,7 @@ struct PersistArgs {
     unsigned long long *phase_ns;  // non-null: block 0 accumulates [work, wait] ns per phase (8 words)
     unsigned long long *item_ctr;  // the sweep's item counter (zero at launch)
     int pfx_max;                   // balanced sweep items up to this many point blocks (<= kPfxMax)
+    int chunk_target;              // controls per sweep item the chunking aims at
 };
 
 __device__ __forceinline__ uint32_t ldcg_u32(const uint32_t *p) { return __ldcg(p); }
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
         // every block list is cut into chunks of at most cl controls, cl set by
         // the longest list, so that no point block holds the step back
         const int max_cnt = max(1, (int)__ldcg(&a.st->max_cnt));
-        int nch = max((int)((P + a.n_pb - 1) / a.n_pb), (max_cnt + 63) / 64);
+        int nch = max((int)((P + a.n_pb - 1) / a.n_pb), (max_cnt + a.chunk_target - 1) / a.chunk_target);
         nch = max(1, min(nch, min(a.n_chunk_max, (max_cnt + 15) / 16)));
         const int cl = (max_cnt + nch - 1) / nch;
         // the items are the chunks the lists occupy (at least one per point
@@ -659,6 +660,10 @@ void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
     // (and the round-robin sweep items at any size, to check both assignments)
     a.pfx_max = kPfxMax;
     if (const char *v = std::getenv("RBFD_TEST_SWEEP_ROUND_ROBIN")) a.pfx_max = std::atoi(v) != 0 ? 0 : kPfxMax;
+    // controls per sweep item: shorter items balance the step's tail, longer
+    // ones cost fewer partial sums (RBFD_SWEEP_CHUNK sets it, 16 to 1024)
+    a.chunk_target = 64;
+    if (const char *v = std::getenv("RBFD_SWEEP_CHUNK")) a.chunk_target = std::max(16, std::min(1024, std::atoi(v)));
     a.phase_ns = m->prof.on ? m->d_phase_ns : nullptr;
     a.item_ctr = reinterpret_cast<unsigned long long *>(&m->d_misc[10]);  // (8-byte aligned)
     RBFD_CUDA(cudaMemsetAsync(a.item_ctr, 0, sizeof(unsigned long long), m->stream));

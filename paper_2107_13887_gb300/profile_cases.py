@@ -1,0 +1,60 @@
+"""Small cases of the library's main kernels, for profiler captures.
+
+Each case runs the hot path once on inputs a profiler can replay in a few
+seconds (a few hundred MB on the device, larger than L2 where the kernel's
+DRAM traffic matters), the same kernels as the benchmark's workloads:
+
+    python -m paper_2107_13887_gb300.profile_cases persist    # k_greedy_persist, k_greedy_newton, k_vol_sweep_f32
+    python -m paper_2107_13887_gb300.profile_cases worklist   # k_vol_worklist over four uneven wings
+
+persist:  the swept wing of the benchmark at 1/15 of its surface (100 x 40 =
+          4,000 points, 400k volume points), its three levels to 1e-5: the
+          Newton start, the persistent list sweep (levels 1 and 2) and the
+          volume update.
+worklist: the four-wing family at 1/25 of its surfaces (1.2k to 10k points)
+          and 60 layers (72k to 600k volume points each, 1.2M in all), two
+          levels to 1e-3, the volume updates of all four in one work-list
+          launch with fixed settings (R / 2 cells, 8 blocks per SM).
+"""
+from __future__ import annotations
+
+import sys
+
+import numpy as np
+
+from . import rbfd, synth
+
+
+def run_persist():
+    c = synth.wing_case(100, 40, 100, displacement="ridge", seed=0, R=(1.5, 0.4, 0.1), eps=1e-5, D=1.0, k=4.0)
+    m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps)
+    m.greedy()
+    out = m.deform(c.xyz_v, c.d_v, c.D, c.k)
+    st = m.stats()
+    print(f"persist case: controls {[len(L.idx) for L in m.levels()]}, greedy {st['greedy_ms']:.1f} ms, "
+          f"deform {st['deform_ms']:.2f} ms, finite {bool(np.isfinite(out).all())}")
+    m.close()
+
+
+def run_worklist():
+    cases = [synth.wing_case(nc, ns, 60, displacement="ridge", seed=s, R=(1.5, 0.4), eps=1e-3, D=1.0, k=4.0)
+             for s, (nc, ns) in enumerate([(40, 30), (80, 40), (100, 60), (125, 80)])]
+    ms = [rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps) for c in cases]
+    rbfd.greedy_batch(ms)
+    outs = [np.empty((c.n_v, 3), np.float32) for c in cases]
+    t = rbfd.deform_worklist(ms, [c.xyz_v for c in cases], [c.d_v for c in cases], [c.D for c in cases],
+                             [c.k for c in cases], outs, autotune=False, ctas_per_sm=8, item_blocks=1,
+                             cell_div=[2, 2, 2, 2])
+    print(f"worklist case: volume points {[c.n_v for c in cases]}, launch {t['launch_ms']:.2f} ms, "
+          f"items {t['items']}")
+    for m in ms:
+        m.close()
+
+
+def main(argv):
+    which = argv[1] if len(argv) > 1 else "persist"
+    {"persist": run_persist, "worklist": run_worklist}[which]()
+
+
+if __name__ == "__main__":
+    main(sys.argv)
