@@ -240,7 +240,54 @@ struct VolArgs {
     // if set: D_l and its FP32 inverse in device memory (they replace Dl, invDlf)
     const double *Dl_dev;
     const float *invDlf_dev;
+    // FP32-input path: the level's control records in the grid's cell order
+    // (4 float4 each), staged by bulk copies; err: set if a staging wait ran out
+    const float4 *rec;
+    unsigned *err;
 };
+
+// ---- bulk copies global -> shared completing on an mbarrier (the TMA
+// engine's 1D form): a cell's controls are contiguous records, so one copy
+// per (cell, tile) segment replaces a gather by every thread
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded: false if the phase did not complete within `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned limit) {
+    for (unsigned i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    // the shared destination was read through the generic proxy before
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+constexpr unsigned kStagePolls = 1u << 22;  // polls of a staging wait (each may suspend briefly): seconds at most
 
 template <int DIM, int BASIS, int MODE>
 __global__ void __launch_bounds__(kThreads) k_vol_sweep(VolArgs a) {
@@ -400,11 +447,23 @@ __global__ void __launch_bounds__(kThreads) k_vol_sweep(VolArgs a) {
 // each side), block-relative coordinates by exact FP32 TwoSum, controls and
 // weights pre-split per level, psi in FP32, double-float accumulator.
 struct VolF32Smem {
+    alignas(16) float4 rec[kTile][4];  // a tile of control records, as the bulk copies leave them
+    uint64_t bar;                      // their mbarrier (one arrival with the tile's byte count)
+    unsigned phase;                    // its current parity
     float sb[6][kThreads / 32];
     uint32_t s_start[kThreads], s_off[kThreads], sw[32];
     float t32[12][kTile];
     unsigned char s_hits[4][kTile];
 };
+
+// The block's mbarrier (once per launch, before its first tile).
+__device__ __forceinline__ void vol_smem_init(VolF32Smem &sm) {
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.bar, 1);
+        sm.phase = 0;
+    }
+    __syncthreads();
+}
 
 // One block of 128 list entries (block index blk of the level's list).
 // COHERENT: the accumulator is read through L2 (another block of the same
@@ -420,6 +479,7 @@ __device__ __forceinline__ void vol_f32_block(const VolArgs &a, int64_t blk, Vol
     const int tid = threadIdx.x;
     const int64_t n_list = a.n_list_dev ? (int64_t)*a.n_list_dev : a.n_list;
     if (blk * kThreads >= n_list) return;  // (block-uniform)
+    unsigned phase = sm.phase;  // the staging mbarrier's parity
     const int64_t i = blk * kThreads + tid;
     const bool valid = i < n_list;
     const uint32_t s = valid ? a.list[i] : 0u;
@@ -482,7 +542,30 @@ __device__ __forceinline__ void vol_f32_block(const VolArgs &a, int64_t blk, Vol
         __syncthreads();
         for (uint32_t w0 = 0; w0 < T; w0 += kTile) {
             const int m = (int)min((uint32_t)kTile, T - w0);
-            if (tid < m) {
+            float4 ch, cl, a0, a1;
+            if (a.rec) {
+                // the tile's records by bulk copies, one per (cell, tile)
+                // segment: a cell's controls are contiguous in the records
+                if (tid == 0) mbar_arrive_expect_tx(&sm.bar, (unsigned)m * 64u);
+                __syncthreads();
+                const uint32_t s_lo = max(off, w0), s_hi = min(off + cnt, w0 + (uint32_t)m);
+                if (s_hi > s_lo)
+                    bulk_copy_g2s(&sm.rec[s_lo - w0][0], a.rec + 4 * (size_t)(st0 + (s_lo - off)), (s_hi - s_lo) * 64u,
+                                  &sm.bar);
+                const bool ok = mbar_wait(&sm.bar, phase, kStagePolls);
+                if (!ok) {  // (not expected) record it, let the copies land, leave the block
+                    atomicExch(a.err, 1u);
+                    mbar_wait(&sm.bar, phase, kStagePolls);
+                }
+                if (__syncthreads_or(!ok)) return;  // the host reports RBFD_ETIMEOUT
+                phase ^= 1u;
+                if (tid < m) {
+                    ch = sm.rec[tid][0];
+                    cl = sm.rec[tid][1];
+                    a0 = sm.rec[tid][2];
+                    a1 = sm.rec[tid][3];
+                }
+            } else if (tid < m) {
                 uint32_t q = w0 + tid;
                 int l = 0, r = kThreads;  // last k with s_off[k] <= q
                 while (r - l > 1) {
@@ -491,10 +574,14 @@ __device__ __forceinline__ void vol_f32_block(const VolArgs &a, int64_t blk, Vol
                     else r = mid;
                 }
                 const uint32_t j = a.cell_ctrl[s_start[l] + (q - s_off[l])];
-                const float4 ch = a.cdf[2 * j], cl = a.cdf[2 * j + 1];
+                ch = a.cdf[2 * j];
+                cl = a.cdf[2 * j + 1];
+                a0 = a.adf[2 * j];
+                a1 = a.adf[2 * j + 1];
+            }
+            if (tid < m) {
                 const df rx = df_add({ch.x, cl.x}, {-lo[0], 0.f}), ry = df_add({ch.y, cl.y}, {-lo[1], 0.f}),
                          rz = df_add({ch.z, cl.z}, {-lo[2], 0.f});
-                const float4 a0 = a.adf[2 * j], a1 = a.adf[2 * j + 1];
                 t32[0][tid] = rx.hi; t32[1][tid] = rx.lo; t32[2][tid] = ry.hi; t32[3][tid] = ry.lo;
                 t32[4][tid] = rz.hi; t32[5][tid] = rz.lo; t32[6][tid] = a0.x; t32[7][tid] = a0.y;
                 t32[8][tid] = a0.z; t32[9][tid] = a0.w; t32[10][tid] = a1.x; t32[11][tid] = a1.y;
@@ -519,6 +606,7 @@ __device__ __forceinline__ void vol_f32_block(const VolArgs &a, int64_t blk, Vol
         va[0] = make_float4(sx.hi, sx.lo, sy.hi, sy.lo);
         va[1] = make_float4(sz.hi, sz.lo, 0.f, 0.f);
     }
+    if (tid == 0) sm.phase = phase;  // (read by the block's next call after a block barrier)
     unsigned u = useful;
     unsigned long long vv = visited;
     for (int o = 16; o > 0; o >>= 1) {
@@ -532,8 +620,9 @@ __device__ __forceinline__ void vol_f32_block(const VolArgs &a, int64_t blk, Vol
 }
 
 template <int DIM, int BASIS>
-__global__ void __launch_bounds__(kThreads) k_vol_sweep_f32(VolArgs a) {
+__global__ void __launch_bounds__(kThreads, 8) k_vol_sweep_f32(VolArgs a) {
     __shared__ VolF32Smem sm;
+    vol_smem_init(sm);
     vol_f32_block<DIM, BASIS, false>(a, (int64_t)blockIdx.x, sm);
 }
 
@@ -566,11 +655,12 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
 }
 
 template <int DIM, int BASIS>
-__global__ void __launch_bounds__(kThreads) k_vol_worklist(const __grid_constant__ WorkList w) {
+__global__ void __launch_bounds__(kThreads, 8) k_vol_worklist(const __grid_constant__ WorkList w) {
     __shared__ VolF32Smem sm;
     __shared__ int s_pre[kWLMax + 1];
     __shared__ unsigned s_item;
     __shared__ int s_fail;
+    vol_smem_init(sm);
     if (threadIdx.x == 0) {
         int acc = 0;
         for (int e = 0; e < w.n; ++e) {
@@ -770,6 +860,8 @@ void deform_one_level(rbfd_mesh *m, int l, int64_t nV, const double4 *vpos, doub
         a.hf = (float)Lv.h;
         a.Rf = (float)Lv.R;
         a.invDlf = Dl > 0.0 ? (float)(1.0 / Dl) : 0.f;
+        a.rec = Lv.d_rec;
+        a.err = &m->d_misc[12];
     }
     m->stats.launches += 4;  // flags, compaction, count (+ scan counted in the scan)
     cudaEvent_t e0 = m->prof.begin(st);
@@ -946,9 +1038,31 @@ void volume_stage_release(rbfd_mesh *m) {
     m->vst_ok = false;
 }
 
+namespace {
+// A staging wait of the FP32-input sweep that ran out (the sweep set the
+// mesh's error word): reported as RBFD_ETIMEOUT (the stream is synchronised).
+void vol_staging_check(rbfd_mesh *m) {
+    uint32_t err = 0;
+    RBFD_CUDA(cudaMemcpy(&err, &m->d_misc[12], sizeof(err), cudaMemcpyDeviceToHost));
+    if (err) {
+        RBFD_CUDA(cudaMemset(&m->d_misc[12], 0, sizeof(err)));
+        fail(RBFD_ETIMEOUT, "volume update: a staging wait exceeded its bound");
+    }
+}
+}  // namespace
+
+void deform_run_impl(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64, double D, double k,
+                     void *out);
+
 void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64, double D, double k,
                 void *out) {
     NvtxRange nvtx("rbfd volume update");
+    deform_run_impl(m, n_v, xyz_v, d_v, f64, D, k, out);
+    vol_staging_check(m);
+}
+
+void deform_run_impl(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64, double D, double k,
+                     void *out) {
     cudaStream_t st = m->stream;
     const int dim = m->dim;
     const size_t es = f64 ? sizeof(double) : sizeof(float);
@@ -1156,6 +1270,8 @@ VolArgs wl_args(rbfd_mesh *m, int l, int64_t n_v, double Dl, int cell_div) {
     a.hf = (float)a.h;
     a.Rf = (float)Lv.R;
     a.invDlf = Dl > 0.0 ? (float)(1.0 / Dl) : 0.f;
+    a.rec = fine ? Lv.f_rec : Lv.d_rec;
+    a.err = &m->d_misc[12];
     return a;
 }
 
@@ -1305,6 +1421,7 @@ void deform_worklist(rbfd_mesh **ms, int n, const int64_t *n_v, const float *con
                 if (l >= (int)m->levels.size() || n_v[i] == 0 || m->levels[l].nc == 0 || !(Dl[i][l] > 0.0)) continue;
                 const int e = w.n++;
                 w.e[e] = wl_args(m, l, n_v[i], Dl[i][l], x.cell_div[i]);
+                w.e[e].err = ctl + 1;  // (a staging wait that ran out fails the launch like a level wait)
                 if (pairs_scratch) w.e[e].pairs = pairs_scratch;
                 w.dep[e] = prev[i];
                 prev[i] = e;
@@ -1560,6 +1677,7 @@ void deform_registered(rbfd_mesh *m, double D, double k, float *out) {
     RBFD_CUDA(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
     m->stats.deform_ms = ms;
     m->prof.flush();
+    vol_staging_check(m);
 }
 
 }  // namespace rbfd

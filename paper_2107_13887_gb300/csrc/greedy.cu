@@ -1039,6 +1039,20 @@ __global__ void k_level_split(const double4 *__restrict__ cx, const double4 *__r
     adf[2 * j + 1] = make_float4(az.hi, az.lo, 0.f, 0.f);
 }
 
+// The level's control records in the cell order of a grid: for position p
+// of cell_ctrl, record p = (coordinates hi, lo, weights hi/lo) of control
+// cell_ctrl[p], four float4.
+__global__ void k_level_records(int n, const uint32_t *__restrict__ cell_ctrl, const float4 *__restrict__ cdf,
+                                const float4 *__restrict__ adf, float4 *__restrict__ rec) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const uint32_t j = cell_ctrl[p];
+    rec[4 * (size_t)p + 0] = cdf[2 * (size_t)j];
+    rec[4 * (size_t)p + 1] = cdf[2 * (size_t)j + 1];
+    rec[4 * (size_t)p + 2] = adf[2 * (size_t)j];
+    rec[4 * (size_t)p + 3] = adf[2 * (size_t)j + 1];
+}
+
 // Uniform grid of cell size h0 (grown while the cell table would exceed 4M
 // cells) over the level's controls, for the volume sweep; bb = the box the
 // controls lie in (lo xyz, hi xyz), known on the host.
@@ -1077,6 +1091,11 @@ void grid_over_controls(rbfd_mesh *m, const Level &L, const double *bb, double h
 void build_control_grid(rbfd_mesh *m, Level &L, const double *bb) {
     grid_over_controls(m, L, bb, L.R, L.g0, L.h, L.gdim, L.d_cell_start, L.d_cell_ctrl);
     L.ncell = L.gdim.x * L.gdim.y * L.gdim.z;
+    const int n = (int)L.nc;
+    L.d_rec = dalloc<float4>((size_t)4 * std::max(n, 1), "level control records");
+    k_level_records<<<cdiv(std::max(n, 1), 256), 256, 0, m->stream>>>(n, L.d_cell_ctrl, L.d_cdf, L.d_adf, L.d_rec);
+    RBFD_CUDA(cudaGetLastError());
+    m->stats.launches += 1;
 }
 
 }  // namespace
@@ -1292,6 +1311,11 @@ static bool newton_enabled() {
 void level_fine_grid(rbfd_mesh *m, Level &L) {
     if (L.f_cell_start || L.nc == 0) return;
     grid_over_controls(m, L, m->h_sbox, 0.5 * L.R, L.f_g0, L.f_h, L.f_gdim, L.f_cell_start, L.f_cell_ctrl);
+    const int n = (int)L.nc;
+    L.f_rec = dalloc<float4>((size_t)4 * n, "level control records (fine grid)");
+    k_level_records<<<cdiv(n, 256), 256, 0, m->stream>>>(n, L.f_cell_ctrl, L.d_cdf, L.d_adf, L.f_rec);
+    RBFD_CUDA(cudaGetLastError());
+    m->stats.launches += 1;
 }
 
 void level_free(Level &L) {
@@ -1305,6 +1329,9 @@ void level_free(Level &L) {
     dfree(L.f_cell_start);
     dfree(L.f_cell_ctrl);
     L.f_cell_start = L.f_cell_ctrl = nullptr;
+    dfree(L.d_rec);
+    dfree(L.f_rec);
+    L.d_rec = L.f_rec = nullptr;
     dfree(L.d_Gs);
     dfree(L.d_Gts);
     dfree(L.d_cids);

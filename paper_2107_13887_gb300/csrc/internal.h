@@ -120,6 +120,10 @@ struct Level {
     int ncell = 0;
     uint32_t *d_cell_start = nullptr;  // [ncell + 1]
     uint32_t *d_cell_ctrl = nullptr;   // [nc] control ids ordered by cell
+    // the controls' double-float records in that cell order, 64 bytes each
+    // (coordinates hi, lo; weights (ax, ay) hi/lo pairs, az pair): the volume
+    // sweep stages a cell's controls with one bulk copy
+    float4 *d_rec = nullptr;
     // kept for a warm start of the next time step (rbfd_greedy_warm): the
     // level's inverse factor G = L^{-1} and its transpose, packed n x n rows,
     // and the controls' sorted positions
@@ -130,6 +134,7 @@ struct Level {
     double f_h = 0;
     int3 f_gdim{0, 0, 0};
     uint32_t *f_cell_start = nullptr, *f_cell_ctrl = nullptr;
+    float4 *f_rec = nullptr;
 };
 
 // Optional per-kernel-class timing with CUDA events on the mesh's stream.

@@ -8,9 +8,10 @@ DRAM traffic matters), the same kernels as the benchmark's workloads:
     python -m paper_2107_13887_gb300.profile_cases worklist   # k_vol_worklist over four uneven wings
 
 persist:  the swept wing of the benchmark at 1/15 of its surface (100 x 40 =
-          4,000 points, 400k volume points), its three levels to 1e-5: the
-          Newton start, the persistent list sweep (levels 1 and 2) and the
-          volume update.
+          4,000 points, 400k volume points), its three levels to 1e-5 in the
+          persistent list sweep alone (engine 2: at this size the Newton
+          start would take every level; on the 60k wing it hands levels 1
+          and 2 to this launch), then the volume update.
 worklist: the four-wing family at 1/25 of its surfaces (1.2k to 10k points)
           and 60 layers (72k to 600k volume points each, 1.2M in all), two
           levels to 1e-3, the volume updates of all four in one work-list
@@ -27,7 +28,7 @@ from . import rbfd, synth
 
 def run_persist():
     c = synth.wing_case(100, 40, 100, displacement="ridge", seed=0, R=(1.5, 0.4, 0.1), eps=1e-5, D=1.0, k=4.0)
-    m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps)
+    m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, engine=2)
     m.greedy()
     out = m.deform(c.xyz_v, c.d_v, c.D, c.k)
     st = m.stats()
