@@ -1307,10 +1307,17 @@ int worklist_max_ctas_per_sm(int dim, int basis) {
 
 }  // namespace
 
-void deform_worklist(rbfd_mesh **ms, int n, const int64_t *n_v, const float *const *xyz_v,
+void deform_worklist(rbfd_mesh **ms, int n, const int64_t *n_v_in, const float *const *xyz_v,
                      const float *const *d_v, const double *D, const double *k, float *const *out,
-                     rbfd_worklist_tune *tune) {
+                     rbfd_worklist_tune *tune, bool registered) {
     NvtxRange nvtx("rbfd work-list volume update");
+    // registered volumes (rbfd_set_volume): already packed and Morton-sorted
+    std::vector<int64_t> n_v_reg;
+    if (registered) {
+        for (int i = 0; i < n; ++i) n_v_reg.push_back(ms[i]->vreg_n);
+        n_v_in = n_v_reg.data();
+    }
+    const int64_t *n_v = n_v_in;
     if (n < 1 || n > 16) fail(RBFD_EINVAL, "rbfd_deform_worklist: 1 to 16 meshes");
     const int dim = ms[0]->dim, basis = ms[0]->opt.basis, dev = ms[0]->device;
     int n_entries = 0;
@@ -1320,7 +1327,7 @@ void deform_worklist(rbfd_mesh **ms, int n, const int64_t *n_v, const float *con
         if (m->opt.precision == RBFD_FP64 || m->dim != dim || m->opt.basis != basis || m->device != dev)
             fail(RBFD_EINVAL, "rbfd_deform_worklist: the meshes must all be mixed precision, of one dimension, "
                               "basis and device (mesh " + std::to_string(i) + " is not)");
-        if (n_v[i] < 0 || n_v[i] >= (int64_t)1 << 31 || (n_v[i] > 0 && (!xyz_v[i] || !out[i])))
+        if (n_v[i] < 0 || n_v[i] >= (int64_t)1 << 31 || (n_v[i] > 0 && ((!registered && !xyz_v[i]) || !out[i])))
             fail(RBFD_EINVAL, "rbfd_deform_worklist: bad volume arrays of mesh " + std::to_string(i));
         if (!(D[i] >= 0.0) || !(k[i] >= 0.0) || (D[i] == 0.0 && k[i] == 0.0))
             fail(RBFD_EINVAL, "rbfd_deform_worklist: D and k must be >= 0 and not both 0");
@@ -1350,7 +1357,22 @@ void deform_worklist(rbfd_mesh **ms, int n, const int64_t *n_v, const float *con
             Dmax = std::max(Dmax, Dl[i][l]);
         }
         RBFD_CUDA(cudaEventRecord(m->ev0, st));
-        const VolumeIO io = volume_io(m, n_v[i], xyz_v[i], d_v ? d_v[i] : nullptr, out[i], false, st);
+        VolumeIO io{nullptr, nullptr, out[i]};
+        if (registered) {
+            if (!m->opt.inputs_on_device && n_v[i] > 0) {  // the output through the staging buffer
+                const size_t need = sizeof(float) * (size_t)n_v[i] * dim;
+                if (need > m->vio_bytes) {
+                    dfree(m->d_vio);
+                    m->d_vio = nullptr;
+                    m->vio_bytes = 0;
+                    m->d_vio = dmalloc(need, "volume output staging");
+                    m->vio_bytes = need;
+                }
+                io.out = m->d_vio;
+            }
+        } else {
+            io = volume_io(m, n_v[i], xyz_v[i], d_v ? d_v[i] : nullptr, out[i], false, st);
+        }
         dout[i] = io.out;
         const int64_t nv = n_v[i];
         if (nv > 0) {
@@ -1366,10 +1388,12 @@ void deform_worklist(rbfd_mesh **ms, int n, const int64_t *n_v, const float *con
             if (!m->d_wl_cnt) m->d_wl_cnt = dalloc<uint32_t>(kWLMax, "work-list list lengths");
             RBFD_CUDA(cudaMemsetAsync(m->d_wl_cnt, 0, sizeof(uint32_t) * kWLMax, st));
             double4 *vin = reinterpret_cast<double4 *>(m->d_vin);
-            double4 *vpos = reinterpret_cast<double4 *>(m->d_vpos);
-            k_vol_pack<<<cdiv(nv, 256), 256, 0, st>>>(io.x, io.d, nv, dim, 0, vin);
-            morton_order(m, nv, vin, vpos, m->d_vorig, st, m->d_red, m->d_bbox, m->sort);
-            if (!io.d && Dmax > 0.0) wall_distance_sorted(m, nv, vpos, Dmax, nullptr);
+            double4 *vpos = registered ? m->d_vreg : reinterpret_cast<double4 *>(m->d_vpos);
+            if (!registered) {
+                k_vol_pack<<<cdiv(nv, 256), 256, 0, st>>>(io.x, io.d, nv, dim, 0, vin);
+                morton_order(m, nv, vin, vpos, m->d_vorig, st, m->d_red, m->d_bbox, m->sort);
+                if (!io.d && Dmax > 0.0) wall_distance_sorted(m, nv, vpos, Dmax, nullptr);
+            }
             deform_acc_init(m, nv, vpos, false, st);
             for (int l = 0; l < L; ++l) {
                 if (!(Dl[i][l] > 0.0)) continue;
@@ -1538,8 +1562,8 @@ void deform_worklist(rbfd_mesh **ms, int n, const int64_t *n_v, const float *con
         RBFD_CUDA(cudaStreamWaitEvent(st, t1, 0));
         const int64_t nv = n_v[i];
         if (nv > 0) {
-            k_scatter_out_df<<<cdiv(nv, 256), 256, 0, st>>>(m->d_vacc, m->d_vorig, nv, dim,
-                                                           static_cast<float *>(dout[i]));
+            k_scatter_out_df<<<cdiv(nv, 256), 256, 0, st>>>(m->d_vacc, registered ? m->d_vreg_orig : m->d_vorig,
+                                                           nv, dim, static_cast<float *>(dout[i]));
             RBFD_CUDA(cudaGetLastError());
             m->stats.launches += 1;
             if (!m->opt.inputs_on_device)

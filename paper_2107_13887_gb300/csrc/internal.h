@@ -331,9 +331,11 @@ void level_fetch(rbfd_mesh *m, Level &L);
 void deform_run(rbfd_mesh *m, int64_t n_v, const void *xyz_v, const void *d_v, bool f64, double D, double k,
                 void *out);
 // rbfd_deform_worklist: the volume updates of n meshes in one work-list launch
+// registered = true: every mesh's registered volume (rbfd_set_volume; n_v,
+// xyz_v and d_v are then ignored), the serving loop's fused volume stage
 void deform_worklist(rbfd_mesh **ms, int n, const int64_t *n_v, const float *const *xyz_v,
                      const float *const *d_v, const double *D, const double *k, float *const *out,
-                     rbfd_worklist_tune *tune);
+                     rbfd_worklist_tune *tune, bool registered = false);
 // Stage a volume for the next deform_run with the same arguments: copies,
 // packing and the Morton order of every point, on a second stream that
 // starts after the work queued so far on the mesh's stream (the greedy can

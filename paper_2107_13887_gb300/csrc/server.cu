@@ -44,6 +44,16 @@ struct MeshSpec {
     int instances = 0;
 };
 
+// A request's volume update waiting for the fused launch.
+struct VolumeJob {
+    rbfd_mesh *inst = nullptr;
+    double D = 0, k = 0;
+    float *out = nullptr;
+    int status = RBFD_OK;
+    std::string msg;
+    bool done = false;
+};
+
 struct Request {
     int mesh = -1;
     std::vector<double> dS;
@@ -69,6 +79,13 @@ struct rbfd_server {
     int running = 0;
     bool shutdown = false;
     std::vector<std::thread> workers;
+    // the volume stage: requests whose greedy is done queue their volume
+    // updates here; one worker at a time runs every queued update of one
+    // dimension and basis in one work-list launch
+    std::mutex vmu;
+    std::condition_variable vcv;
+    std::deque<VolumeJob *> vq;
+    bool vbusy = false;
 };
 
 namespace rbfd {
@@ -89,6 +106,81 @@ size_t mesh_footprint(int dim, int64_t n_s, int64_t n_v, int64_t cap) {
     // Newton-basis values V: n_s doubles per column, at most kNewtonCols columns and 1 GB
     b += std::min<size_t>((size_t)n_s * 8 * std::min<int64_t>(cap, kNewtonCols), (size_t)1 << 30);
     return b + (64ull << 20);                       // small buffers and pool rounding
+}
+
+// The volume update of a request whose greedy is done: queued for the fused
+// launch; the worker that finds no launch running takes every queued update
+// of the oldest one's dimension and basis (up to 16 meshes), runs them in one
+// work-list launch on the registered volumes (cells of size R_l: the same
+// sums as the request's own rbfd_deform_volume, bit for bit) and wakes their
+// workers; the others wait.  Requests in FP64 (or C4 / C6) run theirs alone.
+static void volume_stage(rbfd_server *S, rbfd_mesh *inst, double D, double k, float *out) {
+    if (inst->opt.precision == RBFD_FP64) {
+        deform_registered(inst, D, k, out);
+        return;
+    }
+    VolumeJob job;
+    job.inst = inst;
+    job.D = D;
+    job.k = k;
+    job.out = out;
+    std::unique_lock<std::mutex> lk(S->vmu);
+    S->vq.push_back(&job);
+    for (;;) {
+        if (job.done) break;
+        if (S->vbusy) {
+            S->vcv.wait(lk);
+            continue;
+        }
+        S->vbusy = true;
+        std::vector<VolumeJob *> batch;
+        const int dim = S->vq.front()->inst->dim, basis = S->vq.front()->inst->opt.basis;
+        for (auto it = S->vq.begin(); it != S->vq.end() && batch.size() < 16;) {
+            if ((*it)->inst->dim == dim && (*it)->inst->opt.basis == basis) {
+                batch.push_back(*it);
+                it = S->vq.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        lk.unlock();
+        int status = RBFD_OK;
+        std::string msg;
+        try {
+            NvtxRange nvtx("rbfd fused volume stage");
+            const int n = (int)batch.size();
+            std::vector<rbfd_mesh *> ms(n);
+            std::vector<double> Dv(n), kv(n);
+            std::vector<float *> outs(n);
+            for (int i = 0; i < n; ++i) {
+                ms[i] = batch[i]->inst;
+                Dv[i] = batch[i]->D;
+                kv[i] = batch[i]->k;
+                outs[i] = batch[i]->out;
+            }
+            rbfd_worklist_tune t{};
+            t.autotune = 0;
+            t.ctas_per_sm = 8;
+            t.item_blocks = 1;
+            for (int i = 0; i < 16; ++i) t.cell_div[i] = 1;
+            deform_worklist(ms.data(), n, nullptr, nullptr, nullptr, Dv.data(), kv.data(), outs.data(), &t, true);
+        } catch (const Error &e) {
+            status = e.status;
+            msg = e.msg;
+        } catch (...) {
+            status = RBFD_ECUDA;
+            msg = "server: unexpected internal error in the volume stage";
+        }
+        lk.lock();
+        for (VolumeJob *j : batch) {
+            j->status = status;
+            j->msg = msg;
+            j->done = true;
+        }
+        S->vbusy = false;
+        S->vcv.notify_all();
+    }
+    if (job.status != RBFD_OK) fail(job.status, job.msg);
 }
 
 // Run one admitted request.  inst is an idle resident instance of its mesh,
@@ -135,7 +227,7 @@ static void run_request(rbfd_server *S, uint64_t ticket, rbfd_mesh *inst) {
             status = RBFD_ENOTCONV;  // results valid
             msg = e.msg;
         }
-        deform_registered(inst, M.D, M.k, out);
+        volume_stage(S, inst, M.D, M.k, out);
     } catch (const Error &e) {
         status = e.status;
         msg = e.msg;
