@@ -102,6 +102,7 @@ class rbfd_server_options(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("mem_budget_bytes", ctypes.c_int64),
         ("max_queue", ctypes.c_int64),
+        ("fuse_volume", ctypes.c_int),
     ]
 
 
@@ -671,7 +672,7 @@ class Server:
     """The request loop of ``rbfd_server_*``: register meshes, submit
     displacements (host numpy arrays), poll / wait for the volume results."""
 
-    def __init__(self, slots=4, precision=MIXED, mem_budget_bytes=0, max_queue=4096):
+    def __init__(self, slots=4, precision=MIXED, mem_budget_bytes=0, max_queue=4096, fuse_volume=False):
         lib = load()
         self._lib = lib
         o = rbfd_server_options()
@@ -680,6 +681,7 @@ class Server:
         o.precision = int(precision)
         o.mem_budget_bytes = int(mem_budget_bytes)
         o.max_queue = int(max_queue)
+        o.fuse_volume = 1 if fuse_volume else 0
         h = ctypes.c_void_p()
         _check(lib.rbfd_server_create(ctypes.byref(h), ctypes.byref(o)))
         self.h = h

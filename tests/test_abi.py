@@ -73,11 +73,16 @@ def test_struct_layout_matches_header(tmp_path):
         " offsetof(rbfd_stats, persist_phase_ms), offsetof(rbfd_stats, wall_pairs_exact));\n"
         'printf("%zu %zu\\n", sizeof(rbfd_quality), offsetof(rbfd_quality, hist));\n'
         'printf("%zu %zu %zu\\n", sizeof(rbfd_job), offsetof(rbfd_job, opt), offsetof(rbfd_job, out));\n'
+        'printf("%zu %zu %zu\\n", sizeof(rbfd_worklist_tune), offsetof(rbfd_worklist_tune, launch_ms),'
+        " offsetof(rbfd_worklist_tune, items));\n"
+        'printf("%zu %zu %zu\\n", sizeof(rbfd_server_options), offsetof(rbfd_server_options, max_queue),'
+        " offsetof(rbfd_server_options, fuse_volume));\n"
+        'printf("%zu %zu\\n", offsetof(rbfd_stats, newton_pairs_useful), offsetof(rbfd_stats, eq12_pairs));\n'
         "return 0;}\n"
     )
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
-    a, b, c, d = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:4]
+    a, b, c, d, e, f, g = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:7]
     so, onc, ost, ori = map(int, a.split())
     ss, ocr, ovp, owp = map(int, b.split())
     assert so == ctypes.sizeof(rbfd.rbfd_options)
@@ -93,6 +98,14 @@ def test_struct_layout_matches_header(tmp_path):
     sj, oo, ou = map(int, d.split())
     assert sj == ctypes.sizeof(rbfd.rbfd_job)
     assert oo == rbfd.rbfd_job.opt.offset and ou == rbfd.rbfd_job.out.offset
+    st, ol, oi = map(int, e.split())
+    assert st == ctypes.sizeof(rbfd.rbfd_worklist_tune)
+    assert ol == rbfd.rbfd_worklist_tune.launch_ms.offset and oi == rbfd.rbfd_worklist_tune.items.offset
+    sso, omq, ofv = map(int, f.split())
+    assert sso == ctypes.sizeof(rbfd.rbfd_server_options)
+    assert omq == rbfd.rbfd_server_options.max_queue.offset and ofv == rbfd.rbfd_server_options.fuse_volume.offset
+    onp, oeq = map(int, g.split())
+    assert onp == rbfd.rbfd_stats.newton_pairs_useful.offset and oeq == rbfd.rbfd_stats.eq12_pairs.offset
 
 
 def test_argument_checks_before_any_device_work(lib):

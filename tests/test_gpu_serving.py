@@ -108,16 +108,16 @@ def test_server_rejects_bad_requests():
 
 
 def test_fused_volume_stage_same_bits_alone_and_in_the_mix():
-    """Four slots: the volume updates of requests whose greedy is done run
-    in one work-list launch (cells of size R_l: the same sums as a request
-    alone).  One slot: every request alone.  Each mesh's requests run in order
+    """Four slots with fuse_volume: the volume updates of requests whose
+    greedy is done run in one work-list launch (cells of size R_l: the same
+    sums as a request alone).  One slot: every request alone.  Each mesh's requests run in order
     on its own resident instance (warm starts) in both servers, so every
     result must agree bit for bit."""
     cases = [synth.wing_case(40, 15, 6, displacement="ridge", seed=s, R=(1.5, 0.4), eps=1e-3, D=1.0, k=4.0)
              for s in (3, 4, 5)] + [_airfoil(seed=2), _airfoil(seed=6)]
     results = []
     for slots in (4, 1):
-        srv = rbfd.Server(slots=slots)
+        srv = rbfd.Server(slots=slots, fuse_volume=True)
         ids = [srv.add_mesh(c.xyz_s, c.xyz_v, c.d_v, c.R, c.eps, c.D, c.k) for c in cases]
         tickets = []
         for t in range(4):
