@@ -74,6 +74,9 @@ OPS_PER_PAIR_FP32 = {2: 13, 3: 16}
 # eta 7, phi 63, accumulate 2 x 27 -> 210; 3D -> 284
 OPS_PER_PAIR_DF = {2: 210, 3: 284}
 FP32_LANES_PER_SM = 128
+# FP64 multiply-adds per SM per clock on GB300 (the nominal 1.25 TFLOP/s over
+# 152 SMs at 2.07 GHz is about 4 flops, two FMAs, per SM per clock)
+FP64_FMA_PER_SM_CLK = 2
 CPU_BASELINE_S = 15.0  # about this much oracle time behind the cpu_baseline figure
 
 # DRAM bytes (read + written) per launch from an ncu capture, each with the
@@ -318,6 +321,16 @@ def roofline_of(stats, dim, sms, sm_clock_hz, precision_mixed):
         traffic = cap[0]
     phases = [round(sum(s["persist_phase_ms"][q] for s in stats), 3) for q in range(8)]
     vol_ms, vol_pairs = kinds["vol"][0], kinds["vol"][2]
+    # the persistent launch keeps two pipes busy: the double-float sweep on
+    # the FP32 pipe and the rows of G in FP64 (k (k + 1) / 2 multiply-adds
+    # for the step adding control k).  Its two-pipe fraction is the time each
+    # part needs at its own pipe's peak, summed, over the launch's time.
+    p_ms, _, p_pairs = kinds["persist"]
+    fp64_fma_peak = sms * FP64_FMA_PER_SM_CLK * sm_clock_hz
+    grow_fma = tot("persist_grow_fma")
+    frac_pipes = None
+    if precision_mixed and p_ms > 0:
+        frac_pipes = (p_pairs * OPS_PER_PAIR_DF[dim] / peak + grow_fma / fp64_fma_peak) / (p_ms / 1e3)
     return {
         "bound": "alu", "kernel": names[dom],
         "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
@@ -333,6 +346,9 @@ def roofline_of(stats, dim, sms, sm_clock_hz, precision_mixed):
         # block 0 of the persistent launch, summed over levels and steps:
         # [2p] work of phase p (sweep, argmax + phi column, G phi, G row), [2p+1] wait at its barrier
         "persist_phase_ms": phases,
+        "persist_pipes": {"grow_fp64_fma": int(grow_fma),
+                          "fp64_fma_peak_per_s": fp64_fma_peak,
+                          "frac": round(frac_pipes, 5) if frac_pipes is not None else None},
         "vol_sweep": {"ms": round(vol_ms, 3), "pairs_useful": int(vol_pairs),
                       "frac": round(fr(vol_pairs, vol_ms, OPS_PER_PAIR_FP32[dim]), 5),
                       "frac_df_ops": round(fr(vol_pairs, vol_ms, OPS_PER_PAIR_DF[dim]), 5) if precision_mixed

@@ -69,6 +69,13 @@ typedef struct rbfd_options {
                               is cheaper; 2 = the persistent list sweep only; 1 = separate
                               launches for every step */
     int grid_ctas;         /* blocks of the persistent launch (0 = chosen from the mesh size) */
+    int prune;             /* 1 (default): the persistent list sweep skips a point block while
+                              a bound shows that none of its points can hold the step's
+                              argmax (the bound: the block's max |E| at its last sweep plus
+                              |w_n| times the sum of |G row n| over its control list, summed
+                              over the steps since, plus the sweep's rounding).  The picks
+                              and the stop test are those of a full sweep; fewer pairs are
+                              evaluated.  0: every block every step */
 } rbfd_options;
 
 typedef struct rbfd_mesh rbfd_mesh;
@@ -174,11 +181,21 @@ typedef struct rbfd_stats {
        where a list sweep of the same step evaluates the nonzeros of Eq. 12:
        eq12_pairs counts those for every greedy step and the confirm sweeps,
        whichever engine ran (the method's own pair count, as Section 3 states
-       it); pairs_useful = sweep_pairs_useful + vol_pairs_useful +
+       it), less the point blocks a pruned sweep skipped (opt.prune; those
+       are counted in sweep_pairs_skipped); pairs_useful = sweep_pairs_useful + vol_pairs_useful +
        newton_pairs_useful is what was evaluated */
     int64_t newton_pairs_useful;
     int64_t newton_pairs_formed;
     int64_t eq12_pairs;
+    /* FP64 multiply-adds the persistent list sweep spent on the rows of the
+       inverse factor G in the last rbfd_greedy (k (k + 1) / 2 for the step that
+       adds control k) */
+    int64_t persist_grow_fma;
+    /* pairs (block points x list length, as sweep_pairs_visited counts
+       them) and point-block steps the pruned list sweep skipped, since
+       creation */
+    int64_t sweep_pairs_skipped;
+    int64_t sweep_blocks_skipped;
 } rbfd_stats;
 
 int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st);

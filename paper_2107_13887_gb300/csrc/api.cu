@@ -422,6 +422,7 @@ void rbfd_options_default(rbfd_options *opt) {
     opt->profile = 0;
     opt->engine = 0;
     opt->grid_ctas = 0;
+    opt->prune = 1;
 }
 
 int rbfd_create(rbfd_mesh **out, int dim, int64_t n_s, const double *xyz_s, const double *dS, int n_levels,
@@ -449,6 +450,7 @@ int rbfd_create(rbfd_mesh **out, int dim, int64_t n_s, const double *xyz_s, cons
         if (o.engine < 0 || o.engine > 2) rbfd::fail(RBFD_EINVAL, "rbfd_create: engine must be 0, 1 or 2");
         if (o.grid_ctas < 0 || o.grid_ctas > rbfd::kMaxPersistCTAs)
             rbfd::fail(RBFD_EINVAL, "rbfd_create: grid_ctas must be in [0, 2048]");
+        if (o.prune != 0 && o.prune != 1) rbfd::fail(RBFD_EINVAL, "rbfd_create: prune must be 0 or 1");
         if (!(eps > 0.0) || (!o.eps_absolute && !(eps < 1.0)) || !std::isfinite(eps))
             rbfd::fail(RBFD_EINVAL, "rbfd_create: eps must be in (0, 1) (or > 0 when absolute)");
         for (int l = 0; l < n_levels; ++l)
@@ -587,6 +589,8 @@ int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st) {
         st->newton_pairs_useful = (int64_t)pr[8];
         st->newton_pairs_formed = (int64_t)pr[9];
         st->eq12_pairs = (int64_t)(pr[0] + pr[10]);
+        st->sweep_pairs_skipped = (int64_t)pr[11];
+        st->sweep_blocks_skipped = (int64_t)pr[12];
         st->pairs_useful = (int64_t)(pr[0] + pr[2] + pr[8]);
         st->pairs_visited = (int64_t)(pr[1] + pr[3] + pr[9]);
         st->sweep_ms = m->prof.ms[rbfd::kProfSweep];

@@ -1179,6 +1179,11 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     rest.add(m->d_part, (size_t)m->n_chunk_max * n);
     rest.add(m->d_pb_key, std::max(m->n_pb, 1024));
     rest.add(m->d_pb_idx, std::max(m->n_pb, 1024));
+    if (m->opt.prune && m->n_pb <= kPfxMax) {
+        rest.add(m->d_bnd, (size_t)6 * m->n_pb);
+        rest.add(m->d_rev, (size_t)(cap + 1) * m->n_pb);
+        rest.add(m->d_rev_cnt, cap + 1);
+    }
     rest.add(m->d_pred, (size_t)4 * kMaxPersistCTAs);
     rest.add(m->d_nz_k, cap + 1);
     rest.add(m->d_nz_v, cap + 1);
@@ -1412,6 +1417,7 @@ void greedy_run(rbfd_mesh *m, bool wait, bool warm) {
         t_host = t;
     };
     m->stats.newton_steps = 0;
+    m->stats.persist_grow_fma = 0;
     m->stats.refine_sweeps = 0;
     m->stats.confirm_resumes = 0;
     RBFD_CUDA(cudaEventRecord(m->ev_g0, st));
@@ -1611,6 +1617,12 @@ void greedy_run(rbfd_mesh *m, bool wait, bool warm) {
                     fail(RBFD_ESINGULAR, "Phi_cc is not positive definite at level " + std::to_string(l) +
                                              " (coincident or near-coincident controls)");
                 if (!m->h_st->stop) fail(RBFD_ECUDA, "persistent greedy ended without a stop decision");
+                {
+                    // the launch's FP64 multiply-adds for the rows of G: a step
+                    // that adds control k forms k (k + 1) / 2 of them
+                    auto tri = [](int64_t q) { return q > 0 ? (q - 1) * q * (q + 1) / 6 : 0; };
+                    m->stats.persist_grow_fma += tri(m->h_st->n) - tri(n);
+                }
                 n = m->h_st->n;
                 stopped = true;
             }

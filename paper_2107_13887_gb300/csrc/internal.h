@@ -209,10 +209,18 @@ struct rbfd_mesh {
     unsigned int *d_pb_done = nullptr;
     double *d_pb_key = nullptr;
     int *d_pb_idx = nullptr;
+    // pruned list sweep (meshes of at most kPfxMax point blocks): per step
+    // parity and point block the block's max |E| at its last sweep, the bound
+    // accumulated since, the sum of |alpha| over its list ([2][3][n_pb]);
+    // the point blocks listing each control ([cap + 1][n_pb], counts [cap + 1])
+    double *d_bnd = nullptr;
+    uint32_t *d_rev = nullptr;
+    uint32_t *d_rev_cnt = nullptr;
     unsigned long long *d_pairs = nullptr;  // [16]: surface sweep useful, visited; volume useful, visited;
                                             //     wall distance search, exact pass; Newton basis terms;
                                             //     deform points; Newton phi values within R, all formed;
-                                            //     Eq. 12 nonzeros of the Newton steps
+                                            //     Eq. 12 nonzeros of the Newton steps; pairs and block
+                                            //     steps the pruned sweep skipped
     rbfd::GreedyState *d_st = nullptr;
     rbfd::GreedyState *h_st = nullptr;  // pinned
     rbfd::GridBarrier *h_bar = nullptr; // pinned
@@ -305,6 +313,7 @@ struct rbfd_mesh {
 
 namespace rbfd {
 constexpr int kMaxPersistCTAs = 2048;
+constexpr int kPfxMax = 2048;  // point blocks up to which the persistent sweep balances its items (and prunes)
 constexpr int kNewtonCols = 4096;  // most controls a Newton-basis launch carries (y staged in shared memory)
 int newton_columns(rbfd_mesh *m);
 void newton_reserve(rbfd_mesh *m);

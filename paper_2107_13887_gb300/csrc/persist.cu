@@ -41,7 +41,6 @@ namespace rbfd {
 namespace {
 
 constexpr int kT = 128;        // threads per block (4 warps)
-constexpr int kPfxMax = 2048;  // point blocks up to which the sweep's items are balanced (prefix in shared memory)
 
 
 struct PersistArgs {
@@ -73,14 +72,41 @@ struct PersistArgs {
     unsigned long long *item_ctr;  // the sweep's item counter (zero at launch)
     int pfx_max;                   // balanced sweep items up to this many point blocks (<= kPfxMax)
     int chunk_target;              // controls per sweep item the chunking aims at
+    // pruned sweep (balanced items only): bnd[(parity * 3 + q) * n_pb + b] with
+    // q = 0 the block's max |E| over unselected points at its last sweep, 1
+    // the bound on how far any |E| of the block has moved since, 2 the sum of
+    // |alpha| (1-norm) over its list then; rev[k * n_pb + i] the point blocks
+    // whose list holds control k (rev_cnt[k] of them); err_u the relative
+    // rounding of one operation of the sweep's arithmetic, with margin
+    int prune;
+    double err_u;
+    double *bnd;
+    uint32_t *rev, *rev_cnt;
 };
+
+// Bounds on what a sweep of point block b would find now, from its state at
+// its last sweep: hi >= the largest |E| it could compute for an unselected
+// point, lo <= the largest it would compute.  acc bounds the move of the
+// exact E of the stored weights since then; err bounds the rounding of the
+// sweep then and now (list terms and chunk sums, each of relative error
+// err_u on sums of at most A + 2 acc, the weights having moved by at most
+// sqrt(3) acc in the 1-norm), plus the subtraction from dS_l (|dS_l| <= S0).
+__device__ __forceinline__ void block_bounds(const PersistArgs &a, const double *bst, int b, int cnt, int nch,
+                                             double &lo, double &hi) {
+    const double M = __ldcg(bst + b);
+    const double acc = __ldcg(bst + a.n_pb + b) * (1.0 + 1e-12);
+    const double A = __ldcg(bst + 2 * a.n_pb + b);
+    const double err = (double)(cnt + 2 * nch + 16) * a.err_u * (A + 2.0 * acc + a.S0);
+    lo = M - acc - 2.0 * err;
+    hi = M + acc + 2.0 * err;
+}
 
 __device__ __forceinline__ uint32_t ldcg_u32(const uint32_t *p) { return __ldcg(p); }
 __device__ __forceinline__ double ldcg_d(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ float4 ldcg_f4(const float4 *p) { return __ldcg(p); }
 
 template <int DIM, int BASIS, int MODE>
-__global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
+__global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
     __shared__ double t64[6][kTile];
     __shared__ float t32[12][kTile];
     __shared__ double sk[32];
@@ -92,6 +118,8 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
     __shared__ unsigned char s_hits[4][kTile];
     __shared__ unsigned s_pfx[kPfxMax + 1];
     __shared__ int s_item;
+    __shared__ double sA[4];
+    __shared__ unsigned s_nsw;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned P = gridDim.x;
@@ -129,6 +157,21 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
     // with N items takes N + P fetches (every block's last fetch finds none),
     // so every block knows the step's base
     unsigned long long item_base = 0;
+    const bool keep_bounds = a.prune && a.n_pb <= a.pfx_max;
+    if (keep_bounds) {
+        // the point blocks listing each control the level already has (the
+        // counts were zeroed before the launch); later controls are entered
+        // as they are listed
+        for (int t = blockIdx.x * 4 + warp; t < a.n_pb; t += P * 4) {
+            const int cnt = (int)ldcg_u32(&a.nb_cnt[t]);
+            for (int q = lane; q < cnt; q += 32) {
+                const uint32_t j = ldcg_u32(&a.nb_list[(size_t)t * a.cap + q]);
+                const uint32_t pos = atomicAdd(&a.rev_cnt[j], 1u);
+                a.rev[(size_t)j * a.n_pb + pos] = (uint32_t)t;
+            }
+        }
+        RBFD_SYNC(0)
+    }
     for (int guard = 0; guard <= a.cap; ++guard) {
         // ------------------------------------------------ phase 1: sweep (+ the step's decision)
         // every block list is cut into chunks of at most cl controls, cl set by
@@ -143,16 +186,64 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
         // chunk).  (Beyond kPfxMax point blocks: every (point block, chunk)
         // pair is an item, the unoccupied ones skipped.)
         const bool balanced = a.n_pb <= a.pfx_max;
+        // bounds of this step (written by the last) and of the next
+        const double *bcur = keep_bounds ? a.bnd + (size_t)((guard & 1) * 3) * a.n_pb : nullptr;
+        double *bnext = keep_bounds ? a.bnd + (size_t)(((guard & 1) ^ 1) * 3) * a.n_pb : nullptr;
+        const bool prune_now = keep_bounds && guard > 0;  // (the launch's first step sweeps every block)
         int n_items = a.n_pb * nch;
+        int n_swept = a.n_pb;
         if (balanced) {
             const int per = (a.n_pb + kT - 1) / kT;
             const int b0 = min(a.n_pb, tid * per), b1 = min(a.n_pb, b0 + per);
-            unsigned mine = 0;
+            // a block is skipped if even its upper bound stays below the
+            // largest lower bound: the block attaining that is swept and
+            // finds at least as much, so the argmax and the stop test are
+            // those of a full sweep
+            double LB = -INFINITY;
+            if (prune_now) {
+                double lmax = -INFINITY;
+                for (int b = b0; b < b1; ++b) {
+                    double lo, hi;
+                    block_bounds(a, bcur, b, (int)ldcg_u32(&a.nb_cnt[b]), nch, lo, hi);
+                    lmax = fmax(lmax, lo);
+                }
+                for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+                if (lane == 0) sk[warp] = lmax;
+                if (tid == 0) s_nsw = 0;
+                __syncthreads();
+                LB = fmax(fmax(sk[0], sk[1]), fmax(sk[2], sk[3]));
+                __syncthreads();
+            }
+            unsigned mine = 0, swept = 0;
+            unsigned long long skip_pairs = 0;
             for (int b = b0; b < b1; ++b) {
                 const int cb = (int)ldcg_u32(&a.nb_cnt[b]);
-                const unsigned ub = (unsigned)min(nch, max(1, (cb + cl - 1) / cl));
+                unsigned ub = (unsigned)min(nch, max(1, (cb + cl - 1) / cl));
+                if (prune_now) {
+                    double lo, hi;
+                    block_bounds(a, bcur, b, cb, nch, lo, hi);
+                    if (hi < LB) {
+                        ub = 0;
+                        if (blockIdx.x == 0) {  // the block's state carries over to the next step
+                            bnext[b] = __ldcg(bcur + b);
+                            bnext[a.n_pb + b] = __ldcg(bcur + a.n_pb + b);
+                            bnext[2 * a.n_pb + b] = __ldcg(bcur + 2 * a.n_pb + b);
+                            skip_pairs += (unsigned long long)min((int64_t)kPB, a.n_s - (int64_t)b * kPB) *
+                                          (unsigned long long)cb;
+                        }
+                    } else {
+                        ++swept;
+                    }
+                }
                 s_pfx[b] = ub;
                 mine += ub;
+            }
+            if (prune_now) {
+                if (swept) atomicAdd(&s_nsw, swept);
+                if (blockIdx.x == 0 && b1 > b0 && (b1 - b0) > (int)swept) {
+                    atomicAdd(&a.pairs[11], skip_pairs);
+                    atomicAdd(&a.pairs[12], (unsigned long long)((b1 - b0) - (int)swept));
+                }
             }
             unsigned tot;
             unsigned run = block_excl_scan_u32(mine, s_scan, &tot);
@@ -167,6 +258,7 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
             }
             __syncthreads();
             n_items = (int)tot;
+            if (prune_now) n_swept = (int)s_nsw;
         }
         // balanced: items taken from the counter as blocks come free (their
         // costs differ with the density of controls); the next index is
@@ -214,6 +306,7 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
                 }
             }
             unsigned useful = 0;
+            double abs_alpha = 0.0;  // |alpha| (1-norm) over the chunk's controls (pruning bound)
             float3 wlo, whi;
             if (MODE == 1) warp_box(valid, qx.hi, qy.hi, qz.hi, wlo, whi);
             const float R2m = (float)(1.002 * a.R) * (float)(1.002 * a.R);  // filter margin
@@ -222,6 +315,7 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
                 if (tid < m) {
                     const uint32_t j = ldcg_u32(&a.nb_list[(size_t)pb * a.cap + t0 + tid]);
                     const double4 c = ldcg_d4(&a.cx[j]), al = ldcg_d4(&a.alpha[j]);
+                    if (keep_bounds) abs_alpha += (fabs(al.x) + fabs(al.y)) + fabs(al.z);
                     if (MODE == 0) {
                         t64[0][tid] = c.x; t64[1][tid] = c.y; t64[2][tid] = c.z;
                         t64[3][tid] = al.x; t64[4][tid] = al.y; t64[5][tid] = al.z;
@@ -265,7 +359,14 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
                 acc64[1] = df_to_double(acc[1]);
                 acc64[2] = df_to_double(acc[2]);
             }
-            if (valid) a.part[(size_t)ch * a.n_s + p] = make_double4(acc64[0], acc64[1], acc64[2], 0.0);
+            double chunk_abs = 0.0;  // (thread 0: the chunk's |alpha| sum, in the w slot of its partial)
+            if (keep_bounds) {
+                abs_alpha = warp_sum_d(abs_alpha);
+                if (lane == 0) sA[warp] = abs_alpha;
+                __syncthreads();
+                if (tid == 0) chunk_abs = (sA[0] + sA[1]) + (sA[2] + sA[3]);
+            }
+            if (valid) a.part[(size_t)ch * a.n_s + p] = make_double4(acc64[0], acc64[1], acc64[2], chunk_abs);
             {
                 unsigned u = useful;
                 for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
@@ -281,12 +382,13 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
             // point block to finish then takes the step's decision
             __threadfence();
             __syncthreads();
-            if (tid == 0) s_last = atomicAdd(&a.pb_done[pb], 1u) == (unsigned)(used - 1);
+            if (tid == 0) s_last = atomicAdd(&a.pb_done[pb], 1u) == (unsigned)(used - 1);  // (used >= 1)
             __syncthreads();
             if (s_last) {
                 __threadfence();
                 double key = -1.0;
                 int orig = -1;
+                double s3 = 0.0;  // (thread 0: the list's |alpha| sum)
                 if (valid) {
                     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
                     int c = 0;
@@ -299,6 +401,7 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
                             s0 = __dadd_rn(s0, v[q].x);
                             s1 = __dadd_rn(s1, v[q].y);
                             s2 = __dadd_rn(s2, v[q].z);
+                            s3 += v[q].w;
                         }
                     }
                     for (; c < used; ++c) {
@@ -306,6 +409,7 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
                         s0 = __dadd_rn(s0, v.x);
                         s1 = __dadd_rn(s1, v.y);
                         s2 = __dadd_rn(s2, v.z);
+                        s3 += v.w;
                     }
                     const double4 cu = a.cur[p];
                     const double e0 = __dsub_rn(cu.x, s0), e1 = __dsub_rn(cu.y, s1);
@@ -323,8 +427,13 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
                     a.pb_key[pb] = key;
                     a.pb_idx[pb] = orig;
                     a.pb_done[pb] = 0;
+                    if (keep_bounds) {
+                        bnext[pb] = key > 0.0 ? sqrt(key) : 0.0;
+                        bnext[a.n_pb + pb] = 0.0;
+                        bnext[2 * a.n_pb + pb] = s3;
+                    }
                     __threadfence();
-                    s_lead = atomicAdd(&a.st->pb_done, 1u) == (unsigned)(a.n_pb - 1);
+                    s_lead = atomicAdd(&a.st->pb_done, 1u) == (unsigned)(n_swept - 1);
                 }
                 __syncthreads();
                 if (s_lead) {
@@ -464,8 +573,16 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
                     a.nb_list[(size_t)t * a.cap + k] = (uint32_t)n;
                     a.nb_cnt[t] = k + 1;
                     atomicMax(&a.st->max_cnt, (int)(k + 1));
+                    if (keep_bounds) {
+                        const uint32_t pos = atomicAdd(&a.rev_cnt[n], 1u);
+                        a.rev[(size_t)n * a.n_pb + pos] = (uint32_t)t;
+                    }
                 }
             }
+            // c_n's own block has lost the point its maximum was taken at:
+            // no lower bound from it until it is swept again (which its
+            // infinite bound forces)
+            if (keep_bounds && first_block) bnext[a.n_pb + c / kPB] = INFINITY;
         }
         double yy = 0, yw0 = 0, yw1 = 0, yw2 = 0;
         for (int j = blockIdx.x * 4 + warp; j < n; j += P * 4) {
@@ -547,8 +664,25 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
             a.w[n] = make_double4(wn0, wn1, wn2, 0.0);
             a.alpha[n] = make_double4(wn0 / l, wn1 / l, wn2 / l, 0.0);
         }
-        // g_k = -(sum_{j >= k} y_j G_jk) / l, one warp per k over row k of G^T
-        for (int k = blockIdx.x * 4 + warp; k < n; k += P * 4) {
+        // g_k = -(sum_{j >= k} y_j G_jk) / l, one warp per k over row k of G^T.
+        // Pruning: alpha_k moves by w_n g_k, so |E| moves by at most
+        // |w_n| |g_k| at the points within R of control k: that is added to
+        // the bound of every block listing k (k = n too, g_n = 1 / l)
+        // The k are dealt to the warps in rounds of P * 4, every other round
+        // in reverse order, so that every warp's rows add up to about the
+        // same length (row k has n - k entries)
+        const double wnorm = keep_bounds ? sqrt(wn0 * wn0 + wn1 * wn1 + wn2 * wn2) * (1.0 + 1e-12) : 0.0;
+        const int n_k = keep_bounds ? n + 1 : n, W = (int)P * 4, gw = blockIdx.x * 4 + warp;
+        for (int r = 0; r * W < n_k; ++r) {
+            const int k = r * W + ((r & 1) ? W - 1 - gw : gw);
+            if (k >= n_k) continue;
+            if (k == n) {  // (only with pruning)
+                const double inc = wnorm / l;
+                const int rc = (int)ldcg_u32(&a.rev_cnt[k]);
+                const uint32_t *rv = a.rev + (size_t)k * a.n_pb;
+                for (int q = lane; q < rc; q += 32) atomicAdd(&bnext[a.n_pb + ldcg_u32(rv + q)], inc);
+                continue;
+            }
             const double *trow = a.Gt + (size_t)k * a.cap;
             // eight row entries in flight per lane: the rows stream from HBM
             // at the FP64 pipe's rate only with that many loads outstanding
@@ -582,6 +716,12 @@ __global__ void __launch_bounds__(kT) k_greedy_persist(PersistArgs a) {
             }
             for (; j < n; j += 32) s0 = fma(ldcg_d(trow + j), ldcg_d(a.y + j), s0);
             const double t = warp_sum_d((s0 + s1) + (s2 + s3));
+            if (keep_bounds) {
+                const double inc = wnorm * fabs(t / l);
+                const int rc = (int)ldcg_u32(&a.rev_cnt[k]);
+                const uint32_t *rv = a.rev + (size_t)k * a.n_pb;
+                for (int q = lane; q < rc; q += 32) atomicAdd(&bnext[a.n_pb + ldcg_u32(rv + q)], inc);
+            }
             if (lane == 0) {
                 const double g = -t / l;
                 Grow[k] = g;
@@ -682,6 +822,14 @@ void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
     // ones cost fewer partial sums (RBFD_SWEEP_CHUNK sets it, 16 to 1024)
     a.chunk_target = 64;
     if (const char *v = std::getenv("RBFD_SWEEP_CHUNK")) a.chunk_target = std::max(16, std::min(1024, std::atoi(v)));
+    a.prune = (m->opt.prune && m->d_bnd && m->n_pb <= a.pfx_max) ? 1 : 0;
+    // relative rounding per operation: FP64 2^-53, double-float about 2^-44;
+    // a factor 16 of margin on each
+    a.err_u = m->opt.precision == RBFD_FP64 ? 0x1p-49 : 0x1p-40;
+    a.bnd = m->d_bnd;
+    a.rev = m->d_rev;
+    a.rev_cnt = m->d_rev_cnt;
+    if (a.prune) RBFD_CUDA(cudaMemsetAsync(a.rev_cnt, 0, sizeof(uint32_t) * (size_t)(m->cap + 1), m->stream));
     a.phase_ns = m->prof.on ? m->d_phase_ns : nullptr;
     a.item_ctr = reinterpret_cast<unsigned long long *>(&m->d_misc[10]);  // (8-byte aligned)
     RBFD_CUDA(cudaMemsetAsync(a.item_ctr, 0, sizeof(unsigned long long), m->stream));

@@ -97,7 +97,7 @@ size_t mesh_footprint(int dim, int64_t n_s, int64_t n_v, int64_t cap) {
     const int64_t nch = std::max<int64_t>(128, (608 + n_pb - 1) / n_pb);
     size_t b = 0;
     b += 16ull * cap * cap;                         // G and its transpose
-    b += 4ull * n_pb * cap;                         // block lists
+    b += 8ull * n_pb * cap;                         // block lists and their reverse (pruned sweep)
     b += (size_t)n_s * (4 * 32 + 2 * 16 + 16);      // sorted surface, targets, error, df coords, perms
     b += (size_t)nch * n_s * 32;                    // sweep partials
     b += (size_t)cap * (6 * 32 + 8 * 8) + 32ull * (cap / 256 + 2) * cap;

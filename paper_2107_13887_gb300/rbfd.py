@@ -42,6 +42,7 @@ class rbfd_options(ctypes.Structure):
         ("profile", ctypes.c_int),
         ("engine", ctypes.c_int),
         ("grid_ctas", ctypes.c_int),
+        ("prune", ctypes.c_int),
     ]
 
 
@@ -82,6 +83,9 @@ class rbfd_stats(ctypes.Structure):
         ("newton_pairs_useful", ctypes.c_int64),
         ("newton_pairs_formed", ctypes.c_int64),
         ("eq12_pairs", ctypes.c_int64),
+        ("persist_grow_fma", ctypes.c_int64),
+        ("sweep_pairs_skipped", ctypes.c_int64),
+        ("sweep_blocks_skipped", ctypes.c_int64),
     ]
 
 
@@ -260,7 +264,7 @@ def default_options() -> rbfd_options:
 
 
 def _create_args(xyz_s, dS, R, precision=MIXED, basis=2, first_point=0, nc_cap=0, stream=None,
-                 eps_absolute=False, refine_iters=3, profile=False, engine=0, grid_ctas=0):
+                 eps_absolute=False, refine_iters=3, profile=False, engine=0, grid_ctas=0, prune=True):
     """rbfd_create's arrays (FP64, contiguous) and options."""
     on_dev = _is_torch_cuda(xyz_s)
     if on_dev:
@@ -284,6 +288,7 @@ def _create_args(xyz_s, dS, R, precision=MIXED, basis=2, first_point=0, nc_cap=0
     o.profile = 1 if profile else 0
     o.engine = int(engine)
     o.grid_ctas = int(grid_ctas)
+    o.prune = 1 if prune else 0
     return xyz_s, dS, Rv, o
 
 
@@ -302,13 +307,13 @@ class Mesh:
     ``rbfd_destroy`` on ``close()`` / garbage collection."""
 
     def __init__(self, xyz_s, dS, R, eps, precision=MIXED, basis=2, first_point=0, nc_cap=0, stream=None,
-                 eps_absolute=False, refine_iters=3, profile=False, engine=0, grid_ctas=0):
+                 eps_absolute=False, refine_iters=3, profile=False, engine=0, grid_ctas=0, prune=True):
         lib = load()
         self._lib = lib
         xyz_s, dS, Rv, o = _create_args(xyz_s, dS, R, precision=precision, basis=basis, first_point=first_point,
                                         nc_cap=nc_cap, stream=stream, eps_absolute=eps_absolute,
                                         refine_iters=refine_iters, profile=profile, engine=engine,
-                                        grid_ctas=grid_ctas)
+                                        grid_ctas=grid_ctas, prune=prune)
         self._keep = (xyz_s, dS)
         self.n_s, self.dim = (int(x) for x in xyz_s.shape)
         self.on_device = bool(o.inputs_on_device)
@@ -642,7 +647,7 @@ def run_jobs(jobs, allow_not_converged: bool = True):
     keep = []
     for i, j in enumerate(jobs):
         opts = {key: j[key] for key in ("precision", "basis", "first_point", "nc_cap", "stream", "eps_absolute",
-                                        "refine_iters", "profile", "engine", "grid_ctas") if key in j}
+                                        "refine_iters", "profile", "engine", "grid_ctas", "prune") if key in j}
         xyz_s, dS, Rv, o = _create_args(j["xyz_s"], j["dS"], j["R"], **opts)
         keep.append((xyz_s, dS, Rv, o, j))
         a = arr[i]

@@ -78,11 +78,13 @@ def test_struct_layout_matches_header(tmp_path):
         'printf("%zu %zu %zu\\n", sizeof(rbfd_server_options), offsetof(rbfd_server_options, max_queue),'
         " offsetof(rbfd_server_options, fuse_volume));\n"
         'printf("%zu %zu\\n", offsetof(rbfd_stats, newton_pairs_useful), offsetof(rbfd_stats, eq12_pairs));\n'
+        'printf("%zu %zu %zu\\n", offsetof(rbfd_options, prune), offsetof(rbfd_stats, persist_grow_fma),'
+        " offsetof(rbfd_stats, sweep_blocks_skipped));\n"
         "return 0;}\n"
     )
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
-    a, b, c, d, e, f, g = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:7]
+    a, b, c, d, e, f, g, h = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:8]
     so, onc, ost, ori = map(int, a.split())
     ss, ocr, ovp, owp = map(int, b.split())
     assert so == ctypes.sizeof(rbfd.rbfd_options)
@@ -106,6 +108,9 @@ def test_struct_layout_matches_header(tmp_path):
     assert omq == rbfd.rbfd_server_options.max_queue.offset and ofv == rbfd.rbfd_server_options.fuse_volume.offset
     onp, oeq = map(int, g.split())
     assert onp == rbfd.rbfd_stats.newton_pairs_useful.offset and oeq == rbfd.rbfd_stats.eq12_pairs.offset
+    opr, ogf, obs = map(int, h.split())
+    assert opr == rbfd.rbfd_options.prune.offset
+    assert ogf == rbfd.rbfd_stats.persist_grow_fma.offset and obs == rbfd.rbfd_stats.sweep_blocks_skipped.offset
 
 
 def test_argument_checks_before_any_device_work(lib):
