@@ -69,13 +69,15 @@ typedef struct rbfd_options {
                               is cheaper; 2 = the persistent list sweep only; 1 = separate
                               launches for every step */
     int grid_ctas;         /* blocks of the persistent launch (0 = chosen from the mesh size) */
-    int prune;             /* 1 (default): the persistent list sweep skips a point block while
-                              a bound shows that none of its points can hold the step's
-                              argmax (the bound: the block's max |E| at its last sweep plus
-                              |w_n| times the sum of |G row n| over its control list, summed
-                              over the steps since, plus the sweep's rounding).  The picks
-                              and the stop test are those of a full sweep; fewer pairs are
-                              evaluated.  0: every block every step */
+    int prune;             /* 1 (default): the persistent list sweep skips a warp of 32
+                              points while a bound shows that none of them can hold the
+                              step's argmax (the bound: the warp's max |E| at its last sweep
+                              plus, for every step since, |w_n| times the sum over the
+                              controls of |G row n| phi(distance to the warp's box / R), plus
+                              the sweep's rounding).  The picks and the stop test are those
+                              of a full sweep; fewer pairs are evaluated.  Meshes of up to
+                              2,048 point blocks (262,144 surface points).  0: every point
+                              every step */
 } rbfd_options;
 
 typedef struct rbfd_mesh rbfd_mesh;
@@ -191,11 +193,11 @@ typedef struct rbfd_stats {
        inverse factor G in the last rbfd_greedy (k (k + 1) / 2 for the step that
        adds control k) */
     int64_t persist_grow_fma;
-    /* pairs (block points x list length, as sweep_pairs_visited counts
-       them) and point-block steps the pruned list sweep skipped, since
-       creation */
+    /* pairs (points x their block's list length, as sweep_pairs_visited
+       counts them) and steps of a warp of 32 points that the pruned list
+       sweep skipped, since creation */
     int64_t sweep_pairs_skipped;
-    int64_t sweep_blocks_skipped;
+    int64_t sweep_warps_skipped;
 } rbfd_stats;
 
 int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st);

@@ -590,7 +590,7 @@ int rbfd_get_stats(rbfd_mesh *m, rbfd_stats *st) {
         st->newton_pairs_formed = (int64_t)pr[9];
         st->eq12_pairs = (int64_t)(pr[0] + pr[10]);
         st->sweep_pairs_skipped = (int64_t)pr[11];
-        st->sweep_blocks_skipped = (int64_t)pr[12];
+        st->sweep_warps_skipped = (int64_t)pr[12];
         st->pairs_useful = (int64_t)(pr[0] + pr[2] + pr[8]);
         st->pairs_visited = (int64_t)(pr[1] + pr[3] + pr[9]);
         st->sweep_ms = m->prof.ms[rbfd::kProfSweep];

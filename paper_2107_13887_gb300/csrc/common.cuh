@@ -170,6 +170,28 @@ __device__ __forceinline__ df phi_df(df eta) {
     return df_mul(t8, q);
 }
 
+// An upper bound on phi(eta) of Table 1 from FP32 arithmetic: eta is taken
+// 2^-20 smaller (phi decreases on [0, 1]) and the value 2^-18 larger, more
+// than the rounding of the dozen FP32 operations (each within 2^-24).
+template <int BASIS>
+__device__ __forceinline__ float phi_f32_upper(float eta) {
+    eta = fmaxf(eta * (1.0f - 0x1p-20f), 0.0f);
+    if (!(eta < 1.0f)) return 0.0f;
+    const float t = 1.0f - eta, t2 = t * t;
+    float v;
+    if (BASIS == 0) {
+        v = t2;
+    } else if (BASIS == 2) {
+        v = (t2 * t2) * (4.0f * eta + 1.0f);
+    } else if (BASIS == 4) {
+        v = (t2 * t2 * t2) * ((35.0f / 3.0f) * eta * eta + 6.0f * eta + 1.0f);
+    } else {
+        const float t4 = t2 * t2;
+        v = (t4 * t4) * (((32.0f * eta + 25.0f) * eta + 8.0f) * eta + 1.0f);
+    }
+    return fminf(v * (1.0f + 0x1p-18f), 1.0f);
+}
+
 // One pair of the double-float evaluation: phi(|q - c| / R) for a point q and
 // a control c, both given relative to the same origin as (hi, lo) floats.
 // t32 holds the staged controls: rows 0..5 = x hi, x lo, y hi, y lo, z hi, z lo.
@@ -286,6 +308,37 @@ __device__ __forceinline__ void hits_accumulate_df(df qx, df qy, df qz, const fl
         acc[0] = df_add(acc[0], df_mul(f0, {t32[6][q0], t32[7][q0]}));
         acc[1] = df_add(acc[1], df_mul(f0, {t32[8][q0], t32[9][q0]}));
         if (DIM == 3) acc[2] = df_add(acc[2], df_mul(f0, {t32[10][q0], t32[11][q0]}));
+    }
+}
+
+// hits_accumulate_df that also sums phi |alpha|_1 in FP32 (row 12 of t32:
+// |alpha_x| + |alpha_y| + |alpha_z| rounded up), the scale of the sum's
+// rounding that the pruned sweep's bounds need.
+template <int DIM, int BASIS>
+__device__ __forceinline__ void hits_accumulate_df_abs(df qx, df qy, df qz, const float (*t32)[kTile],
+                                                       const unsigned char *hits, int cnt, df invR, df acc[3],
+                                                       unsigned &useful, float &sabs) {
+    int i = 0;
+    for (; i + 2 <= cnt; i += 2) {
+        const int q0 = hits[i], q1 = hits[i + 1];
+        const df f0 = pair_phi_df<DIM, BASIS>(qx, qy, qz, t32, q0, invR, useful);
+        const df f1 = pair_phi_df<DIM, BASIS>(qx, qy, qz, t32, q1, invR, useful);
+        acc[0] = df_add(acc[0], df_mul(f0, {t32[6][q0], t32[7][q0]}));
+        acc[1] = df_add(acc[1], df_mul(f0, {t32[8][q0], t32[9][q0]}));
+        if (DIM == 3) acc[2] = df_add(acc[2], df_mul(f0, {t32[10][q0], t32[11][q0]}));
+        acc[0] = df_add(acc[0], df_mul(f1, {t32[6][q1], t32[7][q1]}));
+        acc[1] = df_add(acc[1], df_mul(f1, {t32[8][q1], t32[9][q1]}));
+        if (DIM == 3) acc[2] = df_add(acc[2], df_mul(f1, {t32[10][q1], t32[11][q1]}));
+        sabs = fmaf(f0.hi, t32[12][q0], sabs);
+        sabs = fmaf(f1.hi, t32[12][q1], sabs);
+    }
+    if (i < cnt) {
+        const int q0 = hits[i];
+        const df f0 = pair_phi_df<DIM, BASIS>(qx, qy, qz, t32, q0, invR, useful);
+        acc[0] = df_add(acc[0], df_mul(f0, {t32[6][q0], t32[7][q0]}));
+        acc[1] = df_add(acc[1], df_mul(f0, {t32[8][q0], t32[9][q0]}));
+        if (DIM == 3) acc[2] = df_add(acc[2], df_mul(f0, {t32[10][q0], t32[11][q0]}));
+        sabs = fmaf(f0.hi, t32[12][q0], sabs);
     }
 }
 

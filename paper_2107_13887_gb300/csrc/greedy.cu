@@ -111,7 +111,7 @@ __global__ void k_gather_sorted(const uint32_t *__restrict__ perm, int64_t n, co
 // double-float (hi, lo) pairs for the mixed-precision sweep.
 __global__ void k_point_blocks(const double4 *__restrict__ xs, int64_t n, double4 *__restrict__ lo_out,
                                double4 *__restrict__ hi_out, double4 *__restrict__ org_out,
-                               float4 *__restrict__ xhi, float4 *__restrict__ xlo) {
+                               float4 *__restrict__ xhi, float4 *__restrict__ xlo, float4 *__restrict__ wbox) {
     __shared__ double s[6][kPB / 32];
     int64_t i = (int64_t)blockIdx.x * kPB + threadIdx.x;
     bool valid = i < n;
@@ -129,6 +129,11 @@ __global__ void k_point_blocks(const double4 *__restrict__ xs, int64_t n, double
             s[k][w] = lo[k];
             s[3 + k][w] = hi[k];
         }
+    if (wbox && lane == 0) {  // each warp's box in FP32, rounded outward (empty for a warp with no point)
+        const size_t ww = (size_t)blockIdx.x * (kPB / 32) + w;
+        wbox[2 * ww] = make_float4(__double2float_rd(lo[0]), __double2float_rd(lo[1]), __double2float_rd(lo[2]), 0.f);
+        wbox[2 * ww + 1] = make_float4(__double2float_ru(hi[0]), __double2float_ru(hi[1]), __double2float_ru(hi[2]), 0.f);
+    }
     __syncthreads();
     for (int k = 0; k < 3; ++k) {
         lo[k] = s[k][0];
@@ -1180,7 +1185,8 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     rest.add(m->d_pb_key, std::max(m->n_pb, 1024));
     rest.add(m->d_pb_idx, std::max(m->n_pb, 1024));
     if (m->opt.prune && m->n_pb <= kPfxMax) {
-        rest.add(m->d_bnd, (size_t)6 * m->n_pb);
+        rest.add(m->d_bnd, (size_t)6 * 4 * m->n_pb);
+        rest.add(m->d_wbox, (size_t)2 * 4 * m->n_pb);
         rest.add(m->d_rev, (size_t)(cap + 1) * m->n_pb);
         rest.add(m->d_rev_cnt, cap + 1);
     }
@@ -1237,7 +1243,8 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     k_gather_sorted<<<cdiv(n, 256), 256, 0, st>>>(m->d_perm, n, x4, d4, m->d_xs, m->d_dS, m->d_inv);
     RBFD_CUDA(cudaGetLastError());
     // point blocks
-    k_point_blocks<<<m->n_pb, kPB, 0, st>>>(m->d_xs, n, m->d_pb_lo, m->d_pb_hi, m->d_pb_org, m->d_xs_hi, m->d_xs_lo);
+    k_point_blocks<<<m->n_pb, kPB, 0, st>>>(m->d_xs, n, m->d_pb_lo, m->d_pb_hi, m->d_pb_org, m->d_xs_hi, m->d_xs_lo,
+                                            m->d_wbox);
     RBFD_CUDA(cudaGetLastError());
 
     m->stats.launches += 6;  // unpack, bbox x2, morton, gather, point blocks

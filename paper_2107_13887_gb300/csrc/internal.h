@@ -210,10 +210,13 @@ struct rbfd_mesh {
     double *d_pb_key = nullptr;
     int *d_pb_idx = nullptr;
     // pruned list sweep (meshes of at most kPfxMax point blocks): per step
-    // parity and point block the block's max |E| at its last sweep, the bound
-    // accumulated since, the sum of |alpha| over its list ([2][3][n_pb]);
-    // the point blocks listing each control ([cap + 1][n_pb], counts [cap + 1])
+    // parity and warp of points (32 points, 4 per point block) the warp's max
+    // |E| at its last sweep, the bound accumulated since, the largest
+    // sum_c phi |alpha_c| at its points then ([2][3][4 n_pb]); each warp's box
+    // in FP32 rounded outward ([4 n_pb][lo, hi]); the point blocks listing
+    // each control ([cap + 1][n_pb], counts [cap + 1])
     double *d_bnd = nullptr;
+    float4 *d_wbox = nullptr;
     uint32_t *d_rev = nullptr;
     uint32_t *d_rev_cnt = nullptr;
     unsigned long long *d_pairs = nullptr;  // [16]: surface sweep useful, visited; volume useful, visited;

@@ -72,33 +72,60 @@ struct PersistArgs {
     unsigned long long *item_ctr;  // the sweep's item counter (zero at launch)
     int pfx_max;                   // balanced sweep items up to this many point blocks (<= kPfxMax)
     int chunk_target;              // controls per sweep item the chunking aims at
-    // pruned sweep (balanced items only): bnd[(parity * 3 + q) * n_pb + b] with
-    // q = 0 the block's max |E| over unselected points at its last sweep, 1
-    // the bound on how far any |E| of the block has moved since, 2 the sum of
-    // |alpha| (1-norm) over its list then; rev[k * n_pb + i] the point blocks
+    // pruned sweep (balanced items only), per warp of points w (32 points,
+    // w = 4 pb + warp): bnd[(parity * 3 + q) * 4 n_pb + w] with q = 0 the
+    // warp's max |E| over unselected points at its last sweep, 1 the bound
+    // on how far any |E| of the warp has moved since, 2 the largest
+    // sum_c phi |alpha_c|_1 at its points then; wbox[2 w], [2 w + 1] the
+    // warp's box in FP32 rounded outward; rev[k * n_pb + i] the point blocks
     // whose list holds control k (rev_cnt[k] of them); err_u the relative
-    // rounding of one operation of the sweep's arithmetic, with margin
+    // rounding of one operation of the sweep's arithmetic, with margin;
+    // marg bounds the FP32 rounding of a control-to-box distance
     int prune;
     double err_u;
     double *bnd;
+    const float4 *wbox;
+    float marg;
     uint32_t *rev, *rev_cnt;
 };
 
-// Bounds on what a sweep of point block b would find now, from its state at
-// its last sweep: hi >= the largest |E| it could compute for an unselected
-// point, lo <= the largest it would compute.  acc bounds the move of the
-// exact E of the stored weights since then; err bounds the rounding of the
-// sweep then and now (list terms and chunk sums, each of relative error
-// err_u on sums of at most A + 2 acc, the weights having moved by at most
-// sqrt(3) acc in the 1-norm), plus the subtraction from dS_l (|dS_l| <= S0).
-__device__ __forceinline__ void block_bounds(const PersistArgs &a, const double *bst, int b, int cnt, int nch,
-                                             double &lo, double &hi) {
-    const double M = __ldcg(bst + b);
-    const double acc = __ldcg(bst + a.n_pb + b) * (1.0 + 1e-12);
-    const double A = __ldcg(bst + 2 * a.n_pb + b);
+// Bounds on what a sweep of warp w would find now, from its state at its
+// last sweep: hi >= the largest |E| it could compute for an unselected point,
+// lo <= the largest it would compute.  acc bounds the move of the exact E of
+// the stored weights since then; err bounds the rounding of the sweep then
+// and now (at most cnt list terms and 2 nch chunk sums, each of relative
+// error err_u on sums of at most A + 2 acc: the weights moved by at most
+// sqrt(3) acc in phi-weighted 1-norm), plus the subtraction from dS_l
+// (|dS_l| <= S0).
+__device__ __forceinline__ void warp_bounds(const PersistArgs &a, const double *bst, int w, int cnt, int nch,
+                                            double &lo, double &hi) {
+    const int n_w = 4 * a.n_pb;
+    const double M = __ldcg(bst + w);
+    const double acc = __ldcg(bst + n_w + w) * (1.0 + 1e-12);
+    const double A = __ldcg(bst + 2 * n_w + w);
     const double err = (double)(cnt + 2 * nch + 16) * a.err_u * (A + 2.0 * acc + a.S0);
     lo = M - acc - 2.0 * err;
     hi = M + acc + 2.0 * err;
+}
+
+// A control at x (FP32, absolute) moved the weights by inc / |phi| times
+// phi: add inc times an upper bound of phi(dist(x, box) / R) to the move
+// bound of every warp of point block t within R of x (the distance shrunk by
+// marg for the FP32 rounding).
+template <int BASIS>
+__device__ __forceinline__ void push_bound(const PersistArgs &a, double *acc, int t, float3 x, double inc,
+                                           float invR) {
+#pragma unroll
+    for (int w4 = 0; w4 < 4; ++w4) {
+        const int w = 4 * t + w4;
+        const float4 lo = __ldg(&a.wbox[2 * w]), hi = __ldg(&a.wbox[2 * w + 1]);
+        const float dx = fmaxf(fmaxf(lo.x - x.x, x.x - hi.x), 0.0f);
+        const float dy = fmaxf(fmaxf(lo.y - x.y, x.y - hi.y), 0.0f);
+        const float dz = fmaxf(fmaxf(lo.z - x.z, x.z - hi.z), 0.0f);
+        const float d = fmaxf(sqrtf(dx * dx + dy * dy + dz * dz) - a.marg, 0.0f);
+        const float f = phi_f32_upper<BASIS>(d * invR);
+        if (f > 0.0f) atomicAdd(&acc[w], inc * (double)f);
+    }
 }
 
 __device__ __forceinline__ uint32_t ldcg_u32(const uint32_t *p) { return __ldcg(p); }
@@ -107,8 +134,8 @@ __device__ __forceinline__ float4 ldcg_f4(const float4 *p) { return __ldcg(p); }
 
 template <int DIM, int BASIS, int MODE>
 __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
-    __shared__ double t64[6][kTile];
-    __shared__ float t32[12][kTile];
+    __shared__ double t64[7][kTile];
+    __shared__ float t32[13][kTile];
     __shared__ double sk[32];
     __shared__ int si[32];
     __shared__ double scol[4][32];
@@ -118,7 +145,6 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
     __shared__ unsigned char s_hits[4][kTile];
     __shared__ unsigned s_pfx[kPfxMax + 1];
     __shared__ int s_item;
-    __shared__ double sA[4];
     __shared__ unsigned s_nsw;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -187,25 +213,29 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
         // pair is an item, the unoccupied ones skipped.)
         const bool balanced = a.n_pb <= a.pfx_max;
         // bounds of this step (written by the last) and of the next
-        const double *bcur = keep_bounds ? a.bnd + (size_t)((guard & 1) * 3) * a.n_pb : nullptr;
-        double *bnext = keep_bounds ? a.bnd + (size_t)(((guard & 1) ^ 1) * 3) * a.n_pb : nullptr;
-        const bool prune_now = keep_bounds && guard > 0;  // (the launch's first step sweeps every block)
+        const int n_w = 4 * a.n_pb;
+        const double *bcur = keep_bounds ? a.bnd + (size_t)((guard & 1) * 3) * n_w : nullptr;
+        double *bnext = keep_bounds ? a.bnd + (size_t)(((guard & 1) ^ 1) * 3) * n_w : nullptr;
+        const bool prune_now = keep_bounds && guard > 0;  // (the launch's first step sweeps every warp)
         int n_items = a.n_pb * nch;
         int n_swept = a.n_pb;
+        // a warp of points is skipped if even its upper bound stays below the
+        // largest lower bound: the warp attaining that is swept and finds at
+        // least as much, so the argmax and the stop test are those of a full
+        // sweep.  A point block is swept if one of its warps is.
+        double LB = -INFINITY;
         if (balanced) {
             const int per = (a.n_pb + kT - 1) / kT;
             const int b0 = min(a.n_pb, tid * per), b1 = min(a.n_pb, b0 + per);
-            // a block is skipped if even its upper bound stays below the
-            // largest lower bound: the block attaining that is swept and
-            // finds at least as much, so the argmax and the stop test are
-            // those of a full sweep
-            double LB = -INFINITY;
             if (prune_now) {
                 double lmax = -INFINITY;
                 for (int b = b0; b < b1; ++b) {
-                    double lo, hi;
-                    block_bounds(a, bcur, b, (int)ldcg_u32(&a.nb_cnt[b]), nch, lo, hi);
-                    lmax = fmax(lmax, lo);
+                    const int cb = (int)ldcg_u32(&a.nb_cnt[b]);
+                    for (int w4 = 0; w4 < 4; ++w4) {
+                        double lo, hi;
+                        warp_bounds(a, bcur, 4 * b + w4, cb, nch, lo, hi);
+                        lmax = fmax(lmax, lo);
+                    }
                 }
                 for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
                 if (lane == 0) sk[warp] = lmax;
@@ -214,35 +244,40 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                 LB = fmax(fmax(sk[0], sk[1]), fmax(sk[2], sk[3]));
                 __syncthreads();
             }
-            unsigned mine = 0, swept = 0;
+            unsigned mine = 0, swept = 0, skip_w = 0;
             unsigned long long skip_pairs = 0;
             for (int b = b0; b < b1; ++b) {
                 const int cb = (int)ldcg_u32(&a.nb_cnt[b]);
                 unsigned ub = (unsigned)min(nch, max(1, (cb + cl - 1) / cl));
                 if (prune_now) {
-                    double lo, hi;
-                    block_bounds(a, bcur, b, cb, nch, lo, hi);
-                    if (hi < LB) {
-                        ub = 0;
-                        if (blockIdx.x == 0) {  // the block's state carries over to the next step
-                            bnext[b] = __ldcg(bcur + b);
-                            bnext[a.n_pb + b] = __ldcg(bcur + a.n_pb + b);
-                            bnext[2 * a.n_pb + b] = __ldcg(bcur + 2 * a.n_pb + b);
-                            skip_pairs += (unsigned long long)min((int64_t)kPB, a.n_s - (int64_t)b * kPB) *
+                    int act = 0;
+                    for (int w4 = 0; w4 < 4; ++w4) {
+                        const int w = 4 * b + w4;
+                        double lo, hi;
+                        warp_bounds(a, bcur, w, cb, nch, lo, hi);
+                        if (hi >= LB) {
+                            ++act;
+                        } else if (blockIdx.x == 0) {  // the warp's state carries over to the next step
+                            bnext[w] = __ldcg(bcur + w);
+                            bnext[n_w + w] = __ldcg(bcur + n_w + w);
+                            bnext[2 * n_w + w] = __ldcg(bcur + 2 * n_w + w);
+                            const int64_t p0 = (int64_t)w * 32;
+                            skip_pairs += (unsigned long long)max((int64_t)0, min((int64_t)32, a.n_s - p0)) *
                                           (unsigned long long)cb;
+                            ++skip_w;
                         }
-                    } else {
-                        ++swept;
                     }
+                    if (act == 0) ub = 0;
+                    else ++swept;
                 }
                 s_pfx[b] = ub;
                 mine += ub;
             }
             if (prune_now) {
                 if (swept) atomicAdd(&s_nsw, swept);
-                if (blockIdx.x == 0 && b1 > b0 && (b1 - b0) > (int)swept) {
+                if (blockIdx.x == 0 && skip_w) {
                     atomicAdd(&a.pairs[11], skip_pairs);
-                    atomicAdd(&a.pairs[12], (unsigned long long)((b1 - b0) - (int)swept));
+                    atomicAdd(&a.pairs[12], (unsigned long long)skip_w);
                 }
             }
             unsigned tot;
@@ -306,7 +341,16 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                 }
             }
             unsigned useful = 0;
-            double abs_alpha = 0.0;  // |alpha| (1-norm) over the chunk's controls (pruning bound)
+            // this warp's points are evaluated unless its bound skips them
+            // (the same decision as in the prefix above: same inputs)
+            bool wact = true;
+            if (prune_now) {
+                double blo, bhi;
+                warp_bounds(a, bcur, 4 * pb + warp, cnt, nch, blo, bhi);
+                wact = bhi >= LB;
+            }
+            double sabs64 = 0.0;  // sum_c phi |alpha_c|_1 at this point (pruning bounds)
+            float sabs = 0.0f;
             float3 wlo, whi;
             if (MODE == 1) warp_box(valid, qx.hi, qy.hi, qz.hi, wlo, whi);
             const float R2m = (float)(1.002 * a.R) * (float)(1.002 * a.R);  // filter margin
@@ -315,11 +359,13 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                 if (tid < m) {
                     const uint32_t j = ldcg_u32(&a.nb_list[(size_t)pb * a.cap + t0 + tid]);
                     const double4 c = ldcg_d4(&a.cx[j]), al = ldcg_d4(&a.alpha[j]);
-                    if (keep_bounds) abs_alpha += (fabs(al.x) + fabs(al.y)) + fabs(al.z);
+                    const double aabs = (fabs(al.x) + fabs(al.y)) + fabs(al.z);
                     if (MODE == 0) {
                         t64[0][tid] = c.x; t64[1][tid] = c.y; t64[2][tid] = c.z;
                         t64[3][tid] = al.x; t64[4][tid] = al.y; t64[5][tid] = al.z;
+                        t64[6][tid] = aabs;
                     } else {
+                        t32[12][tid] = __double2float_ru(aabs);
                         df rx = df_from_double(c.x - org.x), ry = df_from_double(c.y - org.y),
                            rz = df_from_double(c.z - org.z);
                         df ax = df_from_double(al.x), ay = df_from_double(al.y), az = df_from_double(al.z);
@@ -333,7 +379,7 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                     // a warp skips a control farther than R from all its points
                     // (phi is exactly 0 there, the sums do not change)
                     const double R2hi = __dmul_rn(__dmul_rn(a.R, a.R), 1.0 + 1e-12);
-                    for (int q = 0; q < m; ++q) {
+                    for (int q = 0; wact && q < m; ++q) {
                         const double s2 = dist2_f64<DIM>(px, py, pz, t64[0][q], t64[1][q], t64[2][q]);
                         if (!__any_sync(0xffffffffu, valid && s2 <= R2hi)) continue;
                         if (valid) {
@@ -343,14 +389,20 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                             acc64[0] = __dadd_rn(acc64[0], __dmul_rn(t64[3][q], f));
                             acc64[1] = __dadd_rn(acc64[1], __dmul_rn(t64[4][q], f));
                             if (DIM == 3) acc64[2] = __dadd_rn(acc64[2], __dmul_rn(t64[5][q], f));
+                            if (keep_bounds) sabs64 = fma(f, t64[6][q], sabs64);
                         }
                     }
-                } else {
+                } else if (wact) {
                     // every lane of the warp takes part in the filter, then only
                     // the lanes with a point accumulate
                     const int nh = warp_hits<DIM>(t32, m, wlo, whi, R2m, s_hits[warp]);
-                    if (valid)
-                        hits_accumulate_df<DIM, BASIS>(qx, qy, qz, t32, s_hits[warp], nh, invR, acc, useful);
+                    if (valid) {
+                        if (keep_bounds)
+                            hits_accumulate_df_abs<DIM, BASIS>(qx, qy, qz, t32, s_hits[warp], nh, invR, acc, useful,
+                                                               sabs);
+                        else
+                            hits_accumulate_df<DIM, BASIS>(qx, qy, qz, t32, s_hits[warp], nh, invR, acc, useful);
+                    }
                 }
                 __syncthreads();
             }
@@ -359,14 +411,10 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                 acc64[1] = df_to_double(acc[1]);
                 acc64[2] = df_to_double(acc[2]);
             }
-            double chunk_abs = 0.0;  // (thread 0: the chunk's |alpha| sum, in the w slot of its partial)
-            if (keep_bounds) {
-                abs_alpha = warp_sum_d(abs_alpha);
-                if (lane == 0) sA[warp] = abs_alpha;
-                __syncthreads();
-                if (tid == 0) chunk_abs = (sA[0] + sA[1]) + (sA[2] + sA[3]);
-            }
-            if (valid) a.part[(size_t)ch * a.n_s + p] = make_double4(acc64[0], acc64[1], acc64[2], chunk_abs);
+            // (w slot: this chunk's share of sum_c phi |alpha_c|_1 at the point)
+            if (valid)
+                a.part[(size_t)ch * a.n_s + p] =
+                    make_double4(acc64[0], acc64[1], acc64[2], MODE == 0 ? sabs64 : (double)sabs);
             {
                 unsigned u = useful;
                 for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
@@ -388,8 +436,8 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                 __threadfence();
                 double key = -1.0;
                 int orig = -1;
-                double s3 = 0.0;  // (thread 0: the list's |alpha| sum)
-                if (valid) {
+                double s3 = 0.0;  // sum_c phi |alpha_c|_1 at this point (pruning bounds)
+                if (valid && wact) {  // (a skipped warp's points keep their last key: below the argmax)
                     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
                     int c = 0;
                     for (; c + 8 <= used; c += 8) {  // eight independent loads in flight
@@ -422,16 +470,28 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                         orig = (int)a.perm[p];
                     }
                 }
+                if (keep_bounds && wact) {
+                    // the warp's state for the next steps: its max |E| over the
+                    // unselected points, no move yet, and the largest scale of
+                    // the sums (the FP32 sums of phi |alpha| rounded up by a
+                    // margin over their cnt terms)
+                    double km = key, sm = s3;
+                    for (int o = 16; o > 0; o >>= 1) {
+                        km = fmax(km, __shfl_xor_sync(0xffffffffu, km, o));
+                        sm = fmax(sm, __shfl_xor_sync(0xffffffffu, sm, o));
+                    }
+                    if (lane == 0) {
+                        const int w = 4 * pb + warp;
+                        bnext[w] = km > 0.0 ? sqrt(km) : 0.0;
+                        bnext[n_w + w] = 0.0;
+                        bnext[2 * n_w + w] = sm * (1.0 + (double)(cnt + 16) * 0x1p-22);
+                    }
+                }
                 block_argmax(key, orig, sk, si);
                 if (tid == 0) {
                     a.pb_key[pb] = key;
                     a.pb_idx[pb] = orig;
                     a.pb_done[pb] = 0;
-                    if (keep_bounds) {
-                        bnext[pb] = key > 0.0 ? sqrt(key) : 0.0;
-                        bnext[a.n_pb + pb] = 0.0;
-                        bnext[2 * a.n_pb + pb] = s3;
-                    }
                     __threadfence();
                     s_lead = atomicAdd(&a.st->pb_done, 1u) == (unsigned)(n_swept - 1);
                 }
@@ -579,10 +639,10 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                     }
                 }
             }
-            // c_n's own block has lost the point its maximum was taken at:
-            // no lower bound from it until it is swept again (which its
-            // infinite bound forces)
-            if (keep_bounds && first_block) bnext[a.n_pb + c / kPB] = INFINITY;
+            // c_n's own warp has lost the point its maximum was taken at: no
+            // lower bound from it until it is swept again (which its infinite
+            // bound forces)
+            if (keep_bounds && first_block) bnext[n_w + c / 32] = INFINITY;
         }
         double yy = 0, yw0 = 0, yw1 = 0, yw2 = 0;
         for (int j = blockIdx.x * 4 + warp; j < n; j += P * 4) {
@@ -680,7 +740,10 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                 const double inc = wnorm / l;
                 const int rc = (int)ldcg_u32(&a.rev_cnt[k]);
                 const uint32_t *rv = a.rev + (size_t)k * a.n_pb;
-                for (int q = lane; q < rc; q += 32) atomicAdd(&bnext[a.n_pb + ldcg_u32(rv + q)], inc);
+                const float4 xk = ldcg_f4(&a.cdf[k]);
+                for (int q = lane; q < rc; q += 32)
+                    push_bound<BASIS>(a, bnext + n_w, (int)ldcg_u32(rv + q), make_float3(xk.x, xk.y, xk.z), inc,
+                                      invR.hi);
                 continue;
             }
             const double *trow = a.Gt + (size_t)k * a.cap;
@@ -720,7 +783,10 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                 const double inc = wnorm * fabs(t / l);
                 const int rc = (int)ldcg_u32(&a.rev_cnt[k]);
                 const uint32_t *rv = a.rev + (size_t)k * a.n_pb;
-                for (int q = lane; q < rc; q += 32) atomicAdd(&bnext[a.n_pb + ldcg_u32(rv + q)], inc);
+                const float4 xk = ldcg_f4(&a.cdf[k]);
+                for (int q = lane; q < rc; q += 32)
+                    push_bound<BASIS>(a, bnext + n_w, (int)ldcg_u32(rv + q), make_float3(xk.x, xk.y, xk.z), inc,
+                                      invR.hi);
             }
             if (lane == 0) {
                 const double g = -t / l;
@@ -822,11 +888,19 @@ void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
     // ones cost fewer partial sums (RBFD_SWEEP_CHUNK sets it, 16 to 1024)
     a.chunk_target = 64;
     if (const char *v = std::getenv("RBFD_SWEEP_CHUNK")) a.chunk_target = std::max(16, std::min(1024, std::atoi(v)));
-    a.prune = (m->opt.prune && m->d_bnd && m->n_pb <= a.pfx_max) ? 1 : 0;
+    a.prune = (m->opt.prune && m->d_bnd && m->d_wbox && m->n_pb <= a.pfx_max) ? 1 : 0;
     // relative rounding per operation: FP64 2^-53, double-float about 2^-44;
     // a factor 16 of margin on each
     a.err_u = m->opt.precision == RBFD_FP64 ? 0x1p-49 : 0x1p-40;
     a.bnd = m->d_bnd;
+    a.wbox = m->d_wbox;
+    {
+        // FP32 rounding of a control-to-box distance: the control's hi part
+        // (2^-24 relative per coordinate) and the arithmetic, with margin
+        double xmax = R;
+        for (int q = 0; q < 6; ++q) xmax = std::max(xmax, std::fabs(m->h_sbox[q]));
+        a.marg = (float)(0x1p-19 * (xmax + R));
+    }
     a.rev = m->d_rev;
     a.rev_cnt = m->d_rev_cnt;
     if (a.prune) RBFD_CUDA(cudaMemsetAsync(a.rev_cnt, 0, sizeof(uint32_t) * (size_t)(m->cap + 1), m->stream));

@@ -85,7 +85,7 @@ class rbfd_stats(ctypes.Structure):
         ("eq12_pairs", ctypes.c_int64),
         ("persist_grow_fma", ctypes.c_int64),
         ("sweep_pairs_skipped", ctypes.c_int64),
-        ("sweep_blocks_skipped", ctypes.c_int64),
+        ("sweep_warps_skipped", ctypes.c_int64),
     ]
 
 

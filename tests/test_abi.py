@@ -79,7 +79,7 @@ def test_struct_layout_matches_header(tmp_path):
         " offsetof(rbfd_server_options, fuse_volume));\n"
         'printf("%zu %zu\\n", offsetof(rbfd_stats, newton_pairs_useful), offsetof(rbfd_stats, eq12_pairs));\n'
         'printf("%zu %zu %zu\\n", offsetof(rbfd_options, prune), offsetof(rbfd_stats, persist_grow_fma),'
-        " offsetof(rbfd_stats, sweep_blocks_skipped));\n"
+        " offsetof(rbfd_stats, sweep_warps_skipped));\n"
         "return 0;}\n"
     )
     exe = tmp_path / "layout"
@@ -110,7 +110,7 @@ def test_struct_layout_matches_header(tmp_path):
     assert onp == rbfd.rbfd_stats.newton_pairs_useful.offset and oeq == rbfd.rbfd_stats.eq12_pairs.offset
     opr, ogf, obs = map(int, h.split())
     assert opr == rbfd.rbfd_options.prune.offset
-    assert ogf == rbfd.rbfd_stats.persist_grow_fma.offset and obs == rbfd.rbfd_stats.sweep_blocks_skipped.offset
+    assert ogf == rbfd.rbfd_stats.persist_grow_fma.offset and obs == rbfd.rbfd_stats.sweep_warps_skipped.offset
 
 
 def test_argument_checks_before_any_device_work(lib):

@@ -46,8 +46,8 @@ def test_pruned_persistent_sweep_equals_full_sweep(precision):
     rc1, pruned, st1 = _levels(c, precision=precision, engine=2, prune=True, profile=True)
     assert rc0 == rc1 == rbfd.OK
     _same_levels(full, pruned)
-    assert st0["sweep_blocks_skipped"] == 0 and st0["sweep_pairs_skipped"] == 0
-    assert st1["sweep_blocks_skipped"] > 0
+    assert st0["sweep_warps_skipped"] == 0 and st0["sweep_pairs_skipped"] == 0
+    assert st1["sweep_warps_skipped"] > 0
     # the skipped pairs are pairs the full sweep visited
     assert st1["sweep_pairs_visited"] < st0["sweep_pairs_visited"]
     assert st1["sweep_pairs_visited"] + st1["sweep_pairs_skipped"] >= st0["sweep_pairs_visited"] * 0.999
@@ -63,13 +63,13 @@ def test_pruned_sweep_matches_the_oracle_sequence():
     ref = oracle.greedy(c.xyz_s, c.dS, c.R, c.eps, n_threads=NT)
     assert min(ref.gap) > 1e-7
     rc, levels, st = _levels(c, precision=rbfd.FP64, engine=2, prune=True)
-    assert rc == rbfd.OK and st["sweep_blocks_skipped"] > 0
+    assert rc == rbfd.OK and st["sweep_warps_skipped"] > 0
     assert len(levels) == len(ref.idx)
     for l, L in enumerate(levels):
         assert np.array_equal(L.idx, ref.idx[l]), f"level {l}"
     check_replay(c, levels)
     rc, levels, st = _levels(c, precision=rbfd.MIXED, engine=2, prune=True)
-    assert rc == rbfd.OK and st["sweep_blocks_skipped"] > 0
+    assert rc == rbfd.OK and st["sweep_warps_skipped"] > 0
     check_replay(c, levels)
 
 
@@ -95,7 +95,7 @@ def test_round_robin_items_do_not_prune(monkeypatch):
     c = synth.wing_case(60, 30, 2, displacement="ridge", seed=1, R=(1.0, 0.3), eps=1e-4, D=1.0, k=4.0,
                         wall_distance=False)
     rc0, a, st = _levels(c, engine=2, prune=True, profile=True)
-    assert st["sweep_blocks_skipped"] == 0
+    assert st["sweep_warps_skipped"] == 0
     monkeypatch.delenv("RBFD_TEST_SWEEP_ROUND_ROBIN")
     rc1, b, _ = _levels(c, engine=2, prune=True)
     assert rc0 == rc1
