@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
     __shared__ unsigned s_scan[32];
     __shared__ unsigned char s_hits[4][kTile];
     __shared__ unsigned s_pfx[kPfxMax + 1];
+    __shared__ unsigned s_order[kPfxMax];  // pruned steps: point block | chunks << 16, in item order
     __shared__ int s_item;
     __shared__ unsigned s_nsw;
 
@@ -245,6 +246,7 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                 __syncthreads();
             }
             unsigned mine = 0, swept = 0, skip_w = 0;
+            unsigned bc0 = 0, bc1 = 0, bc2 = 0, bc3 = 0;
             unsigned long long skip_pairs = 0;
             for (int b = b0; b < b1; ++b) {
                 const int cb = (int)ldcg_u32(&a.nb_cnt[b]);
@@ -269,9 +271,16 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                     }
                     if (act == 0) ub = 0;
                     else ++swept;
+                    // (bucket of the item order: 4 active warps first, then 3, 2, at most 1)
+                    const int bk = act >= 2 ? 4 - act : 3;
+                    bc0 += bk == 0;
+                    bc1 += bk == 1;
+                    bc2 += bk == 2;
+                    bc3 += bk == 3;
+                    ub |= (unsigned)bk << 16;
                 }
                 s_pfx[b] = ub;
-                mine += ub;
+                mine += ub & 0xFFFFu;
             }
             if (prune_now) {
                 if (swept) atomicAdd(&s_nsw, swept);
@@ -281,11 +290,42 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                 }
             }
             unsigned tot;
-            unsigned run = block_excl_scan_u32(mine, s_scan, &tot);
-            for (int b = b0; b < b1; ++b) {
-                const unsigned ub = s_pfx[b];
-                s_pfx[b] = run;
-                run += ub;
+            if (prune_now) {
+                // Items go out heaviest first: the point blocks with four
+                // warps to sweep, then three, two, one (stable within each),
+                // so that the step's last items are light ones.  Positions by
+                // a counting sort (two scans of packed 16-bit counts), then
+                // the chunk prefix over the sorted order.
+                unsigned t01, t23;
+                const unsigned e01 = block_excl_scan_u32(bc0 | (bc1 << 16), s_scan, &t01);
+                const unsigned e23 = block_excl_scan_u32(bc2 | (bc3 << 16), s_scan, &t23);
+                unsigned p0 = e01 & 0xFFFFu, p1 = (t01 & 0xFFFFu) + (e01 >> 16),
+                         p2 = (t01 & 0xFFFFu) + (t01 >> 16) + (e23 & 0xFFFFu),
+                         p3 = (t01 & 0xFFFFu) + (t01 >> 16) + (t23 & 0xFFFFu) + (e23 >> 16);
+                for (int b = b0; b < b1; ++b) {
+                    const unsigned v = s_pfx[b], k = v >> 16;
+                    const unsigned at = k == 0 ? p0 : k == 1 ? p1 : k == 2 ? p2 : p3;
+                    s_order[at] = (unsigned)b | ((v & 0xFFFFu) << 16);
+                    p0 += k == 0;
+                    p1 += k == 1;
+                    p2 += k == 2;
+                    p3 += k == 3;
+                }
+                __syncthreads();
+                unsigned m2 = 0;
+                for (int i = b0; i < b1; ++i) m2 += s_order[i] >> 16;
+                unsigned run = block_excl_scan_u32(m2, s_scan, &tot);
+                for (int i = b0; i < b1; ++i) {
+                    s_pfx[i] = run;
+                    run += s_order[i] >> 16;
+                }
+            } else {
+                unsigned run = block_excl_scan_u32(mine, s_scan, &tot);
+                for (int b = b0; b < b1; ++b) {
+                    const unsigned ub = s_pfx[b];
+                    s_pfx[b] = run;
+                    run += ub;
+                }
             }
             if (tid == 0) {
                 s_pfx[a.n_pb] = tot;
@@ -297,24 +337,21 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
         }
         // balanced: items taken from the counter as blocks come free (their
         // costs differ with the density of controls); the next index is
-        // fetched while the current item runs.  Otherwise every P-th item.
+        // fetched when the current item is done, so that no block holds an
+        // item back while others run out at the end of the step.  Otherwise
+        // every P-th item.
         int item = balanced ? s_item : (int)blockIdx.x;
-        unsigned long long nxt = 0;
         for (; item < n_items; item = balanced ? s_item : item + (int)P) {
-            if (balanced) {
-                __syncthreads();  // every thread has read s_item
-                if (tid == 0) nxt = atomicAdd(a.item_ctr, 1ull);
-            }
             int pb, ch, cnt, used;
             if (balanced) {
-                int bl = 0, bh = a.n_pb;  // s_pfx[bl] <= item < s_pfx[bh]
+                int bl = 0, bh = a.n_pb;  // s_pfx[bl] <= item < s_pfx[bh] (item order)
                 while (bh - bl > 1) {
                     const int mid = (bl + bh) >> 1;
                     if (s_pfx[mid] <= (unsigned)item) bl = mid; else bh = mid;
                 }
-                pb = bl;
-                ch = item - (int)s_pfx[pb];
-                used = (int)(s_pfx[pb + 1] - s_pfx[pb]);
+                pb = prune_now ? (int)(s_order[bl] & 0xFFFFu) : bl;
+                ch = item - (int)s_pfx[bl];
+                used = (int)(s_pfx[bl + 1] - s_pfx[bl]);
                 cnt = (int)ldcg_u32(&a.nb_cnt[pb]);
             } else {
                 pb = item / nch;
@@ -424,8 +461,6 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                     atomicAdd(&a.pairs[1], nv * (unsigned long long)(hi - lo));
                 }
             }
-            // (the next item, read after the barriers below)
-            if (balanced && tid == 0) s_item = (int)(nxt - item_base);
             // last chunk of this point block: E, key, block argmax; the last
             // point block to finish then takes the step's decision
             __threadfence();
@@ -539,6 +574,7 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                         } else {
                             // double-float on the FP32 pipe from the split coordinates,
                             // four entries at a time (their loads issued together)
+                            const float Rnear = (float)(1.002 * a.R) + a.marg, R2near = Rnear * Rnear;
                             for (int q = q0; q < q1; q += 4) {
                                 uint32_t kk[4];
 #pragma unroll
@@ -549,14 +585,26 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                                     h[u] = q + u < q1 ? ldcg_f4(&a.cdf[kk[u]]) : make_float4(0, 0, 0, 0);
                                     l[u] = q + u < q1 ? ldcg_f4(&a.cdf[a.cap + 1 + kk[u]]) : make_float4(0, 0, 0, 0);
                                 }
+                                // FP32 pre-filter on the hi parts: a control beyond
+                                // (1.002 R + marg) has phi exactly 0 in double-float too
+                                bool near[4];
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) {
+                                    const float fx = h[u].x - xcx.hi, fy = h[u].y - xcy.hi, fz = h[u].z - xcz.hi;
+                                    near[u] = q + u < q1 && fx * fx + fy * fy + (DIM == 3 ? fz * fz : 0.0f) <= R2near;
+                                }
 #pragma unroll
                                 for (int u = 0; u < 4; ++u) {
                                     if (q + u >= q1) break;
-                                    const df dx = df_add({h[u].x, l[u].x}, df_neg(xcx)),
-                                             dy = df_add({h[u].y, l[u].y}, df_neg(xcy));
-                                    df r2 = df_add(df_sqr(dx), df_sqr(dy));
-                                    if (DIM == 3) r2 = df_add(r2, df_sqr(df_add({h[u].z, l[u].z}, df_neg(xcz))));
-                                    const double f = df_to_double(phi_df<BASIS>(df_mul(df_sqrt(r2), invR)));
+                                    double f = 0.0;
+                                    if (near[u]) {
+                                        const df dx = df_add({h[u].x, l[u].x}, df_neg(xcx)),
+                                                 dy = df_add({h[u].y, l[u].y}, df_neg(xcy));
+                                        df r2 = df_add(df_sqr(dx), df_sqr(dy));
+                                        if (DIM == 3)
+                                            r2 = df_add(r2, df_sqr(df_add({h[u].z, l[u].z}, df_neg(xcz))));
+                                        f = df_to_double(phi_df<BASIS>(df_mul(df_sqrt(r2), invR)));
+                                    }
                                     a.phi[q + u] = f;
                                     mine += (f != 0.0);
                                 }
@@ -605,6 +653,11 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                         }
                     }
                 }
+            }
+            if (balanced) {
+                // (every thread has read s_item: block barriers came after the read)
+                if (tid == 0) s_item = (int)(atomicAdd(a.item_ctr, 1ull) - item_base);
+                __syncthreads();
             }
         }
         if (balanced) item_base += (unsigned long long)n_items + P;
