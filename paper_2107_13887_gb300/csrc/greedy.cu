@@ -1155,6 +1155,7 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     zero.add(m->d_phase_ns, 8);
     zero.add(m->d_lvl, 8);
     zero.add(m->d_pb_done, m->n_pb);
+    zero.add(m->d_grp_done, (size_t)m->n_pb * ((m->n_chunk_max + 15) / 16));
     rest.add(m->d_bbox, 8);
     rest.add(m->d_perm, n);
     rest.add(m->d_inv, n);
@@ -1182,6 +1183,7 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     rest.add(m->d_nb_cnt, m->n_pb);
     rest.add(m->d_nb_list, (size_t)m->n_pb * cap);
     rest.add(m->d_part, (size_t)m->n_chunk_max * n);
+    rest.add(m->d_gpart4, (size_t)((m->n_chunk_max + 15) / 16) * n);
     rest.add(m->d_pb_key, std::max(m->n_pb, 1024));
     rest.add(m->d_pb_idx, std::max(m->n_pb, 1024));
     if (m->opt.prune && m->n_pb <= kPfxMax) {

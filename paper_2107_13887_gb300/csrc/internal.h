@@ -205,6 +205,8 @@ struct rbfd_mesh {
     uint32_t *d_nb_cnt = nullptr; // controls listed per point block
     uint32_t *d_nb_list = nullptr;// [n_pb][cap]
     double4 *d_part = nullptr;    // sweep partial sums [n_chunk_max][n_s]
+    double4 *d_gpart4 = nullptr;  // their group sums [ceil(n_chunk_max / 16)][n_s] (persistent sweep)
+    unsigned int *d_grp_done = nullptr;  // [n_pb][ceil(n_chunk_max / 16)] chunk counters of the groups
     int n_chunk_max = 1;
     unsigned int *d_pb_done = nullptr;
     double *d_pb_key = nullptr;

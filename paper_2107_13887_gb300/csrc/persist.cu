@@ -41,6 +41,7 @@ namespace rbfd {
 namespace {
 
 constexpr int kT = 128;        // threads per block (4 warps)
+constexpr int kRG = 16;        // chunk partial sums reduced per group (two-level reduction)
 
 
 struct PersistArgs {
@@ -60,6 +61,9 @@ struct PersistArgs {
     uint32_t *nz_k;
     double *nz_v;
     double4 *part;
+    double4 *gpart;          // group partial sums [max_grp][n_s]
+    unsigned int *grp_done;  // [n_pb][max_grp] finished chunks per group (zero between steps)
+    int max_grp;
     unsigned int *pb_done;
     double *pb_key;
     int *pb_idx;
@@ -128,6 +132,32 @@ __device__ __forceinline__ void push_bound(const PersistArgs &a, double *acc, in
     }
 }
 
+// Adds the partial sums [c0, c1) of point p (stride apart) in order, eight
+// loads in flight.
+__device__ __forceinline__ void sum_parts(const double4 *base, size_t stride, int c0, int c1, double &s0,
+                                          double &s1, double &s2, double &s3) {
+    int c = c0;
+    for (; c + 8 <= c1; c += 8) {
+        double4 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = ldcg_d4(base + (size_t)(c + q) * stride);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            s0 = __dadd_rn(s0, v[q].x);
+            s1 = __dadd_rn(s1, v[q].y);
+            s2 = __dadd_rn(s2, v[q].z);
+            s3 += v[q].w;
+        }
+    }
+    for (; c < c1; ++c) {
+        const double4 v = ldcg_d4(base + (size_t)c * stride);
+        s0 = __dadd_rn(s0, v.x);
+        s1 = __dadd_rn(s1, v.y);
+        s2 = __dadd_rn(s2, v.z);
+        s3 += v.w;
+    }
+}
+
 __device__ __forceinline__ uint32_t ldcg_u32(const uint32_t *p) { return __ldcg(p); }
 __device__ __forceinline__ double ldcg_d(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ float4 ldcg_f4(const float4 *p) { return __ldcg(p); }
@@ -140,7 +170,7 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
     __shared__ int si[32];
     __shared__ double scol[4][32];
     __shared__ double sred[4][4];
-    __shared__ bool s_last, s_lead;
+    __shared__ bool s_last, s_lead, s_glast;
     __shared__ unsigned s_scan[32];
     __shared__ unsigned char s_hits[4][kTile];
     __shared__ unsigned s_pfx[kPfxMax + 1];
@@ -461,12 +491,38 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                     atomicAdd(&a.pairs[1], nv * (unsigned long long)(hi - lo));
                 }
             }
-            // last chunk of this point block: E, key, block argmax; the last
-            // point block to finish then takes the step's decision
+            // The chunks' partial sums are reduced in two levels, in a fixed
+            // order: the last chunk of each group of kRG sums the group's,
+            // the last group of the point block sums the groups' and forms E,
+            // the key and the block argmax; the last point block to finish
+            // then takes the step's decision
             __threadfence();
             __syncthreads();
-            if (tid == 0) s_last = atomicAdd(&a.pb_done[pb], 1u) == (unsigned)(used - 1);  // (used >= 1)
+            const int ng = (used + kRG - 1) / kRG, grp = ch / kRG;
+            if (tid == 0) {
+                const int gs = min(kRG, used - grp * kRG);
+                const bool gl = ng == 1 ? atomicAdd(&a.pb_done[pb], 1u) == (unsigned)(used - 1)  // (used >= 1)
+                                        : atomicAdd(&a.grp_done[(size_t)pb * a.max_grp + grp], 1u) ==
+                                              (unsigned)(gs - 1);
+                s_last = ng == 1 && gl;
+                s_glast = ng > 1 && gl;
+            }
             __syncthreads();
+            if (s_glast) {
+                __threadfence();
+                if (valid && wact) {
+                    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                    sum_parts(a.part + p, (size_t)a.n_s, grp * kRG, min(used, (grp + 1) * kRG), s0, s1, s2, s3);
+                    a.gpart[(size_t)grp * a.n_s + p] = make_double4(s0, s1, s2, s3);
+                }
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) {
+                    a.grp_done[(size_t)pb * a.max_grp + grp] = 0;
+                    s_last = atomicAdd(&a.pb_done[pb], 1u) == (unsigned)(ng - 1);
+                }
+                __syncthreads();
+            }
             if (s_last) {
                 __threadfence();
                 double key = -1.0;
@@ -474,26 +530,10 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                 double s3 = 0.0;  // sum_c phi |alpha_c|_1 at this point (pruning bounds)
                 if (valid && wact) {  // (a skipped warp's points keep their last key: below the argmax)
                     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-                    int c = 0;
-                    for (; c + 8 <= used; c += 8) {  // eight independent loads in flight
-                        double4 v[8];
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) v[q] = ldcg_d4(&a.part[(size_t)(c + q) * a.n_s + p]);
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            s0 = __dadd_rn(s0, v[q].x);
-                            s1 = __dadd_rn(s1, v[q].y);
-                            s2 = __dadd_rn(s2, v[q].z);
-                            s3 += v[q].w;
-                        }
-                    }
-                    for (; c < used; ++c) {
-                        double4 v = ldcg_d4(&a.part[(size_t)c * a.n_s + p]);
-                        s0 = __dadd_rn(s0, v.x);
-                        s1 = __dadd_rn(s1, v.y);
-                        s2 = __dadd_rn(s2, v.z);
-                        s3 += v.w;
-                    }
+                    if (ng == 1)
+                        sum_parts(a.part + p, (size_t)a.n_s, 0, used, s0, s1, s2, s3);
+                    else
+                        sum_parts(a.gpart + p, (size_t)a.n_s, 0, ng, s0, s1, s2, s3);
                     const double4 cu = a.cur[p];
                     const double e0 = __dsub_rn(cu.x, s0), e1 = __dsub_rn(cu.y, s1);
                     const double e2 = (DIM == 3) ? __dsub_rn(cu.z, s2) : 0.0;
@@ -926,6 +966,12 @@ void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
     a.nz_v = m->d_nz_v;
     a.part = m->d_part;
     a.pb_done = m->d_pb_done;
+    a.gpart = m->d_gpart4;
+    a.grp_done = m->d_grp_done;
+    a.max_grp = (m->n_chunk_max + kRG - 1) / kRG;
+    // (the completion counters start at zero even after a launch that ended early)
+    RBFD_CUDA(cudaMemsetAsync(a.pb_done, 0, sizeof(unsigned) * (size_t)m->n_pb, m->stream));
+    RBFD_CUDA(cudaMemsetAsync(a.grp_done, 0, sizeof(unsigned) * (size_t)m->n_pb * a.max_grp, m->stream));
     a.pb_key = m->d_pb_key;
     a.pb_idx = m->d_pb_idx;
     a.bar = m->d_bar;

@@ -99,7 +99,7 @@ size_t mesh_footprint(int dim, int64_t n_s, int64_t n_v, int64_t cap) {
     b += 16ull * cap * cap;                         // G and its transpose
     b += 8ull * n_pb * cap;                         // block lists and their reverse (pruned sweep)
     b += (size_t)n_s * (4 * 32 + 2 * 16 + 16);      // sorted surface, targets, error, df coords, perms
-    b += (size_t)nch * n_s * 32;                    // sweep partials
+    b += (size_t)(nch + (nch + 15) / 16) * n_s * 32;  // sweep partials and their group sums
     b += (size_t)cap * (6 * 32 + 8 * 8) + 32ull * (cap / 256 + 2) * cap;
     b += (size_t)n_v * (32 * 3 + 4 * 6);            // registered + working volume buffers
     // Newton-basis values V: n_s doubles per column, at most kNewtonCols columns and 1 GB
