@@ -1240,7 +1240,9 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     const int nbb = std::min<int>(cdiv(n, 256), 256);
     k_bbox_partial<<<nbb, 256, 0, st>>>(x4, n, part);
     k_bbox_final<<<1, 192, 0, st>>>(part, nbb, m->d_bbox);
-    morton_keys_f64_dev(x4, n, m->dim, m->d_bbox, keys, m->d_perm, st);
+    // (cubic cells: the wing's surface box is 3.5 x 0.12 x 3 chords, and
+    // per-axis cells made the 128-point blocks' boxes 1.6x as wide)
+    morton_keys_f64_dev(x4, n, m->dim, m->d_bbox, keys, m->d_perm, st, 0, true);
     radix_sort_pairs(keys, m->d_perm, n, m->dim == 2 ? 32 : 30, m->sort, st);
     k_gather_sorted<<<cdiv(n, 256), 256, 0, st>>>(m->d_perm, n, x4, d4, m->d_xs, m->d_dS, m->d_inv);
     RBFD_CUDA(cudaGetLastError());

@@ -87,9 +87,9 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *t
 
 // Morton keys of points relative to the box bbox[6] in device memory: 2D 16
 // bits per axis, 3D 10 bits, shifted right by `shift` bits (coarser keys,
-// fewer radix passes).
+// fewer radix passes); iso: cubic cells of the box's longest extent.
 void morton_keys_f64_dev(const double4 *xyz, size_t n, int dim, const double *bbox, uint32_t *keys, uint32_t *vals,
-                         cudaStream_t st, int shift = 0);
+                         cudaStream_t st, int shift = 0, bool iso = false);
 // Volume points: 24-bit Morton keys (12 bits per axis in 2D, 8 in 3D), three radix passes.
 constexpr int kVolKeyBits = 24;
 inline int vol_key_shift(int dim) { return dim == 2 ? 32 - kVolKeyBits : 30 - kVolKeyBits; }

@@ -188,14 +188,21 @@ __device__ __forceinline__ uint32_t morton(double x, double y, double z, int dim
 // Morton keys with the box read from device memory (lo xyz, hi xyz), so that
 // no host round trip separates the box reduction from the keys.  The three
 // reciprocal extents are computed once per block (an FP64 division costs
-// several times the rest of a key).
+// several times the rest of a key).  iso: every axis takes the box's longest
+// extent (cubic cells; a thin box would otherwise get cells much finer
+// across it than along it, and runs of consecutive keys long boxes).
 __global__ void k_morton_f64_dev(const double4 *__restrict__ p, size_t n, int dim, const double *__restrict__ bb,
-                                 int shift, uint32_t *keys, uint32_t *vals) {
+                                 int shift, int iso, uint32_t *keys, uint32_t *vals) {
     __shared__ double s_lo[3], s_inv[3];
     if (threadIdx.x < 3) {
         const int a = threadIdx.x;
         s_lo[a] = bb[a];
-        s_inv[a] = (bb[a + 3] > bb[a]) ? 1.0 / (bb[a + 3] - bb[a]) : 0.0;
+        double e = bb[a + 3] - bb[a];
+        if (iso) {
+            e = fmax(bb[3] - bb[0], bb[4] - bb[1]);
+            if (dim == 3) e = fmax(e, bb[5] - bb[2]);
+        }
+        s_inv[a] = (e > 0.0) ? 1.0 / e : 0.0;
     }
     __syncthreads();
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -418,9 +425,9 @@ void radix_sort_pairs(uint32_t *keys, uint32_t *vals, size_t n, int key_bits, So
 }
 
 void morton_keys_f64_dev(const double4 *xyz, size_t n, int dim, const double *bbox, uint32_t *keys, uint32_t *vals,
-                         cudaStream_t st, int shift) {
+                         cudaStream_t st, int shift, bool iso) {
     if (!n) return;
-    k_morton_f64_dev<<<grid1(n, 256), 256, 0, st>>>(xyz, n, dim, bbox, shift, keys, vals);
+    k_morton_f64_dev<<<grid1(n, 256), 256, 0, st>>>(xyz, n, dim, bbox, shift, iso ? 1 : 0, keys, vals);
     RBFD_CUDA(cudaGetLastError());
 }
 
