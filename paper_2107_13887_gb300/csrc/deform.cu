@@ -792,7 +792,7 @@ void morton_order(rbfd_mesh *m, int64_t n, const double4 *vin, double4 *vsorted,
     const int nbb = std::min<int>(cdiv(n, 256), 256);
     k_bbox_partial_v<<<nbb, 256, 0, st>>>(vin, n, red);
     k_bbox_reduce<<<1, 192, 0, st>>>(red, nbb, box);
-    morton_keys_f64_dev(vin, n, dim, box, m->d_vkeys, orig, st, vol_key_shift(dim));
+    morton_keys_f64_dev(vin, n, dim, box, m->d_vkeys, orig, st, vol_key_shift(dim), true);  // (cubic cells)
     radix_sort_pairs(m->d_vkeys, orig, (size_t)n, kVolKeyBits, ss, st);
     k_gather_vol<<<cdiv(n, 256), 256, 0, st>>>(vin, orig, n, vsorted);
     RBFD_CUDA(cudaGetLastError());
@@ -1809,7 +1809,7 @@ void deform_noalloc_run(rbfd_mesh *m, int64_t n_v, const float *xyz_v, const flo
         k_bbox_idx<<<nbb, 256, 0, st>>>(vin, vlist, nV, m->d_red);
         k_bbox_reduce<<<1, 192, 0, st>>>(m->d_red, nbb, m->d_bbox);
         k_gather_vol<<<cdiv(nV, 256), 256, 0, st>>>(vin, vlist, nV, vpos);
-        morton_keys_f64_dev(vpos, nV, dim, m->d_bbox, vkeys, vorig, st, vol_key_shift(dim));
+        morton_keys_f64_dev(vpos, nV, dim, m->d_bbox, vkeys, vorig, st, vol_key_shift(dim), true);
         radix_sort_pairs(vkeys, vorig, (size_t)nV, kVolKeyBits, ss, st);
         k_gather_vol<<<cdiv(nV, 256), 256, 0, st>>>(vpos, vorig, nV, vin);  // vin := sorted points
         k_gather_u32<<<cdiv(nV, 256), 256, 0, st>>>(vlist, vorig, nV, vflag);
