@@ -1187,12 +1187,12 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     rest.add(m->d_pb_key, std::max(m->n_pb, 1024));
     rest.add(m->d_pb_idx, std::max(m->n_pb, 1024));
     if (m->opt.prune && m->n_pb <= kPfxMax) {
-        rest.add(m->d_bnd, (size_t)6 * 4 * m->n_pb);
+        rest.add(m->d_bnd, (size_t)2 * 4 * m->n_pb);
         rest.add(m->d_wbox, (size_t)2 * 4 * m->n_pb);
         rest.add(m->d_rev, (size_t)(cap + 1) * m->n_pb);
         rest.add(m->d_rev_cnt, cap + 1);
     }
-    rest.add(m->d_pred, (size_t)4 * kMaxPersistCTAs);
+    rest.add(m->d_pred, (size_t)4 * kMaxPersistCTAs + 8);
     rest.add(m->d_nz_k, cap + 1);
     rest.add(m->d_nz_v, cap + 1);
     rest.add(m->d_lvl_hist, m->n_levels_req);

@@ -213,11 +213,12 @@ struct rbfd_mesh {
     int *d_pb_idx = nullptr;
     // pruned list sweep (meshes of at most kPfxMax point blocks): per step
     // parity and warp of points (32 points, 4 per point block) the warp's max
-    // |E| at its last sweep, the bound accumulated since, the largest
-    // sum_c phi |alpha_c| at its points then ([2][3][4 n_pb]); each warp's box
+    // |E| at its last sweep (rounded up, down), the bound accumulated since,
+    // the largest sum_c phi |alpha_c| at its points then, in FP32
+    // ([2][4 n_pb]); each warp's box
     // in FP32 rounded outward ([4 n_pb][lo, hi]); the point blocks listing
     // each control ([cap + 1][n_pb], counts [cap + 1])
-    double *d_bnd = nullptr;
+    float4 *d_bnd = nullptr;
     float4 *d_wbox = nullptr;
     uint32_t *d_rev = nullptr;
     uint32_t *d_rev_cnt = nullptr;
@@ -236,7 +237,7 @@ struct rbfd_mesh {
     int batch_ctas_cap = 0;          // set by the batch calls: blocks this mesh may use
     int batch_share = 0;             // meshes whose greedy runs beside this one (batch calls, server)
     rbfd::GridBarrier *d_bar = nullptr;
-    double *d_pred = nullptr;       // [kMaxPersistCTAs][4] per-block y.y, y.w
+    double *d_pred = nullptr;       // [kMaxPersistCTAs][4] per-block y.y, y.w; then the pivot and w_n (8)
     // Newton-basis launch (made on first use): V[k][i] = v_k(x_i) for k < newton_cols
     int newton_cols = 0;
     double *d_V = nullptr;

@@ -77,17 +77,19 @@ struct PersistArgs {
     int pfx_max;                   // balanced sweep items up to this many point blocks (<= kPfxMax)
     int chunk_target;              // controls per sweep item the chunking aims at
     // pruned sweep (balanced items only), per warp of points w (32 points,
-    // w = 4 pb + warp): bnd[(parity * 3 + q) * 4 n_pb + w] with q = 0 the
-    // warp's max |E| over unselected points at its last sweep, 1 the bound
-    // on how far any |E| of the warp has moved since, 2 the largest
-    // sum_c phi |alpha_c|_1 at its points then; wbox[2 w], [2 w + 1] the
-    // warp's box in FP32 rounded outward; rev[k * n_pb + i] the point blocks
-    // whose list holds control k (rev_cnt[k] of them); err_u the relative
-    // rounding of one operation of the sweep's arithmetic, with margin;
-    // marg bounds the FP32 rounding of a control-to-box distance
+    // w = 4 pb + warp): bnd[parity * 4 n_pb + w] = {M rounded up, M rounded
+    // down, acc, A} in FP32 (every block evaluates every warp's bounds each
+    // step: in FP64 that arithmetic alone took 40 us per step on the FP64
+    // pipe), with M the warp's max |E| over unselected points at its last
+    // sweep, acc the bound on how far any |E| of the warp has moved since, A
+    // the largest sum_c phi |alpha_c|_1 at its points then; wbox[2 w], [2 w +
+    // 1] the warp's box in FP32 rounded outward; rev[k * n_pb + i] the point
+    // blocks whose list holds control k (rev_cnt[k] of them); err_u the
+    // relative rounding of one operation of the sweep's arithmetic, with
+    // margin; marg bounds the FP32 rounding of a control-to-box distance
     int prune;
-    double err_u;
-    double *bnd;
+    float err_u, S0f;
+    float4 *bnd;
     const float4 *wbox;
     float marg;
     uint32_t *rev, *rev_cnt;
@@ -101,15 +103,18 @@ struct PersistArgs {
 // error err_u on sums of at most A + 2 acc: the weights moved by at most
 // sqrt(3) acc in phi-weighted 1-norm), plus the subtraction from dS_l
 // (|dS_l| <= S0).
-__device__ __forceinline__ void warp_bounds(const PersistArgs &a, const double *bst, int w, int cnt, int nch,
-                                            double &lo, double &hi) {
-    const int n_w = 4 * a.n_pb;
-    const double M = __ldcg(bst + w);
-    const double acc = __ldcg(bst + n_w + w) * (1.0 + 1e-12);
-    const double A = __ldcg(bst + 2 * n_w + w);
-    const double err = (double)(cnt + 2 * nch + 16) * a.err_u * (A + 2.0 * acc + a.S0);
-    lo = M - acc - 2.0 * err;
-    hi = M + acc + 2.0 * err;
+// (All in FP32 with margins: acc is a sum of at most cap < 2^16 FP32
+// atomic additions, each rounded within 2^-24 of the running sum, so 2^-8
+// covers it; every other operation here is within 2^-24, covered by the
+// 2^-20 factors.)
+__device__ __forceinline__ void warp_bounds(const PersistArgs &a, const float4 *bst, int w, int cnt, int nch,
+                                            float &lo, float &hi) {
+    const float4 s = __ldcg(bst + w);
+    const float acc = s.z * (1.0f + 0x1p-8f);
+    const float err = (float)(cnt + 2 * nch + 16) * a.err_u * (s.w + 2.0f * acc + a.S0f) * (1.0f + 0x1p-20f);
+    const float mv = (acc + 2.0f * err) * (1.0f + 0x1p-20f);
+    lo = s.y * (1.0f - 0x1p-20f) - mv;
+    hi = (s.x + mv) * (1.0f + 0x1p-20f);
 }
 
 // A control at x (FP32, absolute) moved the weights by inc / |phi| times
@@ -117,7 +122,7 @@ __device__ __forceinline__ void warp_bounds(const PersistArgs &a, const double *
 // bound of every warp of point block t within R of x (the distance shrunk by
 // marg for the FP32 rounding).
 template <int BASIS>
-__device__ __forceinline__ void push_bound(const PersistArgs &a, double *acc, int t, float3 x, double inc,
+__device__ __forceinline__ void push_bound(const PersistArgs &a, float4 *bst, int t, float3 x, float inc,
                                            float invR) {
 #pragma unroll
     for (int w4 = 0; w4 < 4; ++w4) {
@@ -128,7 +133,7 @@ __device__ __forceinline__ void push_bound(const PersistArgs &a, double *acc, in
         const float dz = fmaxf(fmaxf(lo.z - x.z, x.z - hi.z), 0.0f);
         const float d = fmaxf(sqrtf(dx * dx + dy * dy + dz * dz) - a.marg, 0.0f);
         const float f = phi_f32_upper<BASIS>(d * invR);
-        if (f > 0.0f) atomicAdd(&acc[w], inc * (double)f);
+        if (f > 0.0f) atomicAdd(&bst[w].z, inc * f * (1.0f + 0x1p-20f));
     }
 }
 
@@ -245,8 +250,8 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
         const bool balanced = a.n_pb <= a.pfx_max;
         // bounds of this step (written by the last) and of the next
         const int n_w = 4 * a.n_pb;
-        const double *bcur = keep_bounds ? a.bnd + (size_t)((guard & 1) * 3) * n_w : nullptr;
-        double *bnext = keep_bounds ? a.bnd + (size_t)(((guard & 1) ^ 1) * 3) * n_w : nullptr;
+        const float4 *bcur = keep_bounds ? a.bnd + (size_t)(guard & 1) * n_w : nullptr;
+        float4 *bnext = keep_bounds ? a.bnd + (size_t)((guard & 1) ^ 1) * n_w : nullptr;
         const bool prune_now = keep_bounds && guard > 0;  // (the launch's first step sweeps every warp)
         int n_items = a.n_pb * nch;
         int n_swept = a.n_pb;
@@ -254,25 +259,25 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
         // largest lower bound: the warp attaining that is swept and finds at
         // least as much, so the argmax and the stop test are those of a full
         // sweep.  A point block is swept if one of its warps is.
-        double LB = -INFINITY;
+        float LB = -INFINITY;
         if (balanced) {
             const int per = (a.n_pb + kT - 1) / kT;
             const int b0 = min(a.n_pb, tid * per), b1 = min(a.n_pb, b0 + per);
             if (prune_now) {
-                double lmax = -INFINITY;
+                float lmax = -INFINITY;
                 for (int b = b0; b < b1; ++b) {
                     const int cb = (int)ldcg_u32(&a.nb_cnt[b]);
                     for (int w4 = 0; w4 < 4; ++w4) {
-                        double lo, hi;
+                        float lo, hi;
                         warp_bounds(a, bcur, 4 * b + w4, cb, nch, lo, hi);
-                        lmax = fmax(lmax, lo);
+                        lmax = fmaxf(lmax, lo);
                     }
                 }
-                for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+                for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
                 if (lane == 0) sk[warp] = lmax;
                 if (tid == 0) s_nsw = 0;
                 __syncthreads();
-                LB = fmax(fmax(sk[0], sk[1]), fmax(sk[2], sk[3]));
+                LB = (float)fmax(fmax(sk[0], sk[1]), fmax(sk[2], sk[3]));
                 __syncthreads();
             }
             unsigned mine = 0, swept = 0, skip_w = 0;
@@ -285,14 +290,12 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                     int act = 0;
                     for (int w4 = 0; w4 < 4; ++w4) {
                         const int w = 4 * b + w4;
-                        double lo, hi;
+                        float lo, hi;
                         warp_bounds(a, bcur, w, cb, nch, lo, hi);
                         if (hi >= LB) {
                             ++act;
                         } else if (blockIdx.x == 0) {  // the warp's state carries over to the next step
                             bnext[w] = __ldcg(bcur + w);
-                            bnext[n_w + w] = __ldcg(bcur + n_w + w);
-                            bnext[2 * n_w + w] = __ldcg(bcur + 2 * n_w + w);
                             const int64_t p0 = (int64_t)w * 32;
                             skip_pairs += (unsigned long long)max((int64_t)0, min((int64_t)32, a.n_s - p0)) *
                                           (unsigned long long)cb;
@@ -412,7 +415,7 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
             // (the same decision as in the prefix above: same inputs)
             bool wact = true;
             if (prune_now) {
-                double blo, bhi;
+                float blo, bhi;
                 warp_bounds(a, bcur, 4 * pb + warp, cnt, nch, blo, bhi);
                 wact = bhi >= LB;
             }
@@ -556,10 +559,9 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                         sm = fmax(sm, __shfl_xor_sync(0xffffffffu, sm, o));
                     }
                     if (lane == 0) {
-                        const int w = 4 * pb + warp;
-                        bnext[w] = km > 0.0 ? sqrt(km) : 0.0;
-                        bnext[n_w + w] = 0.0;
-                        bnext[2 * n_w + w] = sm * (1.0 + (double)(cnt + 16) * 0x1p-22);
+                        const double Mw = km > 0.0 ? sqrt(km) : 0.0;
+                        bnext[4 * pb + warp] = make_float4(__double2float_ru(Mw), __double2float_rd(Mw), 0.0f,
+                                                           __double2float_ru(sm * (1.0 + (double)(cnt + 16) * 0x1p-22)));
                     }
                 }
                 block_argmax(key, orig, sk, si);
@@ -735,7 +737,7 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
             // c_n's own warp has lost the point its maximum was taken at: no
             // lower bound from it until it is swept again (which its infinite
             // bound forces)
-            if (keep_bounds && first_block) bnext[n_w + c / 32] = INFINITY;
+            if (keep_bounds && first_block) bnext[c / 32].z = INFINITY;
         }
         double yy = 0, yw0 = 0, yw1 = 0, yw2 = 0;
         for (int j = blockIdx.x * 4 + warp; j < n; j += P * 4) {
@@ -772,10 +774,16 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
         }
         __syncthreads();
         if (tid < 4) a.red[blockIdx.x * 4 + tid] = sred[0][tid] + sred[1][tid] + sred[2][tid] + sred[3][tid];
-        RBFD_SYNC(2)
-
-        // ------------------------------------------------ phase 4: G row n (= G^T column n), alpha
-        {
+        // The last block here sums every block's partial y.y, y.w (in block
+        // order: the same sums whichever block it is) and derives the pivot
+        // and w_n once for the grid, in red[4 P ...]: on GB300's FP64 pipe
+        // that reduction repeated in every block cost about 13 us per step.
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) s_glast = atomicAdd(&a.st->red_done, 1u) == P - 1;
+        __syncthreads();
+        if (s_glast) {
+            __threadfence();
             double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
             for (unsigned b = tid; b < P; b += kT) {
                 v0 += ldcg_d(&a.red[b * 4 + 0]);
@@ -794,11 +802,26 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                 scol[warp][3] = v3;
             }
             __syncthreads();
+            if (tid == 0) {
+                double r4[4];
+                for (int q = 0; q < 4; ++q) r4[q] = ((scol[0][q] + scol[1][q]) + scol[2][q]) + scol[3][q];
+                const double l2 = 1.0 - r4[0];  // phi(0) = 1 for every Wendland function
+                const double l = sqrt(l2);
+                const double4 bc = a.cur[c];
+                double *out = a.red + 4 * (size_t)P;
+                out[0] = l2;
+                out[1] = l;
+                out[2] = (bc.x - r4[1]) / l;
+                out[3] = (bc.y - r4[2]) / l;
+                out[4] = (bc.z - r4[3]) / l;
+                a.st->red_done = 0;
+            }
         }
-        double r4[4];
-        for (int q = 0; q < 4; ++q) r4[q] = ((scol[0][q] + scol[1][q]) + scol[2][q]) + scol[3][q];
-        __syncthreads();
-        const double l2 = 1.0 - r4[0];  // phi(0) = 1 for every Wendland function
+        RBFD_SYNC(2)
+
+        // ------------------------------------------------ phase 4: G row n (= G^T column n), alpha
+        const double *piv = a.red + 4 * (size_t)P;
+        const double l2 = ldcg_d(piv);
         if (!(l2 > a.piv_tol_per_n * (n + 1))) {
             if (first_block) {
                 a.st->status = RBFD_ESINGULAR;
@@ -807,9 +830,7 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
             }
             RBFD_EXIT()
         }
-        const double l = sqrt(l2);
-        const double4 bc = a.cur[c];
-        const double wn0 = (bc.x - r4[1]) / l, wn1 = (bc.y - r4[2]) / l, wn2 = (bc.z - r4[3]) / l;
+        const double l = ldcg_d(piv + 1), wn0 = ldcg_d(piv + 2), wn1 = ldcg_d(piv + 3), wn2 = ldcg_d(piv + 4);
         double *Grow = a.G + (size_t)n * a.cap;
         if (first_block) {
             Grow[n] = 1.0 / l;
@@ -830,12 +851,12 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
             const int k = r * W + ((r & 1) ? W - 1 - gw : gw);
             if (k >= n_k) continue;
             if (k == n) {  // (only with pruning)
-                const double inc = wnorm / l;
+                const float inc = __double2float_ru(wnorm / l);
                 const int rc = (int)ldcg_u32(&a.rev_cnt[k]);
                 const uint32_t *rv = a.rev + (size_t)k * a.n_pb;
                 const float4 xk = ldcg_f4(&a.cdf[k]);
                 for (int q = lane; q < rc; q += 32)
-                    push_bound<BASIS>(a, bnext + n_w, (int)ldcg_u32(rv + q), make_float3(xk.x, xk.y, xk.z), inc,
+                    push_bound<BASIS>(a, bnext, (int)ldcg_u32(rv + q), make_float3(xk.x, xk.y, xk.z), inc,
                                       invR.hi);
                 continue;
             }
@@ -873,12 +894,12 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
             for (; j < n; j += 32) s0 = fma(ldcg_d(trow + j), ldcg_d(a.y + j), s0);
             const double t = warp_sum_d((s0 + s1) + (s2 + s3));
             if (keep_bounds) {
-                const double inc = wnorm * fabs(t / l);
+                const float inc = __double2float_ru(wnorm * fabs(t / l));
                 const int rc = (int)ldcg_u32(&a.rev_cnt[k]);
                 const uint32_t *rv = a.rev + (size_t)k * a.n_pb;
                 const float4 xk = ldcg_f4(&a.cdf[k]);
                 for (int q = lane; q < rc; q += 32)
-                    push_bound<BASIS>(a, bnext + n_w, (int)ldcg_u32(rv + q), make_float3(xk.x, xk.y, xk.z), inc,
+                    push_bound<BASIS>(a, bnext, (int)ldcg_u32(rv + q), make_float3(xk.x, xk.y, xk.z), inc,
                                       invR.hi);
             }
             if (lane == 0) {
@@ -972,6 +993,7 @@ void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
     // (the completion counters start at zero even after a launch that ended early)
     RBFD_CUDA(cudaMemsetAsync(a.pb_done, 0, sizeof(unsigned) * (size_t)m->n_pb, m->stream));
     RBFD_CUDA(cudaMemsetAsync(a.grp_done, 0, sizeof(unsigned) * (size_t)m->n_pb * a.max_grp, m->stream));
+    RBFD_CUDA(cudaMemsetAsync(&m->d_st->red_done, 0, sizeof(unsigned), m->stream));
     a.pb_key = m->d_pb_key;
     a.pb_idx = m->d_pb_idx;
     a.bar = m->d_bar;
@@ -990,7 +1012,8 @@ void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
     a.prune = (m->opt.prune && m->d_bnd && m->d_wbox && m->n_pb <= a.pfx_max) ? 1 : 0;
     // relative rounding per operation: FP64 2^-53, double-float about 2^-44;
     // a factor 16 of margin on each
-    a.err_u = m->opt.precision == RBFD_FP64 ? 0x1p-49 : 0x1p-40;
+    a.err_u = m->opt.precision == RBFD_FP64 ? 0x1p-49f : 0x1p-40f;
+    a.S0f = (float)(m->S0 * (1.0 + 0x1p-20));
     a.bnd = m->d_bnd;
     a.wbox = m->d_wbox;
     {
