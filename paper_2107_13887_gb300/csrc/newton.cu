@@ -1091,7 +1091,10 @@ void newton_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
     }
     a.piv_tol_per_n = 8.0 * 1.1102230246251565e-16;
     a.piv_tol_df_per_n = 5.684341886080802e-14;  // 2^-44
-    a.switch_ratio = 3.0;
+    // (the pruned list sweep made the hand-over pay earlier: on the 60k wing
+    // ratios 1.25 to 2 gave 10.46 s against 10.70 s at 3, and below 1.25
+    // level 0 left the Newton basis too, 10.72 s)
+    a.switch_ratio = 2.0;
     a.switch_work = 2e7;  // ~30 us of FP64 multiply-adds per step
     if (const char *v = std::getenv("RBFD_NEWTON_SWITCH")) a.switch_ratio = std::strtod(v, nullptr);
     a.xs = m->d_xs;
