@@ -337,6 +337,24 @@ def roofline_of(stats, dim, sms, sm_clock_hz, precision_mixed):
     frac_pipes = None
     if precision_mixed and p_ms > 0:
         frac_pipes = (p_pairs * OPS_PER_PAIR_DF[dim] / peak + grow_fma / fp64_fma_peak) / (p_ms / 1e3)
+    # a2 (the sweep and the step's decision) and a4 (the growth: y = G phi and
+    # the rows of G) apart, each over the wall time of its phases in the
+    # launch (block 0's work plus its wait at the phase's barrier).  In FP64
+    # mode the sweep's pairs run on the FP64 pipe: its survey-unit operations
+    # are set against that pipe's instruction rate.
+    a2_s = (phases[0] + phases[1]) / 1e3
+    a4_s = (phases[4] + phases[5] + phases[6] + phases[7]) / 1e3
+    rows_s = (phases[6] + phases[7]) / 1e3
+    a2_peak = peak if precision_mixed else fp64_fma_peak
+    by_phase = {
+        "a2_sweep": {"s": round(a2_s, 3), "pairs_useful": int(p_pairs),
+                     "frac": round(p_pairs * OPS_PER_PAIR_FP32[dim] / a2_s / a2_peak, 5) if a2_s > 0 else None,
+                     "frac_df_ops": round(p_pairs * OPS_PER_PAIR_DF[dim] / a2_s / peak, 5)
+                     if a2_s > 0 and precision_mixed else None,
+                     "peak": "FP32 issue" if precision_mixed else "FP64 instructions (152 x 2 per clock)"},
+        "a4_grow": {"s": round(a4_s, 3), "g_rows_s": round(rows_s, 3), "g_rows_fp64_fma": int(grow_fma),
+                    "g_rows_frac": round(grow_fma / rows_s / fp64_fma_peak, 5) if rows_s > 0 else None},
+    }
     return {
         "bound": "alu", "kernel": names[dom],
         "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
@@ -352,6 +370,7 @@ def roofline_of(stats, dim, sms, sm_clock_hz, precision_mixed):
         # block 0 of the persistent launch, summed over levels and steps:
         # [2p] work of phase p (sweep, argmax + phi column, G phi, G row), [2p+1] wait at its barrier
         "persist_phase_ms": phases,
+        "persist_by_phase": by_phase,
         "persist_pipes": {"grow_fp64_fma": int(grow_fma),
                           "fp64_fma_peak_per_s": fp64_fma_peak,
                           "frac": round(frac_pipes, 5) if frac_pipes is not None else None},
