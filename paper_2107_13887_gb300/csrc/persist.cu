@@ -107,9 +107,8 @@ struct PersistArgs {
 // atomic additions, each rounded within 2^-24 of the running sum, so 2^-8
 // covers it; every other operation here is within 2^-24, covered by the
 // 2^-20 factors.)
-__device__ __forceinline__ void warp_bounds(const PersistArgs &a, const float4 *bst, int w, int cnt, int nch,
-                                            float &lo, float &hi) {
-    const float4 s = __ldcg(bst + w);
+__device__ __forceinline__ void warp_bounds(const PersistArgs &a, const float4 s, int cnt, int nch, float &lo,
+                                            float &hi) {
     const float acc = s.z * (1.0f + 0x1p-8f);
     const float err = (float)(cnt + 2 * nch + 16) * a.err_u * (s.w + 2.0f * acc + a.S0f) * (1.0f + 0x1p-20f);
     const float mv = (acc + 2.0f * err) * (1.0f + 0x1p-20f);
@@ -180,6 +179,7 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
     __shared__ unsigned char s_hits[4][kTile];
     __shared__ unsigned s_pfx[kPfxMax + 1];
     __shared__ unsigned s_order[kPfxMax];  // pruned steps: point block | chunks << 16, in item order
+    __shared__ unsigned s_act[kPfxMax / 8];  // pruned steps: one bit per warp of points, set if it is swept
     __shared__ int s_item;
     __shared__ unsigned s_nsw;
 
@@ -263,15 +263,19 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
         if (balanced) {
             const int per = (a.n_pb + kT - 1) / kT;
             const int b0 = min(a.n_pb, tid * per), b1 = min(a.n_pb, b0 + per);
+            unsigned long long skip_pairs = 0;
+            unsigned skip_w = 0;
             if (prune_now) {
+                // Two passes over the warps' states, consecutive lanes on
+                // consecutive warps (coalesced: with a thread per point block
+                // the loads took 11 us a pass, every block reading): LB, then
+                // one bit per warp in s_act.  Block 0 carries a skipped warp's
+                // state over to the next step.
                 float lmax = -INFINITY;
-                for (int b = b0; b < b1; ++b) {
-                    const int cb = (int)ldcg_u32(&a.nb_cnt[b]);
-                    for (int w4 = 0; w4 < 4; ++w4) {
-                        float lo, hi;
-                        warp_bounds(a, bcur, 4 * b + w4, cb, nch, lo, hi);
-                        lmax = fmaxf(lmax, lo);
-                    }
+                for (int w = tid; w < n_w; w += kT) {
+                    float lo, hi;
+                    warp_bounds(a, __ldcg(bcur + w), (int)ldcg_u32(&a.nb_cnt[w >> 2]), nch, lo, hi);
+                    lmax = fmaxf(lmax, lo);
                 }
                 for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
                 if (lane == 0) sk[warp] = lmax;
@@ -279,29 +283,34 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                 __syncthreads();
                 LB = (float)fmax(fmax(sk[0], sk[1]), fmax(sk[2], sk[3]));
                 __syncthreads();
-            }
-            unsigned mine = 0, swept = 0, skip_w = 0;
-            unsigned bc0 = 0, bc1 = 0, bc2 = 0, bc3 = 0;
-            unsigned long long skip_pairs = 0;
-            for (int b = b0; b < b1; ++b) {
-                const int cb = (int)ldcg_u32(&a.nb_cnt[b]);
-                unsigned ub = (unsigned)min(nch, max(1, (cb + cl - 1) / cl));
-                if (prune_now) {
-                    int act = 0;
-                    for (int w4 = 0; w4 < 4; ++w4) {
-                        const int w = 4 * b + w4;
+                for (int w0 = warp * 32; w0 < n_w; w0 += kT) {
+                    const int w = w0 + lane;
+                    bool act = false;
+                    if (w < n_w) {
+                        const float4 s = __ldcg(bcur + w);
+                        const int cb = (int)ldcg_u32(&a.nb_cnt[w >> 2]);
                         float lo, hi;
-                        warp_bounds(a, bcur, w, cb, nch, lo, hi);
-                        if (hi >= LB) {
-                            ++act;
-                        } else if (blockIdx.x == 0) {  // the warp's state carries over to the next step
-                            bnext[w] = __ldcg(bcur + w);
-                            const int64_t p0 = (int64_t)w * 32;
-                            skip_pairs += (unsigned long long)max((int64_t)0, min((int64_t)32, a.n_s - p0)) *
+                        warp_bounds(a, s, cb, nch, lo, hi);
+                        act = hi >= LB;
+                        if (!act && blockIdx.x == 0) {
+                            bnext[w] = s;
+                            skip_pairs += (unsigned long long)max((int64_t)0, min((int64_t)32, a.n_s - (int64_t)w * 32)) *
                                           (unsigned long long)cb;
                             ++skip_w;
                         }
                     }
+                    const unsigned bits = __ballot_sync(0xffffffffu, act);
+                    if (lane == 0) s_act[w0 >> 5] = bits;
+                }
+                __syncthreads();
+            }
+            unsigned mine = 0, swept = 0;
+            unsigned bc0 = 0, bc1 = 0, bc2 = 0, bc3 = 0;
+            for (int b = b0; b < b1; ++b) {
+                const int cb = (int)ldcg_u32(&a.nb_cnt[b]);
+                unsigned ub = (unsigned)min(nch, max(1, (cb + cl - 1) / cl));
+                if (prune_now) {
+                    const int act = __popc((s_act[b >> 3] >> ((b & 7) * 4)) & 0xFu);
                     if (act == 0) ub = 0;
                     else ++swept;
                     // (bucket of the item order: 4 active warps first, then 3, 2, at most 1)
@@ -317,7 +326,7 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
             }
             if (prune_now) {
                 if (swept) atomicAdd(&s_nsw, swept);
-                if (blockIdx.x == 0 && skip_w) {
+                if (blockIdx.x == 0 && skip_w) {  // (counters of the skipped work)
                     atomicAdd(&a.pairs[11], skip_pairs);
                     atomicAdd(&a.pairs[12], (unsigned long long)skip_w);
                 }
@@ -413,12 +422,8 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
             unsigned useful = 0;
             // this warp's points are evaluated unless its bound skips them
             // (the same decision as in the prefix above: same inputs)
-            bool wact = true;
-            if (prune_now) {
-                float blo, bhi;
-                warp_bounds(a, bcur, 4 * pb + warp, cnt, nch, blo, bhi);
-                wact = bhi >= LB;
-            }
+            const int wsel = 4 * pb + warp;
+            const bool wact = !prune_now || ((s_act[wsel >> 5] >> (wsel & 31)) & 1u);
             double sabs64 = 0.0;  // sum_c phi |alpha_c|_1 at this point (pruning bounds)
             float sabs = 0.0f;
             float3 wlo, whi;
