@@ -6,7 +6,7 @@ DRAM traffic matters), the same kernels as the benchmark's workloads:
 
     python -m paper_2107_13887_gb300.profile_cases persist    # k_greedy_persist, k_greedy_newton, k_vol_sweep_f32
     python -m paper_2107_13887_gb300.profile_cases worklist   # k_vol_worklist over four uneven wings
-    python -m paper_2107_13887_gb300.profile_cases persist_mid  # k_greedy_persist, 760 blocks
+    python -m paper_2107_13887_gb300.profile_cases persist_mid  # k_greedy_persist, 304 blocks
 
 persist:  the swept wing of the benchmark at 1/15 of its surface (100 x 40 =
           4,000 points, 400k volume points), its three levels to 1e-5 in the
@@ -16,8 +16,8 @@ persist:  the swept wing of the benchmark at 1/15 of its surface (100 x 40 =
 persist_mid: the swept wing at a quarter of the benchmark's surface (200 x
           75 = 15,000 points), the three levels in the persistent list sweep
           alone with at most 6,000 controls per level (G and G^T 0.6 GB):
-          the third launch (R = 0.1, 6,000 steps) runs on the full grid of
-          760 blocks, the regime of the benchmark's last level.
+          the third launch (R = 0.1, 6,000 steps) runs 304 blocks (118 point
+          blocks) with G rows of up to 6,000 entries.
 worklist: the four-wing family at 1/25 of its surfaces (1.2k to 10k points)
           and 60 layers (72k to 600k volume points each, 1.2M in all), two
           levels to 1e-3, the volume updates of all four in one work-list
