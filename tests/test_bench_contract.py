@@ -54,3 +54,33 @@ def test_clock_sampler_parses_nvidia_smi_lines():
     assert s.stop()["reasons"] == ["hw_thermal_slowdown"]
     s.lines = []
     assert s.stop() is None
+
+
+def test_roofline_splits_the_persistent_launch_by_phase():
+    """The dominant kernel's roofline: survey-unit pair work against the FP32
+    issue rate, the two-pipe fraction (double-float pairs at the FP32 rate
+    plus the G rows' FP64 multiply-adds at the FP64 rate, over the launch's
+    time), and the sweep (a2) and growth (a4) apart over their phases' time."""
+    import bench
+
+    st = dict(persist_ms=10000.0, persist_launches=2, sweep_pairs_useful=4e10, newton_ms=500.0,
+              newton_launches=3, newton_pairs_useful=1e9, vol_ms=100.0, vol_launches=3, vol_pairs_useful=4e9,
+              sweep_ms=0.0, sweep_launches=0, persist_grow_fma=2e12,
+              persist_phase_ms=[1500.0, 1500.0, 0.0, 0.0, 600.0, 400.0, 5000.0, 1000.0])
+    sms, clk = 152, 2.07e9
+    fp32_peak = sms * 128 * clk
+    fp64_fma = sms * 2 * clk
+    r = bench.roofline_of([st], 3, sms, clk, True)
+    assert r["kernel"].startswith("k_greedy_persist")
+    assert abs(r["frac"] - 4e10 * 16 / 10.0 / fp32_peak) < 1e-12
+    want = (4e10 * 284 / fp32_peak + 2e12 / fp64_fma) / 10.0
+    assert abs(r["persist_pipes"]["frac"] - round(want, 5)) < 1e-5
+    a2, a4 = r["persist_by_phase"]["a2_sweep"], r["persist_by_phase"]["a4_grow"]
+    assert a2["s"] == 3.0 and a4["s"] == 7.0 and a4["g_rows_s"] == 6.0
+    assert abs(a2["frac"] - round(4e10 * 16 / 3.0 / fp32_peak, 5)) < 1e-5
+    assert abs(a4["g_rows_frac"] - round(2e12 / 6.0 / fp64_fma, 5)) < 1e-5
+    # FP64 mode: the sweep's pairs run on the FP64 pipe
+    r = bench.roofline_of([st], 3, sms, clk, False)
+    a2 = r["persist_by_phase"]["a2_sweep"]
+    assert a2["frac_df_ops"] is None and abs(a2["frac"] - round(4e10 * 16 / 3.0 / fp64_fma, 5)) < 1e-5
+    assert r["persist_pipes"]["frac"] is None
