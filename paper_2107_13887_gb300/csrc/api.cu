@@ -787,10 +787,35 @@ int rbfd_greedy_batch(rbfd_mesh **meshes, int n) {
         }
     int rc = share_grid(meshes, n);
     if (rc != RBFD_OK) return rc;
+    // the meshes still in their greedy share the persistent blocks: a finished
+    // mesh's share goes to the others' next launches (on one device only)
+    std::atomic<int> active{n};
+    bool one_device = n > 1;
+    for (int i = 1; i < n; ++i) one_device = one_device && meshes[i]->device == meshes[0]->device;
+    if (one_device) {
+        int total = 0;
+        rc = guarded([&] { total = rbfd::persist_max_ctas(meshes[0]); });
+        if (rc != RBFD_OK) {
+            unshare_grid(meshes, n);
+            return rc;
+        }
+        for (int i = 0; i < n; ++i) {
+            meshes[i]->batch_active = &active;
+            meshes[i]->batch_total = total;
+        }
+    }
     rc = run_batch(n, [&](int i) {
+        struct Leave {  // (also when the greedy fails)
+            std::atomic<int> &a;
+            ~Leave() { a.fetch_sub(1); }
+        } leave{active};
         RBFD_CUDA(cudaSetDevice(meshes[i]->device));
         rbfd::greedy_run(meshes[i]);
     }, "rbfd_greedy_batch");
+    for (int i = 0; i < n; ++i) {
+        meshes[i]->batch_active = nullptr;
+        meshes[i]->batch_total = 0;
+    }
     unshare_grid(meshes, n);
     return rc;
 }

@@ -1605,19 +1605,29 @@ void greedy_run(rbfd_mesh *m, bool wait, bool warm) {
                     }
                 }
             }
-            if (!stopped && !split && (m->opt.engine == 0 || m->opt.engine == 2)) {
+            for (bool yielded = true; yielded && !stopped && !split && (m->opt.engine == 0 || m->opt.engine == 2);) {
                 const int maxc = std::min(persist_max_ctas(m), kMaxPersistCTAs);
                 if (maxc < 1) fail(RBFD_ECUDA, "persistent greedy kernel cannot be resident on this device");
                 // small meshes: few blocks keep the barriers cheap; large ones fill the GPU
                 int ctas = m->opt.grid_ctas > 0 ? m->opt.grid_ctas
                                                 : (m->n_pb <= 128 ? std::min(std::max(64, 4 * m->n_pb), 2 * 152)
                                                                   : std::min(4 * m->n_pb, 8 * 152));
-                if (m->batch_ctas_cap > 0) ctas = std::min(ctas, m->batch_ctas_cap);
+                // a batch's meshes share the blocks; once some have finished,
+                // the others' next launches take the freed share (their
+                // launches then yield every kYieldSteps steps to pick it up)
+                int max_steps = 0;
+                if (m->batch_active) {
+                    const int act = std::max(1, m->batch_active->load());
+                    ctas = std::min(ctas, std::max(1, m->batch_total / act));
+                    if (act > 1) max_steps = kYieldSteps;
+                } else if (m->batch_ctas_cap > 0) {
+                    ctas = std::min(ctas, m->batch_ctas_cap);
+                }
                 ctas = std::max(1, std::min(ctas, maxc));
                 RBFD_CUDA(cudaMemsetAsync(m->d_bar, 0, sizeof(GridBarrier), st));
                 NvtxRange nvtx_persist("rbfd persistent list sweep");
                 cudaEvent_t e0 = m->prof.begin(st);
-                persist_run_level(m, L.R, L.tau, ctas);
+                persist_run_level(m, L.R, L.tau, ctas, max_steps);
                 m->prof.end(kProfPersist, e0, st, 1);
                 volume_stage_enqueue(m);  // (a staged volume: while this level runs)
                 m->stats.persist_ctas = ctas;
@@ -1635,7 +1645,13 @@ void greedy_run(rbfd_mesh *m, bool wait, bool warm) {
                     m->stats.persist_grow_fma += tri(m->h_st->n) - tri(n);
                 }
                 n = m->h_st->n;
-                stopped = true;
+                yielded = m->h_st->handoff != 0;  // (stopped at the step limit: relaunch)
+                if (yielded) {
+                    RBFD_CUDA(cudaMemsetAsync(&m->d_st->stop, 0, sizeof(int), st));
+                    RBFD_CUDA(cudaMemsetAsync(&m->d_st->handoff, 0, sizeof(int), st));
+                } else {
+                    stopped = true;
+                }
             }
             // ... or separate launches per step, in batches (engine 1).  In
             // the surface split every step sweeps this rank's range of point

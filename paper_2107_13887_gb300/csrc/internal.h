@@ -2,6 +2,7 @@
 // the C ABI (api.cu) drives.  Not part of the public interface.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -235,6 +236,10 @@ struct rbfd_mesh {
     uint32_t *d_ckeys = nullptr;        // [cap + 1] control cell keys
     // persistent engine
     int batch_ctas_cap = 0;          // set by the batch calls: blocks this mesh may use
+    // rbfd_greedy_batch: the batch's meshes still in their greedy and the
+    // blocks they share (a finished mesh's share goes to the others)
+    std::atomic<int> *batch_active = nullptr;
+    int batch_total = 0;
     int batch_share = 0;             // meshes whose greedy runs beside this one (batch calls, server)
     rbfd::GridBarrier *d_bar = nullptr;
     double *d_pred = nullptr;       // [kMaxPersistCTAs][4] per-block y.y, y.w; then the pivot and w_n (8)
@@ -327,7 +332,10 @@ void newton_reserve(rbfd_mesh *m);
 bool newton_fits(rbfd_mesh *m, int ctas);
 void newton_run_level(rbfd_mesh *m, double R, double tau, int ctas);
 int persist_max_ctas(rbfd_mesh *m);
-void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas);
+// max_steps > 0: the launch ends after that many steps with st->handoff set
+// (the level goes on in the next launch)
+void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas, int max_steps = 0);
+constexpr int kYieldSteps = 1024;  // steps of a batch mesh's launch while other meshes still run
 // wait = false: the greedy returns once its work is queued; its last wait and
 // epilogue (level scalars, timing) happen in greedy_finish
 // warm = true: start every level from the previous run's controls and

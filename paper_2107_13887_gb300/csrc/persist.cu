@@ -76,6 +76,7 @@ struct PersistArgs {
     unsigned long long *item_ctr;  // the sweep's item counter (zero at launch)
     int pfx_max;                   // balanced sweep items up to this many point blocks (<= kPfxMax)
     int chunk_target;              // controls per sweep item the chunking aims at
+    int max_steps;                 // > 0: end the launch after that many steps (st->handoff = 1)
     // pruned sweep (balanced items only), per warp of points w (32 points,
     // w = 4 pb + warp): bnd[parity * 4 n_pb + w] = {M rounded up, M rounded
     // down, acc, A} in FP32 (every block evaluates every warp's bounds each
@@ -235,6 +236,16 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
         RBFD_SYNC(0)
     }
     for (int guard = 0; guard <= a.cap; ++guard) {
+        // (a step limit ends the launch here, between steps, every block
+        // alike; the host relaunches it from st->n)
+        if (a.max_steps > 0 && guard >= a.max_steps) {
+            if (blockIdx.x == 0 && tid == 0) {
+                a.st->n = n;
+                a.st->handoff = 1;
+                a.st->stop = 1;
+            }
+            RBFD_EXIT()
+        }
         // ------------------------------------------------ phase 1: sweep (+ the step's decision)
         // every block list is cut into chunks of at most cl controls, cl set by
         // the longest list, so that no point block holds the step back
@@ -951,7 +962,7 @@ int persist_max_ctas(rbfd_mesh *m) {
     return std::max(0, occ * sms);
 }
 
-void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
+void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas, int max_steps) {
     PersistArgs a{};
     a.n_s = m->n_s;
     a.n_pb = m->n_pb;
@@ -1012,6 +1023,7 @@ void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas) {
     if (const char *v = std::getenv("RBFD_TEST_SWEEP_ROUND_ROBIN")) a.pfx_max = std::atoi(v) != 0 ? 0 : kPfxMax;
     // controls per sweep item: shorter items balance the step's tail, longer
     // ones cost fewer partial sums (RBFD_SWEEP_CHUNK sets it, 16 to 1024)
+    a.max_steps = max_steps;
     a.chunk_target = 64;
     if (const char *v = std::getenv("RBFD_SWEEP_CHUNK")) a.chunk_target = std::max(16, std::min(1024, std::atoi(v)));
     a.prune = (m->opt.prune && m->d_bnd && m->d_wbox && m->n_pb <= a.pfx_max) ? 1 : 0;
