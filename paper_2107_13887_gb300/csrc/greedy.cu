@@ -1620,6 +1620,9 @@ void greedy_run(rbfd_mesh *m, bool wait, bool warm) {
                     const int act = std::max(1, m->batch_active->load());
                     ctas = std::min(ctas, std::max(1, m->batch_total / act));
                     if (act > 1) max_steps = kYieldSteps;
+                    // (test hook: a shorter step limit, to exercise the relaunches)
+                    if (const char *v = std::getenv("RBFD_TEST_YIELD_STEPS"); v && act > 1)
+                        max_steps = std::max(1, std::atoi(v));
                 } else if (m->batch_ctas_cap > 0) {
                     ctas = std::min(ctas, m->batch_ctas_cap);
                 }

@@ -712,6 +712,33 @@ def test_run_jobs_device_radii_and_capped_job():
         m.close()
 
 
+def test_batch_relaunches_match_single_meshes(monkeypatch):
+    """In a batch, a mesh's persistent launch ends every few steps while other
+    meshes still run and is relaunched on the share of the blocks the
+    finished meshes left (test hook: every 7 steps).  The relaunched level
+    goes on from the state the launch left: the same controls as each mesh
+    alone, the weights within the rounding of a different block count."""
+    monkeypatch.setenv("RBFD_TEST_YIELD_STEPS", "7")
+    names = ["airfoil_horns_2lvl", "wing_ridge_2lvl", "airfoil_pitch_2lvl"]
+    cases = [CASES[n] for n in names]
+    single = []
+    for c in cases:
+        m = rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, engine=2)
+        m.greedy()
+        single.append(m.levels())
+        m.close()
+    ms = [rbfd.Mesh(c.xyz_s, c.dS, c.R, c.eps, engine=2, profile=True) for c in cases]
+    rbfd.greedy_batch(ms)
+    launches = [m.stats()["persist_launches"] for m in ms]
+    for m, lv1 in zip(ms, single):
+        for x, y in zip(m.levels(), lv1):
+            assert np.array_equal(x.idx, y.idx)
+            assert np.abs(x.alpha - y.alpha).max() <= 1e-6 * max(np.abs(y.alpha).max(), 1e-300)
+        m.close()
+    # (the first meshes to finish leave the others relaunching)
+    assert max(launches) > max(len(lv) for lv in single)
+
+
 @pytest.mark.parametrize("precision", [rbfd.FP64, rbfd.MIXED], ids=["fp64", "mixed"])
 def test_batch_matches_single_meshes(precision):
     names = ["airfoil_horns_2lvl", "wing_ridge_2lvl", "airfoil_pitch_2lvl", "airfoil_bump_333"]
