@@ -6,24 +6,34 @@
 //   phase 1  surface error sweep (Eq. 12): items (point block, chunk of its
 //            control list), the chunk length set by the longest list so that
 //            heavy blocks near the ice spread over many blocks; chunk partial
-//            sums -> scratch; the last chunk of each point block (atomic
-//            counter) reduces them in chunk order in FP64, forms
-//            E = dS_l - sum and the key |E|^2, and writes the block's argmax;
+//            sums -> scratch; the chunk partials are reduced in FP64 in a
+//            fixed order, in two levels (groups of 16 chunks, then the
+//            groups; atomic counters find the last of each), and the last
+//            forms E = dS_l - sum and the key |E|^2 and writes the block's
+//            argmax;
 //            the last point block to finish (second counter) takes the step's
 //            decision: global argmax, stop test max|E|/S0 < tau_l in FP64,
 //            and, if the level goes on, the nonzeros of phi(|r_cn - r_ck|/R)
 //            (only controls on c_n's block list can be within R) and c_n.
+//            With pruning, only the warps of 32 points whose bounds show
+//            they may hold the argmax are swept (warp_bounds below); the
+//            items go out heaviest first.
 //   -- barrier --
 //   phase 3  c_n listed in every point block within R of it (after the
 //            barrier: no sweep reads the lists any more); y = G phi over the
 //            nonzeros of phi (one warp per row of the inverse factor
-//            G = L^{-1}); per-block partial sums of y.y, y.w.
+//            G = L^{-1}); per-block partial sums of y.y, y.w, which the last
+//            block sums into l = sqrt(1 - y.y) and w_n = (dS_l(c_n) - y.w) / l.
 //   -- barrier --
-//   phase 4  l = sqrt(1 - y.y), w_n = (dS_l(c_n) - y.w) / l; the new row
-//            g = -(y^T G) / l as one warp per column over the rows of the
-//            transposed copy G^T (contiguous reads); G row n, G^T column n,
-//            alpha += w_n g.
+//   phase 4  the new row g = -(y^T G) / l as one warp per column over the
+//            rows of the transposed copy G^T (contiguous reads), the columns
+//            dealt to the warps in snake order; G row n, G^T column n,
+//            alpha += w_n g; with pruning, the move bound of every warp near
+//            each updated control.
 //   -- barrier --
+//
+// A batch mesh's launch may end between steps after a step limit (st->handoff)
+// and be relaunched from st->n.
 //
 // The barrier is a counter plus generation word in global memory; a block
 // that waits longer than a fixed number of polls sets an error word and
