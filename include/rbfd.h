@@ -423,8 +423,11 @@ int rbfd_greedy_split(rbfd_mesh *m, int rank, int world, rbfd_maxloc_fn maxloc, 
  * chain of small, latency-bound steps (Section 3); independent meshes (several
  * ice shapes, several grids) run side by side: one host thread per mesh, each
  * on the mesh's own stream, the persistent launches sized so that they are
- * resident together.  Give every mesh its own stream (the default) for
- * overlap.  Returns the first failing mesh's status (RBFD_ENOTCONV only if no
+ * resident together.  On one device the meshes still in their greedy share
+ * the blocks: while several run, a mesh's persistent launch ends every 1,024
+ * steps and the next one takes the share that finished meshes left (the
+ * controls are those of the mesh alone; the weights agree to rounding).
+ * Give every mesh its own stream (the default) for overlap.  Returns the first failing mesh's status (RBFD_ENOTCONV only if no
  * mesh failed otherwise); every mesh that succeeded holds its results.
  */
 int rbfd_greedy_batch(rbfd_mesh **meshes, int n);
