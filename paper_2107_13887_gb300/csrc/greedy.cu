@@ -1188,6 +1188,7 @@ void mesh_prepare(rbfd_mesh *m, const double *xyz_s, const double *dS) {
     rest.add(m->d_pb_idx, std::max(m->n_pb, 1024));
     if (m->opt.prune && m->n_pb <= kPfxMax) {
         rest.add(m->d_bnd, (size_t)2 * 4 * m->n_pb);
+        rest.add(m->d_bacc, (size_t)2 * 4 * m->n_pb);
         rest.add(m->d_wbox, (size_t)2 * 4 * m->n_pb);
         rest.add(m->d_rev, (size_t)(cap + 1) * m->n_pb);
         rest.add(m->d_rev_cnt, cap + 1);

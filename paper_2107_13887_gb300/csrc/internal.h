@@ -220,6 +220,7 @@ struct rbfd_mesh {
     // in FP32 rounded outward ([4 n_pb][lo, hi]); the point blocks listing
     // each control ([cap + 1][n_pb], counts [cap + 1])
     float4 *d_bnd = nullptr;
+    double *d_bacc = nullptr;  // the bound accumulated since, summed in FP64 ([2][4 n_pb])
     float4 *d_wbox = nullptr;
     uint32_t *d_rev = nullptr;
     uint32_t *d_rev_cnt = nullptr;

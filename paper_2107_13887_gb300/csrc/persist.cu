@@ -101,6 +101,7 @@ struct PersistArgs {
     int prune;
     float err_u, S0f;
     float4 *bnd;
+    double *bacc;  // [parity * 4 n_pb + w]: the move bound acc, summed in FP64 (the .z of bnd is unused)
     const float4 *wbox;
     float marg;
     uint32_t *rev, *rev_cnt;
@@ -114,13 +115,14 @@ struct PersistArgs {
 // error err_u on sums of at most A + 2 acc: the weights moved by at most
 // sqrt(3) acc in phi-weighted 1-norm), plus the subtraction from dS_l
 // (|dS_l| <= S0).
-// (All in FP32 with margins: acc is a sum of at most cap < 2^16 FP32
-// atomic additions, each rounded within 2^-24 of the running sum, so 2^-8
-// covers it; every other operation here is within 2^-24, covered by the
-// 2^-20 factors.)
-__device__ __forceinline__ void warp_bounds(const PersistArgs &a, const float4 s, int cnt, int nch, float &lo,
-                                            float &hi) {
-    const float acc = s.z * (1.0f + 0x1p-8f);
+// (In FP32 with margins, but acc is summed in FP64 by atomic additions,
+// each within 2^-53 of the running sum: over fewer than 2^40 additions that
+// is within 2^-13, and acc is taken rounded up and raised by 2^-8; every
+// other operation here is within 2^-24, covered by the 2^-20 factors.  In
+// FP32 the sum itself would lose the small additions a far warp receives.)
+__device__ __forceinline__ void warp_bounds(const PersistArgs &a, const float4 s, double accd, int cnt, int nch,
+                                            float &lo, float &hi) {
+    const float acc = __double2float_ru(accd) * (1.0f + 0x1p-8f);
     const float err = (float)(cnt + 2 * nch + 16) * a.err_u * (s.w + 2.0f * acc + a.S0f) * (1.0f + 0x1p-20f);
     const float mv = (acc + 2.0f * err) * (1.0f + 0x1p-20f);
     lo = s.y * (1.0f - 0x1p-20f) - mv;
@@ -132,7 +134,7 @@ __device__ __forceinline__ void warp_bounds(const PersistArgs &a, const float4 s
 // bound of every warp of point block t within R of x (the distance shrunk by
 // marg for the FP32 rounding).
 template <int BASIS>
-__device__ __forceinline__ void push_bound(const PersistArgs &a, float4 *bst, int t, float3 x, float inc,
+__device__ __forceinline__ void push_bound(const PersistArgs &a, double *acc, int t, float3 x, float inc,
                                            float invR) {
 #pragma unroll
     for (int w4 = 0; w4 < 4; ++w4) {
@@ -143,7 +145,7 @@ __device__ __forceinline__ void push_bound(const PersistArgs &a, float4 *bst, in
         const float dz = fmaxf(fmaxf(lo.z - x.z, x.z - hi.z), 0.0f);
         const float d = fmaxf(sqrtf(dx * dx + dy * dy + dz * dz) - a.marg, 0.0f);
         const float f = phi_f32_upper<BASIS>(d * invR);
-        if (f > 0.0f) atomicAdd(&bst[w].z, inc * f * (1.0f + 0x1p-20f));
+        if (f > 0.0f) atomicAdd(&acc[w], (double)(inc * f * (1.0f + 0x1p-20f)));
     }
 }
 
@@ -273,6 +275,8 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
         const int n_w = 4 * a.n_pb;
         const float4 *bcur = keep_bounds ? a.bnd + (size_t)(guard & 1) * n_w : nullptr;
         float4 *bnext = keep_bounds ? a.bnd + (size_t)((guard & 1) ^ 1) * n_w : nullptr;
+        const double *acur = keep_bounds ? a.bacc + (size_t)(guard & 1) * n_w : nullptr;
+        double *anext = keep_bounds ? a.bacc + (size_t)((guard & 1) ^ 1) * n_w : nullptr;
         const bool prune_now = keep_bounds && guard > 0;  // (the launch's first step sweeps every warp)
         int n_items = a.n_pb * nch;
         int n_swept = a.n_pb;
@@ -295,7 +299,7 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                 float lmax = -INFINITY;
                 for (int w = tid; w < n_w; w += kT) {
                     float lo, hi;
-                    warp_bounds(a, __ldcg(bcur + w), (int)ldcg_u32(&a.nb_cnt[w >> 2]), nch, lo, hi);
+                    warp_bounds(a, __ldcg(bcur + w), __ldcg(acur + w), (int)ldcg_u32(&a.nb_cnt[w >> 2]), nch, lo, hi);
                     lmax = fmaxf(lmax, lo);
                 }
                 for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
@@ -309,12 +313,14 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                     bool act = false;
                     if (w < n_w) {
                         const float4 s = __ldcg(bcur + w);
+                        const double accd = __ldcg(acur + w);
                         const int cb = (int)ldcg_u32(&a.nb_cnt[w >> 2]);
                         float lo, hi;
-                        warp_bounds(a, s, cb, nch, lo, hi);
+                        warp_bounds(a, s, accd, cb, nch, lo, hi);
                         act = hi >= LB;
                         if (!act && blockIdx.x == 0) {
                             bnext[w] = s;
+                            anext[w] = accd;
                             skip_pairs += (unsigned long long)max((int64_t)0, min((int64_t)32, a.n_s - (int64_t)w * 32)) *
                                           (unsigned long long)cb;
                             ++skip_w;
@@ -586,6 +592,7 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                     }
                     if (lane == 0) {
                         const double Mw = km > 0.0 ? sqrt(km) : 0.0;
+                        anext[4 * pb + warp] = 0.0;
                         bnext[4 * pb + warp] = make_float4(__double2float_ru(Mw), __double2float_rd(Mw), 0.0f,
                                                            __double2float_ru(sm * (1.0 + (double)(cnt + 16) * 0x1p-22)));
                     }
@@ -763,7 +770,7 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
             // c_n's own warp has lost the point its maximum was taken at: no
             // lower bound from it until it is swept again (which its infinite
             // bound forces)
-            if (keep_bounds && first_block) bnext[c / 32].z = INFINITY;
+            if (keep_bounds && first_block) anext[c / 32] = INFINITY;
         }
         double yy = 0, yw0 = 0, yw1 = 0, yw2 = 0;
         for (int j = blockIdx.x * 4 + warp; j < n; j += P * 4) {
@@ -882,7 +889,7 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                 const uint32_t *rv = a.rev + (size_t)k * a.n_pb;
                 const float4 xk = ldcg_f4(&a.cdf[k]);
                 for (int q = lane; q < rc; q += 32)
-                    push_bound<BASIS>(a, bnext, (int)ldcg_u32(rv + q), make_float3(xk.x, xk.y, xk.z), inc,
+                    push_bound<BASIS>(a, anext, (int)ldcg_u32(rv + q), make_float3(xk.x, xk.y, xk.z), inc,
                                       invR.hi);
                 continue;
             }
@@ -925,7 +932,7 @@ __global__ void __launch_bounds__(kT, 5) k_greedy_persist(PersistArgs a) {
                 const uint32_t *rv = a.rev + (size_t)k * a.n_pb;
                 const float4 xk = ldcg_f4(&a.cdf[k]);
                 for (int q = lane; q < rc; q += 32)
-                    push_bound<BASIS>(a, bnext, (int)ldcg_u32(rv + q), make_float3(xk.x, xk.y, xk.z), inc,
+                    push_bound<BASIS>(a, anext, (int)ldcg_u32(rv + q), make_float3(xk.x, xk.y, xk.z), inc,
                                       invR.hi);
             }
             if (lane == 0) {
@@ -1036,12 +1043,13 @@ void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas, int max_ste
     a.max_steps = max_steps;
     a.chunk_target = 64;
     if (const char *v = std::getenv("RBFD_SWEEP_CHUNK")) a.chunk_target = std::max(16, std::min(1024, std::atoi(v)));
-    a.prune = (m->opt.prune && m->d_bnd && m->d_wbox && m->n_pb <= a.pfx_max) ? 1 : 0;
+    a.prune = (m->opt.prune && m->d_bnd && m->d_bacc && m->d_wbox && m->n_pb <= a.pfx_max) ? 1 : 0;
     // relative rounding per operation: FP64 2^-53, double-float about 2^-44;
     // a factor 16 of margin on each
     a.err_u = m->opt.precision == RBFD_FP64 ? 0x1p-49f : 0x1p-40f;
     a.S0f = (float)(m->S0 * (1.0 + 0x1p-20));
     a.bnd = m->d_bnd;
+    a.bacc = m->d_bacc;
     a.wbox = m->d_wbox;
     {
         // FP32 rounding of a control-to-box distance: the control's hi part
