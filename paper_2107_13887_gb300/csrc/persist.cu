@@ -1039,9 +1039,12 @@ void persist_run_level(rbfd_mesh *m, double R, double tau, int ctas, int max_ste
     a.pfx_max = kPfxMax;
     if (const char *v = std::getenv("RBFD_TEST_SWEEP_ROUND_ROBIN")) a.pfx_max = std::atoi(v) != 0 ? 0 : kPfxMax;
     // controls per sweep item: shorter items balance the step's tail, longer
-    // ones cost fewer partial sums (RBFD_SWEEP_CHUNK sets it, 16 to 1024)
+    // ones cost fewer partial sums (RBFD_SWEEP_CHUNK sets it, 16 to 1024).
+    // With the pruned sweep a step has few point blocks to sweep, so short
+    // items win: the 60k wing's step took 9.96 / 10.10 / 10.42 / 10.75 s at
+    // 32 / 64 / 96 / 128 controls.
     a.max_steps = max_steps;
-    a.chunk_target = 64;
+    a.chunk_target = 32;
     if (const char *v = std::getenv("RBFD_SWEEP_CHUNK")) a.chunk_target = std::max(16, std::min(1024, std::atoi(v)));
     a.prune = (m->opt.prune && m->d_bnd && m->d_bacc && m->d_wbox && m->n_pb <= a.pfx_max) ? 1 : 0;
     // relative rounding per operation: FP64 2^-53, double-float about 2^-44;
