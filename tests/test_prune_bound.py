@@ -105,3 +105,35 @@ def test_move_bound_holds_and_never_skips_the_argmax():
         acc += bound
         E = E_new
     assert len(ctrl) > 20 and skipped_any  # (the rule skipped warps on this case)
+
+
+def test_move_bound_sum_needs_fp64():
+    """The per-warp move bound is a sum of many atomic additions in any order:
+    a far warp receives small increments against a running sum that may be
+    far larger.  Summed in FP32 they can vanish (each is rounded against the
+    running sum), so the FP32 sum read with the kernel's 2^-8 margin can fall
+    below the exact sum; summed in FP64 (each addition within 2^-53 of the
+    running sum) and read rounded up to FP32 with the same margin, it cannot.
+    """
+    import math
+
+    rng = np.random.default_rng(0)
+    # one large increment (a near control) and a million small ones (far
+    # controls, each under half an FP32 ulp of the running sum)
+    inc = np.concatenate([[1.0], np.full(1_000_000, 1e-8)])
+    exact = math.fsum(inc)
+    s32 = np.cumsum(inc.astype(np.float32), dtype=np.float32)[-1]
+    assert float(s32) * (1 + 2.0 ** -8) < exact  # the FP32 sum is no bound
+    for order in (np.arange(len(inc)), rng.permutation(len(inc))):
+        s64 = np.cumsum(inc[order], dtype=np.float64)[-1]
+        read = np.float32(s64)  # FP32, rounded up
+        if float(read) < s64:
+            read = np.nextafter(read, np.float32(np.inf))
+        read = float(read)
+        assert read * (1 + 2.0 ** -8) >= exact
+        assert abs(s64 - exact) <= len(inc) * 2.0 ** -53 * exact
+    # increments of every size in random order
+    inc = np.exp(rng.uniform(np.log(1e-12), np.log(1.0), 200_000))
+    exact = math.fsum(inc)
+    s64 = np.cumsum(inc[rng.permutation(len(inc))], dtype=np.float64)[-1]
+    assert abs(s64 - exact) <= len(inc) * 2.0 ** -53 * exact
