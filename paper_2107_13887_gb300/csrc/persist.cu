@@ -89,11 +89,12 @@ struct PersistArgs {
     int max_steps;                 // > 0: end the launch after that many steps (st->handoff = 1)
     // pruned sweep (balanced items only), per warp of points w (32 points,
     // w = 4 pb + warp): bnd[parity * 4 n_pb + w] = {M rounded up, M rounded
-    // down, acc, A} in FP32 (every block evaluates every warp's bounds each
+    // down, unused, A} in FP32 (every block evaluates every warp's bounds each
     // step: in FP64 that arithmetic alone took 40 us per step on the FP64
     // pipe), with M the warp's max |E| over unselected points at its last
-    // sweep, acc the bound on how far any |E| of the warp has moved since, A
-    // the largest sum_c phi |alpha_c|_1 at its points then; wbox[2 w], [2 w +
+    // sweep and A the largest sum_c phi |alpha_c|_1 at its points then;
+    // bacc[parity * 4 n_pb + w] = acc, the bound on how far any |E| of the
+    // warp has moved since (a sum of atomic additions, in FP64); wbox[2 w], [2 w +
     // 1] the warp's box in FP32 rounded outward; rev[k * n_pb + i] the point
     // blocks whose list holds control k (rev_cnt[k] of them); err_u the
     // relative rounding of one operation of the sweep's arithmetic, with
@@ -101,7 +102,7 @@ struct PersistArgs {
     int prune;
     float err_u, S0f;
     float4 *bnd;
-    double *bacc;  // [parity * 4 n_pb + w]: the move bound acc, summed in FP64 (the .z of bnd is unused)
+    double *bacc;
     const float4 *wbox;
     float marg;
     uint32_t *rev, *rev_cnt;
